@@ -1,0 +1,215 @@
+/*
+ * aderdg.h -- C ABI of the GB300 (sm_103a) ADER-DG predictor/corrector.
+ *
+ * The library advances hyperbolic systems Q_t + div F(Q) = 0 on periodic
+ * uniform Cartesian meshes with the unlimited ADER discontinuous Galerkin
+ * scheme of Dumbser, Fambri, Tavelli, Bader and Weinzierl (2018):
+ *   - nodal tensor-product basis on N+1 Gauss-Legendre nodes per direction
+ *     (Sec. 2.1),
+ *   - element-local space-time predictor solved by a discrete Picard
+ *     iteration (Sec. 2.2, eq. pde.st2; derivative matrix eq. D_kl),
+ *   - corrector: diagonal mass, volume integral and Rusanov face fluxes on
+ *     the time-averaged predictor (Sec. 2.1, eq. pde.nc.gw2, pc.scheme with
+ *     B = 0, rusanov),
+ *   - CFL time step dt = alpha / sum_d lambda_d^max / dx_d (Sec. 3).
+ *
+ * Conventions shared by every entry point
+ *   - Status: every function returns int; ADERDG_OK (0) on success, a
+ *     negative ADERDG_E_* code on failure, ADERDG_PENDING (> 0) only from
+ *     aderdg_poll.  aderdg_last_error() returns a thread-local message for
+ *     the last failure of the calling thread.  No C++ exception crosses the
+ *     ABI.
+ *   - State layout ("AoS", Sec. 2.2): u[e][s][v], double, variable index v
+ *     fastest, then the spatial node s = sx + n*sy + n^2*sz (n = N+1), then
+ *     the element e = ex + Cx*(ey + Cy*ez).  Node sx of element ex sits at
+ *     x = lo_x + (ex + xi_sx) * dx, xi the Gauss-Legendre nodes of [0,1]
+ *     returned by aderdg_gl_nodes.
+ *   - Memory: "where" = ADERDG_HOST for host pointers, ADERDG_DEVICE for
+ *     device pointers of the current CUDA device.  Host buffers are copied
+ *     before the call returns; device buffers are read on the handle's
+ *     stream and must stay valid until the next aderdg_sync on it.
+ *   - Handles are opaque and owned by the library; all device memory of a
+ *     handle comes from the allocator given at creation (NULL: cudaMalloc)
+ *     and is released by aderdg_destroy.
+ *   - All device work of a handle is issued on its CUDA stream; calls are
+ *     asynchronous unless documented as synchronising.
+ *   - There is no CPU fallback: on a machine without a usable CUDA device,
+ *     aderdg_create fails with ADERDG_E_CUDA.
+ */
+#ifndef ADERDG_H
+#define ADERDG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define ADERDG_OK 0
+#define ADERDG_PENDING 1          /* aderdg_poll: not finished yet */
+#define ADERDG_E_INVAL (-1)       /* bad argument (sizes, N, pde, pointers) */
+#define ADERDG_E_NOMEM (-2)       /* allocation failed / admission impossible */
+#define ADERDG_E_CUDA (-3)        /* CUDA runtime error (message has details) */
+#define ADERDG_E_NONFINITE (-4)   /* a non-finite value appeared in the state */
+#define ADERDG_E_TIMEOUT (-5)     /* a bounded device wait gave up */
+#define ADERDG_E_BUSY (-6)        /* queue full */
+#define ADERDG_E_UNSUPPORTED (-7) /* valid but not compiled (e.g. N too large) */
+#define ADERDG_E_CANCELLED (-8)   /* request cancelled */
+
+/* ---- PDE systems -------------------------------------------------------
+ * ADVECTION   m = 1,   F_d = a_d u, p = (a_x, a_y, a_z)
+ * EULER       m = d+2, Q = (rho, rho v, rho E), ideal gas
+ *             p = (gamma-1)(rho E - rho |v|^2 / 2)  (Sec. 3.1, eq. euler);
+ *             p[0] = gamma
+ * ELASTICITY  m = 9,   Q = (sxx, syy, szz, sxy, syz, sxz, u, v, w),
+ *             velocity-stress form of Sec. 3.2 with alpha = 1 and constant
+ *             material; p = (rho, lambda, mu); d = 3 only                */
+#define ADERDG_PDE_ADVECTION 1
+#define ADERDG_PDE_EULER 2
+#define ADERDG_PDE_ELASTICITY 3
+
+/* ---- precision modes ---------------------------------------------------
+ * FP64        everything in double
+ * MIXED_FP32  predictor, face fluxes and lift in float; the update
+ *             u += dt*(...), the CFL reduction and the totals in double   */
+#define ADERDG_FP64 0
+#define ADERDG_MIXED_FP32 1
+
+#define ADERDG_HOST 0
+#define ADERDG_DEVICE 1
+
+typedef struct {
+    int dim;            /* 2 or 3 */
+    int64_t cells[3];   /* elements per direction (> 0); unused entries ignored */
+    double lo[3], hi[3];/* box; periodic in every direction */
+} aderdg_mesh_t;
+
+typedef struct {
+    int kind;           /* ADERDG_PDE_* */
+    double p[8];        /* parameters, see above */
+} aderdg_pde_t;
+
+/* Optional device allocator (e.g. a framework's caching allocator).
+ * alloc returns a device pointer of at least `bytes` bytes, 256-byte
+ * aligned, or NULL; free releases it. */
+typedef struct {
+    void *(*alloc)(size_t bytes, void *ctx);
+    void (*free)(void *ptr, void *ctx);
+    void *ctx;
+} aderdg_alloc_t;
+
+typedef struct {
+    int precision;              /* ADERDG_FP64 / ADERDG_MIXED_FP32 */
+    int picard_iters;           /* Picard iterations P; 0 -> N+1 */
+    double cfl_alpha;           /* CFL coefficient; 0 -> library default
+                                   (0.9 x the von Neumann limit of the scheme) */
+    void *cuda_stream;          /* cudaStream_t; NULL -> the legacy stream */
+    const aderdg_alloc_t *alloc;/* NULL -> cudaMalloc / cudaFree */
+} aderdg_config_t;
+
+typedef struct aderdg_s aderdg_t;
+
+/* Sizes and cost model of a handle (algorithmic counts per step). */
+typedef struct {
+    int dim, N, nvar, precision, picard_iters;
+    int64_t elements;           /* E */
+    int64_t dofs;               /* E (N+1)^d, the paper's DOF count (Sec. 3.1) */
+    double cfl_alpha;
+    double flops_predictor;     /* algorithmic flops of one predictor launch */
+    double flops_corrector;     /* algorithmic flops of one corrector launch */
+    double bytes_predictor;     /* algorithmic HBM bytes of one predictor launch */
+    double bytes_corrector;     /* algorithmic HBM bytes of one corrector launch */
+    size_t device_bytes;        /* device memory held by the handle */
+} aderdg_info_t;
+
+/* Thread-local message of the last failure (never NULL). */
+const char *aderdg_last_error(void);
+
+/* ABI version (major*10000 + minor*100 + patch). */
+int aderdg_version(void);
+
+/* The library's N+1 Gauss-Legendre nodes x[] and weights w[] on [0,1]
+ * (Sec. 2.1), increasing.  1 <= N <= 9.  Host pointers, n = N+1 entries. */
+int aderdg_gl_nodes(int N, double *x, double *w);
+
+/* Default CFL coefficient for degree N (0.9 x the von Neumann limit of the
+ * scheme for 1D linear advection; the paper's Sec. 3 only bounds it by
+ * 1/(2N+1), and 0.9/(2N+1) is unstable for N >= 3). */
+double aderdg_default_alpha(int N);
+
+/* Create a solver for one periodic mesh, degree N, nVar variables.
+ * Supported: d = 2 with N = 1..7 for ADVECTION and EULER; d = 3 with
+ * N = 1..4 for ADVECTION, EULER and ELASTICITY.  nVar must equal the PDE's
+ * m.  The state is zero and t = 0 until aderdg_set_state.  On failure *out
+ * is set to NULL. */
+int aderdg_create(const aderdg_mesh_t *mesh, int N, int nVar, const aderdg_pde_t *pde,
+                  const aderdg_config_t *cfg, aderdg_t **out);
+
+/* Release all device memory of the handle (synchronises its stream). */
+int aderdg_destroy(aderdg_t *h);
+
+int aderdg_get_info(const aderdg_t *h, aderdg_info_t *info);
+
+/* Upload a state (layout above, E n^d m doubles) at time t; computes the
+ * wave-speed maxima the next CFL step needs and clears the step counter
+ * and the error flags. */
+int aderdg_set_state(aderdg_t *h, const double *u, int where, double t);
+
+/* Download the state.  Synchronising.  t and step may be NULL.  Returns
+ * ADERDG_E_NONFINITE if a non-finite value was produced since set_state. */
+int aderdg_get_state(aderdg_t *h, double *u, int where, double *t, int64_t *step);
+
+/* Space-time predictor (Sec. 2.2) of every element with time step dt:
+ * Picard iterations, time averages, volume integral and face traces (kept
+ * on the device for aderdg_corrector).  dt > 0. */
+int aderdg_predictor(aderdg_t *h, double dt);
+
+/* Corrector (eq. pde.nc.gw2) with time step dt: Rusanov fluxes on every
+ * face from the predictor's traces, surface lift, u += dt*(volume -
+ * surface), and the new wave-speed maxima.  Must follow aderdg_predictor
+ * with the same dt.  Does not advance t. */
+int aderdg_corrector(aderdg_t *h, double dt);
+
+/* Predictor outputs in the oracle's layout, for checking:
+ *   volume[e][s][v]               (E n^d m)    volume term / diagonal mass
+ *   qface[e][d][side][p][v],
+ *   fface[e][d][side][p][v]       (E d 2 n^(d-1) m) time-averaged traces,
+ * side 0 = face xi_d = 0, p = the other spatial indices in increasing order.
+ * Any pointer may be NULL.  Synchronising. */
+int aderdg_get_predictor_outputs(aderdg_t *h, double *volume, double *qface, double *fface,
+                                 int where);
+
+/* One full step: dt from the CFL condition on the current state, clipped so
+ * that t does not pass t_end (the clipped step sets t = t_end exactly),
+ * then predictor and corrector.  No step is taken once t >= t_end.  dt is
+ * computed and kept on the device; if dt_taken is non-NULL the call
+ * synchronises and returns it (0 if no step was taken). */
+int aderdg_step(aderdg_t *h, double t_end, double *dt_taken);
+
+/* Steps until t_end or max_steps, as a replayed CUDA graph of steps;
+ * synchronises every few steps to read the device time. */
+int aderdg_advance(aderdg_t *h, double t_end, int64_t max_steps);
+
+/* The CFL time step of the current state (synchronising). */
+int aderdg_cfl_dt(aderdg_t *h, double *dt);
+
+/* Conserved totals M_v = sum_e |Omega_e| sum_s w_s u[e][s][v] (nVar doubles,
+ * host), by a fixed-order reduction (deterministic).  Synchronising. */
+int aderdg_mass(aderdg_t *h, double *per_var);
+
+/* Wait for all work of the handle; reports a pending device error flag. */
+int aderdg_sync(aderdg_t *h);
+
+/* Kernel timing for measurement tools.  With enable != 0, every step
+ * records CUDA events on the handle's stream around its predictor and
+ * corrector launches; aderdg_profile_read waits for the most recent step
+ * and returns the two durations in milliseconds.  Disabled by default. */
+int aderdg_profile(aderdg_t *h, int enable);
+int aderdg_profile_read(aderdg_t *h, float *ms_predictor, float *ms_corrector);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ADERDG_H */

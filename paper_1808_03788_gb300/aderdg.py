@@ -1,0 +1,386 @@
+"""ctypes binding of libaderdg.so with the names of include/aderdg.h.
+
+Argument marshalling only: every step of the ADER-DG path runs in the CUDA
+kernels of the library.  PyTorch provides device memory (through the
+library's allocator hook, so buffers come from torch's caching allocator)
+and streams.  There is no CPU fallback: if the library cannot be built or
+loaded, or no CUDA device is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+ADERDG_OK = 0
+ADERDG_PENDING = 1
+ADERDG_E_INVAL = -1
+ADERDG_E_NOMEM = -2
+ADERDG_E_CUDA = -3
+ADERDG_E_NONFINITE = -4
+ADERDG_E_TIMEOUT = -5
+ADERDG_E_BUSY = -6
+ADERDG_E_UNSUPPORTED = -7
+ADERDG_E_CANCELLED = -8
+
+ADERDG_PDE_ADVECTION, ADERDG_PDE_EULER, ADERDG_PDE_ELASTICITY = 1, 2, 3
+ADERDG_FP64, ADERDG_MIXED_FP32 = 0, 1
+ADERDG_HOST, ADERDG_DEVICE = 0, 1
+
+
+class AderdgError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("aderdg error %d: %s" % (code, msg))
+        self.code = code
+
+
+class aderdg_mesh_t(C.Structure):
+    _fields_ = [("dim", C.c_int), ("cells", C.c_int64 * 3), ("lo", C.c_double * 3), ("hi", C.c_double * 3)]
+
+
+class aderdg_pde_t(C.Structure):
+    _fields_ = [("kind", C.c_int), ("p", C.c_double * 8)]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+class aderdg_alloc_t(C.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("ctx", C.c_void_p)]
+
+
+class aderdg_config_t(C.Structure):
+    _fields_ = [("precision", C.c_int), ("picard_iters", C.c_int), ("cfl_alpha", C.c_double),
+                ("cuda_stream", C.c_void_p), ("alloc", C.POINTER(aderdg_alloc_t))]
+
+
+class aderdg_info_t(C.Structure):
+    _fields_ = [("dim", C.c_int), ("N", C.c_int), ("nvar", C.c_int), ("precision", C.c_int),
+                ("picard_iters", C.c_int), ("elements", C.c_int64), ("dofs", C.c_int64),
+                ("cfl_alpha", C.c_double), ("flops_predictor", C.c_double),
+                ("flops_corrector", C.c_double), ("bytes_predictor", C.c_double),
+                ("bytes_corrector", C.c_double), ("device_bytes", C.c_size_t)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+_DP = C.POINTER(C.c_double)
+_H = C.c_void_p
+
+# name -> (restype, argtypes); mirrors include/aderdg.h
+_SIGS = {
+    "aderdg_last_error": (C.c_char_p, []),
+    "aderdg_version": (C.c_int, []),
+    "aderdg_gl_nodes": (C.c_int, [C.c_int, _DP, _DP]),
+    "aderdg_default_alpha": (C.c_double, [C.c_int]),
+    "aderdg_create": (C.c_int, [C.POINTER(aderdg_mesh_t), C.c_int, C.c_int, C.POINTER(aderdg_pde_t),
+                                C.POINTER(aderdg_config_t), C.POINTER(_H)]),
+    "aderdg_destroy": (C.c_int, [_H]),
+    "aderdg_get_info": (C.c_int, [_H, C.POINTER(aderdg_info_t)]),
+    "aderdg_set_state": (C.c_int, [_H, C.c_void_p, C.c_int, C.c_double]),
+    "aderdg_get_state": (C.c_int, [_H, C.c_void_p, C.c_int, _DP, C.POINTER(C.c_int64)]),
+    "aderdg_predictor": (C.c_int, [_H, C.c_double]),
+    "aderdg_corrector": (C.c_int, [_H, C.c_double]),
+    "aderdg_get_predictor_outputs": (C.c_int, [_H, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    "aderdg_step": (C.c_int, [_H, C.c_double, _DP]),
+    "aderdg_advance": (C.c_int, [_H, C.c_double, C.c_int64]),
+    "aderdg_cfl_dt": (C.c_int, [_H, _DP]),
+    "aderdg_mass": (C.c_int, [_H, _DP]),
+    "aderdg_sync": (C.c_int, [_H]),
+    "aderdg_profile": (C.c_int, [_H, C.c_int]),
+    "aderdg_profile_read": (C.c_int, [_H, C.POINTER(C.c_float), C.POINTER(C.c_float)]),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Build (if stale) and load libaderdg.so; raises if that is impossible."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            L = C.CDLL(path)
+            for name, (res, args) in _SIGS.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc < 0:
+        raise AderdgError(rc, load().aderdg_last_error().decode())
+    return rc
+
+
+# ---- thin functions with the C names ------------------------------------------
+
+def aderdg_version() -> int:
+    return load().aderdg_version()
+
+
+def aderdg_gl_nodes(N: int):
+    x = np.zeros(N + 1)
+    w = np.zeros(N + 1)
+    _check(load().aderdg_gl_nodes(N, x.ctypes.data_as(_DP), w.ctypes.data_as(_DP)))
+    return x, w
+
+
+def aderdg_default_alpha(N: int) -> float:
+    return load().aderdg_default_alpha(N)
+
+
+def nvar(pde: int, dim: int) -> int:
+    return {1: 1, 2: dim + 2, 3: 9}[pde]
+
+
+class _TorchAllocator:
+    """aderdg_alloc_t backed by torch's CUDA caching allocator."""
+
+    def __init__(self):
+        import torch
+        self._torch = torch
+        self._blocks = {}
+        self._alloc = ALLOC_FN(self._do_alloc)
+        self._free = FREE_FN(self._do_free)
+        self.struct = aderdg_alloc_t(self._alloc, self._free, None)
+
+    def _do_alloc(self, nbytes, ctx):
+        try:
+            t = self._torch.empty(int(nbytes), dtype=self._torch.uint8, device="cuda")
+        except Exception:
+            return None
+        p = t.data_ptr()
+        self._blocks[p] = t
+        return p
+
+    def _do_free(self, ptr, ctx):
+        self._blocks.pop(ptr, None)
+
+
+class Solver:
+    """One ADER-DG solve on a periodic Cartesian mesh (a handle of the C ABI).
+
+    u layout: [E, n^d, m] float64, variable fastest, x-fastest nodes,
+    x-fastest elements (include/aderdg.h)."""
+
+    def __init__(self, pde: int, dim: int, cells, lo, hi, N: int, params=(),
+                 precision: int = ADERDG_FP64, picard: int = 0, alpha: float = 0.0,
+                 stream=None, torch_alloc: bool = True):
+        L = load()
+        self.dim, self.N, self.pde = dim, N, pde
+        self.m = nvar(pde, dim)
+        self.n = N + 1
+        self.ns = self.n ** dim
+        self.cells = tuple(int(c) for c in cells[:dim])
+        self.E = int(np.prod(self.cells))
+        mesh = aderdg_mesh_t()
+        mesh.dim = dim
+        for d in range(3):
+            mesh.cells[d] = self.cells[d] if d < dim else 1
+            mesh.lo[d] = float(lo[d]) if d < dim else 0.0
+            mesh.hi[d] = float(hi[d]) if d < dim else 1.0
+        p = aderdg_pde_t()
+        p.kind = pde
+        for i, v in enumerate(params):
+            p.p[i] = float(v)
+        cfg = aderdg_config_t()
+        cfg.precision = precision
+        cfg.picard_iters = picard
+        cfg.cfl_alpha = alpha
+        self._alloc = None
+        if stream is not None:
+            cfg.cuda_stream = C.c_void_p(int(stream))
+        if torch_alloc:
+            self._alloc = _TorchAllocator()
+            cfg.alloc = C.pointer(self._alloc.struct)
+        self._h = _H()
+        _check(L.aderdg_create(C.byref(mesh), N, self.m, C.byref(p), C.byref(cfg), C.byref(self._h)))
+        self._L = L
+
+    # lifetime
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._L.aderdg_destroy(self._h)
+            self._h = _H()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    # state
+    def set_state(self, u, t: float = 0.0):
+        if hasattr(u, "data_ptr"):  # torch tensor on the device
+            assert u.dtype.itemsize == 8 and u.is_contiguous() and u.numel() == self.E * self.ns * self.m
+            _check(self._L.aderdg_set_state(self._h, C.c_void_p(u.data_ptr()), ADERDG_DEVICE, float(t)))
+            return
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        assert u.size == self.E * self.ns * self.m, (u.shape, self.E, self.ns, self.m)
+        _check(self._L.aderdg_set_state(self._h, u.ctypes.data, ADERDG_HOST, float(t)))
+
+    def get_state(self, out=None, check=True):
+        """Returns (u [E, n^d, m], t, step).  out may be a device tensor."""
+        t = C.c_double(0)
+        k = C.c_int64(0)
+        if out is not None and hasattr(out, "data_ptr"):
+            assert out.is_cuda and out.is_contiguous() and out.numel() * out.element_size() == self.E * self.ns * self.m * 8
+            rc = self._L.aderdg_get_state(self._h, C.c_void_p(out.data_ptr()), ADERDG_DEVICE, C.byref(t), C.byref(k))
+            u = out
+        elif out is not None:  # host numpy array (e.g. a view of pinned memory)
+            assert out.dtype == np.float64 and out.flags.c_contiguous and out.size == self.E * self.ns * self.m
+            rc = self._L.aderdg_get_state(self._h, out.ctypes.data, ADERDG_HOST, C.byref(t), C.byref(k))
+            u = out
+        else:
+            u = np.empty((self.E, self.ns, self.m))
+            rc = self._L.aderdg_get_state(self._h, u.ctypes.data, ADERDG_HOST, C.byref(t), C.byref(k))
+        if check:
+            _check(rc)
+        return u, t.value, k.value
+
+    # the hot path
+    def predictor(self, dt: float):
+        _check(self._L.aderdg_predictor(self._h, float(dt)))
+
+    def corrector(self, dt: float):
+        _check(self._L.aderdg_corrector(self._h, float(dt)))
+
+    def predictor_outputs(self):
+        nf = self.n ** (self.dim - 1)
+        V = np.empty((self.E, self.ns, self.m))
+        qf = np.empty((self.E, self.dim, 2, nf, self.m))
+        ff = np.empty((self.E, self.dim, 2, nf, self.m))
+        _check(self._L.aderdg_get_predictor_outputs(self._h, V.ctypes.data, qf.ctypes.data, ff.ctypes.data,
+                                                    ADERDG_HOST))
+        return V, qf, ff
+
+    def step(self, t_end: float, sync_dt: bool = False):
+        if sync_dt:
+            dt = C.c_double(0)
+            _check(self._L.aderdg_step(self._h, float(t_end), C.byref(dt)))
+            return dt.value
+        _check(self._L.aderdg_step(self._h, float(t_end), None))
+        return None
+
+    def advance(self, t_end: float, max_steps: int = 2 ** 62):
+        _check(self._L.aderdg_advance(self._h, float(t_end), int(max_steps)))
+
+    def cfl_dt(self) -> float:
+        dt = C.c_double(0)
+        _check(self._L.aderdg_cfl_dt(self._h, C.byref(dt)))
+        return dt.value
+
+    def mass(self) -> np.ndarray:
+        M = np.zeros(self.m)
+        _check(self._L.aderdg_mass(self._h, M.ctypes.data_as(_DP)))
+        return M
+
+    def sync(self):
+        _check(self._L.aderdg_sync(self._h))
+
+    def profile(self, enable: bool = True):
+        _check(self._L.aderdg_profile(self._h, int(enable)))
+
+    def profile_read(self):
+        a, b = C.c_float(0), C.c_float(0)
+        _check(self._L.aderdg_profile_read(self._h, C.byref(a), C.byref(b)))
+        return a.value, b.value
+
+    def info(self) -> dict:
+        i = aderdg_info_t()
+        _check(self._L.aderdg_get_info(self._h, C.byref(i)))
+        return {k: getattr(i, k) for k, _ in aderdg_info_t._fields_}
+
+    def node_coords(self, lo, hi) -> np.ndarray:
+        """Physical coordinates of every node from the library's GL nodes."""
+        x, _ = aderdg_gl_nodes(self.N)
+        n, dim = self.n, self.dim
+        X = np.empty((self.E, self.ns, dim))
+        idx = np.indices(self.cells[::-1]).reshape(dim, -1)[::-1]  # x fastest
+        sd = np.indices((n,) * dim).reshape(dim, -1)[::-1]
+        for d in range(dim):
+            h = (hi[d] - lo[d]) / self.cells[d]
+            X[:, :, d] = lo[d] + (idx[d][:, None] + x[sd[d]][None, :]) * h
+        return X
+
+
+# functions with the C names, on Solver handles
+def aderdg_create(pde, dim, cells, lo, hi, N, params=(), **kw) -> Solver:
+    return Solver(pde, dim, cells, lo, hi, N, params, **kw)
+
+
+def aderdg_destroy(s: Solver):
+    s.close()
+
+
+def aderdg_set_state(s: Solver, u, t=0.0):
+    s.set_state(u, t)
+
+
+def aderdg_get_state(s: Solver):
+    return s.get_state()
+
+
+def aderdg_predictor(s: Solver, dt):
+    s.predictor(dt)
+
+
+def aderdg_corrector(s: Solver, dt):
+    s.corrector(dt)
+
+
+def aderdg_get_predictor_outputs(s: Solver):
+    return s.predictor_outputs()
+
+
+def aderdg_step(s: Solver, t_end, sync_dt=False):
+    return s.step(t_end, sync_dt)
+
+
+def aderdg_advance(s: Solver, t_end, max_steps=2 ** 62):
+    s.advance(t_end, max_steps)
+
+
+def aderdg_cfl_dt(s: Solver):
+    return s.cfl_dt()
+
+
+def aderdg_mass(s: Solver):
+    return s.mass()
+
+
+def aderdg_sync(s: Solver):
+    s.sync()
+
+
+def aderdg_get_info(s: Solver):
+    return s.info()
+
+
+def aderdg_profile(s: Solver, enable=True):
+    s.profile(enable)
+
+
+def aderdg_profile_read(s: Solver):
+    return s.profile_read()

@@ -1,0 +1,149 @@
+// Host-side construction of the 1D nodal basis of the scheme (Sec. 2.1):
+// Gauss-Legendre nodes and weights on [0,1] and the small operators the
+// kernels use.  Methods (chosen for robustness in double precision):
+//   - nodes: eigenvalues of the symmetric tridiagonal Jacobi matrix of the
+//     Legendre polynomials (Golub-Welsch), found by Sturm-sequence bisection
+//   - weights: w = 2 / ((1 - y^2) P_n'(y)^2) on [-1,1], halved for [0,1]
+//   - Lagrange derivative matrix and boundary values: barycentric formulas
+//   - K1 = F1 F1^T - (W Dhat)^T inverted by Gauss-Jordan elimination with
+//     partial pivoting.
+#include <cmath>
+#include <cstring>
+
+#include "basis.h"
+
+namespace aderdg {
+
+namespace {
+
+// Number of eigenvalues of the n x n Jacobi matrix (zero diagonal,
+// off-diagonal b_k = k / sqrt(4k^2 - 1)) that are smaller than x.
+int sturm_count(int n, double x)
+{
+    int count = 0;
+    double q = -x;  // d_1 - x with d = 0
+    if (q < 0) ++count;
+    for (int k = 1; k < n; ++k) {
+        const double b2 = double(k) * k / (4.0 * k * k - 1.0);
+        if (q == 0.0) q = 1e-300;
+        q = -x - b2 / q;
+        if (q < 0) ++count;
+    }
+    return count;
+}
+
+void legendre_and_derivative(int n, double y, double &p, double &dp)
+{
+    double pm1 = 1.0, pc = y;
+    if (n == 0) { p = 1.0; dp = 0.0; return; }
+    for (int k = 2; k <= n; ++k) {
+        const double pn = ((2.0 * k - 1.0) * y * pc - (k - 1.0) * pm1) / k;
+        pm1 = pc;
+        pc = pn;
+    }
+    p = pc;
+    dp = n * (pm1 - y * pc) / (1.0 - y * y);
+}
+
+}  // namespace
+
+int gauss_legendre01(int n, double *x, double *w)
+{
+    if (n < 1 || n > 16) return -1;
+    for (int k = 0; k < n; ++k) {
+        // k-th smallest eigenvalue in (-1, 1): bisection on the Sturm count
+        double lo = -1.0, hi = 1.0;
+        for (int it = 0; it < 200 && hi - lo > 0.0; ++it) {
+            const double mid = 0.5 * (lo + hi);
+            if (mid == lo || mid == hi) break;
+            if (sturm_count(n, mid) > k) hi = mid; else lo = mid;
+        }
+        const double y = 0.5 * (lo + hi);
+        double p, dp;
+        legendre_and_derivative(n, y, p, dp);
+        x[k] = 0.5 * (1.0 + y);
+        w[k] = 1.0 / ((1.0 - y * y) * dp * dp);
+    }
+    return 0;
+}
+
+int build_basis(int N, Basis &b)
+{
+    const int n = N + 1;
+    if (n < 1 || n > NMAX) return -1;
+    std::memset(&b, 0, sizeof(b));
+    b.n = n;
+    double x[NMAX], bw[NMAX];
+    if (gauss_legendre01(n, x, b.w)) return -1;
+    // barycentric weights bw_k = 1 / prod_{j != k} (x_k - x_j)
+    for (int k = 0; k < n; ++k) {
+        double prod = 1.0;
+        for (int j = 0; j < n; ++j)
+            if (j != k) prod *= (x[k] - x[j]);
+        bw[k] = 1.0 / prod;
+    }
+    // Dhat[j][k] = (bw_k / bw_j) / (x_j - x_k), diagonal = - row sum
+    for (int j = 0; j < n; ++j) {
+        double diag = 0.0;
+        for (int k = 0; k < n; ++k) {
+            if (k == j) continue;
+            const double v = (bw[k] / bw[j]) / (x[j] - x[k]);
+            b.D[j * n + k] = v;
+            diag -= v;
+        }
+        b.D[j * n + j] = diag;
+    }
+    // boundary values by the barycentric formula of the second kind
+    for (int side = 0; side < 2; ++side) {
+        const double xi = side ? 1.0 : 0.0;
+        double den = 0.0, t[NMAX];
+        for (int k = 0; k < n; ++k) { t[k] = bw[k] / (xi - x[k]); den += t[k]; }
+        double *phi = side ? b.F1 : b.F0;
+        for (int k = 0; k < n; ++k) phi[k] = t[k] / den;
+    }
+    for (int k = 0; k < n; ++k) b.inv_w[k] = 1.0 / b.w[k];
+    // Kw[k][j] = w_j Dhat[j][k] / w_k
+    for (int k = 0; k < n; ++k)
+        for (int j = 0; j < n; ++j) b.Kw[k * n + j] = b.w[j] * b.D[j * n + k] / b.w[k];
+    // K1[k][l] = F1_k F1_l - w_l Dhat[l][k]; invert by Gauss-Jordan
+    double A[NMAX][2 * NMAX];
+    for (int k = 0; k < n; ++k) {
+        for (int l = 0; l < n; ++l) {
+            A[k][l] = b.F1[k] * b.F1[l] - b.w[l] * b.D[l * n + k];
+            A[k][n + l] = (k == l) ? 1.0 : 0.0;
+        }
+    }
+    for (int c = 0; c < n; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < n; ++r)
+            if (std::fabs(A[r][c]) > std::fabs(A[piv][c])) piv = r;
+        if (A[piv][c] == 0.0) return -2;
+        if (piv != c)
+            for (int j = 0; j < 2 * n; ++j) { double t = A[c][j]; A[c][j] = A[piv][j]; A[piv][j] = t; }
+        const double ip = 1.0 / A[c][c];
+        for (int j = 0; j < 2 * n; ++j) A[c][j] *= ip;
+        for (int r = 0; r < n; ++r) {
+            if (r == c) continue;
+            const double f = A[r][c];
+            if (f == 0.0) continue;
+            for (int j = 0; j < 2 * n; ++j) A[r][j] -= f * A[c][j];
+        }
+    }
+    // iK1W = K1^{-1} diag(w)
+    for (int t = 0; t < n; ++t)
+        for (int tp = 0; tp < n; ++tp) b.iK1W[t * n + tp] = A[t][n + tp] * b.w[tp];
+    return 0;
+}
+
+// 0.9 x the von Neumann stability limit of the scheme for 1D linear
+// advection (limits 0.3335, 0.1709, 0.1040, 0.0699, 0.0501, 0.0377, 0.0294,
+// 0.0236, 0.0193 for N = 1..9); the paper bounds alpha by 1/(2N+1) only.
+double default_alpha(int N)
+{
+    static const double a[10] = {0.9, 0.3001, 0.1538, 0.0936, 0.0629,
+                                 0.0451, 0.0339, 0.0265, 0.0212, 0.0174};
+    if (N >= 0 && N <= 9) return a[N];
+    return 0.5 / (2.0 * N + 1.0);
+}
+
+}  // namespace aderdg

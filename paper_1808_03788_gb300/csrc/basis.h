@@ -1,0 +1,9 @@
+// Host-side basis construction (see basis.cpp).
+#pragma once
+#include "common.cuh"
+
+namespace aderdg {
+int gauss_legendre01(int n, double *x, double *w);
+int build_basis(int N, Basis &b);
+double default_alpha(int N);
+}  // namespace aderdg

@@ -1,0 +1,208 @@
+// Shared device-side definitions of the ADER-DG library: the 1D basis
+// passed to every kernel, the per-solve device control block, the PDE
+// functions and the kernel parameter block.
+//
+// Notation (Dumbser et al. 2018, Sec. 2.1-2.2): n = N+1 Gauss-Legendre
+// nodes xi_k and weights w_k on [0,1]; Lagrange basis phi_k;
+//   Dhat[j][k] = phi_k'(xi_j)          nodal derivative (eq. D_kl times h)
+//   Kw[k][j]   = w_j Dhat[j][k] / w_k   volume-integral operator divided by
+//                                       the diagonal mass (eq. pde.nc.gw2)
+//   iK1W       = K1^{-1} diag(w),  K1 = F1 F1^T - (W Dhat)^T   (eq. pde.st2)
+//   F0[k] = phi_k(0), F1[k] = phi_k(1).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace aderdg {
+
+constexpr int NMAX = 8;  // largest n = N+1 compiled
+
+struct Basis {
+    int n;
+    double w[NMAX], F0[NMAX], F1[NMAX], inv_w[NMAX];
+    double D[NMAX * NMAX];     // Dhat, row-major [j][k]
+    double Kw[NMAX * NMAX];    // [k][j]
+    double iK1W[NMAX * NMAX];  // [t][t']
+};
+
+// Per-solve control block in device memory.  The corrector accumulates the
+// wave-speed maxima of the new state into lam_acc (bit patterns of
+// non-negative doubles, so integer max == double max); the dt kernel turns
+// them into the next CFL step.
+enum : unsigned { FLAG_NONFINITE = 1u, FLAG_DONE = 2u, FLAG_TIMEOUT = 4u };
+
+struct Control {
+    double t;          // time of the state after the step in flight
+    double t_end;
+    double dt;         // dt of the step in flight (0: no step)
+    double alpha;
+    double inv_dx[3];
+    int dim;
+    int pad0;
+    unsigned long long lam_acc[3];  // max |lambda_d| of the current state
+    double lam_used[3];             // maxima the last dt was computed from
+    long long step;
+    unsigned int flags;
+    unsigned int pad1;
+};
+
+struct PdeParams {
+    double p[8];
+};
+
+// Kernel parameter block (passed by value).
+struct KParams {
+    long long E;
+    int cells[3];
+    int picard;
+    double inv_dx[3];
+    const double *u;   // state u^n            [E][NS][M]
+    double *u_out;     // state u^{n+1} (may alias u)
+    void *V;           // volume term          [E][NS][M] of T
+    void *tr;          // trace records        [E][DIM][2][NF][RS] of T
+    Control *ctl;
+    double dt_arg;
+    int use_ctl_dt;    // 1: dt from ctl->dt (device-side CFL), 0: dt_arg
+    int pad;
+    PdeParams pde;
+    Basis b;
+};
+
+__host__ __device__ constexpr int ipow(int b, int e)
+{
+    int r = 1;
+    for (int i = 0; i < e; ++i) r *= b;
+    return r;
+}
+__host__ __device__ constexpr int round_up(int a, int b) { return (a + b - 1) / b * b; }
+
+// ---------------------------------------------------------------------------
+// PDE functions.  flux(): all DIM flux components F_d(q) at one point;
+// max_eig(): largest |eigenvalue| of dF_d/dQ.
+// ---------------------------------------------------------------------------
+
+// Linear advection F_d = a_d u.
+template <int DIM>
+struct Advection {
+    static constexpr int M = 1;
+    static constexpr int KIND = 1;
+    static constexpr int FLUX_FLOPS = DIM;        // per point, all directions
+    static constexpr int EIG_FLOPS = 0;
+    template <typename T>
+    __device__ __forceinline__ static void flux(const PdeParams &P, const T *q, T (*f)[M]) {
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) f[d][0] = T(P.p[d]) * q[0];
+    }
+    template <typename T>
+    __device__ __forceinline__ static T max_eig(const PdeParams &P, const T *, int d) {
+        return fabs(T(P.p[d]));
+    }
+};
+
+// Euler equations (Sec. 3.1, eq. euler), ideal gas.
+template <int DIM>
+struct Euler {
+    static constexpr int M = DIM + 2;
+    static constexpr int KIND = 2;
+    // 1 reciprocal, DIM products for v, DIM FMA + 2 for p, per direction:
+    // DIM FMA/products for momentum + 1 add for pressure + 2 for energy
+    static constexpr int FLUX_FLOPS = 1 + DIM + 2 * DIM + 3 + DIM * (2 * DIM + 3);
+    static constexpr int EIG_FLOPS = 2 * DIM + 8;
+    template <typename T>
+    __device__ __forceinline__ static void flux(const PdeParams &P, const T *q, T (*f)[M]) {
+        const T gm1 = T(P.p[0] - 1.0);
+        const T ir = T(1) / q[0];
+        T v[DIM];
+        T kin = T(0);
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) { v[k] = q[1 + k] * ir; kin += q[1 + k] * v[k]; }
+        const T E = q[DIM + 1];
+        const T p = gm1 * (E - T(0.5) * kin);
+        const T Ep = E + p;
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) {
+            f[d][0] = q[1 + d];
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) f[d][1 + k] = q[1 + k] * v[d] + (k == d ? p : T(0));
+            f[d][DIM + 1] = v[d] * Ep;
+        }
+    }
+    template <typename T>
+    __device__ __forceinline__ static T max_eig(const PdeParams &P, const T *q, int d) {
+        const T g = T(P.p[0]);
+        const T ir = T(1) / q[0];
+        T kin = T(0);
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) kin += q[1 + k] * q[1 + k];
+        const T p = (g - T(1)) * (q[DIM + 1] - T(0.5) * kin * ir);
+        return fabs(q[1 + d] * ir) + sqrt(g * p * ir);
+    }
+};
+
+// Velocity-stress linear elasticity (Sec. 3.2 with alpha = 1, constant
+// rho, lambda, mu): Q = (sxx, syy, szz, sxy, syz, sxz, u, v, w).
+struct Elastic3 {
+    static constexpr int M = 9;
+    static constexpr int KIND = 3;
+    static constexpr int FLUX_FLOPS = 3 * 9;
+    static constexpr int EIG_FLOPS = 0;
+    template <typename T>
+    __device__ __forceinline__ static void flux(const PdeParams &P, const T *q, T (*f)[M]) {
+        const T irho = T(1.0 / P.p[0]);
+        const T lam = T(P.p[1]), mu = T(P.p[2]);
+        const T l2m = T(P.p[1] + 2.0 * P.p[2]);
+        const T u = q[6], v = q[7], w = q[8];
+        // x
+        f[0][0] = -l2m * u; f[0][1] = -lam * u; f[0][2] = -lam * u;
+        f[0][3] = -mu * v;  f[0][4] = T(0);     f[0][5] = -mu * w;
+        f[0][6] = -q[0] * irho; f[0][7] = -q[3] * irho; f[0][8] = -q[5] * irho;
+        // y
+        f[1][0] = -lam * v; f[1][1] = -l2m * v; f[1][2] = -lam * v;
+        f[1][3] = -mu * u;  f[1][4] = -mu * w;  f[1][5] = T(0);
+        f[1][6] = -q[3] * irho; f[1][7] = -q[1] * irho; f[1][8] = -q[4] * irho;
+        // z
+        f[2][0] = -lam * w; f[2][1] = -lam * w; f[2][2] = -l2m * w;
+        f[2][3] = T(0);     f[2][4] = -mu * v;  f[2][5] = -mu * u;
+        f[2][6] = -q[5] * irho; f[2][7] = -q[4] * irho; f[2][8] = -q[2] * irho;
+    }
+    template <typename T>
+    __device__ __forceinline__ static T max_eig(const PdeParams &P, const T *, int) {
+        return T(sqrt((P.p[1] + 2.0 * P.p[2]) / P.p[0]));
+    }
+};
+
+// Launch geometry of the per-element kernels.
+template <class PDE, int DIM, int N>
+struct Geom {
+    static constexpr int n = N + 1;
+    static constexpr int M = PDE::M;
+    static constexpr int NS = ipow(n, DIM);        // spatial nodes
+    static constexpr int NST = NS * n;             // space-time nodes
+    static constexpr int NF = ipow(n, DIM - 1);    // nodes per face
+    static constexpr int RS = 2 * M + 2;           // trace record: q(M) F(M) lambda pad
+    static constexpr int NREC = DIM * 2 * NF;      // records per element
+    // predictor: one thread per space-time node
+    static constexpr int P_TPE = round_up(NST, 32);
+    static constexpr int P_EPB = P_TPE >= 256 ? 1 : 256 / P_TPE;
+    static constexpr int P_THREADS = P_TPE * P_EPB;
+    // corrector: one thread per spatial node (at least a warp)
+    static constexpr int C_TPE = round_up(NS, 32);
+    static constexpr int C_EPB = C_TPE >= 256 ? 1 : 256 / C_TPE;
+    static constexpr int C_THREADS = C_TPE * C_EPB;
+};
+
+// Host-visible description of the compiled kernels of one (PDE, d, N, precision).
+struct KernelSet {
+    void (*predictor)(KParams);
+    int pred_threads, pred_epb;
+    size_t pred_smem;
+    void (*corrector)(KParams);
+    int corr_threads, corr_epb;
+    size_t corr_smem;
+    void (*cfl)(KParams);
+    int nvar, rs, elem_bytes;  // elem_bytes = sizeof(T)
+    int flux_flops, eig_flops;  // per point, for the cost model
+};
+
+}  // namespace aderdg

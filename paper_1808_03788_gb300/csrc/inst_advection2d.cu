@@ -1,0 +1,23 @@
+// Kernel instantiations for 2D linear advection, N = 1..7.
+#include "kernels.cuh"
+
+namespace aderdg {
+
+const KernelSet *ks_advection2d(int N, int prec)
+{
+#define ADERDG_CASE(NN) \
+    case NN: return prec ? &KS<Advection<2>, 2, NN, float>::value : &KS<Advection<2>, 2, NN, double>::value;
+    switch (N) {
+        ADERDG_CASE(1)
+        ADERDG_CASE(2)
+        ADERDG_CASE(3)
+        ADERDG_CASE(4)
+        ADERDG_CASE(5)
+        ADERDG_CASE(6)
+        ADERDG_CASE(7)
+    default: return nullptr;
+    }
+#undef ADERDG_CASE
+}
+
+}  // namespace aderdg

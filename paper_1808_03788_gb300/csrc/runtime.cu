@@ -1,0 +1,710 @@
+// Solver runtime behind the C ABI of include/aderdg.h: handle creation,
+// device buffers, the per-step launch sequence (dt -> predictor ->
+// corrector), CUDA-graph replay for multi-step advances, and the small
+// generic kernels (CFL step, conserved totals, trace unpacking).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include <cuda_runtime.h>
+
+#include "../../include/aderdg.h"
+#include "basis.h"
+#include "common.cuh"
+
+namespace aderdg {
+const KernelSet *ks_advection2d(int N, int prec);
+const KernelSet *ks_advection3d(int N, int prec);
+const KernelSet *ks_euler2d(int N, int prec);
+const KernelSet *ks_euler3d(int N, int prec);
+const KernelSet *ks_elastic3d(int N, int prec);
+}  // namespace aderdg
+
+using namespace aderdg;
+
+namespace {
+
+thread_local std::string g_err = "no error";
+
+int fail(int code, const std::string &msg)
+{
+    g_err = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    return fail(ADERDG_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                        \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+const KernelSet *find_kernels(int pde, int dim, int N, int prec)
+{
+    if (pde == ADERDG_PDE_ADVECTION && dim == 2) return ks_advection2d(N, prec);
+    if (pde == ADERDG_PDE_ADVECTION && dim == 3) return ks_advection3d(N, prec);
+    if (pde == ADERDG_PDE_EULER && dim == 2) return ks_euler2d(N, prec);
+    if (pde == ADERDG_PDE_EULER && dim == 3) return ks_euler3d(N, prec);
+    if (pde == ADERDG_PDE_ELASTICITY && dim == 3) return ks_elastic3d(N, prec);
+    return nullptr;
+}
+
+int pde_nvar(int pde, int dim)
+{
+    if (pde == ADERDG_PDE_ADVECTION) return 1;
+    if (pde == ADERDG_PDE_EULER) return dim + 2;
+    if (pde == ADERDG_PDE_ELASTICITY) return 9;
+    return -1;
+}
+
+// ---------------------------------------------------------------------------
+// generic kernels
+// ---------------------------------------------------------------------------
+
+// CFL step of Sec. 3 from the maxima of the current state, clipped to
+// t_end; consumes the maxima (the corrector refills them for u^{n+1}).
+__global__ void k_dt(Control *c)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const double t = c->t;
+    if (!(t < c->t_end)) {
+        c->dt = 0.0;
+        c->flags |= FLAG_DONE;
+        return;
+    }
+    c->flags &= ~FLAG_DONE;
+    double S = 0.0;
+    for (int d = 0; d < c->dim; ++d) {
+        const double lam = __longlong_as_double((long long)c->lam_acc[d]);
+        c->lam_used[d] = lam;
+        S += lam * c->inv_dx[d];
+    }
+    const double dtc = c->alpha / S;
+    double dt, tn;
+    if (t + dtc >= c->t_end) { dt = c->t_end - t; tn = c->t_end; }
+    else { dt = dtc; tn = t + dtc; }
+    if (!(dt > 0.0) || !isfinite(dt)) {  // non-finite maxima: stop, flag it
+        c->dt = 0.0;
+        c->flags |= FLAG_NONFINITE;
+        return;
+    }
+    c->dt = dt;
+    c->t = tn;
+    c->step += 1;
+    for (int d = 0; d < 3; ++d) c->lam_acc[d] = 0ull;
+}
+
+// dt the CFL condition gives for the current maxima (no clip, no update).
+__global__ void k_cfl_query(const Control *c, double *out)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double S = 0.0;
+    for (int d = 0; d < c->dim; ++d) S += __longlong_as_double((long long)c->lam_acc[d]) * c->inv_dx[d];
+    out[0] = c->alpha / S;
+}
+
+// Conserved totals, stage 1: block b sums the elements b, b + G, b + 2G, ...
+// per thread in a fixed order, then a fixed-shape tree per block.
+constexpr int MASS_THREADS = 256;
+constexpr int MASS_BLOCKS = 304;
+
+__global__ void __launch_bounds__(MASS_THREADS)
+k_mass_partial(const double *u, long long E, int NS, int M, int n, int dim, Basis b, double vol,
+               double *partial)
+{
+    __shared__ double red[MASS_THREADS * 9];
+    double acc[9];
+    for (int v = 0; v < 9; ++v) acc[v] = 0.0;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < E; e += stride) {
+        for (int s = 0; s < NS; ++s) {
+            double ws = vol;
+            int r = s;
+            for (int d = 0; d < dim; ++d) { ws *= b.w[r % n]; r /= n; }
+            for (int v = 0; v < M; ++v) acc[v] += ws * u[(e * NS + s) * M + v];
+        }
+    }
+    for (int v = 0; v < M; ++v) red[threadIdx.x * 9 + v] = acc[v];
+    __syncthreads();
+    for (int h = MASS_THREADS / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h)
+            for (int v = 0; v < M; ++v) red[threadIdx.x * 9 + v] += red[(threadIdx.x + h) * 9 + v];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int v = 0; v < M; ++v) partial[blockIdx.x * 9 + v] = red[v];
+}
+
+__global__ void k_mass_final(const double *partial, int nb, int M, double *out)
+{
+    const int v = threadIdx.x;
+    if (v >= M) return;
+    double s = 0.0;
+    for (int i = 0; i < nb; ++i) s += partial[i * 9 + v];
+    out[v] = s;
+}
+
+// Predictor trace records [e][d][side][p][RS] (T) -> oracle layout
+// qface/fface [e][d][side][p][v] (double).
+template <typename T>
+__global__ void k_unpack_traces(const T *tr, long long nrec_total, int M, int RS, double *qf, double *ff)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= nrec_total * M) return;
+    const long long r = i / M;
+    const int v = (int)(i - r * M);
+    if (qf) qf[i] = double(tr[r * RS + v]);
+    if (ff) ff[i] = double(tr[r * RS + M + v]);
+}
+
+template <typename T>
+__global__ void k_widen(const T *src, long long count, double *dst)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < count) dst[i] = double(src[i]);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// the handle
+// ---------------------------------------------------------------------------
+
+struct aderdg_s {
+    int dim = 0, N = 0, n = 0, M = 0, pde = 0, precision = 0, picard = 0;
+    long long E = 0;
+    int NS = 0, NF = 0, NREC = 0;
+    double dx[3] = {1, 1, 1};
+    double lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1};
+    double alpha = 0;
+    const KernelSet *ks = nullptr;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    aderdg_alloc_t alloc{};
+    bool has_alloc = false;
+    double *u = nullptr;
+    void *V = nullptr;
+    void *tr = nullptr;
+    Control *ctl = nullptr;
+    double *scratch = nullptr;  // mass partials + small outputs
+    double *host_pinned = nullptr;
+    KParams kp{};
+    Basis basis{};
+    size_t device_bytes = 0;
+    cudaGraphExec_t graph = nullptr;
+    int graph_steps = 0;
+    int device = 0;
+    bool profiling = false;
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+};
+
+namespace {
+
+void *dev_alloc(aderdg_t *h, size_t bytes)
+{
+    void *p = nullptr;
+    bytes = (bytes + 255) / 256 * 256;
+    if (h->has_alloc) p = h->alloc.alloc(bytes, h->alloc.ctx);
+    else if (cudaMalloc(&p, bytes) != cudaSuccess) p = nullptr;
+    if (p) h->device_bytes += bytes;
+    return p;
+}
+
+void dev_free(aderdg_t *h, void *p)
+{
+    if (!p) return;
+    if (h->has_alloc) h->alloc.free(p, h->alloc.ctx);
+    else cudaFree(p);
+}
+
+int launch_predictor(aderdg_t *h, int use_ctl, double dt)
+{
+    KParams kp = h->kp;
+    kp.use_ctl_dt = use_ctl;
+    kp.dt_arg = dt;
+    const long long blocks = (h->E + h->ks->pred_epb - 1) / h->ks->pred_epb;
+    h->ks->predictor<<<(unsigned)blocks, h->ks->pred_threads, h->ks->pred_smem, h->stream>>>(kp);
+    CK(cudaGetLastError());
+    return ADERDG_OK;
+}
+
+int launch_corrector(aderdg_t *h, int use_ctl, double dt)
+{
+    KParams kp = h->kp;
+    kp.use_ctl_dt = use_ctl;
+    kp.dt_arg = dt;
+    const long long blocks = (h->E + h->ks->corr_epb - 1) / h->ks->corr_epb;
+    h->ks->corrector<<<(unsigned)blocks, h->ks->corr_threads, h->ks->corr_smem, h->stream>>>(kp);
+    CK(cudaGetLastError());
+    return ADERDG_OK;
+}
+
+int enqueue_step(aderdg_t *h)
+{
+    k_dt<<<1, 32, 0, h->stream>>>(h->ctl);
+    CK(cudaGetLastError());
+    if (h->profiling) CK(cudaEventRecord(h->ev[0], h->stream));
+    int rc = launch_predictor(h, 1, 0.0);
+    if (rc) return rc;
+    if (h->profiling) CK(cudaEventRecord(h->ev[1], h->stream));
+    rc = launch_corrector(h, 1, 0.0);
+    if (rc) return rc;
+    if (h->profiling) CK(cudaEventRecord(h->ev[2], h->stream));
+    return ADERDG_OK;
+}
+
+int read_ctl(aderdg_t *h, Control *out)
+{
+    CK(cudaMemcpyAsync(h->host_pinned, h->ctl, sizeof(Control), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    std::memcpy(out, h->host_pinned, sizeof(Control));
+    return ADERDG_OK;
+}
+
+int check_flags(const Control &c)
+{
+    if (c.flags & FLAG_NONFINITE) return fail(ADERDG_E_NONFINITE, "non-finite value in the state");
+    if (c.flags & FLAG_TIMEOUT) return fail(ADERDG_E_TIMEOUT, "bounded device wait expired");
+    return ADERDG_OK;
+}
+
+int set_t_end(aderdg_t *h, double t_end)
+{
+    std::memcpy(h->host_pinned + 64, &t_end, sizeof(double));
+    CK(cudaMemcpyAsync(&h->ctl->t_end, h->host_pinned + 64, sizeof(double), cudaMemcpyHostToDevice,
+                       h->stream));
+    // the pinned staging slot is reused: wait until the copy has read it
+    CK(cudaStreamSynchronize(h->stream));
+    return ADERDG_OK;
+}
+
+void fill_cost(const aderdg_t *h, aderdg_info_t *info)
+{
+    const double n = h->n, M = h->M, NS = h->NS, NST = h->NS * h->n, NREC = h->NREC, D = h->dim;
+    const double P = h->picard, FF = h->ks->flux_flops, EF = h->ks->eig_flops;
+    const double per_iter = NST * FF + D * M * NST * (2 * n + 2) + M * NST * (2 * n + 1);
+    const double pred = P * per_iter + NST * FF + (1 + D) * NS * M * 2 * n + NS * M * D * (2 * n + 2)
+                        + NREC * M * 4 * n + NREC * EF;
+    const double corr = NREC * M * 6 + NREC + NS * M * (5 * D + 3) + NS * D * (EF + 1);
+    info->flops_predictor = pred * h->E;
+    info->flops_corrector = corr * h->E;
+    const double b = h->ks->elem_bytes;
+    info->bytes_predictor = h->E * (8.0 * NS * M + b * NS * M + b * NREC * h->ks->rs);
+    info->bytes_corrector = h->E * (16.0 * NS * M + b * NS * M + 2.0 * b * NREC * h->ks->rs);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+
+extern "C" {
+
+const char *aderdg_last_error(void) { return g_err.c_str(); }
+
+int aderdg_version(void) { return 100; }
+
+int aderdg_gl_nodes(int N, double *x, double *w)
+{
+    if (N < 1 || N > 9 || !x || !w) return fail(ADERDG_E_INVAL, "aderdg_gl_nodes: need 1 <= N <= 9");
+    if (gauss_legendre01(N + 1, x, w)) return fail(ADERDG_E_INVAL, "gauss_legendre01 failed");
+    return ADERDG_OK;
+}
+
+double aderdg_default_alpha(int N) { return default_alpha(N); }
+
+int aderdg_create(const aderdg_mesh_t *mesh, int N, int nVar, const aderdg_pde_t *pde,
+                  const aderdg_config_t *cfg, aderdg_t **out)
+{
+    if (!out) return fail(ADERDG_E_INVAL, "out is NULL");
+    *out = nullptr;
+    if (!mesh || !pde) return fail(ADERDG_E_INVAL, "mesh/pde is NULL");
+    if (mesh->dim < 2 || mesh->dim > 3) return fail(ADERDG_E_INVAL, "dim must be 2 or 3");
+    const int m = pde_nvar(pde->kind, mesh->dim);
+    if (m < 0) return fail(ADERDG_E_INVAL, "unknown pde kind");
+    if (nVar != m) return fail(ADERDG_E_INVAL, "nVar does not match the PDE");
+    if (N < 1 || N > 9) return fail(ADERDG_E_INVAL, "N must be in 1..9");
+    long long E = 1;
+    for (int d = 0; d < mesh->dim; ++d) {
+        if (mesh->cells[d] <= 0 || mesh->cells[d] > (1 << 30)) return fail(ADERDG_E_INVAL, "bad cell count");
+        if (!(mesh->hi[d] > mesh->lo[d])) return fail(ADERDG_E_INVAL, "hi must exceed lo");
+        E *= mesh->cells[d];
+    }
+    if (E > (1LL << 31)) return fail(ADERDG_E_INVAL, "too many elements");
+    const int prec = cfg ? cfg->precision : ADERDG_FP64;
+    if (prec != ADERDG_FP64 && prec != ADERDG_MIXED_FP32) return fail(ADERDG_E_INVAL, "bad precision");
+    const KernelSet *ks = find_kernels(pde->kind, mesh->dim, N, prec);
+    if (!ks) return fail(ADERDG_E_UNSUPPORTED, "no kernels compiled for this (pde, dim, N)");
+    if (pde->kind == ADERDG_PDE_EULER && !(pde->p[0] > 1.0)) return fail(ADERDG_E_INVAL, "gamma must be > 1");
+    if (pde->kind == ADERDG_PDE_ELASTICITY && !(pde->p[0] > 0 && pde->p[2] > 0 && pde->p[1] + 2 * pde->p[2] > 0))
+        return fail(ADERDG_E_INVAL, "bad elastic parameters");
+
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return fail(ADERDG_E_CUDA, "no CUDA device available (the library has no CPU path)");
+    }
+
+    aderdg_t *h = new aderdg_s();
+    cudaGetDevice(&h->device);
+    h->dim = mesh->dim;
+    h->N = N;
+    h->n = N + 1;
+    h->M = m;
+    h->pde = pde->kind;
+    h->precision = prec;
+    h->picard = (cfg && cfg->picard_iters > 0) ? cfg->picard_iters : N + 1;
+    h->alpha = (cfg && cfg->cfl_alpha > 0) ? cfg->cfl_alpha : default_alpha(N);
+    h->E = E;
+    h->NS = ipow(h->n, h->dim);
+    h->NF = ipow(h->n, h->dim - 1);
+    h->NREC = h->dim * 2 * h->NF;
+    h->ks = ks;
+    for (int d = 0; d < 3; ++d) {
+        h->lo[d] = d < h->dim ? mesh->lo[d] : 0.0;
+        h->hi[d] = d < h->dim ? mesh->hi[d] : 1.0;
+        h->dx[d] = d < h->dim ? (mesh->hi[d] - mesh->lo[d]) / mesh->cells[d] : 1.0;
+    }
+    if (cfg && cfg->alloc) {
+        if (!cfg->alloc->alloc || !cfg->alloc->free) { delete h; return fail(ADERDG_E_INVAL, "allocator incomplete"); }
+        h->alloc = *cfg->alloc;
+        h->has_alloc = true;
+    }
+    if (cfg && cfg->cuda_stream) h->stream = (cudaStream_t)cfg->cuda_stream;
+    else {
+        if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete h;
+            return fail(ADERDG_E_CUDA, "cudaStreamCreate failed");
+        }
+        h->own_stream = true;
+    }
+    if (build_basis(N, h->basis)) { aderdg_destroy(h); return fail(ADERDG_E_INVAL, "basis construction failed"); }
+
+    const size_t nstate = (size_t)E * h->NS * m;
+    h->u = (double *)dev_alloc(h, nstate * sizeof(double));
+    h->V = dev_alloc(h, nstate * ks->elem_bytes);
+    h->tr = dev_alloc(h, (size_t)E * h->NREC * ks->rs * ks->elem_bytes);
+    h->ctl = (Control *)dev_alloc(h, sizeof(Control));
+    h->scratch = (double *)dev_alloc(h, sizeof(double) * (MASS_BLOCKS * 9 + 64));
+    if (!h->u || !h->V || !h->tr || !h->ctl || !h->scratch) {
+        aderdg_destroy(h);
+        return fail(ADERDG_E_NOMEM, "device allocation failed");
+    }
+    if (cudaMallocHost(&h->host_pinned, 4096) != cudaSuccess) {
+        h->host_pinned = nullptr;
+        aderdg_destroy(h);
+        return fail(ADERDG_E_NOMEM, "pinned host allocation failed");
+    }
+    // kernels with > 48 KB of dynamic shared memory need an opt-in
+    if (ks->pred_smem > 48 * 1024 &&
+        cudaFuncSetAttribute((const void *)ks->predictor, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)ks->pred_smem) != cudaSuccess) {
+        aderdg_destroy(h);
+        return fail(ADERDG_E_CUDA, "predictor shared memory opt-in failed");
+    }
+    if (ks->corr_smem > 48 * 1024 &&
+        cudaFuncSetAttribute((const void *)ks->corrector, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)ks->corr_smem) != cudaSuccess) {
+        aderdg_destroy(h);
+        return fail(ADERDG_E_CUDA, "corrector shared memory opt-in failed");
+    }
+
+    KParams &kp = h->kp;
+    std::memset(&kp, 0, sizeof(kp));
+    kp.E = E;
+    for (int d = 0; d < 3; ++d) {
+        kp.cells[d] = d < h->dim ? (int)mesh->cells[d] : 1;
+        kp.inv_dx[d] = 1.0 / h->dx[d];
+    }
+    kp.picard = h->picard;
+    kp.u = h->u;
+    kp.u_out = h->u;
+    kp.V = h->V;
+    kp.tr = h->tr;
+    kp.ctl = h->ctl;
+    for (int i = 0; i < 8; ++i) kp.pde.p[i] = pde->p[i];
+    kp.b = h->basis;
+
+    Control c;
+    std::memset(&c, 0, sizeof(c));
+    c.alpha = h->alpha;
+    c.dim = h->dim;
+    for (int d = 0; d < 3; ++d) c.inv_dx[d] = kp.inv_dx[d];
+    c.t_end = 0.0;
+    if (cudaMemsetAsync(h->u, 0, nstate * sizeof(double), h->stream) != cudaSuccess ||
+        cudaMemcpyAsync(h->ctl, &c, sizeof(c), cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess) {
+        aderdg_destroy(h);
+        return fail(ADERDG_E_CUDA, "initialisation failed");
+    }
+    *out = h;
+    return ADERDG_OK;
+}
+
+int aderdg_destroy(aderdg_t *h)
+{
+    if (!h) return ADERDG_OK;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    dev_free(h, h->u);
+    dev_free(h, h->V);
+    dev_free(h, h->tr);
+    dev_free(h, h->ctl);
+    dev_free(h, h->scratch);
+    if (h->host_pinned) cudaFreeHost(h->host_pinned);
+    for (auto &e : h->ev)
+        if (e) cudaEventDestroy(e);
+    if (h->own_stream) cudaStreamDestroy(h->stream);
+    delete h;
+    return ADERDG_OK;
+}
+
+int aderdg_get_info(const aderdg_t *h, aderdg_info_t *info)
+{
+    if (!h || !info) return fail(ADERDG_E_INVAL, "NULL argument");
+    std::memset(info, 0, sizeof(*info));
+    info->dim = h->dim;
+    info->N = h->N;
+    info->nvar = h->M;
+    info->precision = h->precision;
+    info->picard_iters = h->picard;
+    info->elements = h->E;
+    info->dofs = h->E * h->NS;
+    info->cfl_alpha = h->alpha;
+    info->device_bytes = h->device_bytes;
+    fill_cost(h, info);
+    return ADERDG_OK;
+}
+
+int aderdg_set_state(aderdg_t *h, const double *u, int where, double t)
+{
+    if (!h || !u) return fail(ADERDG_E_INVAL, "NULL argument");
+    if (!std::isfinite(t)) return fail(ADERDG_E_INVAL, "t must be finite");
+    const size_t bytes = (size_t)h->E * h->NS * h->M * sizeof(double);
+    CK(cudaMemcpyAsync(h->u, u, bytes, where == ADERDG_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                       h->stream));
+    Control c;
+    std::memset(&c, 0, sizeof(c));
+    c.t = t;
+    c.t_end = t;
+    c.alpha = h->alpha;
+    c.dim = h->dim;
+    for (int d = 0; d < 3; ++d) c.inv_dx[d] = h->kp.inv_dx[d];
+    std::memcpy(h->host_pinned, &c, sizeof(c));
+    CK(cudaMemcpyAsync(h->ctl, h->host_pinned, sizeof(c), cudaMemcpyHostToDevice, h->stream));
+    h->ks->cfl<<<(unsigned)std::min<long long>(4 * 152, (h->E * h->NS + 255) / 256), 256, 0, h->stream>>>(h->kp);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(h->stream));  // the pinned staging buffer is reused
+    return ADERDG_OK;
+}
+
+int aderdg_get_state(aderdg_t *h, double *u, int where, double *t, int64_t *step)
+{
+    if (!h || !u) return fail(ADERDG_E_INVAL, "NULL argument");
+    const size_t bytes = (size_t)h->E * h->NS * h->M * sizeof(double);
+    CK(cudaMemcpyAsync(u, h->u, bytes, where == ADERDG_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                       h->stream));
+    Control c;
+    int rc = read_ctl(h, &c);
+    if (rc) return rc;
+    if (t) *t = c.t;
+    if (step) *step = c.step;
+    return check_flags(c);
+}
+
+int aderdg_predictor(aderdg_t *h, double dt)
+{
+    if (!h) return fail(ADERDG_E_INVAL, "NULL handle");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(ADERDG_E_INVAL, "dt must be positive and finite");
+    return launch_predictor(h, 0, dt);
+}
+
+int aderdg_corrector(aderdg_t *h, double dt)
+{
+    if (!h) return fail(ADERDG_E_INVAL, "NULL handle");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(ADERDG_E_INVAL, "dt must be positive and finite");
+    CK(cudaMemsetAsync(h->ctl->lam_acc, 0, sizeof(h->ctl->lam_acc), h->stream));
+    return launch_corrector(h, 0, dt);
+}
+
+int aderdg_get_predictor_outputs(aderdg_t *h, double *volume, double *qface, double *fface, int where)
+{
+    if (!h) return fail(ADERDG_E_INVAL, "NULL handle");
+    const long long nstate = h->E * h->NS * h->M;
+    const long long nrec = h->E * h->NREC;
+    const long long ntr = nrec * h->M;
+    const int eb = h->ks->elem_bytes;
+    double *tmp = nullptr;
+    if (where != ADERDG_DEVICE) {
+        const size_t need = sizeof(double) * (size_t)std::max(nstate, 2 * ntr);
+        tmp = (double *)dev_alloc(h, need);
+        if (!tmp) return fail(ADERDG_E_NOMEM, "temporary allocation failed");
+    }
+    int rc = ADERDG_OK;
+    auto run = [&]() -> int {
+        if (volume) {
+            double *dst = where == ADERDG_DEVICE ? volume : tmp;
+            const unsigned blocks = (unsigned)((nstate + 255) / 256);
+            if (eb == 8) k_widen<double><<<blocks, 256, 0, h->stream>>>((const double *)h->V, nstate, dst);
+            else k_widen<float><<<blocks, 256, 0, h->stream>>>((const float *)h->V, nstate, dst);
+            CK(cudaGetLastError());
+            if (where != ADERDG_DEVICE)
+                CK(cudaMemcpyAsync(volume, tmp, nstate * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+            CK(cudaStreamSynchronize(h->stream));
+        }
+        if (qface || fface) {
+            double *dq = where == ADERDG_DEVICE ? qface : (qface ? tmp : nullptr);
+            double *df = where == ADERDG_DEVICE ? fface : (fface ? tmp + ntr : nullptr);
+            const unsigned blocks = (unsigned)((ntr + 255) / 256);
+            if (eb == 8)
+                k_unpack_traces<double><<<blocks, 256, 0, h->stream>>>((const double *)h->tr, nrec, h->M, h->ks->rs, dq, df);
+            else
+                k_unpack_traces<float><<<blocks, 256, 0, h->stream>>>((const float *)h->tr, nrec, h->M, h->ks->rs, dq, df);
+            CK(cudaGetLastError());
+            if (where != ADERDG_DEVICE) {
+                if (qface) CK(cudaMemcpyAsync(qface, dq, ntr * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+                if (fface) CK(cudaMemcpyAsync(fface, df, ntr * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+            }
+            CK(cudaStreamSynchronize(h->stream));
+        }
+        return ADERDG_OK;
+    };
+    rc = run();
+    if (tmp) {
+        cudaStreamSynchronize(h->stream);
+        dev_free(h, tmp);
+        h->device_bytes -= (sizeof(double) * (size_t)std::max(nstate, 2 * ntr) + 255) / 256 * 256;
+    }
+    return rc;
+}
+
+int aderdg_step(aderdg_t *h, double t_end, double *dt_taken)
+{
+    if (!h) return fail(ADERDG_E_INVAL, "NULL handle");
+    if (!std::isfinite(t_end)) return fail(ADERDG_E_INVAL, "t_end must be finite");
+    int rc = set_t_end(h, t_end);
+    if (rc) return rc;
+    rc = enqueue_step(h);
+    if (rc) return rc;
+    if (dt_taken) {
+        Control c;
+        rc = read_ctl(h, &c);
+        if (rc) return rc;
+        *dt_taken = c.dt;
+        return check_flags(c);
+    }
+    return ADERDG_OK;
+}
+
+int aderdg_advance(aderdg_t *h, double t_end, int64_t max_steps)
+{
+    if (!h) return fail(ADERDG_E_INVAL, "NULL handle");
+    if (!std::isfinite(t_end) || max_steps < 0) return fail(ADERDG_E_INVAL, "bad t_end / max_steps");
+    int rc = set_t_end(h, t_end);
+    if (rc) return rc;
+    constexpr int CHUNK = 16;
+    if (!h->graph) {
+        // capture CHUNK steps once; every replay re-reads dt and t on the device
+        cudaStreamCaptureStatus st;
+        bool ok = cudaStreamIsCapturing(h->stream, &st) == cudaSuccess && st == cudaStreamCaptureStatusNone &&
+                  h->stream != nullptr;
+        cudaGraph_t g = nullptr;
+        if (ok && cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+            for (int i = 0; i < CHUNK && ok; ++i) ok = enqueue_step(h) == ADERDG_OK;
+            if (cudaStreamEndCapture(h->stream, &g) != cudaSuccess) ok = false;
+            if (ok && cudaGraphInstantiate(&h->graph, g, 0) != cudaSuccess) { ok = false; h->graph = nullptr; }
+            if (g) cudaGraphDestroy(g);
+        }
+        cudaGetLastError();  // a failed capture falls back to plain launches
+        h->graph_steps = h->graph ? CHUNK : 0;
+    }
+    int64_t done = 0;
+    while (done < max_steps) {
+        const int64_t k = std::min<int64_t>(CHUNK, max_steps - done);
+        if (h->graph && k == CHUNK) {
+            CK(cudaGraphLaunch(h->graph, h->stream));
+        } else {
+            for (int64_t i = 0; i < k; ++i) {
+                rc = enqueue_step(h);
+                if (rc) return rc;
+            }
+        }
+        done += k;
+        Control c;
+        rc = read_ctl(h, &c);
+        if (rc) return rc;
+        rc = check_flags(c);
+        if (rc) return rc;
+        if (!(c.t < t_end)) break;
+    }
+    return ADERDG_OK;
+}
+
+int aderdg_cfl_dt(aderdg_t *h, double *dt)
+{
+    if (!h || !dt) return fail(ADERDG_E_INVAL, "NULL argument");
+    k_cfl_query<<<1, 32, 0, h->stream>>>(h->ctl, h->scratch + MASS_BLOCKS * 9);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(dt, h->scratch + MASS_BLOCKS * 9, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return ADERDG_OK;
+}
+
+int aderdg_mass(aderdg_t *h, double *per_var)
+{
+    if (!h || !per_var) return fail(ADERDG_E_INVAL, "NULL argument");
+    double vol = 1.0;
+    for (int d = 0; d < h->dim; ++d) vol *= h->dx[d];
+    k_mass_partial<<<MASS_BLOCKS, MASS_THREADS, 0, h->stream>>>(h->u, h->E, h->NS, h->M, h->n, h->dim, h->basis, vol,
+                                                                h->scratch);
+    CK(cudaGetLastError());
+    k_mass_final<<<1, 32, 0, h->stream>>>(h->scratch, MASS_BLOCKS, h->M, h->scratch + MASS_BLOCKS * 9 + 8);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(per_var, h->scratch + MASS_BLOCKS * 9 + 8, sizeof(double) * h->M, cudaMemcpyDeviceToHost,
+                       h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return ADERDG_OK;
+}
+
+int aderdg_sync(aderdg_t *h)
+{
+    if (!h) return fail(ADERDG_E_INVAL, "NULL handle");
+    Control c;
+    int rc = read_ctl(h, &c);
+    if (rc) return rc;
+    return check_flags(c);
+}
+
+int aderdg_profile(aderdg_t *h, int enable)
+{
+    if (!h) return fail(ADERDG_E_INVAL, "NULL handle");
+    if (enable && !h->ev[0])
+        for (auto &e : h->ev) CK(cudaEventCreate(&e));
+    if (h->graph) {  // a captured graph would keep the old recording choice
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
+    h->profiling = enable != 0;
+    return ADERDG_OK;
+}
+
+int aderdg_profile_read(aderdg_t *h, float *ms_predictor, float *ms_corrector)
+{
+    if (!h || !h->profiling) return fail(ADERDG_E_INVAL, "profiling is not enabled");
+    CK(cudaEventSynchronize(h->ev[2]));
+    float a = 0.f, b = 0.f;
+    CK(cudaEventElapsedTime(&a, h->ev[0], h->ev[1]));
+    CK(cudaEventElapsedTime(&b, h->ev[1], h->ev[2]));
+    if (ms_predictor) *ms_predictor = a;
+    if (ms_corrector) *ms_corrector = b;
+    return ADERDG_OK;
+}
+
+}  // extern "C"
