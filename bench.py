@@ -45,11 +45,13 @@ WORKLOADS = {
 }
 DEFAULT_WORKLOAD = "euler2d_vortex_200x200_N4"
 
-# FP64 peak of one GB300 (the profiling recipe's nominal 1.25 TFLOP/s, i.e.
-# 2 DFMA per clock per SM x 152 SMs x ~2.06 GHz).  No measured FP64 figure
-# exists in the driver's peak file.
-FP64_PEAK_TFLOPS = 1.25
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # FFMA issue: 128 lanes/SM/clock
+# ALU peaks of one GB300 from unit counts and the maximum SM clock (152 SMs,
+# 2070 MHz): FP64 at 2 DFMA per clock per SM (the nominal 1.25 TFLOP/s),
+# FP32 at 128 FFMA lanes per clock per SM.  The driver's peak file has no
+# FP64/FP32 figures; bench.py also reports its own FMA-chain probe.
+SMS, SM_MHZ = 152, 2070.0
+FP64_PEAK_TFLOPS = SMS * SM_MHZ * 1e6 * 2 * 2 / 1e12
+FP32_PEAK_TFLOPS = SMS * SM_MHZ * 1e6 * 128 * 2 / 1e12
 
 
 def _initial_state(w, X):
@@ -306,14 +308,21 @@ def run_ours(args, w, rank, world):
         s.close()
         return 0
 
+    probe = {}
+    for kind, name in ((0, "fp64"), (1, "fp32")):
+        try:
+            probe[name] = A.aderdg_peak_tflops(kind)
+        except Exception as e:  # the probe is context only
+            probe[name] = None
     pred_avg = statistics.mean(pred_ms)
     corr_avg = statistics.mean(corr_ms)
     if args.precision == "fp64":
         achieved = info["flops_predictor"] / (pred_avg / 1e3) / 1e12
         roofline = {"bound": "alu", "kernel": "k_predictor (FP64 DFMA pipe)", "achieved": achieved,
                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                    "peak_source": "nominal FP64 rate of GB300 from the profiling recipe (no measured "
-                                   "FP64 figure in MEASURED_PEAKS.json)",
+                    "peak_source": "derived: 152 SMs x 2 DFMA/clock x 2070 MHz (nominal 1.25 TFLOP/s); "
+                                   "no FP64 figure in MEASURED_PEAKS.json",
+                    "peak_probe_tflops": probe.get("fp64"),
                     "traffic": _traffic("k_predictor", args.workload, args.precision),
                     "algorithmic_flops_per_launch": info["flops_predictor"],
                     "launch_ms": pred_avg}
@@ -321,7 +330,8 @@ def run_ours(args, w, rank, world):
         achieved = info["flops_predictor"] / (pred_avg / 1e3) / 1e12
         roofline = {"bound": "alu", "kernel": "k_predictor (FP32 FFMA pipe)", "achieved": achieved,
                     "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
-                    "peak_source": "FP32 FMA issue rate derived from 152 SMs x 128 lanes x 2 flops x 2.07 GHz",
+                    "peak_source": "derived: 152 SMs x 128 FFMA lanes x 2070 MHz",
+                    "peak_probe_tflops": probe.get("fp32"),
                     "traffic": _traffic("k_predictor", args.workload, args.precision),
                     "algorithmic_flops_per_launch": info["flops_predictor"],
                     "launch_ms": pred_avg}

@@ -209,6 +209,12 @@ int aderdg_sync(aderdg_t *h);
 int aderdg_profile(aderdg_t *h, int enable);
 int aderdg_profile_read(aderdg_t *h, float *ms_predictor, float *ms_corrector);
 
+/* Measurement utility: the FMA throughput this GPU sustains, in TFLOP/s
+ * (FMA = 2 flops), from independent FMA chains on every SM.  kind 0: FP64
+ * (DFMA), kind 1: FP32 (FFMA).  Synchronising; runs for ~0.1 s.  Used as
+ * the denominator of the ALU rooflines. */
+int aderdg_peak_tflops(int kind, double *tflops);
+
 #ifdef __cplusplus
 }
 #endif

@@ -95,6 +95,7 @@ _SIGS = {
     "aderdg_sync": (C.c_int, [_H]),
     "aderdg_profile": (C.c_int, [_H, C.c_int]),
     "aderdg_profile_read": (C.c_int, [_H, C.POINTER(C.c_float), C.POINTER(C.c_float)]),
+    "aderdg_peak_tflops": (C.c_int, [C.c_int, _DP]),
 }
 
 
@@ -384,3 +385,10 @@ def aderdg_profile(s: Solver, enable=True):
 
 def aderdg_profile_read(s: Solver):
     return s.profile_read()
+
+
+def aderdg_peak_tflops(kind: int) -> float:
+    """Measured FMA throughput (TFLOP/s): kind 0 FP64, kind 1 FP32."""
+    v = C.c_double(0)
+    _check(load().aderdg_peak_tflops(int(kind), C.byref(v)))
+    return v.value
