@@ -209,6 +209,38 @@ int aderdg_sync(aderdg_t *h);
 int aderdg_profile(aderdg_t *h, int enable);
 int aderdg_profile_read(aderdg_t *h, float *ms_predictor, float *ms_corrector);
 
+/* ---- a step that allocates nothing ---------------------------------------
+ * The paper has no counterpart; this is an integration aid of the library.
+ *
+ * One ADER-DG step with the given dt -- predictor then corrector, the same
+ * kernels and result as aderdg_predictor + aderdg_corrector on a handle --
+ * from u_in to u_out, caller-owned device buffers in the state layout above
+ * (they may be the same buffer).  No handle is created.
+ *
+ * For callers that cannot call cudaMalloc: code that runs inside a CUDA
+ * graph capture or a stream-ordered region where an allocation would
+ * synchronise the device or is not permitted, frameworks whose memory must
+ * all come from their own allocator, and real-time or embedded hosts that
+ * forbid allocation after start-up.  This call allocates no memory at all:
+ * the volume term, the face traces and the control block live in one fixed
+ * device array of ADERDG_NOALLOC_SCRATCH_BYTES (32 MiB), part of the
+ * library module, which every GPU that loads the library holds until the
+ * process exits.  Meshes whose scratch would exceed it are rejected with
+ * ADERDG_E_INVAL (message gives the size needed).
+ *
+ * The first call on a device looks the array's device address up
+ * (cudaGetSymbolAddress, once per device, with that device current); make
+ * that first call before any stream capture.  All calls share the array
+ * and it keeps the last call's contents: calls whose work overlaps on the
+ * GPU (other streams, other host threads) race on it, so serialise them.
+ * Work is queued on cuda_stream (NULL: the legacy stream); the call does
+ * not synchronise and does not check for non-finite values.  Errors are
+ * reported through aderdg_last_error. */
+#define ADERDG_NOALLOC_SCRATCH_BYTES (32u << 20)
+int aderdg_step_noalloc(const aderdg_mesh_t *mesh, int N, int nVar, const aderdg_pde_t *pde,
+                        int precision, int picard_iters, const double *u_in, double *u_out,
+                        double dt, void *cuda_stream);
+
 /* Measurement utility: the FMA throughput this GPU sustains, in TFLOP/s
  * (FMA = 2 flops), from independent FMA chains on every SM.  kind 0: FP64
  * (DFMA), kind 1: FP32 (FFMA).  Synchronising; runs for ~0.1 s.  Used as

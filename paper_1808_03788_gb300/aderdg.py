@@ -96,6 +96,8 @@ _SIGS = {
     "aderdg_profile": (C.c_int, [_H, C.c_int]),
     "aderdg_profile_read": (C.c_int, [_H, C.POINTER(C.c_float), C.POINTER(C.c_float)]),
     "aderdg_peak_tflops": (C.c_int, [C.c_int, _DP]),
+    "aderdg_step_noalloc": (C.c_int, [C.POINTER(aderdg_mesh_t), C.c_int, C.c_int, C.POINTER(aderdg_pde_t),
+                                      C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_double, C.c_void_p]),
 }
 
 
@@ -392,3 +394,25 @@ def aderdg_peak_tflops(kind: int) -> float:
     v = C.c_double(0)
     _check(load().aderdg_peak_tflops(int(kind), C.byref(v)))
     return v.value
+
+
+ADERDG_NOALLOC_SCRATCH_BYTES = 32 << 20
+
+
+def aderdg_step_noalloc(pde: int, dim: int, cells, lo, hi, N: int, params, u_in, u_out, dt: float,
+                        precision: int = ADERDG_FP64, picard: int = 0, stream=None):
+    """One step u_in -> u_out (device tensors, float64, state layout) that
+    allocates nothing; see include/aderdg.h."""
+    mesh = aderdg_mesh_t()
+    mesh.dim = dim
+    for d in range(3):
+        mesh.cells[d] = int(cells[d]) if d < dim else 1
+        mesh.lo[d] = float(lo[d]) if d < dim else 0.0
+        mesh.hi[d] = float(hi[d]) if d < dim else 1.0
+    p = aderdg_pde_t()
+    p.kind = pde
+    for i, v in enumerate(params):
+        p.p[i] = float(v)
+    _check(load().aderdg_step_noalloc(C.byref(mesh), N, nvar(pde, dim), C.byref(p), precision, picard,
+                                      C.c_void_p(u_in.data_ptr()), C.c_void_p(u_out.data_ptr()),
+                                      float(dt), C.c_void_p(int(stream) if stream else 0)))

@@ -1,0 +1,166 @@
+// aderdg_step_noalloc: one ADER-DG step (predictor + corrector, given dt)
+// on caller-owned device buffers, with no device allocation at all.
+//
+// Who needs it: callers that cannot call cudaMalloc -- code running inside
+// a CUDA-graph capture or a stream-ordered region where an allocation
+// would synchronise or be illegal, hosts whose memory is owned by another
+// allocator that must see every byte, and embedded/real-time callers that
+// forbid allocation after start-up.  The regular handle API allocates its
+// volume-term and face-trace buffers at aderdg_create; this entry point
+// keeps them in one fixed, file-scope device array instead.
+//
+// The scratch array below (ADERDG_NOALLOC_SCRATCH_BYTES = 32 MiB) is part
+// of the module: every GPU that loads the library holds it until the
+// process exits.  All calls share it and it keeps the last call's
+// contents, so two calls whose work overlaps on the GPU (different streams,
+// or different host threads) race on it; serialise them.
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include <cuda_runtime.h>
+
+#include "../../include/aderdg.h"
+#include "basis.h"
+#include "common.cuh"
+
+namespace aderdg {
+void set_last_error(const char *msg);
+const KernelSet *ks_advection2d(int N, int prec);
+const KernelSet *ks_advection3d(int N, int prec);
+const KernelSet *ks_euler2d(int N, int prec);
+const KernelSet *ks_euler3d(int N, int prec);
+const KernelSet *ks_elastic3d(int N, int prec);
+}  // namespace aderdg
+
+using namespace aderdg;
+
+namespace {
+
+constexpr size_t SCRATCH_BYTES = ADERDG_NOALLOC_SCRATCH_BYTES;
+
+// The scratch: volume term, face-trace records and the control block of
+// the step in flight.  Host code must not pass this name to a kernel (on
+// the host it is only a stand-in); it uses the device address that
+// cudaGetSymbolAddress returns.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[SCRATCH_BYTES];
+
+constexpr int MAX_DEVICES = 64;
+std::mutex g_mu;
+void *g_scratch_dev[MAX_DEVICES] = {};
+
+int fail(int code, const std::string &m)
+{
+    set_last_error(m.c_str());
+    return code;
+}
+
+size_t align256(size_t b) { return (b + 255) / 256 * 256; }
+
+const KernelSet *kernels_for(int pde, int dim, int N, int prec)
+{
+    if (pde == ADERDG_PDE_ADVECTION && dim == 2) return ks_advection2d(N, prec);
+    if (pde == ADERDG_PDE_ADVECTION && dim == 3) return ks_advection3d(N, prec);
+    if (pde == ADERDG_PDE_EULER && dim == 2) return ks_euler2d(N, prec);
+    if (pde == ADERDG_PDE_EULER && dim == 3) return ks_euler3d(N, prec);
+    if (pde == ADERDG_PDE_ELASTICITY && dim == 3) return ks_elastic3d(N, prec);
+    return nullptr;
+}
+
+// Device address of the scratch on the current device; looked up once per
+// device (with that device current) and cached.
+int scratch_address(void **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(ADERDG_E_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    if (dev < 0 || dev >= MAX_DEVICES) return fail(ADERDG_E_CUDA, "device ordinal out of range");
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (!g_scratch_dev[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(ADERDG_E_CUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
+        g_scratch_dev[dev] = p;
+    }
+    *out = g_scratch_dev[dev];
+    return ADERDG_OK;
+}
+
+}  // namespace
+
+extern "C" int aderdg_step_noalloc(const aderdg_mesh_t *mesh, int N, int nVar, const aderdg_pde_t *pde,
+                                   int precision, int picard_iters, const double *u_in, double *u_out,
+                                   double dt, void *cuda_stream)
+{
+    if (!mesh || !pde || !u_in || !u_out) return fail(ADERDG_E_INVAL, "NULL argument");
+    if (mesh->dim < 2 || mesh->dim > 3) return fail(ADERDG_E_INVAL, "dim must be 2 or 3");
+    const int m = pde->kind == ADERDG_PDE_ADVECTION ? 1
+                  : pde->kind == ADERDG_PDE_EULER   ? mesh->dim + 2
+                  : pde->kind == ADERDG_PDE_ELASTICITY ? 9 : -1;
+    if (m < 0 || nVar != m) return fail(ADERDG_E_INVAL, "unknown pde or nVar mismatch");
+    if (precision != ADERDG_FP64 && precision != ADERDG_MIXED_FP32) return fail(ADERDG_E_INVAL, "bad precision");
+    if (!(dt > 0.0)) return fail(ADERDG_E_INVAL, "dt must be positive");
+    const KernelSet *ks = (N >= 1 && N <= 9) ? kernels_for(pde->kind, mesh->dim, N, precision) : nullptr;
+    if (!ks) return fail(ADERDG_E_UNSUPPORTED, "no kernels compiled for this (pde, dim, N)");
+    long long E = 1;
+    for (int d = 0; d < mesh->dim; ++d) {
+        if (mesh->cells[d] <= 0 || !(mesh->hi[d] > mesh->lo[d])) return fail(ADERDG_E_INVAL, "bad mesh");
+        E *= mesh->cells[d];
+    }
+    const int n = N + 1;
+    const int NS = ipow(n, mesh->dim), NF = ipow(n, mesh->dim - 1), NREC = mesh->dim * 2 * NF;
+    const size_t v_bytes = align256((size_t)E * NS * m * ks->elem_bytes);
+    const size_t tr_bytes = align256((size_t)E * NREC * ks->rs * ks->elem_bytes);
+    const size_t need = v_bytes + tr_bytes + align256(sizeof(Control));
+    if (need > SCRATCH_BYTES)
+        return fail(ADERDG_E_INVAL, "mesh too large for the static scratch: needs " + std::to_string(need) +
+                                        " bytes, limit " + std::to_string(SCRATCH_BYTES) + " bytes");
+
+    void *base = nullptr;
+    int rc = scratch_address(&base);
+    if (rc) return rc;
+    unsigned char *sb = static_cast<unsigned char *>(base);
+    Control *ctl = reinterpret_cast<Control *>(sb + v_bytes + tr_bytes);
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+
+    KParams kp;
+    std::memset(&kp, 0, sizeof(kp));
+    kp.E = E;
+    for (int d = 0; d < 3; ++d) {
+        kp.cells[d] = d < mesh->dim ? (int)mesh->cells[d] : 1;
+        kp.inv_dx[d] = d < mesh->dim ? 1.0 / ((mesh->hi[d] - mesh->lo[d]) / mesh->cells[d]) : 1.0;
+    }
+    kp.picard = picard_iters > 0 ? picard_iters : N + 1;
+    kp.u = u_in;
+    kp.u_out = u_out;
+    kp.V = sb;
+    kp.tr = sb + v_bytes;
+    kp.ctl = ctl;
+    kp.dt_arg = dt;
+    kp.use_ctl_dt = 0;
+    for (int i = 0; i < 8; ++i) kp.pde.p[i] = pde->p[i];
+    if (build_basis(N, kp.b)) return fail(ADERDG_E_INVAL, "basis construction failed");
+
+    // large shared-memory kernels need the opt-in (no allocation involved)
+    if (ks->pred_smem > 48 * 1024 &&
+        cudaFuncSetAttribute((const void *)ks->predictor, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)ks->pred_smem) != cudaSuccess)
+        return fail(ADERDG_E_CUDA, "predictor shared-memory opt-in failed");
+    if (ks->corr_smem > 48 * 1024 &&
+        cudaFuncSetAttribute((const void *)ks->corrector, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)ks->corr_smem) != cudaSuccess)
+        return fail(ADERDG_E_CUDA, "corrector shared-memory opt-in failed");
+
+    // the corrector max-reduces wave speeds and ORs flags into the control
+    // block: it must start at zero on every call
+    cudaError_t e = cudaMemsetAsync(ctl, 0, sizeof(Control), st);
+    if (e != cudaSuccess) return fail(ADERDG_E_CUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
+    const unsigned pb = (unsigned)((E + ks->pred_epb - 1) / ks->pred_epb);
+    ks->predictor<<<pb, ks->pred_threads, ks->pred_smem, st>>>(kp);
+    const unsigned cb = (unsigned)((E + ks->corr_epb - 1) / ks->corr_epb);
+    ks->corrector<<<cb, ks->corr_threads, ks->corr_smem, st>>>(kp);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(ADERDG_E_CUDA, std::string("launch: ") + cudaGetErrorString(e));
+    return ADERDG_OK;
+}

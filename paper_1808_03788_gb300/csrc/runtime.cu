@@ -172,6 +172,11 @@ __global__ void k_widen(const T *src, long long count, double *dst)
 
 }  // namespace
 
+namespace aderdg {
+// lets other translation units of the library report through aderdg_last_error
+void set_last_error(const char *msg) { g_err = msg; }
+}  // namespace aderdg
+
 // ---------------------------------------------------------------------------
 // the handle
 // ---------------------------------------------------------------------------
