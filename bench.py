@@ -79,7 +79,7 @@ class ClockSampler:
         self.thread = None
 
     def start(self):
-        cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "200"]
+        cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "50"]
         if self.gpu_id:
             cmd += ["-i", self.gpu_id]
         try:
@@ -213,31 +213,19 @@ def _config(args, w, world):
 # the CUDA path
 # ---------------------------------------------------------------------------
 
-def run_ours(args, w, rank, world):
+def _time_single(A, torch, w, prec, stream, steps, warmup, flush, world):
+    """Time `steps` device-CFL steps of one solve (L2 flushed between steps),
+    with per-kernel CUDA events.  Returns the solver and the timings."""
     import numpy as np
-    import torch
-
-    import paper_1808_03788_gb300.aderdg as A
-
-    dev = torch.cuda.current_device()
-    stream = torch.cuda.Stream()
-    prec = A.ADERDG_FP64 if args.precision == "fp64" else A.ADERDG_MIXED_FP32
     s = A.Solver(w["pde"], w["dim"], w["cells"], w["lo"], w["hi"], w["N"], w["params"], precision=prec,
                  stream=stream.cuda_stream)
-    info = s.info()
-    cfgd = _config(args, w, world)
-    assert (info["cfl_alpha"], info["picard_iters"], info["dofs"]) == \
-        (cfgd["cfl_alpha"], cfgd["picard_iters"], cfgd["dofs"]), (info, cfgd)
     X = s.node_coords(w["lo"], w["hi"])
     U0 = np.ascontiguousarray(_initial_state(w, X))
-    dofs = info["dofs"]
     t_far = 1e30
-
-    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
     s.set_state(U0)
     s.profile(True)
     with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             flush.zero_()
             s.step(t_far)
             s.profile_read()
@@ -245,14 +233,9 @@ def run_ours(args, w, rank, world):
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
-
-        clocks = ClockSampler(_gpu_id() if rank == 0 else None)
-        if rank == 0:
-            clocks.start()
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(args.steps)]
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         pred_ms, corr_ms = [], []
-        for k in range(args.steps):
+        for k in range(steps):
             flush.zero_()
             ev[k][0].record(stream)
             s.step(t_far)
@@ -265,8 +248,176 @@ def run_ours(args, w, rank, world):
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
-        clk = clocks.stop() if rank == 0 else None
-    s.sync()
+    s.profile(False)
+    return s, U0, step_ms, pred_ms, corr_ms
+
+
+def _roofline(info, pred_avg, prec_name, probe, workload):
+    achieved = info["flops_predictor"] / (pred_avg / 1e3) / 1e12
+    if prec_name == "fp64":
+        return {"bound": "alu", "kernel": "k_predictor (FP64 DFMA pipe)", "achieved": achieved,
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                "peak_source": "derived: 152 SMs x 2 DFMA/clock x 2070 MHz (nominal 1.25 TFLOP/s); "
+                               "no FP64 figure in MEASURED_PEAKS.json",
+                "peak_probe_tflops": probe.get("fp64"),
+                "traffic": _traffic("k_predictor", workload, prec_name),
+                "algorithmic_flops_per_launch": info["flops_predictor"], "launch_ms": pred_avg}
+    return {"bound": "alu", "kernel": "k_predictor (FP32 FFMA pipe)", "achieved": achieved,
+            "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+            "peak_source": "derived: 152 SMs x 128 FFMA lanes x 2070 MHz",
+            "peak_probe_tflops": probe.get("fp32"),
+            "traffic": _traffic("k_predictor", workload, prec_name),
+            "algorithmic_flops_per_launch": info["flops_predictor"], "launch_ms": pred_avg}
+
+
+def _kernels(info, pred_avg, corr_avg, hbm):
+    corr_gbs = info["bytes_corrector"] / (corr_avg / 1e3) / 1e9
+    return {
+        "k_predictor": {"ms": pred_avg, "tflops": info["flops_predictor"] / (pred_avg / 1e3) / 1e12,
+                        "gbs": info["bytes_predictor"] / (pred_avg / 1e3) / 1e9},
+        "k_corrector": {"ms": corr_avg, "tflops": info["flops_corrector"] / (corr_avg / 1e3) / 1e12,
+                        "gbs": corr_gbs, "hbm_frac": corr_gbs / hbm, "hbm_peak_gbs": hbm},
+    }
+
+
+def _equal_l2(A, w, steps):
+    """Advance the FP64 and the mixed path `steps` CFL steps from the same
+    initial state; relative L2 distance of the two and each one's L2 error
+    against the exact translated vortex."""
+    import numpy as np
+
+    from paper_1808_03788_gb300 import inputs
+    out = {}
+    res = {}
+    for name, prec in (("fp64", A.ADERDG_FP64), ("mixed", A.ADERDG_MIXED_FP32)):
+        with A.Solver(w["pde"], w["dim"], w["cells"], w["lo"], w["hi"], w["N"], w["params"], precision=prec) as s:
+            X = s.node_coords(w["lo"], w["hi"])
+            s.set_state(_initial_state(w, X))
+            s.advance(1e30, max_steps=steps)
+            U, t, k = s.get_state()
+            _, wq = A.aderdg_gl_nodes(w["N"])
+            res[name] = (U, t, k, X, wq)
+    U64, t64, k64, X, wq = res["fp64"]
+    Umx, tmx, kmx, _, _ = res["mixed"]
+    n = w["N"] + 1
+    wn = np.ones(1)
+    for _ in range(w["dim"]):
+        wn = np.kron(wq, wn)
+    vol = np.prod([(w["hi"][d] - w["lo"][d]) / w["cells"][d] for d in range(w["dim"])])
+    W = (vol * wn)[None, :, None]
+    l2 = lambda a: np.sqrt(np.sum(W * a * a, axis=(0, 1)))
+    rel = float(np.max(l2(Umx - U64) / l2(U64)))
+    out["steps"] = k64
+    out["t"] = t64
+    out["mixed_vs_fp64_rel_l2"] = rel
+    if w["ic"] == "vortex":
+        out["fp64_l2_err_vs_exact_rho"] = float(l2(U64 - inputs.euler_vortex(X, t=t64))[0])
+        out["mixed_l2_err_vs_exact_rho"] = float(l2(Umx - inputs.euler_vortex(X, t=tmx))[0])
+    out["equal_at_1e-6"] = rel <= 1e-6
+    return out
+
+
+def _batched(A, torch, steps, warmup, count):
+    """The batched workload: `count` independent 2D Euler vortex solves
+    (meshes k^2, k in {32, ..., 256}; N in 2..6; eps in [1, 5]; centres in
+    [3, 7]^2; seed 1808), FP32 predictor / FP64 update, one graph step each."""
+    from paper_1808_03788_gb300 import inputs
+    rec = inputs.batched_vortex_recipe(count)
+    specs = [A.make_spec(2, 2, r["cells"], (0, 0), (10, 10), r["N"], (1.4,)) for r in rec]
+    b = A.Batch(specs, precision=A.ADERDG_MIXED_FP32, torch_alloc=False)
+    nodes = {N: A.aderdg_gl_nodes(N)[0] for N in range(2, 7)}
+    for i, r in enumerate(rec):
+        X = inputs.node_coords_torch(r["cells"], (0, 0), (10, 10), nodes[r["N"]])
+        b.set_state(i, inputs.euler_vortex_torch(X, eps=r["eps"], center=r["center"]))
+        del X
+    info = b.info()
+    t_far = [1e30] * count
+    b.advance(t_far, max_steps=warmup)
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    b.advance(None, max_steps=steps)
+    t1.record()
+    t1.synchronize()
+    ms = t0.elapsed_time(t1)
+    b.close()
+    return {"value": info["dofs"] * steps / (ms / 1e3), "unit": UNIT, "solves": count,
+            "dofs_per_step": info["dofs"], "groups": info["groups"], "steps": steps,
+            "ms_per_step": ms / steps, "device_bytes": info["device_bytes"],
+            "timing": "CUDA events around aderdg_batch_advance (graph-replayed, host check every 8 steps)",
+            "dtype": "f32+f64"}
+
+
+def _served(A, requests, rate, seed=1808):
+    """The served stream: the first `requests` of the seeded Poisson stream
+    (mean `rate`/s, 50/50 2D Euler vortex / 3D elasticity pulse, run to
+    t = 1), submitted at their arrival times to a continuous-batching server."""
+    import numpy as np
+
+    from paper_1808_03788_gb300 import inputs
+    rec = inputs.served_stream_recipe(requests, rate, seed)
+    srv = A.Server(precision=A.ADERDG_MIXED_FP32)
+    prepared = []
+    for r in rec:
+        if r["pde"] == 2:
+            spec = A.make_spec(2, 2, r["cells"], (0, 0), (10, 10), r["N"], (1.4,))
+            x, _ = A.aderdg_gl_nodes(r["N"])
+            X = inputs.node_coords_torch(r["cells"], (0, 0), (10, 10), x, device="cpu")
+            u0 = inputs.euler_vortex_torch(X, eps=r["eps"], center=r["center"]).numpy()
+        else:
+            spec = A.make_spec(3, 3, r["cells"], (0, 0, 0), (1, 1, 1), r["N"], (1.0, 2.0, 1.0))
+            x, _ = A.aderdg_gl_nodes(r["N"])
+            X = inputs.node_coords_torch(r["cells"], (0,) * 3, (1,) * 3, x, device="cpu")
+            u0 = inputs.elastic_pulse_torch(X, x0=r["x0"]).numpy()
+        prepared.append((r["arrival"], spec, u0, r["t_end"], A.spec_size(spec) // A.nvar(r["pde"], r["dim"])))
+    t0 = time.perf_counter()
+    tickets = []
+    for arr, spec, u0, t_end, dofs in prepared:
+        delay = arr - (time.perf_counter() - t0)
+        if delay > 0:
+            time.sleep(delay)
+        tickets.append((srv.submit(spec, u0, t_end), dofs))
+    results = {}
+    while len(results) < len(tickets):
+        for tk, dofs in tickets:
+            if tk not in results:
+                r = srv.poll(tk)
+                if r is not None:
+                    results[tk] = (r, dofs)
+        time.sleep(0.001)
+    makespan = time.perf_counter() - t0
+    srv.close()
+    lat = np.array([r["latency_s"] for r, _ in results.values()])
+    work = sum(r["steps"] * d for r, d in results.values())
+    ok = sum(1 for r, _ in results.values() if r["status"] == 0)
+    return {"requests": len(tickets), "ok": ok, "rate_per_s": rate, "p50_latency_s": float(np.percentile(lat, 50)),
+            "p99_latency_s": float(np.percentile(lat, 99)), "mean_queue_s":
+                float(np.mean([r["queue_s"] for r, _ in results.values()])),
+            "makespan_s": makespan, "dof_updates": work, "value": work / makespan, "unit": UNIT,
+            "dtype": "f32+f64"}
+
+
+def run_ours(args, w, rank, world):
+    import numpy as np
+    import torch
+
+    import paper_1808_03788_gb300.aderdg as A
+
+    stream = torch.cuda.Stream()
+    prec = A.ADERDG_FP64 if args.precision == "fp64" else A.ADERDG_MIXED_FP32
+    cfgd = _config(args, w, world)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+
+    clocks = ClockSampler(_gpu_id() if rank == 0 else None)
+    if rank == 0:
+        clocks.start()
+    s, U0, step_ms, pred_ms, corr_ms = _time_single(A, torch, w, prec, stream, args.steps, args.warmup, flush, world)
+    clk = clocks.stop() if rank == 0 else None
+    info = s.info()
+    assert (info["cfl_alpha"], info["picard_iters"], info["dofs"]) == \
+        (cfgd["cfl_alpha"], cfgd["picard_iters"], cfgd["dofs"]), (info, cfgd)
+    dofs = info["dofs"]
     total_ms = sum(step_ms)
     if world > 1:
         t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
@@ -275,10 +426,10 @@ def run_ours(args, w, rank, world):
     value = world * dofs * args.steps / (total_ms / 1e3)
 
     # ---- end to end through the public API with host buffers ------------------
+    t_far = 1e30
     e2e_steps = max(1, min(args.steps, args.e2e_steps))
     host_in = torch.from_numpy(U0.copy()).pin_memory()
     host_out = torch.empty_like(host_in).pin_memory()
-    s.profile(False)
     e2e_ms = []
     with torch.cuda.stream(stream):
         for _ in range(2):
@@ -294,6 +445,7 @@ def run_ours(args, w, rank, world):
             b.record(stream)
             b.synchronize()
             e2e_ms.append(a.elapsed_time(b))
+    s.close()
     e2e_total = sum(e2e_ms)
     if world > 1:
         t = torch.tensor([e2e_total], device="cuda", dtype=torch.float64)
@@ -305,50 +457,42 @@ def run_ours(args, w, rank, world):
            "steps": e2e_steps, "api": "aderdg_set_state(HOST) + aderdg_step + aderdg_get_state(HOST)"}
 
     if rank != 0:
-        s.close()
         return 0
 
     probe = {}
     for kind, name in ((0, "fp64"), (1, "fp32")):
         try:
-            probe[name] = A.aderdg_peak_tflops(kind)
-        except Exception as e:  # the probe is context only
+            probe[name] = None if args.no_probe else A.aderdg_peak_tflops(kind)
+        except Exception:  # the probe is context only
             probe[name] = None
-    pred_avg = statistics.mean(pred_ms)
-    corr_avg = statistics.mean(corr_ms)
-    if args.precision == "fp64":
-        achieved = info["flops_predictor"] / (pred_avg / 1e3) / 1e12
-        roofline = {"bound": "alu", "kernel": "k_predictor (FP64 DFMA pipe)", "achieved": achieved,
-                    "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                    "peak_source": "derived: 152 SMs x 2 DFMA/clock x 2070 MHz (nominal 1.25 TFLOP/s); "
-                                   "no FP64 figure in MEASURED_PEAKS.json",
-                    "peak_probe_tflops": probe.get("fp64"),
-                    "traffic": _traffic("k_predictor", args.workload, args.precision),
-                    "algorithmic_flops_per_launch": info["flops_predictor"],
-                    "launch_ms": pred_avg}
-    else:
-        achieved = info["flops_predictor"] / (pred_avg / 1e3) / 1e12
-        roofline = {"bound": "alu", "kernel": "k_predictor (FP32 FFMA pipe)", "achieved": achieved,
-                    "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
-                    "peak_source": "derived: 152 SMs x 128 FFMA lanes x 2070 MHz",
-                    "peak_probe_tflops": probe.get("fp32"),
-                    "traffic": _traffic("k_predictor", args.workload, args.precision),
-                    "algorithmic_flops_per_launch": info["flops_predictor"],
-                    "launch_ms": pred_avg}
-    corr_gbs = info["bytes_corrector"] / (corr_avg / 1e3) / 1e9
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         pass
     hbm = peaks.get("hbm_gbs", 6800.0)
-    kernels = {
-        "k_predictor": {"ms": pred_avg, "tflops": info["flops_predictor"] / (pred_avg / 1e3) / 1e12,
-                        "gbs": info["bytes_predictor"] / (pred_avg / 1e3) / 1e9},
-        "k_corrector": {"ms": corr_avg, "tflops": info["flops_corrector"] / (corr_avg / 1e3) / 1e12,
-                        "gbs": corr_gbs, "hbm_frac": corr_gbs / hbm,
-                        "hbm_peak_gbs": hbm},
-    }
+    pred_avg, corr_avg = statistics.mean(pred_ms), statistics.mean(corr_ms)
+    roofline = _roofline(info, pred_avg, args.precision, probe, args.workload)
+    kernels = _kernels(info, pred_avg, corr_avg, hbm)
+
+    # ---- the rest of the metric: mixed at equal L2 error, batched, served ----------
+    variants = {}
+    if not args.no_variants:
+        other = "mixed" if args.precision == "fp64" else "fp64"
+        oprec = A.ADERDG_MIXED_FP32 if other == "mixed" else A.ADERDG_FP64
+        s2, _, st2, pr2, co2 = _time_single(A, torch, w, oprec, stream, args.steps, args.warmup, flush, 1)
+        i2 = s2.info()
+        s2.close()
+        p2, c2 = statistics.mean(pr2), statistics.mean(co2)
+        variants[other] = {"value": dofs * args.steps / (sum(st2) / 1e3), "ms_per_step": sum(st2) / args.steps,
+                           "unit": UNIT, "dtype": "f32+f64" if other == "mixed" else "f64",
+                           "roofline": _roofline(i2, p2, other, probe, args.workload),
+                           "kernels": _kernels(i2, p2, c2, hbm)}
+        variants["equal_l2"] = _equal_l2(A, w, args.l2_steps)
+        if args.batched_solves > 0:
+            variants["batched"] = _batched(A, torch, max(8, min(args.steps, 64)), 8, args.batched_solves)
+        if args.served_requests > 0:
+            variants["served"] = _served(A, args.served_requests, args.served_rate)
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
@@ -363,16 +507,16 @@ def run_ours(args, w, rank, world):
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if args.precision == "fp64" else "f32+f64",
         "data": "synthetic",
-        "config": _config(args, w, world),
+        "config": cfgd,
         "roofline": roofline,
         "kernels": kernels,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "clocks": clk,
         "gpu_launches": 3 * args.steps,
+        "variants": variants,
     }
     print(json.dumps(line), flush=True)
-    s.close()
     return 0
 
 
@@ -387,6 +531,13 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--cpu-steps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-probe", action="store_true", help="skip the FMA peak probe")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="only the headline path (no mixed/batched/served/equal-L2 runs)")
+    ap.add_argument("--l2-steps", type=int, default=100)
+    ap.add_argument("--batched-solves", type=int, default=256)
+    ap.add_argument("--served-requests", type=int, default=24)
+    ap.add_argument("--served-rate", type=float, default=200.0)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("note: fewer than 3 warm-up steps", file=sys.stderr)

@@ -209,6 +209,99 @@ int aderdg_sync(aderdg_t *h);
 int aderdg_profile(aderdg_t *h, int enable);
 int aderdg_profile_read(aderdg_t *h, float *ms_predictor, float *ms_corrector);
 
+/* ---- many independent solves in one launch per step ----------------------
+ * A batch holds independent solves of any mix of meshes, degrees and PDEs.
+ * Each step computes every solve's own CFL dt on the device, then launches
+ * one predictor and one corrector per (PDE, dimension, degree, parameters)
+ * group, each covering all solves of that group (tiles of consecutive
+ * elements numbered solve after solve); aderdg_batch_advance replays the
+ * step sequence as one CUDA graph per step.  A solve's arithmetic does not
+ * depend on the batch it is in: its results are bitwise the same alone and
+ * in any mix. */
+typedef struct aderdg_batch_s aderdg_batch_t;
+
+typedef struct {
+    aderdg_mesh_t mesh;
+    int N;
+    aderdg_pde_t pde;
+} aderdg_solve_spec_t;
+
+/* Create a batch of `count` solves (state zero, t = 0).  cfg applies to all
+ * of them (precision, Picard count: 0 -> N+1 per solve, CFL alpha: 0 ->
+ * default per N, stream, allocator). */
+int aderdg_batch_create(const aderdg_solve_spec_t *specs, int count, const aderdg_config_t *cfg,
+                        aderdg_batch_t **out);
+int aderdg_batch_destroy(aderdg_batch_t *b);
+
+/* Upload / download the state of solve i (layout as for a single solve). */
+int aderdg_batch_set_state(aderdg_batch_t *b, int i, const double *u, int where, double t);
+int aderdg_batch_get_state(aderdg_batch_t *b, int i, double *u, int where, double *t, int64_t *step);
+
+/* One step of every solve that has not reached its t_end (t_end: `count`
+ * host doubles, or NULL to keep the previous ones). */
+int aderdg_batch_step(aderdg_batch_t *b, const double *t_end);
+
+/* Steps until every solve reaches t_end[i] (host array, or NULL to keep
+ * the previous ones) or max_steps; the step sequence is a replayed CUDA
+ * graph.  Synchronises every few steps.  Returns ADERDG_E_NONFINITE if any
+ * solve produced a non-finite value (the others keep going). */
+int aderdg_batch_advance(aderdg_batch_t *b, const double *t_end, int64_t max_steps);
+
+/* Totals: DOFs (sum over solves of E (N+1)^d), device bytes, groups. */
+int aderdg_batch_info(const aderdg_batch_t *b, int64_t *dofs, size_t *device_bytes, int *groups);
+
+/* Per-solve status after a synchronising call: 0 running, 1 done (t >=
+ * t_end), ADERDG_E_NONFINITE.  status: `count` ints (host). */
+int aderdg_batch_status(aderdg_batch_t *b, int *status);
+
+/* ---- serving: continuous batching of incoming solves --------------------
+ * A server owns a device-memory budget and a background scheduler thread.
+ * aderdg_submit copies a request (mesh, N, PDE, initial state, t_end) and
+ * returns a ticket at once.  The scheduler admits queued requests while
+ * their device memory fits the budget (oldest first), keeps admitted
+ * states resident, advances all of them together in batched steps (new
+ * requests join between steps, finished ones leave), and copies each
+ * finished state back to host memory.  aderdg_poll reports PENDING until
+ * then, after which the result stays readable until aderdg_release. */
+typedef struct aderdg_server_s aderdg_server_t;
+
+typedef struct {
+    size_t device_budget_bytes;  /* 0: 90 % of the free device memory */
+    int max_queue;               /* queued (not yet admitted) requests; 0: 100000 */
+    int steps_per_round;         /* steps between admission rounds; 0: 8 */
+    int precision;               /* ADERDG_FP64 / ADERDG_MIXED_FP32 */
+    void *cuda_stream;           /* NULL: a stream of the server's own */
+} aderdg_server_config_t;
+
+typedef struct {
+    aderdg_solve_spec_t spec;
+    const double *u0;            /* host, E (N+1)^d m doubles, copied */
+    double t_end;
+} aderdg_request_t;
+
+typedef struct {
+    int status;                  /* ADERDG_OK, ADERDG_PENDING or an error */
+    double latency_s;            /* submit -> result on the host */
+    double queue_s;              /* submit -> admission */
+    double t;                    /* final time */
+    int64_t steps;
+    const double *u;             /* final state (library-owned until release) */
+    size_t n_values;
+} aderdg_result_t;
+
+int aderdg_server_create(const aderdg_server_config_t *cfg, aderdg_server_t **out);
+/* Stops the scheduler, drops unfinished requests, frees everything. */
+int aderdg_server_destroy(aderdg_server_t *s);
+/* ADERDG_E_BUSY if the queue is full, ADERDG_E_NOMEM if the request could
+ * never fit the budget, ADERDG_E_INVAL / UNSUPPORTED for bad specs. */
+int aderdg_submit(aderdg_server_t *s, const aderdg_request_t *req, uint64_t *ticket);
+int aderdg_poll(aderdg_server_t *s, uint64_t ticket, aderdg_result_t *res);
+int aderdg_release(aderdg_server_t *s, uint64_t ticket);
+int aderdg_cancel(aderdg_server_t *s, uint64_t ticket);
+/* Server counters: queued, active, finished, device bytes in use. */
+int aderdg_server_stats(aderdg_server_t *s, int64_t *queued, int64_t *active, int64_t *finished,
+                        size_t *bytes_in_use);
+
 /* ---- a step that allocates nothing ---------------------------------------
  * The paper has no counterpart; this is an integration aid of the library.
  *

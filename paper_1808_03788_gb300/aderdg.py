@@ -67,6 +67,24 @@ class aderdg_info_t(C.Structure):
                 ("bytes_corrector", C.c_double), ("device_bytes", C.c_size_t)]
 
 
+class aderdg_solve_spec_t(C.Structure):
+    _fields_ = [("mesh", aderdg_mesh_t), ("N", C.c_int), ("pde", aderdg_pde_t)]
+
+
+class aderdg_server_config_t(C.Structure):
+    _fields_ = [("device_budget_bytes", C.c_size_t), ("max_queue", C.c_int), ("steps_per_round", C.c_int),
+                ("precision", C.c_int), ("cuda_stream", C.c_void_p)]
+
+
+class aderdg_request_t(C.Structure):
+    _fields_ = [("spec", aderdg_solve_spec_t), ("u0", C.POINTER(C.c_double)), ("t_end", C.c_double)]
+
+
+class aderdg_result_t(C.Structure):
+    _fields_ = [("status", C.c_int), ("latency_s", C.c_double), ("queue_s", C.c_double), ("t", C.c_double),
+                ("steps", C.c_int64), ("u", C.POINTER(C.c_double)), ("n_values", C.c_size_t)]
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -96,6 +114,23 @@ _SIGS = {
     "aderdg_profile": (C.c_int, [_H, C.c_int]),
     "aderdg_profile_read": (C.c_int, [_H, C.POINTER(C.c_float), C.POINTER(C.c_float)]),
     "aderdg_peak_tflops": (C.c_int, [C.c_int, _DP]),
+    "aderdg_batch_create": (C.c_int, [C.POINTER(aderdg_solve_spec_t), C.c_int, C.POINTER(aderdg_config_t),
+                                      C.POINTER(_H)]),
+    "aderdg_batch_destroy": (C.c_int, [_H]),
+    "aderdg_batch_set_state": (C.c_int, [_H, C.c_int, C.c_void_p, C.c_int, C.c_double]),
+    "aderdg_batch_get_state": (C.c_int, [_H, C.c_int, C.c_void_p, C.c_int, _DP, C.POINTER(C.c_int64)]),
+    "aderdg_batch_step": (C.c_int, [_H, _DP]),
+    "aderdg_batch_advance": (C.c_int, [_H, _DP, C.c_int64]),
+    "aderdg_batch_info": (C.c_int, [_H, C.POINTER(C.c_int64), C.POINTER(C.c_size_t), C.POINTER(C.c_int)]),
+    "aderdg_batch_status": (C.c_int, [_H, C.POINTER(C.c_int)]),
+    "aderdg_server_create": (C.c_int, [C.POINTER(aderdg_server_config_t), C.POINTER(_H)]),
+    "aderdg_server_destroy": (C.c_int, [_H]),
+    "aderdg_submit": (C.c_int, [_H, C.POINTER(aderdg_request_t), C.POINTER(C.c_uint64)]),
+    "aderdg_poll": (C.c_int, [_H, C.c_uint64, C.POINTER(aderdg_result_t)]),
+    "aderdg_release": (C.c_int, [_H, C.c_uint64]),
+    "aderdg_cancel": (C.c_int, [_H, C.c_uint64]),
+    "aderdg_server_stats": (C.c_int, [_H, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                      C.POINTER(C.c_size_t)]),
     "aderdg_step_noalloc": (C.c_int, [C.POINTER(aderdg_mesh_t), C.c_int, C.c_int, C.POINTER(aderdg_pde_t),
                                       C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_double, C.c_void_p]),
 }
@@ -416,3 +451,168 @@ def aderdg_step_noalloc(pde: int, dim: int, cells, lo, hi, N: int, params, u_in,
     _check(load().aderdg_step_noalloc(C.byref(mesh), N, nvar(pde, dim), C.byref(p), precision, picard,
                                       C.c_void_p(u_in.data_ptr()), C.c_void_p(u_out.data_ptr()),
                                       float(dt), C.c_void_p(int(stream) if stream else 0)))
+
+
+# ---- batched solves -------------------------------------------------------------
+
+def make_spec(pde: int, dim: int, cells, lo, hi, N: int, params=()) -> aderdg_solve_spec_t:
+    sp = aderdg_solve_spec_t()
+    sp.mesh.dim = dim
+    for d in range(3):
+        sp.mesh.cells[d] = int(cells[d]) if d < dim else 1
+        sp.mesh.lo[d] = float(lo[d]) if d < dim else 0.0
+        sp.mesh.hi[d] = float(hi[d]) if d < dim else 1.0
+    sp.N = N
+    sp.pde.kind = pde
+    for i, v in enumerate(params):
+        sp.pde.p[i] = float(v)
+    return sp
+
+
+def spec_size(sp: aderdg_solve_spec_t) -> int:
+    dim = sp.mesh.dim
+    E = 1
+    for d in range(dim):
+        E *= sp.mesh.cells[d]
+    return E * (sp.N + 1) ** dim * nvar(sp.pde.kind, dim)
+
+
+class Batch:
+    """Many independent solves advanced together (aderdg_batch_*)."""
+
+    def __init__(self, specs, precision: int = ADERDG_FP64, picard: int = 0, alpha: float = 0.0,
+                 stream=None, torch_alloc: bool = True):
+        L = load()
+        self._L = L
+        self.specs = list(specs)
+        arr = (aderdg_solve_spec_t * len(self.specs))(*self.specs)
+        cfg = aderdg_config_t()
+        cfg.precision = precision
+        cfg.picard_iters = picard
+        cfg.cfl_alpha = alpha
+        if stream is not None:
+            cfg.cuda_stream = C.c_void_p(int(stream))
+        self._alloc = None
+        if torch_alloc:
+            self._alloc = _TorchAllocator()
+            cfg.alloc = C.pointer(self._alloc.struct)
+        self._h = _H()
+        _check(L.aderdg_batch_create(arr, len(self.specs), C.byref(cfg), C.byref(self._h)))
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._L.aderdg_batch_destroy(self._h)
+            self._h = _H()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __len__(self):
+        return len(self.specs)
+
+    def set_state(self, i: int, u, t: float = 0.0):
+        if hasattr(u, "data_ptr"):  # device tensor
+            assert u.is_cuda and u.is_contiguous() and u.numel() == spec_size(self.specs[i])
+            _check(self._L.aderdg_batch_set_state(self._h, i, C.c_void_p(u.data_ptr()), ADERDG_DEVICE, float(t)))
+            return
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        assert u.size == spec_size(self.specs[i])
+        _check(self._L.aderdg_batch_set_state(self._h, i, u.ctypes.data, ADERDG_HOST, float(t)))
+
+    def get_state(self, i: int, check: bool = True):
+        u = np.empty(spec_size(self.specs[i]))
+        t = C.c_double(0)
+        k = C.c_int64(0)
+        rc = self._L.aderdg_batch_get_state(self._h, i, u.ctypes.data, ADERDG_HOST, C.byref(t), C.byref(k))
+        if check:
+            _check(rc)
+        return u, t.value, k.value
+
+    def step(self, t_end=None):
+        te = None if t_end is None else np.ascontiguousarray(np.broadcast_to(t_end, (len(self),)), dtype=np.float64)
+        _check(self._L.aderdg_batch_step(self._h, None if te is None else te.ctypes.data_as(_DP)))
+
+    def advance(self, t_end=None, max_steps: int = 2 ** 62, check: bool = True):
+        te = None if t_end is None else np.ascontiguousarray(np.broadcast_to(t_end, (len(self),)), dtype=np.float64)
+        rc = self._L.aderdg_batch_advance(self._h, None if te is None else te.ctypes.data_as(_DP), int(max_steps))
+        if check:
+            _check(rc)
+        return rc
+
+    def status(self):
+        st = (C.c_int * len(self))()
+        _check(self._L.aderdg_batch_status(self._h, st))
+        return list(st)
+
+    def info(self):
+        d, b, g = C.c_int64(0), C.c_size_t(0), C.c_int(0)
+        _check(self._L.aderdg_batch_info(self._h, C.byref(d), C.byref(b), C.byref(g)))
+        return {"dofs": d.value, "device_bytes": b.value, "groups": g.value}
+
+
+# ---- serving ------------------------------------------------------------------------
+
+class Server:
+    """Continuous-batching request server (aderdg_server_*)."""
+
+    def __init__(self, precision: int = ADERDG_FP64, budget_bytes: int = 0, max_queue: int = 0,
+                 steps_per_round: int = 0):
+        L = load()
+        self._L = L
+        cfg = aderdg_server_config_t()
+        cfg.device_budget_bytes = budget_bytes
+        cfg.max_queue = max_queue
+        cfg.steps_per_round = steps_per_round
+        cfg.precision = precision
+        self._h = _H()
+        _check(L.aderdg_server_create(C.byref(cfg), C.byref(self._h)))
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._L.aderdg_server_destroy(self._h)
+            self._h = _H()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, spec: aderdg_solve_spec_t, u0, t_end: float) -> int:
+        u0 = np.ascontiguousarray(u0, dtype=np.float64)
+        assert u0.size == spec_size(spec)
+        req = aderdg_request_t()
+        req.spec = spec
+        req.u0 = u0.ctypes.data_as(_DP)
+        req.t_end = float(t_end)
+        tk = C.c_uint64(0)
+        _check(self._L.aderdg_submit(self._h, C.byref(req), C.byref(tk)))
+        return tk.value
+
+    def poll(self, ticket: int):
+        """None while pending, else a dict (state copied out as numpy)."""
+        r = aderdg_result_t()
+        rc = self._L.aderdg_poll(self._h, C.c_uint64(ticket), C.byref(r))
+        if rc == ADERDG_PENDING:
+            return None
+        out = {"status": r.status, "latency_s": r.latency_s, "queue_s": r.queue_s, "t": r.t, "steps": r.steps,
+               "u": None}
+        if r.status == ADERDG_OK and r.u:
+            out["u"] = np.ctypeslib.as_array(r.u, shape=(r.n_values,)).copy()
+        if rc < 0 and r.status == ADERDG_PENDING:
+            _check(rc)
+        return out
+
+    def release(self, ticket: int):
+        _check(self._L.aderdg_release(self._h, C.c_uint64(ticket)))
+
+    def cancel(self, ticket: int):
+        _check(self._L.aderdg_cancel(self._h, C.c_uint64(ticket)))
+
+    def stats(self):
+        q, a, f, b = C.c_int64(0), C.c_int64(0), C.c_int64(0), C.c_size_t(0)
+        _check(self._L.aderdg_server_stats(self._h, C.byref(q), C.byref(a), C.byref(f), C.byref(b)))
+        return {"queued": q.value, "active": a.value, "finished": f.value, "bytes": b.value}

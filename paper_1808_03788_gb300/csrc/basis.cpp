@@ -135,6 +135,36 @@ int build_basis(int N, Basis &b)
     return 0;
 }
 
+namespace {
+template <typename T>
+void fill_typed(const Basis &b, Ops<T> &o)
+{
+    std::memset(&o, 0, sizeof(o));
+    const int n = b.n;
+    for (int d = 0; d < 3; ++d)
+        for (int i = 0; i < n * n; ++i) {
+            o.Dm[d][i] = T(-b.D[i]);
+            o.Kv[d][i] = T(b.Kw[i]);
+        }
+    for (int i = 0; i < n * n; ++i) o.iK1W[i] = T(b.iK1W[i]);
+    for (int t = 0; t < n; ++t) {
+        double c = 0.0;
+        for (int tp = 0; tp < n; ++tp) c += b.iK1W[t * n + tp];
+        o.c1[t] = T(c);
+        o.w[t] = T(b.w[t]);
+        o.F0[t] = T(b.F0[t]);
+        o.F1[t] = T(b.F1[t]);
+        o.inv_w[t] = T(b.inv_w[t]);
+    }
+}
+}  // namespace
+
+void fill_ops(KParams &kp)
+{
+    fill_typed<double>(kp.b, kp.od);
+    fill_typed<float>(kp.b, kp.of);
+}
+
 // 0.9 x the von Neumann stability limit of the scheme for 1D linear
 // advection (limits 0.3335, 0.1709, 0.1040, 0.0699, 0.0501, 0.0377, 0.0294,
 // 0.0236, 0.0193 for N = 1..9); the paper bounds alpha by 1/(2N+1) only.

@@ -51,9 +51,26 @@ struct PdeParams {
     double p[8];
 };
 
-// Kernel parameter block (passed by value).
-struct KParams {
+// Operators in the compute type (filled on the host by fill_ops).  Indexed
+// with compile-time constants inside unrolled loops, they are read straight
+// from the kernel-parameter constant bank.  They do not depend on the mesh
+// spacing, so one table serves every solve of a launch.
+template <typename T>
+struct Ops {
+    T Dm[3][NMAX * NMAX];  // -Dhat                   [i][j] (same for every d)
+    T Kv[3][NMAX * NMAX];  // Kw                      [k][j] (same for every d)
+    T iK1W[NMAX * NMAX];   // K1^{-1} W               [t][t']
+    T c1[NMAX];            // row sums of iK1W (time integral of a constant)
+    T w[NMAX], F0[NMAX], F1[NMAX], inv_w[NMAX];
+};
+
+// One solve of a launch (device memory).  Tiles of EPB consecutive
+// elements are numbered solve after solve: this solve owns tiles
+// [tile0_p, tile0_p + ceil(E / EPB_predictor)) of the predictor launch and
+// likewise tile0_c for the corrector.
+struct SolveDesc {
     long long E;
+    long long tile0_p, tile0_c;
     int cells[3];
     int picard;
     double inv_dx[3];
@@ -62,12 +79,24 @@ struct KParams {
     void *V;           // volume term          [E][NS][M] of T
     void *tr;          // trace records        [E][DIM][2][NF][RS] of T
     Control *ctl;
+};
+
+// Kernel parameter block (passed by value).
+struct KParams {
+    const SolveDesc *solves;  // device array, tile0 ascending
+    int nsolves;
+    int use_ctl_dt;           // 1: dt of each solve from its ctl->dt, 0: dt_arg
+    long long ntiles;         // tiles of this launch (predictor or corrector)
     double dt_arg;
-    int use_ctl_dt;    // 1: dt from ctl->dt (device-side CFL), 0: dt_arg
-    int pad;
     PdeParams pde;
     Basis b;
+    Ops<double> od;
+    Ops<float> of;
 };
+
+template <typename T> __host__ __device__ inline const Ops<T> &ops_of(const KParams &P);
+template <> __host__ __device__ inline const Ops<double> &ops_of<double>(const KParams &P) { return P.od; }
+template <> __host__ __device__ inline const Ops<float> &ops_of<float>(const KParams &P) { return P.of; }
 
 __host__ __device__ constexpr int ipow(int b, int e)
 {
@@ -182,14 +211,6 @@ struct Geom {
     static constexpr int NF = ipow(n, DIM - 1);    // nodes per face
     static constexpr int RS = 2 * M + 2;           // trace record: q(M) F(M) lambda pad
     static constexpr int NREC = DIM * 2 * NF;      // records per element
-    // predictor: one thread per space-time node
-    static constexpr int P_TPE = round_up(NST, 32);
-    static constexpr int P_EPB = P_TPE >= 256 ? 1 : 256 / P_TPE;
-    static constexpr int P_THREADS = P_TPE * P_EPB;
-    // corrector: one thread per spatial node (at least a warp)
-    static constexpr int C_TPE = round_up(NS, 32);
-    static constexpr int C_EPB = C_TPE >= 256 ? 1 : 256 / C_TPE;
-    static constexpr int C_THREADS = C_TPE * C_EPB;
 };
 
 // Host-visible description of the compiled kernels of one (PDE, d, N, precision).

@@ -7,12 +7,17 @@
 //  k_corrector  Rusanov fluxes on the time-averaged traces (eq. pc.scheme
 //               with B = 0, eq. rusanov), surface lift and element update
 //               (eq. pde.nc.gw2), wave-speed maxima for the next CFL step
+//  k_cfl        wave-speed maxima of a state (first step after an upload)
 //
-// One CTA holds EPB elements; each element is worked on by a group of
-// threads, one per space-time node (predictor) or spatial node (corrector).
-// The element's working set lives in shared memory and registers, so u^n is
-// read once and the space-time DOFs never touch HBM (the cache-blocking
-// property of Sec. 2.2 mapped onto an SM).
+// Every launch serves a list of independent solves (same PDE, dimension
+// and degree; any mesh size and spacing) described by SolveDesc entries in
+// device memory.  The launch's tiles -- EPB consecutive elements of one
+// solve -- are numbered solve after solve; a CTA finds its solve by binary
+// search over the tile offsets and loops over tiles with a grid stride, so
+// the grid can be sized to the GPU (persistent) or to the tile count.
+// Within a tile the element working set stays in shared memory and
+// registers: u^n is read once and the space-time DOFs never reach HBM (the
+// cache-blocking property of Sec. 2.2 mapped onto an SM).
 #pragma once
 
 #include "common.cuh"
@@ -22,360 +27,621 @@ namespace aderdg {
 template <typename T>
 __device__ __forceinline__ T tmax(T a, T b) { return a > b ? a : b; }
 
-// shared-memory footprint (bytes) of the predictor, shared part + per group
-template <class PDE, int DIM, int N, typename T>
-struct PredSmem {
-    using G = Geom<PDE, DIM, N>;
-    static constexpr int SHARED = round_up(3 * G::n * G::n + 3 * G::n, 2);
-    // work buffer: space-time values, later the per-face traces
-    static constexpr int BUFN = G::NST > G::NREC ? G::NST : G::NREC;
-    static constexpr int GROUP = BUFN * G::M + G::NS * G::M * (2 + DIM);
-    static constexpr size_t BYTES = sizeof(T) * (size_t)(SHARED + G::P_EPB * GROUP);
+__host__ __device__ constexpr int cmin(int a, int b) { return a < b ? a : b; }
+__host__ __device__ constexpr int cmax(int a, int b) { return a > b ? a : b; }
+__host__ __device__ constexpr int cgcd(int a, int b) { return b == 0 ? a : cgcd(b, a % b); }
+__host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) / 16 * 16; }
+
+// Load/store the M values of one node with the widest vector access the
+// node size allows (float4 for 4 floats, 2 x double2 for 4 doubles, ...).
+template <int B> struct VecOf;
+template <> struct VecOf<16> { using t = float4; };
+template <> struct VecOf<8> { using t = float2; };
+template <> struct VecOf<4> { using t = float; };
+
+template <typename T, int M>
+struct NodeIO {
+    static constexpr int BYTES = (int)sizeof(T) * M;
+    static constexpr int VB = BYTES % 16 == 0 ? 16 : (BYTES % 8 == 0 ? 8 : (int)sizeof(T));
+    static constexpr int K = VB / (int)sizeof(T);  // values per access
+    using VT = typename VecOf<VB>::t;
+    __device__ __forceinline__ static void load(const T *p, T *x)
+    {
+#pragma unroll
+        for (int i = 0; i < M / K; ++i) {
+            const VT w = reinterpret_cast<const VT *>(p)[i];
+            const T *ws = reinterpret_cast<const T *>(&w);
+#pragma unroll
+            for (int k = 0; k < K; ++k) x[i * K + k] = ws[k];
+        }
+    }
+    __device__ __forceinline__ static void store(T *p, const T *x)
+    {
+#pragma unroll
+        for (int i = 0; i < M / K; ++i) {
+            VT w;
+            T *ws = reinterpret_cast<T *>(&w);
+#pragma unroll
+            for (int k = 0; k < K; ++k) ws[k] = x[i * K + k];
+            reinterpret_cast<VT *>(p)[i] = w;
+        }
+    }
 };
 
+// Tile -> solve: the last solve whose first tile is <= tile.
+__device__ __forceinline__ int find_solve(const SolveDesc *S, int nsolves, long long tile, int which)
+{
+    int lo = 0, hi = nsolves - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        const long long t0 = which ? S[mid].tile0_c : S[mid].tile0_p;
+        if (t0 <= tile) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ double solve_dt(const KParams &P, const SolveDesc &S)
+{
+    return P.use_ctl_dt ? S.ctl->dt : P.dt_arg;
+}
+
+// ===========================================================================
+// Predictor
+// ===========================================================================
+//
+// Thread (element g, spatial node s) owns the time pencil q[0..n)[0..M) of
+// node s in registers.  One Picard iteration:
+//   1. F_d(q[t]) at its n nodes -> shared buffer F_d[t][s][v]
+//   2. each thread takes one d-pencil per direction (there are exactly NS of
+//      them: n time levels x NF face positions) and overwrites it in place
+//      with -Dhat F_d (the n x n operator is read from the parameter bank
+//      with compile-time indices)
+//   3. back on the time pencil: R = sum_d (1/dx_d) (-Dhat F_d),
+//      q[t] = u + dt sum_t' iK1W[t][t'] R[t']
+// The first iteration starts from q = u, constant in time, so its flux and
+// derivatives are taken once per spatial node and q[t] = u + dt c1[t] R with
+// c1 the row sums of iK1W (the general iteration applied to a time-constant q).
 template <class PDE, int DIM, int N, typename T>
-__global__ void __launch_bounds__(Geom<PDE, DIM, N>::P_THREADS)
+struct PredCfg {
+    using G = Geom<PDE, DIM, N>;
+    static constexpr int n = G::n, M = G::M, NS = G::NS, NST = G::NST, NF = G::NF, NREC = G::NREC;
+    static constexpr int DIMS = DIM;
+    // per-element shared buffer: DIM space-time flux fields, later
+    // qbar | Fbar_d | face-trace stash
+    static constexpr int ELEM = cmax(DIM * NST * M, ((1 + DIM) * NS + NREC) * M);
+    // FP64: smaller CTAs, several per SM (independent barrier domains keep
+    // the DFMA pipe fed); FP32: 256-thread CTAs
+    static constexpr int TARGET = sizeof(T) == 8 ? 128 : 256;
+    static constexpr int MINB = sizeof(T) == 8 ? (n * M < 24 ? 3 : 2) : ((n * M <= 20 || (M == 9 && n <= 4)) ? 3 : 2);
+    static constexpr int EPB_T = cmax(1, TARGET / NS);
+    static constexpr int EPB_S = cmax(1, (int)((110 * 1024) / (ELEM * sizeof(T))));
+    static constexpr int EPB = cmin(EPB_T, EPB_S);
+    static constexpr int THREADS = round_up(EPB * NS, 32);
+    static constexpr int SHARED = round_up(DIM * n * n + 2 * n, 4);  // Kw, F0, F1
+    static constexpr size_t BYTES = sizeof(T) * (size_t)(SHARED + EPB * ELEM);
+};
+
+// -Dhat F_d along direction D on pencil (t, p), in place.
+template <class C, int D, typename T>
+__device__ __forceinline__ void contract_pencil(T *Fd, int t, int p, const T *Dm)
+{
+    constexpr int n = C::n, M = C::M, NS = C::NS;
+    constexpr int pd = ipow(n, D);
+    using IO = NodeIO<T, M>;
+    const int s0 = (p % pd) + (p / pd) * pd * n;
+    T *base = Fd + (t * NS + s0) * M;
+    T x[n][M];
+#pragma unroll
+    for (int j = 0; j < n; ++j) IO::load(base + j * pd * M, x[j]);
+#pragma unroll
+    for (int i = 0; i < n; ++i) {
+        T y[M];
+#pragma unroll
+        for (int v = 0; v < M; ++v) {
+            T acc = Dm[i * n] * x[0][v];
+#pragma unroll
+            for (int j = 1; j < n; ++j) acc += Dm[i * n + j] * x[j][v];
+            y[v] = acc;
+        }
+        IO::store(base + i * pd * M, y);
+    }
+}
+
+template <class C, typename T, int D = 0>
+__device__ __forceinline__ void contract_all(T *ebuf, int t, int p, const Ops<T> &O)
+{
+    if constexpr (D < C::DIMS) {
+        contract_pencil<C, D, T>(ebuf + D * C::NST * C::M, t, p, O.Dm[D]);
+        contract_all<C, T, D + 1>(ebuf, t, p, O);
+    }
+}
+
+// dx_0 R at time level t of node s: R_0 + sum_{d>0} (dx_0/dx_d) R_d (the
+// factor 1/dx_0 is folded into dt by the caller, so isotropic and
+// anisotropic meshes cost the same).
+template <class C, typename T>
+__device__ __forceinline__ void gather_R(const T *ebuf, int t, int s, const T *ratio, T *R)
+{
+    constexpr int M = C::M, NS = C::NS, NST = C::NST;
+    NodeIO<T, M>::load(ebuf + (t * NS + s) * M, R);
+#pragma unroll
+    for (int d = 1; d < C::DIMS; ++d) {
+        T r[M];
+        NodeIO<T, M>::load(ebuf + (d * NST + t * NS + s) * M, r);
+#pragma unroll
+        for (int v = 0; v < M; ++v) R[v] += ratio[d] * r[v];
+    }
+}
+
+template <class PDE, int DIM, int N, typename T>
+__global__ void __launch_bounds__(PredCfg<PDE, DIM, N, T>::THREADS, PredCfg<PDE, DIM, N, T>::MINB)
 k_predictor(const KParams P)
 {
-    using G = Geom<PDE, DIM, N>;
-    using S = PredSmem<PDE, DIM, N, T>;
-    constexpr int n = G::n, M = G::M, NS = G::NS, NST = G::NST, NF = G::NF;
-    constexpr int TPE = G::P_TPE, EPB = G::P_EPB, RS = G::RS;
-
-    const double dt = P.use_ctl_dt ? P.ctl->dt : P.dt_arg;
-    if (!(dt > 0.0)) return;  // uniform over the grid: no step in flight
+    using C = PredCfg<PDE, DIM, N, T>;
+    constexpr int n = C::n, M = C::M, NS = C::NS, NST = C::NST, NF = C::NF, NREC = C::NREC;
+    constexpr int EPB = C::EPB, RS = Geom<PDE, DIM, N>::RS;
+    const Ops<T> &O = ops_of<T>(P);
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *sD = reinterpret_cast<T *>(smem_raw);
-    T *sA = sD + n * n;     // dt * iK1 W
-    T *sK = sA + n * n;     // Kw
-    T *sF0 = sK + n * n;
+    T *sKw = reinterpret_cast<T *>(smem_raw);  // DIM x n x n (unscaled)
+    T *sF0 = sKw + DIM * n * n;
     T *sF1 = sF0 + n;
-    T *sw = sF1 + n;
-    const int g = threadIdx.x / TPE;
-    const int l = threadIdx.x - g * TPE;
-    T *buf = reinterpret_cast<T *>(smem_raw) + S::SHARED + g * S::GROUP;  // BUFN*M
-    T *qbar = buf + S::BUFN * M;      // NS*M
-    T *Fbar = qbar + NS * M;          // DIM*NS*M
-    T *us = Fbar + DIM * NS * M;      // NS*M
+    const int tid = threadIdx.x;
+    const bool act = tid < EPB * NS;
+    const int g = act ? tid / NS : 0;
+    const int s = act ? tid - g * NS : 0;
+    const int tk = s / NF, pk = s - (s / NF) * NF;  // this thread's d-pencils
+    T *ebuf = reinterpret_cast<T *>(smem_raw) + C::SHARED + g * C::ELEM;
+    T *sQ = ebuf;                             // qbar[s][v]
+    T *sFb = ebuf + NS * M;                   // Fbar[d][s][v]
+    T *sStash = ebuf + (1 + DIM) * NS * M;    // face traces of qbar
 
-    for (int i = threadIdx.x; i < n * n; i += blockDim.x) {
-        sD[i] = T(P.b.D[i]);
-        sA[i] = T(dt * P.b.iK1W[i]);
-        sK[i] = T(P.b.Kw[i]);
+    for (int i = tid; i < DIM * n * n; i += blockDim.x) sKw[i] = O.Kv[i / (n * n)][i % (n * n)];
+    for (int i = tid; i < n; i += blockDim.x) {
+        sF0[i] = O.F0[i];
+        sF1[i] = O.F1[i];
     }
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        sF0[i] = T(P.b.F0[i]);
-        sF1[i] = T(P.b.F1[i]);
-        sw[i] = T(P.b.w[i]);
-    }
-
-    const long long e = (long long)blockIdx.x * EPB + g;
-    const bool valid = e < P.E;
-    const long long ec = valid ? e : P.E - 1;  // tail groups recompute the last element
-    const double *ue = P.u + ec * (NS * M);
-    for (int i = l; i < NS * M; i += TPE) us[i] = T(ue[i]);
     __syncthreads();
 
-    const int node = l;
-    const bool act = node < NST;
-    const int t = act ? node / NS : 0;
-    const int s = act ? node - t * NS : 0;
-    int sd[DIM];
-    {
-        int r = s;
-#pragma unroll
-        for (int d = 0; d < DIM; ++d) { sd[d] = r % n; r /= n; }
-    }
-    T u0[M], q[M];
-#pragma unroll
-    for (int v = 0; v < M; ++v) { u0[v] = us[s * M + v]; q[v] = u0[v]; }
-
-    // ---- Picard iterations of eq. pde.st2 --------------------------------
-    for (int it = 0; it < P.picard; ++it) {
-        T F[DIM][M];
-        PDE::flux(P.pde, q, F);
-        T R[M];
-#pragma unroll
-        for (int v = 0; v < M; ++v) R[v] = T(0);
+    for (long long tile = blockIdx.x; tile < P.ntiles; tile += gridDim.x) {
+        const int si = find_solve(P.solves, P.nsolves, tile, 0);
+        const SolveDesc &S = P.solves[si];
+        const double dt = solve_dt(P, S);
+        if (!(dt > 0.0)) continue;  // uniform over the CTA: this solve takes no step
+        const T dtT = T(dt * S.inv_dx[0]);  // dt / dx_0 (see gather_R)
+        T idx[DIM], ratio[DIM];
 #pragma unroll
         for (int d = 0; d < DIM; ++d) {
+            idx[d] = T(S.inv_dx[d]);
+            ratio[d] = T(S.inv_dx[d] / S.inv_dx[0]);
+        }
+
+        const long long e = (tile - S.tile0_p) * EPB + g;
+        const bool valid = act && e < S.E;
+        const long long ec = e < S.E ? e : S.E - 1;  // tail groups recompute the last element
+        T u[M];
+#pragma unroll
+        for (int v = 0; v < M; ++v) u[v] = T(S.u[(ec * NS + s) * M + v]);
+
+        T q[n][M];
+        // ---- iteration 1 from the time-constant guess ----------------------
+        {
+            T F[DIM][M];
+            PDE::flux(P.pde, u, F);
             if (act) {
 #pragma unroll
-                for (int v = 0; v < M; ++v) buf[node * M + v] = F[d][v];
+                for (int d = 0; d < DIM; ++d) NodeIO<T, M>::store(ebuf + (d * NST + s) * M, F[d]);
             }
             __syncthreads();
-            if (act) {
-                const int stride = ipow(n, d);
-                const int base = node - sd[d] * stride;
-                const T *Drow = sD + sd[d] * n;
-                const T idx = T(P.inv_dx[d]);
+            if (act && s < NF) contract_all<C, T>(ebuf, 0, s, O);
+            __syncthreads();
+            T R[M];
+            gather_R<C, T>(ebuf, 0, s, ratio, R);
 #pragma unroll
-                for (int v = 0; v < M; ++v) {
-                    T acc = T(0);
+            for (int t = 0; t < n; ++t)
 #pragma unroll
-                    for (int j = 0; j < n; ++j) acc += Drow[j] * buf[(base + j * stride) * M + v];
-                    R[v] -= idx * acc;
+                for (int v = 0; v < M; ++v) q[t][v] = u[v] + dtT * (O.c1[t] * R[v]);
+            __syncthreads();
+        }
+        // ---- remaining Picard iterations of eq. pde.st2 --------------------
+        for (int it = 1; it < S.picard; ++it) {
+#pragma unroll
+            for (int t = 0; t < n; ++t) {
+                T F[DIM][M];
+                PDE::flux(P.pde, q[t], F);
+                if (act) {
+#pragma unroll
+                    for (int d = 0; d < DIM; ++d) NodeIO<T, M>::store(ebuf + (d * NST + t * NS + s) * M, F[d]);
                 }
             }
             __syncthreads();
-        }
-        if (act) {
+            if (act) contract_all<C, T>(ebuf, tk, pk, O);
+            __syncthreads();
+            {
+                T R[n][M];
 #pragma unroll
-            for (int v = 0; v < M; ++v) buf[node * M + v] = R[v];
+                for (int t = 0; t < n; ++t) gather_R<C, T>(ebuf, t, s, ratio, R[t]);
+#pragma unroll
+                for (int v = 0; v < M; ++v)
+#pragma unroll
+                    for (int t = 0; t < n; ++t) {
+                        T acc = O.iK1W[t * n] * R[0][v];
+#pragma unroll
+                        for (int tp = 1; tp < n; ++tp) acc += O.iK1W[t * n + tp] * R[tp][v];
+                        q[t][v] = u[v] + dtT * acc;
+                    }
+            }
+            __syncthreads();
         }
-        __syncthreads();
-        if (act) {
-            const T *Arow = sA + t * n;
+
+        // ---- time averages qbar, Fbar_d (registers) ------------------------
+        T qb[M], Fb[DIM][M];
+#pragma unroll
+        for (int v = 0; v < M; ++v) {
+            qb[v] = T(0);
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) Fb[d][v] = T(0);
+        }
+#pragma unroll
+        for (int t = 0; t < n; ++t) {
+            T F[DIM][M];
+            PDE::flux(P.pde, q[t], F);
+            const T wt = O.w[t];
 #pragma unroll
             for (int v = 0; v < M; ++v) {
-                T acc = T(0);
+                qb[v] += wt * q[t][v];
 #pragma unroll
-                for (int tp = 0; tp < n; ++tp) acc += Arow[tp] * buf[(tp * NS + s) * M + v];
-                q[v] = u0[v] + acc;
+                for (int d = 0; d < DIM; ++d) Fb[d][v] += wt * F[d][v];
+            }
+        }
+        if (act) {
+            NodeIO<T, M>::store(sQ + s * M, qb);
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) NodeIO<T, M>::store(sFb + (d * NS + s) * M, Fb[d]);
+        }
+        __syncthreads();
+
+        // ---- volume term V = sum_d (1/dx_d) Kw Fbar_d ----------------------
+        if (valid) {
+            T *Vout = reinterpret_cast<T *>(S.V) + ec * (NS * M);
+            int kd[DIM];
+            {
+                int r = s;
+#pragma unroll
+                for (int d = 0; d < DIM; ++d) { kd[d] = r % n; r /= n; }
+            }
+            T Vn[M];
+#pragma unroll
+            for (int v = 0; v < M; ++v) Vn[v] = T(0);
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) {
+                const int pd = ipow(n, d);
+                const int base = s - kd[d] * pd;
+                const T *Krow = sKw + (d * n + kd[d]) * n;
+                T a[M];
+#pragma unroll
+                for (int v = 0; v < M; ++v) a[v] = T(0);
+#pragma unroll
+                for (int j = 0; j < n; ++j) {
+                    T f[M];
+                    NodeIO<T, M>::load(sFb + (d * NS + base + j * pd) * M, f);
+#pragma unroll
+                    for (int v = 0; v < M; ++v) a[v] += Krow[j] * f[v];
+                }
+#pragma unroll
+                for (int v = 0; v < M; ++v) Vn[v] += idx[d] * a[v];
+            }
+#pragma unroll
+            for (int v = 0; v < M; ++v) Vout[s * M + v] = Vn[v];
+        }
+
+        // ---- face traces of the time averages ------------------------------
+        T *trE = reinterpret_cast<T *>(S.tr) + ec * (NREC * RS);
+        if (act) {
+            for (int i = s; i < NREC * M; i += NS) {
+                const int rec = i / M, v = i - rec * M;
+                const int d = rec / (2 * NF);
+                const int side = (rec / NF) & 1;
+                const int p = rec - (rec / NF) * NF;
+                const int pd = ipow(n, d);
+                const int s0 = (p % pd) + (p / pd) * pd * n;
+                const T *phi = side ? sF1 : sF0;
+                T aq = T(0), af = T(0);
+#pragma unroll
+                for (int j = 0; j < n; ++j) {
+                    aq += phi[j] * sQ[(s0 + j * pd) * M + v];
+                    af += phi[j] * sFb[(d * NS + s0 + j * pd) * M + v];
+                }
+                sStash[rec * M + v] = aq;
+                if (valid) {
+                    trE[rec * RS + v] = aq;
+                    trE[rec * RS + M + v] = af;
+                }
             }
         }
         __syncthreads();
-    }
-
-    // ---- time averages qbar, Fbar_d --------------------------------------
-    T F[DIM][M];
-    PDE::flux(P.pde, q, F);
-    if (act) {
-#pragma unroll
-        for (int v = 0; v < M; ++v) buf[node * M + v] = q[v];
-    }
-    __syncthreads();
-    for (int i = l; i < NS * M; i += TPE) {
-        T acc = T(0);
-#pragma unroll
-        for (int tt = 0; tt < n; ++tt) acc += sw[tt] * buf[tt * NS * M + i];
-        qbar[i] = acc;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int d = 0; d < DIM; ++d) {
-        if (act) {
-#pragma unroll
-            for (int v = 0; v < M; ++v) buf[node * M + v] = F[d][v];
-        }
-        __syncthreads();
-        for (int i = l; i < NS * M; i += TPE) {
-            T acc = T(0);
-#pragma unroll
-            for (int tt = 0; tt < n; ++tt) acc += sw[tt] * buf[tt * NS * M + i];
-            Fbar[d * NS * M + i] = acc;
-        }
-        __syncthreads();
-    }
-
-    // ---- volume term V = sum_d (1/dx_d) Kw_d Fbar_d ------------------------
-    T *Vout = reinterpret_cast<T *>(P.V) + ec * (NS * M);
-    for (int i = l; i < NS * M; i += TPE) {
-        const int si = i / M, v = i - si * M;
-        T acc = T(0);
-        int r = si;
-#pragma unroll
-        for (int d = 0; d < DIM; ++d) {
-            const int k = r % n;
-            r /= n;
-            const int stride = ipow(n, d);
-            const int base = si - k * stride;
-            const T *Krow = sK + k * n;
-            T a = T(0);
-#pragma unroll
-            for (int j = 0; j < n; ++j) a += Krow[j] * Fbar[(d * NS + base + j * stride) * M + v];
-            acc += T(P.inv_dx[d]) * a;
-        }
-        if (valid) Vout[i] = acc;
-    }
-
-    // ---- face traces of the time averages ----------------------------------
-    T *trE = reinterpret_cast<T *>(P.tr) + ec * (G::NREC * RS);
-    for (int i = l; i < G::NREC * M; i += TPE) {
-        const int rec = i / M, v = i - rec * M;
-        const int d = rec / (2 * NF);
-        const int side = (rec / NF) & 1;
-        const int p = rec - (rec / NF) * NF;
-        const int pd = ipow(n, d);
-        const int s0 = (p % pd) + (p / pd) * pd * n;
-        const T *phi = side ? sF1 : sF0;
-        T aq = T(0), af = T(0);
-#pragma unroll
-        for (int j = 0; j < n; ++j) {
-            aq += phi[j] * qbar[(s0 + j * pd) * M + v];
-            af += phi[j] * Fbar[(d * NS + s0 + j * pd) * M + v];
-        }
-        buf[rec * M + v] = aq;  // for the wave speed below
         if (valid) {
-            trE[rec * RS + v] = aq;
-            trE[rec * RS + M + v] = af;
+            for (int rec = s; rec < NREC; rec += NS) {
+                const int d = rec / (2 * NF);
+                trE[rec * RS + 2 * M] = PDE::max_eig(P.pde, sStash + rec * M, d);
+                trE[rec * RS + 2 * M + 1] = T(0);
+            }
         }
-    }
-    __syncthreads();
-    for (int rec = l; rec < G::NREC; rec += TPE) {
-        const int d = rec / (2 * NF);
-        const T lam = PDE::max_eig(P.pde, buf + rec * M, d);
-        if (valid) {
-            trE[rec * RS + 2 * M] = lam;
-            trE[rec * RS + 2 * M + 1] = T(0);
-        }
+        __syncthreads();  // ebuf is reused by the next tile
     }
 }
 
+// ===========================================================================
+// Corrector
+// ===========================================================================
+
+// Non-finite test and double -> float narrowing on the integer bits
+// (truncating the mantissa; values below the float range become 0).  The
+// wave speeds of the mixed path only feed the CFL maxima, so truncation is
+// harmless, and the FP64 pipe stays free for the state update.
+__device__ __forceinline__ bool dbl_nonfinite(double x)
+{
+    return ((__double2hiint(x) >> 20) & 0x7ff) == 0x7ff;
+}
+
+__device__ __forceinline__ float dbl_to_flt_trunc(double x)
+{
+    const int hi = __double2hiint(x);
+    const unsigned lo = (unsigned)__double2loint(x);
+    const unsigned sign = (unsigned)hi & 0x80000000u;
+    const int e = ((hi >> 20) & 0x7ff) - 1023 + 127;
+    const unsigned mant = (((unsigned)hi & 0xfffffu) << 3) | (lo >> 29);
+    unsigned bits = sign | ((unsigned)e << 23) | mant;
+    bits = e <= 0 ? sign : bits;
+    bits = e >= 255 ? (sign | 0x7f800000u) : bits;
+    return __uint_as_float(bits);
+}
+
+template <typename T>
+__device__ __forceinline__ T narrow(double x);
+template <>
+__device__ __forceinline__ double narrow<double>(double x) { return x; }
+template <>
+__device__ __forceinline__ float narrow<float>(double x) { return dbl_to_flt_trunc(x); }
+
+// A CTA takes a tile of EPB consecutive elements.  All its inputs -- its own
+// trace records (one contiguous range), the 2d neighbour face chunks of
+// every element, u^n and V -- are staged into shared memory with cp.async
+// first (every load in flight at once), then: Rusanov flux per (element,
+// face node, variable); lift and FP64 update per (element, node, variable)
+// with coalesced stores; wave-speed maxima per node, one atomic per CTA.
+
+__device__ __forceinline__ void cp_async(void *dst, const void *src, int bytes)
+{
+    const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+    if (bytes == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(src));
+    else if (bytes == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(src));
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(src));
+}
+
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+template <int GRAN>
+__device__ __forceinline__ void stage(void *dst, const void *src, int bytes)
+{
+    const int units = bytes / GRAN;
+    unsigned char *d = static_cast<unsigned char *>(dst);
+    const unsigned char *s = static_cast<const unsigned char *>(src);
+    for (int i = threadIdx.x; i < units; i += blockDim.x) cp_async(d + i * GRAN, s + i * GRAN, GRAN);
+}
+
 template <class PDE, int DIM, int N, typename T>
-struct CorrSmem {
+struct CorrCfg {
     using G = Geom<PDE, DIM, N>;
-    static constexpr int SHARED = 3 * NMAX;  // F0, F1, 1/w (double)
-    static constexpr int GROUP = G::NREC * G::M + G::NS * G::M;  // F*, u^{n+1}
-    static constexpr size_t BYTES = sizeof(double) * SHARED + sizeof(T) * (size_t)G::C_EPB * G::NREC * G::M
-                                    + sizeof(double) * (size_t)G::C_EPB * G::NS * G::M + 64 * sizeof(double);
+    static constexpr int n = G::n, M = G::M, NS = G::NS, NF = G::NF, NREC = G::NREC, RS = G::RS;
+    static constexpr size_t OWN = sizeof(T) * NREC * RS;          // per element
+    static constexpr size_t NB = sizeof(T) * 2 * DIM * NF * RS;   // per element
+    static constexpr size_t UB = sizeof(double) * NS * M;
+    static constexpr size_t VB = sizeof(T) * NS * M;
+    static constexpr size_t FS = sizeof(T) * NREC * M;
+    static constexpr size_t PER_ELEM = align16(OWN) + align16(NB) + align16(UB) + align16(VB) + align16(FS);
+    static constexpr int EPB_T = cmax(1, 256 / NS);
+    static constexpr int EPB_S = cmax(1, (int)((110 * 1024) / PER_ELEM));
+    static constexpr int EPB = cmin(EPB_T, EPB_S);
+    static constexpr int THREADS = 256;
+    static constexpr size_t O_OWN = 0;
+    static constexpr size_t O_NB = align16(EPB * OWN);
+    static constexpr size_t O_U = O_NB + align16(EPB * NB);
+    static constexpr size_t O_V = O_U + align16(EPB * UB);
+    static constexpr size_t O_FS = O_V + align16(EPB * VB);
+    static constexpr size_t O_LIFT = O_FS + align16(EPB * FS);
+    static constexpr size_t O_NBIDX = O_LIFT + align16(sizeof(T) * 2 * 3 * NMAX);
+    static constexpr size_t O_RED = O_NBIDX + align16(sizeof(int) * EPB * 2 * DIM);
+    static constexpr size_t BYTES = O_RED + 64 * sizeof(double);
+    // copy granules (bytes): the largest of 16/8/4 dividing offsets and sizes
+    static constexpr int G_OWN = cgcd((int)OWN, 16);
+    static constexpr int G_NB = cgcd((int)(sizeof(T) * RS), 16);
+    static constexpr int G_U = cgcd((int)UB, 16);
+    static constexpr int G_V = cgcd((int)VB, 16);
 };
 
-__device__ __forceinline__ long long neighbour(long long e, const int *cells, int d, int off)
+// neighbour of element e (x-fastest numbering, cells cx, cy, cz) along d,
+// periodic
+__device__ __forceinline__ int neighbour(int e, int cx, int cy, int cz, int d, int off)
 {
-    long long idx[3] = {0, 0, 0}, r = e;
-    idx[0] = r % cells[0]; r /= cells[0];
-    idx[1] = r % cells[1]; r /= cells[1];
-    idx[2] = r;
-    long long c = idx[d] + off;
-    if (c < 0) c += cells[d];
-    if (c >= cells[d]) c -= cells[d];
-    idx[d] = c;
-    return idx[0] + (long long)cells[0] * (idx[1] + (long long)cells[1] * idx[2]);
+    int ix = e % cx;
+    const int r = e / cx;
+    int iy = r % cy;
+    int iz = r / cy;
+    if (d == 0) ix = ix + off < 0 ? cx - 1 : (ix + off >= cx ? 0 : ix + off);
+    else if (d == 1) iy = iy + off < 0 ? cy - 1 : (iy + off >= cy ? 0 : iy + off);
+    else iz = iz + off < 0 ? cz - 1 : (iz + off >= cz ? 0 : iz + off);
+    return ix + cx * (iy + cy * iz);
 }
 
 template <class PDE, int DIM, int N, typename T>
-__global__ void __launch_bounds__(Geom<PDE, DIM, N>::C_THREADS)
+__global__ void __launch_bounds__(256)
 k_corrector(const KParams P)
 {
-    using G = Geom<PDE, DIM, N>;
-    constexpr int n = G::n, M = G::M, NS = G::NS, NF = G::NF, RS = G::RS;
-    constexpr int TPE = G::C_TPE, EPB = G::C_EPB, NREC = G::NREC;
-
-    const double dt = P.use_ctl_dt ? P.ctl->dt : P.dt_arg;
-    if (!(dt > 0.0)) return;
+    using C = CorrCfg<PDE, DIM, N, T>;
+    constexpr int n = C::n, M = C::M, NS = C::NS, NF = C::NF, NREC = C::NREC, RS = C::RS, EPB = C::EPB;
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    double *sF0 = reinterpret_cast<double *>(smem_raw);
-    double *sF1 = sF0 + NMAX;
-    double *sIw = sF1 + NMAX;
-    double *red = sIw + NMAX;  // 64 doubles for the block reduction
-    const int g = threadIdx.x / TPE;
-    const int l = threadIdx.x - g * TPE;
-    double *un = red + 64 + g * (NS * M);
-    T *Fs = reinterpret_cast<T *>(red + 64 + EPB * NS * M) + g * (NREC * M);
+    T *sOwn = reinterpret_cast<T *>(smem_raw + C::O_OWN);
+    T *sNb = reinterpret_cast<T *>(smem_raw + C::O_NB);
+    double *sU = reinterpret_cast<double *>(smem_raw + C::O_U);
+    T *sV = reinterpret_cast<T *>(smem_raw + C::O_V);
+    T *sFs = reinterpret_cast<T *>(smem_raw + C::O_FS);
+    T *sL = reinterpret_cast<T *>(smem_raw + C::O_LIFT);  // [side][d][k]
+    int *sNbIdx = reinterpret_cast<int *>(smem_raw + C::O_NBIDX);
+    double *red = reinterpret_cast<double *>(smem_raw + C::O_RED);
 
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        sF0[i] = P.b.F0[i];
-        sF1[i] = P.b.F1[i];
-        sIw[i] = P.b.inv_w[i];
-    }
-    const long long e = (long long)blockIdx.x * EPB + g;
-    const bool valid = e < P.E;
-    const long long ec = valid ? e : P.E - 1;
-    const T *tr = reinterpret_cast<const T *>(P.tr);
+    for (long long tile = blockIdx.x; tile < P.ntiles; tile += gridDim.x) {
+        const int si = find_solve(P.solves, P.nsolves, tile, 1);
+        const SolveDesc S = P.solves[si];
+        const double dt = solve_dt(P, S);
+        if (!(dt > 0.0)) continue;  // uniform over the CTA
 
-    // ---- Rusanov flux on every face node of this element -------------------
-    for (int i = l; i < NREC * M; i += TPE) {
-        const int rec = i / M, v = i - rec * M;
-        const int d = rec / (2 * NF);
-        const int side = (rec / NF) & 1;
-        const int p = rec - (rec / NF) * NF;
-        const long long en = neighbour(ec, P.cells, d, side ? 1 : -1);
-        const T *own = tr + (ec * NREC + rec) * RS;
-        const T *nb = tr + (en * NREC + (rec + (side ? -NF : NF))) * RS;
-        const T *L = side ? own : nb;
-        const T *R = side ? nb : own;
-        const T smax = tmax(L[2 * M], R[2 * M]);
-        Fs[rec * M + v] = T(0.5) * (L[M + v] + R[M + v]) - T(0.5) * smax * (R[v] - L[v]);
-        (void)p;
-    }
-    __syncthreads();
+        const int e0 = (int)((tile - S.tile0_c) * EPB);
+        const int ne = (S.E - e0) < EPB ? (int)(S.E - e0) : EPB;
+        const T *tr = reinterpret_cast<const T *>(S.tr);
 
-    // ---- surface lift and update u^{n+1} = u^n + dt (V - surface) ----------
-    const double *ue = P.u + ec * (NS * M);
-    const T *Ve = reinterpret_cast<const T *>(P.V) + ec * (NS * M);
-    double *uo = P.u_out + ec * (NS * M);
-    for (int i = l; i < NS * M; i += TPE) {
-        const int si = i / M, v = i - si * M;
-        T surf = T(0);
-        int r = si;
-#pragma unroll
-        for (int d = 0; d < DIM; ++d) {
-            const int k = r % n;
-            r /= n;
-            const int pd = ipow(n, d);
-            const int p = (si % pd) + (si / (pd * n)) * pd;
-            const T fp = Fs[((d * 2 + 1) * NF + p) * M + v];
-            const T fm = Fs[((d * 2 + 0) * NF + p) * M + v];
-            surf += T(P.inv_dx[d] * sIw[k]) * (T(sF1[k]) * fp - T(sF0[k]) * fm);
+        // ---- stage everything -----------------------------------------------
+        for (int c = threadIdx.x; c < ne * 2 * DIM; c += blockDim.x) {
+            const int el = c / (2 * DIM), d = (c / 2) % DIM, side = c & 1;
+            sNbIdx[c] = neighbour(e0 + el, S.cells[0], S.cells[1], S.cells[2], d, side ? 1 : -1);
         }
-        const double unew = ue[i] + dt * double(Ve[i] - surf);
-        un[i] = unew;
-        if (valid) uo[i] = unew;
-    }
-    __syncthreads();
+        for (int i = threadIdx.x; i < DIM * n; i += blockDim.x) {
+            const int d = i / n, k = i % n;
+            const double idx = P.solves[si].inv_dx[d];  // runtime index: read from global
+            sL[(0 * 3 + d) * NMAX + k] = T(idx * P.b.inv_w[k] * P.b.F0[k]);
+            sL[(1 * 3 + d) * NMAX + k] = T(idx * P.b.inv_w[k] * P.b.F1[k]);
+        }
+        stage<C::G_OWN>(sOwn, tr + (long long)e0 * NREC * RS, ne * (int)C::OWN);
+        stage<C::G_U>(sU, S.u + (long long)e0 * NS * M, ne * (int)C::UB);
+        stage<C::G_V>(sV, reinterpret_cast<const T *>(S.V) + (long long)e0 * NS * M, ne * (int)C::VB);
+        __syncthreads();  // neighbour indices
+        {
+            constexpr int units = (int)(sizeof(T) * NF * RS) / C::G_NB;
+            for (int i = threadIdx.x; i < ne * 2 * DIM * units; i += blockDim.x) {
+                const int u_ = i % units;
+                const int c = i / units;  // chunk (element, d, side)
+                const int d = (c / 2) % DIM;
+                const int side = c & 1;
+                const T *src = tr + (((long long)sNbIdx[c] * DIM + d) * 2 + (1 - side)) * NF * RS;
+                unsigned char *dst = reinterpret_cast<unsigned char *>(sNb + (size_t)c * NF * RS);
+                cp_async(dst + u_ * C::G_NB, reinterpret_cast<const unsigned char *>(src) + u_ * C::G_NB, C::G_NB);
+            }
+        }
+        cp_async_wait_all();
+        __syncthreads();
 
-    // ---- wave-speed maxima of u^{n+1} and non-finite check -----------------
-    double lmax[DIM];
+        // ---- Rusanov flux per (element, face node, variable) ----------------
+        for (int i = threadIdx.x; i < ne * NREC * M; i += blockDim.x) {
+            const int el = i / (NREC * M);
+            const int r = i - el * (NREC * M);
+            const int rec = r / M, v = r - rec * M;
+            const int d = rec / (2 * NF);
+            const int side = (rec / NF) & 1;
+            const int p = rec - (rec / NF) * NF;
+            const T *own = sOwn + (el * NREC + rec) * RS;
+            const T *nb = sNb + ((size_t)(el * DIM + d) * 2 + side) * NF * RS + p * RS;
+            const T *L = side ? own : nb;
+            const T *R = side ? nb : own;
+            const T smax = tmax(L[2 * M], R[2 * M]);
+            sFs[(el * NREC + rec) * M + v] = T(0.5) * (L[M + v] + R[M + v]) - T(0.5) * smax * (R[v] - L[v]);
+        }
+        __syncthreads();
+
+        // ---- surface lift and update u^{n+1} = u^n + dt (V - surface) ------
+        double *uo = S.u_out + (long long)e0 * NS * M;
+        for (int i = threadIdx.x; i < ne * NS * M; i += blockDim.x) {
+            const int el = i / (NS * M);
+            const int r = i - el * (NS * M);
+            const int sn = r / M, v = r - sn * M;
+            T surf = T(0);
+            int rr = sn;
 #pragma unroll
-    for (int d = 0; d < DIM; ++d) lmax[d] = 0.0;
-    bool bad = false;
-    if (valid) {
-        for (int si = l; si < NS; si += TPE) {
+            for (int d = 0; d < DIM; ++d) {
+                const int k = rr % n;
+                rr /= n;
+                const int pd = ipow(n, d);
+                const int p = (sn % pd) + (sn / (pd * n)) * pd;
+                const T fp = sFs[(el * NREC + (d * 2 + 1) * NF + p) * M + v];
+                const T fm = sFs[(el * NREC + (d * 2 + 0) * NF + p) * M + v];
+                surf += sL[(3 + d) * NMAX + k] * fp - sL[d * NMAX + k] * fm;
+            }
+            const double unew = sU[i] + dt * double(sV[i] - surf);
+            sU[i] = unew;
+            uo[i] = unew;
+        }
+        __syncthreads();
+
+        // ---- wave-speed maxima of u^{n+1} and non-finite check -------------
+        // (in the compute type T; only the per-CTA maxima are widened)
+        T lmax[DIM];
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) lmax[d] = T(0);
+        bool bad = false;
+        for (int i = threadIdx.x; i < ne * NS; i += blockDim.x) {
             T qs[M];
 #pragma unroll
             for (int v = 0; v < M; ++v) {
-                const double x = un[si * M + v];
-                bad |= !isfinite(x);
-                qs[v] = T(x);
+                const double x = sU[i * M + v];
+                bad |= dbl_nonfinite(x);
+                qs[v] = narrow<T>(x);
             }
 #pragma unroll
             for (int d = 0; d < DIM; ++d) {
-                const double lam = double(PDE::max_eig(P.pde, qs, d));
-                bad |= !(lam >= 0.0);
-                lmax[d] = fmax(lmax[d], lam);
+                const T lam = PDE::max_eig(P.pde, qs, d);
+                bad |= !(lam >= T(0));
+                lmax[d] = lam > lmax[d] ? lam : lmax[d];
             }
         }
-    }
 #pragma unroll
-    for (int d = 0; d < DIM; ++d) {
-        double x = lmax[d];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
-        lmax[d] = x;
-    }
-    const unsigned anybad = __any_sync(0xffffffffu, bad);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    __syncthreads();  // 'red' is free: everyone is past the update loop
-    if (lane == 0) {
-#pragma unroll
-        for (int d = 0; d < DIM; ++d) red[warp * 4 + d] = lmax[d];
-        red[warp * 4 + 3] = anybad ? 1.0 : 0.0;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const int nw = blockDim.x >> 5;
-        double b = 0.0;
         for (int d = 0; d < DIM; ++d) {
-            double x = 0.0;
-            for (int w = 0; w < nw; ++w) x = fmax(x, red[w * 4 + d]);
-            atomicMax(&P.ctl->lam_acc[d], (unsigned long long)__double_as_longlong(x));
+            T x = lmax[d];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const T y = __shfl_xor_sync(0xffffffffu, x, o);
+                x = y > x ? y : x;
+            }
+            lmax[d] = x;
         }
-        for (int w = 0; w < nw; ++w) b = fmax(b, red[w * 4 + 3]);
-        if (b > 0.0) atomicOr(&P.ctl->flags, FLAG_NONFINITE);
+        const unsigned anybad = __any_sync(0xffffffffu, bad);
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        if (lane == 0) {
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) red[warp * 4 + d] = double(lmax[d]);
+            red[warp * 4 + 3] = anybad ? 1.0 : 0.0;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const int nw = blockDim.x >> 5;
+            double b = 0.0;
+            for (int d = 0; d < DIM; ++d) {
+                double x = 0.0;
+                for (int w = 0; w < nw; ++w) x = fmax(x, red[w * 4 + d]);
+                atomicMax(&S.ctl->lam_acc[d], (unsigned long long)__double_as_longlong(x));
+            }
+            for (int w = 0; w < nw; ++w) b = fmax(b, red[w * 4 + 3]);
+            if (b > 0.0) atomicOr(&S.ctl->flags, FLAG_NONFINITE);
+        }
+        __syncthreads();  // shared buffers are reused by the next tile
     }
 }
 
-// Wave-speed maxima of the current state (the CFL input of the first step
-// after a state upload): grid-stride over all nodes, one atomic per warp.
+// Wave-speed maxima of the current state of solve 0 of the launch (the CFL
+// input of the first step after an upload): grid-stride over all nodes,
+// one atomic per warp.
 template <class PDE, int DIM, int N, typename T>
 __global__ void __launch_bounds__(256) k_cfl(const KParams P)
 {
     using G = Geom<PDE, DIM, N>;
     constexpr int M = G::M;
-    const long long total = P.E * G::NS;
+    const SolveDesc &S = P.solves[0];
+    const long long total = S.E * G::NS;
     double lmax[DIM];
 #pragma unroll
     for (int d = 0; d < DIM; ++d) lmax[d] = 0.0;
@@ -385,9 +651,9 @@ __global__ void __launch_bounds__(256) k_cfl(const KParams P)
         T q[M];
 #pragma unroll
         for (int v = 0; v < M; ++v) {
-            const double x = P.u[i * M + v];
-            bad |= !isfinite(x);
-            q[v] = T(x);
+            const double x = S.u[i * M + v];
+            bad |= dbl_nonfinite(x);
+            q[v] = narrow<T>(x);
         }
 #pragma unroll
         for (int d = 0; d < DIM; ++d) {
@@ -401,22 +667,23 @@ __global__ void __launch_bounds__(256) k_cfl(const KParams P)
         double x = lmax[d];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
-        if ((threadIdx.x & 31) == 0) atomicMax(&P.ctl->lam_acc[d], (unsigned long long)__double_as_longlong(x));
+        if ((threadIdx.x & 31) == 0) atomicMax(&S.ctl->lam_acc[d], (unsigned long long)__double_as_longlong(x));
     }
-    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(&P.ctl->flags, FLAG_NONFINITE);
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(&S.ctl->flags, FLAG_NONFINITE);
 }
 
 template <class PDE, int DIM, int N, typename T>
 struct KS {
-    using G = Geom<PDE, DIM, N>;
     static const KernelSet value;
 };
 
 template <class PDE, int DIM, int N, typename T>
 const KernelSet KS<PDE, DIM, N, T>::value = {
-    &k_predictor<PDE, DIM, N, T>, G::P_THREADS, G::P_EPB, PredSmem<PDE, DIM, N, T>::BYTES,
-    &k_corrector<PDE, DIM, N, T>, G::C_THREADS, G::C_EPB, CorrSmem<PDE, DIM, N, T>::BYTES,
+    &k_predictor<PDE, DIM, N, T>, PredCfg<PDE, DIM, N, T>::THREADS, PredCfg<PDE, DIM, N, T>::EPB,
+    PredCfg<PDE, DIM, N, T>::BYTES,
+    &k_corrector<PDE, DIM, N, T>, CorrCfg<PDE, DIM, N, T>::THREADS, CorrCfg<PDE, DIM, N, T>::EPB,
+    CorrCfg<PDE, DIM, N, T>::BYTES,
     &k_cfl<PDE, DIM, N, T>,
-    G::M, G::RS, (int)sizeof(T), PDE::FLUX_FLOPS, PDE::EIG_FLOPS};
+    Geom<PDE, DIM, N>::M, Geom<PDE, DIM, N>::RS, (int)sizeof(T), PDE::FLUX_FLOPS, PDE::EIG_FLOPS};
 
 }  // namespace aderdg

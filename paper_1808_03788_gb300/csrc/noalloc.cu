@@ -112,7 +112,7 @@ extern "C" int aderdg_step_noalloc(const aderdg_mesh_t *mesh, int N, int nVar, c
     const int NS = ipow(n, mesh->dim), NF = ipow(n, mesh->dim - 1), NREC = mesh->dim * 2 * NF;
     const size_t v_bytes = align256((size_t)E * NS * m * ks->elem_bytes);
     const size_t tr_bytes = align256((size_t)E * NREC * ks->rs * ks->elem_bytes);
-    const size_t need = v_bytes + tr_bytes + align256(sizeof(Control));
+    const size_t need = v_bytes + tr_bytes + align256(sizeof(Control)) + align256(sizeof(SolveDesc));
     if (need > SCRATCH_BYTES)
         return fail(ADERDG_E_INVAL, "mesh too large for the static scratch: needs " + std::to_string(need) +
                                         " bytes, limit " + std::to_string(SCRATCH_BYTES) + " bytes");
@@ -122,25 +122,32 @@ extern "C" int aderdg_step_noalloc(const aderdg_mesh_t *mesh, int N, int nVar, c
     if (rc) return rc;
     unsigned char *sb = static_cast<unsigned char *>(base);
     Control *ctl = reinterpret_cast<Control *>(sb + v_bytes + tr_bytes);
+    SolveDesc *d_desc = reinterpret_cast<SolveDesc *>(sb + v_bytes + tr_bytes + align256(sizeof(Control)));
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+
+    SolveDesc sd;
+    std::memset(&sd, 0, sizeof(sd));
+    sd.E = E;
+    for (int d = 0; d < 3; ++d) {
+        sd.cells[d] = d < mesh->dim ? (int)mesh->cells[d] : 1;
+        sd.inv_dx[d] = d < mesh->dim ? 1.0 / ((mesh->hi[d] - mesh->lo[d]) / mesh->cells[d]) : 1.0;
+    }
+    sd.picard = picard_iters > 0 ? picard_iters : N + 1;
+    sd.u = u_in;
+    sd.u_out = u_out;
+    sd.V = sb;
+    sd.tr = sb + v_bytes;
+    sd.ctl = ctl;
 
     KParams kp;
     std::memset(&kp, 0, sizeof(kp));
-    kp.E = E;
-    for (int d = 0; d < 3; ++d) {
-        kp.cells[d] = d < mesh->dim ? (int)mesh->cells[d] : 1;
-        kp.inv_dx[d] = d < mesh->dim ? 1.0 / ((mesh->hi[d] - mesh->lo[d]) / mesh->cells[d]) : 1.0;
-    }
-    kp.picard = picard_iters > 0 ? picard_iters : N + 1;
-    kp.u = u_in;
-    kp.u_out = u_out;
-    kp.V = sb;
-    kp.tr = sb + v_bytes;
-    kp.ctl = ctl;
+    kp.solves = d_desc;
+    kp.nsolves = 1;
     kp.dt_arg = dt;
     kp.use_ctl_dt = 0;
     for (int i = 0; i < 8; ++i) kp.pde.p[i] = pde->p[i];
     if (build_basis(N, kp.b)) return fail(ADERDG_E_INVAL, "basis construction failed");
+    fill_ops(kp);
 
     // large shared-memory kernels need the opt-in (no allocation involved)
     if (ks->pred_smem > 48 * 1024 &&
@@ -156,10 +163,14 @@ extern "C" int aderdg_step_noalloc(const aderdg_mesh_t *mesh, int N, int nVar, c
     // block: it must start at zero on every call
     cudaError_t e = cudaMemsetAsync(ctl, 0, sizeof(Control), st);
     if (e != cudaSuccess) return fail(ADERDG_E_CUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
-    const unsigned pb = (unsigned)((E + ks->pred_epb - 1) / ks->pred_epb);
-    ks->predictor<<<pb, ks->pred_threads, ks->pred_smem, st>>>(kp);
-    const unsigned cb = (unsigned)((E + ks->corr_epb - 1) / ks->corr_epb);
-    ks->corrector<<<cb, ks->corr_threads, ks->corr_smem, st>>>(kp);
+    // the descriptor is a copy into the scratch, not an allocation; the
+    // pageable source is consumed before cudaMemcpyAsync returns
+    e = cudaMemcpyAsync(d_desc, &sd, sizeof(sd), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return fail(ADERDG_E_CUDA, std::string("cudaMemcpyAsync: ") + cudaGetErrorString(e));
+    kp.ntiles = (E + ks->pred_epb - 1) / ks->pred_epb;
+    ks->predictor<<<(unsigned)kp.ntiles, ks->pred_threads, ks->pred_smem, st>>>(kp);
+    kp.ntiles = (E + ks->corr_epb - 1) / ks->corr_epb;
+    ks->corrector<<<(unsigned)kp.ntiles, ks->corr_threads, ks->corr_smem, st>>>(kp);
     e = cudaGetLastError();
     if (e != cudaSuccess) return fail(ADERDG_E_CUDA, std::string("launch: ") + cudaGetErrorString(e));
     return ADERDG_OK;

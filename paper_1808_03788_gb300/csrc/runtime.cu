@@ -13,6 +13,7 @@
 #include "../../include/aderdg.h"
 #include "basis.h"
 #include "common.cuh"
+#include "control.cuh"
 
 namespace aderdg {
 const KernelSet *ks_advection2d(int N, int prec);
@@ -67,37 +68,11 @@ int pde_nvar(int pde, int dim)
 // generic kernels
 // ---------------------------------------------------------------------------
 
-// CFL step of Sec. 3 from the maxima of the current state, clipped to
-// t_end; consumes the maxima (the corrector refills them for u^{n+1}).
+// CFL step of Sec. 3 for the handle's solve (control.cuh).
 __global__ void k_dt(Control *c)
 {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    const double t = c->t;
-    if (!(t < c->t_end)) {
-        c->dt = 0.0;
-        c->flags |= FLAG_DONE;
-        return;
-    }
-    c->flags &= ~FLAG_DONE;
-    double S = 0.0;
-    for (int d = 0; d < c->dim; ++d) {
-        const double lam = __longlong_as_double((long long)c->lam_acc[d]);
-        c->lam_used[d] = lam;
-        S += lam * c->inv_dx[d];
-    }
-    const double dtc = c->alpha / S;
-    double dt, tn;
-    if (t + dtc >= c->t_end) { dt = c->t_end - t; tn = c->t_end; }
-    else { dt = dtc; tn = t + dtc; }
-    if (!(dt > 0.0) || !isfinite(dt)) {  // non-finite maxima: stop, flag it
-        c->dt = 0.0;
-        c->flags |= FLAG_NONFINITE;
-        return;
-    }
-    c->dt = dt;
-    c->t = tn;
-    c->step += 1;
-    for (int d = 0; d < 3; ++d) c->lam_acc[d] = 0ull;
+    dt_update(c);
 }
 
 // dt the CFL condition gives for the current maxima (no clip, no update).
@@ -201,6 +176,9 @@ struct aderdg_s {
     double *host_pinned = nullptr;
     KParams kp{};
     Basis basis{};
+    SolveDesc desc{};             // host copy of the single solve's descriptor
+    SolveDesc *d_desc = nullptr;  // device copy
+    double inv_dx[3] = {1, 1, 1};
     size_t device_bytes = 0;
     cudaGraphExec_t graph = nullptr;
     int graph_steps = 0;
@@ -233,8 +211,8 @@ int launch_predictor(aderdg_t *h, int use_ctl, double dt)
     KParams kp = h->kp;
     kp.use_ctl_dt = use_ctl;
     kp.dt_arg = dt;
-    const long long blocks = (h->E + h->ks->pred_epb - 1) / h->ks->pred_epb;
-    h->ks->predictor<<<(unsigned)blocks, h->ks->pred_threads, h->ks->pred_smem, h->stream>>>(kp);
+    kp.ntiles = (h->E + h->ks->pred_epb - 1) / h->ks->pred_epb;
+    h->ks->predictor<<<(unsigned)kp.ntiles, h->ks->pred_threads, h->ks->pred_smem, h->stream>>>(kp);
     CK(cudaGetLastError());
     return ADERDG_OK;
 }
@@ -244,8 +222,8 @@ int launch_corrector(aderdg_t *h, int use_ctl, double dt)
     KParams kp = h->kp;
     kp.use_ctl_dt = use_ctl;
     kp.dt_arg = dt;
-    const long long blocks = (h->E + h->ks->corr_epb - 1) / h->ks->corr_epb;
-    h->ks->corrector<<<(unsigned)blocks, h->ks->corr_threads, h->ks->corr_smem, h->stream>>>(kp);
+    kp.ntiles = (h->E + h->ks->corr_epb - 1) / h->ks->corr_epb;
+    h->ks->corrector<<<(unsigned)kp.ntiles, h->ks->corr_threads, h->ks->corr_smem, h->stream>>>(kp);
     CK(cudaGetLastError());
     return ADERDG_OK;
 }
@@ -289,13 +267,18 @@ int set_t_end(aderdg_t *h, double t_end)
     return ADERDG_OK;
 }
 
+// Algorithmic counts of the kernels as formulated (FMA = 2 flops; a
+// reciprocal or square root = 1): first Picard iteration on the
+// time-constant guess, P-1 full iterations, time averages, volume term,
+// traces; corrector Rusanov + lift + update + wave speeds.
 void fill_cost(const aderdg_t *h, aderdg_info_t *info)
 {
-    const double n = h->n, M = h->M, NS = h->NS, NST = h->NS * h->n, NREC = h->NREC, D = h->dim;
+    const double n = h->n, M = h->M, NS = h->NS, NST = h->NS * h->n, NF = h->NF, NREC = h->NREC, D = h->dim;
     const double P = h->picard, FF = h->ks->flux_flops, EF = h->ks->eig_flops;
-    const double per_iter = NST * FF + D * M * NST * (2 * n + 2) + M * NST * (2 * n + 1);
-    const double pred = P * per_iter + NST * FF + (1 + D) * NS * M * 2 * n + NS * M * D * (2 * n + 2)
-                        + NREC * M * 4 * n + NREC * EF;
+    const double it1 = NS * FF + D * NF * M * 2 * n * n + NS * M * (D - 1) + n * NS * M * 3;
+    const double itk = NST * FF + D * NS * M * 2 * n * n + NST * M * (D - 1) + NS * M * n * (2 * n + 2);
+    const double fin = NST * FF + (1 + D) * NST * M * 2 + NS * M * D * 2 * n + NREC * M * 4 * n + NREC * EF;
+    const double pred = it1 + (P - 1) * itk + fin;
     const double corr = NREC * M * 6 + NREC + NS * M * (5 * D + 3) + NS * D * (EF + 1);
     info->flops_predictor = pred * h->E;
     info->flops_corrector = corr * h->E;
@@ -398,7 +381,8 @@ int aderdg_create(const aderdg_mesh_t *mesh, int N, int nVar, const aderdg_pde_t
     h->tr = dev_alloc(h, (size_t)E * h->NREC * ks->rs * ks->elem_bytes);
     h->ctl = (Control *)dev_alloc(h, sizeof(Control));
     h->scratch = (double *)dev_alloc(h, sizeof(double) * (MASS_BLOCKS * 9 + 64));
-    if (!h->u || !h->V || !h->tr || !h->ctl || !h->scratch) {
+    h->d_desc = (SolveDesc *)dev_alloc(h, sizeof(SolveDesc));
+    if (!h->u || !h->V || !h->tr || !h->ctl || !h->scratch || !h->d_desc) {
         aderdg_destroy(h);
         return fail(ADERDG_E_NOMEM, "device allocation failed");
     }
@@ -421,29 +405,36 @@ int aderdg_create(const aderdg_mesh_t *mesh, int N, int nVar, const aderdg_pde_t
         return fail(ADERDG_E_CUDA, "corrector shared memory opt-in failed");
     }
 
+    SolveDesc &sd = h->desc;
+    std::memset(&sd, 0, sizeof(sd));
+    sd.E = E;
+    for (int d = 0; d < 3; ++d) {
+        sd.cells[d] = d < h->dim ? (int)mesh->cells[d] : 1;
+        h->inv_dx[d] = 1.0 / h->dx[d];
+        sd.inv_dx[d] = h->inv_dx[d];
+    }
+    sd.picard = h->picard;
+    sd.u = h->u;
+    sd.u_out = h->u;
+    sd.V = h->V;
+    sd.tr = h->tr;
+    sd.ctl = h->ctl;
     KParams &kp = h->kp;
     std::memset(&kp, 0, sizeof(kp));
-    kp.E = E;
-    for (int d = 0; d < 3; ++d) {
-        kp.cells[d] = d < h->dim ? (int)mesh->cells[d] : 1;
-        kp.inv_dx[d] = 1.0 / h->dx[d];
-    }
-    kp.picard = h->picard;
-    kp.u = h->u;
-    kp.u_out = h->u;
-    kp.V = h->V;
-    kp.tr = h->tr;
-    kp.ctl = h->ctl;
+    kp.solves = h->d_desc;
+    kp.nsolves = 1;
     for (int i = 0; i < 8; ++i) kp.pde.p[i] = pde->p[i];
     kp.b = h->basis;
+    fill_ops(kp);
 
     Control c;
     std::memset(&c, 0, sizeof(c));
     c.alpha = h->alpha;
     c.dim = h->dim;
-    for (int d = 0; d < 3; ++d) c.inv_dx[d] = kp.inv_dx[d];
+    for (int d = 0; d < 3; ++d) c.inv_dx[d] = h->inv_dx[d];
     c.t_end = 0.0;
-    if (cudaMemsetAsync(h->u, 0, nstate * sizeof(double), h->stream) != cudaSuccess ||
+    if (cudaMemcpyAsync(h->d_desc, &sd, sizeof(sd), cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
+        cudaMemsetAsync(h->u, 0, nstate * sizeof(double), h->stream) != cudaSuccess ||
         cudaMemcpyAsync(h->ctl, &c, sizeof(c), cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
         cudaStreamSynchronize(h->stream) != cudaSuccess) {
         aderdg_destroy(h);
@@ -463,6 +454,7 @@ int aderdg_destroy(aderdg_t *h)
     dev_free(h, h->tr);
     dev_free(h, h->ctl);
     dev_free(h, h->scratch);
+    dev_free(h, h->d_desc);
     if (h->host_pinned) cudaFreeHost(h->host_pinned);
     for (auto &e : h->ev)
         if (e) cudaEventDestroy(e);
@@ -501,7 +493,7 @@ int aderdg_set_state(aderdg_t *h, const double *u, int where, double t)
     c.t_end = t;
     c.alpha = h->alpha;
     c.dim = h->dim;
-    for (int d = 0; d < 3; ++d) c.inv_dx[d] = h->kp.inv_dx[d];
+    for (int d = 0; d < 3; ++d) c.inv_dx[d] = h->inv_dx[d];
     std::memcpy(h->host_pinned, &c, sizeof(c));
     CK(cudaMemcpyAsync(h->ctl, h->host_pinned, sizeof(c), cudaMemcpyHostToDevice, h->stream));
     h->ks->cfl<<<(unsigned)std::min<long long>(4 * 152, (h->E * h->NS + 255) / 256), 256, 0, h->stream>>>(h->kp);

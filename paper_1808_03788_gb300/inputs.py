@@ -218,3 +218,56 @@ def served_stream_recipe(count: int = 2000, rate: float = 200.0, seed: int = 180
             out.append(dict(arrival=t, pde=PDE_ELASTICITY, dim=3, cells=(k, k, k), N=N,
                             x0=tuple(float(v) for v in x0), t_end=1.0))
     return out
+
+
+# ---------------------------------------------------------------------------
+# Device-side (torch) versions for large workloads: the same closed forms,
+# evaluated on CUDA tensors so that multi-GB initial states need no host trip
+# ---------------------------------------------------------------------------
+
+def node_coords_torch(cells, lo, hi, nodes, device="cuda"):
+    """Node coordinates [E, n^d, d] (x-fastest elements and nodes) from the
+    1D nodes on [0, 1]."""
+    import torch
+    dim = len(cells)
+    x = torch.as_tensor(nodes, dtype=torch.float64, device=device)
+    n = x.numel()
+    E = 1
+    for c in cells:
+        E *= c
+    e = torch.arange(E, device=device)
+    s = torch.arange(n ** dim, device=device)
+    X = torch.empty((E, n ** dim, dim), dtype=torch.float64, device=device)
+    re, rs = e.clone(), s.clone()
+    for d in range(dim):
+        ie, js = re % cells[d], rs % n
+        re, rs = re // cells[d], rs // n
+        h = (hi[d] - lo[d]) / cells[d]
+        X[:, :, d] = lo[d] + (ie[:, None].double() + x[js][None, :]) * h
+    return X
+
+
+def euler_vortex_torch(X, eps=5.0, center=(5.0, 5.0), gamma=1.4, lo=(0.0, 0.0), hi=(10.0, 10.0)):
+    """euler_vortex at t = 0 on a CUDA tensor of coordinates."""
+    import torch
+    dx = X[..., 0] - center[0]
+    dy = X[..., 1] - center[1]
+    r2 = dx * dx + dy * dy
+    dT = -(gamma - 1.0) * eps * eps / (8.0 * gamma * math.pi ** 2) * torch.exp(1.0 - r2)
+    g = eps / (2.0 * math.pi) * torch.exp(0.5 * (1.0 - r2))
+    rho = (1.0 + dT) ** (1.0 / (gamma - 1.0))
+    p = rho ** gamma
+    u, v = 1.0 - g * dy, 1.0 + g * dx
+    E = p / (gamma - 1.0) + 0.5 * rho * (u * u + v * v)
+    return torch.stack([rho, rho * u, rho * v, E], dim=-1).contiguous()
+
+
+def elastic_pulse_torch(X, x0=(0.5, 0.5, 0.5), width=0.01):
+    import torch
+    r2 = sum((X[..., d] - x0[d]) ** 2 for d in range(3))
+    g = torch.exp(-r2 / width)
+    out = torch.zeros(X.shape[:-1] + (9,), dtype=torch.float64, device=X.device)
+    out[..., 6] = g
+    out[..., 7] = g
+    out[..., 8] = g
+    return out
