@@ -182,6 +182,13 @@ def nvar(pde: int, dim: int) -> int:
     return {1: 1, 2: dim + 2, 3: 9}[pde]
 
 
+def _torch_ready():
+    """Device tensors handed to the library are read on the library's stream:
+    wait until torch's current stream has finished writing them."""
+    import torch
+    torch.cuda.current_stream().synchronize()
+
+
 class _TorchAllocator:
     """aderdg_alloc_t backed by torch's CUDA caching allocator."""
 
@@ -272,6 +279,7 @@ class Solver:
     def set_state(self, u, t: float = 0.0):
         if hasattr(u, "data_ptr"):  # torch tensor on the device
             assert u.dtype.itemsize == 8 and u.is_contiguous() and u.numel() == self.E * self.ns * self.m
+            _torch_ready()
             _check(self._L.aderdg_set_state(self._h, C.c_void_p(u.data_ptr()), ADERDG_DEVICE, float(t)))
             return
         u = np.ascontiguousarray(u, dtype=np.float64)
@@ -516,6 +524,7 @@ class Batch:
     def set_state(self, i: int, u, t: float = 0.0):
         if hasattr(u, "data_ptr"):  # device tensor
             assert u.is_cuda and u.is_contiguous() and u.numel() == spec_size(self.specs[i])
+            _torch_ready()
             _check(self._L.aderdg_batch_set_state(self._h, i, C.c_void_p(u.data_ptr()), ADERDG_DEVICE, float(t)))
             return
         u = np.ascontiguousarray(u, dtype=np.float64)

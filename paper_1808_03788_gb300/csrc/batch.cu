@@ -112,6 +112,7 @@ struct Slot {
     size_t bytes = 0;
     double *u = nullptr;
     void *V = nullptr, *tr = nullptr;
+    double *ref = nullptr;
     int ctl_index = -1;
     // placement in the current group arrays (for k_cfl)
     int group = -1, member = -1;
@@ -120,7 +121,8 @@ struct Slot {
 size_t slot_bytes(const Slot &s)
 {
     const size_t ns = (size_t)s.E * s.NS * s.M;
-    return a256(ns * 8) + a256(ns * s.ks->elem_bytes) + a256((size_t)s.E * s.NREC * s.ks->rs * s.ks->elem_bytes);
+    return a256(ns * 8) + a256(ns * s.ks->elem_bytes) + a256((size_t)s.E * s.NREC * s.ks->rs * s.ks->elem_bytes) +
+           a256((size_t)s.E * s.ks->rf * 8);
 }
 
 int make_slot(const aderdg_solve_spec_t &sp, int prec, int picard, double alpha, Slot &s)
@@ -252,6 +254,10 @@ public:
         s->u = reinterpret_cast<double *>(b);
         s->V = b + a256(ns * 8);
         s->tr = b + a256(ns * 8) + a256(ns * s->ks->elem_bytes);
+        s->ref = s->ks->rf > 0
+                     ? reinterpret_cast<double *>(b + a256(ns * 8) + a256(ns * s->ks->elem_bytes) +
+                                                  a256((size_t)s->E * s->NREC * s->ks->rs * s->ks->elem_bytes))
+                     : nullptr;
         s->ctl_index = ctl_free.back();
         ctl_free.pop_back();
         Control c;
@@ -319,6 +325,7 @@ public:
                 d.u_out = s->u;
                 d.V = s->V;
                 d.tr = s->tr;
+                d.ref = s->ref;
                 d.ctl = ctl_of(s);
             }
             g.ntp = tp;

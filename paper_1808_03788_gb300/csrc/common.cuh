@@ -78,6 +78,8 @@ struct SolveDesc {
     double *u_out;     // state u^{n+1} (may alias u)
     void *V;           // volume term          [E][NS][M] of T
     void *tr;          // trace records        [E][DIM][2][NF][RS] of T
+    double *ref;       // FP32 path: reference state and flux per element
+                       // [E][M + DIM M] (q_ref, F_d(q_ref)); unused in FP64
     Control *ctl;
 };
 
@@ -111,6 +113,16 @@ __host__ __device__ constexpr int round_up(int a, int b) { return (a + b - 1) / 
 // max_eig(): largest |eigenvalue| of dF_d/dQ.
 // ---------------------------------------------------------------------------
 
+// The FP32 path works with perturbations about a per-element reference
+// state q_ref (held in FP64 in memory): flux_delta returns
+// F_d(q_ref + dq) - F_d(q_ref) evaluated from small quantities only, so its
+// rounding error scales with |dq| instead of |q|.  Linear systems need no
+// reference data (the perturbation flux is the flux of dq).
+template <typename T, int M>
+struct NoRef {
+    T q[M];
+};
+
 // Linear advection F_d = a_d u.
 template <int DIM>
 struct Advection {
@@ -118,6 +130,15 @@ struct Advection {
     static constexpr int KIND = 1;
     static constexpr int FLUX_FLOPS = DIM;        // per point, all directions
     static constexpr int EIG_FLOPS = 0;
+    template <typename T> using Ref = NoRef<T, M>;
+    template <typename T>
+    __device__ __forceinline__ static void make_ref(const PdeParams &, const double *q, Ref<T> &r) {
+        r.q[0] = T(q[0]);
+    }
+    template <typename T>
+    __device__ __forceinline__ static void flux_delta(const PdeParams &P, const Ref<T> &, const T *dq, T (*f)[M]) {
+        flux(P, dq, f);
+    }
     template <typename T>
     __device__ __forceinline__ static void flux(const PdeParams &P, const T *q, T (*f)[M]) {
 #pragma unroll
@@ -138,6 +159,55 @@ struct Euler {
     // DIM FMA/products for momentum + 1 add for pressure + 2 for energy
     static constexpr int FLUX_FLOPS = 1 + DIM + 2 * DIM + 3 + DIM * (2 * DIM + 3);
     static constexpr int EIG_FLOPS = 2 * DIM + 8;
+    template <typename T>
+    struct Ref {
+        T q[M];
+        T u0[DIM], EP0;  // reference velocity and E + p
+    };
+    // reference quantities in the compute type (their rounding only enters
+    // the perturbation flux multiplied by perturbations)
+    template <typename T>
+    __device__ __forceinline__ static void make_ref(const PdeParams &P, const double *q, Ref<T> &r) {
+#pragma unroll
+        for (int v = 0; v < M; ++v) r.q[v] = T(q[v]);
+        const T ir = T(1) / r.q[0];
+        T kin2 = T(0);
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) {
+            r.u0[k] = r.q[1 + k] * ir;
+            kin2 += r.q[1 + k] * r.u0[k];
+        }
+        const T p = T(P.p[0] - 1.0) * (r.q[DIM + 1] - T(0.5) * kin2);
+        r.EP0 = r.q[DIM + 1] + p;
+    }
+    // F(q_ref + dq) - F(q_ref) from the perturbations:
+    //   du = (dm - u0 drho) / rho,  u = u0 + du,
+    //   dkin = (m0 . du + dm . u) / 2,  dp = (gamma - 1)(dE - dkin),
+    //   dF_rho = dm_d,  dF_m_k = m0_k du_d + dm_k u_d + dp [k == d],
+    //   dF_E = du_d (E + p) + u0_d (dE + dp).
+    template <typename T>
+    __device__ __forceinline__ static void flux_delta(const PdeParams &P, const Ref<T> &r, const T *dq, T (*f)[M]) {
+        const T gm1 = T(P.p[0] - 1.0);
+        const T ir = T(1) / (r.q[0] + dq[0]);
+        T du[DIM], u[DIM];
+        T dkin2 = T(0);
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) {
+            du[k] = (dq[1 + k] - r.u0[k] * dq[0]) * ir;
+            u[k] = r.u0[k] + du[k];
+            dkin2 += r.q[1 + k] * du[k] + dq[1 + k] * u[k];
+        }
+        const T dE = dq[DIM + 1];
+        const T dp = gm1 * (dE - T(0.5) * dkin2);
+        const T Ep = r.EP0 + (dE + dp);
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) {
+            f[d][0] = dq[1 + d];
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) f[d][1 + k] = r.q[1 + k] * du[d] + dq[1 + k] * u[d] + (k == d ? dp : T(0));
+            f[d][DIM + 1] = du[d] * Ep + r.u0[d] * (dE + dp);
+        }
+    }
     template <typename T>
     __device__ __forceinline__ static void flux(const PdeParams &P, const T *q, T (*f)[M]) {
         const T gm1 = T(P.p[0] - 1.0);
@@ -176,6 +246,16 @@ struct Elastic3 {
     static constexpr int KIND = 3;
     static constexpr int FLUX_FLOPS = 3 * 9;
     static constexpr int EIG_FLOPS = 0;
+    template <typename T> using Ref = NoRef<T, M>;
+    template <typename T>
+    __device__ __forceinline__ static void make_ref(const PdeParams &, const double *q, Ref<T> &r) {
+#pragma unroll
+        for (int v = 0; v < M; ++v) r.q[v] = T(q[v]);
+    }
+    template <typename T>
+    __device__ __forceinline__ static void flux_delta(const PdeParams &P, const Ref<T> &, const T *dq, T (*f)[M]) {
+        flux(P, dq, f);
+    }
     template <typename T>
     __device__ __forceinline__ static void flux(const PdeParams &P, const T *q, T (*f)[M]) {
         const T irho = T(1.0 / P.p[0]);
@@ -224,6 +304,7 @@ struct KernelSet {
     void (*cfl)(KParams);
     int nvar, rs, elem_bytes;  // elem_bytes = sizeof(T)
     int flux_flops, eig_flops;  // per point, for the cost model
+    int rf;                     // doubles per element of the FP32 reference record (0: none)
 };
 
 }  // namespace aderdg

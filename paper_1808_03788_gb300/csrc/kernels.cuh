@@ -119,6 +119,10 @@ struct PredCfg {
     static constexpr int THREADS = round_up(EPB * NS, 32);
     static constexpr int SHARED = round_up(DIM * n * n + 2 * n, 4);  // Kw, F0, F1
     static constexpr size_t BYTES = sizeof(T) * (size_t)(SHARED + EPB * ELEM);
+    // FP32 path: perturbation form about the element's node SREF
+    static constexpr bool DELTA = sizeof(T) == 4;
+    static constexpr int SREF = NS / 2;
+    static constexpr int RF = M;  // reference record: q_ref
 };
 
 // -Dhat F_d along direction D on pencil (t, p), in place.
@@ -219,15 +223,30 @@ k_predictor(const KParams P)
         const long long e = (tile - S.tile0_p) * EPB + g;
         const bool valid = act && e < S.E;
         const long long ec = e < S.E ? e : S.E - 1;  // tail groups recompute the last element
+        // FP32 path: perturbations about the element's reference node
+        typename PDE::template Ref<T> ref;
+        double uref[M];
         T u[M];
+        if constexpr (C::DELTA) {
 #pragma unroll
-        for (int v = 0; v < M; ++v) u[v] = T(S.u[(ec * NS + s) * M + v]);
+            for (int v = 0; v < M; ++v) uref[v] = S.u[(ec * NS + C::SREF) * M + v];
+            PDE::make_ref(P.pde, uref, ref);
+#pragma unroll
+            for (int v = 0; v < M; ++v) u[v] = T(S.u[(ec * NS + s) * M + v] - uref[v]);
+        } else {
+#pragma unroll
+            for (int v = 0; v < M; ++v) u[v] = T(S.u[(ec * NS + s) * M + v]);
+        }
+        auto flx = [&](const T *qq, T(*FF)[M]) {
+            if constexpr (C::DELTA) PDE::flux_delta(P.pde, ref, qq, FF);
+            else PDE::flux(P.pde, qq, FF);
+        };
 
         T q[n][M];
         // ---- iteration 1 from the time-constant guess ----------------------
         {
             T F[DIM][M];
-            PDE::flux(P.pde, u, F);
+            flx(u, F);
             if (act) {
 #pragma unroll
                 for (int d = 0; d < DIM; ++d) NodeIO<T, M>::store(ebuf + (d * NST + s) * M, F[d]);
@@ -248,7 +267,7 @@ k_predictor(const KParams P)
 #pragma unroll
             for (int t = 0; t < n; ++t) {
                 T F[DIM][M];
-                PDE::flux(P.pde, q[t], F);
+                flx(q[t], F);
                 if (act) {
 #pragma unroll
                     for (int d = 0; d < DIM; ++d) NodeIO<T, M>::store(ebuf + (d * NST + t * NS + s) * M, F[d]);
@@ -285,7 +304,7 @@ k_predictor(const KParams P)
 #pragma unroll
         for (int t = 0; t < n; ++t) {
             T F[DIM][M];
-            PDE::flux(P.pde, q[t], F);
+            flx(q[t], F);
             const T wt = O.w[t];
 #pragma unroll
             for (int v = 0; v < M; ++v) {
@@ -363,8 +382,17 @@ k_predictor(const KParams P)
         if (valid) {
             for (int rec = s; rec < NREC; rec += NS) {
                 const int d = rec / (2 * NF);
-                trE[rec * RS + 2 * M] = PDE::max_eig(P.pde, sStash + rec * M, d);
+                T full[M];
+#pragma unroll
+                for (int v = 0; v < M; ++v) full[v] = sStash[rec * M + v] + (C::DELTA ? ref.q[v] : T(0));
+                trE[rec * RS + 2 * M] = PDE::max_eig(P.pde, full, d);
                 trE[rec * RS + 2 * M + 1] = T(0);
+            }
+            if constexpr (C::DELTA) {
+                if (s == 0) {  // the reference state, kept in FP64 for the corrector
+#pragma unroll
+                    for (int v = 0; v < M; ++v) S.ref[ec * C::RF + v] = uref[v];
+                }
             }
         }
         __syncthreads();  // ebuf is reused by the next tile
@@ -457,7 +485,10 @@ struct CorrCfg {
     static constexpr size_t O_FS = O_V + align16(EPB * VB);
     static constexpr size_t O_LIFT = O_FS + align16(EPB * FS);
     static constexpr size_t O_NBIDX = O_LIFT + align16(sizeof(T) * 2 * 3 * NMAX);
-    static constexpr size_t O_RED = O_NBIDX + align16(sizeof(int) * EPB * 2 * DIM);
+    static constexpr size_t O_DEL = O_NBIDX + align16(sizeof(int) * EPB * 2 * DIM);
+    static constexpr bool DELTA = sizeof(T) == 4;
+    static constexpr int RF = M;
+    static constexpr size_t O_RED = O_DEL + (DELTA ? align16(sizeof(T) * EPB * 2 * DIM * 2 * M) : 0);
     static constexpr size_t BYTES = O_RED + 64 * sizeof(double);
     // copy granules (bytes): the largest of 16/8/4 dividing offsets and sizes
     static constexpr int G_OWN = cgcd((int)OWN, 16);
@@ -495,6 +526,7 @@ k_corrector(const KParams P)
     T *sFs = reinterpret_cast<T *>(smem_raw + C::O_FS);
     T *sL = reinterpret_cast<T *>(smem_raw + C::O_LIFT);  // [side][d][k]
     int *sNbIdx = reinterpret_cast<int *>(smem_raw + C::O_NBIDX);
+    T *sDel = reinterpret_cast<T *>(smem_raw + C::O_DEL);  // [el][d][side][dF | dq][M]
     double *red = reinterpret_cast<double *>(smem_raw + C::O_RED);
 
     for (long long tile = blockIdx.x; tile < P.ntiles; tile += gridDim.x) {
@@ -534,6 +566,37 @@ k_corrector(const KParams P)
                 cp_async(dst + u_ * C::G_NB, reinterpret_cast<const unsigned char *>(src) + u_ * C::G_NB, C::G_NB);
             }
         }
+        if constexpr (C::DELTA) {
+            // reference differences across every face, sign +1 on the
+            // xi_d = 1 face and -1 on the xi_d = 0 face:  dq = q_ref(nb) -
+            // q_ref(own) formed in FP64 and rounded (it is O(h)), and
+            // dF = F_d(q_ref(nb)) - F_d(q_ref(own)) by the perturbation flux
+            for (int c = threadIdx.x; c < ne * 2 * DIM; c += blockDim.x) {
+                const int el = c / (2 * DIM), d = (c / 2) % DIM, side = c & 1;
+                const double *ro = S.ref + (long long)(e0 + el) * C::RF;
+                const double *rn = S.ref + (long long)sNbIdx[c] * C::RF;
+                double qo[M];
+                T dq[M];
+#pragma unroll
+                for (int v = 0; v < M; ++v) {
+                    qo[v] = ro[v];
+                    dq[v] = T(rn[v] - qo[v]);
+                }
+                typename PDE::template Ref<T> rr;
+                PDE::make_ref(P.pde, qo, rr);
+                T dF[DIM][M];
+                PDE::flux_delta(P.pde, rr, dq, dF);
+                const T sg = side ? T(1) : T(-1);
+#pragma unroll
+                for (int v = 0; v < M; ++v) {
+                    T f = dF[0][v];
+#pragma unroll
+                    for (int k = 1; k < DIM; ++k) f = d == k ? dF[k][v] : f;
+                    sDel[(c * 2 + 0) * M + v] = sg * f;
+                    sDel[(c * 2 + 1) * M + v] = sg * dq[v];
+                }
+            }
+        }
         cp_async_wait_all();
         __syncthreads();
 
@@ -550,7 +613,14 @@ k_corrector(const KParams P)
             const T *L = side ? own : nb;
             const T *R = side ? nb : own;
             const T smax = tmax(L[2 * M], R[2 * M]);
-            sFs[(el * NREC + rec) * M + v] = T(0.5) * (L[M + v] + R[M + v]) - T(0.5) * smax * (R[v] - L[v]);
+            T f = T(0.5) * (L[M + v] + R[M + v]) - T(0.5) * smax * (R[v] - L[v]);
+            if constexpr (C::DELTA) {
+                // traces are perturbations about each element's own reference:
+                // add the reference part of the Rusanov flux minus own F_ref
+                const T *dl = sDel + ((((el * DIM + d) * 2 + side) * 2) * M);
+                f += (side ? T(0.5) : T(-0.5)) * dl[v] - T(0.5) * smax * dl[M + v];
+            }
+            sFs[(el * NREC + rec) * M + v] = f;
         }
         __syncthreads();
 
@@ -684,6 +754,7 @@ const KernelSet KS<PDE, DIM, N, T>::value = {
     &k_corrector<PDE, DIM, N, T>, CorrCfg<PDE, DIM, N, T>::THREADS, CorrCfg<PDE, DIM, N, T>::EPB,
     CorrCfg<PDE, DIM, N, T>::BYTES,
     &k_cfl<PDE, DIM, N, T>,
-    Geom<PDE, DIM, N>::M, Geom<PDE, DIM, N>::RS, (int)sizeof(T), PDE::FLUX_FLOPS, PDE::EIG_FLOPS};
+    Geom<PDE, DIM, N>::M, Geom<PDE, DIM, N>::RS, (int)sizeof(T), PDE::FLUX_FLOPS, PDE::EIG_FLOPS,
+    PredCfg<PDE, DIM, N, T>::DELTA ? PredCfg<PDE, DIM, N, T>::RF : 0};
 
 }  // namespace aderdg

@@ -112,7 +112,8 @@ extern "C" int aderdg_step_noalloc(const aderdg_mesh_t *mesh, int N, int nVar, c
     const int NS = ipow(n, mesh->dim), NF = ipow(n, mesh->dim - 1), NREC = mesh->dim * 2 * NF;
     const size_t v_bytes = align256((size_t)E * NS * m * ks->elem_bytes);
     const size_t tr_bytes = align256((size_t)E * NREC * ks->rs * ks->elem_bytes);
-    const size_t need = v_bytes + tr_bytes + align256(sizeof(Control)) + align256(sizeof(SolveDesc));
+    const size_t ref_bytes = align256((size_t)E * ks->rf * sizeof(double));
+    const size_t need = v_bytes + tr_bytes + align256(sizeof(Control)) + align256(sizeof(SolveDesc)) + ref_bytes;
     if (need > SCRATCH_BYTES)
         return fail(ADERDG_E_INVAL, "mesh too large for the static scratch: needs " + std::to_string(need) +
                                         " bytes, limit " + std::to_string(SCRATCH_BYTES) + " bytes");
@@ -137,6 +138,9 @@ extern "C" int aderdg_step_noalloc(const aderdg_mesh_t *mesh, int N, int nVar, c
     sd.u_out = u_out;
     sd.V = sb;
     sd.tr = sb + v_bytes;
+    sd.ref = ks->rf > 0 ? reinterpret_cast<double *>(sb + v_bytes + tr_bytes + align256(sizeof(Control)) +
+                                                     align256(sizeof(SolveDesc)))
+                        : nullptr;
     sd.ctl = ctl;
 
     KParams kp;

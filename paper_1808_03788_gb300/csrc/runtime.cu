@@ -173,6 +173,7 @@ struct aderdg_s {
     void *tr = nullptr;
     Control *ctl = nullptr;
     double *scratch = nullptr;  // mass partials + small outputs
+    double *ref = nullptr;      // FP32 path: per-element reference records
     double *host_pinned = nullptr;
     KParams kp{};
     Basis basis{};
@@ -382,7 +383,8 @@ int aderdg_create(const aderdg_mesh_t *mesh, int N, int nVar, const aderdg_pde_t
     h->ctl = (Control *)dev_alloc(h, sizeof(Control));
     h->scratch = (double *)dev_alloc(h, sizeof(double) * (MASS_BLOCKS * 9 + 64));
     h->d_desc = (SolveDesc *)dev_alloc(h, sizeof(SolveDesc));
-    if (!h->u || !h->V || !h->tr || !h->ctl || !h->scratch || !h->d_desc) {
+    if (ks->rf > 0) h->ref = (double *)dev_alloc(h, sizeof(double) * (size_t)E * ks->rf);
+    if (!h->u || !h->V || !h->tr || !h->ctl || !h->scratch || !h->d_desc || (ks->rf > 0 && !h->ref)) {
         aderdg_destroy(h);
         return fail(ADERDG_E_NOMEM, "device allocation failed");
     }
@@ -418,6 +420,7 @@ int aderdg_create(const aderdg_mesh_t *mesh, int N, int nVar, const aderdg_pde_t
     sd.u_out = h->u;
     sd.V = h->V;
     sd.tr = h->tr;
+    sd.ref = h->ref;
     sd.ctl = h->ctl;
     KParams &kp = h->kp;
     std::memset(&kp, 0, sizeof(kp));
@@ -455,6 +458,7 @@ int aderdg_destroy(aderdg_t *h)
     dev_free(h, h->ctl);
     dev_free(h, h->scratch);
     dev_free(h, h->d_desc);
+    dev_free(h, h->ref);
     if (h->host_pinned) cudaFreeHost(h->host_pinned);
     for (auto &e : h->ev)
         if (e) cudaEventDestroy(e);
