@@ -320,6 +320,7 @@ public:
                 tp += (s->E + g.ks->pred_epb - 1) / g.ks->pred_epb;
                 tc += (s->E + g.ks->corr_epb - 1) / g.ks->corr_epb;
                 for (int k = 0; k < 3; ++k) { d.cells[k] = s->cells[k]; d.inv_dx[k] = s->inv_dx[k]; }
+                fill_desc_spacing(d);
                 d.picard = s->picard;
                 d.u = s->u;
                 d.u_out = s->u;

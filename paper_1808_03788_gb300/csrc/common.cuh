@@ -74,6 +74,8 @@ struct SolveDesc {
     int cells[3];
     int picard;
     double inv_dx[3];
+    float inv_dx_f[3]; // 1/dx_d and dx_0/dx_d in FP32 (precomputed on the host)
+    float ratio_f[3];
     const double *u;   // state u^n            [E][NS][M]
     double *u_out;     // state u^{n+1} (may alias u)
     void *V;           // volume term          [E][NS][M] of T
@@ -82,6 +84,14 @@ struct SolveDesc {
                        // [E][M + DIM M] (q_ref, F_d(q_ref)); unused in FP64
     Control *ctl;
 };
+
+inline void fill_desc_spacing(SolveDesc &d)
+{
+    for (int k = 0; k < 3; ++k) {
+        d.inv_dx_f[k] = (float)d.inv_dx[k];
+        d.ratio_f[k] = (float)(d.inv_dx[k] / d.inv_dx[0]);
+    }
+}
 
 // Kernel parameter block (passed by value).
 struct KParams {
@@ -132,8 +142,8 @@ struct Advection {
     static constexpr int EIG_FLOPS = 0;
     template <typename T> using Ref = NoRef<T, M>;
     template <typename T>
-    __device__ __forceinline__ static void make_ref(const PdeParams &, const double *q, Ref<T> &r) {
-        r.q[0] = T(q[0]);
+    __device__ __forceinline__ static void make_ref(const PdeParams &, const T *q, Ref<T> &r) {
+        r.q[0] = q[0];
     }
     template <typename T>
     __device__ __forceinline__ static void flux_delta(const PdeParams &P, const Ref<T> &, const T *dq, T (*f)[M]) {
@@ -167,9 +177,9 @@ struct Euler {
     // reference quantities in the compute type (their rounding only enters
     // the perturbation flux multiplied by perturbations)
     template <typename T>
-    __device__ __forceinline__ static void make_ref(const PdeParams &P, const double *q, Ref<T> &r) {
+    __device__ __forceinline__ static void make_ref(const PdeParams &P, const T *q, Ref<T> &r) {
 #pragma unroll
-        for (int v = 0; v < M; ++v) r.q[v] = T(q[v]);
+        for (int v = 0; v < M; ++v) r.q[v] = q[v];
         const T ir = T(1) / r.q[0];
         T kin2 = T(0);
 #pragma unroll
@@ -248,9 +258,9 @@ struct Elastic3 {
     static constexpr int EIG_FLOPS = 0;
     template <typename T> using Ref = NoRef<T, M>;
     template <typename T>
-    __device__ __forceinline__ static void make_ref(const PdeParams &, const double *q, Ref<T> &r) {
+    __device__ __forceinline__ static void make_ref(const PdeParams &, const T *q, Ref<T> &r) {
 #pragma unroll
-        for (int v = 0; v < M; ++v) r.q[v] = T(q[v]);
+        for (int v = 0; v < M; ++v) r.q[v] = q[v];
     }
     template <typename T>
     __device__ __forceinline__ static void flux_delta(const PdeParams &P, const Ref<T> &, const T *dq, T (*f)[M]) {

@@ -85,6 +85,61 @@ __device__ __forceinline__ double solve_dt(const KParams &P, const SolveDesc &S)
     return P.use_ctl_dt ? S.ctl->dt : P.dt_arg;
 }
 
+// Non-finite test and float <-> double conversions on the integer bits, so
+// that the FP64 pipe only carries the arithmetic the method needs in FP64.
+__device__ __forceinline__ bool dbl_nonfinite(double x)
+{
+    return ((__double2hiint(x) >> 20) & 0x7ff) == 0x7ff;
+}
+
+// double -> float, round to nearest even (an unbiased rounding: the FP32
+// path accumulates these values over many steps); results below the normal
+// float range become signed zero, beyond it signed infinity
+__device__ __forceinline__ float dbl_to_flt_rn(double x)
+{
+    const int hi = __double2hiint(x);
+    const unsigned lo = (unsigned)__double2loint(x);
+    const unsigned sign = (unsigned)hi & 0x80000000u;
+    const int e = ((hi >> 20) & 0x7ff) - 1023 + 127;
+    const unsigned mant = (((unsigned)hi & 0xfffffu) << 3) | (lo >> 29);
+    const unsigned rem = lo & 0x1fffffffu;
+    unsigned bits = ((unsigned)e << 23) | mant;
+    bits += (rem > 0x10000000u || (rem == 0x10000000u && (mant & 1u))) ? 1u : 0u;  // may carry into e
+    bits |= sign;
+    bits = e <= 0 ? sign : bits;
+    bits = (e >= 255 || (bits & 0x7f800000u) == 0x7f800000u) ? (sign | 0x7f800000u) : bits;
+    return __uint_as_float(bits);
+}
+
+// float -> double widening on the integer bits (exact for normal numbers and
+// zero; FP32 denormals, which the FP32 path never produces at these
+// magnitudes, are flushed to zero)
+__device__ __forceinline__ double flt_to_dbl(float f)
+{
+    const unsigned b = __float_as_uint(f);
+    const unsigned e = (b >> 23) & 0xffu;
+    const unsigned long long sign = (unsigned long long)(b & 0x80000000u) << 32;
+    unsigned long long bits = sign | ((unsigned long long)(e + 896u) << 52) |
+                              ((unsigned long long)(b & 0x7fffffu) << 29);
+    bits = e == 0 ? sign : bits;
+    bits = e == 0xffu ? (sign | 0x7ff0000000000000ull | ((unsigned long long)(b & 0x7fffffu) << 29)) : bits;
+    return __longlong_as_double((long long)bits);
+}
+
+template <typename T>
+__device__ __forceinline__ double widen(T x);
+template <>
+__device__ __forceinline__ double widen<double>(double x) { return x; }
+template <>
+__device__ __forceinline__ double widen<float>(float x) { return flt_to_dbl(x); }
+
+template <typename T>
+__device__ __forceinline__ T narrow(double x);
+template <>
+__device__ __forceinline__ double narrow<double>(double x) { return x; }
+template <>
+__device__ __forceinline__ float narrow<float>(double x) { return dbl_to_flt_rn(x); }
+
 // ===========================================================================
 // Predictor
 // ===========================================================================
@@ -117,7 +172,7 @@ struct PredCfg {
     static constexpr int EPB_S = cmax(1, (int)((110 * 1024) / (ELEM * sizeof(T))));
     static constexpr int EPB = cmin(EPB_T, EPB_S);
     static constexpr int THREADS = round_up(EPB * NS, 32);
-    static constexpr int SHARED = round_up(DIM * n * n + 2 * n, 4);  // Kw, F0, F1
+    static constexpr int SHARED = round_up(DIM * n * n + 2 * n + 1, 4);  // Kw, F0, F1, dt/dx
     static constexpr size_t BYTES = sizeof(T) * (size_t)(SHARED + EPB * ELEM);
     // FP32 path: perturbation form about the element's node SREF
     static constexpr bool DELTA = sizeof(T) == 4;
@@ -190,6 +245,7 @@ k_predictor(const KParams P)
     T *sKw = reinterpret_cast<T *>(smem_raw);  // DIM x n x n (unscaled)
     T *sF0 = sKw + DIM * n * n;
     T *sF1 = sF0 + n;
+    T *sDt = sF1 + n;                          // dt / dx_0 of the current tile
     const int tid = threadIdx.x;
     const bool act = tid < EPB * NS;
     const int g = act ? tid / NS : 0;
@@ -212,12 +268,17 @@ k_predictor(const KParams P)
         const SolveDesc &S = P.solves[si];
         const double dt = solve_dt(P, S);
         if (!(dt > 0.0)) continue;  // uniform over the CTA: this solve takes no step
-        const T dtT = T(dt * S.inv_dx[0]);  // dt / dx_0 (see gather_R)
+        if (tid == 0) sDt[0] = T(dt * S.inv_dx[0]);  // dt / dx_0 (see gather_R), read after a barrier
         T idx[DIM], ratio[DIM];
 #pragma unroll
         for (int d = 0; d < DIM; ++d) {
-            idx[d] = T(S.inv_dx[d]);
-            ratio[d] = T(S.inv_dx[d] / S.inv_dx[0]);
+            if constexpr (sizeof(T) == 4) {
+                idx[d] = S.inv_dx_f[d];
+                ratio[d] = S.ratio_f[d];
+            } else {
+                idx[d] = S.inv_dx[d];
+                ratio[d] = S.inv_dx[d] / S.inv_dx[0];
+            }
         }
 
         const long long e = (tile - S.tile0_p) * EPB + g;
@@ -230,9 +291,14 @@ k_predictor(const KParams P)
         if constexpr (C::DELTA) {
 #pragma unroll
             for (int v = 0; v < M; ++v) uref[v] = S.u[(ec * NS + C::SREF) * M + v];
-            PDE::make_ref(P.pde, uref, ref);
+            {
+                T urf[M];
 #pragma unroll
-            for (int v = 0; v < M; ++v) u[v] = T(S.u[(ec * NS + s) * M + v] - uref[v]);
+                for (int v = 0; v < M; ++v) urf[v] = narrow<T>(uref[v]);
+                PDE::make_ref(P.pde, urf, ref);
+            }
+#pragma unroll
+            for (int v = 0; v < M; ++v) u[v] = narrow<T>(S.u[(ec * NS + s) * M + v] - uref[v]);
         } else {
 #pragma unroll
             for (int v = 0; v < M; ++v) u[v] = T(S.u[(ec * NS + s) * M + v]);
@@ -256,6 +322,7 @@ k_predictor(const KParams P)
             __syncthreads();
             T R[M];
             gather_R<C, T>(ebuf, 0, s, ratio, R);
+            const T dtT = sDt[0];
 #pragma unroll
             for (int t = 0; t < n; ++t)
 #pragma unroll
@@ -277,6 +344,7 @@ k_predictor(const KParams P)
             if (act) contract_all<C, T>(ebuf, tk, pk, O);
             __syncthreads();
             {
+                const T dtT = sDt[0];
                 T R[n][M];
 #pragma unroll
                 for (int t = 0; t < n; ++t) gather_R<C, T>(ebuf, t, s, ratio, R[t]);
@@ -402,35 +470,6 @@ k_predictor(const KParams P)
 // ===========================================================================
 // Corrector
 // ===========================================================================
-
-// Non-finite test and double -> float narrowing on the integer bits
-// (truncating the mantissa; values below the float range become 0).  The
-// wave speeds of the mixed path only feed the CFL maxima, so truncation is
-// harmless, and the FP64 pipe stays free for the state update.
-__device__ __forceinline__ bool dbl_nonfinite(double x)
-{
-    return ((__double2hiint(x) >> 20) & 0x7ff) == 0x7ff;
-}
-
-__device__ __forceinline__ float dbl_to_flt_trunc(double x)
-{
-    const int hi = __double2hiint(x);
-    const unsigned lo = (unsigned)__double2loint(x);
-    const unsigned sign = (unsigned)hi & 0x80000000u;
-    const int e = ((hi >> 20) & 0x7ff) - 1023 + 127;
-    const unsigned mant = (((unsigned)hi & 0xfffffu) << 3) | (lo >> 29);
-    unsigned bits = sign | ((unsigned)e << 23) | mant;
-    bits = e <= 0 ? sign : bits;
-    bits = e >= 255 ? (sign | 0x7f800000u) : bits;
-    return __uint_as_float(bits);
-}
-
-template <typename T>
-__device__ __forceinline__ T narrow(double x);
-template <>
-__device__ __forceinline__ double narrow<double>(double x) { return x; }
-template <>
-__device__ __forceinline__ float narrow<float>(double x) { return dbl_to_flt_trunc(x); }
 
 // A CTA takes a tile of EPB consecutive elements.  All its inputs -- its own
 // trace records (one contiguous range), the 2d neighbour face chunks of
@@ -580,10 +619,15 @@ k_corrector(const KParams P)
 #pragma unroll
                 for (int v = 0; v < M; ++v) {
                     qo[v] = ro[v];
-                    dq[v] = T(rn[v] - qo[v]);
+                    dq[v] = narrow<T>(rn[v] - qo[v]);
                 }
                 typename PDE::template Ref<T> rr;
-                PDE::make_ref(P.pde, qo, rr);
+                {
+                    T qf[M];
+#pragma unroll
+                    for (int v = 0; v < M; ++v) qf[v] = narrow<T>(qo[v]);
+                    PDE::make_ref(P.pde, qf, rr);
+                }
                 T dF[DIM][M];
                 PDE::flux_delta(P.pde, rr, dq, dF);
                 const T sg = side ? T(1) : T(-1);
@@ -642,7 +686,7 @@ k_corrector(const KParams P)
                 const T fm = sFs[(el * NREC + (d * 2 + 0) * NF + p) * M + v];
                 surf += sL[(3 + d) * NMAX + k] * fp - sL[d * NMAX + k] * fm;
             }
-            const double unew = sU[i] + dt * double(sV[i] - surf);
+            const double unew = sU[i] + dt * widen<T>(sV[i] - surf);
             sU[i] = unew;
             uo[i] = unew;
         }

@@ -415,6 +415,7 @@ int aderdg_create(const aderdg_mesh_t *mesh, int N, int nVar, const aderdg_pde_t
         h->inv_dx[d] = 1.0 / h->dx[d];
         sd.inv_dx[d] = h->inv_dx[d];
     }
+    fill_desc_spacing(sd);
     sd.picard = h->picard;
     sd.u = h->u;
     sd.u_out = h->u;
