@@ -213,6 +213,18 @@ def _config(args, w, world):
 # the CUDA path
 # ---------------------------------------------------------------------------
 
+def _max_over_ranks(x: float, world: int, device: str = "cuda") -> float:
+    """The slowest rank's time: every rank gets the max (barrier semantics
+    of an all-reduce).  One process per GPU; the GPU path uses NCCL, the
+    host tests gloo."""
+    if world <= 1:
+        return x
+    import torch
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _time_single(A, torch, w, prec, stream, steps, warmup, flush, world):
     """Time `steps` device-CFL steps of one solve (L2 flushed between steps),
     with per-kernel CUDA events.  Returns the solver and the timings."""
@@ -317,6 +329,30 @@ def _equal_l2(A, w, steps):
     return out
 
 
+def _elastic(A, torch, stream, flush, steps):
+    """The 3D linear-elasticity workload (64^3 elements, N = 3, 9 variables,
+    Gaussian velocity pulse): both paths, and how far apart they are after
+    the timed steps."""
+    import numpy as np
+    w = dict(WORKLOADS["elastic3d_pulse_64^3_N3"])
+    out = {"workload": "elastic3d_pulse_64^3_N3"}
+    states = {}
+    for name, prec in (("fp64", A.ADERDG_FP64), ("mixed", A.ADERDG_MIXED_FP32)):
+        s, _, st, pr, co = _time_single(A, torch, w, prec, stream, steps, 2, flush, 1)
+        info = s.info()
+        states[name] = s.get_state()[0]
+        s.close()
+        out[name] = {"value": info["dofs"] * steps / (sum(st) / 1e3), "ms_per_step": sum(st) / steps,
+                     "predictor_ms": statistics.mean(pr), "corrector_ms": statistics.mean(co),
+                     "predictor_tflops": info["flops_predictor"] / (statistics.mean(pr) / 1e3) / 1e12}
+    a, b = states["mixed"], states["fp64"]
+    num = np.sqrt(np.sum((a - b) ** 2, axis=(0, 1)))
+    den = np.sqrt(np.sum(b ** 2, axis=(0, 1)))
+    out["mixed_vs_fp64_rel_l2"] = float(np.max(num[den > 0] / den[den > 0]))
+    out["steps"] = steps + 2
+    return out
+
+
 def _batched(A, torch, steps, warmup, count):
     """The batched workload: `count` independent 2D Euler vortex solves
     (meshes k^2, k in {32, ..., 256}; N in 2..6; eps in [1, 5]; centres in
@@ -418,11 +454,7 @@ def run_ours(args, w, rank, world):
     assert (info["cfl_alpha"], info["picard_iters"], info["dofs"]) == \
         (cfgd["cfl_alpha"], cfgd["picard_iters"], cfgd["dofs"]), (info, cfgd)
     dofs = info["dofs"]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = _max_over_ranks(sum(step_ms), world)
     value = world * dofs * args.steps / (total_ms / 1e3)
 
     # ---- end to end through the public API with host buffers ------------------
@@ -446,11 +478,7 @@ def run_ours(args, w, rank, world):
             b.synchronize()
             e2e_ms.append(a.elapsed_time(b))
     s.close()
-    e2e_total = sum(e2e_ms)
-    if world > 1:
-        t = torch.tensor([e2e_total], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_total = float(t.item())
+    e2e_total = _max_over_ranks(sum(e2e_ms), world)
     state_bytes = U0.nbytes
     e2e = {"value": world * dofs * e2e_steps / (e2e_total / 1e3), "unit": UNIT,
            "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes,
@@ -489,6 +517,8 @@ def run_ours(args, w, rank, world):
                            "roofline": _roofline(i2, p2, other, probe, args.workload),
                            "kernels": _kernels(i2, p2, c2, hbm)}
         variants["equal_l2"] = _equal_l2(A, w, args.l2_steps)
+        if args.elastic_steps > 0 and args.workload != "elastic3d_pulse_64^3_N3":
+            variants["elastic3d"] = _elastic(A, torch, stream, flush, args.elastic_steps)
         if args.batched_solves > 0:
             variants["batched"] = _batched(A, torch, max(8, min(args.steps, 64)), 8, args.batched_solves)
         if args.served_requests > 0:
@@ -535,6 +565,7 @@ def main():
     ap.add_argument("--no-variants", action="store_true",
                     help="only the headline path (no mixed/batched/served/equal-L2 runs)")
     ap.add_argument("--l2-steps", type=int, default=100)
+    ap.add_argument("--elastic-steps", type=int, default=4)
     ap.add_argument("--batched-solves", type=int, default=256)
     ap.add_argument("--served-requests", type=int, default=24)
     ap.add_argument("--served-rate", type=float, default=200.0)
