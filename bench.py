@@ -225,12 +225,12 @@ def _max_over_ranks(x: float, world: int, device: str = "cuda") -> float:
     return float(t.item())
 
 
-def _time_single(A, torch, w, prec, stream, steps, warmup, flush, world):
+def _time_single(A, torch, w, prec, stream, steps, warmup, flush, world, shapes=(0, 0)):
     """Time `steps` device-CFL steps of one solve (L2 flushed between steps),
     with per-kernel CUDA events.  Returns the solver and the timings."""
     import numpy as np
     s = A.Solver(w["pde"], w["dim"], w["cells"], w["lo"], w["hi"], w["N"], w["params"], precision=prec,
-                 stream=stream.cuda_stream)
+                 stream=stream.cuda_stream, shapes=shapes)
     X = s.node_coords(w["lo"], w["hi"])
     U0 = np.ascontiguousarray(_initial_state(w, X))
     t_far = 1e30
@@ -285,6 +285,8 @@ def _roofline(info, pred_avg, prec_name, probe, workload):
 def _kernels(info, pred_avg, corr_avg, hbm):
     corr_gbs = info["bytes_corrector"] / (corr_avg / 1e3) / 1e9
     return {
+        "tile_shapes": {k: info[k] for k in ("pred_shape", "pred_threads", "pred_epb",
+                                             "corr_shape", "corr_threads", "corr_epb")},
         "k_predictor": {"ms": pred_avg, "tflops": info["flops_predictor"] / (pred_avg / 1e3) / 1e12,
                         "gbs": info["bytes_predictor"] / (pred_avg / 1e3) / 1e9},
         "k_corrector": {"ms": corr_avg, "tflops": info["flops_corrector"] / (corr_avg / 1e3) / 1e12,
@@ -329,7 +331,7 @@ def _equal_l2(A, w, steps):
     return out
 
 
-def _elastic(A, torch, stream, flush, steps):
+def _elastic(A, torch, stream, flush, steps, shapes=(0, 0)):
     """The 3D linear-elasticity workload (64^3 elements, N = 3, 9 variables,
     Gaussian velocity pulse): both paths, and how far apart they are after
     the timed steps."""
@@ -338,7 +340,7 @@ def _elastic(A, torch, stream, flush, steps):
     out = {"workload": "elastic3d_pulse_64^3_N3"}
     states = {}
     for name, prec in (("fp64", A.ADERDG_FP64), ("mixed", A.ADERDG_MIXED_FP32)):
-        s, _, st, pr, co = _time_single(A, torch, w, prec, stream, steps, 2, flush, 1)
+        s, _, st, pr, co = _time_single(A, torch, w, prec, stream, steps, 2, flush, 1, shapes)
         info = s.info()
         states[name] = s.get_state()[0]
         s.close()
@@ -353,14 +355,14 @@ def _elastic(A, torch, stream, flush, steps):
     return out
 
 
-def _batched(A, torch, steps, warmup, count):
+def _batched(A, torch, steps, warmup, count, shapes=(0, 0)):
     """The batched workload: `count` independent 2D Euler vortex solves
     (meshes k^2, k in {32, ..., 256}; N in 2..6; eps in [1, 5]; centres in
     [3, 7]^2; seed 1808), FP32 predictor / FP64 update, one graph step each."""
     from paper_1808_03788_gb300 import inputs
     rec = inputs.batched_vortex_recipe(count)
     specs = [A.make_spec(2, 2, r["cells"], (0, 0), (10, 10), r["N"], (1.4,)) for r in rec]
-    b = A.Batch(specs, precision=A.ADERDG_MIXED_FP32, torch_alloc=False)
+    b = A.Batch(specs, precision=A.ADERDG_MIXED_FP32, torch_alloc=False, shapes=shapes)
     nodes = {N: A.aderdg_gl_nodes(N)[0] for N in range(2, 7)}
     for i, r in enumerate(rec):
         X = inputs.node_coords_torch(r["cells"], (0, 0), (10, 10), nodes[r["N"]])
@@ -385,7 +387,7 @@ def _batched(A, torch, steps, warmup, count):
             "dtype": "f32+f64"}
 
 
-def _served(A, requests, rate, seed=1808):
+def _served(A, requests, rate, seed=1808, shapes=(0, 0)):
     """The served stream: the first `requests` of the seeded Poisson stream
     (mean `rate`/s, 50/50 2D Euler vortex / 3D elasticity pulse, run to
     t = 1), submitted at their arrival times to a continuous-batching server."""
@@ -393,7 +395,12 @@ def _served(A, requests, rate, seed=1808):
 
     from paper_1808_03788_gb300 import inputs
     rec = inputs.served_stream_recipe(requests, rate, seed)
-    srv = A.Server(precision=A.ADERDG_MIXED_FP32)
+    if shapes == "auto":  # tune every (PDE, N) of the stream before it starts
+        for key in sorted({(r["pde"], r["dim"], r["N"]) for r in rec}):
+            sp = A.make_spec(key[0], key[1], (8,) * key[1], (0,) * key[1], (1,) * key[1], key[2],
+                             (1.4,) if key[0] == 2 else (1.0, 2.0, 1.0))
+            A.aderdg_autotune(sp, A.ADERDG_MIXED_FP32)
+    srv = A.Server(precision=A.ADERDG_MIXED_FP32, shapes=shapes)
     prepared = []
     for r in rec:
         if r["pde"] == 2:
@@ -448,7 +455,16 @@ def run_ours(args, w, rank, world):
     clocks = ClockSampler(_gpu_id() if rank == 0 else None)
     if rank == 0:
         clocks.start()
-    s, U0, step_ms, pred_ms, corr_ms = _time_single(A, torch, w, prec, stream, args.steps, args.warmup, flush, world)
+    shapes = "auto" if args.shapes == "auto" else (0, 0)
+    tune = {}
+    if shapes == "auto":  # timed here, before anything is measured; handles then find the choice
+        sp = A.make_spec(w["pde"], w["dim"], w["cells"], w["lo"], w["hi"], w["N"], w["params"])
+        for name, pr in (("fp64", A.ADERDG_FP64), ("mixed", A.ADERDG_MIXED_FP32)):
+            ch, ms = A.aderdg_autotune(sp, pr, force=True)
+            tune[name] = {"chosen": list(ch), "predictor_ms": ms[:A.ADERDG_NUM_SHAPES],
+                          "corrector_ms": ms[A.ADERDG_NUM_SHAPES:]}
+    s, U0, step_ms, pred_ms, corr_ms = _time_single(A, torch, w, prec, stream, args.steps, args.warmup, flush, world,
+                                                    shapes)
     clk = clocks.stop() if rank == 0 else None
     info = s.info()
     assert (info["cfl_alpha"], info["picard_iters"], info["dofs"]) == \
@@ -508,7 +524,7 @@ def run_ours(args, w, rank, world):
     if not args.no_variants:
         other = "mixed" if args.precision == "fp64" else "fp64"
         oprec = A.ADERDG_MIXED_FP32 if other == "mixed" else A.ADERDG_FP64
-        s2, _, st2, pr2, co2 = _time_single(A, torch, w, oprec, stream, args.steps, args.warmup, flush, 1)
+        s2, _, st2, pr2, co2 = _time_single(A, torch, w, oprec, stream, args.steps, args.warmup, flush, 1, shapes)
         i2 = s2.info()
         s2.close()
         p2, c2 = statistics.mean(pr2), statistics.mean(co2)
@@ -518,11 +534,18 @@ def run_ours(args, w, rank, world):
                            "kernels": _kernels(i2, p2, c2, hbm)}
         variants["equal_l2"] = _equal_l2(A, w, args.l2_steps)
         if args.elastic_steps > 0 and args.workload != "elastic3d_pulse_64^3_N3":
-            variants["elastic3d"] = _elastic(A, torch, stream, flush, args.elastic_steps)
+            variants["elastic3d"] = _elastic(A, torch, stream, flush, args.elastic_steps, shapes)
         if args.batched_solves > 0:
-            variants["batched"] = _batched(A, torch, max(8, min(args.steps, 64)), 8, args.batched_solves)
+            variants["batched"] = _batched(A, torch, max(8, min(args.steps, 64)), 8, args.batched_solves, shapes)
         if args.served_requests > 0:
-            variants["served"] = _served(A, args.served_requests, args.served_rate)
+            variants["served"] = _served(A, args.served_requests, args.served_rate, shapes=shapes)
+            sv = variants["served"]
+            if args.served_scaled > 0 and sv["ok"] > 0:
+                # the same stream at 80 % of the capacity the first run measured
+                mean_work = sv["dof_updates"] / sv["requests"]
+                rate = 0.8 * sv["value"] / mean_work
+                variants["served_80pct"] = _served(A, args.served_scaled, rate, shapes=shapes)
+                variants["served_80pct"]["rate_rule"] = "0.8 x measured DOF-updates/s / mean DOF-updates per request"
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
@@ -544,6 +567,7 @@ def run_ours(args, w, rank, world):
         "e2e": e2e,
         "clocks": clk,
         "gpu_launches": 3 * args.steps,
+        "autotune": tune or None,
         "variants": variants,
     }
     print(json.dumps(line), flush=True)
@@ -569,6 +593,10 @@ def main():
     ap.add_argument("--batched-solves", type=int, default=256)
     ap.add_argument("--served-requests", type=int, default=24)
     ap.add_argument("--served-rate", type=float, default=200.0)
+    ap.add_argument("--served-scaled", type=int, default=12,
+                    help="requests of a second served run at 80 %% of the measured capacity (0: skip)")
+    ap.add_argument("--shapes", default="auto", choices=["auto", "default"],
+                    help="tile shapes of the kernels: autotuned (default) or shape 0")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("note: fewer than 3 warm-up steps", file=sys.stderr)

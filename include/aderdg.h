@@ -80,6 +80,16 @@ extern "C" {
 #define ADERDG_HOST 0
 #define ADERDG_DEVICE 1
 
+/* ---- tile shapes -------------------------------------------------------
+ * The predictor and the corrector are each compiled in ADERDG_NUM_SHAPES
+ * launch shapes (CTA size and elements per CTA; shape 0 is the default,
+ * 1 and 2 halve and double the CTA).  Every shape computes bit-identical
+ * results; only the speed differs.  ADERDG_SHAPE_AUTOTUNE picks the shape
+ * measured fastest on the current device for the (PDE, d, N, precision). */
+#define ADERDG_NUM_SHAPES 3
+#define ADERDG_SHAPE_DEFAULT 0
+#define ADERDG_SHAPE_AUTOTUNE (-1)
+
 typedef struct {
     int dim;            /* 2 or 3 */
     int64_t cells[3];   /* elements per direction (> 0); unused entries ignored */
@@ -107,6 +117,11 @@ typedef struct {
                                    (0.9 x the von Neumann limit of the scheme) */
     void *cuda_stream;          /* cudaStream_t; NULL -> the legacy stream */
     const aderdg_alloc_t *alloc;/* NULL -> cudaMalloc / cudaFree */
+    int pred_shape;             /* predictor tile shape: 0 .. ADERDG_NUM_SHAPES-1
+                                   or ADERDG_SHAPE_AUTOTUNE */
+    int corr_shape;             /* corrector tile shape, likewise */
+    const char *tune_cache;     /* text file of autotuned shapes, read and
+                                   appended; NULL -> process memory only */
 } aderdg_config_t;
 
 typedef struct aderdg_s aderdg_t;
@@ -122,6 +137,9 @@ typedef struct {
     double bytes_predictor;     /* algorithmic HBM bytes of one predictor launch */
     double bytes_corrector;     /* algorithmic HBM bytes of one corrector launch */
     size_t device_bytes;        /* device memory held by the handle */
+    int pred_shape, pred_threads, pred_epb;  /* predictor shape in use: index,
+                                                CTA threads, elements per CTA */
+    int corr_shape, corr_threads, corr_epb;  /* corrector, likewise */
 } aderdg_info_t;
 
 /* Thread-local message of the last failure (never NULL). */
@@ -271,6 +289,8 @@ typedef struct {
     int steps_per_round;         /* steps between admission rounds; 0: 8 */
     int precision;               /* ADERDG_FP64 / ADERDG_MIXED_FP32 */
     void *cuda_stream;           /* NULL: a stream of the server's own */
+    int pred_shape, corr_shape;  /* tile shapes, as in aderdg_config_t */
+    const char *tune_cache;      /* as in aderdg_config_t */
 } aderdg_server_config_t;
 
 typedef struct {
@@ -333,6 +353,25 @@ int aderdg_server_stats(aderdg_server_t *s, int64_t *queued, int64_t *active, in
 int aderdg_step_noalloc(const aderdg_mesh_t *mesh, int N, int nVar, const aderdg_pde_t *pde,
                         int precision, int picard_iters, const double *u_in, double *u_out,
                         double dt, void *cuda_stream);
+
+/* ---- tile-shape autotuning ---------------------------------------------
+ * Not part of the paper's method (its kernels are tuned offline by its
+ * code generator); a performance aid of this library.
+ *
+ * Times every compiled predictor and corrector shape of spec's (PDE, d, N)
+ * at `precision` on a synthetic periodic mesh of about 2^21 nodes (the
+ * spec's mesh and state are not used; the cost of a step does not depend
+ * on the data) and returns the fastest shape indices in shapes[0]
+ * (predictor) and shapes[1] (corrector).  The choice is kept for the
+ * process and, if tune_cache is not NULL, appended to that text file; a
+ * later call finds it there without timing unless flags has
+ * ADERDG_TUNE_FORCE.  ms (NULL or 2 * ADERDG_NUM_SHAPES floats) receives
+ * the measured milliseconds per launch, predictor shapes first (-1 where
+ * nothing was timed).  Synchronising; allocates and frees device memory
+ * (about 2^21 x m x 40 bytes). */
+#define ADERDG_TUNE_FORCE 1
+int aderdg_autotune(const aderdg_solve_spec_t *spec, int precision, const char *tune_cache, int flags,
+                    int shapes[2], float *ms);
 
 /* Measurement utility: the FMA throughput this GPU sustains, in TFLOP/s
  * (FMA = 2 flops), from independent FMA chains on every SM.  kind 0: FP64

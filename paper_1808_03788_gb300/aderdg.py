@@ -30,6 +30,9 @@ ADERDG_E_CANCELLED = -8
 ADERDG_PDE_ADVECTION, ADERDG_PDE_EULER, ADERDG_PDE_ELASTICITY = 1, 2, 3
 ADERDG_FP64, ADERDG_MIXED_FP32 = 0, 1
 ADERDG_HOST, ADERDG_DEVICE = 0, 1
+ADERDG_NUM_SHAPES = 3
+ADERDG_SHAPE_DEFAULT, ADERDG_SHAPE_AUTOTUNE = 0, -1
+ADERDG_TUNE_FORCE = 1
 
 
 class AderdgError(RuntimeError):
@@ -56,7 +59,8 @@ class aderdg_alloc_t(C.Structure):
 
 class aderdg_config_t(C.Structure):
     _fields_ = [("precision", C.c_int), ("picard_iters", C.c_int), ("cfl_alpha", C.c_double),
-                ("cuda_stream", C.c_void_p), ("alloc", C.POINTER(aderdg_alloc_t))]
+                ("cuda_stream", C.c_void_p), ("alloc", C.POINTER(aderdg_alloc_t)),
+                ("pred_shape", C.c_int), ("corr_shape", C.c_int), ("tune_cache", C.c_char_p)]
 
 
 class aderdg_info_t(C.Structure):
@@ -64,7 +68,9 @@ class aderdg_info_t(C.Structure):
                 ("picard_iters", C.c_int), ("elements", C.c_int64), ("dofs", C.c_int64),
                 ("cfl_alpha", C.c_double), ("flops_predictor", C.c_double),
                 ("flops_corrector", C.c_double), ("bytes_predictor", C.c_double),
-                ("bytes_corrector", C.c_double), ("device_bytes", C.c_size_t)]
+                ("bytes_corrector", C.c_double), ("device_bytes", C.c_size_t),
+                ("pred_shape", C.c_int), ("pred_threads", C.c_int), ("pred_epb", C.c_int),
+                ("corr_shape", C.c_int), ("corr_threads", C.c_int), ("corr_epb", C.c_int)]
 
 
 class aderdg_solve_spec_t(C.Structure):
@@ -73,7 +79,8 @@ class aderdg_solve_spec_t(C.Structure):
 
 class aderdg_server_config_t(C.Structure):
     _fields_ = [("device_budget_bytes", C.c_size_t), ("max_queue", C.c_int), ("steps_per_round", C.c_int),
-                ("precision", C.c_int), ("cuda_stream", C.c_void_p)]
+                ("precision", C.c_int), ("cuda_stream", C.c_void_p), ("pred_shape", C.c_int),
+                ("corr_shape", C.c_int), ("tune_cache", C.c_char_p)]
 
 
 class aderdg_request_t(C.Structure):
@@ -114,6 +121,8 @@ _SIGS = {
     "aderdg_profile": (C.c_int, [_H, C.c_int]),
     "aderdg_profile_read": (C.c_int, [_H, C.POINTER(C.c_float), C.POINTER(C.c_float)]),
     "aderdg_peak_tflops": (C.c_int, [C.c_int, _DP]),
+    "aderdg_autotune": (C.c_int, [C.POINTER(aderdg_solve_spec_t), C.c_int, C.c_char_p, C.c_int,
+                                  C.POINTER(C.c_int), C.POINTER(C.c_float)]),
     "aderdg_batch_create": (C.c_int, [C.POINTER(aderdg_solve_spec_t), C.c_int, C.POINTER(aderdg_config_t),
                                       C.POINTER(_H)]),
     "aderdg_batch_destroy": (C.c_int, [_H]),
@@ -213,6 +222,15 @@ class _TorchAllocator:
         self._blocks.pop(ptr, None)
 
 
+def _set_shapes(cfg, shapes, tune_cache):
+    """Tile-shape request: (predictor, corrector) indices, ADERDG_SHAPE_AUTOTUNE,
+    or the string "auto" for both."""
+    if shapes == "auto":
+        shapes = (ADERDG_SHAPE_AUTOTUNE, ADERDG_SHAPE_AUTOTUNE)
+    cfg.pred_shape, cfg.corr_shape = int(shapes[0]), int(shapes[1])
+    cfg.tune_cache = None if tune_cache is None else os.fsencode(tune_cache)
+
+
 class Solver:
     """One ADER-DG solve on a periodic Cartesian mesh (a handle of the C ABI).
 
@@ -221,7 +239,7 @@ class Solver:
 
     def __init__(self, pde: int, dim: int, cells, lo, hi, N: int, params=(),
                  precision: int = ADERDG_FP64, picard: int = 0, alpha: float = 0.0,
-                 stream=None, torch_alloc: bool = True):
+                 stream=None, torch_alloc: bool = True, shapes=(0, 0), tune_cache=None):
         L = load()
         self.dim, self.N, self.pde = dim, N, pde
         self.m = nvar(pde, dim)
@@ -243,6 +261,7 @@ class Solver:
         cfg.precision = precision
         cfg.picard_iters = picard
         cfg.cfl_alpha = alpha
+        _set_shapes(cfg, shapes, tune_cache)
         self._alloc = None
         if stream is not None:
             cfg.cuda_stream = C.c_void_p(int(stream))
@@ -439,6 +458,18 @@ def aderdg_peak_tflops(kind: int) -> float:
     return v.value
 
 
+def aderdg_autotune(spec: aderdg_solve_spec_t, precision: int = ADERDG_MIXED_FP32, tune_cache=None,
+                    force: bool = False):
+    """Fastest (predictor, corrector) tile shapes for spec's (PDE, d, N) and
+    the measured ms per launch of every shape (-1: not timed, found cached)."""
+    shapes = (C.c_int * 2)()
+    ms = (C.c_float * (2 * ADERDG_NUM_SHAPES))()
+    _check(load().aderdg_autotune(C.byref(spec), int(precision),
+                                  None if tune_cache is None else os.fsencode(tune_cache),
+                                  ADERDG_TUNE_FORCE if force else 0, shapes, ms))
+    return (shapes[0], shapes[1]), list(ms)
+
+
 ADERDG_NOALLOC_SCRATCH_BYTES = 32 << 20
 
 
@@ -489,7 +520,7 @@ class Batch:
     """Many independent solves advanced together (aderdg_batch_*)."""
 
     def __init__(self, specs, precision: int = ADERDG_FP64, picard: int = 0, alpha: float = 0.0,
-                 stream=None, torch_alloc: bool = True):
+                 stream=None, torch_alloc: bool = True, shapes=(0, 0), tune_cache=None):
         L = load()
         self._L = L
         self.specs = list(specs)
@@ -498,6 +529,7 @@ class Batch:
         cfg.precision = precision
         cfg.picard_iters = picard
         cfg.cfl_alpha = alpha
+        _set_shapes(cfg, shapes, tune_cache)
         if stream is not None:
             cfg.cuda_stream = C.c_void_p(int(stream))
         self._alloc = None
@@ -568,7 +600,7 @@ class Server:
     """Continuous-batching request server (aderdg_server_*)."""
 
     def __init__(self, precision: int = ADERDG_FP64, budget_bytes: int = 0, max_queue: int = 0,
-                 steps_per_round: int = 0):
+                 steps_per_round: int = 0, shapes=(0, 0), tune_cache=None):
         L = load()
         self._L = L
         cfg = aderdg_server_config_t()
@@ -576,6 +608,8 @@ class Server:
         cfg.max_queue = max_queue
         cfg.steps_per_round = steps_per_round
         cfg.precision = precision
+        _set_shapes(cfg, shapes, tune_cache)
+        self._cache = cfg.tune_cache  # keeps the bytes alive while the server runs
         self._h = _H()
         _check(L.aderdg_server_create(C.byref(cfg), C.byref(self._h)))
 

@@ -9,6 +9,7 @@ from __future__ import annotations
 import concurrent.futures as cf
 import glob
 import os
+import re
 import shutil
 import subprocess
 import sys
@@ -32,12 +33,33 @@ def _nvcc() -> str:
     raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libaderdg.so")
 
 
+INST_SRC = os.path.join(CSRC, "inst.cu")
+_PDE_TYPE = {"advection": "Advection<%d>", "euler": "Euler<%d>", "elastic": "Elastic3"}
+
+
+def instances():
+    """(accessor name, PDE type, d, N, T) of every kernel instance: the
+    entries of csrc/instances.h, each in double and float."""
+    with open(os.path.join(CSRC, "instances.h")) as f:
+        text = f.read()
+    out = []
+    for tag, d, n in re.findall(r"X\((\w+), (\d), (\d)\)", text):
+        pde = _PDE_TYPE[tag] % int(d) if "%d" in _PDE_TYPE[tag] else _PDE_TYPE[tag]
+        for t, suffix in (("double", "f64"), ("float", "f32")):
+            out.append(("ks_%s%sd_n%s_%s" % (tag, d, n, suffix), pde, int(d), int(n), t))
+    if not out:
+        raise RuntimeError("no kernel instances found in csrc/instances.h")
+    return out
+
+
 def sources():
-    return sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cpp")))
+    """Translation units other than the instance template inst.cu."""
+    srcs = glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cpp"))
+    return sorted(s for s in srcs if s != INST_SRC)
 
 
 def _deps():
-    return sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h")) + \
+    return sources() + [INST_SRC] + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h")) + \
         [os.path.join(INCLUDE, "aderdg.h")]
 
 
@@ -48,11 +70,18 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(p) <= t for p in _deps())
 
 
-def _compile(src: str, extra: list[str]) -> str:
-    obj = os.path.join(BUILD, os.path.basename(src) + ".o")
-    if src.endswith(".cu"):
+def _compile(src, extra: list[str]) -> str:
+    if isinstance(src, tuple):  # a kernel instance of inst.cu
+        name, pde, d, n, t = src
+        obj = os.path.join(BUILD, name + ".o")
+        defs = ["-DADERDG_INST_NAME=" + name, "-DADERDG_INST_PDE=" + pde, "-DADERDG_INST_DIM=%d" % d,
+                "-DADERDG_INST_N=%d" % n, "-DADERDG_INST_T=" + t]
+        cmd = [_nvcc(), "-c", INST_SRC, "-o", obj] + NVFLAGS + defs + extra
+    elif src.endswith(".cu"):
+        obj = os.path.join(BUILD, os.path.basename(src) + ".o")
         cmd = [_nvcc(), "-c", src, "-o", obj] + NVFLAGS + extra
     else:
+        obj = os.path.join(BUILD, os.path.basename(src) + ".o")
         cmd = ["g++", "-c", src, "-o", obj] + CXXFLAGS + [f"-I{os.path.dirname(_nvcc())}/../include"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
@@ -66,7 +95,8 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     extra = extra or []
-    srcs = sources()
+    # the slowest units first: the instances with the most nodes
+    srcs = sorted(instances(), key=lambda i: -(i[3] + 1) ** i[2]) + sources()
     workers = min(len(srcs), max(2, os.cpu_count() or 2))
     with cf.ThreadPoolExecutor(workers) as ex:
         objs = list(ex.map(lambda s: _compile(s, extra), srcs))

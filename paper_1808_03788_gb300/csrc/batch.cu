@@ -30,14 +30,10 @@
 #include "basis.h"
 #include "common.cuh"
 #include "control.cuh"
+#include "tune.h"
 
 namespace aderdg {
 void set_last_error(const char *msg);
-const KernelSet *ks_advection2d(int N, int prec);
-const KernelSet *ks_advection3d(int N, int prec);
-const KernelSet *ks_euler2d(int N, int prec);
-const KernelSet *ks_euler3d(int N, int prec);
-const KernelSet *ks_elastic3d(int N, int prec);
 }  // namespace aderdg
 
 using namespace aderdg;
@@ -61,12 +57,7 @@ size_t a256(size_t b) { return (b + 255) / 256 * 256; }
 const KernelSet *kernels_for(int pde, int dim, int N, int prec)
 {
     if (N < 1 || N > 9) return nullptr;
-    if (pde == ADERDG_PDE_ADVECTION && dim == 2) return ks_advection2d(N, prec);
-    if (pde == ADERDG_PDE_ADVECTION && dim == 3) return ks_advection3d(N, prec);
-    if (pde == ADERDG_PDE_EULER && dim == 2) return ks_euler2d(N, prec);
-    if (pde == ADERDG_PDE_EULER && dim == 3) return ks_euler3d(N, prec);
-    if (pde == ADERDG_PDE_ELASTICITY && dim == 3) return ks_elastic3d(N, prec);
-    return nullptr;
+    return lookup_kernels(pde, dim, N, prec);
 }
 
 int nvar_of(int pde, int dim)
@@ -175,7 +166,8 @@ __global__ void k_set_tend(Control *const *ctls, const double *t_end, int count)
 struct Group {
     int pde = 0, dim = 0, N = 0;
     PdeParams pp{};
-    const KernelSet *ks = nullptr;
+    const KernelSet *ks = nullptr;  // compiled kernels of the group
+    KernelSet kso{};                // the same with the tile shapes in use
     KParams kp{};
     std::vector<Slot *> members;
     SolveDesc *d_desc = nullptr;
@@ -193,6 +185,8 @@ public:
     Mem mem;
     cudaStream_t st = nullptr;
     int prec = ADERDG_FP64;
+    int pred_req = 0, corr_req = 0;  // requested tile shapes (index or ADERDG_SHAPE_AUTOTUNE)
+    std::string tune_cache;          // empty: none
     int device = 0;
     // control blocks: one pool, slots index into it
     Control *d_ctl = nullptr;
@@ -304,6 +298,12 @@ public:
             s->member = (int)ng[gi].members.size();
             ng[gi].members.push_back(s);
         }
+        // tile shapes per group (may autotune on first use of a key)
+        for (Group &g : ng) {
+            const int rc = resolve_shapes(g.ks, g.pde, g.dim, g.N, prec, g.pp, pred_req, corr_req,
+                                          tune_cache.empty() ? nullptr : tune_cache.c_str(), &g.kso);
+            if (rc) return rc;
+        }
         // reuse device descriptor arrays of old groups where possible
         for (Group &g : groups) mem.put(g.d_desc, sizeof(SolveDesc) * g.cap);
         groups.clear();
@@ -317,8 +317,8 @@ public:
                 d.E = s->E;
                 d.tile0_p = tp;
                 d.tile0_c = tc;
-                tp += (s->E + g.ks->pred_epb - 1) / g.ks->pred_epb;
-                tc += (s->E + g.ks->corr_epb - 1) / g.ks->corr_epb;
+                tp += (s->E + g.kso.pred_epb - 1) / g.kso.pred_epb;
+                tc += (s->E + g.kso.corr_epb - 1) / g.kso.corr_epb;
                 for (int k = 0; k < 3; ++k) { d.cells[k] = s->cells[k]; d.inv_dx[k] = s->inv_dx[k]; }
                 fill_desc_spacing(d);
                 d.picard = s->picard;
@@ -342,12 +342,6 @@ public:
             g.kp.pde = g.pp;
             if (build_basis(g.N, g.kp.b)) return fail(ADERDG_E_INVAL, "basis construction failed");
             fill_ops(g.kp);
-            if (g.ks->pred_smem > 48 * 1024)
-                CKB(cudaFuncSetAttribute((const void *)g.ks->predictor, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)g.ks->pred_smem));
-            if (g.ks->corr_smem > 48 * 1024)
-                CKB(cudaFuncSetAttribute((const void *)g.ks->corrector, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)g.ks->corr_smem));
             groups.push_back(g);
         }
         // control pointers in active order
@@ -413,9 +407,9 @@ public:
         for (Group &g : groups) {
             KParams kp = g.kp;
             kp.ntiles = g.ntp;
-            g.ks->predictor<<<(unsigned)g.ntp, g.ks->pred_threads, g.ks->pred_smem, st>>>(kp);
+            g.kso.predictor<<<(unsigned)g.ntp, g.kso.pred_threads, g.kso.pred_smem, st>>>(kp);
             kp.ntiles = g.ntc;
-            g.ks->corrector<<<(unsigned)g.ntc, g.ks->corr_threads, g.ks->corr_smem, st>>>(kp);
+            g.kso.corrector<<<(unsigned)g.ntc, g.kso.corr_threads, g.kso.corr_smem, st>>>(kp);
         }
         CKB(cudaGetLastError());
         return ADERDG_OK;
@@ -486,6 +480,8 @@ int aderdg_batch_create(const aderdg_solve_spec_t *specs, int count, const aderd
     if (!specs || count <= 0) return fail(ADERDG_E_INVAL, "need count > 0 specs");
     const int prec = cfg ? cfg->precision : ADERDG_FP64;
     if (prec != ADERDG_FP64 && prec != ADERDG_MIXED_FP32) return fail(ADERDG_E_INVAL, "bad precision");
+    if (cfg && (!valid_shape_request(cfg->pred_shape) || !valid_shape_request(cfg->corr_shape)))
+        return fail(ADERDG_E_INVAL, "bad tile shape request");
     std::vector<Slot> tmp(count);
     for (int i = 0; i < count; ++i) {
         int rc = make_slot(specs[i], prec, cfg ? cfg->picard_iters : 0, cfg ? cfg->cfl_alpha : 0.0, tmp[i]);
@@ -506,6 +502,11 @@ int aderdg_batch_create(const aderdg_solve_spec_t *specs, int count, const aderd
         b->own_stream = true;
     }
     int rc = b->eng.init(count, st, cfg ? cfg->alloc : nullptr, prec);
+    if (cfg) {
+        b->eng.pred_req = cfg->pred_shape;
+        b->eng.corr_req = cfg->corr_shape;
+        if (cfg->tune_cache) b->eng.tune_cache = cfg->tune_cache;
+    }
     for (int i = 0; rc == ADERDG_OK && i < count; ++i) {
         Slot *s = new Slot(tmp[i]);
         rc = b->eng.add(s, 0.0);
@@ -791,6 +792,10 @@ int aderdg_server_create(const aderdg_server_config_t *cfg, aderdg_server_t **ou
     aderdg_server_t *s = new aderdg_server_s();
     s->prec = cfg ? cfg->precision : ADERDG_FP64;
     if (s->prec != ADERDG_FP64 && s->prec != ADERDG_MIXED_FP32) { delete s; return fail(ADERDG_E_INVAL, "bad precision"); }
+    if (cfg && (!valid_shape_request(cfg->pred_shape) || !valid_shape_request(cfg->corr_shape))) {
+        delete s;
+        return fail(ADERDG_E_INVAL, "bad tile shape request");
+    }
     if (cfg && cfg->max_queue > 0) s->max_queue = cfg->max_queue;
     if (cfg && cfg->steps_per_round > 0) s->steps_per_round = cfg->steps_per_round;
     size_t free_b = 0, total_b = 0;
@@ -805,6 +810,11 @@ int aderdg_server_create(const aderdg_server_config_t *cfg, aderdg_server_t **ou
         s->own_stream = true;
     }
     int rc = s->eng.init(4096, st, nullptr, s->prec);
+    if (cfg) {
+        s->eng.pred_req = cfg->pred_shape;
+        s->eng.corr_req = cfg->corr_shape;
+        if (cfg->tune_cache) s->eng.tune_cache = cfg->tune_cache;
+    }
     if (rc) {
         std::string m = aderdg_last_error();
         s->eng.release();

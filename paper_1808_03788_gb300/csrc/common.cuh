@@ -312,7 +312,20 @@ struct Geom {
     static constexpr int NREC = DIM * 2 * NF;      // records per element
 };
 
-// Host-visible description of the compiled kernels of one (PDE, d, N, precision).
+// One compiled launch shape of a per-element kernel: CTA size, elements per
+// CTA, dynamic shared memory.
+struct TileShape {
+    void (*kernel)(KParams);
+    int threads, epb;
+    size_t smem;
+};
+
+// Number of compiled tile shapes per kernel (shape 0 is the default).
+constexpr int NSHAPE = 3;
+
+// Host-visible description of the compiled kernels of one (PDE, d, N,
+// precision).  predictor/corrector and their sizes are the shapes in use;
+// pshape/cshape list every compiled shape for the autotuner.
 struct KernelSet {
     void (*predictor)(KParams);
     int pred_threads, pred_epb;
@@ -324,6 +337,20 @@ struct KernelSet {
     int nvar, rs, elem_bytes;  // elem_bytes = sizeof(T)
     int flux_flops, eig_flops;  // per point, for the cost model
     int rf;                     // doubles per element of the FP32 reference record (0: none)
+    TileShape pshape[NSHAPE], cshape[NSHAPE];
+    int pred_shape, corr_shape;  // indices of the shapes in use
 };
+
+// Copy of ks that launches predictor shape ps and corrector shape cs.
+inline KernelSet with_shapes(const KernelSet &ks, int ps, int cs)
+{
+    KernelSet k = ks;
+    const TileShape &p = ks.pshape[ps], &c = ks.cshape[cs];
+    k.predictor = p.kernel; k.pred_threads = p.threads; k.pred_epb = p.epb; k.pred_smem = p.smem;
+    k.corrector = c.kernel; k.corr_threads = c.threads; k.corr_epb = c.epb; k.corr_smem = c.smem;
+    k.pred_shape = ps;
+    k.corr_shape = cs;
+    return k;
+}
 
 }  // namespace aderdg

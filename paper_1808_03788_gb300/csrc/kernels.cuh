@@ -156,7 +156,7 @@ __device__ __forceinline__ float narrow<float>(double x) { return dbl_to_flt_rn(
 // The first iteration starts from q = u, constant in time, so its flux and
 // derivatives are taken once per spatial node and q[t] = u + dt c1[t] R with
 // c1 the row sums of iK1W (the general iteration applied to a time-constant q).
-template <class PDE, int DIM, int N, typename T>
+template <class PDE, int DIM, int N, typename T, int TS = 0>
 struct PredCfg {
     using G = Geom<PDE, DIM, N>;
     static constexpr int n = G::n, M = G::M, NS = G::NS, NST = G::NST, NF = G::NF, NREC = G::NREC;
@@ -164,14 +164,19 @@ struct PredCfg {
     // per-element shared buffer: DIM space-time flux fields, later
     // qbar | Fbar_d | face-trace stash
     static constexpr int ELEM = cmax(DIM * NST * M, ((1 + DIM) * NS + NREC) * M);
-    // FP64: smaller CTAs, several per SM (independent barrier domains keep
-    // the DFMA pipe fed); FP32: 256-thread CTAs
-    static constexpr int TARGET = sizeof(T) == 8 ? 128 : 256;
-    static constexpr int MINB = sizeof(T) == 8 ? (n * M < 24 ? 3 : 2) : ((n * M <= 20 || (M == 9 && n <= 4)) ? 3 : 2);
-    static constexpr int EPB_T = cmax(1, TARGET / NS);
+    // Shape 0 -- FP64: smaller CTAs, several per SM (independent barrier
+    // domains keep the DFMA pipe fed); FP32: 256-thread CTAs.  Shapes 1 and
+    // 2 halve and double the CTA at the same register cap per thread.
+    static constexpr int TARGET0 = sizeof(T) == 8 ? 128 : 256;
+    static constexpr int MINB0 = sizeof(T) == 8 ? (n * M < 24 ? 3 : 2) : ((n * M <= 20 || (M == 9 && n <= 4)) ? 3 : 2);
+    static constexpr int TARGET = TS == 1 ? TARGET0 / 2 : (TS == 2 ? TARGET0 * 2 : TARGET0);
     static constexpr int EPB_S = cmax(1, (int)((110 * 1024) / (ELEM * sizeof(T))));
-    static constexpr int EPB = cmin(EPB_T, EPB_S);
+    static constexpr int EPB = cmin(cmax(1, TARGET / NS), EPB_S);
     static constexpr int THREADS = round_up(EPB * NS, 32);
+    static constexpr int THREADS0 = round_up(cmin(cmax(1, TARGET0 / NS), EPB_S) * NS, 32);
+    // resident CTAs per SM for the launch bounds: the register cap per
+    // thread of shape 0 (65536 / (THREADS0 MINB0)) is kept
+    static constexpr int MINB = cmax(1, cmin(2048 / THREADS, (THREADS0 * MINB0) / THREADS));
     static constexpr int SHARED = round_up(DIM * n * n + 2 * n + 1, 4);  // Kw, F0, F1, dt/dx
     static constexpr size_t BYTES = sizeof(T) * (size_t)(SHARED + EPB * ELEM);
     // FP32 path: perturbation form about the element's node SREF
@@ -232,11 +237,11 @@ __device__ __forceinline__ void gather_R(const T *ebuf, int t, int s, const T *r
     }
 }
 
-template <class PDE, int DIM, int N, typename T>
-__global__ void __launch_bounds__(PredCfg<PDE, DIM, N, T>::THREADS, PredCfg<PDE, DIM, N, T>::MINB)
+template <class PDE, int DIM, int N, typename T, int TS>
+__global__ void __launch_bounds__(PredCfg<PDE, DIM, N, T, TS>::THREADS, PredCfg<PDE, DIM, N, T, TS>::MINB)
 k_predictor(const KParams P)
 {
-    using C = PredCfg<PDE, DIM, N, T>;
+    using C = PredCfg<PDE, DIM, N, T, TS>;
     constexpr int n = C::n, M = C::M, NS = C::NS, NST = C::NST, NF = C::NF, NREC = C::NREC;
     constexpr int EPB = C::EPB, RS = Geom<PDE, DIM, N>::RS;
     const Ops<T> &O = ops_of<T>(P);
@@ -503,7 +508,7 @@ __device__ __forceinline__ void stage(void *dst, const void *src, int bytes)
     for (int i = threadIdx.x; i < units; i += blockDim.x) cp_async(d + i * GRAN, s + i * GRAN, GRAN);
 }
 
-template <class PDE, int DIM, int N, typename T>
+template <class PDE, int DIM, int N, typename T, int TS = 0>
 struct CorrCfg {
     using G = Geom<PDE, DIM, N>;
     static constexpr int n = G::n, M = G::M, NS = G::NS, NF = G::NF, NREC = G::NREC, RS = G::RS;
@@ -513,10 +518,11 @@ struct CorrCfg {
     static constexpr size_t VB = sizeof(T) * NS * M;
     static constexpr size_t FS = sizeof(T) * NREC * M;
     static constexpr size_t PER_ELEM = align16(OWN) + align16(NB) + align16(UB) + align16(VB) + align16(FS);
-    static constexpr int EPB_T = cmax(1, 256 / NS);
+    // shapes 0, 1, 2: 256-, 128- and 512-thread CTAs
+    static constexpr int THREADS = TS == 1 ? 128 : (TS == 2 ? 512 : 256);
+    static constexpr int EPB_T = cmax(1, THREADS / NS);
     static constexpr int EPB_S = cmax(1, (int)((110 * 1024) / PER_ELEM));
     static constexpr int EPB = cmin(EPB_T, EPB_S);
-    static constexpr int THREADS = 256;
     static constexpr size_t O_OWN = 0;
     static constexpr size_t O_NB = align16(EPB * OWN);
     static constexpr size_t O_U = O_NB + align16(EPB * NB);
@@ -550,11 +556,11 @@ __device__ __forceinline__ int neighbour(int e, int cx, int cy, int cz, int d, i
     return ix + cx * (iy + cy * iz);
 }
 
-template <class PDE, int DIM, int N, typename T>
-__global__ void __launch_bounds__(256)
+template <class PDE, int DIM, int N, typename T, int TS>
+__global__ void __launch_bounds__(CorrCfg<PDE, DIM, N, T, TS>::THREADS)
 k_corrector(const KParams P)
 {
-    using C = CorrCfg<PDE, DIM, N, T>;
+    using C = CorrCfg<PDE, DIM, N, T, TS>;
     constexpr int n = C::n, M = C::M, NS = C::NS, NF = C::NF, NREC = C::NREC, RS = C::RS, EPB = C::EPB;
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -791,14 +797,31 @@ struct KS {
     static const KernelSet value;
 };
 
+template <class PDE, int DIM, int N, typename T, int TS>
+constexpr TileShape pred_shape()
+{
+    using C = PredCfg<PDE, DIM, N, T, TS>;
+    return TileShape{&k_predictor<PDE, DIM, N, T, TS>, C::THREADS, C::EPB, C::BYTES};
+}
+
+template <class PDE, int DIM, int N, typename T, int TS>
+constexpr TileShape corr_shape()
+{
+    using C = CorrCfg<PDE, DIM, N, T, TS>;
+    return TileShape{&k_corrector<PDE, DIM, N, T, TS>, C::THREADS, C::EPB, C::BYTES};
+}
+
 template <class PDE, int DIM, int N, typename T>
 const KernelSet KS<PDE, DIM, N, T>::value = {
-    &k_predictor<PDE, DIM, N, T>, PredCfg<PDE, DIM, N, T>::THREADS, PredCfg<PDE, DIM, N, T>::EPB,
+    &k_predictor<PDE, DIM, N, T, 0>, PredCfg<PDE, DIM, N, T>::THREADS, PredCfg<PDE, DIM, N, T>::EPB,
     PredCfg<PDE, DIM, N, T>::BYTES,
-    &k_corrector<PDE, DIM, N, T>, CorrCfg<PDE, DIM, N, T>::THREADS, CorrCfg<PDE, DIM, N, T>::EPB,
+    &k_corrector<PDE, DIM, N, T, 0>, CorrCfg<PDE, DIM, N, T>::THREADS, CorrCfg<PDE, DIM, N, T>::EPB,
     CorrCfg<PDE, DIM, N, T>::BYTES,
     &k_cfl<PDE, DIM, N, T>,
     Geom<PDE, DIM, N>::M, Geom<PDE, DIM, N>::RS, (int)sizeof(T), PDE::FLUX_FLOPS, PDE::EIG_FLOPS,
-    PredCfg<PDE, DIM, N, T>::DELTA ? PredCfg<PDE, DIM, N, T>::RF : 0};
+    PredCfg<PDE, DIM, N, T>::DELTA ? PredCfg<PDE, DIM, N, T>::RF : 0,
+    {pred_shape<PDE, DIM, N, T, 0>(), pred_shape<PDE, DIM, N, T, 1>(), pred_shape<PDE, DIM, N, T, 2>()},
+    {corr_shape<PDE, DIM, N, T, 0>(), corr_shape<PDE, DIM, N, T, 1>(), corr_shape<PDE, DIM, N, T, 2>()},
+    0, 0};
 
 }  // namespace aderdg

@@ -23,14 +23,10 @@
 #include "../../include/aderdg.h"
 #include "basis.h"
 #include "common.cuh"
+#include "tune.h"
 
 namespace aderdg {
 void set_last_error(const char *msg);
-const KernelSet *ks_advection2d(int N, int prec);
-const KernelSet *ks_advection3d(int N, int prec);
-const KernelSet *ks_euler2d(int N, int prec);
-const KernelSet *ks_euler3d(int N, int prec);
-const KernelSet *ks_elastic3d(int N, int prec);
 }  // namespace aderdg
 
 using namespace aderdg;
@@ -59,12 +55,7 @@ size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 
 const KernelSet *kernels_for(int pde, int dim, int N, int prec)
 {
-    if (pde == ADERDG_PDE_ADVECTION && dim == 2) return ks_advection2d(N, prec);
-    if (pde == ADERDG_PDE_ADVECTION && dim == 3) return ks_advection3d(N, prec);
-    if (pde == ADERDG_PDE_EULER && dim == 2) return ks_euler2d(N, prec);
-    if (pde == ADERDG_PDE_EULER && dim == 3) return ks_euler3d(N, prec);
-    if (pde == ADERDG_PDE_ELASTICITY && dim == 3) return ks_elastic3d(N, prec);
-    return nullptr;
+    return lookup_kernels(pde, dim, N, prec);
 }
 
 // Device address of the scratch on the current device; looked up once per

@@ -14,14 +14,8 @@
 #include "basis.h"
 #include "common.cuh"
 #include "control.cuh"
+#include "tune.h"
 
-namespace aderdg {
-const KernelSet *ks_advection2d(int N, int prec);
-const KernelSet *ks_advection3d(int N, int prec);
-const KernelSet *ks_euler2d(int N, int prec);
-const KernelSet *ks_euler3d(int N, int prec);
-const KernelSet *ks_elastic3d(int N, int prec);
-}  // namespace aderdg
 
 using namespace aderdg;
 
@@ -48,12 +42,7 @@ int cuda_fail(cudaError_t e, const char *what)
 
 const KernelSet *find_kernels(int pde, int dim, int N, int prec)
 {
-    if (pde == ADERDG_PDE_ADVECTION && dim == 2) return ks_advection2d(N, prec);
-    if (pde == ADERDG_PDE_ADVECTION && dim == 3) return ks_advection3d(N, prec);
-    if (pde == ADERDG_PDE_EULER && dim == 2) return ks_euler2d(N, prec);
-    if (pde == ADERDG_PDE_EULER && dim == 3) return ks_euler3d(N, prec);
-    if (pde == ADERDG_PDE_ELASTICITY && dim == 3) return ks_elastic3d(N, prec);
-    return nullptr;
+    return lookup_kernels(pde, dim, N, prec);
 }
 
 int pde_nvar(int pde, int dim)
@@ -163,7 +152,8 @@ struct aderdg_s {
     double dx[3] = {1, 1, 1};
     double lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1};
     double alpha = 0;
-    const KernelSet *ks = nullptr;
+    const KernelSet *ks = nullptr;  // = &kso
+    KernelSet kso{};                // kernels with the tile shapes in use
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     aderdg_alloc_t alloc{};
@@ -355,7 +345,14 @@ int aderdg_create(const aderdg_mesh_t *mesh, int N, int nVar, const aderdg_pde_t
     h->NS = ipow(h->n, h->dim);
     h->NF = ipow(h->n, h->dim - 1);
     h->NREC = h->dim * 2 * h->NF;
-    h->ks = ks;
+    {
+        PdeParams pp;
+        for (int i = 0; i < 8; ++i) pp.p[i] = pde->p[i];
+        const int rc = resolve_shapes(ks, pde->kind, mesh->dim, N, prec, pp, cfg ? cfg->pred_shape : 0,
+                                      cfg ? cfg->corr_shape : 0, cfg ? cfg->tune_cache : nullptr, &h->kso);
+        if (rc) { delete h; return rc; }
+    }
+    h->ks = ks = &h->kso;
     for (int d = 0; d < 3; ++d) {
         h->lo[d] = d < h->dim ? mesh->lo[d] : 0.0;
         h->hi[d] = d < h->dim ? mesh->hi[d] : 1.0;
@@ -392,19 +389,6 @@ int aderdg_create(const aderdg_mesh_t *mesh, int N, int nVar, const aderdg_pde_t
         h->host_pinned = nullptr;
         aderdg_destroy(h);
         return fail(ADERDG_E_NOMEM, "pinned host allocation failed");
-    }
-    // kernels with > 48 KB of dynamic shared memory need an opt-in
-    if (ks->pred_smem > 48 * 1024 &&
-        cudaFuncSetAttribute((const void *)ks->predictor, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)ks->pred_smem) != cudaSuccess) {
-        aderdg_destroy(h);
-        return fail(ADERDG_E_CUDA, "predictor shared memory opt-in failed");
-    }
-    if (ks->corr_smem > 48 * 1024 &&
-        cudaFuncSetAttribute((const void *)ks->corrector, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)ks->corr_smem) != cudaSuccess) {
-        aderdg_destroy(h);
-        return fail(ADERDG_E_CUDA, "corrector shared memory opt-in failed");
     }
 
     SolveDesc &sd = h->desc;
@@ -481,6 +465,12 @@ int aderdg_get_info(const aderdg_t *h, aderdg_info_t *info)
     info->dofs = h->E * h->NS;
     info->cfl_alpha = h->alpha;
     info->device_bytes = h->device_bytes;
+    info->pred_shape = h->ks->pred_shape;
+    info->pred_threads = h->ks->pred_threads;
+    info->pred_epb = h->ks->pred_epb;
+    info->corr_shape = h->ks->corr_shape;
+    info->corr_threads = h->ks->corr_threads;
+    info->corr_epb = h->ks->corr_epb;
     fill_cost(h, info);
     return ADERDG_OK;
 }

@@ -1,0 +1,23 @@
+// Tile-shape selection for the per-element kernels (see tune.cu).
+#pragma once
+#include "common.cuh"
+
+namespace aderdg {
+
+// A tile-shape request is a shape index or ADERDG_SHAPE_AUTOTUNE (-1).
+inline bool valid_shape_request(int r) { return r == -1 || (r >= 0 && r < NSHAPE); }
+
+// Kernel set of one (PDE, d, N, precision), or NULL if none is compiled.
+const KernelSet *lookup_kernels(int pde, int dim, int N, int prec);
+
+// Copy of *ks launching the requested predictor / corrector shapes.  A
+// request is a shape index (0 .. NSHAPE-1) or ADERDG_SHAPE_AUTOTUNE, which
+// takes the fastest shape measured for this (PDE, d, N, precision) on the
+// current device: from the process-wide table, else from the text file
+// `cache` (may be NULL), else by timing every shape (and appending the
+// result to `cache`).  Opts the chosen kernels in to their dynamic shared
+// memory.  Returns an ADERDG_* status.
+int resolve_shapes(const KernelSet *ks, int pde, int dim, int N, int prec, const PdeParams &pp, int pred_req,
+                   int corr_req, const char *cache, KernelSet *out);
+
+}  // namespace aderdg

@@ -1,0 +1,98 @@
+"""Tile shapes and the autotuner: every compiled launch shape of the
+predictor and the corrector gives a result bitwise equal to the default
+shape's (the per-element arithmetic does not depend on how elements are
+grouped into CTAs), the autotuner returns valid shapes, keeps them in its
+cache file and reads them back, and autotuned batches equal default ones."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1808_03788_gb300 import aderdg as A
+from paper_1808_03788_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+EL = (1.0, 2.0, 1.0)
+
+# (pde, dim, cells, lo, hi, N, params, t_end): ragged element counts so
+# that every shape has a partial last tile
+CASES = [
+    (2, 2, (7, 5), (0, 0), (10, 10), 4, (1.4,), 0.2),
+    (2, 2, (5, 3), (0, 0), (10, 10), 2, (1.4,), 0.3),
+    (3, 3, (3, 2, 3), (0, 0, 0), (1, 1, 1), 3, EL, 0.02),
+    (1, 2, (6, 5), (0, 0), (1, 1), 6, (1.0, 1.0), 0.03),
+]
+
+
+def _ic(case):
+    pde, dim, cells, lo, hi, N, params, _ = case
+    X = oracle.node_coords(oracle.make_cfg(dim, cells, lo, hi, N, pde, params))
+    if pde == 2:
+        return inputs.euler_vortex(X)
+    if pde == 3:
+        return inputs.elastic_pulse(X, width=0.05)
+    return inputs.advection_sine(X)
+
+
+def _run(case, shapes, precision):
+    pde, dim, cells, lo, hi, N, params, t_end = case
+    with A.Solver(pde, dim, cells, lo, hi, N, params, precision=precision, shapes=shapes) as s:
+        s.set_state(_ic(case))
+        s.advance(t_end)
+        U, t, k = s.get_state()
+        info = s.info()
+    return U, k, info
+
+
+@pytest.mark.parametrize("precision", [A.ADERDG_FP64, A.ADERDG_MIXED_FP32])
+@pytest.mark.parametrize("case", CASES, ids=lambda c: "pde%d_d%d_N%d" % (c[0], c[1], c[5]))
+def test_every_shape_is_bitwise_the_default(case, precision):
+    U0, k0, info0 = _run(case, (0, 0), precision)
+    assert k0 > 0
+    assert info0["pred_shape"] == 0 and info0["corr_shape"] == 0
+    seen = set()
+    for ps in range(A.ADERDG_NUM_SHAPES):
+        for cs in range(A.ADERDG_NUM_SHAPES):
+            if (ps, cs) == (0, 0):
+                continue
+            U, k, info = _run(case, (ps, cs), precision)
+            assert (info["pred_shape"], info["corr_shape"]) == (ps, cs)
+            seen.add((info["pred_threads"], info["pred_epb"], info["corr_threads"], info["corr_epb"]))
+            assert k == k0
+            np.testing.assert_array_equal(U, U0, err_msg="shapes %d/%d" % (ps, cs))
+    assert len(seen) >= 2  # the shapes really differ
+
+
+def test_autotune_cache_roundtrip(tmp_path):
+    cache = tmp_path / "shapes.txt"
+    sp = A.make_spec(2, 2, (40, 40), (0, 0), (10, 10), 4, (1.4,))
+    shapes, ms = A.aderdg_autotune(sp, A.ADERDG_MIXED_FP32, tune_cache=str(cache), force=True)
+    assert all(0 <= s < A.ADERDG_NUM_SHAPES for s in shapes)
+    assert all(t > 0 for t in ms), ms
+    # the chosen shapes are the fastest up to the 2 % hysteresis
+    P, Cr = ms[:A.ADERDG_NUM_SHAPES], ms[A.ADERDG_NUM_SHAPES:]
+    assert P[shapes[0]] <= min(P) / 0.98 + 1e-9 and Cr[shapes[1]] <= min(Cr) / 0.98 + 1e-9
+    line = cache.read_text().strip().splitlines()[-1].split()
+    assert line[0].startswith("pde2_d2_N4_p1_") and (int(line[1]), int(line[2])) == tuple(shapes)
+    # a second call finds the choice without timing
+    again, ms2 = A.aderdg_autotune(sp, A.ADERDG_MIXED_FP32, tune_cache=str(cache))
+    assert tuple(again) == tuple(shapes) and all(t == -1 for t in ms2)
+    # handles created with the autotune request use it
+    with A.Solver(2, 2, (12, 12), (0, 0), (10, 10), 4, (1.4,), precision=A.ADERDG_MIXED_FP32,
+                  shapes="auto", tune_cache=str(cache)) as s:
+        info = s.info()
+    assert (info["pred_shape"], info["corr_shape"]) == tuple(shapes)
+
+
+def test_autotuned_batch_equals_default_batch():
+    cases = CASES[:3]
+    out = []
+    for shapes in [(0, 0), "auto"]:
+        b = A.Batch([A.make_spec(*c[:7]) for c in cases], precision=A.ADERDG_MIXED_FP32, shapes=shapes)
+        for i, c in enumerate(cases):
+            b.set_state(i, _ic(c))
+        b.advance([c[7] for c in cases])
+        out.append([b.get_state(i)[0] for i in range(len(cases))])
+        b.close()
+    for a, c in zip(*out):
+        np.testing.assert_array_equal(a, c)

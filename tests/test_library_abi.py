@@ -104,3 +104,57 @@ def test_no_cpu_fallback_without_gpu():
     assert "no CUDA device" in msg
     with pytest.raises(A.AderdgError):
         A.Solver(A.ADERDG_PDE_EULER, 2, (4, 4), (0, 0), (1, 1), 3, [1.4], torch_alloc=False)
+
+
+_STRUCTS = ["aderdg_mesh_t", "aderdg_pde_t", "aderdg_alloc_t", "aderdg_config_t", "aderdg_info_t",
+            "aderdg_solve_spec_t", "aderdg_server_config_t", "aderdg_request_t", "aderdg_result_t"]
+
+
+def test_binding_struct_layouts_match_the_header(tmp_path):
+    """Size and field offsets of every ABI struct as the C compiler lays it
+    out from include/aderdg.h == the ctypes mirror of the binding."""
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "aderdg.h"', 'int main(void) {']
+    for name in _STRUCTS:
+        st = getattr(A, name)
+        lines.append('printf("%s size %%zu\\n", sizeof(%s));' % (name, name))
+        for f, _ in st._fields_:
+            lines.append('printf("%s %s %%zu\\n", offsetof(%s, %s));' % (name, f, name, f))
+    lines += ['return 0;', '}']
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    import subprocess
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for name in _STRUCTS:
+        st = getattr(A, name)
+        assert got[(name, "size")] == C.sizeof(st), name
+        for f, _ in st._fields_:
+            assert got[(name, f)] == getattr(st, f).offset, (name, f)
+
+
+def test_tile_shape_requests_are_validated():
+    """A shape index outside 0..ADERDG_NUM_SHAPES-1 (other than the autotune
+    request) is rejected before any device work."""
+    cfg = A.aderdg_config_t()
+    cfg.precision = A.ADERDG_FP64
+    cfg.pred_shape = A.ADERDG_NUM_SHAPES
+    sp = A.make_spec(A.ADERDG_PDE_EULER, 2, (4, 4), (0, 0), (1, 1), 2, (1.4,))
+    h = A._H()
+    rc = A.load().aderdg_batch_create(C.byref(sp), 1, C.byref(cfg), C.byref(h))
+    assert rc == A.ADERDG_E_INVAL
+    assert b"tile shape" in A.load().aderdg_last_error()
+
+
+def test_instance_list_covers_the_documented_orders():
+    """The build compiles 2D advection/Euler for N = 1..7 and 3D advection,
+    Euler and elasticity for N = 1..4, each in double and float."""
+    from paper_1808_03788_gb300 import build
+    inst = build.instances()
+    keys = {(name.split("_")[1], d, n, t) for name, _, d, n, t in inst}
+    want = {(tag + "%dd" % d, d, n, t) for tag, d, ns in [("advection", 2, range(1, 8)), ("euler", 2, range(1, 8)),
+                                                           ("advection", 3, range(1, 5)), ("euler", 3, range(1, 5)),
+                                                           ("elastic", 3, range(1, 5))]
+            for n in ns for t in ("double", "float")}
+    assert keys == want
