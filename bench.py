@@ -225,12 +225,12 @@ def _max_over_ranks(x: float, world: int, device: str = "cuda") -> float:
     return float(t.item())
 
 
-def _time_single(A, torch, w, prec, stream, steps, warmup, flush, world, shapes=(0, 0)):
+def _time_single(A, torch, w, prec, stream, steps, warmup, flush, world, shapes=(0, 0), guess=0, picard=0):
     """Time `steps` device-CFL steps of one solve (L2 flushed between steps),
     with per-kernel CUDA events.  Returns the solver and the timings."""
     import numpy as np
     s = A.Solver(w["pde"], w["dim"], w["cells"], w["lo"], w["hi"], w["N"], w["params"], precision=prec,
-                 stream=stream.cuda_stream, shapes=shapes)
+                 stream=stream.cuda_stream, shapes=shapes, guess=guess, picard=picard)
     X = s.node_coords(w["lo"], w["hi"])
     U0 = np.ascontiguousarray(_initial_state(w, X))
     t_far = 1e30
@@ -292,6 +292,46 @@ def _kernels(info, pred_avg, corr_avg, hbm):
         "k_corrector": {"ms": corr_avg, "tflops": info["flops_corrector"] / (corr_avg / 1e3) / 1e12,
                         "gbs": corr_gbs, "hbm_frac": corr_gbs / hbm, "hbm_peak_gbs": hbm},
     }
+
+
+def _guess_variant(A, torch, w, stream, flush, steps, warmup, shapes, l2_steps, probe, hbm, workload):
+    """The third-order initial guess of Sec. 2.2 with the paper's N-2 Picard
+    iterations: both precisions timed like the headline, and the L2 errors
+    against the exact vortex after `l2_steps` steps next to the trivial
+    guess's."""
+    import numpy as np
+
+    from paper_1808_03788_gb300 import inputs
+    P = max(1, w["N"] - 2)
+    out = {"initial_guess": "third order (k1 = L(u), k2 = L(u + dt k1))", "picard_iters": P}
+    for name, prec in (("fp64", A.ADERDG_FP64), ("mixed", A.ADERDG_MIXED_FP32)):
+        s, _, st, pr, co = _time_single(A, torch, w, prec, stream, steps, warmup, flush, 1, shapes,
+                                        A.ADERDG_GUESS_ORDER3, P)
+        info = s.info()
+        s.close()
+        p, c = statistics.mean(pr), statistics.mean(co)
+        out[name] = {"value": info["dofs"] * steps / (sum(st) / 1e3), "ms_per_step": sum(st) / steps, "unit": UNIT,
+                     "roofline": _roofline(info, p, name, probe, workload), "kernels": _kernels(info, p, c, hbm)}
+    if w["ic"] == "vortex" and l2_steps > 0:
+        _, wq = A.aderdg_gl_nodes(w["N"])
+        wn = np.ones(1)
+        for _ in range(w["dim"]):
+            wn = np.kron(wq, wn)
+        vol = np.prod([(w["hi"][d] - w["lo"][d]) / w["cells"][d] for d in range(w["dim"])])
+        W = (vol * wn)[None, :, None]
+        for name, prec, guess, picard in (("fp64_trivial", A.ADERDG_FP64, 0, 0),
+                                          ("fp64_order3", A.ADERDG_FP64, A.ADERDG_GUESS_ORDER3, P),
+                                          ("mixed_order3", A.ADERDG_MIXED_FP32, A.ADERDG_GUESS_ORDER3, P)):
+            with A.Solver(w["pde"], w["dim"], w["cells"], w["lo"], w["hi"], w["N"], w["params"], precision=prec,
+                          guess=guess, picard=picard) as s:
+                X = s.node_coords(w["lo"], w["hi"])
+                s.set_state(_initial_state(w, X))
+                s.advance(1e30, max_steps=l2_steps)
+                U, t, k = s.get_state()
+            e = U - inputs.euler_vortex(X, t=t)
+            out["l2_err_vs_exact_rho_" + name] = float(np.sqrt(np.sum(W * e * e, axis=(0, 1)))[0])
+        out["l2_steps"] = l2_steps
+    return out
 
 
 def _equal_l2(A, w, steps):
@@ -533,6 +573,9 @@ def run_ours(args, w, rank, world):
                            "roofline": _roofline(i2, p2, other, probe, args.workload),
                            "kernels": _kernels(i2, p2, c2, hbm)}
         variants["equal_l2"] = _equal_l2(A, w, args.l2_steps)
+        if args.guess_variant:
+            variants["guess_order3"] = _guess_variant(A, torch, w, stream, flush, args.steps, args.warmup, shapes,
+                                                      args.l2_steps, probe, hbm, args.workload)
         if args.elastic_steps > 0 and args.workload != "elastic3d_pulse_64^3_N3":
             variants["elastic3d"] = _elastic(A, torch, stream, flush, args.elastic_steps, shapes)
         if args.batched_solves > 0:
@@ -595,6 +638,8 @@ def main():
     ap.add_argument("--served-rate", type=float, default=200.0)
     ap.add_argument("--served-scaled", type=int, default=12,
                     help="requests of a second served run at 80 %% of the measured capacity (0: skip)")
+    ap.add_argument("--no-guess-variant", dest="guess_variant", action="store_false",
+                    help="skip the third-order initial guess variant")
     ap.add_argument("--shapes", default="auto", choices=["auto", "default"],
                     help="tile shapes of the kernels: autotuned (default) or shape 0")
     args = ap.parse_args()

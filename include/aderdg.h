@@ -80,6 +80,19 @@ extern "C" {
 #define ADERDG_HOST 0
 #define ADERDG_DEVICE 1
 
+/* ---- initial guess of the Picard iteration (Sec. 2.2) ------------------
+ * TRIVIAL  q0 = u(t^n)                                    (default)
+ * ORDER2   q0 = u + tau L(u)                              (second order)
+ * ORDER3   q0 = u + tau k1 + tau^2 (k2 - k1) / (2 dt),    (third order)
+ *          k1 = L(u), k2 = L(u + dt k1)
+ * with tau = t - t^n and L(w) = -div F(w), the element-local nodal
+ * derivative of the flux.  The default Picard count after a guess of
+ * degree k in time is max(1, N + 1 - k): N+1 for TRIVIAL, N for ORDER2,
+ * N-1 for ORDER3 (the paper notes N - k iterations suffice). */
+#define ADERDG_GUESS_TRIVIAL 0
+#define ADERDG_GUESS_ORDER2 1
+#define ADERDG_GUESS_ORDER3 2
+
 /* ---- tile shapes -------------------------------------------------------
  * The predictor and the corrector are each compiled in ADERDG_NUM_SHAPES
  * launch shapes (CTA size and elements per CTA; shape 0 is the default,
@@ -112,7 +125,8 @@ typedef struct {
 
 typedef struct {
     int precision;              /* ADERDG_FP64 / ADERDG_MIXED_FP32 */
-    int picard_iters;           /* Picard iterations P; 0 -> N+1 */
+    int picard_iters;           /* Picard iterations P after the initial guess;
+                                   0 -> max(1, N + 1 - degree of the guess) */
     double cfl_alpha;           /* CFL coefficient; 0 -> library default
                                    (0.9 x the von Neumann limit of the scheme) */
     void *cuda_stream;          /* cudaStream_t; NULL -> the legacy stream */
@@ -122,6 +136,7 @@ typedef struct {
     int corr_shape;             /* corrector tile shape, likewise */
     const char *tune_cache;     /* text file of autotuned shapes, read and
                                    appended; NULL -> process memory only */
+    int initial_guess;          /* ADERDG_GUESS_* (0: trivial) */
 } aderdg_config_t;
 
 typedef struct aderdg_s aderdg_t;
@@ -140,6 +155,7 @@ typedef struct {
     int pred_shape, pred_threads, pred_epb;  /* predictor shape in use: index,
                                                 CTA threads, elements per CTA */
     int corr_shape, corr_threads, corr_epb;  /* corrector, likewise */
+    int initial_guess;                       /* ADERDG_GUESS_* */
 } aderdg_info_t;
 
 /* Thread-local message of the last failure (never NULL). */
@@ -245,8 +261,8 @@ typedef struct {
 } aderdg_solve_spec_t;
 
 /* Create a batch of `count` solves (state zero, t = 0).  cfg applies to all
- * of them (precision, Picard count: 0 -> N+1 per solve, CFL alpha: 0 ->
- * default per N, stream, allocator). */
+ * of them (precision, initial guess, Picard count: 0 -> the default rule per
+ * solve's N, CFL alpha: 0 -> default per N, stream, allocator, tile shapes). */
 int aderdg_batch_create(const aderdg_solve_spec_t *specs, int count, const aderdg_config_t *cfg,
                         aderdg_batch_t **out);
 int aderdg_batch_destroy(aderdg_batch_t *b);
@@ -291,6 +307,7 @@ typedef struct {
     void *cuda_stream;           /* NULL: a stream of the server's own */
     int pred_shape, corr_shape;  /* tile shapes, as in aderdg_config_t */
     const char *tune_cache;      /* as in aderdg_config_t */
+    int initial_guess;           /* ADERDG_GUESS_*, Picard count by the default rule */
 } aderdg_server_config_t;
 
 typedef struct {

@@ -53,6 +53,7 @@ class Cfg(C.Structure):
         ("prm", C.c_double * 8),
         ("picard", C.c_int),
         ("alpha", C.c_double),
+        ("guess", C.c_int),
     ]
 
 
@@ -87,6 +88,7 @@ def lib():
             L.orc_max_eigs.argtypes = [cp, dp, dp]
             L.orc_max_eigs.restype = None
             L.orc_predictor.argtypes = [cp, dp, C.c_double, dp, dp, dp, C.POINTER(C.c_int)]
+            L.orc_initial_guess.argtypes = [cp, dp, C.c_double, dp]
             L.orc_volume.argtypes = [cp, dp, dp]
             L.orc_traces.argtypes = [cp, dp, dp, dp, dp]
             L.orc_rusanov.argtypes = [cp, C.c_int, dp, dp, dp, dp, dp]
@@ -117,7 +119,10 @@ def nvar(pde: int, dim: int) -> int:
     return lib().orc_nvar(pde, dim)
 
 
-def make_cfg(dim, cells, lo, hi, N, pde, prm=(), picard=0, alpha=0.0) -> Cfg:
+GUESS_TRIVIAL, GUESS_ORDER2, GUESS_ORDER3 = 0, 1, 2
+
+
+def make_cfg(dim, cells, lo, hi, N, pde, prm=(), picard=0, alpha=0.0, guess=GUESS_TRIVIAL) -> Cfg:
     c = Cfg()
     c.dim = dim
     for d in range(3):
@@ -131,6 +136,7 @@ def make_cfg(dim, cells, lo, hi, N, pde, prm=(), picard=0, alpha=0.0) -> Cfg:
         c.prm[i] = float(v)
     c.picard = picard
     c.alpha = alpha
+    c.guess = guess
     return c
 
 
@@ -199,6 +205,18 @@ def predictor(cfg: Cfg, u: np.ndarray, dt: float):
     if rc:
         raise RuntimeError("orc_predictor failed: %d" % rc)
     return qhat, qbar, Fbar, it.value
+
+
+def initial_guess(cfg: Cfg, u: np.ndarray, dt: float) -> np.ndarray:
+    """One element: the initial guess q0[n, n^d, m] of cfg.guess (Sec. 2.2)."""
+    n = cfg.N + 1
+    ns = n ** cfg.dim
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    assert u.size == ns * cfg.m
+    q0 = np.zeros((n, ns, cfg.m))
+    if lib().orc_initial_guess(C.byref(cfg), _p(u), float(dt), _p(q0)):
+        raise RuntimeError("orc_initial_guess failed")
+    return q0
 
 
 def volume(cfg: Cfg, Fbar: np.ndarray) -> np.ndarray:

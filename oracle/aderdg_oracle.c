@@ -62,8 +62,12 @@ typedef struct {
     int m;            /* number of variables */
     int pde;          /* 1 advection, 2 Euler, 3 elasticity */
     double prm[8];    /* advection: a_x a_y a_z; Euler: gamma; elasticity: rho lambda mu */
-    int picard;       /* > 0 fixed count, 0 -> N+1, < 0 -> to convergence */
+    int picard;       /* > 0 fixed count, 0 -> default (see orc_picard_count),
+                         < 0 -> to convergence */
     double alpha;     /* CFL coefficient; 0 -> default table (see orc_alpha) */
+    int guess;        /* initial guess of the Picard iteration (Sec. 2.2):
+                         0 trivial q = u(t^n); 1 second order u + tau L(u);
+                         2 third order u + tau k1 + tau^2 (k2 - k1) / (2 dt) */
 } orc_cfg;
 
 /* ------------------------------------------------------------------------ */
@@ -324,7 +328,18 @@ static int make_basis(int N, basis *b)
     return lu_factor(b->n, b->K1lu, b->piv);
 }
 
-int orc_picard_count(const orc_cfg *c) { return c->picard == 0 ? c->N + 1 : c->picard; }
+/* Default Picard count: N+1 from the trivial guess (reading R3); an
+ * initial guess of degree k in time (k = 1, 2 for guesses 1, 2) is already
+ * of order k+1, so one iteration fewer per degree: N+1-k, at least 1.  The
+ * paper's sufficiency rule (a degree N-1 guess needs one iteration, Sec.
+ * 2.2) corresponds to N-k; the default keeps the one extra iteration the
+ * trivial guess has. */
+int orc_picard_count(const orc_cfg *c)
+{
+    if (c->picard != 0) return c->picard;
+    int P = c->N + 1 - (c->guess == 1 ? 1 : c->guess == 2 ? 2 : 0);
+    return P < 1 ? 1 : P;
+}
 
 /* Default CFL coefficient alpha(N) = 0.9 x the von Neumann stability limit
  * of this scheme for 1D linear advection (the paper's bound alpha < 1/(2N+1)
@@ -353,6 +368,58 @@ double orc_alpha(const orc_cfg *c)
  *
  * Outputs (any may be NULL): qhat[t][s][v] (n^{d+1} m), qbar[s][v] (n^d m),
  * Fbar[d][s][v] (dim n^d m).  Returns the number of iterations done. */
+/* L(w) = -sum_d (1/dx_d) Dhat_d F_d(w) at the spatial nodes of one element:
+ * the element-local approximation of the time derivative of Sec. 2.2 (the
+ * L operator with S = 0 and B = 0), with the same nodal derivative as the
+ * predictor (reading R2).  tmp holds dim ns m values. */
+static void l_operator(const orc_cfg *c, const basis *b, const double *w, double *Lw, double *tmp)
+{
+    const int n = b->n, dim = c->dim, m = c->m, ns = ipow(n, dim);
+    for (int d = 0; d < dim; ++d)
+        for (int s = 0; s < ns; ++s) orc_flux(c, &w[(size_t)s * m], d, &tmp[((size_t)d * ns + s) * m]);
+    for (int s = 0; s < ns; ++s)
+        for (int v = 0; v < m; ++v) {
+            double r = 0.0;
+            for (int d = 0; d < dim; ++d) {
+                int sd = digit(s, n, d);
+                double acc = 0.0;
+                for (int j = 0; j < n; ++j)
+                    acc += b->Dhat[sd * n + j] * tmp[((size_t)d * ns + with_digit(s, n, d, j)) * m + v];
+                r -= acc / cell_dx(c, d);
+            }
+            Lw[(size_t)s * m + v] = r;
+        }
+}
+
+/* Initial guess q0 at the space-time nodes (t^n + tau_t, x_s),
+ * tau_t = xi_t dt (Sec. 2.2, written as a Taylor series in time):
+ *   0: q0 = u (the trivial guess)
+ *   1: q0 = u + tau L(u)                                  (second order)
+ *   2: q0 = u + tau k1 + tau^2 (k2 - k1) / (2 dt),
+ *      k1 = L(u), k2 = L(u + dt k1)                       (third order)
+ * gw holds (3 + dim) ns m values. */
+static void initial_guess(const orc_cfg *c, const basis *b, const double *u, double dt, double *q,
+                          double *gw)
+{
+    const int n = b->n, ns = ipow(n, c->dim), m = c->m;
+    const size_t nsm = (size_t)ns * m;
+    double *k1 = gw, *k2 = gw + nsm, *w = gw + 2 * nsm, *tmp = gw + 3 * nsm;
+    if (c->guess == 1 || c->guess == 2) l_operator(c, b, u, k1, tmp);
+    if (c->guess == 2) {
+        for (size_t i = 0; i < nsm; ++i) w[i] = u[i] + dt * k1[i];
+        l_operator(c, b, w, k2, tmp);
+    }
+    for (int t = 0; t < n; ++t) {
+        const double tau = b->x[t] * dt;
+        for (size_t i = 0; i < nsm; ++i) {
+            double v = u[i];
+            if (c->guess == 1 || c->guess == 2) v += tau * k1[i];
+            if (c->guess == 2) v += 0.5 * tau * tau * (k2[i] - k1[i]) / dt;
+            q[(size_t)t * nsm + i] = v;
+        }
+    }
+}
+
 static int predictor_elem(const orc_cfg *c, const basis *b, const double *u, double dt,
                           double *qhat, double *qbar, double *Fbar, double *work)
 {
@@ -365,9 +432,7 @@ static int predictor_elem(const orc_cfg *c, const basis *b, const double *u, dou
     double dx[3];
     for (int d = 0; d < dim; ++d) dx[d] = cell_dx(c, d);
 
-    for (int t = 0; t < n; ++t)
-        for (int s = 0; s < ns; ++s)
-            for (int v = 0; v < m; ++v) q[((size_t)t * ns + s) * m + v] = u[(size_t)s * m + v];
+    initial_guess(c, b, u, dt, q, work + (size_t)nst * m * (3 + dim));
 
     int P = orc_picard_count(c);
     int to_conv = P < 0;
@@ -437,8 +502,8 @@ static int predictor_elem(const orc_cfg *c, const basis *b, const double *u, dou
 static size_t predictor_work_len(const orc_cfg *c)
 {
     int n = c->N + 1;
-    size_t nst = (size_t)ipow(n, c->dim + 1);
-    return nst * c->m * (3 + c->dim);
+    size_t nst = (size_t)ipow(n, c->dim + 1), ns = (size_t)ipow(n, c->dim);
+    return nst * c->m * (3 + c->dim) + ns * c->m * (3 + c->dim);
 }
 
 /* Volume integral of the corrector (third integral of eq. pde.nc.gw2) divided
@@ -512,6 +577,18 @@ int orc_predictor(const orc_cfg *c, const double *u, double dt, double *qhat,
     int it = predictor_elem(c, &b, u, dt, qhat, qbar, Fbar, work);
     free(work);
     if (iters) *iters = it;
+    return 0;
+}
+
+/* The initial guess alone (no Picard iteration) for one element. */
+int orc_initial_guess(const orc_cfg *c, const double *u, double dt, double *q0)
+{
+    basis b;
+    if (make_basis(c->N, &b)) return -1;
+    double *gw = malloc(sizeof(double) * (size_t)ipow(c->N + 1, c->dim) * c->m * (3 + c->dim));
+    if (!gw) return -2;
+    initial_guess(c, &b, u, dt, q0, gw);
+    free(gw);
     return 0;
 }
 

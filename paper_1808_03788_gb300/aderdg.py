@@ -33,6 +33,7 @@ ADERDG_HOST, ADERDG_DEVICE = 0, 1
 ADERDG_NUM_SHAPES = 3
 ADERDG_SHAPE_DEFAULT, ADERDG_SHAPE_AUTOTUNE = 0, -1
 ADERDG_TUNE_FORCE = 1
+ADERDG_GUESS_TRIVIAL, ADERDG_GUESS_ORDER2, ADERDG_GUESS_ORDER3 = 0, 1, 2
 
 
 class AderdgError(RuntimeError):
@@ -60,7 +61,8 @@ class aderdg_alloc_t(C.Structure):
 class aderdg_config_t(C.Structure):
     _fields_ = [("precision", C.c_int), ("picard_iters", C.c_int), ("cfl_alpha", C.c_double),
                 ("cuda_stream", C.c_void_p), ("alloc", C.POINTER(aderdg_alloc_t)),
-                ("pred_shape", C.c_int), ("corr_shape", C.c_int), ("tune_cache", C.c_char_p)]
+                ("pred_shape", C.c_int), ("corr_shape", C.c_int), ("tune_cache", C.c_char_p),
+                ("initial_guess", C.c_int)]
 
 
 class aderdg_info_t(C.Structure):
@@ -70,7 +72,8 @@ class aderdg_info_t(C.Structure):
                 ("flops_corrector", C.c_double), ("bytes_predictor", C.c_double),
                 ("bytes_corrector", C.c_double), ("device_bytes", C.c_size_t),
                 ("pred_shape", C.c_int), ("pred_threads", C.c_int), ("pred_epb", C.c_int),
-                ("corr_shape", C.c_int), ("corr_threads", C.c_int), ("corr_epb", C.c_int)]
+                ("corr_shape", C.c_int), ("corr_threads", C.c_int), ("corr_epb", C.c_int),
+                ("initial_guess", C.c_int)]
 
 
 class aderdg_solve_spec_t(C.Structure):
@@ -80,7 +83,7 @@ class aderdg_solve_spec_t(C.Structure):
 class aderdg_server_config_t(C.Structure):
     _fields_ = [("device_budget_bytes", C.c_size_t), ("max_queue", C.c_int), ("steps_per_round", C.c_int),
                 ("precision", C.c_int), ("cuda_stream", C.c_void_p), ("pred_shape", C.c_int),
-                ("corr_shape", C.c_int), ("tune_cache", C.c_char_p)]
+                ("corr_shape", C.c_int), ("tune_cache", C.c_char_p), ("initial_guess", C.c_int)]
 
 
 class aderdg_request_t(C.Structure):
@@ -239,7 +242,8 @@ class Solver:
 
     def __init__(self, pde: int, dim: int, cells, lo, hi, N: int, params=(),
                  precision: int = ADERDG_FP64, picard: int = 0, alpha: float = 0.0,
-                 stream=None, torch_alloc: bool = True, shapes=(0, 0), tune_cache=None):
+                 stream=None, torch_alloc: bool = True, shapes=(0, 0), tune_cache=None,
+                 guess: int = ADERDG_GUESS_TRIVIAL):
         L = load()
         self.dim, self.N, self.pde = dim, N, pde
         self.m = nvar(pde, dim)
@@ -261,6 +265,7 @@ class Solver:
         cfg.precision = precision
         cfg.picard_iters = picard
         cfg.cfl_alpha = alpha
+        cfg.initial_guess = guess
         _set_shapes(cfg, shapes, tune_cache)
         self._alloc = None
         if stream is not None:
@@ -520,7 +525,8 @@ class Batch:
     """Many independent solves advanced together (aderdg_batch_*)."""
 
     def __init__(self, specs, precision: int = ADERDG_FP64, picard: int = 0, alpha: float = 0.0,
-                 stream=None, torch_alloc: bool = True, shapes=(0, 0), tune_cache=None):
+                 stream=None, torch_alloc: bool = True, shapes=(0, 0), tune_cache=None,
+                 guess: int = ADERDG_GUESS_TRIVIAL):
         L = load()
         self._L = L
         self.specs = list(specs)
@@ -529,6 +535,7 @@ class Batch:
         cfg.precision = precision
         cfg.picard_iters = picard
         cfg.cfl_alpha = alpha
+        cfg.initial_guess = guess
         _set_shapes(cfg, shapes, tune_cache)
         if stream is not None:
             cfg.cuda_stream = C.c_void_p(int(stream))
@@ -600,7 +607,8 @@ class Server:
     """Continuous-batching request server (aderdg_server_*)."""
 
     def __init__(self, precision: int = ADERDG_FP64, budget_bytes: int = 0, max_queue: int = 0,
-                 steps_per_round: int = 0, shapes=(0, 0), tune_cache=None):
+                 steps_per_round: int = 0, shapes=(0, 0), tune_cache=None,
+                 guess: int = ADERDG_GUESS_TRIVIAL):
         L = load()
         self._L = L
         cfg = aderdg_server_config_t()
@@ -608,6 +616,7 @@ class Server:
         cfg.max_queue = max_queue
         cfg.steps_per_round = steps_per_round
         cfg.precision = precision
+        cfg.initial_guess = guess
         _set_shapes(cfg, shapes, tune_cache)
         self._cache = cfg.tune_cache  # keeps the bytes alive while the server runs
         self._h = _H()

@@ -75,6 +75,7 @@ int build_basis(int N, Basis &b)
     b.n = n;
     double x[NMAX], bw[NMAX];
     if (gauss_legendre01(n, x, b.w)) return -1;
+    for (int k = 0; k < n; ++k) b.x[k] = x[k];
     // barycentric weights bw_k = 1 / prod_{j != k} (x_k - x_j)
     for (int k = 0; k < n; ++k) {
         double prod = 1.0;
@@ -155,6 +156,8 @@ void fill_typed(const Basis &b, Ops<T> &o)
         o.F0[t] = T(b.F0[t]);
         o.F1[t] = T(b.F1[t]);
         o.inv_w[t] = T(b.inv_w[t]);
+        o.xi[t] = T(b.x[t]);
+        o.hxi2[t] = T(0.5 * b.x[t] * b.x[t]);
     }
 }
 }  // namespace
@@ -174,6 +177,12 @@ double default_alpha(int N)
                                  0.0451, 0.0339, 0.0265, 0.0212, 0.0174};
     if (N >= 0 && N <= 9) return a[N];
     return 0.5 / (2.0 * N + 1.0);
+}
+
+int default_picard(int N, int guess)
+{
+    const int k = guess == 1 ? 1 : (guess == 2 ? 2 : 0);
+    return N + 1 - k < 1 ? 1 : N + 1 - k;
 }
 
 }  // namespace aderdg

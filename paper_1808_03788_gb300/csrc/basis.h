@@ -6,6 +6,9 @@ namespace aderdg {
 int gauss_legendre01(int n, double *x, double *w);
 int build_basis(int N, Basis &b);
 double default_alpha(int N);
+// Picard iterations after an initial guess (0 trivial, 1 second order, 2
+// third order): max(1, N + 1 - degree of the guess in time)
+int default_picard(int N, int guess);
 // fill kp.od / kp.of from kp.b
 void fill_ops(KParams &kp);
 }  // namespace aderdg

@@ -92,7 +92,7 @@ struct Mem {
 };
 
 struct Slot {
-    int pde = 0, dim = 0, N = 0, M = 0, NS = 0, NF = 0, NREC = 0, picard = 0;
+    int pde = 0, dim = 0, N = 0, M = 0, NS = 0, NF = 0, NREC = 0, picard = 0, guess = 0;
     long long E = 0;
     int cells[3] = {1, 1, 1};
     double inv_dx[3] = {1, 1, 1}, vol = 1;
@@ -116,7 +116,7 @@ size_t slot_bytes(const Slot &s)
            a256((size_t)s.E * s.ks->rf * 8);
 }
 
-int make_slot(const aderdg_solve_spec_t &sp, int prec, int picard, double alpha, Slot &s)
+int make_slot(const aderdg_solve_spec_t &sp, int prec, int guess, int picard, double alpha, Slot &s)
 {
     const aderdg_mesh_t &m = sp.mesh;
     if (m.dim < 2 || m.dim > 3) return fail(ADERDG_E_INVAL, "dim must be 2 or 3");
@@ -125,6 +125,7 @@ int make_slot(const aderdg_solve_spec_t &sp, int prec, int picard, double alpha,
     const KernelSet *ks = kernels_for(sp.pde.kind, m.dim, sp.N, prec);
     if (!ks) return fail(ADERDG_E_UNSUPPORTED, "no kernels compiled for this (pde, dim, N)");
     if (sp.pde.kind == ADERDG_PDE_EULER && !(sp.pde.p[0] > 1.0)) return fail(ADERDG_E_INVAL, "gamma must be > 1");
+    if (guess < ADERDG_GUESS_TRIVIAL || guess > ADERDG_GUESS_ORDER3) return fail(ADERDG_E_INVAL, "bad initial guess");
     s = Slot();
     s.pde = sp.pde.kind;
     s.dim = m.dim;
@@ -133,7 +134,8 @@ int make_slot(const aderdg_solve_spec_t &sp, int prec, int picard, double alpha,
     s.NS = ipow(sp.N + 1, m.dim);
     s.NF = ipow(sp.N + 1, m.dim - 1);
     s.NREC = m.dim * 2 * s.NF;
-    s.picard = picard > 0 ? picard : sp.N + 1;
+    s.guess = guess;
+    s.picard = picard > 0 ? picard : default_picard(sp.N, guess);
     s.alpha = alpha > 0 ? alpha : default_alpha(sp.N);
     s.ks = ks;
     s.E = 1;
@@ -322,6 +324,7 @@ public:
                 for (int k = 0; k < 3; ++k) { d.cells[k] = s->cells[k]; d.inv_dx[k] = s->inv_dx[k]; }
                 fill_desc_spacing(d);
                 d.picard = s->picard;
+                d.guess = s->guess;
                 d.u = s->u;
                 d.u_out = s->u;
                 d.V = s->V;
@@ -484,7 +487,8 @@ int aderdg_batch_create(const aderdg_solve_spec_t *specs, int count, const aderd
         return fail(ADERDG_E_INVAL, "bad tile shape request");
     std::vector<Slot> tmp(count);
     for (int i = 0; i < count; ++i) {
-        int rc = make_slot(specs[i], prec, cfg ? cfg->picard_iters : 0, cfg ? cfg->cfl_alpha : 0.0, tmp[i]);
+        int rc = make_slot(specs[i], prec, cfg ? cfg->initial_guess : 0, cfg ? cfg->picard_iters : 0,
+                           cfg ? cfg->cfl_alpha : 0.0, tmp[i]);
         if (rc) return rc;
     }
     int ndev = 0;
@@ -659,6 +663,7 @@ struct aderdg_server_s {
     int max_queue = 100000;
     int steps_per_round = 8;
     int prec = ADERDG_FP64;
+    int guess = ADERDG_GUESS_TRIVIAL;
     std::mutex mu;
     std::condition_variable cv;
     std::deque<Request *> queue;                         // submitted, not admitted
@@ -796,6 +801,11 @@ int aderdg_server_create(const aderdg_server_config_t *cfg, aderdg_server_t **ou
         delete s;
         return fail(ADERDG_E_INVAL, "bad tile shape request");
     }
+    s->guess = cfg ? cfg->initial_guess : ADERDG_GUESS_TRIVIAL;
+    if (s->guess < ADERDG_GUESS_TRIVIAL || s->guess > ADERDG_GUESS_ORDER3) {
+        delete s;
+        return fail(ADERDG_E_INVAL, "bad initial guess");
+    }
     if (cfg && cfg->max_queue > 0) s->max_queue = cfg->max_queue;
     if (cfg && cfg->steps_per_round > 0) s->steps_per_round = cfg->steps_per_round;
     size_t free_b = 0, total_b = 0;
@@ -849,7 +859,7 @@ int aderdg_submit(aderdg_server_t *s, const aderdg_request_t *req, uint64_t *tic
     if (!s || !req || !ticket || !req->u0) return fail(ADERDG_E_INVAL, "NULL argument");
     if (!(req->t_end > 0) || !std::isfinite(req->t_end)) return fail(ADERDG_E_INVAL, "t_end must be positive");
     Request *r = new Request();
-    int rc = make_slot(req->spec, s->prec, 0, 0.0, r->spec);
+    int rc = make_slot(req->spec, s->prec, s->guess, 0, 0.0, r->spec);
     if (rc) { delete r; return rc; }
     if (r->spec.bytes > s->budget) {
         delete r;

@@ -20,6 +20,7 @@ constexpr int NMAX = 8;  // largest n = N+1 compiled
 
 struct Basis {
     int n;
+    double x[NMAX];            // Gauss-Legendre nodes on [0, 1]
     double w[NMAX], F0[NMAX], F1[NMAX], inv_w[NMAX];
     double D[NMAX * NMAX];     // Dhat, row-major [j][k]
     double Kw[NMAX * NMAX];    // [k][j]
@@ -62,6 +63,8 @@ struct Ops {
     T iK1W[NMAX * NMAX];   // K1^{-1} W               [t][t']
     T c1[NMAX];            // row sums of iK1W (time integral of a constant)
     T w[NMAX], F0[NMAX], F1[NMAX], inv_w[NMAX];
+    T xi[NMAX];            // time nodes on [0, 1] (initial guesses)
+    T hxi2[NMAX];          // xi^2 / 2
 };
 
 // One solve of a launch (device memory).  Tiles of EPB consecutive
@@ -72,7 +75,8 @@ struct SolveDesc {
     long long E;
     long long tile0_p, tile0_c;
     int cells[3];
-    int picard;
+    int picard;        // Picard iterations after the initial guess
+    int guess;         // initial guess: 0 trivial, 1 second order, 2 third order (Sec. 2.2)
     double inv_dx[3];
     float inv_dx_f[3]; // 1/dx_d and dx_0/dx_d in FP32 (precomputed on the host)
     float ratio_f[3];
@@ -80,8 +84,7 @@ struct SolveDesc {
     double *u_out;     // state u^{n+1} (may alias u)
     void *V;           // volume term          [E][NS][M] of T
     void *tr;          // trace records        [E][DIM][2][NF][RS] of T
-    double *ref;       // FP32 path: reference state and flux per element
-                       // [E][M + DIM M] (q_ref, F_d(q_ref)); unused in FP64
+    double *ref;       // FP32 path: reference state per element [E][M]; unused in FP64
     Control *ctl;
 };
 

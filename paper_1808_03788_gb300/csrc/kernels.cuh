@@ -153,9 +153,12 @@ __device__ __forceinline__ float narrow<float>(double x) { return dbl_to_flt_rn(
 //      with compile-time indices)
 //   3. back on the time pencil: R = sum_d (1/dx_d) (-Dhat F_d),
 //      q[t] = u + dt sum_t' iK1W[t][t'] R[t']
-// The first iteration starts from q = u, constant in time, so its flux and
-// derivatives are taken once per spatial node and q[t] = u + dt c1[t] R with
-// c1 the row sums of iK1W (the general iteration applied to a time-constant q).
+// Initial guesses (Sec. 2.2) need the flux of time-constant states only: one
+// flux per spatial node and the t = 0 pencils.  From the trivial guess
+// q = u the first iteration is taken that way, q[t] = u + dt c1[t] R with c1
+// the row sums of iK1W (the general iteration applied to a time-constant
+// q); the second- and third-order guesses are Taylor polynomials in
+// tau = xi dt built from R(u) and R(u + dt L(u)).
 template <class PDE, int DIM, int N, typename T, int TS = 0>
 struct PredCfg {
     using G = Geom<PDE, DIM, N>;
@@ -313,11 +316,12 @@ k_predictor(const KParams P)
             else PDE::flux(P.pde, qq, FF);
         };
 
-        T q[n][M];
-        // ---- iteration 1 from the time-constant guess ----------------------
-        {
+        // R(w) = dx_0 L(w) at this thread's spatial node, L(w) = -sum_d
+        // (1/dx_d) Dhat_d F_d(w): flux of the time-constant w, t = 0 pencils
+        // only (ebuf's t = 0 slice; free again when this returns)
+        auto spatial_R = [&](const T *w, T *R) {
             T F[DIM][M];
-            flx(u, F);
+            flx(w, F);
             if (act) {
 #pragma unroll
                 for (int d = 0; d < DIM; ++d) NodeIO<T, M>::store(ebuf + (d * NST + s) * M, F[d]);
@@ -325,17 +329,48 @@ k_predictor(const KParams P)
             __syncthreads();
             if (act && s < NF) contract_all<C, T>(ebuf, 0, s, O);
             __syncthreads();
-            T R[M];
             gather_R<C, T>(ebuf, 0, s, ratio, R);
-            const T dtT = sDt[0];
-#pragma unroll
-            for (int t = 0; t < n; ++t)
-#pragma unroll
-                for (int v = 0; v < M; ++v) q[t][v] = u[v] + dtT * (O.c1[t] * R[v]);
             __syncthreads();
+        };
+
+        T q[n][M];
+        int it0;  // Picard iterations already taken
+        {
+            T R1[M];
+            spatial_R(u, R1);
+            const T dtT = sDt[0];
+            if (S.guess == 2) {
+                // third-order guess (Sec. 2.2): q = u + tau k1 + tau^2 (k2 - k1) / (2 dt),
+                // tau = xi dt, k1 = L(u), k2 = L(u + dt k1)
+                T w[M], R2[M];
+#pragma unroll
+                for (int v = 0; v < M; ++v) w[v] = u[v] + dtT * R1[v];
+                spatial_R(w, R2);
+#pragma unroll
+                for (int t = 0; t < n; ++t)
+#pragma unroll
+                    for (int v = 0; v < M; ++v)
+                        q[t][v] = u[v] + dtT * (O.xi[t] * R1[v] + O.hxi2[t] * (R2[v] - R1[v]));
+                it0 = 0;
+            } else if (S.guess == 1) {
+                // second-order guess: q = u + tau L(u)
+#pragma unroll
+                for (int t = 0; t < n; ++t)
+#pragma unroll
+                    for (int v = 0; v < M; ++v) q[t][v] = u[v] + dtT * (O.xi[t] * R1[v]);
+                it0 = 0;
+            } else {
+                // trivial guess q = u: its first Picard iteration, taken on
+                // the time-constant q (one flux per spatial node)
+#pragma unroll
+                for (int t = 0; t < n; ++t)
+#pragma unroll
+                    for (int v = 0; v < M; ++v) q[t][v] = u[v] + dtT * (O.c1[t] * R1[v]);
+                it0 = 1;
+            }
         }
-        // ---- remaining Picard iterations of eq. pde.st2 --------------------
-        for (int it = 1; it < S.picard; ++it) {
+        // ---- Picard iterations of eq. pde.st2 ------------------------------
+        for (int it = it0; it < S.picard; ++it) {
 #pragma unroll
             for (int t = 0; t < n; ++t) {
                 T F[DIM][M];

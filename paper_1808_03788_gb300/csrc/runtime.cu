@@ -146,7 +146,7 @@ void set_last_error(const char *msg) { g_err = msg; }
 // ---------------------------------------------------------------------------
 
 struct aderdg_s {
-    int dim = 0, N = 0, n = 0, M = 0, pde = 0, precision = 0, picard = 0;
+    int dim = 0, N = 0, n = 0, M = 0, pde = 0, precision = 0, picard = 0, guess = 0;
     long long E = 0;
     int NS = 0, NF = 0, NREC = 0;
     double dx[3] = {1, 1, 1};
@@ -259,9 +259,11 @@ int set_t_end(aderdg_t *h, double t_end)
 }
 
 // Algorithmic counts of the kernels as formulated (FMA = 2 flops; a
-// reciprocal or square root = 1): first Picard iteration on the
-// time-constant guess, P-1 full iterations, time averages, volume term,
-// traces; corrector Rusanov + lift + update + wave speeds.
+// reciprocal or square root = 1): the initial guess (trivial: the first
+// Picard iteration on the time-constant guess, then P-1 full iterations;
+// second / third order: one / two time-constant L evaluations, then P full
+// iterations), time averages, volume term, traces; corrector Rusanov +
+// lift + update + wave speeds.
 void fill_cost(const aderdg_t *h, aderdg_info_t *info)
 {
     const double n = h->n, M = h->M, NS = h->NS, NST = h->NS * h->n, NF = h->NF, NREC = h->NREC, D = h->dim;
@@ -269,7 +271,11 @@ void fill_cost(const aderdg_t *h, aderdg_info_t *info)
     const double it1 = NS * FF + D * NF * M * 2 * n * n + NS * M * (D - 1) + n * NS * M * 3;
     const double itk = NST * FF + D * NS * M * 2 * n * n + NST * M * (D - 1) + NS * M * n * (2 * n + 2);
     const double fin = NST * FF + (1 + D) * NST * M * 2 + NS * M * D * 2 * n + NREC * M * 4 * n + NREC * EF;
-    const double pred = it1 + (P - 1) * itk + fin;
+    double pred;
+    if (h->guess == 2) pred = 2 * it1 + 2 * NS * M + P * itk + fin;  // it1 counts 3 flops per q value, the
+                                                                     // Taylor form 6 over two evaluations
+    else if (h->guess == 1) pred = it1 + P * itk + fin;
+    else pred = it1 + (P - 1) * itk + fin;
     const double corr = NREC * M * 6 + NREC + NS * M * (5 * D + 3) + NS * D * (EF + 1);
     info->flops_predictor = pred * h->E;
     info->flops_corrector = corr * h->E;
@@ -339,7 +345,12 @@ int aderdg_create(const aderdg_mesh_t *mesh, int N, int nVar, const aderdg_pde_t
     h->M = m;
     h->pde = pde->kind;
     h->precision = prec;
-    h->picard = (cfg && cfg->picard_iters > 0) ? cfg->picard_iters : N + 1;
+    h->guess = cfg ? cfg->initial_guess : ADERDG_GUESS_TRIVIAL;
+    if (h->guess < ADERDG_GUESS_TRIVIAL || h->guess > ADERDG_GUESS_ORDER3) {
+        delete h;
+        return fail(ADERDG_E_INVAL, "bad initial guess");
+    }
+    h->picard = (cfg && cfg->picard_iters > 0) ? cfg->picard_iters : default_picard(N, h->guess);
     h->alpha = (cfg && cfg->cfl_alpha > 0) ? cfg->cfl_alpha : default_alpha(N);
     h->E = E;
     h->NS = ipow(h->n, h->dim);
@@ -401,6 +412,7 @@ int aderdg_create(const aderdg_mesh_t *mesh, int N, int nVar, const aderdg_pde_t
     }
     fill_desc_spacing(sd);
     sd.picard = h->picard;
+    sd.guess = h->guess;
     sd.u = h->u;
     sd.u_out = h->u;
     sd.V = h->V;
@@ -461,6 +473,7 @@ int aderdg_get_info(const aderdg_t *h, aderdg_info_t *info)
     info->nvar = h->M;
     info->precision = h->precision;
     info->picard_iters = h->picard;
+    info->initial_guess = h->guess;
     info->elements = h->E;
     info->dofs = h->E * h->NS;
     info->cfl_alpha = h->alpha;

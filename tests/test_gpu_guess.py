@@ -1,0 +1,144 @@
+"""Parity of the CUDA path with the oracle for the second- and third-order
+initial guesses of the Picard iteration (Sec. 2.2), through the C ABI.
+Same tolerances as the trivial guess: one predictor call within 1e-12 of
+the data scale, full runs within 1e-11 relative L2 in FP64 and 1e-6 in the
+mixed path; batched solves equal the same solves alone bitwise."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1808_03788_gb300 import aderdg as A
+from paper_1808_03788_gb300 import inputs
+from helpers import l2_abs, l2_rel
+
+pytestmark = pytest.mark.gpu
+
+GAMMA = 1.4
+EL = (1.0, 2.0, 1.0)
+GUESSES = [A.ADERDG_GUESS_ORDER2, A.ADERDG_GUESS_ORDER3]
+
+# (pde, dim, N, cells, L, params)
+CASES = (
+    [(1, 2, N, (5, 3), 1.0, (0.7, -1.1)) for N in (1, 3, 6)]
+    + [(2, 2, N, (5, 3), 2.0, (GAMMA,)) for N in (1, 2, 3, 4, 5, 7)]
+    + [(2, 3, N, (3, 2, 2), 2.0, (GAMMA,)) for N in (2, 4)]
+    + [(3, 3, N, (3, 2, 2), 1.0, EL) for N in (1, 3)]
+)
+
+
+def _ids(c):
+    return "pde%d-%dd-N%d" % (c[0], c[1], c[2])
+
+
+def _pair(pde, dim, N, cells, L, params, guess, precision=A.ADERDG_FP64, picard=0):
+    cfg = oracle.make_cfg(dim, cells, [0.0] * dim, [L] * dim, N, pde, params, picard=picard, guess=guess)
+    s = A.Solver(pde, dim, cells, [0.0] * dim, [L] * dim, N, params, precision=precision, picard=picard,
+                 guess=guess)
+    return cfg, s
+
+
+def _state(cfg, pde, seed):
+    X = oracle.node_coords(cfg)
+    L = [cfg.hi[d] - cfg.lo[d] for d in range(cfg.dim)]
+    U = inputs.smooth_random_state(pde, X, L, seed=seed, amp=0.2)
+    if pde == 2:
+        return 0.5 * (U + inputs.random_state(pde, cfg.dim, *U.shape[:2], seed=seed + 1, amp=0.05))
+    return U + 0.1 * inputs.random_state(pde, cfg.dim, *U.shape[:2], seed=seed + 1)
+
+
+def _scale(a):
+    return max(1.0, float(np.abs(a).max()))
+
+
+@pytest.mark.parametrize("guess", GUESSES)
+@pytest.mark.parametrize("case", CASES, ids=_ids)
+def test_predictor_outputs_match_oracle(case, guess):
+    pde = case[0]
+    cfg, s = _pair(*case, guess=guess)
+    assert s.info()["picard_iters"] == oracle.lib().orc_picard_count(cfg)
+    assert s.info()["initial_guess"] == guess
+    U = _state(cfg, pde, seed=500 + case[2])
+    dt = oracle.cfl_dt(cfg, U)
+    _, Vo, qfo, ffo = oracle.step(cfg, U, dt, with_parts=True)
+    s.set_state(U)
+    s.predictor(dt)
+    V, qf, ff = s.predictor_outputs()
+    assert np.abs(V - Vo).max() <= 1e-12 * _scale(Vo)
+    assert np.abs(qf - qfo).max() <= 1e-12 * _scale(qfo)
+    assert np.abs(ff - ffo).max() <= 1e-12 * _scale(ffo)
+
+
+@pytest.mark.parametrize("picard", [0, 2])
+def test_full_run_euler_vortex_third_order_guess(picard):
+    """FP64 full run, default count (N-1) and the paper's minimum (N-2)."""
+    case = (2, 2, 4, (24, 20), 10.0, (GAMMA,))
+    cfg, s = _pair(*case, guess=A.ADERDG_GUESS_ORDER3, picard=picard)
+    U0 = inputs.euler_vortex(oracle.node_coords(cfg))
+    Uo, to, ko, _ = oracle.run(cfg, U0, t_end=0.4)
+    s.set_state(U0)
+    s.advance(0.4)
+    Ug, t, k = s.get_state()
+    assert (t, k) == (to, ko)
+    assert l2_rel(cfg, Ug, Uo) <= 1e-11
+
+
+def test_full_run_elasticity_third_order_guess():
+    case = (3, 3, 3, (5, 4, 4), 1.0, EL)
+    cfg, s = _pair(*case, guess=A.ADERDG_GUESS_ORDER3, picard=1)
+    U0 = inputs.elastic_pulse(oracle.node_coords(cfg))
+    Uo, to, ko, _ = oracle.run(cfg, U0, t_end=0.05)
+    s.set_state(U0)
+    s.advance(0.05)
+    Ug, t, k = s.get_state()
+    assert (t, k) == (to, ko)
+    assert l2_rel(cfg, Ug, Uo) <= 1e-11
+
+
+def test_mixed_full_run_third_order_guess():
+    case = (2, 2, 4, (24, 20), 10.0, (GAMMA,))
+    cfg, s = _pair(*case, guess=A.ADERDG_GUESS_ORDER3, picard=2, precision=A.ADERDG_MIXED_FP32)
+    U0 = inputs.euler_vortex(oracle.node_coords(cfg))
+    Uo, to, ko, _ = oracle.run(cfg, U0, t_end=0.4)
+    s.set_state(U0)
+    s.advance(0.4)
+    Ug, t, k = s.get_state()
+    assert t == to and abs(k - ko) <= 1
+    assert l2_rel(cfg, Ug, Uo) <= 1e-6
+
+
+def test_third_order_guess_same_error_as_trivial_guess():
+    """At the vortex's resolution the third-order guess with N-2 iterations
+    has the L2 error of the trivial guess with N+1 against the exact
+    solution (both FP64, GPU)."""
+    N, cells = 4, (40, 40)
+    errs = []
+    for guess, picard in ((A.ADERDG_GUESS_TRIVIAL, 0), (A.ADERDG_GUESS_ORDER3, N - 2)):
+        cfg, s = _pair(2, 2, N, cells, 10.0, (GAMMA,), guess=guess, picard=picard)
+        X = oracle.node_coords(cfg)
+        s.set_state(inputs.euler_vortex(X))
+        s.advance(0.5)
+        Ug, t, _ = s.get_state()
+        errs.append(l2_abs(cfg, Ug, inputs.euler_vortex(X, t=t)))
+    np.testing.assert_allclose(errs[1], errs[0], rtol=1e-6)
+
+
+def test_batch_with_guess_equals_alone():
+    mix = [(2, 2, (6, 5), (0, 0), (10, 10), 2, (GAMMA,)), (2, 2, (8, 8), (0, 0), (10, 10), 4, (GAMMA,)),
+           (3, 3, (3, 3, 2), (0, 0, 0), (1, 1, 1), 3, EL)]
+    t_end = [0.3, 0.2, 0.02]
+    ics = []
+    for c in mix:
+        X = oracle.node_coords(oracle.make_cfg(c[1], c[2], c[3], c[4], c[5], c[0], c[6]))
+        ics.append(inputs.euler_vortex(X) if c[0] == 2 else inputs.elastic_pulse(X, width=0.05))
+    for prec in (A.ADERDG_FP64, A.ADERDG_MIXED_FP32):
+        b = A.Batch([A.make_spec(*c) for c in mix], precision=prec, guess=A.ADERDG_GUESS_ORDER3)
+        for i, u in enumerate(ics):
+            b.set_state(i, u)
+        b.advance(t_end)
+        for i, c in enumerate(mix):
+            with A.Solver(*c, precision=prec, guess=A.ADERDG_GUESS_ORDER3) as s:
+                s.set_state(ics[i])
+                s.advance(t_end[i])
+                alone = s.get_state()[0]
+            np.testing.assert_array_equal(b.get_state(i)[0], alone.reshape(-1))
+        b.close()

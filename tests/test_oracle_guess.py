@@ -1,0 +1,144 @@
+"""Pins of the oracle's initial guesses of the Picard iteration (Sec. 2.2:
+the second-order guess u + tau L(u) and the third-order guess
+u + tau k1 + tau^2 (k2 - k1) / (2 dt), k1 = L(u), k2 = L(u + dt k1)).
+
+For linear advection u_t + a.grad u = 0 the exact solution is
+u0(x - a t), and L(u) = -a.grad u is exact on polynomial data, so each
+guess reproduces the exact space-time solution when it is a polynomial in
+t of the guess's degree, and misses it by exactly the next Taylor term
+otherwise.  A guess only moves the starting point: iterated to
+convergence, every guess reaches the same space-time solution."""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1808_03788_gb300 import inputs
+from helpers import euler_cfg, l2_abs, order
+
+
+def _poly(dim, degree, seed):
+    """Random polynomial of total degree <= degree: {exponents: coefficient}."""
+    rng = np.random.default_rng(seed)
+    return {k: rng.uniform(-1, 1) for k in itertools.product(range(degree + 1), repeat=dim) if sum(k) <= degree}
+
+
+def _eval(coef, X):
+    out = np.zeros(X.shape[0])
+    for k, c in coef.items():
+        term = np.full(X.shape[0], c)
+        for d, p in enumerate(k):
+            term = term * X[:, d] ** p
+        out += term
+    return out
+
+
+def _space_time(cfg, coef, a, dt):
+    """Exact q(x_s, t^n + tau_t) = u0(x_s - a tau_t) at the element-0 nodes."""
+    n = cfg.N + 1
+    X = oracle.node_coords(cfg)[0]
+    tau, _ = oracle.gauss_legendre(n)
+    return np.stack([_eval(coef, X - np.asarray(a)[None, :] * (t * dt)) for t in tau])[:, :, None], X, tau
+
+
+@pytest.mark.parametrize("dim,N", [(1, 3), (2, 2), (2, 4)])
+def test_second_order_guess_is_exact_for_linear_data(dim, N):
+    a = [1.7, -0.6][:dim]
+    cfg = oracle.make_cfg(dim, [4] * dim, [0.0] * dim, [1.0] * dim, N, oracle.PDE_ADVECTION, a,
+                          guess=oracle.GUESS_ORDER2)
+    coef = _poly(dim, 1, seed=dim + N)
+    dt = 0.03
+    ex, X, _ = _space_time(cfg, coef, a, dt)
+    q0 = oracle.initial_guess(cfg, _eval(coef, X)[:, None], dt)
+    np.testing.assert_allclose(q0, ex, rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("dim,N", [(1, 3), (2, 2), (2, 4), (3, 2)])
+def test_third_order_guess_is_exact_for_quadratic_data(dim, N):
+    a = [1.7, -0.6, 0.9][:dim]
+    cfg = oracle.make_cfg(dim, [4] * dim, [0.0] * dim, [1.0] * dim, N, oracle.PDE_ADVECTION, a,
+                          guess=oracle.GUESS_ORDER3)
+    coef = _poly(dim, 2, seed=10 * dim + N)
+    dt = 0.05
+    ex, X, _ = _space_time(cfg, coef, a, dt)
+    q0 = oracle.initial_guess(cfg, _eval(coef, X)[:, None], dt)
+    np.testing.assert_allclose(q0, ex, rtol=0, atol=1e-12)
+    # and the second-order guess is not (the data is quadratic)
+    cfg.guess = oracle.GUESS_ORDER2
+    assert np.abs(oracle.initial_guess(cfg, _eval(coef, X)[:, None], dt) - ex).max() > 1e-5
+
+
+def test_third_order_guess_misses_exactly_the_cubic_term():
+    """u0 = x^3: the exact solution (x - a tau)^3 minus the guess is
+    -a^3 tau^3; every lower Taylor term (coefficients 1, -3a x^2, 3 a^2 x)
+    is reproduced."""
+    a, N, dt = 1.3, 3, 0.07
+    cfg = oracle.make_cfg(1, [3], [0.0], [1.0], N, oracle.PDE_ADVECTION, [a], guess=oracle.GUESS_ORDER3)
+    coef = {(3,): 1.0}
+    ex, X, tau = _space_time(cfg, coef, [a], dt)
+    q0 = oracle.initial_guess(cfg, _eval(coef, X)[:, None], dt)
+    want = (a * tau * dt) ** 3
+    np.testing.assert_allclose((q0 - ex)[:, :, 0], np.broadcast_to(want[:, None], (N + 1, N + 1)),
+                               rtol=1e-11, atol=1e-14)
+
+
+@pytest.mark.parametrize("guess", [oracle.GUESS_TRIVIAL, oracle.GUESS_ORDER2, oracle.GUESS_ORDER3])
+def test_constant_state_guess_is_the_state(guess):
+    cfg = euler_cfg((3, 3), N=3)
+    cfg.guess = guess
+    q = inputs.random_state(oracle.PDE_EULER, 2, 1, 1, seed=4)[0, 0]
+    u = np.tile(q, (16, 1))
+    np.testing.assert_allclose(oracle.initial_guess(cfg, u, 0.02), np.broadcast_to(u, (4, 16, 4)), atol=1e-13)
+
+
+@pytest.mark.parametrize("guess", [oracle.GUESS_ORDER2, oracle.GUESS_ORDER3])
+def test_guess_only_moves_the_starting_point(guess):
+    """Iterated to convergence (nonlinear Euler), every guess reaches the
+    same space-time solution as the trivial guess."""
+    cfg = euler_cfg((5, 5), N=3, L=2.0, picard=-1)
+    X = oracle.node_coords(cfg)
+    U = inputs.smooth_random_state(oracle.PDE_EULER, X, [2.0, 2.0], seed=5)
+    dt = 0.5 * oracle.cfl_dt(cfg, U)
+    ref = oracle.predictor(cfg, U[7], dt)
+    cfg.guess = guess
+    got = oracle.predictor(cfg, U[7], dt)
+    np.testing.assert_allclose(got[0], ref[0], rtol=0, atol=1e-12)
+    # and it gets there in fewer iterations
+    assert got[3] < ref[3], (got[3], ref[3])
+
+
+def test_default_picard_counts():
+    for N in range(1, 8):
+        for guess, want in ((0, N + 1), (1, N), (2, max(1, N - 1))):
+            cfg = euler_cfg((2, 2), N=N)
+            cfg.guess = guess
+            assert oracle.lib().orc_picard_count(cfg) == want
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4])
+def test_third_order_guess_converged_for_linear_advection(N):
+    """For 1D linear advection the third-order guess followed by
+    max(1, N-2) Picard iterations is the converged predictor (the trivial
+    guess needs N), so whole steps agree to round-off."""
+    K = 5
+    rng = np.random.default_rng(N)
+    U = rng.standard_normal((K, N + 1, 1))
+    mk = lambda g, P: oracle.make_cfg(1, [K], [0.0], [1.0], N, oracle.PDE_ADVECTION, [1.0], picard=P, guess=g)
+    ref = oracle.step(mk(0, N + 1), U, 0.02)
+    got = oracle.step(mk(2, max(1, N - 2)), U, 0.02)
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("N", [3, 4])
+def test_third_order_guess_design_order(N):
+    """Euler density wave with the third-order guess and the paper's minimum
+    of N-2 Picard iterations keeps the design order N+1."""
+    errs = []
+    for c in (8, 16):
+        cfg = euler_cfg((c, c), N=N, L=1.0, picard=max(1, N - 2))
+        cfg.guess = oracle.GUESS_ORDER3
+        X = oracle.node_coords(cfg)
+        U1, t, _, _ = oracle.run(cfg, inputs.euler_density_wave(X, L=1.0), t_end=0.2)
+        errs.append(l2_abs(cfg, U1, inputs.euler_density_wave(X, L=1.0, t=t))[0])
+    assert order(*errs) > N + 1 - 0.5, errs
