@@ -179,6 +179,27 @@ double default_alpha(int N)
     return 0.5 / (2.0 * N + 1.0);
 }
 
+void fill_pde_consts(int kind, PdeParams &P)
+{
+    for (int i = 0; i < 8; ++i) P.c[i] = 0.0;
+    if (kind == 1) {  // advection
+        for (int d = 0; d < 3; ++d) {
+            P.c[d] = P.p[d];
+            P.c[3 + d] = std::fabs(P.p[d]);
+        }
+    } else if (kind == 2) {  // Euler
+        P.c[0] = P.p[0] - 1.0;
+        P.c[1] = P.p[0];
+    } else if (kind == 3) {  // elasticity
+        P.c[0] = 1.0 / P.p[0];
+        P.c[1] = P.p[1];
+        P.c[2] = P.p[2];
+        P.c[3] = P.p[1] + 2.0 * P.p[2];
+        P.c[4] = std::sqrt((P.p[1] + 2.0 * P.p[2]) / P.p[0]);
+    }
+    for (int i = 0; i < 8; ++i) P.cf[i] = (float)P.c[i];
+}
+
 int default_picard(int N, int guess)
 {
     const int k = guess == 1 ? 1 : (guess == 2 ? 2 : 0);

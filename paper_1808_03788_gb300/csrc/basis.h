@@ -9,6 +9,8 @@ double default_alpha(int N);
 // Picard iterations after an initial guess (0 trivial, 1 second order, 2
 // third order): max(1, N + 1 - degree of the guess in time)
 int default_picard(int N, int guess);
+// derived constants P.c / P.cf of PDE kind `kind` from P.p (see PdeParams)
+void fill_pde_consts(int kind, PdeParams &P);
 // fill kp.od / kp.of from kp.b
 void fill_ops(KParams &kp);
 }  // namespace aderdg

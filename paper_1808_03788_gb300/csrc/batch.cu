@@ -149,6 +149,7 @@ int make_slot(const aderdg_solve_spec_t &sp, int prec, int guess, int picard, do
     }
     if (s.E > (1LL << 31)) return fail(ADERDG_E_INVAL, "too many elements");
     for (int i = 0; i < 8; ++i) s.pp.p[i] = sp.pde.p[i];
+    fill_pde_consts(s.pde, s.pp);
     s.bytes = slot_bytes(s);
     return ADERDG_OK;
 }

@@ -48,9 +48,26 @@ struct Control {
     unsigned int pad1;
 };
 
+// PDE parameters as given (aderdg_pde_t) and constants derived from them
+// on the host (fill_pde_consts), in double and rounded to float, so that
+// the kernels do no per-call parameter arithmetic or double->float
+// conversion:
+//   advection   c[d] = a_d, c[3 + d] = |a_d|
+//   Euler       c[0] = gamma - 1, c[1] = gamma
+//   elasticity  c[0] = 1/rho, c[1] = lambda, c[2] = mu, c[3] = lambda + 2 mu,
+//               c[4] = c_p = sqrt((lambda + 2 mu) / rho)
 struct PdeParams {
     double p[8];
+    double c[8];
+    float cf[8];
 };
+
+template <typename T>
+__host__ __device__ __forceinline__ T pconst(const PdeParams &P, int i);
+template <>
+__host__ __device__ __forceinline__ double pconst<double>(const PdeParams &P, int i) { return P.c[i]; }
+template <>
+__host__ __device__ __forceinline__ float pconst<float>(const PdeParams &P, int i) { return P.cf[i]; }
 
 // Operators in the compute type (filled on the host by fill_ops).  Indexed
 // with compile-time constants inside unrolled loops, they are read straight
@@ -164,11 +181,11 @@ struct Advection {
     template <typename T>
     __device__ __forceinline__ static void flux(const PdeParams &P, const T *q, T (*f)[M]) {
 #pragma unroll
-        for (int d = 0; d < DIM; ++d) f[d][0] = T(P.p[d]) * q[0];
+        for (int d = 0; d < DIM; ++d) f[d][0] = pconst<T>(P, d) * q[0];
     }
     template <typename T>
     __device__ __forceinline__ static T max_eig(const PdeParams &P, const T *, int d) {
-        return fabs(T(P.p[d]));
+        return pconst<T>(P, 3 + d);
     }
 };
 
@@ -199,7 +216,7 @@ struct Euler {
             r.u0[k] = r.q[1 + k] * ir;
             kin2 += r.q[1 + k] * r.u0[k];
         }
-        const T p = T(P.p[0] - 1.0) * (r.q[DIM + 1] - T(0.5) * kin2);
+        const T p = pconst<T>(P, 0) * (r.q[DIM + 1] - T(0.5) * kin2);
         r.EP0 = r.q[DIM + 1] + p;
     }
     // F(q_ref + dq) - F(q_ref) from the perturbations:
@@ -209,7 +226,7 @@ struct Euler {
     //   dF_E = du_d (E + p) + u0_d (dE + dp).
     template <typename T>
     __device__ __forceinline__ static void flux_delta(const PdeParams &P, const Ref<T> &r, const T *dq, T (*f)[M]) {
-        const T gm1 = T(P.p[0] - 1.0);
+        const T gm1 = pconst<T>(P, 0);
         const T ir = recip(r.q[0] + dq[0]);
         T du[DIM], u[DIM];
         T dkin2 = T(0);
@@ -232,7 +249,7 @@ struct Euler {
     }
     template <typename T>
     __device__ __forceinline__ static void flux(const PdeParams &P, const T *q, T (*f)[M]) {
-        const T gm1 = T(P.p[0] - 1.0);
+        const T gm1 = pconst<T>(P, 0);
         const T ir = recip(q[0]);
         T v[DIM];
         T kin = T(0);
@@ -251,12 +268,12 @@ struct Euler {
     }
     template <typename T>
     __device__ __forceinline__ static T max_eig(const PdeParams &P, const T *q, int d) {
-        const T g = T(P.p[0]);
+        const T g = pconst<T>(P, 1);
         const T ir = recip(q[0]);
         T kin = T(0);
 #pragma unroll
         for (int k = 0; k < DIM; ++k) kin += q[1 + k] * q[1 + k];
-        const T p = (g - T(1)) * (q[DIM + 1] - T(0.5) * kin * ir);
+        const T p = pconst<T>(P, 0) * (q[DIM + 1] - T(0.5) * kin * ir);
         return fabs(q[1 + d] * ir) + sqrt(g * p * ir);
     }
 };
@@ -280,9 +297,9 @@ struct Elastic3 {
     }
     template <typename T>
     __device__ __forceinline__ static void flux(const PdeParams &P, const T *q, T (*f)[M]) {
-        const T irho = T(1.0 / P.p[0]);
-        const T lam = T(P.p[1]), mu = T(P.p[2]);
-        const T l2m = T(P.p[1] + 2.0 * P.p[2]);
+        const T irho = pconst<T>(P, 0);
+        const T lam = pconst<T>(P, 1), mu = pconst<T>(P, 2);
+        const T l2m = pconst<T>(P, 3);
         const T u = q[6], v = q[7], w = q[8];
         // x
         f[0][0] = -l2m * u; f[0][1] = -lam * u; f[0][2] = -lam * u;
@@ -299,7 +316,7 @@ struct Elastic3 {
     }
     template <typename T>
     __device__ __forceinline__ static T max_eig(const PdeParams &P, const T *, int) {
-        return T(sqrt((P.p[1] + 2.0 * P.p[2]) / P.p[0]));
+        return pconst<T>(P, 4);
     }
 };
 

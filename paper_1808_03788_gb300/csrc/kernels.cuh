@@ -223,6 +223,33 @@ __device__ __forceinline__ void contract_all(T *ebuf, int t, int p, const Ops<T>
     }
 }
 
+// -Dhat F_d on one variable v of the t = 0 pencil p along d, in place; item
+// = (d, p, v) with v fastest, so that the DIM NF M items of an element
+// spread over all its threads (the time-constant L evaluations of the
+// initial guesses touch t = 0 only).  The operator is the same for every
+// d (Ops::Dm[0]); the FMA order is contract_pencil's.
+template <class C, typename T>
+__device__ __forceinline__ void contract_item_t0(T *ebuf, int item, const T *Dm)
+{
+    constexpr int n = C::n, M = C::M, NF = C::NF, NST = C::NST;
+    const int d = item / (NF * M);
+    const int r = item - d * (NF * M);
+    const int p = r / M, v = r - p * M;
+    const int pd = d == 0 ? 1 : (d == 1 ? n : n * n);
+    const int s0 = (p % pd) + (p / pd) * pd * n;
+    T *base = ebuf + (d * NST + s0) * M + v;
+    T x[n];
+#pragma unroll
+    for (int j = 0; j < n; ++j) x[j] = base[j * pd * M];
+#pragma unroll
+    for (int i = 0; i < n; ++i) {
+        T acc = Dm[i * n] * x[0];
+#pragma unroll
+        for (int j = 1; j < n; ++j) acc += Dm[i * n + j] * x[j];
+        base[i * pd * M] = acc;
+    }
+}
+
 // dx_0 R at time level t of node s: R_0 + sum_{d>0} (dx_0/dx_d) R_d (the
 // factor 1/dx_0 is folded into dt by the caller, so isotropic and
 // anisotropic meshes cost the same).
@@ -327,7 +354,8 @@ k_predictor(const KParams P)
                 for (int d = 0; d < DIM; ++d) NodeIO<T, M>::store(ebuf + (d * NST + s) * M, F[d]);
             }
             __syncthreads();
-            if (act && s < NF) contract_all<C, T>(ebuf, 0, s, O);
+            if (act)
+                for (int item = s; item < DIM * NF * M; item += NS) contract_item_t0<C, T>(ebuf, item, O.Dm[0]);
             __syncthreads();
             gather_R<C, T>(ebuf, 0, s, ratio, R);
             __syncthreads();

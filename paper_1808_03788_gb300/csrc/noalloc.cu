@@ -142,6 +142,7 @@ extern "C" int aderdg_step_noalloc(const aderdg_mesh_t *mesh, int N, int nVar, c
     kp.dt_arg = dt;
     kp.use_ctl_dt = 0;
     for (int i = 0; i < 8; ++i) kp.pde.p[i] = pde->p[i];
+    fill_pde_consts(pde->kind, kp.pde);
     if (build_basis(N, kp.b)) return fail(ADERDG_E_INVAL, "basis construction failed");
     fill_ops(kp);
 

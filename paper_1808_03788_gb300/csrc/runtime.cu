@@ -359,6 +359,7 @@ int aderdg_create(const aderdg_mesh_t *mesh, int N, int nVar, const aderdg_pde_t
     {
         PdeParams pp;
         for (int i = 0; i < 8; ++i) pp.p[i] = pde->p[i];
+        fill_pde_consts(pde->kind, pp);
         const int rc = resolve_shapes(ks, pde->kind, mesh->dim, N, prec, pp, cfg ? cfg->pred_shape : 0,
                                       cfg ? cfg->corr_shape : 0, cfg ? cfg->tune_cache : nullptr, &h->kso);
         if (rc) { delete h; return rc; }
@@ -424,6 +425,7 @@ int aderdg_create(const aderdg_mesh_t *mesh, int N, int nVar, const aderdg_pde_t
     kp.solves = h->d_desc;
     kp.nsolves = 1;
     for (int i = 0; i < 8; ++i) kp.pde.p[i] = pde->p[i];
+    fill_pde_consts(pde->kind, kp.pde);
     kp.b = h->basis;
     fill_ops(kp);
 

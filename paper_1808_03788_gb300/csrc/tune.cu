@@ -323,6 +323,7 @@ extern "C" int aderdg_autotune(const aderdg_solve_spec_t *spec, int precision, c
     if (!ks) return fail(ADERDG_E_UNSUPPORTED, "no kernels compiled for this (pde, dim, N)");
     PdeParams pp;
     for (int i = 0; i < 8; ++i) pp.p[i] = spec->pde.p[i];
+    fill_pde_consts(spec->pde.kind, pp);
     Choice c{0, 0};
     const int rc = tuned(ks, spec->pde.kind, spec->mesh.dim, spec->N, precision, pp, tune_cache,
                          (flags & ADERDG_TUNE_FORCE) != 0, &c, ms);
