@@ -495,14 +495,19 @@ def run_ours(args, w, rank, world):
     clocks = ClockSampler(_gpu_id() if rank == 0 else None)
     if rank == 0:
         clocks.start()
-    shapes = "auto" if args.shapes == "auto" else (0, 0)
+    if args.shapes == "auto":
+        shapes = "auto"
+    elif args.shapes == "default":
+        shapes = (0, 0)
+    else:  # explicit "predictor,corrector" shape indices
+        shapes = tuple(int(x) for x in args.shapes.split(","))
     tune = {}
     if shapes == "auto":  # timed here, before anything is measured; handles then find the choice
         sp = A.make_spec(w["pde"], w["dim"], w["cells"], w["lo"], w["hi"], w["N"], w["params"])
         for name, pr in (("fp64", A.ADERDG_FP64), ("mixed", A.ADERDG_MIXED_FP32)):
             ch, ms = A.aderdg_autotune(sp, pr, force=True)
-            tune[name] = {"chosen": list(ch), "predictor_ms": ms[:A.ADERDG_NUM_SHAPES],
-                          "corrector_ms": ms[A.ADERDG_NUM_SHAPES:]}
+            tune[name] = {"chosen": list(ch), "predictor_ms": ms[:A.ADERDG_NUM_PRED_SHAPES],
+                          "corrector_ms": ms[A.ADERDG_NUM_PRED_SHAPES:]}
     s, U0, step_ms, pred_ms, corr_ms = _time_single(A, torch, w, prec, stream, args.steps, args.warmup, flush, world,
                                                     shapes)
     clk = clocks.stop() if rank == 0 else None
@@ -640,8 +645,9 @@ def main():
                     help="requests of a second served run at 80 %% of the measured capacity (0: skip)")
     ap.add_argument("--no-guess-variant", dest="guess_variant", action="store_false",
                     help="skip the third-order initial guess variant")
-    ap.add_argument("--shapes", default="auto", choices=["auto", "default"],
-                    help="tile shapes of the kernels: autotuned (default) or shape 0")
+    ap.add_argument("--shapes", default="auto",
+                    help="tile shapes of the kernels: auto (autotuned, default), default (shape 0) or "
+                         "'P,C' (predictor and corrector shape indices)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("note: fewer than 3 warm-up steps", file=sys.stderr)

@@ -94,12 +94,18 @@ extern "C" {
 #define ADERDG_GUESS_ORDER3 2
 
 /* ---- tile shapes -------------------------------------------------------
- * The predictor and the corrector are each compiled in ADERDG_NUM_SHAPES
- * launch shapes (CTA size and elements per CTA; shape 0 is the default,
- * 1 and 2 halve and double the CTA).  Every shape computes bit-identical
- * results; only the speed differs.  ADERDG_SHAPE_AUTOTUNE picks the shape
- * measured fastest on the current device for the (PDE, d, N, precision). */
-#define ADERDG_NUM_SHAPES 3
+ * The predictor is compiled in ADERDG_NUM_PRED_SHAPES launch variants and
+ * the corrector in ADERDG_NUM_CORR_SHAPES (shape 0 is the default).
+ * Shapes 0-2 of both are CTA sizes (default, half, double).  Predictor
+ * shapes 3 and 4 are, for 2D FP32 solves whose n x n x m space-time plane
+ * fits the registers, a kernel in which each thread owns that plane (about
+ * 128 and 256 threads per CTA); elsewhere they repeat shapes 0 and 2.  For
+ * a given (PDE, d, N, precision) every shape computes bit-identical results
+ * except that the two predictor kernels round differently (both within
+ * the path's tolerance); only the speed differs.  ADERDG_SHAPE_AUTOTUNE
+ * picks the shapes measured fastest on the current device. */
+#define ADERDG_NUM_PRED_SHAPES 5
+#define ADERDG_NUM_CORR_SHAPES 3
 #define ADERDG_SHAPE_DEFAULT 0
 #define ADERDG_SHAPE_AUTOTUNE (-1)
 
@@ -131,9 +137,10 @@ typedef struct {
                                    (0.9 x the von Neumann limit of the scheme) */
     void *cuda_stream;          /* cudaStream_t; NULL -> the legacy stream */
     const aderdg_alloc_t *alloc;/* NULL -> cudaMalloc / cudaFree */
-    int pred_shape;             /* predictor tile shape: 0 .. ADERDG_NUM_SHAPES-1
+    int pred_shape;             /* predictor shape: 0 .. ADERDG_NUM_PRED_SHAPES-1
                                    or ADERDG_SHAPE_AUTOTUNE */
-    int corr_shape;             /* corrector tile shape, likewise */
+    int corr_shape;             /* corrector shape: 0 .. ADERDG_NUM_CORR_SHAPES-1
+                                   or ADERDG_SHAPE_AUTOTUNE */
     const char *tune_cache;     /* text file of autotuned shapes, read and
                                    appended; NULL -> process memory only */
     int initial_guess;          /* ADERDG_GUESS_* (0: trivial) */
@@ -382,9 +389,9 @@ int aderdg_step_noalloc(const aderdg_mesh_t *mesh, int N, int nVar, const aderdg
  * (predictor) and shapes[1] (corrector).  The choice is kept for the
  * process and, if tune_cache is not NULL, appended to that text file; a
  * later call finds it there without timing unless flags has
- * ADERDG_TUNE_FORCE.  ms (NULL or 2 * ADERDG_NUM_SHAPES floats) receives
- * the measured milliseconds per launch, predictor shapes first (-1 where
- * nothing was timed).  Synchronising; allocates and frees device memory
+ * ADERDG_TUNE_FORCE.  ms (NULL or ADERDG_NUM_PRED_SHAPES +
+ * ADERDG_NUM_CORR_SHAPES floats) receives the measured milliseconds per
+ * launch, predictor shapes first (-1 where nothing was timed).  Synchronising; allocates and frees device memory
  * (about 2^21 x m x 40 bytes). */
 #define ADERDG_TUNE_FORCE 1
 int aderdg_autotune(const aderdg_solve_spec_t *spec, int precision, const char *tune_cache, int flags,

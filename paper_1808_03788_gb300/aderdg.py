@@ -30,7 +30,7 @@ ADERDG_E_CANCELLED = -8
 ADERDG_PDE_ADVECTION, ADERDG_PDE_EULER, ADERDG_PDE_ELASTICITY = 1, 2, 3
 ADERDG_FP64, ADERDG_MIXED_FP32 = 0, 1
 ADERDG_HOST, ADERDG_DEVICE = 0, 1
-ADERDG_NUM_SHAPES = 3
+ADERDG_NUM_PRED_SHAPES, ADERDG_NUM_CORR_SHAPES = 5, 3
 ADERDG_SHAPE_DEFAULT, ADERDG_SHAPE_AUTOTUNE = 0, -1
 ADERDG_TUNE_FORCE = 1
 ADERDG_GUESS_TRIVIAL, ADERDG_GUESS_ORDER2, ADERDG_GUESS_ORDER3 = 0, 1, 2
@@ -468,7 +468,7 @@ def aderdg_autotune(spec: aderdg_solve_spec_t, precision: int = ADERDG_MIXED_FP3
     """Fastest (predictor, corrector) tile shapes for spec's (PDE, d, N) and
     the measured ms per launch of every shape (-1: not timed, found cached)."""
     shapes = (C.c_int * 2)()
-    ms = (C.c_float * (2 * ADERDG_NUM_SHAPES))()
+    ms = (C.c_float * (ADERDG_NUM_PRED_SHAPES + ADERDG_NUM_CORR_SHAPES))()
     _check(load().aderdg_autotune(C.byref(spec), int(precision),
                                   None if tune_cache is None else os.fsencode(tune_cache),
                                   ADERDG_TUNE_FORCE if force else 0, shapes, ms))

@@ -484,7 +484,7 @@ int aderdg_batch_create(const aderdg_solve_spec_t *specs, int count, const aderd
     if (!specs || count <= 0) return fail(ADERDG_E_INVAL, "need count > 0 specs");
     const int prec = cfg ? cfg->precision : ADERDG_FP64;
     if (prec != ADERDG_FP64 && prec != ADERDG_MIXED_FP32) return fail(ADERDG_E_INVAL, "bad precision");
-    if (cfg && (!valid_shape_request(cfg->pred_shape) || !valid_shape_request(cfg->corr_shape)))
+    if (cfg && !valid_shape_requests(cfg->pred_shape, cfg->corr_shape))
         return fail(ADERDG_E_INVAL, "bad tile shape request");
     std::vector<Slot> tmp(count);
     for (int i = 0; i < count; ++i) {
@@ -798,7 +798,7 @@ int aderdg_server_create(const aderdg_server_config_t *cfg, aderdg_server_t **ou
     aderdg_server_t *s = new aderdg_server_s();
     s->prec = cfg ? cfg->precision : ADERDG_FP64;
     if (s->prec != ADERDG_FP64 && s->prec != ADERDG_MIXED_FP32) { delete s; return fail(ADERDG_E_INVAL, "bad precision"); }
-    if (cfg && (!valid_shape_request(cfg->pred_shape) || !valid_shape_request(cfg->corr_shape))) {
+    if (cfg && !valid_shape_requests(cfg->pred_shape, cfg->corr_shape)) {
         delete s;
         return fail(ADERDG_E_INVAL, "bad tile shape request");
     }

@@ -340,8 +340,10 @@ struct TileShape {
     size_t smem;
 };
 
-// Number of compiled tile shapes per kernel (shape 0 is the default).
-constexpr int NSHAPE = 3;
+// Number of compiled shapes of the predictor and the corrector (shape 0 is
+// the default).
+constexpr int NSHAPE_P = 5;
+constexpr int NSHAPE_C = 3;
 
 // Host-visible description of the compiled kernels of one (PDE, d, N,
 // precision).  predictor/corrector and their sizes are the shapes in use;
@@ -357,7 +359,7 @@ struct KernelSet {
     int nvar, rs, elem_bytes;  // elem_bytes = sizeof(T)
     int flux_flops, eig_flops;  // per point, for the cost model
     int rf;                     // doubles per element of the FP32 reference record (0: none)
-    TileShape pshape[NSHAPE], cshape[NSHAPE];
+    TileShape pshape[NSHAPE_P], cshape[NSHAPE_C];
     int pred_shape, corr_shape;  // indices of the shapes in use
 };
 

@@ -535,6 +535,8 @@ k_predictor(const KParams P)
     }
 }
 
+#include "predictor_xt.cuh"
+
 // ===========================================================================
 // Corrector
 // ===========================================================================
@@ -860,11 +862,23 @@ struct KS {
     static const KernelSet value;
 };
 
+// Predictor shapes: 0-2 k_predictor with CTAs of the default, half and
+// double size; 3-4 the plane-owning k_predictor_xt (about 128 and 256
+// threads) where it applies (2D FP32, small planes), else shapes 0 and 2.
 template <class PDE, int DIM, int N, typename T, int TS>
 constexpr TileShape pred_shape()
 {
-    using C = PredCfg<PDE, DIM, N, T, TS>;
-    return TileShape{&k_predictor<PDE, DIM, N, T, TS>, C::THREADS, C::EPB, C::BYTES};
+    if constexpr (TS >= 3) {
+        if constexpr (DIM == 2 && sizeof(T) == 4 && use_xt<PDE, N>()) {
+            using C = PredXtCfg<PDE, N, TS == 3 ? 0 : 2>;
+            return TileShape{&k_predictor_xt<PDE, N, TS == 3 ? 0 : 2>, C::THREADS, C::EPB, C::BYTES};
+        } else {
+            return pred_shape<PDE, DIM, N, T, TS == 3 ? 0 : 2>();
+        }
+    } else {
+        using C = PredCfg<PDE, DIM, N, T, TS>;
+        return TileShape{&k_predictor<PDE, DIM, N, T, TS>, C::THREADS, C::EPB, C::BYTES};
+    }
 }
 
 template <class PDE, int DIM, int N, typename T, int TS>
@@ -876,14 +890,15 @@ constexpr TileShape corr_shape()
 
 template <class PDE, int DIM, int N, typename T>
 const KernelSet KS<PDE, DIM, N, T>::value = {
-    &k_predictor<PDE, DIM, N, T, 0>, PredCfg<PDE, DIM, N, T>::THREADS, PredCfg<PDE, DIM, N, T>::EPB,
-    PredCfg<PDE, DIM, N, T>::BYTES,
+    pred_shape<PDE, DIM, N, T, 0>().kernel, pred_shape<PDE, DIM, N, T, 0>().threads,
+    pred_shape<PDE, DIM, N, T, 0>().epb, pred_shape<PDE, DIM, N, T, 0>().smem,
     &k_corrector<PDE, DIM, N, T, 0>, CorrCfg<PDE, DIM, N, T>::THREADS, CorrCfg<PDE, DIM, N, T>::EPB,
     CorrCfg<PDE, DIM, N, T>::BYTES,
     &k_cfl<PDE, DIM, N, T>,
     Geom<PDE, DIM, N>::M, Geom<PDE, DIM, N>::RS, (int)sizeof(T), PDE::FLUX_FLOPS, PDE::EIG_FLOPS,
     PredCfg<PDE, DIM, N, T>::DELTA ? PredCfg<PDE, DIM, N, T>::RF : 0,
-    {pred_shape<PDE, DIM, N, T, 0>(), pred_shape<PDE, DIM, N, T, 1>(), pred_shape<PDE, DIM, N, T, 2>()},
+    {pred_shape<PDE, DIM, N, T, 0>(), pred_shape<PDE, DIM, N, T, 1>(), pred_shape<PDE, DIM, N, T, 2>(),
+     pred_shape<PDE, DIM, N, T, 3>(), pred_shape<PDE, DIM, N, T, 4>()},
     {corr_shape<PDE, DIM, N, T, 0>(), corr_shape<PDE, DIM, N, T, 1>(), corr_shape<PDE, DIM, N, T, 2>()},
     0, 0};
 

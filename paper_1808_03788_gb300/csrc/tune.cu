@@ -1,7 +1,8 @@
 // Tile-shape autotuner of the per-element kernels.
 //
-// Each predictor and corrector is compiled in NSHAPE launch shapes (CTA
-// size / elements per CTA) that compute bit-identical results.  The tuner
+// The predictor and the corrector are compiled in NSHAPE_P / NSHAPE_C
+// launch variants (CTA sizes; for the predictor also a second kernel
+// layout) that compute the same results.  The tuner
 // times every shape of one (PDE, d, N, precision) on a synthetic periodic
 // mesh of about 2^21 nodes -- the cost of a step does not depend on the
 // data, only on the shapes and sizes -- and keeps the fastest, per process
@@ -98,7 +99,7 @@ bool read_cache(const char *path, const std::string &key, Choice *out)
     int a = 0, b = 0;
     bool found = false;
     while (std::fscanf(f, "%255s %d %d", k, &a, &b) == 3) {
-        if (key == k && a >= 0 && a < NSHAPE && b >= 0 && b < NSHAPE) {
+        if (key == k && a >= 0 && a < NSHAPE_P && b >= 0 && b < NSHAPE_C) {
             *out = {a, b};
             found = true;  // the last line for a key wins
         }
@@ -234,16 +235,16 @@ int measure(const KernelSet *ks, int pde, int dim, int N, int m, const PdeParams
     CKT(cudaMemcpyAsync(dd, &sd, sizeof(sd), cudaMemcpyHostToDevice, st));
     CKT(cudaMemcpyAsync(ctl, &c, sizeof(c), cudaMemcpyHostToDevice, st));
 
-    for (int i = 0; i < NSHAPE; ++i) {
+    for (int i = 0; i < NSHAPE_P; ++i) {
         float t = 0.f;
         if ((rc = time_shape(ks->pshape[i], kp, E, st, ea, eb, &t))) goto done;
         if (ms) ms[i] = t;
         if (i == 0 || t < 0.98f * bp) { best.pred = i; bp = t; }
     }
-    for (int i = 0; i < NSHAPE; ++i) {
+    for (int i = 0; i < NSHAPE_C; ++i) {
         float t = 0.f;
         if ((rc = time_shape(ks->cshape[i], kp, E, st, ea, eb, &t))) goto done;
-        if (ms) ms[NSHAPE + i] = t;
+        if (ms) ms[NSHAPE_P + i] = t;
         if (i == 0 || t < 0.98f * bc) { best.corr = i; bc = t; }
     }
     *out = best;
@@ -274,7 +275,7 @@ int tuned(const KernelSet *ks, int pde, int dim, int N, int prec, const PdeParam
     const std::string key = make_key(pde, dim, N, prec);
     std::lock_guard<std::mutex> lk(g_mu);
     if (ms)
-        for (int i = 0; i < 2 * NSHAPE; ++i) ms[i] = -1.f;
+        for (int i = 0; i < NSHAPE_P + NSHAPE_C; ++i) ms[i] = -1.f;
     if (!force) {
         auto it = g_table.find(key);
         if (it != g_table.end()) { *out = it->second; return ADERDG_OK; }
@@ -296,8 +297,7 @@ namespace aderdg {
 int resolve_shapes(const KernelSet *ks, int pde, int dim, int N, int prec, const PdeParams &pp, int pred_req,
                    int corr_req, const char *cache, KernelSet *out)
 {
-    if (!valid_shape_request(pred_req) || !valid_shape_request(corr_req))
-        return fail(ADERDG_E_INVAL, "bad tile shape request");
+    if (!valid_shape_requests(pred_req, corr_req)) return fail(ADERDG_E_INVAL, "bad tile shape request");
     Choice c{pred_req, corr_req};
     if (pred_req == ADERDG_SHAPE_AUTOTUNE || corr_req == ADERDG_SHAPE_AUTOTUNE) {
         Choice t{0, 0};

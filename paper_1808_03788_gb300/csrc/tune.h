@@ -5,13 +5,17 @@
 namespace aderdg {
 
 // A tile-shape request is a shape index or ADERDG_SHAPE_AUTOTUNE (-1).
-inline bool valid_shape_request(int r) { return r == -1 || (r >= 0 && r < NSHAPE); }
+inline bool valid_shape_request(int r, int count) { return r == -1 || (r >= 0 && r < count); }
+inline bool valid_shape_requests(int pred, int corr)
+{
+    return valid_shape_request(pred, NSHAPE_P) && valid_shape_request(corr, NSHAPE_C);
+}
 
 // Kernel set of one (PDE, d, N, precision), or NULL if none is compiled.
 const KernelSet *lookup_kernels(int pde, int dim, int N, int prec);
 
 // Copy of *ks launching the requested predictor / corrector shapes.  A
-// request is a shape index (0 .. NSHAPE-1) or ADERDG_SHAPE_AUTOTUNE, which
+// request is a shape index (0 .. NSHAPE_P-1 / NSHAPE_C-1) or ADERDG_SHAPE_AUTOTUNE, which
 // takes the fastest shape measured for this (PDE, d, N, precision) on the
 // current device: from the process-wide table, else from the text file
 // `cache` (may be NULL), else by timing every shape (and appending the

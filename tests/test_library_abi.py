@@ -135,11 +135,11 @@ def test_binding_struct_layouts_match_the_header(tmp_path):
 
 
 def test_tile_shape_requests_are_validated():
-    """A shape index outside 0..ADERDG_NUM_SHAPES-1 (other than the autotune
-    request) is rejected before any device work."""
+    """A shape index outside 0..ADERDG_NUM_PRED_SHAPES-1 (other than the
+    autotune request) is rejected before any device work."""
     cfg = A.aderdg_config_t()
     cfg.precision = A.ADERDG_FP64
-    cfg.pred_shape = A.ADERDG_NUM_SHAPES
+    cfg.pred_shape = A.ADERDG_NUM_PRED_SHAPES
     sp = A.make_spec(A.ADERDG_PDE_EULER, 2, (4, 4), (0, 0), (1, 1), 2, (1.4,))
     h = A._H()
     rc = A.load().aderdg_batch_create(C.byref(sp), 1, C.byref(cfg), C.byref(h))
