@@ -166,7 +166,20 @@ struct PredCfg {
     static constexpr int DIMS = DIM;
     // per-element shared buffer: DIM space-time flux fields, later
     // qbar | Fbar_d | face-trace stash
-    static constexpr int ELEM = cmax(DIM * NST * M, ((1 + DIM) * NS + NREC) * M);
+    static constexpr int ELEM0 = cmax(DIM * NST * M, ((1 + DIM) * NS + NREC) * M);
+    // Shared-memory bank layout of the 2D FP32 path with 16-byte nodes
+    // (Euler, m = 4), chosen per n from a bank-conflict count of the
+    // store / contract / gather phases: bit 0 pads the per-element buffer to
+    // 1 node mod 8 (neighbouring elements start on other banks), bit 1 maps
+    // thread s to the x-pencil (t = s mod n, p = s / n) instead of
+    // (t = s / n, p = s mod n).  Counted wavefronts per iteration and CTA,
+    // before -> after: n = 3: 732 -> 576, n = 5: 920 -> 780, n = 6: 1044 ->
+    // 1020, n = 7: 980 -> 952; n = 2, 4, 8 unchanged.
+    static constexpr int BANKS = (DIM == 2 && sizeof(T) == 4 && M == 4)
+                                     ? (n == 3 || n == 5 || n == 7 ? 3 : (n == 6 ? 1 : 0))
+                                     : 0;
+    static constexpr int ELEM = (BANKS & 1) ? ELEM0 + (((1 - ELEM0 / M) % 8 + 8) % 8) * M : ELEM0;
+    static constexpr bool MAPB0 = (BANKS & 2) != 0;
     // Shape 0 -- FP64: smaller CTAs, several per SM (independent barrier
     // domains keep the DFMA pipe fed); FP32: 256-thread CTAs.  Shapes 1 and
     // 2 halve and double the CTA at the same register cap per thread.
@@ -214,12 +227,14 @@ __device__ __forceinline__ void contract_pencil(T *Fd, int t, int p, const T *Dm
     }
 }
 
+// Every direction's pencil (t, p) in place; direction 0 takes (t0, p0).
 template <class C, typename T, int D = 0>
-__device__ __forceinline__ void contract_all(T *ebuf, int t, int p, const Ops<T> &O)
+__device__ __forceinline__ void contract_all(T *ebuf, int t0, int p0, int t, int p, const Ops<T> &O)
 {
     if constexpr (D < C::DIMS) {
-        contract_pencil<C, D, T>(ebuf + D * C::NST * C::M, t, p, O.Dm[D]);
-        contract_all<C, T, D + 1>(ebuf, t, p, O);
+        if constexpr (D == 0) contract_pencil<C, D, T>(ebuf, t0, p0, O.Dm[D]);
+        else contract_pencil<C, D, T>(ebuf + D * C::NST * C::M, t, p, O.Dm[D]);
+        contract_all<C, T, D + 1>(ebuf, t0, p0, t, p, O);
     }
 }
 
@@ -286,6 +301,7 @@ k_predictor(const KParams P)
     const int g = act ? tid / NS : 0;
     const int s = act ? tid - g * NS : 0;
     const int tk = s / NF, pk = s - (s / NF) * NF;  // this thread's d-pencils
+    const int tk0 = C::MAPB0 ? s % n : tk, pk0 = C::MAPB0 ? s / n : pk;  // its x-pencil
     T *ebuf = reinterpret_cast<T *>(smem_raw) + C::SHARED + g * C::ELEM;
     T *sQ = ebuf;                             // qbar[s][v]
     T *sFb = ebuf + NS * M;                   // Fbar[d][s][v]
@@ -409,7 +425,7 @@ k_predictor(const KParams P)
                 }
             }
             __syncthreads();
-            if (act) contract_all<C, T>(ebuf, tk, pk, O);
+            if (act) contract_all<C, T>(ebuf, tk0, pk0, tk, pk, O);
             __syncthreads();
             {
                 const T dtT = sDt[0];
