@@ -561,8 +561,9 @@ k_predictor(const KParams P)
 // trace records (one contiguous range), the 2d neighbour face chunks of
 // every element, u^n and V -- are staged into shared memory with cp.async
 // first (every load in flight at once), then: Rusanov flux per (element,
-// face node, variable); lift and FP64 update per (element, node, variable)
-// with coalesced stores; wave-speed maxima per node, one atomic per CTA.
+// face record), all variables; per (element, node): lift, FP64 update with
+// vector stores and the wave speeds of the new state from registers; one
+// atomic per CTA for the maxima.
 
 __device__ __forceinline__ void cp_async(void *dst, const void *src, int bytes)
 {
@@ -731,11 +732,10 @@ k_corrector(const KParams P)
         cp_async_wait_all();
         __syncthreads();
 
-        // ---- Rusanov flux per (element, face node, variable) ----------------
-        for (int i = threadIdx.x; i < ne * NREC * M; i += blockDim.x) {
-            const int el = i / (NREC * M);
-            const int r = i - el * (NREC * M);
-            const int rec = r / M, v = r - rec * M;
+        // ---- Rusanov flux per (element, face record), all variables --------
+        for (int i = threadIdx.x; i < ne * NREC; i += blockDim.x) {
+            const int el = i / NREC;
+            const int rec = i - el * NREC;
             const int d = rec / (2 * NF);
             const int side = (rec / NF) & 1;
             const int p = rec - (rec / NF) * NF;
@@ -744,55 +744,62 @@ k_corrector(const KParams P)
             const T *L = side ? own : nb;
             const T *R = side ? nb : own;
             const T smax = tmax(L[2 * M], R[2 * M]);
-            T f = T(0.5) * (L[M + v] + R[M + v]) - T(0.5) * smax * (R[v] - L[v]);
-            if constexpr (C::DELTA) {
-                // traces are perturbations about each element's own reference:
-                // add the reference part of the Rusanov flux minus own F_ref
-                const T *dl = sDel + ((((el * DIM + d) * 2 + side) * 2) * M);
-                f += (side ? T(0.5) : T(-0.5)) * dl[v] - T(0.5) * smax * dl[M + v];
-            }
-            sFs[(el * NREC + rec) * M + v] = f;
-        }
-        __syncthreads();
-
-        // ---- surface lift and update u^{n+1} = u^n + dt (V - surface) ------
-        double *uo = S.u_out + (long long)e0 * NS * M;
-        for (int i = threadIdx.x; i < ne * NS * M; i += blockDim.x) {
-            const int el = i / (NS * M);
-            const int r = i - el * (NS * M);
-            const int sn = r / M, v = r - sn * M;
-            T surf = T(0);
-            int rr = sn;
+            const T *dl = sDel + ((((el * DIM + d) * 2 + side) * 2) * M);
+            T f[M];
 #pragma unroll
-            for (int d = 0; d < DIM; ++d) {
-                const int k = rr % n;
-                rr /= n;
-                const int pd = ipow(n, d);
-                const int p = (sn % pd) + (sn / (pd * n)) * pd;
-                const T fp = sFs[(el * NREC + (d * 2 + 1) * NF + p) * M + v];
-                const T fm = sFs[(el * NREC + (d * 2 + 0) * NF + p) * M + v];
-                surf += sL[(3 + d) * NMAX + k] * fp - sL[d * NMAX + k] * fm;
+            for (int v = 0; v < M; ++v) {
+                f[v] = T(0.5) * (L[M + v] + R[M + v]) - T(0.5) * smax * (R[v] - L[v]);
+                if constexpr (C::DELTA) {
+                    // traces are perturbations about each element's own reference:
+                    // add the reference part of the Rusanov flux minus own F_ref
+                    f[v] += (side ? T(0.5) : T(-0.5)) * dl[v] - T(0.5) * smax * dl[M + v];
+                }
             }
-            const double unew = sU[i] + dt * widen<T>(sV[i] - surf);
-            sU[i] = unew;
-            uo[i] = unew;
+#pragma unroll
+            for (int v = 0; v < M; ++v) sFs[(el * NREC + rec) * M + v] = f[v];
         }
         __syncthreads();
 
-        // ---- wave-speed maxima of u^{n+1} and non-finite check -------------
-        // (in the compute type T; only the per-CTA maxima are widened)
+        // ---- per node: surface lift, update u^{n+1} = u^n + dt (V - surface),
+        // ---- then the wave speeds of u^{n+1} and the non-finite check -------
+        // (wave speeds in the compute type T; only the per-CTA maxima are widened)
+        double *uo = S.u_out + (long long)e0 * NS * M;
         T lmax[DIM];
 #pragma unroll
         for (int d = 0; d < DIM; ++d) lmax[d] = T(0);
         bool bad = false;
         for (int i = threadIdx.x; i < ne * NS; i += blockDim.x) {
-            T qs[M];
+            const int el = i / NS;
+            const int sn = i - el * NS;
+            int kk[DIM], pp[DIM];
+            {
+                int rr = sn;
+#pragma unroll
+                for (int d = 0; d < DIM; ++d) {
+                    kk[d] = rr % n;
+                    rr /= n;
+                    const int pd = ipow(n, d);
+                    pp[d] = (sn % pd) + (sn / (pd * n)) * pd;
+                }
+            }
+            double un[M];
+            T vn[M], qs[M];
+            NodeIO<double, M>::load(sU + i * M, un);
+            NodeIO<T, M>::load(sV + i * M, vn);
 #pragma unroll
             for (int v = 0; v < M; ++v) {
-                const double x = sU[i * M + v];
-                bad |= dbl_nonfinite(x);
-                qs[v] = narrow<T>(x);
+                T surf = T(0);
+#pragma unroll
+                for (int d = 0; d < DIM; ++d) {
+                    const T fp = sFs[(el * NREC + (d * 2 + 1) * NF + pp[d]) * M + v];
+                    const T fm = sFs[(el * NREC + (d * 2 + 0) * NF + pp[d]) * M + v];
+                    surf += sL[(3 + d) * NMAX + kk[d]] * fp - sL[d * NMAX + kk[d]] * fm;
+                }
+                un[v] = un[v] + dt * widen<T>(vn[v] - surf);
+                bad |= dbl_nonfinite(un[v]);
+                qs[v] = narrow<T>(un[v]);
             }
+            NodeIO<double, M>::store(uo + i * M, un);
 #pragma unroll
             for (int d = 0; d < DIM; ++d) {
                 const T lam = PDE::max_eig(P.pde, qs, d);
