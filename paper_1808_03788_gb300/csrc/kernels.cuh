@@ -166,7 +166,17 @@ struct PredCfg {
     static constexpr int DIMS = DIM;
     // per-element shared buffer: DIM space-time flux fields, later
     // qbar | Fbar_d | face-trace stash
-    static constexpr int ELEM0 = cmax(DIM * NST * M, ((1 + DIM) * NS + NREC) * M);
+    // Exchange field F_d[t][s][v] of an element: time slices TSL values apart
+    // (NS m plus TPAD), directions FSL = n TSL apart.  3D FP32 with n = 4
+    // pads every slice by one word and maps x-pencils t-fastest: a count of
+    // the conflicting 4-byte bank accesses of the store / contract / gather
+    // phases gives 7488 -> 4608 wavefronts per iteration and CTA for m = 9,
+    // 4160 -> 3200 for m = 5, 832 -> 640 for m = 1 (no gain for other n).
+    static constexpr bool PAD3 = (DIM == 3 && sizeof(T) == 4 && n == 4);
+    static constexpr int TPAD = PAD3 ? 1 : 0;
+    static constexpr int TSL = NS * M + TPAD;
+    static constexpr int FSL = n * TSL;
+    static constexpr int ELEM0 = cmax(DIM * FSL + (PAD3 ? 1 : 0), ((1 + DIM) * NS + NREC) * M);
     // Shared-memory bank layout of the 2D FP32 path with 16-byte nodes
     // (Euler, m = 4), chosen per n from a bank-conflict count of the
     // store / contract / gather phases: bit 0 pads the per-element buffer to
@@ -179,7 +189,7 @@ struct PredCfg {
                                      ? (n == 3 || n == 5 || n == 7 ? 3 : (n == 6 ? 1 : 0))
                                      : 0;
     static constexpr int ELEM = (BANKS & 1) ? ELEM0 + (((1 - ELEM0 / M) % 8 + 8) % 8) * M : ELEM0;
-    static constexpr bool MAPB0 = (BANKS & 2) != 0;
+    static constexpr bool MAPB0 = (BANKS & 2) != 0 || PAD3;
     // Shape 0 -- FP64: smaller CTAs, several per SM (independent barrier
     // domains keep the DFMA pipe fed); FP32: 256-thread CTAs.  Shapes 1 and
     // 2 halve and double the CTA at the same register cap per thread.
@@ -205,11 +215,11 @@ struct PredCfg {
 template <class C, int D, typename T>
 __device__ __forceinline__ void contract_pencil(T *Fd, int t, int p, const T *Dm)
 {
-    constexpr int n = C::n, M = C::M, NS = C::NS;
+    constexpr int n = C::n, M = C::M;
     constexpr int pd = ipow(n, D);
     using IO = NodeIO<T, M>;
     const int s0 = (p % pd) + (p / pd) * pd * n;
-    T *base = Fd + (t * NS + s0) * M;
+    T *base = Fd + t * C::TSL + s0 * M;
     T x[n][M];
 #pragma unroll
     for (int j = 0; j < n; ++j) IO::load(base + j * pd * M, x[j]);
@@ -233,7 +243,7 @@ __device__ __forceinline__ void contract_all(T *ebuf, int t0, int p0, int t, int
 {
     if constexpr (D < C::DIMS) {
         if constexpr (D == 0) contract_pencil<C, D, T>(ebuf, t0, p0, O.Dm[D]);
-        else contract_pencil<C, D, T>(ebuf + D * C::NST * C::M, t, p, O.Dm[D]);
+        else contract_pencil<C, D, T>(ebuf + D * C::FSL, t, p, O.Dm[D]);
         contract_all<C, T, D + 1>(ebuf, t0, p0, t, p, O);
     }
 }
@@ -246,13 +256,13 @@ __device__ __forceinline__ void contract_all(T *ebuf, int t0, int p0, int t, int
 template <class C, typename T>
 __device__ __forceinline__ void contract_item_t0(T *ebuf, int item, const T *Dm)
 {
-    constexpr int n = C::n, M = C::M, NF = C::NF, NST = C::NST;
+    constexpr int n = C::n, M = C::M, NF = C::NF;
     const int d = item / (NF * M);
     const int r = item - d * (NF * M);
     const int p = r / M, v = r - p * M;
     const int pd = d == 0 ? 1 : (d == 1 ? n : n * n);
     const int s0 = (p % pd) + (p / pd) * pd * n;
-    T *base = ebuf + (d * NST + s0) * M + v;
+    T *base = ebuf + d * C::FSL + s0 * M + v;
     T x[n];
 #pragma unroll
     for (int j = 0; j < n; ++j) x[j] = base[j * pd * M];
@@ -271,12 +281,12 @@ __device__ __forceinline__ void contract_item_t0(T *ebuf, int item, const T *Dm)
 template <class C, typename T>
 __device__ __forceinline__ void gather_R(const T *ebuf, int t, int s, const T *ratio, T *R)
 {
-    constexpr int M = C::M, NS = C::NS, NST = C::NST;
-    NodeIO<T, M>::load(ebuf + (t * NS + s) * M, R);
+    constexpr int M = C::M;
+    NodeIO<T, M>::load(ebuf + t * C::TSL + s * M, R);
 #pragma unroll
     for (int d = 1; d < C::DIMS; ++d) {
         T r[M];
-        NodeIO<T, M>::load(ebuf + (d * NST + t * NS + s) * M, r);
+        NodeIO<T, M>::load(ebuf + d * C::FSL + t * C::TSL + s * M, r);
 #pragma unroll
         for (int v = 0; v < M; ++v) R[v] += ratio[d] * r[v];
     }
@@ -367,7 +377,7 @@ k_predictor(const KParams P)
             flx(w, F);
             if (act) {
 #pragma unroll
-                for (int d = 0; d < DIM; ++d) NodeIO<T, M>::store(ebuf + (d * NST + s) * M, F[d]);
+                for (int d = 0; d < DIM; ++d) NodeIO<T, M>::store(ebuf + d * C::FSL + s * M, F[d]);
             }
             __syncthreads();
             if (act)
@@ -421,7 +431,7 @@ k_predictor(const KParams P)
                 flx(q[t], F);
                 if (act) {
 #pragma unroll
-                    for (int d = 0; d < DIM; ++d) NodeIO<T, M>::store(ebuf + (d * NST + t * NS + s) * M, F[d]);
+                    for (int d = 0; d < DIM; ++d) NodeIO<T, M>::store(ebuf + d * C::FSL + t * C::TSL + s * M, F[d]);
                 }
             }
             __syncthreads();

@@ -184,3 +184,42 @@ def test_server_admission_limits():
     res = _wait(srv, tks)
     assert all(r["status"] == A.ADERDG_OK for r in res.values())
     srv.close()
+
+
+@pytest.mark.parametrize("precision,tol", [(A.ADERDG_FP64, 1e-12), (A.ADERDG_MIXED_FP32, 1e-6)])
+def test_batched_recipe_sampled_step_vs_oracle(precision, tol):
+    """The batched workload's first 16 solves at their real sizes (meshes up
+    to 256^2, N in 2..6, seeded eps and centres) in one batch: one device-CFL
+    step; each solve's dt, and sampled elements of u^{n+1} against the
+    oracle's step of the same elements (FP64 1e-12 of the data scale, mixed
+    1e-6)."""
+    rec = inputs.batched_vortex_recipe(16)
+    b = A.Batch([A.make_spec(2, 2, r["cells"], (0, 0), (10, 10), r["N"], (1.4,)) for r in rec],
+                precision=precision)
+    cases = []
+    for i, r in enumerate(rec):
+        cfg = oracle.make_cfg(2, r["cells"], (0, 0), (10, 10), r["N"], 2, (1.4,))
+        U0 = inputs.euler_vortex(oracle.node_coords(cfg), eps=r["eps"], center=r["center"])
+        b.set_state(i, U0)
+        cases.append((cfg, U0))
+    b.step([1e30] * len(rec))
+    rng = np.random.default_rng(11)
+    for i, (cfg, U0) in enumerate(cases):
+        Ug, t, k = b.get_state(i)
+        assert k == 1
+        dto = oracle.cfl_dt(cfg, U0)
+        if precision == A.ADERDG_FP64:
+            assert abs(t - dto) <= 1e-14 * dto
+        else:  # wave speeds in FP32
+            assert abs(t - dto) <= 1e-6 * dto
+        E = oracle.n_elems(cfg)
+        cx = cfg.cells[0]
+        sel = np.unique(np.concatenate([[0, E - 1, cx - 1, E - cx], rng.integers(0, E, 24)]))
+        Uo = oracle.step_sampled(cfg, U0, t, sel)
+        Ug = Ug.reshape(U0.shape)[sel]
+        scale = max(1.0, float(np.abs(Uo).max()))
+        if precision == A.ADERDG_FP64:
+            assert np.abs(Ug - Uo).max() <= tol * scale
+        else:
+            assert np.linalg.norm(Ug - Uo) <= tol * np.linalg.norm(Uo)
+    b.close()
