@@ -142,3 +142,38 @@ def test_batch_with_guess_equals_alone():
                 alone = s.get_state()[0]
             np.testing.assert_array_equal(b.get_state(i)[0], alone.reshape(-1))
         b.close()
+
+
+def test_server_with_guess_equals_solves_alone():
+    """A server configured with the third-order guess serves results bitwise
+    equal to the same solves alone with that guess (mixed path)."""
+    import time
+    mix = [(2, 2, (6, 5), (0, 0), (10, 10), 2, (GAMMA,), 0.3), (2, 2, (8, 8), (0, 0), (10, 10), 4, (GAMMA,), 0.2),
+           (3, 3, (3, 3, 2), (0, 0, 0), (1, 1, 1), 3, EL, 0.02)]
+    srv = A.Server(precision=A.ADERDG_MIXED_FP32, steps_per_round=4, guess=A.ADERDG_GUESS_ORDER3)
+    ics, tickets = [], []
+    for c in mix:
+        X = oracle.node_coords(oracle.make_cfg(c[1], c[2], c[3], c[4], c[5], c[0], c[6]))
+        u0 = inputs.euler_vortex(X) if c[0] == 2 else inputs.elastic_pulse(X, width=0.05)
+        ics.append(u0)
+        tickets.append(srv.submit(A.make_spec(*c[:7]), u0, c[7]))
+    res = {}
+    t0 = time.time()
+    while len(res) < len(tickets) and time.time() - t0 < 120:
+        for tk in tickets:
+            if tk not in res:
+                r = srv.poll(tk)
+                if r is not None:
+                    res[tk] = r
+        time.sleep(0.002)
+    assert len(res) == len(tickets)
+    for tk, c, u0 in zip(tickets, mix, ics):
+        assert res[tk]["status"] == A.ADERDG_OK
+        with A.Solver(*c[:7], precision=A.ADERDG_MIXED_FP32, guess=A.ADERDG_GUESS_ORDER3) as s:
+            s.set_state(u0)
+            s.advance(c[7])
+            alone, t, k = s.get_state()
+        assert res[tk]["steps"] == k and res[tk]["t"] == t
+        np.testing.assert_array_equal(res[tk]["u"], alone.reshape(-1))
+        srv.release(tk)
+    srv.close()
