@@ -165,7 +165,7 @@ struct PredCfg {
     static constexpr int n = G::n, M = G::M, NS = G::NS, NST = G::NST, NF = G::NF, NREC = G::NREC;
     static constexpr int DIMS = DIM;
     // per-element shared buffer: DIM space-time flux fields, later
-    // qbar | Fbar_d | face-trace stash
+    // qbar | Fbar_d (| face states, where records outnumber threads)
     // Exchange field F_d[t][s][v] of an element: time slices TSL values apart
     // (NS m plus TPAD), directions FSL = n TSL apart.  3D FP32 with n = 4
     // pads every slice by one word and maps x-pencils t-fastest: a count of
@@ -176,7 +176,7 @@ struct PredCfg {
     static constexpr int TPAD = PAD3 ? 1 : 0;
     static constexpr int TSL = NS * M + TPAD;
     static constexpr int FSL = n * TSL;
-    static constexpr int ELEM0 = cmax(DIM * FSL + (PAD3 ? 1 : 0), ((1 + DIM) * NS + NREC) * M);
+    static constexpr int ELEM0 = cmax(DIM * FSL + (PAD3 ? 1 : 0), ((1 + DIM) * NS + (NREC > NS ? NREC : 0)) * M);
     // Shared-memory bank layout of the 2D FP32 path with 16-byte nodes
     // (Euler, m = 4), chosen per n from a bank-conflict count of the
     // store / contract / gather phases: bit 0 pads the per-element buffer to
@@ -315,7 +315,6 @@ k_predictor(const KParams P)
     T *ebuf = reinterpret_cast<T *>(smem_raw) + C::SHARED + g * C::ELEM;
     T *sQ = ebuf;                             // qbar[s][v]
     T *sFb = ebuf + NS * M;                   // Fbar[d][s][v]
-    T *sStash = ebuf + (1 + DIM) * NS * M;    // face traces of qbar
 
     for (int i = tid; i < DIM * n * n; i += blockDim.x) sKw[i] = O.Kv[i / (n * n)][i % (n * n)];
     for (int i = tid; i < n; i += blockDim.x) {
@@ -516,45 +515,87 @@ k_predictor(const KParams P)
             for (int v = 0; v < M; ++v) Vout[s * M + v] = Vn[v];
         }
 
-        // ---- face traces of the time averages ------------------------------
+        // ---- face traces of the time averages and their wave speeds --------
         T *trE = reinterpret_cast<T *>(S.tr) + ec * (NREC * RS);
-        if (act) {
-            for (int i = s; i < NREC * M; i += NS) {
-                const int rec = i / M, v = i - rec * M;
-                const int d = rec / (2 * NF);
-                const int side = (rec / NF) & 1;
-                const int p = rec - (rec / NF) * NF;
-                const int pd = ipow(n, d);
-                const int s0 = (p % pd) + (p / pd) * pd * n;
-                const T *phi = side ? sF1 : sF0;
-                T aq = T(0), af = T(0);
+        if constexpr (NREC <= NS) {
+            // one record (all variables) per thread; wave speed in place
+            if (valid) {
+                for (int rec = s; rec < NREC; rec += NS) {
+                    const int d = rec / (2 * NF);
+                    const int side = (rec / NF) & 1;
+                    const int p = rec - (rec / NF) * NF;
+                    const int pd = d == 0 ? 1 : (d == 1 ? n : n * n);
+                    const int s0 = (p % pd) + (p / pd) * pd * n;
+                    const T *phi = side ? sF1 : sF0;
+                    T aq[M], af[M];
 #pragma unroll
-                for (int j = 0; j < n; ++j) {
-                    aq += phi[j] * sQ[(s0 + j * pd) * M + v];
-                    af += phi[j] * sFb[(d * NS + s0 + j * pd) * M + v];
+                    for (int v = 0; v < M; ++v) { aq[v] = T(0); af[v] = T(0); }
+#pragma unroll
+                    for (int j = 0; j < n; ++j) {
+                        T qj[M], fj[M];
+                        NodeIO<T, M>::load(sQ + (s0 + j * pd) * M, qj);
+                        NodeIO<T, M>::load(sFb + (d * NS + s0 + j * pd) * M, fj);
+                        const T pj = phi[j];
+#pragma unroll
+                        for (int v = 0; v < M; ++v) {
+                            aq[v] += pj * qj[v];
+                            af[v] += pj * fj[v];
+                        }
+                    }
+                    T *r = trE + rec * RS;
+                    T full[M];
+#pragma unroll
+                    for (int v = 0; v < M; ++v) {
+                        r[v] = aq[v];
+                        r[M + v] = af[v];
+                        full[v] = aq[v] + (C::DELTA ? ref.q[v] : T(0));
+                    }
+                    r[2 * M] = PDE::max_eig(P.pde, full, d);
+                    r[2 * M + 1] = T(0);
                 }
-                sStash[rec * M + v] = aq;
-                if (valid) {
-                    trE[rec * RS + v] = aq;
-                    trE[rec * RS + M + v] = af;
+            }
+        } else {
+            // more records than threads: (record, variable) items, then the
+            // wave speeds from the stashed face states
+            T *sStash = ebuf + (1 + DIM) * NS * M;
+            if (act) {
+                for (int i = s; i < NREC * M; i += NS) {
+                    const int rec = i / M, v = i - rec * M;
+                    const int d = rec / (2 * NF);
+                    const int side = (rec / NF) & 1;
+                    const int p = rec - (rec / NF) * NF;
+                    const int pd = ipow(n, d);
+                    const int s0 = (p % pd) + (p / pd) * pd * n;
+                    const T *phi = side ? sF1 : sF0;
+                    T aq = T(0), af = T(0);
+#pragma unroll
+                    for (int j = 0; j < n; ++j) {
+                        aq += phi[j] * sQ[(s0 + j * pd) * M + v];
+                        af += phi[j] * sFb[(d * NS + s0 + j * pd) * M + v];
+                    }
+                    sStash[rec * M + v] = aq;
+                    if (valid) {
+                        trE[rec * RS + v] = aq;
+                        trE[rec * RS + M + v] = af;
+                    }
+                }
+            }
+            __syncthreads();
+            if (valid) {
+                for (int rec = s; rec < NREC; rec += NS) {
+                    const int d = rec / (2 * NF);
+                    T full[M];
+#pragma unroll
+                    for (int v = 0; v < M; ++v) full[v] = sStash[rec * M + v] + (C::DELTA ? ref.q[v] : T(0));
+                    trE[rec * RS + 2 * M] = PDE::max_eig(P.pde, full, d);
+                    trE[rec * RS + 2 * M + 1] = T(0);
                 }
             }
         }
-        __syncthreads();
-        if (valid) {
-            for (int rec = s; rec < NREC; rec += NS) {
-                const int d = rec / (2 * NF);
-                T full[M];
+        if constexpr (C::DELTA) {
+            if (valid && s == 0) {  // the reference state, kept in FP64 for the corrector
 #pragma unroll
-                for (int v = 0; v < M; ++v) full[v] = sStash[rec * M + v] + (C::DELTA ? ref.q[v] : T(0));
-                trE[rec * RS + 2 * M] = PDE::max_eig(P.pde, full, d);
-                trE[rec * RS + 2 * M + 1] = T(0);
-            }
-            if constexpr (C::DELTA) {
-                if (s == 0) {  // the reference state, kept in FP64 for the corrector
-#pragma unroll
-                    for (int v = 0; v < M; ++v) S.ref[ec * C::RF + v] = uref[v];
-                }
+                for (int v = 0; v < M; ++v) S.ref[ec * C::RF + v] = uref[v];
             }
         }
         __syncthreads();  // ebuf is reused by the next tile
