@@ -297,7 +297,7 @@ __global__ void __launch_bounds__(PredCfg<PDE, DIM, N, T, TS>::THREADS, PredCfg<
 k_predictor(const KParams P)
 {
     using C = PredCfg<PDE, DIM, N, T, TS>;
-    constexpr int n = C::n, M = C::M, NS = C::NS, NST = C::NST, NF = C::NF, NREC = C::NREC;
+    constexpr int n = C::n, M = C::M, NS = C::NS, NF = C::NF, NREC = C::NREC;
     constexpr int EPB = C::EPB, RS = Geom<PDE, DIM, N>::RS;
     const Ops<T> &O = ops_of<T>(P);
 
