@@ -650,7 +650,15 @@ struct CorrCfg {
     static constexpr size_t UB = sizeof(double) * NS * M;
     static constexpr size_t VB = sizeof(T) * NS * M;
     static constexpr size_t FS = sizeof(T) * NREC * M;
-    static constexpr size_t PER_ELEM = align16(OWN) + align16(NB) + align16(UB) + align16(VB) + align16(FS);
+    // u^n and V are staged in shared memory, except on the FP64 path when an
+    // element's staged inputs are large (3D elasticity: 43 KB per element):
+    // there the update reads them from global memory once, and the smaller
+    // footprint lets more CTAs share an SM (corrector 7.8 -> 7.2 ms at 64^3,
+    // N = 3; the FP32 path measured slower without the staging)
+    static constexpr bool STAGE_UV =
+        sizeof(T) == 4 || align16(OWN) + align16(NB) + align16(UB) + align16(VB) <= 8192;
+    static constexpr size_t PER_ELEM =
+        align16(OWN) + align16(NB) + (STAGE_UV ? align16(UB) + align16(VB) : 0) + align16(FS);
     // shapes 0, 1, 2: 256-, 128- and 512-thread CTAs
     static constexpr int THREADS = TS == 1 ? 128 : (TS == 2 ? 512 : 256);
     static constexpr int EPB_T = cmax(1, THREADS / NS);
@@ -659,8 +667,8 @@ struct CorrCfg {
     static constexpr size_t O_OWN = 0;
     static constexpr size_t O_NB = align16(EPB * OWN);
     static constexpr size_t O_U = O_NB + align16(EPB * NB);
-    static constexpr size_t O_V = O_U + align16(EPB * UB);
-    static constexpr size_t O_FS = O_V + align16(EPB * VB);
+    static constexpr size_t O_V = O_U + (STAGE_UV ? align16(EPB * UB) : 0);
+    static constexpr size_t O_FS = O_V + (STAGE_UV ? align16(EPB * VB) : 0);
     static constexpr size_t O_LIFT = O_FS + align16(EPB * FS);
     static constexpr size_t O_NBIDX = O_LIFT + align16(sizeof(T) * 2 * 3 * NMAX);
     static constexpr size_t O_DEL = O_NBIDX + align16(sizeof(int) * EPB * 2 * DIM);
@@ -729,8 +737,10 @@ k_corrector(const KParams P)
             sL[(1 * 3 + d) * NMAX + k] = T(idx * P.b.inv_w[k] * P.b.F1[k]);
         }
         stage<C::G_OWN>(sOwn, tr + (long long)e0 * NREC * RS, ne * (int)C::OWN);
-        stage<C::G_U>(sU, S.u + (long long)e0 * NS * M, ne * (int)C::UB);
-        stage<C::G_V>(sV, reinterpret_cast<const T *>(S.V) + (long long)e0 * NS * M, ne * (int)C::VB);
+        if constexpr (C::STAGE_UV) {
+            stage<C::G_U>(sU, S.u + (long long)e0 * NS * M, ne * (int)C::UB);
+            stage<C::G_V>(sV, reinterpret_cast<const T *>(S.V) + (long long)e0 * NS * M, ne * (int)C::VB);
+        }
         __syncthreads();  // neighbour indices
         {
             constexpr int units = (int)(sizeof(T) * NF * RS) / C::G_NB;
@@ -835,8 +845,13 @@ k_corrector(const KParams P)
             }
             double un[M];
             T vn[M], qs[M];
-            NodeIO<double, M>::load(sU + i * M, un);
-            NodeIO<T, M>::load(sV + i * M, vn);
+            if constexpr (C::STAGE_UV) {
+                NodeIO<double, M>::load(sU + i * M, un);
+                NodeIO<T, M>::load(sV + i * M, vn);
+            } else {
+                NodeIO<double, M>::load(S.u + ((long long)e0 * NS + i) * M, un);
+                NodeIO<T, M>::load(reinterpret_cast<const T *>(S.V) + ((long long)e0 * NS + i) * M, vn);
+            }
 #pragma unroll
             for (int v = 0; v < M; ++v) {
                 T surf = T(0);
