@@ -584,7 +584,8 @@ def run_ours(args, w, rank, world):
         if args.elastic_steps > 0 and args.workload != "elastic3d_pulse_64^3_N3":
             variants["elastic3d"] = _elastic(A, torch, stream, flush, args.elastic_steps, shapes)
         if args.batched_solves > 0:
-            variants["batched"] = _batched(A, torch, max(8, min(args.steps, 64)), 8, args.batched_solves, shapes)
+            variants["batched"] = _batched(A, torch, args.batched_steps, args.batched_warmup, args.batched_solves,
+                                           shapes)
         if args.served_requests > 0:
             variants["served"] = _served(A, args.served_requests, args.served_rate, shapes=shapes)
             sv = variants["served"]
@@ -597,10 +598,18 @@ def run_ours(args, w, rank, world):
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
+        import oracle
         v, el, cores = oracle_throughput(w, args.cpu_steps)
+        oracle.set_threads(1)
+        try:
+            v1, el1, _ = oracle_throughput(w, 1)
+        finally:
+            oracle.set_threads(0)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": "%d full ADER-DG steps of the whole %s mesh, plain FP64 C oracle, OpenMP over "
-                         "elements (%.1f s)" % (args.cpu_steps, "x".join(map(str, w["cells"])), el)}
+                         "elements (%.1f s)" % (args.cpu_steps, "x".join(map(str, w["cells"])), el),
+               "single_thread": {"value": v1, "unit": UNIT, "cores": 1,
+                                 "sample": "1 full step of the same mesh on one thread (%.1f s)" % el1}}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -639,6 +648,8 @@ def main():
     ap.add_argument("--l2-steps", type=int, default=100)
     ap.add_argument("--elastic-steps", type=int, default=4)
     ap.add_argument("--batched-solves", type=int, default=256)
+    ap.add_argument("--batched-steps", type=int, default=200, help="timed window of the batched workload")
+    ap.add_argument("--batched-warmup", type=int, default=20)
     ap.add_argument("--served-requests", type=int, default=24)
     ap.add_argument("--served-rate", type=float, default=200.0)
     ap.add_argument("--served-scaled", type=int, default=12,

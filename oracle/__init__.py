@@ -106,6 +106,8 @@ def lib():
             L.orc_alpha.argtypes = [cp]
             L.orc_alpha.restype = C.c_double
             L.orc_threads.argtypes = []
+            L.orc_set_threads.argtypes = [C.c_int]
+            L.orc_set_threads.restype = None
             _lib = L
     return _lib
 
@@ -326,3 +328,8 @@ def alpha(cfg: Cfg) -> float:
 
 def threads() -> int:
     return lib().orc_threads()
+
+
+def set_threads(n: int) -> None:
+    """OpenMP threads of later oracle calls (n <= 0: the default)."""
+    lib().orc_set_threads(int(n))

@@ -856,6 +856,19 @@ int orc_node_coords(const orc_cfg *c, double *X)
     return 0;
 }
 
+/* Sets the OpenMP thread count of later parallel loops (no-op without
+ * OpenMP); n <= 0 restores the default. */
+void orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    static int dflt = 0;
+    if (dflt == 0) dflt = omp_get_max_threads();
+    omp_set_num_threads(n > 0 ? n : dflt);
+#else
+    (void)n;
+#endif
+}
+
 /* Number of OpenMP threads the parallel loops use (1 without OpenMP). */
 int orc_threads(void)
 {
