@@ -26,7 +26,9 @@ struct PredXtCfg {
     static constexpr int TARGET = TS == 1 ? 64 : (TS == 2 ? 256 : 128);
     static constexpr int EPB = cmax(1, TARGET / n);
     static constexpr int THREADS = round_up(EPB * n, 32);
-    static constexpr int MINB = cmax(1, (2 * 128) / THREADS);  // up to 255 registers
+    // shape 0 (about 128 threads): 3 CTAs per SM (168 registers; large planes
+    // spill a little); shape 2 (about 256 threads): one CTA, up to 255 registers
+    static constexpr int MINB = TS == 2 ? 1 : cmax(1, (3 * 128) / THREADS);
     // per element: the F_y / R_y field [t][y][x][v]; its size is padded to
     // 16 mod 128 bytes so that neighbouring elements start on other banks
     static constexpr int ELEM = round_up(NST * M, 32) + 4;
