@@ -310,17 +310,20 @@ typedef struct {
     size_t device_budget_bytes;  /* 0: 90 % of the free device memory */
     int max_queue;               /* queued (not yet admitted) requests; 0: 100000 */
     int steps_per_round;         /* steps between admission rounds; 0: 8 */
-    int precision;               /* ADERDG_FP64 / ADERDG_MIXED_FP32 */
+    int precision;               /* ADERDG_FP64 / ADERDG_MIXED_FP32: requests' default */
     void *cuda_stream;           /* NULL: a stream of the server's own */
     int pred_shape, corr_shape;  /* tile shapes, as in aderdg_config_t */
     const char *tune_cache;      /* as in aderdg_config_t */
-    int initial_guess;           /* ADERDG_GUESS_*, Picard count by the default rule */
+    int initial_guess;           /* ADERDG_GUESS_* (requests' default), Picard count by
+                                    the default rule */
 } aderdg_server_config_t;
 
 typedef struct {
     aderdg_solve_spec_t spec;
     const double *u0;            /* host, E (N+1)^d m doubles, copied */
     double t_end;
+    int precision;               /* ADERDG_FP64 / ADERDG_MIXED_FP32; -1: the server's */
+    int initial_guess;           /* ADERDG_GUESS_*; -1: the server's */
 } aderdg_request_t;
 
 typedef struct {

@@ -87,7 +87,8 @@ class aderdg_server_config_t(C.Structure):
 
 
 class aderdg_request_t(C.Structure):
-    _fields_ = [("spec", aderdg_solve_spec_t), ("u0", C.POINTER(C.c_double)), ("t_end", C.c_double)]
+    _fields_ = [("spec", aderdg_solve_spec_t), ("u0", C.POINTER(C.c_double)), ("t_end", C.c_double),
+                ("precision", C.c_int), ("initial_guess", C.c_int)]
 
 
 class aderdg_result_t(C.Structure):
@@ -633,13 +634,16 @@ class Server:
         except Exception:
             pass
 
-    def submit(self, spec: aderdg_solve_spec_t, u0, t_end: float) -> int:
+    def submit(self, spec: aderdg_solve_spec_t, u0, t_end: float, precision: int = -1, guess: int = -1) -> int:
+        """Queue a solve; precision / guess -1 take the server's."""
         u0 = np.ascontiguousarray(u0, dtype=np.float64)
         assert u0.size == spec_size(spec)
         req = aderdg_request_t()
         req.spec = spec
         req.u0 = u0.ctypes.data_as(_DP)
         req.t_end = float(t_end)
+        req.precision = int(precision)
+        req.initial_guess = int(guess)
         tk = C.c_uint64(0)
         _check(self._L.aderdg_submit(self._h, C.byref(req), C.byref(tk)))
         return tk.value

@@ -92,7 +92,7 @@ struct Mem {
 };
 
 struct Slot {
-    int pde = 0, dim = 0, N = 0, M = 0, NS = 0, NF = 0, NREC = 0, picard = 0, guess = 0;
+    int pde = 0, dim = 0, N = 0, M = 0, NS = 0, NF = 0, NREC = 0, picard = 0, guess = 0, prec = 0;
     long long E = 0;
     int cells[3] = {1, 1, 1};
     double inv_dx[3] = {1, 1, 1}, vol = 1;
@@ -135,6 +135,7 @@ int make_slot(const aderdg_solve_spec_t &sp, int prec, int guess, int picard, do
     s.NF = ipow(sp.N + 1, m.dim - 1);
     s.NREC = m.dim * 2 * s.NF;
     s.guess = guess;
+    s.prec = prec;
     s.picard = picard > 0 ? picard : default_picard(sp.N, guess);
     s.alpha = alpha > 0 ? alpha : default_alpha(sp.N);
     s.ks = ks;
@@ -167,7 +168,7 @@ __global__ void k_set_tend(Control *const *ctls, const double *t_end, int count)
 }
 
 struct Group {
-    int pde = 0, dim = 0, N = 0;
+    int pde = 0, dim = 0, N = 0, prec = 0;
     PdeParams pp{};
     const KernelSet *ks = nullptr;  // compiled kernels of the group
     KernelSet kso{};                // the same with the tile shapes in use
@@ -178,16 +179,18 @@ struct Group {
     long long ntp = 0, ntc = 0;
 };
 
+// solves share a group (one predictor and one corrector launch) when they
+// have the same kernels (PDE, dimension, order, precision) and parameters
 bool same_group(const Group &g, const Slot &s)
 {
-    return g.pde == s.pde && g.dim == s.dim && g.N == s.N && std::memcmp(&g.pp, &s.pp, sizeof(PdeParams)) == 0;
+    return g.ks == s.ks && g.pde == s.pde && g.dim == s.dim && g.N == s.N && g.prec == s.prec &&
+           std::memcmp(&g.pp, &s.pp, sizeof(PdeParams)) == 0;
 }
 
 class Engine {
 public:
     Mem mem;
     cudaStream_t st = nullptr;
-    int prec = ADERDG_FP64;
     int pred_req = 0, corr_req = 0;  // requested tile shapes (index or ADERDG_SHAPE_AUTOTUNE)
     std::string tune_cache;          // empty: none
     int device = 0;
@@ -205,13 +208,12 @@ public:
     cudaGraphExec_t graph = nullptr;
     int graph_steps = 0;
 
-    int init(int capacity, cudaStream_t stream, const aderdg_alloc_t *hook, int precision)
+    int init(int capacity, cudaStream_t stream, const aderdg_alloc_t *hook)
     {
         cudaGetDevice(&device);
         st = stream;
         mem.st = stream;
         if (hook) { mem.hook = *hook; mem.has_hook = true; }
-        prec = precision;
         ctl_cap = std::max(1, capacity);
         d_ctl = (Control *)mem.get(sizeof(Control) * ctl_cap);
         if (!d_ctl) return fail(ADERDG_E_NOMEM, "control pool allocation failed");
@@ -293,7 +295,7 @@ public:
                 if (same_group(ng[i], *s)) { gi = (int)i; break; }
             if (gi < 0) {
                 Group g;
-                g.pde = s->pde; g.dim = s->dim; g.N = s->N; g.pp = s->pp; g.ks = s->ks;
+                g.pde = s->pde; g.dim = s->dim; g.N = s->N; g.prec = s->prec; g.pp = s->pp; g.ks = s->ks;
                 ng.push_back(g);
                 gi = (int)ng.size() - 1;
             }
@@ -303,7 +305,7 @@ public:
         }
         // tile shapes per group (may autotune on first use of a key)
         for (Group &g : ng) {
-            const int rc = resolve_shapes(g.ks, g.pde, g.dim, g.N, prec, g.pp, pred_req, corr_req,
+            const int rc = resolve_shapes(g.ks, g.pde, g.dim, g.N, g.prec, g.pp, pred_req, corr_req,
                                           tune_cache.empty() ? nullptr : tune_cache.c_str(), &g.kso);
             if (rc) return rc;
         }
@@ -506,7 +508,7 @@ int aderdg_batch_create(const aderdg_solve_spec_t *specs, int count, const aderd
         }
         b->own_stream = true;
     }
-    int rc = b->eng.init(count, st, cfg ? cfg->alloc : nullptr, prec);
+    int rc = b->eng.init(count, st, cfg ? cfg->alloc : nullptr);
     if (cfg) {
         b->eng.pred_req = cfg->pred_shape;
         b->eng.corr_req = cfg->corr_shape;
@@ -820,7 +822,7 @@ int aderdg_server_create(const aderdg_server_config_t *cfg, aderdg_server_t **ou
         }
         s->own_stream = true;
     }
-    int rc = s->eng.init(4096, st, nullptr, s->prec);
+    int rc = s->eng.init(4096, st, nullptr);
     if (cfg) {
         s->eng.pred_req = cfg->pred_shape;
         s->eng.corr_req = cfg->corr_shape;
@@ -860,7 +862,10 @@ int aderdg_submit(aderdg_server_t *s, const aderdg_request_t *req, uint64_t *tic
     if (!s || !req || !ticket || !req->u0) return fail(ADERDG_E_INVAL, "NULL argument");
     if (!(req->t_end > 0) || !std::isfinite(req->t_end)) return fail(ADERDG_E_INVAL, "t_end must be positive");
     Request *r = new Request();
-    int rc = make_slot(req->spec, s->prec, s->guess, 0, 0.0, r->spec);
+    const int prec = req->precision < 0 ? s->prec : req->precision;
+    const int guess = req->initial_guess < 0 ? s->guess : req->initial_guess;
+    if (prec != ADERDG_FP64 && prec != ADERDG_MIXED_FP32) { delete r; return fail(ADERDG_E_INVAL, "bad precision"); }
+    int rc = make_slot(req->spec, prec, guess, 0, 0.0, r->spec);
     if (rc) { delete r; return rc; }
     if (r->spec.bytes > s->budget) {
         delete r;

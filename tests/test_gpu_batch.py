@@ -223,3 +223,37 @@ def test_batched_recipe_sampled_step_vs_oracle(precision, tol):
         else:
             assert np.linalg.norm(Ug - Uo) <= tol * np.linalg.norm(Uo)
     b.close()
+
+
+def test_server_mixes_precisions_and_guesses_per_request():
+    """Requests of both precisions and different initial guesses run in one
+    server at once (separate kernel groups of one engine); each result is
+    bitwise the same solve alone with its precision and guess."""
+    srv = A.Server(precision=A.ADERDG_FP64, steps_per_round=3)
+    cases = [(MIX[0], A.ADERDG_FP64, -1), (MIX[0], A.ADERDG_MIXED_FP32, -1), (MIX[1], A.ADERDG_MIXED_FP32, 2),
+             (MIX[4], -1, 2), (MIX[4], A.ADERDG_MIXED_FP32, 0), (MIX[5], A.ADERDG_MIXED_FP32, -1)]
+    U0s = [_ic(c, oracle.node_coords(_cfg(c))) for c, _, _ in cases]
+    tickets = [srv.submit(A.make_spec(*c[:7]), U0s[i], c[7], precision=p, guess=g)
+               for i, (c, p, g) in enumerate(cases)]
+    res = _wait(srv, tickets)
+    for tk, (c, p, g), U0 in zip(tickets, cases, U0s):
+        r = res[tk]
+        assert r["status"] == A.ADERDG_OK
+        pde, dim, cells, lo, hi, N, params, t_end = c
+        prec = A.ADERDG_FP64 if p < 0 else p
+        with A.Solver(pde, dim, cells, lo, hi, N, params, precision=prec, guess=max(g, 0)) as s:
+            s.set_state(U0)
+            s.advance(t_end)
+            Us, ts, ks = s.get_state()
+        assert r["steps"] == ks and r["t"] == ts
+        np.testing.assert_array_equal(r["u"], Us.reshape(-1))
+        srv.release(tk)
+    srv.close()
+
+
+def test_server_rejects_bad_request_precision():
+    srv = A.Server()
+    c = MIX[0]
+    with pytest.raises(A.AderdgError):
+        srv.submit(A.make_spec(*c[:7]), _ic(c, oracle.node_coords(_cfg(c))), c[7], precision=7)
+    srv.close()
