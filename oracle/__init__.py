@@ -89,6 +89,7 @@ def lib():
             L.orc_max_eigs.restype = None
             L.orc_predictor.argtypes = [cp, dp, C.c_double, dp, dp, dp, C.POINTER(C.c_int)]
             L.orc_initial_guess.argtypes = [cp, dp, C.c_double, dp]
+            L.orc_initial_guess_extrap.argtypes = [cp, dp, C.c_double, dp, C.c_double, dp]
             L.orc_volume.argtypes = [cp, dp, dp]
             L.orc_traces.argtypes = [cp, dp, dp, dp, dp]
             L.orc_rusanov.argtypes = [cp, C.c_int, dp, dp, dp, dp, dp]
@@ -121,7 +122,7 @@ def nvar(pde: int, dim: int) -> int:
     return lib().orc_nvar(pde, dim)
 
 
-GUESS_TRIVIAL, GUESS_ORDER2, GUESS_ORDER3 = 0, 1, 2
+GUESS_TRIVIAL, GUESS_ORDER2, GUESS_ORDER3, GUESS_EXTRAP = 0, 1, 2, 3
 
 
 def make_cfg(dim, cells, lo, hi, N, pde, prm=(), picard=0, alpha=0.0, guess=GUESS_TRIVIAL) -> Cfg:
@@ -218,6 +219,20 @@ def initial_guess(cfg: Cfg, u: np.ndarray, dt: float) -> np.ndarray:
     q0 = np.zeros((n, ns, cfg.m))
     if lib().orc_initial_guess(C.byref(cfg), _p(u), float(dt), _p(q0)):
         raise RuntimeError("orc_initial_guess failed")
+    return q0
+
+
+def initial_guess_extrap(cfg: Cfg, u: np.ndarray, dt: float, qprev: np.ndarray, ratio: float) -> np.ndarray:
+    """One element: the extrapolation guess (cfg.guess == GUESS_EXTRAP) from the
+    previous predictor qprev[n, n^d, m] over an interval dt / ratio."""
+    n = cfg.N + 1
+    ns = n ** cfg.dim
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    qprev = np.ascontiguousarray(qprev, dtype=np.float64)
+    assert u.size == ns * cfg.m and qprev.size == n * ns * cfg.m
+    q0 = np.zeros((n, ns, cfg.m))
+    if lib().orc_initial_guess_extrap(C.byref(cfg), _p(u), float(dt), _p(qprev), float(ratio), _p(q0)):
+        raise RuntimeError("orc_initial_guess_extrap failed")
     return q0
 
 

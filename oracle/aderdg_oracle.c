@@ -67,7 +67,9 @@ typedef struct {
     double alpha;     /* CFL coefficient; 0 -> default table (see orc_alpha) */
     int guess;        /* initial guess of the Picard iteration (Sec. 2.2):
                          0 trivial q = u(t^n); 1 second order u + tau L(u);
-                         2 third order u + tau k1 + tau^2 (k2 - k1) / (2 dt) */
+                         2 third order u + tau k1 + tau^2 (k2 - k1) / (2 dt);
+                         3 extrapolation of the previous step's predictor
+                           (orc_run; the first step, and single steps, use 2) */
 } orc_cfg;
 
 /* ------------------------------------------------------------------------ */
@@ -337,7 +339,16 @@ static int make_basis(int N, basis *b)
 int orc_picard_count(const orc_cfg *c)
 {
     if (c->picard != 0) return c->picard;
+    if (c->guess == 3) return 2;  /* a degree-N guess: one iteration, plus one */
     int P = c->N + 1 - (c->guess == 1 ? 1 : c->guess == 2 ? 2 : 0);
+    return P < 1 ? 1 : P;
+}
+
+/* Picard count of a step of the extrapolation guess that has no previous
+ * predictor (it takes the third-order guess and its default count). */
+static int fallback_picard(const orc_cfg *c)
+{
+    int P = c->N + 1 - 2;
     return P < 1 ? 1 : P;
 }
 
@@ -397,15 +408,35 @@ static void l_operator(const orc_cfg *c, const basis *b, const double *w, double
  *   1: q0 = u + tau L(u)                                  (second order)
  *   2: q0 = u + tau k1 + tau^2 (k2 - k1) / (2 dt),
  *      k1 = L(u), k2 = L(u + dt k1)                       (third order)
+ *   3: the previous step's predictor qprev (n time nodes on its interval of
+ *      length dt / ratio) extrapolated in time past its end and shifted to
+ *      start at u:  q0 = u + qprev(1 + xi_t ratio) - qprev(1), the
+ *      polynomials evaluated with the Lagrange basis of the time nodes;
+ *      without qprev, guess 2.
  * gw holds (3 + dim) ns m values. */
 static void initial_guess(const orc_cfg *c, const basis *b, const double *u, double dt, double *q,
-                          double *gw)
+                          double *gw, const double *qprev, double ratio)
 {
     const int n = b->n, ns = ipow(n, c->dim), m = c->m;
     const size_t nsm = (size_t)ns * m;
+    if (c->guess == 3 && qprev) {
+        double L1[ORC_MAXN];
+        orc_lagrange_eval(n, b->x, 1.0, L1);
+        for (int t = 0; t < n; ++t) {
+            double Lt[ORC_MAXN];
+            orc_lagrange_eval(n, b->x, 1.0 + b->x[t] * ratio, Lt);
+            for (size_t i = 0; i < nsm; ++i) {
+                double v = u[i];
+                for (int k = 0; k < n; ++k) v += (Lt[k] - L1[k]) * qprev[(size_t)k * nsm + i];
+                q[(size_t)t * nsm + i] = v;
+            }
+        }
+        return;
+    }
+    const int g = c->guess == 3 ? 2 : c->guess;
     double *k1 = gw, *k2 = gw + nsm, *w = gw + 2 * nsm, *tmp = gw + 3 * nsm;
-    if (c->guess == 1 || c->guess == 2) l_operator(c, b, u, k1, tmp);
-    if (c->guess == 2) {
+    if (g == 1 || g == 2) l_operator(c, b, u, k1, tmp);
+    if (g == 2) {
         for (size_t i = 0; i < nsm; ++i) w[i] = u[i] + dt * k1[i];
         l_operator(c, b, w, k2, tmp);
     }
@@ -413,15 +444,16 @@ static void initial_guess(const orc_cfg *c, const basis *b, const double *u, dou
         const double tau = b->x[t] * dt;
         for (size_t i = 0; i < nsm; ++i) {
             double v = u[i];
-            if (c->guess == 1 || c->guess == 2) v += tau * k1[i];
-            if (c->guess == 2) v += 0.5 * tau * tau * (k2[i] - k1[i]) / dt;
+            if (g == 1 || g == 2) v += tau * k1[i];
+            if (g == 2) v += 0.5 * tau * tau * (k2[i] - k1[i]) / dt;
             q[(size_t)t * nsm + i] = v;
         }
     }
 }
 
 static int predictor_elem(const orc_cfg *c, const basis *b, const double *u, double dt,
-                          double *qhat, double *qbar, double *Fbar, double *work)
+                          double *qhat, double *qbar, double *Fbar, double *work,
+                          const double *qprev, double ratio)
 {
     const int n = b->n, dim = c->dim, m = c->m;
     const int ns = ipow(n, dim), nst = n * ns;
@@ -432,9 +464,9 @@ static int predictor_elem(const orc_cfg *c, const basis *b, const double *u, dou
     double dx[3];
     for (int d = 0; d < dim; ++d) dx[d] = cell_dx(c, d);
 
-    initial_guess(c, b, u, dt, q, work + (size_t)nst * m * (3 + dim));
+    initial_guess(c, b, u, dt, q, work + (size_t)nst * m * (3 + dim), qprev, ratio);
 
-    int P = orc_picard_count(c);
+    int P = (c->guess == 3 && !qprev) ? fallback_picard(c) : orc_picard_count(c);
     int to_conv = P < 0;
     int maxit = to_conv ? 50 : P;
     int it;
@@ -574,9 +606,20 @@ int orc_predictor(const orc_cfg *c, const double *u, double dt, double *qhat,
     if (make_basis(c->N, &b)) return -1;
     double *work = malloc(sizeof(double) * predictor_work_len(c));
     if (!work) return -2;
-    int it = predictor_elem(c, &b, u, dt, qhat, qbar, Fbar, work);
+    int it = predictor_elem(c, &b, u, dt, qhat, qbar, Fbar, work, NULL, 1.0);
     free(work);
     if (iters) *iters = it;
+    return 0;
+}
+
+/* The extrapolation guess alone for one element, from a previous predictor
+ * qprev ([n][n^d][m]) over an interval dt / ratio. */
+int orc_initial_guess_extrap(const orc_cfg *c, const double *u, double dt, const double *qprev, double ratio,
+                             double *q0)
+{
+    basis b;
+    if (c->guess != 3 || make_basis(c->N, &b)) return -1;
+    initial_guess(c, &b, u, dt, q0, NULL, qprev, ratio);
     return 0;
 }
 
@@ -587,7 +630,7 @@ int orc_initial_guess(const orc_cfg *c, const double *u, double dt, double *q0)
     if (make_basis(c->N, &b)) return -1;
     double *gw = malloc(sizeof(double) * (size_t)ipow(c->N + 1, c->dim) * c->m * (3 + c->dim));
     if (!gw) return -2;
-    initial_guess(c, &b, u, dt, q0, gw);
+    initial_guess(c, &b, u, dt, q0, gw, NULL, 1.0);
     free(gw);
     return 0;
 }
@@ -659,7 +702,16 @@ double orc_cfl_dt(const orc_cfg *c, const double *U)
  * on every face, corrector (eq. pde.nc.gw2).  U is overwritten with u^{n+1}.
  * If V_out/qf_out/ff_out are non-NULL, the per-element volume terms and
  * traces are copied there (E n^d m and E 2d n^{d-1} m). */
-int orc_step_ex(const orc_cfg *c, double *U, double dt, double *V_out, double *qf_out, double *ff_out)
+/* Predictors of the previous step, for the extrapolation guess: qhat of
+ * every element ([E][n][n^d][m]) and the step it covered. */
+typedef struct {
+    double *prev, *next;  /* read this step / written this step */
+    double dt_prev;
+    int valid;            /* prev holds a previous step */
+} history;
+
+static int step_impl(const orc_cfg *c, double *U, double dt, double *V_out, double *qf_out, double *ff_out,
+                     history *h)
 {
     basis b;
     if (make_basis(c->N, &b)) return -1;
@@ -684,7 +736,9 @@ int orc_step_ex(const orc_cfg *c, double *U, double dt, double *V_out, double *q
         } else {
 #pragma omp for schedule(static)
             for (long e = 0; e < E; ++e) {
-                predictor_elem(c, &b, &U[(size_t)e * ns * m], dt, NULL, qbar, Fbar, work);
+                const size_t qoff = (size_t)e * n * ns * m;
+                predictor_elem(c, &b, &U[(size_t)e * ns * m], dt, h ? &h->next[qoff] : NULL, qbar, Fbar, work,
+                               (h && h->valid) ? &h->prev[qoff] : NULL, (h && h->valid) ? dt / h->dt_prev : 1.0);
                 volume_elem(c, &b, Fbar, &V[(size_t)e * ns * m]);
                 traces_elem(c, &b, qbar, Fbar, &qf[(size_t)e * fsz], &ff[(size_t)e * fsz]);
             }
@@ -729,6 +783,11 @@ int orc_step_ex(const orc_cfg *c, double *U, double dt, double *V_out, double *q
     return 0;
 }
 
+int orc_step_ex(const orc_cfg *c, double *U, double dt, double *V_out, double *qf_out, double *ff_out)
+{
+    return step_impl(c, U, dt, V_out, qf_out, ff_out, NULL);
+}
+
 int orc_step(const orc_cfg *c, double *U, double dt) { return orc_step_ex(c, U, dt, NULL, NULL, NULL); }
 
 /* Time loop with the CFL step and the clip to t_end:
@@ -740,17 +799,31 @@ int orc_run(const orc_cfg *c, double *U, double t0, double t_end, long max_steps
 {
     double t = t0;
     long k = 0;
+    history hist = {NULL, NULL, 0.0, 0}, *h = NULL;
+    if (c->guess == 3) {  /* the extrapolation guess keeps the predictors */
+        const size_t len = (size_t)n_elems(c) * ipow(c->N + 1, c->dim + 1) * c->m;
+        hist.prev = malloc(sizeof(double) * len);
+        hist.next = malloc(sizeof(double) * len);
+        if (!hist.prev || !hist.next) { free(hist.prev); free(hist.next); return -2; }
+        h = &hist;
+    }
     while (t < t_end && k < max_steps) {
         double dtc = orc_cfl_dt(c, U);
         double dt, tn;
         if (t + dtc >= t_end) { dt = t_end - t; tn = t_end; }
         else { dt = dtc; tn = t + dtc; }
-        int rc = orc_step(c, U, dt);
-        if (rc) return rc;
+        int rc = step_impl(c, U, dt, NULL, NULL, NULL, h);
+        if (rc) { if (h) { free(hist.prev); free(hist.next); } return rc; }
+        if (h) {
+            double *tmp = hist.prev; hist.prev = hist.next; hist.next = tmp;
+            hist.dt_prev = dt;
+            hist.valid = 1;
+        }
         if (dt_hist) dt_hist[k] = dt;
         t = tn;
         ++k;
     }
+    if (h) { free(hist.prev); free(hist.next); }
     if (t_out) *t_out = t;
     if (steps_out) *steps_out = k;
     return 0;
@@ -787,7 +860,7 @@ int orc_step_sampled(const orc_cfg *c, const double *U, double dt, long n_s,
                 ids[0] = e;
                 for (int d = 0; d < dim; ++d) { ids[1 + 2 * d] = neighbour(c, e, d, -1); ids[2 + 2 * d] = neighbour(c, e, d, +1); }
                 for (int k = 0; k < 1 + 2 * dim; ++k) {
-                    predictor_elem(c, &b, &U[(size_t)ids[k] * ns * m], dt, NULL, qbar, Fbar, work);
+                    predictor_elem(c, &b, &U[(size_t)ids[k] * ns * m], dt, NULL, qbar, Fbar, work, NULL, 1.0);
                     if (k == 0) volume_elem(c, &b, Fbar, V);
                     traces_elem(c, &b, qbar, Fbar, &qf[k * fsz], &ff[k * fsz]);
                 }

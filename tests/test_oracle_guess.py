@@ -1,6 +1,7 @@
 """Pins of the oracle's initial guesses of the Picard iteration (Sec. 2.2:
-the second-order guess u + tau L(u) and the third-order guess
-u + tau k1 + tau^2 (k2 - k1) / (2 dt), k1 = L(u), k2 = L(u + dt k1)).
+the second-order guess u + tau L(u), the third-order guess
+u + tau k1 + tau^2 (k2 - k1) / (2 dt), k1 = L(u), k2 = L(u + dt k1), and
+the extrapolation of the previous step's predictor).
 
 For linear advection u_t + a.grad u = 0 the exact solution is
 u0(x - a t), and L(u) = -a.grad u is exact on polynomial data, so each
@@ -142,3 +143,92 @@ def test_third_order_guess_design_order(N):
         U1, t, _, _ = oracle.run(cfg, inputs.euler_density_wave(X, L=1.0), t_end=0.2)
         errs.append(l2_abs(cfg, U1, inputs.euler_density_wave(X, L=1.0, t=t))[0])
     assert order(*errs) > N + 1 - 0.5, errs
+
+
+# ---- extrapolation of the previous step's predictor (Sec. 2.2) ----------------
+
+def _prev_interval(cfg, coef, a, dt_prev):
+    """Exact q at the time nodes of the previous interval [-dt_prev, 0]."""
+    n = cfg.N + 1
+    X = oracle.node_coords(cfg)[0]
+    tau, _ = oracle.gauss_legendre(n)
+    return np.stack([_eval(coef, X - np.asarray(a)[None, :] * ((-1.0 + t) * dt_prev)) for t in tau])[:, :, None]
+
+
+@pytest.mark.parametrize("dim,N,ratio", [(1, 3, 1.0), (1, 4, 0.7), (2, 3, 1.3)])
+def test_extrapolation_guess_is_exact_for_polynomials_in_time(dim, N, ratio):
+    """Linear advection of a polynomial of degree <= N: the solution is a
+    polynomial of degree <= N in time, so extrapolating its interpolant on
+    the previous interval reproduces it on the next one."""
+    a = [1.7, -0.6][:dim]
+    cfg = oracle.make_cfg(dim, [4] * dim, [0.0] * dim, [1.0] * dim, N, oracle.PDE_ADVECTION, a,
+                          guess=oracle.GUESS_EXTRAP)
+    coef = _poly(dim, N, seed=30 + N)
+    dt = 0.04
+    ex, X, _ = _space_time(cfg, coef, a, dt)
+    qprev = _prev_interval(cfg, coef, a, dt / ratio)
+    q0 = oracle.initial_guess_extrap(cfg, _eval(coef, X)[:, None], dt, qprev, ratio)
+    np.testing.assert_allclose(q0, ex, rtol=0, atol=1e-11)
+
+
+def test_extrapolation_guess_misses_the_nodal_polynomial():
+    """u0 = x^{N+1}: in time the solution (x - a t)^{N+1} has leading
+    coefficient c = (-a)^{N+1}; interpolation on the previous interval's
+    nodes tau_k misses c w(tau), w(tau) = prod_k (tau - tau_k), and the
+    shift to u at tau = 0 removes w(0): q0 - exact = -c (w(tau) - w(0))."""
+    N, a, dt, ratio = 3, 1.3, 0.05, 0.8
+    cfg = oracle.make_cfg(1, [3], [0.0], [1.0], N, oracle.PDE_ADVECTION, [a], guess=oracle.GUESS_EXTRAP)
+    coef = {(N + 1,): 1.0}
+    ex, X, tau = _space_time(cfg, coef, [a], dt)
+    dtp = dt / ratio
+    qprev = _prev_interval(cfg, coef, [a], dtp)
+    q0 = oracle.initial_guess_extrap(cfg, _eval(coef, X)[:, None], dt, qprev, ratio)
+    nodes = -dtp + tau * dtp
+    w = lambda s: np.prod(s - nodes)
+    c = (-a) ** (N + 1)
+    want = np.array([-c * (w(t * dt) - w(0.0)) for t in tau])
+    np.testing.assert_allclose((q0 - ex)[:, :, 0], np.broadcast_to(want[:, None], (N + 1, N + 1)),
+                               rtol=1e-9, atol=1e-14)
+
+
+def test_extrapolation_first_step_is_the_third_order_guess():
+    """A single step has no previous predictor: guess 3 falls back to the
+    third-order guess with its default count (bitwise)."""
+    cfg = euler_cfg((5, 4), N=4, L=2.0)
+    X = oracle.node_coords(cfg)
+    U = inputs.smooth_random_state(oracle.PDE_EULER, X, [2.0, 2.0], seed=8)
+    dt = oracle.cfl_dt(cfg, U)
+    cfg.guess = oracle.GUESS_EXTRAP
+    a = oracle.step(cfg, U, dt)
+    cfg.guess = oracle.GUESS_ORDER3
+    b = oracle.step(cfg, U, dt)
+    np.testing.assert_array_equal(a, b)
+    cfg.guess = oracle.GUESS_EXTRAP
+    assert oracle.lib().orc_picard_count(cfg) == 2
+
+
+@pytest.mark.parametrize("N", [3, 4])
+def test_extrapolation_guess_design_order(N):
+    """Euler density wave, extrapolation guess and one Picard iteration per
+    step: design order N+1."""
+    errs = []
+    for c in (8, 16):
+        cfg = euler_cfg((c, c), N=N, L=1.0, picard=1)
+        cfg.guess = oracle.GUESS_EXTRAP
+        X = oracle.node_coords(cfg)
+        U1, t, _, _ = oracle.run(cfg, inputs.euler_density_wave(X, L=1.0), t_end=0.2)
+        errs.append(l2_abs(cfg, U1, inputs.euler_density_wave(X, L=1.0, t=t))[0])
+    assert order(*errs) > N + 1 - 0.5, errs
+
+
+def test_extrapolation_guess_vortex_error_matches_trivial():
+    """Isentropic vortex, N = 4: one Picard iteration after the extrapolation
+    guess gives the trivial guess's L2 error within 0.1 %."""
+    errs = []
+    for guess, picard in ((oracle.GUESS_TRIVIAL, 0), (oracle.GUESS_EXTRAP, 1)):
+        cfg = euler_cfg((20, 20), N=4, L=10.0, picard=picard)
+        cfg.guess = guess
+        X = oracle.node_coords(cfg)
+        U1, t, _, _ = oracle.run(cfg, inputs.euler_vortex(X), t_end=0.5)
+        errs.append(l2_abs(cfg, U1, inputs.euler_vortex(X, t=t))[0])
+    assert abs(errs[1] - errs[0]) <= 1e-3 * errs[0], errs
