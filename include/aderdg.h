@@ -85,13 +85,22 @@ extern "C" {
  * ORDER2   q0 = u + tau L(u)                              (second order)
  * ORDER3   q0 = u + tau k1 + tau^2 (k2 - k1) / (2 dt),    (third order)
  *          k1 = L(u), k2 = L(u + dt k1)
+ * EXTRAP   the previous step's predictor q_prev, extrapolated in time
+ *          past its interval and shifted to start at u:
+ *          q0(t^n + tau) = u + q_prev(1 + tau / dt_prev) - q_prev(1)
+ *          (time in units of the previous step).  A step without a
+ *          previous predictor (the first after aderdg_set_state, or a
+ *          predictor call with an explicit dt) takes ORDER3 with its
+ *          default count.  Holds n^(d+1) m values per element more.
  * with tau = t - t^n and L(w) = -div F(w), the element-local nodal
  * derivative of the flux.  The default Picard count after a guess of
  * degree k in time is max(1, N + 1 - k): N+1 for TRIVIAL, N for ORDER2,
- * N-1 for ORDER3 (the paper notes N - k iterations suffice). */
+ * N-1 for ORDER3 (the paper notes N - k iterations suffice), and 2 for
+ * EXTRAP (degree N). */
 #define ADERDG_GUESS_TRIVIAL 0
 #define ADERDG_GUESS_ORDER2 1
 #define ADERDG_GUESS_ORDER3 2
+#define ADERDG_GUESS_EXTRAP 3
 
 /* ---- tile shapes -------------------------------------------------------
  * The predictor is compiled in ADERDG_NUM_PRED_SHAPES launch variants and

@@ -158,6 +158,10 @@ void fill_typed(const Basis &b, Ops<T> &o)
         o.inv_w[t] = T(b.inv_w[t]);
         o.xi[t] = T(b.x[t]);
         o.hxi2[t] = T(0.5 * b.x[t] * b.x[t]);
+        double prod = 1.0;
+        for (int j = 0; j < n; ++j)
+            if (j != t) prod *= b.x[t] - b.x[j];
+        o.bw[t] = T(1.0 / prod);
     }
 }
 }  // namespace
@@ -202,6 +206,7 @@ void fill_pde_consts(int kind, PdeParams &P)
 
 int default_picard(int N, int guess)
 {
+    if (guess == 3) return 2;  // a degree-N guess: one iteration, plus one
     const int k = guess == 1 ? 1 : (guess == 2 ? 2 : 0);
     return N + 1 - k < 1 ? 1 : N + 1 - k;
 }

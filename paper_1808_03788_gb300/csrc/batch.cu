@@ -104,6 +104,7 @@ struct Slot {
     double *u = nullptr;
     void *V = nullptr, *tr = nullptr;
     double *ref = nullptr;
+    void *qprev = nullptr;     // extrapolation guess: last predictor
     int ctl_index = -1;
     // placement in the current group arrays (for k_cfl)
     int group = -1, member = -1;
@@ -113,7 +114,7 @@ size_t slot_bytes(const Slot &s)
 {
     const size_t ns = (size_t)s.E * s.NS * s.M;
     return a256(ns * 8) + a256(ns * s.ks->elem_bytes) + a256((size_t)s.E * s.NREC * s.ks->rs * s.ks->elem_bytes) +
-           a256((size_t)s.E * s.ks->rf * 8);
+           a256((size_t)s.E * s.ks->rf * 8) + (s.guess == ADERDG_GUESS_EXTRAP ? a256(ns * (s.N + 1) * s.ks->elem_bytes) : 0);
 }
 
 int make_slot(const aderdg_solve_spec_t &sp, int prec, int guess, int picard, double alpha, Slot &s)
@@ -125,7 +126,7 @@ int make_slot(const aderdg_solve_spec_t &sp, int prec, int guess, int picard, do
     const KernelSet *ks = kernels_for(sp.pde.kind, m.dim, sp.N, prec);
     if (!ks) return fail(ADERDG_E_UNSUPPORTED, "no kernels compiled for this (pde, dim, N)");
     if (sp.pde.kind == ADERDG_PDE_EULER && !(sp.pde.p[0] > 1.0)) return fail(ADERDG_E_INVAL, "gamma must be > 1");
-    if (guess < ADERDG_GUESS_TRIVIAL || guess > ADERDG_GUESS_ORDER3) return fail(ADERDG_E_INVAL, "bad initial guess");
+    if (guess < ADERDG_GUESS_TRIVIAL || guess > ADERDG_GUESS_EXTRAP) return fail(ADERDG_E_INVAL, "bad initial guess");
     s = Slot();
     s.pde = sp.pde.kind;
     s.dim = m.dim;
@@ -169,6 +170,7 @@ __global__ void k_set_tend(Control *const *ctls, const double *t_end, int count)
 
 struct Group {
     int pde = 0, dim = 0, N = 0, prec = 0;
+    bool extrap = false;  // its solves use the extrapolation guess (predictor variant)
     PdeParams pp{};
     const KernelSet *ks = nullptr;  // compiled kernels of the group
     KernelSet kso{};                // the same with the tile shapes in use
@@ -184,7 +186,7 @@ struct Group {
 bool same_group(const Group &g, const Slot &s)
 {
     return g.ks == s.ks && g.pde == s.pde && g.dim == s.dim && g.N == s.N && g.prec == s.prec &&
-           std::memcmp(&g.pp, &s.pp, sizeof(PdeParams)) == 0;
+           g.extrap == (s.guess == ADERDG_GUESS_EXTRAP) && std::memcmp(&g.pp, &s.pp, sizeof(PdeParams)) == 0;
 }
 
 class Engine {
@@ -253,10 +255,10 @@ public:
         s->u = reinterpret_cast<double *>(b);
         s->V = b + a256(ns * 8);
         s->tr = b + a256(ns * 8) + a256(ns * s->ks->elem_bytes);
-        s->ref = s->ks->rf > 0
-                     ? reinterpret_cast<double *>(b + a256(ns * 8) + a256(ns * s->ks->elem_bytes) +
-                                                  a256((size_t)s->E * s->NREC * s->ks->rs * s->ks->elem_bytes))
-                     : nullptr;
+        const size_t o_ref = a256(ns * 8) + a256(ns * s->ks->elem_bytes) +
+                             a256((size_t)s->E * s->NREC * s->ks->rs * s->ks->elem_bytes);
+        s->ref = s->ks->rf > 0 ? reinterpret_cast<double *>(b + o_ref) : nullptr;
+        s->qprev = s->guess == ADERDG_GUESS_EXTRAP ? b + o_ref + a256((size_t)s->E * s->ks->rf * 8) : nullptr;
         s->ctl_index = ctl_free.back();
         ctl_free.pop_back();
         Control c;
@@ -296,6 +298,7 @@ public:
             if (gi < 0) {
                 Group g;
                 g.pde = s->pde; g.dim = s->dim; g.N = s->N; g.prec = s->prec; g.pp = s->pp; g.ks = s->ks;
+                g.extrap = s->guess == ADERDG_GUESS_EXTRAP;
                 ng.push_back(g);
                 gi = (int)ng.size() - 1;
             }
@@ -306,7 +309,7 @@ public:
         // tile shapes per group (may autotune on first use of a key)
         for (Group &g : ng) {
             const int rc = resolve_shapes(g.ks, g.pde, g.dim, g.N, g.prec, g.pp, pred_req, corr_req,
-                                          tune_cache.empty() ? nullptr : tune_cache.c_str(), &g.kso);
+                                          tune_cache.empty() ? nullptr : tune_cache.c_str(), g.extrap, &g.kso);
             if (rc) return rc;
         }
         // reuse device descriptor arrays of old groups where possible
@@ -328,6 +331,8 @@ public:
                 fill_desc_spacing(d);
                 d.picard = s->picard;
                 d.guess = s->guess;
+                d.picard_first = default_picard(s->N, ADERDG_GUESS_ORDER3);
+                d.qprev = s->qprev;
                 d.u = s->u;
                 d.u_out = s->u;
                 d.V = s->V;
@@ -805,7 +810,7 @@ int aderdg_server_create(const aderdg_server_config_t *cfg, aderdg_server_t **ou
         return fail(ADERDG_E_INVAL, "bad tile shape request");
     }
     s->guess = cfg ? cfg->initial_guess : ADERDG_GUESS_TRIVIAL;
-    if (s->guess < ADERDG_GUESS_TRIVIAL || s->guess > ADERDG_GUESS_ORDER3) {
+    if (s->guess < ADERDG_GUESS_TRIVIAL || s->guess > ADERDG_GUESS_EXTRAP) {
         delete s;
         return fail(ADERDG_E_INVAL, "bad initial guess");
     }

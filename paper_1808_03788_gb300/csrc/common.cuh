@@ -37,6 +37,7 @@ struct Control {
     double t;          // time of the state after the step in flight
     double t_end;
     double dt;         // dt of the step in flight (0: no step)
+    double dt_prev;    // dt of the step before it (0: none; extrapolation guess)
     double alpha;
     double inv_dx[3];
     int dim;
@@ -82,6 +83,7 @@ struct Ops {
     T w[NMAX], F0[NMAX], F1[NMAX], inv_w[NMAX];
     T xi[NMAX];            // time nodes on [0, 1] (initial guesses)
     T hxi2[NMAX];          // xi^2 / 2
+    T bw[NMAX];            // barycentric weights 1 / prod_{j != k} (xi_k - xi_j)
 };
 
 // One solve of a launch (device memory).  Tiles of EPB consecutive
@@ -93,7 +95,9 @@ struct SolveDesc {
     long long tile0_p, tile0_c;
     int cells[3];
     int picard;        // Picard iterations after the initial guess
-    int guess;         // initial guess: 0 trivial, 1 second order, 2 third order (Sec. 2.2)
+    int picard_first;  // extrapolation guess: iterations of a step without a previous predictor
+    int guess;         // initial guess: 0 trivial, 1 second order, 2 third order,
+                       // 3 extrapolation of the previous predictor (Sec. 2.2)
     double inv_dx[3];
     float inv_dx_f[3]; // 1/dx_d and dx_0/dx_d in FP32 (precomputed on the host)
     float ratio_f[3];
@@ -102,6 +106,7 @@ struct SolveDesc {
     void *V;           // volume term          [E][NS][M] of T
     void *tr;          // trace records        [E][DIM][2][NF][RS] of T
     double *ref;       // FP32 path: reference state per element [E][M]; unused in FP64
+    void *qprev;       // extrapolation guess: last predictor [E][n][NS][M] of T
     Control *ctl;
 };
 
@@ -359,15 +364,16 @@ struct KernelSet {
     int nvar, rs, elem_bytes;  // elem_bytes = sizeof(T)
     int flux_flops, eig_flops;  // per point, for the cost model
     int rf;                     // doubles per element of the FP32 reference record (0: none)
-    TileShape pshape[NSHAPE_P], cshape[NSHAPE_C];
+    TileShape pshape[NSHAPE_P], pshape_ex[NSHAPE_P], cshape[NSHAPE_C];  // pshape_ex: extrapolation guess
     int pred_shape, corr_shape;  // indices of the shapes in use
 };
 
-// Copy of ks that launches predictor shape ps and corrector shape cs.
-inline KernelSet with_shapes(const KernelSet &ks, int ps, int cs)
+// Copy of ks that launches predictor shape ps (its extrapolation-guess
+// variant if ex) and corrector shape cs.
+inline KernelSet with_shapes(const KernelSet &ks, int ps, int cs, bool ex = false)
 {
     KernelSet k = ks;
-    const TileShape &p = ks.pshape[ps], &c = ks.cshape[cs];
+    const TileShape &p = ex ? ks.pshape_ex[ps] : ks.pshape[ps], &c = ks.cshape[cs];
     k.predictor = p.kernel; k.pred_threads = p.threads; k.pred_epb = p.epb; k.pred_smem = p.smem;
     k.corrector = c.kernel; k.corr_threads = c.threads; k.corr_epb = c.epb; k.corr_smem = c.smem;
     k.pred_shape = ps;

@@ -203,13 +203,33 @@ struct PredCfg {
     // resident CTAs per SM for the launch bounds: the register cap per
     // thread of shape 0 (65536 / (THREADS0 MINB0)) is kept
     static constexpr int MINB = cmax(1, cmin(2048 / THREADS, (THREADS0 * MINB0) / THREADS));
-    static constexpr int SHARED = round_up(DIM * n * n + 2 * n + 1, 4);  // Kw, F0, F1, dt/dx
+    static constexpr int SHARED = round_up(DIM * n * n + 2 * n + 1 + n * n, 4);  // Kw, F0, F1, dt/dx, W
     static constexpr size_t BYTES = sizeof(T) * (size_t)(SHARED + EPB * ELEM);
     // FP32 path: perturbation form about the element's node SREF
     static constexpr bool DELTA = sizeof(T) == 4;
     static constexpr int SREF = NS / 2;
     static constexpr int RF = M;  // reference record: q_ref
 };
+
+// Weights of the extrapolation guess: W[t][k] = L_k(1 + xi_t r) - L_k(1),
+// L_k the Lagrange basis of the time nodes (barycentric weights bw), r =
+// dt / dt_prev.  One thread; compile-time indices into the operator table.
+template <typename T, int n>
+__device__ __forceinline__ void extrap_weights(const Ops<T> &O, T r, T *W)
+{
+#pragma unroll
+    for (int t = 0; t < n; ++t) {
+        const T x = T(1) + O.xi[t] * r;
+#pragma unroll
+        for (int k = 0; k < n; ++k) {
+            T L = O.bw[k];
+#pragma unroll
+            for (int j = 0; j < n; ++j)
+                if (j != k) L *= x - O.xi[j];
+            W[t * n + k] = L - O.F1[k];
+        }
+    }
+}
 
 // -Dhat F_d along direction D on pencil (t, p), in place.
 template <class C, int D, typename T>
@@ -292,7 +312,9 @@ __device__ __forceinline__ void gather_R(const T *ebuf, int t, int s, const T *r
     }
 }
 
-template <class PDE, int DIM, int N, typename T, int TS>
+// EX: the variant that serves the extrapolation guess (guess 3); solves with
+// other guesses use EX = false, which carries no code (or registers) for it.
+template <class PDE, int DIM, int N, typename T, int TS, bool EX>
 __global__ void __launch_bounds__(PredCfg<PDE, DIM, N, T, TS>::THREADS, PredCfg<PDE, DIM, N, T, TS>::MINB)
 k_predictor(const KParams P)
 {
@@ -306,6 +328,7 @@ k_predictor(const KParams P)
     T *sF0 = sKw + DIM * n * n;
     T *sF1 = sF0 + n;
     T *sDt = sF1 + n;                          // dt / dx_0 of the current tile
+    T *sW = sDt + 1;                           // extrapolation weights [t][k] of the tile
     const int tid = threadIdx.x;
     const bool act = tid < EPB * NS;
     const int g = act ? tid / NS : 0;
@@ -388,11 +411,37 @@ k_predictor(const KParams P)
 
         T q[n][M];
         int it0;  // Picard iterations already taken
-        {
+        int P_it = S.picard;
+        bool extrap = false;
+        if constexpr (EX) extrap = S.guess == 3 && P.use_ctl_dt && S.ctl->dt_prev > 0.0;
+        if (extrap) {
+            // extrapolation of the previous step's predictor (Sec. 2.2):
+            // q[t] = u + sum_k (L_k(1 + xi_t dt/dt_prev) - L_k(1)) qprev[k]
+            if (tid == 0) extrap_weights<T, n>(O, T(dt / S.ctl->dt_prev), sW);
+            __syncthreads();
+            const T *qp = reinterpret_cast<const T *>(S.qprev) + ec * (n * NS * M);
+#pragma unroll
+            for (int t = 0; t < n; ++t)
+#pragma unroll
+                for (int v = 0; v < M; ++v) q[t][v] = u[v];
+#pragma unroll 1
+            for (int k = 0; k < n; ++k) {  // one previous time level at a time
+                T qk[M];
+                NodeIO<T, M>::load(qp + (k * NS + s) * M, qk);
+#pragma unroll
+                for (int t = 0; t < n; ++t) {
+                    const T wk = sW[t * n + k];
+#pragma unroll
+                    for (int v = 0; v < M; ++v) q[t][v] += wk * qk[v];
+                }
+            }
+            it0 = 0;
+        } else {
             T R1[M];
             spatial_R(u, R1);
             const T dtT = sDt[0];
-            if (S.guess == 2) {
+            if (S.guess == 3) P_it = S.picard_first;  // no previous predictor: the third-order guess
+            if (S.guess == 2 || S.guess == 3) {
                 // third-order guess (Sec. 2.2): q = u + tau k1 + tau^2 (k2 - k1) / (2 dt),
                 // tau = xi dt, k1 = L(u), k2 = L(u + dt k1)
                 T w[M], R2[M];
@@ -423,7 +472,7 @@ k_predictor(const KParams P)
             }
         }
         // ---- Picard iterations of eq. pde.st2 ------------------------------
-        for (int it = it0; it < S.picard; ++it) {
+        for (int it = it0; it < P_it; ++it) {
 #pragma unroll
             for (int t = 0; t < n; ++t) {
                 T F[DIM][M];
@@ -452,6 +501,14 @@ k_predictor(const KParams P)
                     }
             }
             __syncthreads();
+        }
+
+        if constexpr (EX) {
+            if (S.guess == 3 && valid) {  // this step's predictor, for the next step's guess
+                T *qp = reinterpret_cast<T *>(S.qprev) + ec * (n * NS * M);
+#pragma unroll
+                for (int t = 0; t < n; ++t) NodeIO<T, M>::store(qp + (t * NS + s) * M, q[t]);
+            }
         }
 
         // ---- time averages qbar, Fbar_d (registers) ------------------------
@@ -954,19 +1011,19 @@ struct KS {
 // Predictor shapes: 0-2 k_predictor with CTAs of the default, half and
 // double size; 3-4 the plane-owning k_predictor_xt (about 128 and 256
 // threads) where it applies (2D FP32, small planes), else shapes 0 and 2.
-template <class PDE, int DIM, int N, typename T, int TS>
+template <class PDE, int DIM, int N, typename T, int TS, bool EX = false>
 constexpr TileShape pred_shape()
 {
     if constexpr (TS >= 3) {
         if constexpr (DIM == 2 && sizeof(T) == 4 && use_xt<PDE, N>()) {
             using C = PredXtCfg<PDE, N, TS == 3 ? 0 : 2>;
-            return TileShape{&k_predictor_xt<PDE, N, TS == 3 ? 0 : 2>, C::THREADS, C::EPB, C::BYTES};
+            return TileShape{&k_predictor_xt<PDE, N, TS == 3 ? 0 : 2, EX>, C::THREADS, C::EPB, C::BYTES};
         } else {
-            return pred_shape<PDE, DIM, N, T, TS == 3 ? 0 : 2>();
+            return pred_shape<PDE, DIM, N, T, TS == 3 ? 0 : 2, EX>();
         }
     } else {
         using C = PredCfg<PDE, DIM, N, T, TS>;
-        return TileShape{&k_predictor<PDE, DIM, N, T, TS>, C::THREADS, C::EPB, C::BYTES};
+        return TileShape{&k_predictor<PDE, DIM, N, T, TS, EX>, C::THREADS, C::EPB, C::BYTES};
     }
 }
 
@@ -988,6 +1045,9 @@ const KernelSet KS<PDE, DIM, N, T>::value = {
     PredCfg<PDE, DIM, N, T>::DELTA ? PredCfg<PDE, DIM, N, T>::RF : 0,
     {pred_shape<PDE, DIM, N, T, 0>(), pred_shape<PDE, DIM, N, T, 1>(), pred_shape<PDE, DIM, N, T, 2>(),
      pred_shape<PDE, DIM, N, T, 3>(), pred_shape<PDE, DIM, N, T, 4>()},
+    {pred_shape<PDE, DIM, N, T, 0, true>(), pred_shape<PDE, DIM, N, T, 1, true>(),
+     pred_shape<PDE, DIM, N, T, 2, true>(), pred_shape<PDE, DIM, N, T, 3, true>(),
+     pred_shape<PDE, DIM, N, T, 4, true>()},
     {corr_shape<PDE, DIM, N, T, 0>(), corr_shape<PDE, DIM, N, T, 1>(), corr_shape<PDE, DIM, N, T, 2>()},
     0, 0};
 

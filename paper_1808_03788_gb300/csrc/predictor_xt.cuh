@@ -32,8 +32,9 @@ struct PredXtCfg {
     // per element: the F_y / R_y field [t][y][x][v]; its size is padded to
     // 16 mod 128 bytes so that neighbouring elements start on other banks
     static constexpr int ELEM = round_up(NST * M, 32) + 4;
-    // per CTA: dt / dx_0, then Kw and the face values (rows indexed by y)
-    static constexpr int HEAD = round_up(1 + n * n + 2 * n, 4);
+    // per CTA: dt / dx_0, then Kw and the face values (rows indexed by y),
+    // the extrapolation weights [t][k]
+    static constexpr int HEAD = round_up(1 + n * n + 2 * n + n * n, 4);
     static constexpr size_t BYTES = sizeof(float) * ((size_t)HEAD + (size_t)EPB * ELEM);
     static constexpr int SREF = NS / 2;
     static constexpr int RF = M;
@@ -80,7 +81,7 @@ __device__ __forceinline__ void xt_contract_x(const float (*F)[M], float (*R)[M]
         }
 }
 
-template <class PDE, int N, int TS>
+template <class PDE, int N, int TS, bool EX>
 __global__ void __launch_bounds__(PredXtCfg<PDE, N, TS>::THREADS, PredXtCfg<PDE, N, TS>::MINB)
 k_predictor_xt(const KParams P)
 {
@@ -96,6 +97,7 @@ k_predictor_xt(const KParams P)
     float *sKw = sHead + 1;           // Kw [k][j]
     float *sF0 = sKw + n * n;         // face values at xi = 0 and 1
     float *sF1 = sF0 + n;
+    float *sW = sF1 + n;              // extrapolation weights of the tile
     const int tid = threadIdx.x;
     const bool act = tid < EPB * n;
     const int g = act ? tid / n : 0;
@@ -170,10 +172,40 @@ k_predictor_xt(const KParams P)
 
         float A[n][n][M];  // [t][x][v]: q, then F_x and R in place
         int it0;
-        {
+        int P_it = S.picard;
+        bool extrap = false;
+        if constexpr (EX) extrap = S.guess == 3 && P.use_ctl_dt && S.ctl->dt_prev > 0.0;
+        if (extrap) {
+            // extrapolation of the previous step's predictor (Sec. 2.2)
+            if (tid == 0) extrap_weights<float, n>(O, float(dt / S.ctl->dt_prev), sW);
+            __syncthreads();
+            const float *qp = reinterpret_cast<const float *>(S.qprev) + ec * (n * NS * M);
+#pragma unroll
+            for (int t = 0; t < n; ++t)
+#pragma unroll
+                for (int x = 0; x < n; ++x)
+#pragma unroll
+                    for (int v = 0; v < M; ++v) A[t][x][v] = u[x][v];
+#pragma unroll 1
+            for (int k = 0; k < n; ++k) {  // one previous time level at a time
+#pragma unroll
+                for (int x = 0; x < n; ++x) {
+                    float qk[M];
+                    IO::load(qp + (k * NS + y * n + x) * M, qk);
+#pragma unroll
+                    for (int t = 0; t < n; ++t) {
+                        const float wk = sW[t * n + k];
+#pragma unroll
+                        for (int v = 0; v < M; ++v) A[t][x][v] += wk * qk[v];
+                    }
+                }
+            }
+            it0 = 0;
+        } else {
             float R1[n][M];
             spatial_R(u, R1);
-            if (S.guess == 2) {
+            if (S.guess == 3) P_it = S.picard_first;  // no previous predictor: the third-order guess
+            if (S.guess == 2 || S.guess == 3) {
                 float w[n][M], R2[n][M];
 #pragma unroll
                 for (int x = 0; x < n; ++x)
@@ -208,7 +240,7 @@ k_predictor_xt(const KParams P)
         }
 
         // ---- Picard iterations of eq. pde.st2 ------------------------------
-        for (int it = it0; it < S.picard; ++it) {
+        for (int it = it0; it < P_it; ++it) {
 #pragma unroll
             for (int t = 0; t < n; ++t) {
                 float Fx[n][M];
@@ -255,6 +287,16 @@ k_predictor_xt(const KParams P)
                         for (int tp = 1; tp < n; ++tp) acc += O.iK1W[t * n + tp] * Rc[tp][v];
                         A[t][x][v] = u[x][v] + dtT * acc;
                     }
+            }
+        }
+
+        if constexpr (EX) {
+            if (S.guess == 3 && valid) {  // this step's predictor, for the next step's guess
+                float *qp = reinterpret_cast<float *>(S.qprev) + ec * (n * NS * M);
+#pragma unroll
+                for (int t = 0; t < n; ++t)
+#pragma unroll
+                    for (int x = 0; x < n; ++x) IO::store(qp + (t * NS + y * n + x) * M, A[t][x]);
             }
         }
 

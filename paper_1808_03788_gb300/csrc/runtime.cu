@@ -164,6 +164,7 @@ struct aderdg_s {
     Control *ctl = nullptr;
     double *scratch = nullptr;  // mass partials + small outputs
     double *ref = nullptr;      // FP32 path: per-element reference records
+    void *qprev = nullptr;      // extrapolation guess: last predictor [E][n][NS][M]
     double *host_pinned = nullptr;
     KParams kp{};
     Basis basis{};
@@ -272,7 +273,8 @@ void fill_cost(const aderdg_t *h, aderdg_info_t *info)
     const double itk = NST * FF + D * NS * M * 2 * n * n + NST * M * (D - 1) + NS * M * n * (2 * n + 2);
     const double fin = NST * FF + (1 + D) * NST * M * 2 + NS * M * D * 2 * n + NREC * M * 4 * n + NREC * EF;
     double pred;
-    if (h->guess == 2) pred = 2 * it1 + 2 * NS * M + P * itk + fin;  // it1 counts 3 flops per q value, the
+    if (h->guess == 3) pred = NST * M * 2 * n + P * itk + fin;  // steady state (a previous predictor)
+    else if (h->guess == 2) pred = 2 * it1 + 2 * NS * M + P * itk + fin;  // it1 counts 3 flops per q value, the
                                                                      // Taylor form 6 over two evaluations
     else if (h->guess == 1) pred = it1 + P * itk + fin;
     else pred = it1 + (P - 1) * itk + fin;
@@ -346,7 +348,7 @@ int aderdg_create(const aderdg_mesh_t *mesh, int N, int nVar, const aderdg_pde_t
     h->pde = pde->kind;
     h->precision = prec;
     h->guess = cfg ? cfg->initial_guess : ADERDG_GUESS_TRIVIAL;
-    if (h->guess < ADERDG_GUESS_TRIVIAL || h->guess > ADERDG_GUESS_ORDER3) {
+    if (h->guess < ADERDG_GUESS_TRIVIAL || h->guess > ADERDG_GUESS_EXTRAP) {
         delete h;
         return fail(ADERDG_E_INVAL, "bad initial guess");
     }
@@ -361,7 +363,8 @@ int aderdg_create(const aderdg_mesh_t *mesh, int N, int nVar, const aderdg_pde_t
         for (int i = 0; i < 8; ++i) pp.p[i] = pde->p[i];
         fill_pde_consts(pde->kind, pp);
         const int rc = resolve_shapes(ks, pde->kind, mesh->dim, N, prec, pp, cfg ? cfg->pred_shape : 0,
-                                      cfg ? cfg->corr_shape : 0, cfg ? cfg->tune_cache : nullptr, &h->kso);
+                                      cfg ? cfg->corr_shape : 0, cfg ? cfg->tune_cache : nullptr,
+                                      h->guess == ADERDG_GUESS_EXTRAP, &h->kso);
         if (rc) { delete h; return rc; }
     }
     h->ks = ks = &h->kso;
@@ -393,7 +396,9 @@ int aderdg_create(const aderdg_mesh_t *mesh, int N, int nVar, const aderdg_pde_t
     h->scratch = (double *)dev_alloc(h, sizeof(double) * (MASS_BLOCKS * 9 + 64));
     h->d_desc = (SolveDesc *)dev_alloc(h, sizeof(SolveDesc));
     if (ks->rf > 0) h->ref = (double *)dev_alloc(h, sizeof(double) * (size_t)E * ks->rf);
-    if (!h->u || !h->V || !h->tr || !h->ctl || !h->scratch || !h->d_desc || (ks->rf > 0 && !h->ref)) {
+    if (h->guess == ADERDG_GUESS_EXTRAP) h->qprev = dev_alloc(h, nstate * h->n * ks->elem_bytes);
+    if (!h->u || !h->V || !h->tr || !h->ctl || !h->scratch || !h->d_desc || (ks->rf > 0 && !h->ref) ||
+        (h->guess == ADERDG_GUESS_EXTRAP && !h->qprev)) {
         aderdg_destroy(h);
         return fail(ADERDG_E_NOMEM, "device allocation failed");
     }
@@ -414,6 +419,8 @@ int aderdg_create(const aderdg_mesh_t *mesh, int N, int nVar, const aderdg_pde_t
     fill_desc_spacing(sd);
     sd.picard = h->picard;
     sd.guess = h->guess;
+    sd.picard_first = default_picard(N, ADERDG_GUESS_ORDER3);
+    sd.qprev = h->qprev;
     sd.u = h->u;
     sd.u_out = h->u;
     sd.V = h->V;
@@ -458,6 +465,7 @@ int aderdg_destroy(aderdg_t *h)
     dev_free(h, h->scratch);
     dev_free(h, h->d_desc);
     dev_free(h, h->ref);
+    dev_free(h, h->qprev);
     if (h->host_pinned) cudaFreeHost(h->host_pinned);
     for (auto &e : h->ev)
         if (e) cudaEventDestroy(e);

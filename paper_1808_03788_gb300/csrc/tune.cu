@@ -295,7 +295,7 @@ int tuned(const KernelSet *ks, int pde, int dim, int N, int prec, const PdeParam
 namespace aderdg {
 
 int resolve_shapes(const KernelSet *ks, int pde, int dim, int N, int prec, const PdeParams &pp, int pred_req,
-                   int corr_req, const char *cache, KernelSet *out)
+                   int corr_req, const char *cache, bool extrap, KernelSet *out)
 {
     if (!valid_shape_requests(pred_req, corr_req)) return fail(ADERDG_E_INVAL, "bad tile shape request");
     Choice c{pred_req, corr_req};
@@ -306,8 +306,8 @@ int resolve_shapes(const KernelSet *ks, int pde, int dim, int N, int prec, const
         if (pred_req == ADERDG_SHAPE_AUTOTUNE) c.pred = t.pred;
         if (corr_req == ADERDG_SHAPE_AUTOTUNE) c.corr = t.corr;
     }
-    *out = with_shapes(*ks, c.pred, c.corr);
-    int rc = opt_in(ks->pshape[c.pred]);
+    *out = with_shapes(*ks, c.pred, c.corr, extrap);
+    int rc = opt_in(extrap ? ks->pshape_ex[c.pred] : ks->pshape[c.pred]);
     if (!rc) rc = opt_in(ks->cshape[c.corr]);
     return rc;
 }

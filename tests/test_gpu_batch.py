@@ -231,7 +231,8 @@ def test_server_mixes_precisions_and_guesses_per_request():
     bitwise the same solve alone with its precision and guess."""
     srv = A.Server(precision=A.ADERDG_FP64, steps_per_round=3)
     cases = [(MIX[0], A.ADERDG_FP64, -1), (MIX[0], A.ADERDG_MIXED_FP32, -1), (MIX[1], A.ADERDG_MIXED_FP32, 2),
-             (MIX[4], -1, 2), (MIX[4], A.ADERDG_MIXED_FP32, 0), (MIX[5], A.ADERDG_MIXED_FP32, -1)]
+             (MIX[4], -1, 2), (MIX[4], A.ADERDG_MIXED_FP32, 0), (MIX[5], A.ADERDG_MIXED_FP32, -1),
+             (MIX[1], A.ADERDG_MIXED_FP32, 3), (MIX[2], A.ADERDG_FP64, 3)]
     U0s = [_ic(c, oracle.node_coords(_cfg(c))) for c, _, _ in cases]
     tickets = [srv.submit(A.make_spec(*c[:7]), U0s[i], c[7], precision=p, guess=g)
                for i, (c, p, g) in enumerate(cases)]

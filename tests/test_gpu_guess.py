@@ -15,7 +15,7 @@ pytestmark = pytest.mark.gpu
 
 GAMMA = 1.4
 EL = (1.0, 2.0, 1.0)
-GUESSES = [A.ADERDG_GUESS_ORDER2, A.ADERDG_GUESS_ORDER3]
+GUESSES = [A.ADERDG_GUESS_ORDER2, A.ADERDG_GUESS_ORDER3, A.ADERDG_GUESS_EXTRAP]
 
 # (pde, dim, N, cells, L, params)
 CASES = (
@@ -122,7 +122,62 @@ def test_third_order_guess_same_error_as_trivial_guess():
     np.testing.assert_allclose(errs[1], errs[0], rtol=1e-6)
 
 
-def test_batch_with_guess_equals_alone():
+@pytest.mark.parametrize("picard", [0, 1])
+def test_full_run_euler_vortex_extrapolation_guess(picard):
+    """FP64 full run with the extrapolation of the previous predictor (the
+    first step takes the third-order guess): default count (2) and one
+    Picard iteration, against the oracle's run."""
+    case = (2, 2, 4, (24, 20), 10.0, (GAMMA,))
+    cfg, s = _pair(*case, guess=A.ADERDG_GUESS_EXTRAP, picard=picard)
+    U0 = inputs.euler_vortex(oracle.node_coords(cfg))
+    Uo, to, ko, _ = oracle.run(cfg, U0, t_end=0.4)
+    s.set_state(U0)
+    s.advance(0.4)
+    Ug, t, k = s.get_state()
+    assert (t, k) == (to, ko) and k > 2
+    assert l2_rel(cfg, Ug, Uo) <= 1e-11
+
+
+def test_extrapolation_guess_elasticity_and_mixed():
+    case = (3, 3, 3, (5, 4, 4), 1.0, EL)
+    cfg, s = _pair(*case, guess=A.ADERDG_GUESS_EXTRAP, picard=1)
+    U0 = inputs.elastic_pulse(oracle.node_coords(cfg))
+    Uo, to, ko, _ = oracle.run(cfg, U0, t_end=0.05)
+    s.set_state(U0)
+    s.advance(0.05)
+    Ug, t, k = s.get_state()
+    assert (t, k) == (to, ko)
+    assert l2_rel(cfg, Ug, Uo) <= 1e-11
+    for case in [(2, 2, 4, (24, 20), 10.0, (GAMMA,)), (2, 2, 2, (24, 20), 10.0, (GAMMA,))]:
+        cfg, s = _pair(*case, guess=A.ADERDG_GUESS_EXTRAP, picard=1, precision=A.ADERDG_MIXED_FP32)
+        U0 = inputs.euler_vortex(oracle.node_coords(cfg))
+        Uo, to, ko, _ = oracle.run(cfg, U0, t_end=0.4)
+        s.set_state(U0)
+        s.advance(0.4)
+        Ug, t, k = s.get_state()
+        assert t == to and abs(k - ko) <= 1
+        assert l2_rel(cfg, Ug, Uo) <= 1e-6
+
+
+def test_extrapolation_restarts_after_set_state():
+    """A state upload drops the previous predictor: the next step takes the
+    third-order guess again (same result as a fresh handle)."""
+    case = (2, 2, 3, (8, 8), 2.0, (GAMMA,))
+    cfg, s = _pair(*case, guess=A.ADERDG_GUESS_EXTRAP)
+    U0 = _state(cfg, 2, seed=77)
+    s.set_state(U0)
+    s.advance(1e30, max_steps=3)
+    s.set_state(U0)
+    s.advance(1e30, max_steps=2)
+    a = s.get_state()[0]
+    _, s2 = _pair(*case, guess=A.ADERDG_GUESS_EXTRAP)
+    s2.set_state(U0)
+    s2.advance(1e30, max_steps=2)
+    np.testing.assert_array_equal(a, s2.get_state()[0])
+
+
+@pytest.mark.parametrize("guess", [A.ADERDG_GUESS_ORDER3, A.ADERDG_GUESS_EXTRAP])
+def test_batch_with_guess_equals_alone(guess):
     mix = [(2, 2, (6, 5), (0, 0), (10, 10), 2, (GAMMA,)), (2, 2, (8, 8), (0, 0), (10, 10), 4, (GAMMA,)),
            (3, 3, (3, 3, 2), (0, 0, 0), (1, 1, 1), 3, EL)]
     t_end = [0.3, 0.2, 0.02]
@@ -131,12 +186,12 @@ def test_batch_with_guess_equals_alone():
         X = oracle.node_coords(oracle.make_cfg(c[1], c[2], c[3], c[4], c[5], c[0], c[6]))
         ics.append(inputs.euler_vortex(X) if c[0] == 2 else inputs.elastic_pulse(X, width=0.05))
     for prec in (A.ADERDG_FP64, A.ADERDG_MIXED_FP32):
-        b = A.Batch([A.make_spec(*c) for c in mix], precision=prec, guess=A.ADERDG_GUESS_ORDER3)
+        b = A.Batch([A.make_spec(*c) for c in mix], precision=prec, guess=guess)
         for i, u in enumerate(ics):
             b.set_state(i, u)
         b.advance(t_end)
         for i, c in enumerate(mix):
-            with A.Solver(*c, precision=prec, guess=A.ADERDG_GUESS_ORDER3) as s:
+            with A.Solver(*c, precision=prec, guess=guess) as s:
                 s.set_state(ics[i])
                 s.advance(t_end[i])
                 alone = s.get_state()[0]
