@@ -263,7 +263,9 @@ int set_t_end(aderdg_t *h, double t_end)
 // reciprocal or square root = 1): the initial guess (trivial: the first
 // Picard iteration on the time-constant guess, then P-1 full iterations;
 // second / third order: one / two time-constant L evaluations, then P full
-// iterations), time averages, volume term, traces; corrector Rusanov +
+// iterations; extrapolation: an n x n contraction per node and variable,
+// then P full iterations, with the previous predictor read and this one
+// written), time averages, volume term, traces; corrector Rusanov +
 // lift + update + wave speeds.
 void fill_cost(const aderdg_t *h, aderdg_info_t *info)
 {
@@ -283,6 +285,7 @@ void fill_cost(const aderdg_t *h, aderdg_info_t *info)
     info->flops_corrector = corr * h->E;
     const double b = h->ks->elem_bytes;
     info->bytes_predictor = h->E * (8.0 * NS * M + b * NS * M + b * NREC * h->ks->rs);
+    if (h->guess == 3) info->bytes_predictor += h->E * 2.0 * b * NST * M;  // previous predictor in, this one out
     info->bytes_corrector = h->E * (16.0 * NS * M + b * NS * M + 2.0 * b * NREC * h->ks->rs);
 }
 
