@@ -38,7 +38,7 @@ _LIB = os.path.join(_BUILD, "liborc.so")
 _lock = threading.Lock()
 _lib = None
 
-PDE_ADVECTION, PDE_EULER, PDE_ELASTICITY = 1, 2, 3
+PDE_ADVECTION, PDE_EULER, PDE_ELASTICITY, PDE_DIFFUSE_ELASTICITY = 1, 2, 3, 4
 
 
 class Cfg(C.Structure):
@@ -94,6 +94,15 @@ def lib():
             L.orc_traces.argtypes = [cp, dp, dp, dp, dp]
             L.orc_rusanov.argtypes = [cp, C.c_int, dp, dp, dp, dp, dp]
             L.orc_rusanov.restype = None
+            L.orc_ncp.argtypes = [cp, dp, C.c_int, dp, dp]
+            L.orc_ncp.restype = None
+            L.orc_source.argtypes = [cp, dp, dp]
+            L.orc_source.restype = None
+            L.orc_path_jump.argtypes = [cp, C.c_int, dp, dp, dp]
+            L.orc_path_jump.restype = None
+            L.orc_face_flux.argtypes = [cp, C.c_int, dp, dp, dp, dp, dp, dp]
+            L.orc_face_flux.restype = None
+            L.orc_nevolved.argtypes = [cp]
             L.orc_cfl_dt.argtypes = [cp, dp]
             L.orc_cfl_dt.restype = C.c_double
             L.orc_step_ex.argtypes = [cp, dp, C.c_double, dp, dp, dp]
@@ -259,6 +268,40 @@ def rusanov(cfg: Cfg, d: int, qL, fL, qR, fR) -> np.ndarray:
     a = [np.ascontiguousarray(x, dtype=np.float64) for x in (qL, fL, qR, fR)]
     lib().orc_rusanov(C.byref(cfg), d, *[_p(x) for x in a], _p(out))
     return out
+
+
+def ncp(cfg: Cfg, q: np.ndarray, d: int, g: np.ndarray) -> np.ndarray:
+    """Non-conservative product B_d(q) g."""
+    out = np.zeros(cfg.m)
+    lib().orc_ncp(C.byref(cfg), _p(np.ascontiguousarray(q, dtype=np.float64)), d,
+                  _p(np.ascontiguousarray(g, dtype=np.float64)), _p(out))
+    return out
+
+
+def source(cfg: Cfg, q: np.ndarray) -> np.ndarray:
+    out = np.zeros(cfg.m)
+    lib().orc_source(C.byref(cfg), _p(np.ascontiguousarray(q, dtype=np.float64)), _p(out))
+    return out
+
+
+def path_jump(cfg: Cfg, d: int, qL, qR) -> np.ndarray:
+    """int_0^1 B_d(qL + s (qR - qL)) ds (qR - qL), three-point Gauss-Legendre."""
+    out = np.zeros(cfg.m)
+    lib().orc_path_jump(C.byref(cfg), d, _p(np.ascontiguousarray(qL, dtype=np.float64)),
+                        _p(np.ascontiguousarray(qR, dtype=np.float64)), _p(out))
+    return out
+
+
+def face_flux(cfg: Cfg, d: int, qL, fL, qR, fR):
+    """(f_lower, f_upper): the face fluctuations of the lower and upper element."""
+    lo, up = np.zeros(cfg.m), np.zeros(cfg.m)
+    a = [np.ascontiguousarray(x, dtype=np.float64) for x in (qL, fL, qR, fR)]
+    lib().orc_face_flux(C.byref(cfg), d, *[_p(x) for x in a], _p(lo), _p(up))
+    return lo, up
+
+
+def nevolved(cfg: Cfg) -> int:
+    return lib().orc_nevolved(C.byref(cfg))
 
 
 def n_elems(cfg: Cfg) -> int:

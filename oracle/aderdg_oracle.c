@@ -14,13 +14,18 @@
  *     (Sec. 2.2, eq. pde.st2), solved by a discrete Picard iteration started
  *     from the trivial guess q = u(t^n); discrete derivatives are the nodal
  *     derivative matrix D (eq. D_kl) applied dimension by dimension
- *   - corrector (Sec. 2.1, eq. pde.nc.gw2 with B = S = 0): diagonal mass,
- *     volume integral of grad(Phi).F(q_h), face integral of the Rusanov flux
- *     (eq. pc.scheme with B = 0, eq. rusanov) on time-averaged traces
+ *   - corrector (Sec. 2.1, eq. pde.nc.gw2): diagonal mass, volume integrals
+ *     of grad(Phi).F(q_h), Phi B(q_h).grad(q_h) and Phi S(q_h), face
+ *     integral of the path-conservative Rusanov fluctuations (eq. pc.scheme
+ *     with the straight-segment path and a three-point Gauss-Legendre rule
+ *     for the path integral, eq. rusanov) on time-averaged traces
  *   - CFL time step dt = alpha / sum_d lambda_d^max / dx_d (Sec. 3, CFL eq.)
- *   - PDEs: linear advection, Euler (Sec. 3.1, eq. euler, ideal gas), and
- *     the velocity-stress linear elasticity system obtained from Sec. 3.2
- *     with alpha = 1 and constant rho, lambda, mu
+ *   - PDEs: linear advection with an optional linear reaction source
+ *     S = -kappa q, Euler (Sec. 3.1, eq. euler, ideal gas), the
+ *     velocity-stress linear elasticity system obtained from Sec. 3.2 with
+ *     alpha = 1 and constant rho, lambda, mu (conservative form), and the
+ *     diffuse-interface elasticity system of Sec. 3.2 itself (purely
+ *     non-conservative, material parameters and alpha in the state)
  *
  * Readings of points where the paper is silent or ambiguous (listed in the
  * design notes as well):
@@ -37,6 +42,18 @@
  *   R7 alpha defaults to 0.9 x the von Neumann limit of the scheme (the
  *      paper's alpha < 1/(2N+1) is necessary only; 0.9/(2N+1) is unstable
  *      for N >= 3); the last step is clipped to t_end
+ *   R19 diffuse-interface elasticity: state (sigma, w = alpha v, alpha,
+ *      lambda, mu, rho); the stress equation's (1/alpha) grad(alpha v) is
+ *      the gradient of the state variable w, and v = w / alpha; alpha > 0
+ *      everywhere (a vacuum is a small positive alpha); in 2D the
+ *      plane-strain subsystem (sxx, syy, sxy, w1, w2) without szz
+ *   R20 the dissipation matrix Theta = s_max I acts on the evolved
+ *      variables only: the material parameters and alpha obey q_t = 0,
+ *      which Rusanov dissipation of their jumps would violate
+ *   R21 the path-conservative face term uses the time-averaged traces (as
+ *      R5); the lower element of a face receives
+ *      (fL + fR)/2 - Theta (qR - qL)/2 + J/2 and the upper one the same
+ *      with -J/2, J = int_0^1 B_d(psi(s)) ds (qR - qL)
  *
  * Layout: u[e][s][v] with v fastest, then x, y, z (s = sx + n*sy + n^2*sz);
  * space-time qhat[t][s][v] with time slowest (the AoS layout of Sec. 2.2).
@@ -53,6 +70,7 @@
 #endif
 
 #define ORC_MAXN 10   /* n = N+1 <= 10 */
+#define ORC_MAXM 13   /* variables */
 
 typedef struct {
     int dim;          /* 1, 2 or 3 */
@@ -60,8 +78,10 @@ typedef struct {
     double lo[3], hi[3];
     int N;            /* polynomial degree */
     int m;            /* number of variables */
-    int pde;          /* 1 advection, 2 Euler, 3 elasticity */
-    double prm[8];    /* advection: a_x a_y a_z; Euler: gamma; elasticity: rho lambda mu */
+    int pde;          /* 1 advection, 2 Euler, 3 elasticity, 4 diffuse-interface
+                         elasticity */
+    double prm[8];    /* advection: a_x a_y a_z kappa; Euler: gamma; elasticity:
+                         rho lambda mu; diffuse interface: none (all in the state) */
     int picard;       /* > 0 fixed count, 0 -> default (see orc_picard_count),
                          < 0 -> to convergence */
     double alpha;     /* CFL coefficient; 0 -> default table (see orc_alpha) */
@@ -192,8 +212,13 @@ int orc_nvar(int pde, int dim)
     if (pde == 1) return 1;
     if (pde == 2) return dim + 2;
     if (pde == 3) return 9;
+    if (pde == 4) return dim == 3 ? 13 : (dim == 2 ? 9 : -1);
     return -1;
 }
+
+/* Evolved variables: the leading ones.  The diffuse-interface system's last
+ * four (alpha, lambda, mu, rho) obey q_t = 0. */
+int orc_nevolved(const orc_cfg *c) { return c->pde == 4 ? c->m - 4 : c->m; }
 
 /* Sec. 3.1 eq. euler, ideal gas p = (gamma-1)(rhoE - rho|v|^2/2). */
 static void euler_flux(int dim, double gamma, const double *q, int d, double *f)
@@ -240,18 +265,78 @@ static void elastic_flux(const double *prm, const double *q, int d, double *f)
     for (int i = 0; i < 3; ++i) f[6 + i] = -s_row[i][d] / rho;
 }
 
+/* Diffuse-interface linear elasticity (Sec. 3.2), reading R19:
+ *   sigma_t - E : (1/alpha) grad(alpha v) + (1/alpha) E : (v (x) grad alpha) = 0
+ *   (alpha v)_t - (alpha/rho) div sigma - (1/rho) sigma grad alpha = 0
+ *   alpha_t = lambda_t = mu_t = rho_t = 0
+ * with E : G = lambda tr(G) I + mu (G + G^T) (Hooke's law on the velocity
+ * gradient) and state Q = (sigma, w = alpha v, alpha, lambda, mu, rho),
+ * sigma in the order xx yy zz xy yz xz (3D) or xx yy xy (2D).  There is no
+ * flux; every term is a non-conservative product B_d(Q) dQ/dx_d:
+ *   a_i = (1/alpha) dw_i/dx_d - (w_i/alpha^2) dalpha/dx_d   (= dv_i/dx_d)
+ *   sigma_ij row: -(lambda a_d delta_ij + mu (a_i delta_jd + delta_id a_j))
+ *   w_i row:      -(alpha dsigma_id/dx_d + sigma_id dalpha/dx_d) / rho
+ * nc_out = B_d(q) g for the derivative vector g = dQ/dx_d. */
+static int sym_index(int dim, int i, int j)
+{
+    if (i > j) { int t = i; i = j; j = t; }
+    if (dim == 2) return i == j ? i : 2;
+    if (i == j) return i;
+    return (i == 0 && j == 1) ? 3 : ((i == 1 && j == 2) ? 4 : 5);
+}
+
+static void dim_ncp(int dim, const double *q, int d, const double *g, double *out)
+{
+    const int nsig = dim == 3 ? 6 : 3;
+    const double *w = q + nsig;
+    const double alpha = q[nsig + dim], lam = q[nsig + dim + 1], mu = q[nsig + dim + 2], rho = q[nsig + dim + 3];
+    const double ga = g[nsig + dim];
+    double a[3];
+    for (int i = 0; i < dim; ++i) a[i] = g[nsig + i] / alpha - w[i] * ga / (alpha * alpha);
+    for (int i = 0; i < dim; ++i)
+        for (int j = i; j < dim; ++j) {
+            double r = -mu * ((j == d ? a[i] : 0.0) + (i == d ? a[j] : 0.0));
+            if (i == j) r -= lam * a[d];
+            out[sym_index(dim, i, j)] = r;
+        }
+    for (int i = 0; i < dim; ++i) {
+        const int k = sym_index(dim, i, d);
+        out[nsig + i] = -(alpha * g[k] + q[k] * ga) / rho;
+    }
+    for (int v = nsig + dim; v < nsig + dim + 4; ++v) out[v] = 0.0;
+}
+
 void orc_flux(const orc_cfg *c, const double *q, int d, double *f)
 {
     if (c->pde == 1) f[0] = c->prm[d] * q[0];
     else if (c->pde == 2) euler_flux(c->dim, c->prm[0], q, d, f);
-    else elastic_flux(c->prm, q, d, f);
+    else if (c->pde == 3) elastic_flux(c->prm, q, d, f);
+    else for (int v = 0; v < c->m; ++v) f[v] = 0.0;
+}
+
+/* Non-conservative product B_d(q) g (eq. pde); zero for the conservative
+ * systems. */
+void orc_ncp(const orc_cfg *c, const double *q, int d, const double *g, double *out)
+{
+    if (c->pde == 4) dim_ncp(c->dim, q, d, g, out);
+    else for (int v = 0; v < c->m; ++v) out[v] = 0.0;
+}
+
+/* Algebraic source S(q) (eq. pde): -kappa q for advection, zero otherwise. */
+void orc_source(const orc_cfg *c, const double *q, double *S)
+{
+    for (int v = 0; v < c->m; ++v) S[v] = c->pde == 1 ? -c->prm[3] * q[v] : 0.0;
 }
 
 double orc_max_eig(const orc_cfg *c, const double *q, int d)
 {
     if (c->pde == 1) return fabs(c->prm[d]);
     if (c->pde == 2) return euler_eig(c->dim, c->prm[0], q, d);
-    return sqrt((c->prm[1] + 2.0 * c->prm[2]) / c->prm[0]);
+    if (c->pde == 3) return sqrt((c->prm[1] + 2.0 * c->prm[2]) / c->prm[0]);
+    /* diffuse interface: the P-wave speed; the eigenvalues do not depend on
+     * alpha (Sec. 3.2) */
+    const int b = c->m - 3;
+    return sqrt((q[b] + 2.0 * q[b + 1]) / q[b + 2]);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -379,28 +464,48 @@ double orc_alpha(const orc_cfg *c)
  *
  * Outputs (any may be NULL): qhat[t][s][v] (n^{d+1} m), qbar[s][v] (n^d m),
  * Fbar[d][s][v] (dim n^d m).  Returns the number of iterations done. */
-/* L(w) = -sum_d (1/dx_d) Dhat_d F_d(w) at the spatial nodes of one element:
- * the element-local approximation of the time derivative of Sec. 2.2 (the
- * L operator with S = 0 and B = 0), with the same nodal derivative as the
- * predictor (reading R2).  tmp holds dim ns m values. */
-static void l_operator(const orc_cfg *c, const basis *b, const double *w, double *Lw, double *tmp)
+/* L(w) = S(w) - sum_d (1/dx_d) [Dhat_d F_d(w) + B_d(w) Dhat_d w] at the
+ * spatial nodes of one element: the element-local approximation of the time
+ * derivative of Sec. 2.2 (the L operator), with the same nodal derivative as
+ * the predictor (reading R2); with_flux = 0 leaves out the flux divergence
+ * (the corrector's volume integrals of B and S).  tmp holds dim ns m values. */
+static void l_eval(const orc_cfg *c, const basis *b, const double *w, double *Lw, double *tmp, int with_flux)
 {
     const int n = b->n, dim = c->dim, m = c->m, ns = ipow(n, dim);
-    for (int d = 0; d < dim; ++d)
-        for (int s = 0; s < ns; ++s) orc_flux(c, &w[(size_t)s * m], d, &tmp[((size_t)d * ns + s) * m]);
-    for (int s = 0; s < ns; ++s)
-        for (int v = 0; v < m; ++v) {
-            double r = 0.0;
-            for (int d = 0; d < dim; ++d) {
-                int sd = digit(s, n, d);
-                double acc = 0.0;
-                for (int j = 0; j < n; ++j)
-                    acc += b->Dhat[sd * n + j] * tmp[((size_t)d * ns + with_digit(s, n, d, j)) * m + v];
-                r -= acc / cell_dx(c, d);
+    if (with_flux)
+        for (int d = 0; d < dim; ++d)
+            for (int s = 0; s < ns; ++s) orc_flux(c, &w[(size_t)s * m], d, &tmp[((size_t)d * ns + s) * m]);
+    for (int s = 0; s < ns; ++s) {
+        double r[ORC_MAXM];
+        orc_source(c, &w[(size_t)s * m], r);
+        for (int d = 0; d < dim; ++d) {
+            const int sd = digit(s, n, d);
+            double g[ORC_MAXM], nc[ORC_MAXM];
+            for (int v = 0; v < m; ++v) {
+                double acc = 0.0, ga = 0.0;
+                for (int j = 0; j < n; ++j) {
+                    const int sj = with_digit(s, n, d, j);
+                    if (with_flux) acc += b->Dhat[sd * n + j] * tmp[((size_t)d * ns + sj) * m + v];
+                    ga += b->Dhat[sd * n + j] * w[(size_t)sj * m + v];
+                }
+                if (with_flux) r[v] -= acc / cell_dx(c, d);
+                g[v] = ga;
             }
-            Lw[(size_t)s * m + v] = r;
+            orc_ncp(c, &w[(size_t)s * m], d, g, nc);
+            for (int v = 0; v < m; ++v) r[v] -= nc[v] / cell_dx(c, d);
         }
+        for (int v = 0; v < m; ++v) Lw[(size_t)s * m + v] = r[v];
+    }
 }
+
+static void l_operator(const orc_cfg *c, const basis *b, const double *w, double *Lw, double *tmp)
+{
+    l_eval(c, b, w, Lw, tmp, 1);
+}
+
+/* The PDE has a non-conservative product or a source (a volume integral
+ * beyond the flux term). */
+static int has_nc_or_source(const orc_cfg *c) { return c->pde == 4 || (c->pde == 1 && c->prm[3] != 0.0); }
 
 /* Initial guess q0 at the space-time nodes (t^n + tau_t, x_s),
  * tau_t = xi_t dt (Sec. 2.2, written as a Taylor series in time):
@@ -461,9 +566,6 @@ static int predictor_elem(const orc_cfg *c, const basis *b, const double *u, dou
     double *F = q + (size_t)nst * m;      /* dim nst m */
     double *R = F + (size_t)dim * nst * m;/* nst m */
     double *qn = R + (size_t)nst * m;     /* nst m */
-    double dx[3];
-    for (int d = 0; d < dim; ++d) dx[d] = cell_dx(c, d);
-
     initial_guess(c, b, u, dt, q, work + (size_t)nst * m * (3 + dim), qprev, ratio);
 
     int P = (c->guess == 3 && !qprev) ? fallback_picard(c) : orc_picard_count(c);
@@ -471,24 +573,8 @@ static int predictor_elem(const orc_cfg *c, const basis *b, const double *u, dou
     int maxit = to_conv ? 50 : P;
     int it;
     for (it = 0; it < maxit; ++it) {
-        for (int d = 0; d < dim; ++d)
-            for (int l = 0; l < nst; ++l)
-                orc_flux(c, &q[(size_t)l * m], d, &F[((size_t)d * nst + l) * m]);
-        for (int t = 0; t < n; ++t)
-            for (int s = 0; s < ns; ++s)
-                for (int v = 0; v < m; ++v) {
-                    double r = 0.0;
-                    for (int d = 0; d < dim; ++d) {
-                        int sd = digit(s, n, d);
-                        double acc = 0.0;
-                        for (int j = 0; j < n; ++j) {
-                            int sj = with_digit(s, n, d, j);
-                            acc += b->Dhat[sd * n + j] * F[((size_t)d * nst + (size_t)t * ns + sj) * m + v];
-                        }
-                        r -= acc / dx[d];
-                    }
-                    R[((size_t)t * ns + s) * m + v] = r;
-                }
+        /* R = L(q) at every time node: S - sum_d (Dhat_d F_d + B_d Dhat_d q) / dx_d */
+        for (int t = 0; t < n; ++t) l_eval(c, b, &q[(size_t)t * ns * m], &R[(size_t)t * ns * m], F, 1);
         double dmax = 0.0, qmax = 0.0;
         for (int s = 0; s < ns; ++s)
             for (int v = 0; v < m; ++v) {
@@ -558,6 +644,21 @@ static void volume_elem(const orc_cfg *c, const basis *b, const double *Fbar, do
         }
 }
 
+/* Volume integrals of the non-conservative product and the source (fourth
+ * and fifth integrals of eq. pde.nc.gw2), divided by the diagonal mass and
+ * by dt, added to V: with the nodal quadrature in space and the time nodes
+ * in time, V[s] += sum_t w_t [S(q_t) - sum_d (1/dx_d) B_d(q_t) Dhat_d q_t](x_s).
+ * qhat[t][s][v] is the predictor; tmp holds 2 ns m values. */
+static void volume_nc_elem(const orc_cfg *c, const basis *b, const double *qhat, double *V, double *tmp)
+{
+    const int n = b->n, m = c->m, ns = ipow(n, c->dim);
+    double *Lt = tmp;
+    for (int t = 0; t < n; ++t) {
+        l_eval(c, b, &qhat[(size_t)t * ns * m], Lt, NULL, 0);
+        for (size_t i = 0; i < (size_t)ns * m; ++i) V[i] += b->w[t] * Lt[i];
+    }
+}
+
 /* Boundary extrapolation of the time averages to the 2d faces:
  *   qf[d][side][p][v] = sum_j phi_j(side) qbar[s(d=j,perp=p)][v]
  *   ff[d][side][p][v] = sum_j phi_j(side) Fbar_d[s(d=j,perp=p)][v]. */
@@ -593,6 +694,45 @@ void orc_rusanov(const orc_cfg *c, int d, const double *qL, const double *fL,
     double sL = orc_max_eig(c, qL, d), sR = orc_max_eig(c, qR, d);
     double smax = sL > sR ? sL : sR;
     for (int v = 0; v < c->m; ++v) fs[v] = 0.5 * (fL[v] + fR[v]) - 0.5 * smax * (qR[v] - qL[v]);
+}
+
+/* Path integral of eq. pc.scheme along the straight segment
+ * psi(s) = qL + s (qR - qL):  J = int_0^1 B_d(psi(s)) ds (qR - qL), by the
+ * three-point Gauss-Legendre rule on [0,1] (nodes 1/2 -+ sqrt(3/5)/2 and
+ * 1/2, weights 5/18, 8/18, 5/18). */
+void orc_path_jump(const orc_cfg *c, int d, const double *qL, const double *qR, double *J)
+{
+    const double r = 0.5 * sqrt(0.6);
+    const double sg[3] = {0.5 - r, 0.5, 0.5 + r}, wg[3] = {5.0 / 18.0, 8.0 / 18.0, 5.0 / 18.0};
+    const int m = c->m;
+    double dq[ORC_MAXM], psi[ORC_MAXM], b[ORC_MAXM];
+    for (int v = 0; v < m; ++v) { dq[v] = qR[v] - qL[v]; J[v] = 0.0; }
+    for (int k = 0; k < 3; ++k) {
+        for (int v = 0; v < m; ++v) psi[v] = qL[v] + sg[k] * dq[v];
+        orc_ncp(c, psi, d, dq, b);
+        for (int v = 0; v < m; ++v) J[v] += wg[k] * b[v];
+    }
+}
+
+/* Face fluctuations along d between the lower element (its xi_d = 1 trace
+ * qL, fL) and the upper one (its xi_d = 0 trace qR, fR), each in the e_d
+ * convention of the lift (eq. pc.scheme, eq. rusanov; readings R20, R21):
+ *   f_lower = (fL + fR)/2 - Theta (qR - qL)/2 + J/2
+ *   f_upper = (fL + fR)/2 - Theta (qR - qL)/2 - J/2
+ * Theta = s_max on the evolved variables, 0 on the material parameters. */
+void orc_face_flux(const orc_cfg *c, int d, const double *qL, const double *fL, const double *qR,
+                   const double *fR, double *f_lower, double *f_upper)
+{
+    double sL = orc_max_eig(c, qL, d), sR = orc_max_eig(c, qR, d);
+    double smax = sL > sR ? sL : sR;
+    const int mev = orc_nevolved(c);
+    double J[ORC_MAXM];
+    orc_path_jump(c, d, qL, qR, J);
+    for (int v = 0; v < c->m; ++v) {
+        double f = 0.5 * (fL[v] + fR[v]) - (v < mev ? 0.5 * smax * (qR[v] - qL[v]) : 0.0);
+        f_lower[v] = f + 0.5 * J[v];
+        f_upper[v] = f - 0.5 * J[v];
+    }
 }
 
 /* ------------------------------------------------------------------------ */
@@ -740,6 +880,7 @@ static int step_impl(const orc_cfg *c, double *U, double dt, double *V_out, doub
                 predictor_elem(c, &b, &U[(size_t)e * ns * m], dt, h ? &h->next[qoff] : NULL, qbar, Fbar, work,
                                (h && h->valid) ? &h->prev[qoff] : NULL, (h && h->valid) ? dt / h->dt_prev : 1.0);
                 volume_elem(c, &b, Fbar, &V[(size_t)e * ns * m]);
+                if (has_nc_or_source(c)) volume_nc_elem(c, &b, work, &V[(size_t)e * ns * m], work + (size_t)n * ns * m);
                 traces_elem(c, &b, qbar, Fbar, &qf[(size_t)e * fsz], &ff[(size_t)e * fsz]);
             }
         }
@@ -749,18 +890,19 @@ static int step_impl(const orc_cfg *c, double *U, double dt, double *V_out, doub
 
 #pragma omp parallel for schedule(static)
     for (long e = 0; e < E; ++e) {
-        double Fm[3][ORC_MAXN * ORC_MAXN * 9], Fp[3][ORC_MAXN * ORC_MAXN * 9];
+        double Fm[3][ORC_MAXN * ORC_MAXN * ORC_MAXM], Fp[3][ORC_MAXN * ORC_MAXN * ORC_MAXM];
+        double other[ORC_MAXM];
         for (int d = 0; d < dim; ++d) {
             long em = neighbour(c, e, d, -1), ep = neighbour(c, e, d, +1);
             for (int p = 0; p < nf; ++p) {
-                /* face at xi_d = 0: left = em (its side 1), right = e (its side 0) */
+                /* face at xi_d = 0: lower = em (its side 1), upper = e (its side 0) */
                 size_t oL = (size_t)em * fsz + (((size_t)d * 2 + 1) * nf + p) * m;
                 size_t oR = (size_t)e * fsz + (((size_t)d * 2 + 0) * nf + p) * m;
-                orc_rusanov(c, d, &qf[oL], &ff[oL], &qf[oR], &ff[oR], &Fm[d][(size_t)p * m]);
-                /* face at xi_d = 1: left = e (side 1), right = ep (side 0) */
+                orc_face_flux(c, d, &qf[oL], &ff[oL], &qf[oR], &ff[oR], other, &Fm[d][(size_t)p * m]);
+                /* face at xi_d = 1: lower = e (side 1), upper = ep (side 0) */
                 oL = (size_t)e * fsz + (((size_t)d * 2 + 1) * nf + p) * m;
                 oR = (size_t)ep * fsz + (((size_t)d * 2 + 0) * nf + p) * m;
-                orc_rusanov(c, d, &qf[oL], &ff[oL], &qf[oR], &ff[oR], &Fp[d][(size_t)p * m]);
+                orc_face_flux(c, d, &qf[oL], &ff[oL], &qf[oR], &ff[oR], &Fp[d][(size_t)p * m], other);
             }
         }
         for (int s = 0; s < ns; ++s)
@@ -861,7 +1003,10 @@ int orc_step_sampled(const orc_cfg *c, const double *U, double dt, long n_s,
                 for (int d = 0; d < dim; ++d) { ids[1 + 2 * d] = neighbour(c, e, d, -1); ids[2 + 2 * d] = neighbour(c, e, d, +1); }
                 for (int k = 0; k < 1 + 2 * dim; ++k) {
                     predictor_elem(c, &b, &U[(size_t)ids[k] * ns * m], dt, NULL, qbar, Fbar, work, NULL, 1.0);
-                    if (k == 0) volume_elem(c, &b, Fbar, V);
+                    if (k == 0) {
+                        volume_elem(c, &b, Fbar, V);
+                        if (has_nc_or_source(c)) volume_nc_elem(c, &b, work, V, work + (size_t)n * ns * m);
+                    }
                     traces_elem(c, &b, qbar, Fbar, &qf[k * fsz], &ff[k * fsz]);
                 }
                 for (int s = 0; s < ns; ++s)
@@ -869,13 +1014,13 @@ int orc_step_sampled(const orc_cfg *c, const double *U, double dt, long n_s,
                         double surf = 0.0;
                         for (int d = 0; d < dim; ++d) {
                             int sd = digit(s, n, d), p = face_index(s, n, dim, d);
-                            double fm[9], fp[9];
+                            double fm[ORC_MAXM], fp[ORC_MAXM], other[ORC_MAXM];
                             size_t oL = 1 * fsz * (1 + 2 * d) + (((size_t)d * 2 + 1) * nf + p) * m;
                             size_t oR = (((size_t)d * 2 + 0) * nf + p) * m;
-                            orc_rusanov(c, d, &qf[oL], &ff[oL], &qf[oR], &ff[oR], fm);
+                            orc_face_flux(c, d, &qf[oL], &ff[oL], &qf[oR], &ff[oR], other, fm);
                             oL = (((size_t)d * 2 + 1) * nf + p) * m;
                             oR = fsz * (2 + 2 * d) + (((size_t)d * 2 + 0) * nf + p) * m;
-                            orc_rusanov(c, d, &qf[oL], &ff[oL], &qf[oR], &ff[oR], fp);
+                            orc_face_flux(c, d, &qf[oL], &ff[oL], &qf[oR], &ff[oR], fp, other);
                             surf += (b.F1[sd] * fp[v] - b.F0[sd] * fm[v]) / (cell_dx(c, d) * b.w[sd]);
                         }
                         size_t iu = ((size_t)e * ns + s) * m + v;

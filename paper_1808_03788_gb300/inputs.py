@@ -17,6 +17,12 @@ Fields (X has shape [E, n^d, dim]; results are [E, n^d, m], v fastest):
 * ``elastic_pulse``       Gaussian pulse exp(-|x - x0|^2 / w) on the velocity, sigma = 0
 * ``elastic_plane_wave``  exact P- or S-wave of the velocity-stress system
 * ``random_state``        bounded random nodal states (admissible for Euler)
+* ``diffuse_pack``        the state vector of the diffuse-interface elasticity
+                          system (sigma, w = alpha v, alpha, lambda, mu, rho)
+* ``smooth_step``         a smooth (tanh) step between two values, the diffuse
+                          interface profile of the volume fraction or a material
+* ``diffuse_terrain``     3D diffuse-interface workload: solid below a synthetic
+                          sinusoidal topography, vacuum above, a velocity pulse
 """
 from __future__ import annotations
 
@@ -24,11 +30,12 @@ import math
 
 import numpy as np
 
-PDE_ADVECTION, PDE_EULER, PDE_ELASTICITY = 1, 2, 3
+PDE_ADVECTION, PDE_EULER, PDE_ELASTICITY, PDE_DIFFUSE_ELASTICITY = 1, 2, 3, 4
 
 
 def nvar(pde: int, dim: int) -> int:
-    return {PDE_ADVECTION: 1, PDE_EULER: dim + 2, PDE_ELASTICITY: 9}[pde]
+    return {PDE_ADVECTION: 1, PDE_EULER: dim + 2, PDE_ELASTICITY: 9,
+            PDE_DIFFUSE_ELASTICITY: 13 if dim == 3 else 9}[pde]
 
 
 def _wrap(x, lo, L):
@@ -132,6 +139,39 @@ def elastic_plane_wave(X, kind="p", rho=1.0, lam=2.0, mu=1.0, t=0.0, k=1):
         out[..., 7] = f
         out[..., 3] = -mu / cs * f
     return out
+
+
+def diffuse_pack(dim, sigma, w, alpha, lam, mu, rho):
+    """Stack the fields of the diffuse-interface system into [..., m]:
+    sigma (xx yy zz xy yz xz in 3D; xx yy xy in 2D), w = alpha v (dim
+    components), then alpha, lambda, mu, rho.  Scalars broadcast."""
+    nsig = 6 if dim == 3 else 3
+    parts = [np.asarray(sigma[i], dtype=np.float64) for i in range(nsig)]
+    parts += [np.asarray(w[i], dtype=np.float64) for i in range(dim)]
+    parts += [np.asarray(x, dtype=np.float64) for x in (alpha, lam, mu, rho)]
+    shape = np.broadcast_shapes(*[p.shape for p in parts])
+    return np.stack([np.broadcast_to(p, shape) for p in parts], axis=-1)
+
+
+def smooth_step(x, x0, width, a, b):
+    """a for x << x0, b for x >> x0, a tanh profile of the given width."""
+    return a + (b - a) * 0.5 * (1.0 + np.tanh((np.asarray(x, dtype=np.float64) - x0) / width))
+
+
+def diffuse_terrain(X, h0=0.6, amp=0.08, k=2, width=0.02, alpha_vac=1e-2, lam=2.0, mu=1.0, rho=1.0,
+                    x0=(0.5, 0.5, 0.4), pulse=0.005):
+    """3D diffuse-interface workload on the unit box: solid (alpha = 1)
+    below the surface z = h0 + amp sin(2 pi k x) sin(2 pi k y), vacuum
+    (alpha = alpha_vac) above, joined by a tanh profile of the given width;
+    homogeneous material; the velocity w = alpha v carries a Gaussian pulse
+    exp(-|x - x0|^2 / pulse) in all three components, stresses zero."""
+    X = np.asarray(X, dtype=np.float64)
+    h = h0 + amp * np.sin(2 * math.pi * k * X[..., 0]) * np.sin(2 * math.pi * k * X[..., 1])
+    alpha = smooth_step(X[..., 2] - h, 0.0, width, 1.0, alpha_vac)
+    r2 = sum((X[..., d] - x0[d]) ** 2 for d in range(3))
+    g = np.exp(-r2 / pulse)
+    z = np.zeros(X.shape[:-1])
+    return diffuse_pack(3, [z] * 6, [alpha * g] * 3, alpha, lam, mu, rho)
 
 
 def random_state(pde: int, dim: int, E: int, ns: int, seed: int, amp: float = 0.2,
