@@ -59,16 +59,28 @@ extern "C" {
 #define ADERDG_E_CANCELLED (-8)   /* request cancelled */
 
 /* ---- PDE systems -------------------------------------------------------
- * ADVECTION   m = 1,   F_d = a_d u, p = (a_x, a_y, a_z)
+ * ADVECTION   m = 1,   F_d = a_d u, source S = -kappa u (eq. pde);
+ *             p = (a_x, a_y, a_z, kappa), kappa >= 0 (0: pure advection)
  * EULER       m = d+2, Q = (rho, rho v, rho E), ideal gas
  *             p = (gamma-1)(rho E - rho |v|^2 / 2)  (Sec. 3.1, eq. euler);
  *             p[0] = gamma
  * ELASTICITY  m = 9,   Q = (sxx, syy, szz, sxy, syz, sxz, u, v, w),
  *             velocity-stress form of Sec. 3.2 with alpha = 1 and constant
  *             material; p = (rho, lambda, mu); d = 3 only                */
+/* DIFFUSE_ELASTICITY  the diffuse-interface linear elasticity system of
+ *             Sec. 3.2 (purely non-conservative: B(Q) . grad Q, no flux):
+ *             Q = (sigma, w = alpha v, alpha, lambda, mu, rho) with sigma =
+ *             (xx, yy, zz, xy, yz, xz), m = 13, in 3D, and the plane-strain
+ *             (xx, yy, xy), m = 9, in 2D; alpha (volume fraction of the
+ *             solid, > 0; a vacuum is a small positive value) and the
+ *             material fields lambda, mu, rho are part of the state and
+ *             never change; faces use the path-conservative Rusanov
+ *             scheme (eq. pc.scheme, three-point Gauss-Legendre path
+ *             integral).  No parameters.                                 */
 #define ADERDG_PDE_ADVECTION 1
 #define ADERDG_PDE_EULER 2
 #define ADERDG_PDE_ELASTICITY 3
+#define ADERDG_PDE_DIFFUSE_ELASTICITY 4
 
 /* ---- precision modes ---------------------------------------------------
  * FP64        everything in double
@@ -227,6 +239,8 @@ int aderdg_corrector(aderdg_t *h, double dt);
  *   qface[e][d][side][p][v],
  *   fface[e][d][side][p][v]       (E d 2 n^(d-1) m) time-averaged traces,
  * side 0 = face xi_d = 0, p = the other spatial indices in increasing order.
+ * fface is zero for a purely non-conservative system (no flux).  The
+ * volume term includes the non-conservative product and the source.
  * Any pointer may be NULL.  Synchronising. */
 int aderdg_get_predictor_outputs(aderdg_t *h, double *volume, double *qface, double *fface,
                                  int where);

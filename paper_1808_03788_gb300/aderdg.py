@@ -27,7 +27,7 @@ ADERDG_E_BUSY = -6
 ADERDG_E_UNSUPPORTED = -7
 ADERDG_E_CANCELLED = -8
 
-ADERDG_PDE_ADVECTION, ADERDG_PDE_EULER, ADERDG_PDE_ELASTICITY = 1, 2, 3
+ADERDG_PDE_ADVECTION, ADERDG_PDE_EULER, ADERDG_PDE_ELASTICITY, ADERDG_PDE_DIFFUSE_ELASTICITY = 1, 2, 3, 4
 ADERDG_FP64, ADERDG_MIXED_FP32 = 0, 1
 ADERDG_HOST, ADERDG_DEVICE = 0, 1
 ADERDG_NUM_PRED_SHAPES, ADERDG_NUM_CORR_SHAPES = 5, 3
@@ -192,7 +192,7 @@ def aderdg_default_alpha(N: int) -> float:
 
 
 def nvar(pde: int, dim: int) -> int:
-    return {1: 1, 2: dim + 2, 3: 9}[pde]
+    return {1: 1, 2: dim + 2, 3: 9, 4: 13 if dim == 3 else 9}[pde]
 
 
 def _torch_ready():

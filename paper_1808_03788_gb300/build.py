@@ -34,7 +34,8 @@ def _nvcc() -> str:
 
 
 INST_SRC = os.path.join(CSRC, "inst.cu")
-_PDE_TYPE = {"advection": "Advection<%d>", "euler": "Euler<%d>", "elastic": "Elastic3"}
+_PDE_TYPE = {"advection": "Advection<%d>", "euler": "Euler<%d>", "elastic": "Elastic3",
+             "diffuse": "DiffuseElastic<%d>"}
 
 
 def instances():

@@ -183,6 +183,15 @@ double default_alpha(int N)
     return 0.5 / (2.0 * N + 1.0);
 }
 
+int pde_nvar(int kind, int dim)
+{
+    if (kind == 1) return 1;
+    if (kind == 2) return dim + 2;
+    if (kind == 3) return 9;  // compiled for d = 3 only
+    if (kind == 4) return dim == 3 ? 13 : (dim == 2 ? 9 : -1);
+    return -1;
+}
+
 void fill_pde_consts(int kind, PdeParams &P)
 {
     for (int i = 0; i < 8; ++i) P.c[i] = 0.0;
@@ -191,6 +200,7 @@ void fill_pde_consts(int kind, PdeParams &P)
             P.c[d] = P.p[d];
             P.c[3 + d] = std::fabs(P.p[d]);
         }
+        P.c[6] = -P.p[3];  // source coefficient -kappa
     } else if (kind == 2) {  // Euler
         P.c[0] = P.p[0] - 1.0;
         P.c[1] = P.p[0];

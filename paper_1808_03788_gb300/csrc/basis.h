@@ -10,6 +10,8 @@ double default_alpha(int N);
 // third order): max(1, N + 1 - degree of the guess in time); 3
 // (extrapolation, degree N): 2
 int default_picard(int N, int guess);
+// number of variables of PDE kind `kind` in dimension dim (-1: unknown)
+int pde_nvar(int kind, int dim);
 // derived constants P.c / P.cf of PDE kind `kind` from P.p (see PdeParams)
 void fill_pde_consts(int kind, PdeParams &P);
 // fill kp.od / kp.of from kp.b

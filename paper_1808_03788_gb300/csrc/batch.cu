@@ -60,10 +60,7 @@ const KernelSet *kernels_for(int pde, int dim, int N, int prec)
     return lookup_kernels(pde, dim, N, prec);
 }
 
-int nvar_of(int pde, int dim)
-{
-    return pde == ADERDG_PDE_ADVECTION ? 1 : pde == ADERDG_PDE_EULER ? dim + 2 : pde == ADERDG_PDE_ELASTICITY ? 9 : -1;
-}
+int nvar_of(int pde, int dim) { return pde_nvar(pde, dim); }
 
 // ---------------------------------------------------------------------------
 // device memory: the caller's allocator hook, else stream-ordered cudaMallocAsync
@@ -126,6 +123,7 @@ int make_slot(const aderdg_solve_spec_t &sp, int prec, int guess, int picard, do
     const KernelSet *ks = kernels_for(sp.pde.kind, m.dim, sp.N, prec);
     if (!ks) return fail(ADERDG_E_UNSUPPORTED, "no kernels compiled for this (pde, dim, N)");
     if (sp.pde.kind == ADERDG_PDE_EULER && !(sp.pde.p[0] > 1.0)) return fail(ADERDG_E_INVAL, "gamma must be > 1");
+    if (sp.pde.kind == ADERDG_PDE_ADVECTION && !(sp.pde.p[3] >= 0.0)) return fail(ADERDG_E_INVAL, "kappa must be >= 0");
     if (guess < ADERDG_GUESS_TRIVIAL || guess > ADERDG_GUESS_EXTRAP) return fail(ADERDG_E_INVAL, "bad initial guess");
     s = Slot();
     s.pde = sp.pde.kind;

@@ -167,13 +167,25 @@ inline double recip(double x) { return 1.0 / x; }
 #endif
 __host__ __device__ __forceinline__ float recip(float x) { return 1.0f / x; }
 
-// Linear advection F_d = a_d u.
+// Every PDE states: M variables, of which the leading MEV evolve (the rest
+// obey q_t = 0); NCP: the system is purely non-conservative (F = 0, all
+// terms B_d(q) dq/dx_d, see DiffuseElastic); HAS_SRC: an algebraic source
+// S(q) that is linear in q.
+
+// Linear advection F_d = a_d u with the reaction source S = -kappa u
+// (kappa = 0 unless given).
 template <int DIM>
 struct Advection {
     static constexpr int M = 1;
+    static constexpr int MEV = M;
+    static constexpr bool NCP = false, HAS_SRC = true;
     static constexpr int KIND = 1;
-    static constexpr int FLUX_FLOPS = DIM;        // per point, all directions
+    static constexpr int FLUX_FLOPS = DIM + 1;    // per point, all directions (+ the source)
     static constexpr int EIG_FLOPS = 0;
+    template <typename T>
+    __device__ __forceinline__ static void source(const PdeParams &P, const T *q, T *S) {
+        S[0] = pconst<T>(P, 6) * q[0];  // -kappa q
+    }
     template <typename T> using Ref = NoRef<T, M>;
     template <typename T>
     __device__ __forceinline__ static void make_ref(const PdeParams &, const T *q, Ref<T> &r) {
@@ -198,6 +210,8 @@ struct Advection {
 template <int DIM>
 struct Euler {
     static constexpr int M = DIM + 2;
+    static constexpr int MEV = M;
+    static constexpr bool NCP = false, HAS_SRC = false;
     static constexpr int KIND = 2;
     // 1 reciprocal, DIM products for v, DIM FMA + 2 for p, per direction:
     // DIM FMA/products for momentum + 1 add for pressure + 2 for energy
@@ -287,6 +301,8 @@ struct Euler {
 // rho, lambda, mu): Q = (sxx, syy, szz, sxy, syz, sxz, u, v, w).
 struct Elastic3 {
     static constexpr int M = 9;
+    static constexpr int MEV = M;
+    static constexpr bool NCP = false, HAS_SRC = false;
     static constexpr int KIND = 3;
     static constexpr int FLUX_FLOPS = 3 * 9;
     static constexpr int EIG_FLOPS = 0;
@@ -325,7 +341,113 @@ struct Elastic3 {
     }
 };
 
-// Launch geometry of the per-element kernels.
+// Diffuse-interface linear elasticity (Sec. 3.2, the seismic example's
+// system) in the state Q = (sigma, w = alpha v, alpha, lambda, mu, rho),
+// sigma = (xx, yy, zz, xy, yz, xz) in 3D or the plane-strain (xx, yy, xy) in
+// 2D; the last four obey q_t = 0.  No flux: the system is
+//   sigma_t - E : (1/alpha) grad(w) + E : (w/alpha^2 (x) grad alpha) = 0,
+//   w_t - (alpha/rho) div sigma - (1/rho) sigma grad alpha = 0,
+// E : G = lambda tr(G) I + mu (G + G^T).  For a derivative vector g = dQ/dx_d,
+// with a_i = (g_{w_i} - w_i g_alpha / alpha) / alpha  (the velocity derivative):
+//   B_d(q) g |sigma_ij = -(lambda a_d [i == j] + mu (a_i [j == d] + a_j [i == d]))
+//   B_d(q) g |w_i      = -(alpha g_{sigma_id} + sigma_id g_alpha) / rho.
+// B_d(q) g is linear in the evolved variables for fixed material fields, so
+// a time average of it equals it at the time-averaged state.
+template <int DIM>
+struct DiffuseElastic {
+    static constexpr int NSIG = DIM == 3 ? 6 : 3;
+    static constexpr int M = NSIG + DIM + 4;
+    static constexpr int MEV = NSIG + DIM;
+    static constexpr int IA = MEV, IL = MEV + 1, IM = MEV + 2, IR = MEV + 3;  // alpha lambda mu rho
+    static constexpr bool NCP = true, HAS_SRC = false;
+    static constexpr int KIND = 4;
+    // per point and direction: 2 reciprocals, a (DIM x 3), stress rows
+    // (~3 NSIG), momentum rows (3 DIM), accumulation (2 MEV)
+    static constexpr int FLUX_FLOPS = DIM * (2 + 3 * DIM + 3 * NSIG + 3 * DIM + 2 * MEV);
+    static constexpr int EIG_FLOPS = 4;
+    template <typename T> using Ref = NoRef<T, M>;
+    template <typename T>
+    __device__ __forceinline__ static void make_ref(const PdeParams &, const T *q, Ref<T> &r) {
+#pragma unroll
+        for (int v = 0; v < M; ++v) r.q[v] = q[v];
+    }
+    // symmetric-tensor index of (i, j) in the state
+    __host__ __device__ static constexpr int sig(int i, int j) {
+        return i > j ? sig(j, i)
+                     : (i == j ? i : (DIM == 2 ? 2 : (i == 0 && j == 1 ? 3 : (i == 1 && j == 2 ? 4 : 5))));
+    }
+    // out = B_d(q) g for the state q (absolute values) and g = dQ/dx_d, with
+    // the inverses ia = 1/alpha and ir = 1/rho of q precomputed
+    template <typename T>
+    __device__ __forceinline__ static void bdot(const T *q, T ia, T ir, int d, const T *g, T *out) {
+        const T ga = g[IA];
+        T a[DIM];
+#pragma unroll
+        for (int i = 0; i < DIM; ++i) a[i] = (g[NSIG + i] - q[NSIG + i] * ia * ga) * ia;
+        T ad = a[0];
+#pragma unroll
+        for (int k = 1; k < DIM; ++k) ad = d == k ? a[k] : ad;
+        const T lam = q[IL], mu = q[IM], al = q[IA];
+#pragma unroll
+        for (int i = 0; i < DIM; ++i)
+#pragma unroll
+            for (int j = i; j < DIM; ++j) {
+                T r = -mu * ((j == d ? a[i] : T(0)) + (i == d ? a[j] : T(0)));
+                if (i == j) r -= lam * ad;
+                out[sig(i, j)] = r;
+            }
+#pragma unroll
+        for (int i = 0; i < DIM; ++i) {
+            T gs = g[sig(i, 0)], qs = q[sig(i, 0)];
+#pragma unroll
+            for (int k = 1; k < DIM; ++k) {
+                gs = d == k ? g[sig(i, k)] : gs;
+                qs = d == k ? q[sig(i, k)] : qs;
+            }
+            out[NSIG + i] = -(al * gs + qs * ga) * ir;
+        }
+#pragma unroll
+        for (int v = MEV; v < M; ++v) out[v] = T(0);
+    }
+    // J = int_0^1 B_d(qL + s dq) ds dq by the three-point Gauss-Legendre rule
+    // on [0, 1] (eq. pc.scheme, straight-segment path); dq = qR - qL
+    template <typename T>
+    __device__ __forceinline__ static void path_jump(const T *qL, const T *dq, int d, T *J) {
+        const T h = T(0.3872983346207416885);  // sqrt(3/5) / 2
+        const T sg[3] = {T(0.5) - h, T(0.5), T(0.5) + h};
+        const T wg[3] = {T(5.0 / 18.0), T(8.0 / 18.0), T(5.0 / 18.0)};
+#pragma unroll
+        for (int v = 0; v < M; ++v) J[v] = T(0);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            T ps[M], b[M];
+#pragma unroll
+            for (int v = 0; v < M; ++v) ps[v] = qL[v] + sg[k] * dq[v];
+            bdot(ps, recip(ps[IA]), recip(ps[IR]), d, dq, b);
+#pragma unroll
+            for (int v = 0; v < MEV; ++v) J[v] += wg[k] * b[v];
+        }
+    }
+    template <typename T>
+    __device__ __forceinline__ static void flux(const PdeParams &, const T *, T (*f)[M]) {
+#pragma unroll
+        for (int d = 0; d < DIM; ++d)
+#pragma unroll
+            for (int v = 0; v < M; ++v) f[d][v] = T(0);
+    }
+    template <typename T>
+    __device__ __forceinline__ static void flux_delta(const PdeParams &P, const Ref<T> &, const T *q, T (*f)[M]) {
+        flux(P, q, f);
+    }
+    template <typename T>
+    __device__ __forceinline__ static T max_eig(const PdeParams &, const T *q, int) {
+        return sqrt((q[IL] + T(2) * q[IM]) * recip(q[IR]));  // P-wave speed, independent of alpha
+    }
+};
+
+// Launch geometry of the per-element kernels.  A trace record holds the
+// time-averaged state (M), the time-averaged normal flux (M; not for purely
+// non-conservative systems), the wave speed and padding to an even size.
 template <class PDE, int DIM, int N>
 struct Geom {
     static constexpr int n = N + 1;
@@ -333,7 +455,8 @@ struct Geom {
     static constexpr int NS = ipow(n, DIM);        // spatial nodes
     static constexpr int NST = NS * n;             // space-time nodes
     static constexpr int NF = ipow(n, DIM - 1);    // nodes per face
-    static constexpr int RS = 2 * M + 2;           // trace record: q(M) F(M) lambda pad
+    static constexpr int LAM = PDE::NCP ? M : 2 * M;          // wave speed's index in a record
+    static constexpr int RS = (LAM + 1 + 1) / 2 * 2;          // record size
     static constexpr int NREC = DIM * 2 * NF;      // records per element
 };
 
@@ -364,6 +487,7 @@ struct KernelSet {
     int nvar, rs, elem_bytes;  // elem_bytes = sizeof(T)
     int flux_flops, eig_flops;  // per point, for the cost model
     int rf;                     // doubles per element of the FP32 reference record (0: none)
+    int ncp;                    // 1: purely non-conservative system (no flux in the records)
     TileShape pshape[NSHAPE_P], pshape_ex[NSHAPE_P], cshape[NSHAPE_C];  // pshape_ex: extrapolation guess
     int pred_shape, corr_shape;  // indices of the shapes in use
 };

@@ -163,6 +163,7 @@ template <class PDE, int DIM, int N, typename T, int TS = 0>
 struct PredCfg {
     using G = Geom<PDE, DIM, N>;
     static constexpr int n = G::n, M = G::M, NS = G::NS, NST = G::NST, NF = G::NF, NREC = G::NREC;
+    static constexpr int LAM = G::LAM;
     static constexpr int DIMS = DIM;
     // per-element shared buffer: DIM space-time flux fields, later
     // qbar | Fbar_d (| face states, where records outnumber threads)
@@ -194,7 +195,8 @@ struct PredCfg {
     // domains keep the DFMA pipe fed); FP32: 256-thread CTAs.  Shapes 1 and
     // 2 halve and double the CTA at the same register cap per thread.
     static constexpr int TARGET0 = sizeof(T) == 8 ? 128 : 256;
-    static constexpr int MINB0 = sizeof(T) == 8 ? (n * M < 24 ? 3 : 2) : ((n * M <= 20 || (M == 9 && n <= 4)) ? 3 : 2);
+    static constexpr int MINB0 = PDE::NCP ? (sizeof(T) == 8 ? 1 : 2)
+                                 : sizeof(T) == 8 ? (n * M < 24 ? 3 : 2) : ((n * M <= 20 || (M == 9 && n <= 4)) ? 3 : 2);
     static constexpr int TARGET = TS == 1 ? TARGET0 / 2 : (TS == 2 ? TARGET0 * 2 : TARGET0);
     static constexpr int EPB_S = cmax(1, (int)((110 * 1024) / (ELEM * sizeof(T))));
     static constexpr int EPB = cmin(cmax(1, TARGET / NS), EPB_S);
@@ -390,13 +392,62 @@ k_predictor(const KParams P)
             if constexpr (C::DELTA) PDE::flux_delta(P.pde, ref, qq, FF);
             else PDE::flux(P.pde, qq, FF);
         };
+        // the value whose d-derivative each direction needs: the flux F_d, or
+        // for a purely non-conservative system the state itself
+        auto xch = [&](const T *qq, T(*FF)[M]) {
+            if constexpr (PDE::NCP) {
+#pragma unroll
+                for (int d = 0; d < DIM; ++d)
+#pragma unroll
+                    for (int v = 0; v < M; ++v) FF[d][v] = qq[v];
+            } else {
+                flx(qq, FF);
+            }
+        };
+        // the absolute state of a node value (the FP32 path holds perturbations)
+        auto absq = [&](const T *qq, T *qa) {
+#pragma unroll
+            for (int v = 0; v < M; ++v) {
+                if constexpr (C::DELTA) qa[v] = qq[v] + ref.q[v];
+                else qa[v] = qq[v];
+            }
+        };
+        T dx0 = T(0);
+        if constexpr (PDE::HAS_SRC) dx0 = T(1.0 / S.inv_dx[0]);
+        // R = dx_0 L at (t, s) from the exchanged -Dhat_d derivatives in
+        // ebuf: -sum_d (dx_0/dx_d) Dhat_d F_d, or -sum_d (dx_0/dx_d) B_d(q)
+        // Dhat_d q; plus dx_0 S(q).  qq is this node's state at time level t.
+        auto rhs = [&](int t, const T *qq, T *R) {
+            if constexpr (PDE::NCP) {
+                T qa[M];
+                absq(qq, qa);
+                const T ia = recip(qa[PDE::IA]), ir = recip(qa[PDE::IR]);
+#pragma unroll
+                for (int d = 0; d < DIM; ++d) {
+                    T g[M], b[M];
+                    NodeIO<T, M>::load(ebuf + d * C::FSL + t * C::TSL + s * M, g);
+                    PDE::bdot(qa, ia, ir, d, g, b);
+#pragma unroll
+                    for (int v = 0; v < M; ++v) R[v] = d == 0 ? b[v] : R[v] + ratio[d] * b[v];
+                }
+            } else {
+                gather_R<C, T>(ebuf, t, s, ratio, R);
+            }
+            if constexpr (PDE::HAS_SRC) {
+                T qa[M], Sq[M];
+                absq(qq, qa);
+                PDE::source(P.pde, qa, Sq);
+#pragma unroll
+                for (int v = 0; v < M; ++v) R[v] += dx0 * Sq[v];
+            }
+        };
 
-        // R(w) = dx_0 L(w) at this thread's spatial node, L(w) = -sum_d
-        // (1/dx_d) Dhat_d F_d(w): flux of the time-constant w, t = 0 pencils
-        // only (ebuf's t = 0 slice; free again when this returns)
+        // R(w) = dx_0 L(w) at this thread's spatial node for a time-constant
+        // w: t = 0 pencils only (ebuf's t = 0 slice; free again when this
+        // returns).  Every thread of the CTA calls it (barriers).
         auto spatial_R = [&](const T *w, T *R) {
             T F[DIM][M];
-            flx(w, F);
+            xch(w, F);
             if (act) {
 #pragma unroll
                 for (int d = 0; d < DIM; ++d) NodeIO<T, M>::store(ebuf + d * C::FSL + s * M, F[d]);
@@ -405,7 +456,7 @@ k_predictor(const KParams P)
             if (act)
                 for (int item = s; item < DIM * NF * M; item += NS) contract_item_t0<C, T>(ebuf, item, O.Dm[0]);
             __syncthreads();
-            gather_R<C, T>(ebuf, 0, s, ratio, R);
+            rhs(0, w, R);
             __syncthreads();
         };
 
@@ -476,7 +527,7 @@ k_predictor(const KParams P)
 #pragma unroll
             for (int t = 0; t < n; ++t) {
                 T F[DIM][M];
-                flx(q[t], F);
+                xch(q[t], F);
                 if (act) {
 #pragma unroll
                     for (int d = 0; d < DIM; ++d) NodeIO<T, M>::store(ebuf + d * C::FSL + t * C::TSL + s * M, F[d]);
@@ -489,7 +540,7 @@ k_predictor(const KParams P)
                 const T dtT = sDt[0];
                 T R[n][M];
 #pragma unroll
-                for (int t = 0; t < n; ++t) gather_R<C, T>(ebuf, t, s, ratio, R[t]);
+                for (int t = 0; t < n; ++t) rhs(t, q[t], R[t]);
 #pragma unroll
                 for (int v = 0; v < M; ++v)
 #pragma unroll
@@ -521,25 +572,41 @@ k_predictor(const KParams P)
         }
 #pragma unroll
         for (int t = 0; t < n; ++t) {
-            T F[DIM][M];
-            flx(q[t], F);
             const T wt = O.w[t];
 #pragma unroll
-            for (int v = 0; v < M; ++v) {
-                qb[v] += wt * q[t][v];
+            for (int v = 0; v < M; ++v) qb[v] += wt * q[t][v];
+            if constexpr (!PDE::NCP) {
+                T F[DIM][M];
+                flx(q[t], F);
 #pragma unroll
-                for (int d = 0; d < DIM; ++d) Fb[d][v] += wt * F[d][v];
+                for (int v = 0; v < M; ++v)
+#pragma unroll
+                    for (int d = 0; d < DIM; ++d) Fb[d][v] += wt * F[d][v];
             }
         }
+        // purely non-conservative system: the volume integrals of B(q) grad q
+        // at the time nodes average to their value at qbar (B(q) g is linear
+        // in the evolved variables, the material fields are constant in time):
+        // V = L(qbar), one more evaluation on the time-constant qbar
+        T Vnc[M];
+        if constexpr (PDE::NCP) spatial_R(qb, Vnc);
         if (act) {
             NodeIO<T, M>::store(sQ + s * M, qb);
+            if constexpr (!PDE::NCP) {
 #pragma unroll
-            for (int d = 0; d < DIM; ++d) NodeIO<T, M>::store(sFb + (d * NS + s) * M, Fb[d]);
+                for (int d = 0; d < DIM; ++d) NodeIO<T, M>::store(sFb + (d * NS + s) * M, Fb[d]);
+            }
         }
         __syncthreads();
 
-        // ---- volume term V = sum_d (1/dx_d) Kw Fbar_d ----------------------
-        if (valid) {
+        // ---- volume term V = sum_d (1/dx_d) Kw Fbar_d + S(qbar) -------------
+        if constexpr (PDE::NCP) {
+            if (valid) {
+                T *Vout = reinterpret_cast<T *>(S.V) + ec * (NS * M);
+#pragma unroll
+                for (int v = 0; v < M; ++v) Vout[s * M + v] = idx[0] * Vnc[v];
+            }
+        } else if (valid) {
             T *Vout = reinterpret_cast<T *>(S.V) + ec * (NS * M);
             int kd[DIM];
             {
@@ -568,6 +635,13 @@ k_predictor(const KParams P)
 #pragma unroll
                 for (int v = 0; v < M; ++v) Vn[v] += idx[d] * a[v];
             }
+            if constexpr (PDE::HAS_SRC) {  // S linear: its time average is S(qbar)
+                T qa[M], Sq[M];
+                absq(qb, qa);
+                PDE::source(P.pde, qa, Sq);
+#pragma unroll
+                for (int v = 0; v < M; ++v) Vn[v] += Sq[v];
+            }
 #pragma unroll
             for (int v = 0; v < M; ++v) Vout[s * M + v] = Vn[v];
         }
@@ -589,26 +663,28 @@ k_predictor(const KParams P)
                     for (int v = 0; v < M; ++v) { aq[v] = T(0); af[v] = T(0); }
 #pragma unroll
                     for (int j = 0; j < n; ++j) {
-                        T qj[M], fj[M];
+                        T qj[M];
                         NodeIO<T, M>::load(sQ + (s0 + j * pd) * M, qj);
-                        NodeIO<T, M>::load(sFb + (d * NS + s0 + j * pd) * M, fj);
                         const T pj = phi[j];
 #pragma unroll
-                        for (int v = 0; v < M; ++v) {
-                            aq[v] += pj * qj[v];
-                            af[v] += pj * fj[v];
+                        for (int v = 0; v < M; ++v) aq[v] += pj * qj[v];
+                        if constexpr (!PDE::NCP) {
+                            T fj[M];
+                            NodeIO<T, M>::load(sFb + (d * NS + s0 + j * pd) * M, fj);
+#pragma unroll
+                            for (int v = 0; v < M; ++v) af[v] += pj * fj[v];
                         }
                     }
                     T *r = trE + rec * RS;
                     T full[M];
+                    absq(aq, full);
 #pragma unroll
                     for (int v = 0; v < M; ++v) {
                         r[v] = aq[v];
-                        r[M + v] = af[v];
-                        full[v] = aq[v] + (C::DELTA ? ref.q[v] : T(0));
+                        if constexpr (!PDE::NCP) r[M + v] = af[v];
                     }
-                    r[2 * M] = PDE::max_eig(P.pde, full, d);
-                    r[2 * M + 1] = T(0);
+                    r[C::LAM] = PDE::max_eig(P.pde, full, d);
+                    if constexpr (RS > C::LAM + 1) r[C::LAM + 1] = T(0);
                 }
             }
         } else {
@@ -628,12 +704,12 @@ k_predictor(const KParams P)
 #pragma unroll
                     for (int j = 0; j < n; ++j) {
                         aq += phi[j] * sQ[(s0 + j * pd) * M + v];
-                        af += phi[j] * sFb[(d * NS + s0 + j * pd) * M + v];
+                        if constexpr (!PDE::NCP) af += phi[j] * sFb[(d * NS + s0 + j * pd) * M + v];
                     }
                     sStash[rec * M + v] = aq;
                     if (valid) {
                         trE[rec * RS + v] = aq;
-                        trE[rec * RS + M + v] = af;
+                        if constexpr (!PDE::NCP) trE[rec * RS + M + v] = af;
                     }
                 }
             }
@@ -642,10 +718,9 @@ k_predictor(const KParams P)
                 for (int rec = s; rec < NREC; rec += NS) {
                     const int d = rec / (2 * NF);
                     T full[M];
-#pragma unroll
-                    for (int v = 0; v < M; ++v) full[v] = sStash[rec * M + v] + (C::DELTA ? ref.q[v] : T(0));
-                    trE[rec * RS + 2 * M] = PDE::max_eig(P.pde, full, d);
-                    trE[rec * RS + 2 * M + 1] = T(0);
+                    absq(sStash + rec * M, full);
+                    trE[rec * RS + C::LAM] = PDE::max_eig(P.pde, full, d);
+                    if constexpr (RS > C::LAM + 1) trE[rec * RS + C::LAM + 1] = T(0);
                 }
             }
         }
@@ -731,7 +806,11 @@ struct CorrCfg {
     static constexpr size_t O_DEL = O_NBIDX + align16(sizeof(int) * EPB * 2 * DIM);
     static constexpr bool DELTA = sizeof(T) == 4;
     static constexpr int RF = M;
-    static constexpr size_t O_RED = O_DEL + (DELTA ? align16(sizeof(T) * EPB * 2 * DIM * 2 * M) : 0);
+    static constexpr int LAM = G::LAM;
+    // FP32 path of a non-conservative system: each element's reference in T
+    // (the path integral needs absolute face states)
+    static constexpr size_t O_REFO = O_DEL + (DELTA ? align16(sizeof(T) * EPB * 2 * DIM * 2 * M) : 0);
+    static constexpr size_t O_RED = O_REFO + (DELTA && PDE::NCP ? align16(sizeof(T) * EPB * M) : 0);
     static constexpr size_t BYTES = O_RED + 64 * sizeof(double);
     // copy granules (bytes): the largest of 16/8/4 dividing offsets and sizes
     static constexpr int G_OWN = cgcd((int)OWN, 16);
@@ -770,6 +849,7 @@ k_corrector(const KParams P)
     T *sL = reinterpret_cast<T *>(smem_raw + C::O_LIFT);  // [side][d][k]
     int *sNbIdx = reinterpret_cast<int *>(smem_raw + C::O_NBIDX);
     T *sDel = reinterpret_cast<T *>(smem_raw + C::O_DEL);  // [el][d][side][dF | dq][M]
+    T *sRefO = reinterpret_cast<T *>(smem_raw + C::O_REFO);  // [el][M]
     double *red = reinterpret_cast<double *>(smem_raw + C::O_RED);
 
     for (long long tile = blockIdx.x; tile < P.ntiles; tile += gridDim.x) {
@@ -833,6 +913,12 @@ k_corrector(const KParams P)
 #pragma unroll
                     for (int v = 0; v < M; ++v) qf[v] = narrow<T>(qo[v]);
                     PDE::make_ref(P.pde, qf, rr);
+                    if constexpr (PDE::NCP) {
+                        if (d == 0 && side == 0) {
+#pragma unroll
+                            for (int v = 0; v < M; ++v) sRefO[el * M + v] = qf[v];
+                        }
+                    }
                 }
                 T dF[DIM][M];
                 PDE::flux_delta(P.pde, rr, dq, dF);
@@ -861,16 +947,38 @@ k_corrector(const KParams P)
             const T *nb = sNb + ((size_t)(el * DIM + d) * 2 + side) * NF * RS + p * RS;
             const T *L = side ? own : nb;
             const T *R = side ? nb : own;
-            const T smax = tmax(L[2 * M], R[2 * M]);
+            const T smax = tmax(L[C::LAM], R[C::LAM]);
             const T *dl = sDel + ((((el * DIM + d) * 2 + side) * 2) * M);
             T f[M];
+            if constexpr (PDE::NCP) {
+                // path-conservative Rusanov (eq. pc.scheme, eq. rusanov): the
+                // lower element (side 1) receives -Theta dq/2 + J/2, the upper
+                // one -Theta dq/2 - J/2; Theta = s_max on the evolved variables
+                // only (the material fields obey q_t = 0)
+                T dq[M], qa[M], J[M];
 #pragma unroll
-            for (int v = 0; v < M; ++v) {
-                f[v] = T(0.5) * (L[M + v] + R[M + v]) - T(0.5) * smax * (R[v] - L[v]);
-                if constexpr (C::DELTA) {
-                    // traces are perturbations about each element's own reference:
-                    // add the reference part of the Rusanov flux minus own F_ref
-                    f[v] += (side ? T(0.5) : T(-0.5)) * dl[v] - T(0.5) * smax * dl[M + v];
+                for (int v = 0; v < M; ++v) {
+                    dq[v] = R[v] - L[v];
+                    qa[v] = L[v];
+                    if constexpr (C::DELTA) {
+                        // perturbations about each element's own reference
+                        dq[v] += dl[M + v];
+                        qa[v] += sRefO[el * M + v] - (side ? T(0) : dl[M + v]);
+                    }
+                }
+                PDE::path_jump(qa, dq, d, J);
+                const T hs = side ? T(0.5) : T(-0.5);
+#pragma unroll
+                for (int v = 0; v < M; ++v) f[v] = v < PDE::MEV ? hs * J[v] - T(0.5) * smax * dq[v] : T(0);
+            } else {
+#pragma unroll
+                for (int v = 0; v < M; ++v) {
+                    f[v] = T(0.5) * (L[M + v] + R[M + v]) - T(0.5) * smax * (R[v] - L[v]);
+                    if constexpr (C::DELTA) {
+                        // traces are perturbations about each element's own reference:
+                        // add the reference part of the Rusanov flux minus own F_ref
+                        f[v] += (side ? T(0.5) : T(-0.5)) * dl[v] - T(0.5) * smax * dl[M + v];
+                    }
                 }
             }
 #pragma unroll
@@ -1042,7 +1150,7 @@ const KernelSet KS<PDE, DIM, N, T>::value = {
     CorrCfg<PDE, DIM, N, T>::BYTES,
     &k_cfl<PDE, DIM, N, T>,
     Geom<PDE, DIM, N>::M, Geom<PDE, DIM, N>::RS, (int)sizeof(T), PDE::FLUX_FLOPS, PDE::EIG_FLOPS,
-    PredCfg<PDE, DIM, N, T>::DELTA ? PredCfg<PDE, DIM, N, T>::RF : 0,
+    PredCfg<PDE, DIM, N, T>::DELTA ? PredCfg<PDE, DIM, N, T>::RF : 0, PDE::NCP ? 1 : 0,
     {pred_shape<PDE, DIM, N, T, 0>(), pred_shape<PDE, DIM, N, T, 1>(), pred_shape<PDE, DIM, N, T, 2>(),
      pred_shape<PDE, DIM, N, T, 3>(), pred_shape<PDE, DIM, N, T, 4>()},
     {pred_shape<PDE, DIM, N, T, 0, true>(), pred_shape<PDE, DIM, N, T, 1, true>(),

@@ -86,9 +86,7 @@ extern "C" int aderdg_step_noalloc(const aderdg_mesh_t *mesh, int N, int nVar, c
 {
     if (!mesh || !pde || !u_in || !u_out) return fail(ADERDG_E_INVAL, "NULL argument");
     if (mesh->dim < 2 || mesh->dim > 3) return fail(ADERDG_E_INVAL, "dim must be 2 or 3");
-    const int m = pde->kind == ADERDG_PDE_ADVECTION ? 1
-                  : pde->kind == ADERDG_PDE_EULER   ? mesh->dim + 2
-                  : pde->kind == ADERDG_PDE_ELASTICITY ? 9 : -1;
+    const int m = pde_nvar(pde->kind, mesh->dim);
     if (m < 0 || nVar != m) return fail(ADERDG_E_INVAL, "unknown pde or nVar mismatch");
     if (precision != ADERDG_FP64 && precision != ADERDG_MIXED_FP32) return fail(ADERDG_E_INVAL, "bad precision");
     if (!(dt > 0.0)) return fail(ADERDG_E_INVAL, "dt must be positive");

@@ -14,9 +14,10 @@
 #pragma once
 
 // Used where the plane fits the registers: n^2 m <= 100 floats (2D Euler
-// N <= 4, 2D advection N <= 9); larger orders keep k_predictor.
+// N <= 4, 2D advection N <= 9); larger orders and the purely
+// non-conservative systems keep k_predictor.
 template <class PDE, int N>
-constexpr bool use_xt() { return (N + 1) * (N + 1) * PDE::M <= 100; }
+constexpr bool use_xt() { return !PDE::NCP && (N + 1) * (N + 1) * PDE::M <= 100; }
 
 template <class PDE, int N, int TS>
 struct PredXtCfg {
@@ -119,6 +120,7 @@ k_predictor_xt(const KParams P)
         if (tid == 0) sDt[0] = float(dt * S.inv_dx[0]);
         const float ratio1 = S.ratio_f[1];  // dx_0 / dx_1
         const float idx0 = S.inv_dx_f[0], idx1 = S.inv_dx_f[1];
+        const float dx0 = float(1.0 / S.inv_dx[0]);
 
         const long long e = (tile - S.tile0_p) * EPB + g;
         const bool valid = act && e < S.E;
@@ -136,6 +138,17 @@ k_predictor_xt(const KParams P)
             for (int v = 0; v < M; ++v) urf[v] = dbl_to_flt_rn(uref[v]);
             PDE::make_ref(P.pde, urf, ref);
         }
+        // dx_0 S(ref + w) added to R (linear algebraic source, Sec. 2.1)
+        auto add_src = [&](const float *w, float *R) {
+            if constexpr (PDE::HAS_SRC) {
+                float qa[M], Sq[M];
+#pragma unroll
+                for (int v = 0; v < M; ++v) qa[v] = w[v] + ref.q[v];
+                PDE::source(P.pde, qa, Sq);
+#pragma unroll
+                for (int v = 0; v < M; ++v) R[v] += dx0 * Sq[v];
+            }
+        };
         float u[n][M];
 #pragma unroll
         for (int x = 0; x < n; ++x)
@@ -166,6 +179,7 @@ k_predictor_xt(const KParams P)
                 IO::load(eb + (y * n + x) * M, r);
 #pragma unroll
                 for (int v = 0; v < M; ++v) R[x][v] += ratio1 * r[v];
+                add_src(w[x], R[x]);
             }
             __syncthreads();
         };
@@ -244,6 +258,7 @@ k_predictor_xt(const KParams P)
 #pragma unroll
             for (int t = 0; t < n; ++t) {
                 float Fx[n][M];
+                float Sx[PDE::HAS_SRC ? n : 1][M];  // dx_0 S(q) of the row, before A[t] becomes R
 #pragma unroll
                 for (int x = 0; x < n; ++x) {
                     float F[2][M];
@@ -251,8 +266,19 @@ k_predictor_xt(const KParams P)
 #pragma unroll
                     for (int v = 0; v < M; ++v) Fx[x][v] = F[0][v];
                     if (act) IO::store(eb + ((t * n + y) * n + x) * M, F[1]);
+                    if constexpr (PDE::HAS_SRC) {
+#pragma unroll
+                        for (int v = 0; v < M; ++v) Sx[x][v] = 0.f;
+                        add_src(A[t][x], Sx[x]);
+                    }
                 }
                 xt_contract_x<n, M>(Fx, A[t], Dm);
+                if constexpr (PDE::HAS_SRC) {
+#pragma unroll
+                    for (int x = 0; x < n; ++x)
+#pragma unroll
+                        for (int v = 0; v < M; ++v) A[t][x][v] += Sx[x][v];
+                }
             }
             __syncthreads();
             if (act) {
@@ -353,6 +379,14 @@ k_predictor_xt(const KParams P)
                 }
 #pragma unroll
                 for (int v = 0; v < M; ++v) Vn[v] = idx0 * ax[v] + idx1 * ay[v];
+                if constexpr (PDE::HAS_SRC) {  // S linear: its time average is S(qbar)
+                    float qa[M], Sq[M];
+#pragma unroll
+                    for (int v = 0; v < M; ++v) qa[v] = qb[x][v] + ref.q[v];
+                    PDE::source(P.pde, qa, Sq);
+#pragma unroll
+                    for (int v = 0; v < M; ++v) Vn[v] += Sq[v];
+                }
                 IO::store(Vout + (y * n + x) * M, Vn);
             }
 

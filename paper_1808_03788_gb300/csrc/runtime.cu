@@ -45,13 +45,6 @@ const KernelSet *find_kernels(int pde, int dim, int N, int prec)
     return lookup_kernels(pde, dim, N, prec);
 }
 
-int pde_nvar(int pde, int dim)
-{
-    if (pde == ADERDG_PDE_ADVECTION) return 1;
-    if (pde == ADERDG_PDE_EULER) return dim + 2;
-    if (pde == ADERDG_PDE_ELASTICITY) return 9;
-    return -1;
-}
 
 // ---------------------------------------------------------------------------
 // generic kernels
@@ -117,14 +110,15 @@ __global__ void k_mass_final(const double *partial, int nb, int M, double *out)
 // Predictor trace records [e][d][side][p][RS] (T) -> oracle layout
 // qface/fface [e][d][side][p][v] (double).
 template <typename T>
-__global__ void k_unpack_traces(const T *tr, long long nrec_total, int M, int RS, double *qf, double *ff)
+__global__ void k_unpack_traces(const T *tr, long long nrec_total, int M, int RS, int has_flux, double *qf,
+                                double *ff)
 {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= nrec_total * M) return;
     const long long r = i / M;
     const int v = (int)(i - r * M);
     if (qf) qf[i] = double(tr[r * RS + v]);
-    if (ff) ff[i] = double(tr[r * RS + M + v]);
+    if (ff) ff[i] = has_flux ? double(tr[r * RS + M + v]) : 0.0;  // no flux in purely non-conservative records
 }
 
 template <typename T>
@@ -273,14 +267,19 @@ void fill_cost(const aderdg_t *h, aderdg_info_t *info)
     const double P = h->picard, FF = h->ks->flux_flops, EF = h->ks->eig_flops;
     const double it1 = NS * FF + D * NF * M * 2 * n * n + NS * M * (D - 1) + n * NS * M * 3;
     const double itk = NST * FF + D * NS * M * 2 * n * n + NST * M * (D - 1) + NS * M * n * (2 * n + 2);
-    const double fin = NST * FF + (1 + D) * NST * M * 2 + NS * M * D * 2 * n + NREC * M * 4 * n + NREC * EF;
+    // a purely non-conservative system averages q only and takes its volume
+    // term as one more L evaluation on qbar (it1 without the time expansion)
+    const double fin = h->ks->ncp ? NST * M * 2 + (it1 - n * NS * M * 3) + NS * M + NREC * M * 2 * n + NREC * EF
+                                  : NST * FF + (1 + D) * NST * M * 2 + NS * M * D * 2 * n + NREC * M * 4 * n +
+                                        NREC * EF;
     double pred;
     if (h->guess == 3) pred = NST * M * 2 * n + P * itk + fin;  // steady state (a previous predictor)
     else if (h->guess == 2) pred = 2 * it1 + 2 * NS * M + P * itk + fin;  // it1 counts 3 flops per q value, the
                                                                      // Taylor form 6 over two evaluations
     else if (h->guess == 1) pred = it1 + P * itk + fin;
     else pred = it1 + (P - 1) * itk + fin;
-    const double corr = NREC * M * 6 + NREC + NS * M * (5 * D + 3) + NS * D * (EF + 1);
+    double corr = NREC * M * 6 + NREC + NS * M * (5 * D + 3) + NS * D * (EF + 1);
+    if (h->ks->ncp) corr += NREC * 3 * (FF / D + 2 * M);  // three-point path integral per record
     info->flops_predictor = pred * h->E;
     info->flops_corrector = corr * h->E;
     const double b = h->ks->elem_bytes;
@@ -335,6 +334,7 @@ int aderdg_create(const aderdg_mesh_t *mesh, int N, int nVar, const aderdg_pde_t
     if (pde->kind == ADERDG_PDE_EULER && !(pde->p[0] > 1.0)) return fail(ADERDG_E_INVAL, "gamma must be > 1");
     if (pde->kind == ADERDG_PDE_ELASTICITY && !(pde->p[0] > 0 && pde->p[2] > 0 && pde->p[1] + 2 * pde->p[2] > 0))
         return fail(ADERDG_E_INVAL, "bad elastic parameters");
+    if (pde->kind == ADERDG_PDE_ADVECTION && !(pde->p[3] >= 0.0)) return fail(ADERDG_E_INVAL, "kappa must be >= 0");
 
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
@@ -582,9 +582,11 @@ int aderdg_get_predictor_outputs(aderdg_t *h, double *volume, double *qface, dou
             double *df = where == ADERDG_DEVICE ? fface : (fface ? tmp + ntr : nullptr);
             const unsigned blocks = (unsigned)((ntr + 255) / 256);
             if (eb == 8)
-                k_unpack_traces<double><<<blocks, 256, 0, h->stream>>>((const double *)h->tr, nrec, h->M, h->ks->rs, dq, df);
+                k_unpack_traces<double><<<blocks, 256, 0, h->stream>>>((const double *)h->tr, nrec, h->M, h->ks->rs,
+                                                                       !h->ks->ncp, dq, df);
             else
-                k_unpack_traces<float><<<blocks, 256, 0, h->stream>>>((const float *)h->tr, nrec, h->M, h->ks->rs, dq, df);
+                k_unpack_traces<float><<<blocks, 256, 0, h->stream>>>((const float *)h->tr, nrec, h->M, h->ks->rs,
+                                                                      !h->ks->ncp, dq, df);
             CK(cudaGetLastError());
             if (where != ADERDG_DEVICE) {
                 if (qface) CK(cudaMemcpyAsync(qface, dq, ntr * sizeof(double), cudaMemcpyDeviceToHost, h->stream));

@@ -35,6 +35,7 @@ ADERDG_INSTANCES(ADERDG_DECL)
 #define ADERDG_CODE_advection ADERDG_PDE_ADVECTION
 #define ADERDG_CODE_euler ADERDG_PDE_EULER
 #define ADERDG_CODE_elastic ADERDG_PDE_ELASTICITY
+#define ADERDG_CODE_diffuse ADERDG_PDE_DIFFUSE_ELASTICITY
 
 const KernelSet *lookup_kernels(int pde, int dim, int N, int prec)
 {
@@ -127,8 +128,9 @@ int opt_in(const TileShape &t)
 }
 
 // Synthetic state: a valid background plus a small hashed perturbation
-// (ideal gas: rho ~ 1, rho v ~ 0.1, rho E ~ 2.5, so p > 0).
-__global__ void k_fill_synthetic(double *u, long long count, int M, int euler)
+// (ideal gas: rho ~ 1, rho v ~ 0.1, rho E ~ 2.5, so p > 0; diffuse
+// interface: alpha, lambda, mu, rho ~ 1).
+__global__ void k_fill_synthetic(double *u, long long count, int M, int pde)
 {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= count) return;
@@ -139,7 +141,8 @@ __global__ void k_fill_synthetic(double *u, long long count, int M, int euler)
     const double r = double(h >> 11) * (1.0 / 9007199254740992.0);
     const int v = (int)(i % M);
     double base = 0.0;
-    if (euler) base = v == 0 ? 1.0 : (v == M - 1 ? 2.5 : 0.1);
+    if (pde == ADERDG_PDE_EULER) base = v == 0 ? 1.0 : (v == M - 1 ? 2.5 : 0.1);
+    if (pde == ADERDG_PDE_DIFFUSE_ELASTICITY && v >= M - 4) base = 1.0;
     u[i] = base + 0.01 * r;
 }
 
@@ -229,8 +232,7 @@ int measure(const KernelSet *ks, int pde, int dim, int N, int m, const PdeParams
         goto done;
     }
     fill_ops(kp);
-    k_fill_synthetic<<<(unsigned)((nstate + 255) / 256), 256, 0, st>>>(u, (long long)nstate, m,
-                                                                     pde == ADERDG_PDE_EULER);
+    k_fill_synthetic<<<(unsigned)((nstate + 255) / 256), 256, 0, st>>>(u, (long long)nstate, m, pde);
     CKT(cudaGetLastError());
     CKT(cudaMemcpyAsync(dd, &sd, sizeof(sd), cudaMemcpyHostToDevice, st));
     CKT(cudaMemcpyAsync(ctl, &c, sizeof(c), cudaMemcpyHostToDevice, st));
@@ -263,10 +265,7 @@ done:
     return rc;
 }
 
-int nvar_of(int pde, int dim)
-{
-    return pde == ADERDG_PDE_ADVECTION ? 1 : pde == ADERDG_PDE_EULER ? dim + 2 : pde == ADERDG_PDE_ELASTICITY ? 9 : -1;
-}
+int nvar_of(int pde, int dim) { return pde_nvar(pde, dim); }
 
 // Shapes for a key: process table, cache file, or a measurement.
 int tuned(const KernelSet *ks, int pde, int dim, int N, int prec, const PdeParams &pp, const char *cache, bool force,

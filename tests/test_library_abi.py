@@ -63,6 +63,7 @@ def _create(**kw):
     p = A.aderdg_pde_t()
     p.kind = kw.get("kind", A.ADERDG_PDE_EULER)
     p.p[0] = kw.get("gamma", 1.4)
+    p.p[3] = kw.get("kappa", 0.0)
     cfg = A.aderdg_config_t()
     cfg.precision = kw.get("precision", 0)
     h = A._H()
@@ -81,6 +82,10 @@ def _create(**kw):
     (dict(gamma=1.0), A.ADERDG_E_INVAL),
     (dict(precision=9), A.ADERDG_E_INVAL),
     (dict(kind=A.ADERDG_PDE_ELASTICITY, dim=2, nvar=9), A.ADERDG_E_UNSUPPORTED),
+    (dict(kind=A.ADERDG_PDE_DIFFUSE_ELASTICITY, dim=2, nvar=13), A.ADERDG_E_INVAL),
+    (dict(kind=A.ADERDG_PDE_DIFFUSE_ELASTICITY, dim=3, nvar=9), A.ADERDG_E_INVAL),
+    (dict(kind=A.ADERDG_PDE_DIFFUSE_ELASTICITY, dim=2, nvar=9, N=1), A.ADERDG_E_UNSUPPORTED),
+    (dict(kind=A.ADERDG_PDE_ADVECTION, nvar=1, gamma=1.0, kappa=-0.5), A.ADERDG_E_INVAL),
 ])
 def test_create_rejects_bad_arguments(kw, code):
     rc, h, msg = _create(**kw)
@@ -148,13 +153,15 @@ def test_tile_shape_requests_are_validated():
 
 
 def test_instance_list_covers_the_documented_orders():
-    """The build compiles 2D advection/Euler for N = 1..7 and 3D advection,
-    Euler and elasticity for N = 1..4, each in double and float."""
+    """The build compiles 2D advection/Euler for N = 1..7, 3D advection,
+    Euler and elasticity for N = 1..4 and the diffuse-interface system for
+    N = 2..4 (2D) and 2, 3 (3D), each in double and float."""
     from paper_1808_03788_gb300 import build
     inst = build.instances()
     keys = {(name.split("_")[1], d, n, t) for name, _, d, n, t in inst}
     want = {(tag + "%dd" % d, d, n, t) for tag, d, ns in [("advection", 2, range(1, 8)), ("euler", 2, range(1, 8)),
                                                            ("advection", 3, range(1, 5)), ("euler", 3, range(1, 5)),
-                                                           ("elastic", 3, range(1, 5))]
+                                                           ("elastic", 3, range(1, 5)), ("diffuse", 2, range(2, 5)),
+                                                           ("diffuse", 3, range(2, 4))]
             for n in ns for t in ("double", "float")}
     assert keys == want
