@@ -105,9 +105,12 @@ def test_corrector_matches_oracle(case, precision):
 @pytest.mark.parametrize("case", [(2, 3, (8, 6)), (3, 2, (4, 3, 4))], ids=_ids)
 @pytest.mark.parametrize("precision", [A.ADERDG_FP64, A.ADERDG_MIXED_FP32])
 def test_full_run_matches_oracle(case, precision):
+    """Full CFL runs through a diffuse surface (alpha from 1 to 0.3, where
+    multi-dimensional runs of the scheme stay bounded; with alpha <= 0.1
+    they grow, and both paths amplify their rounding differences)."""
     dim, N, cells = case
     cfg, s = _pair(dim, N, cells, precision=precision)
-    U0 = _di_state(cfg, seed=500 + N, alpha_vac=0.02)
+    U0 = _di_state(cfg, seed=500 + N, alpha_vac=0.3)
     Uo, to, ko, _ = oracle.run(cfg, U0, t_end=0.08)
     s.set_state(U0)
     s.advance(0.08)

@@ -307,6 +307,22 @@ def test_material_interface_transmits_the_impedance_ratio():
     assert abs(refl / (-amp * (Z2 - Z1) / (Z1 + Z2)) - 1) < 0.15
 
 
+def test_multidimensional_run_with_a_soft_surface_stays_bounded():
+    """2D run through a diffuse surface (alpha 1 -> 0.3, tanh of width 0.12)
+    with varying material: bounded energy-like amplitudes to t = 1 (with
+    alpha <= 0.1 this discretization grows without bound in 2D and 3D)."""
+    c = oracle.make_cfg(2, (8, 6), [0, 0], [1, 1], 3, DI, [])
+    X = oracle.node_coords(c)
+    z = X[..., 1]
+    alpha = inputs.smooth_step(z, 0.5, 0.12, 1.0, 0.3)
+    f = np.sin(2 * math.pi * X[..., 0]) * np.cos(2 * math.pi * z)
+    U0 = inputs.diffuse_pack(2, [0.3 * f, 0.2 * f, 0.1 * f], [alpha * f, -alpha * f], alpha,
+                             2.0 + 0.5 * np.sin(2 * math.pi * X[..., 0]), 1.0, 1.2)
+    U, t, k, _ = oracle.run(c, U0, 1.0)
+    assert t == 1.0 and np.isfinite(U).all()
+    assert np.abs(U[..., :5]).max() < 3.0 * np.abs(U0[..., :5]).max()
+
+
 def _pade_sub(N, z):
     """[N / N+1] Pade approximant of exp(z) (closed-form coefficients)."""
     L, M = N, N + 1
