@@ -139,7 +139,9 @@ def test_free_surface_slab_matches_oracle():
         s.advance(0.55)
         Ug, t, k = s.get_state()
     assert (t, k) == (to, ko)
-    assert l2_rel(c, Ug[..., :5], Uo[..., :5]) <= 1e-11
+    live = [0, 1, 3]  # sxx, syy, w_x; sxy and w_y stay at rounding level (~1e-16) on both sides
+    assert l2_rel(c, Ug[..., live], Uo[..., live]) <= 1e-11
+    assert np.abs(Ug[..., [2, 4]]).max() < 1e-12 and np.abs(Uo[..., [2, 4]]).max() < 1e-12
     assert Ug[..., 0][(x > 0.3) & (x < 1.1)].max() > 1.7  # the reflected, sign-flipped stress
 
 
@@ -196,7 +198,7 @@ def test_batch_mixes_non_conservative_and_conservative_solves():
         b.set_state(i, U)
     b.advance(t_end)
     for i, (sp, U) in enumerate(zip(specs, states)):
-        a = [(0, 0), (10, 10), (1, 1)][i]
+        a = [(1, 1), (10, 10), (1, 1)][i]
         with A.Solver(sp.pde.kind, 2, (sp.mesh.cells[0], sp.mesh.cells[1]), (0, 0), a, sp.N,
                       tuple(sp.pde.p[:4])) as s:
             s.set_state(U)
