@@ -42,6 +42,10 @@ WORKLOADS = {
                                     params=(1.0, 2.0, 1.0), ic="pulse"),
     "advection2d_sine_16x16_N3": dict(pde=1, dim=2, cells=(16, 16), N=3, lo=(0.0, 0.0), hi=(1.0, 1.0),
                                       params=(1.0, 1.0), ic="sine"),
+    # the seismic example's base grid (80^3, N = 3) with a synthetic
+    # topography in place of the terrain data
+    "diffuse3d_terrain_80^3_N3": dict(pde=4, dim=3, cells=(80, 80, 80), N=3, lo=(0.0,) * 3, hi=(1.0,) * 3,
+                                      params=(), ic="terrain"),
 }
 DEFAULT_WORKLOAD = "euler2d_vortex_200x200_N4"
 
@@ -60,6 +64,8 @@ def _initial_state(w, X):
         return inputs.euler_vortex(X, lo=w["lo"], hi=w["hi"])
     if w["ic"] == "pulse":
         return inputs.elastic_pulse(X)
+    if w["ic"] == "terrain":
+        return inputs.diffuse_terrain(X)
     return inputs.advection_sine(X, lo=w["lo"], hi=w["hi"])
 
 
@@ -381,13 +387,14 @@ def _equal_l2(A, w, steps):
     return out
 
 
-def _elastic(A, torch, stream, flush, steps, shapes=(0, 0)):
-    """The 3D linear-elasticity workload (64^3 elements, N = 3, 9 variables,
-    Gaussian velocity pulse): both paths, and how far apart they are after
-    the timed steps."""
+def _elastic(A, torch, stream, flush, steps, shapes=(0, 0), workload="elastic3d_pulse_64^3_N3"):
+    """A 3D elasticity workload -- the conservative system (64^3 elements,
+    N = 3, 9 variables, Gaussian velocity pulse) or the diffuse-interface
+    one (80^3, N = 3, 13 variables, synthetic topography): both paths, and
+    how far apart they are after the timed steps."""
     import numpy as np
-    w = dict(WORKLOADS["elastic3d_pulse_64^3_N3"])
-    out = {"workload": "elastic3d_pulse_64^3_N3"}
+    w = dict(WORKLOADS[workload])
+    out = {"workload": workload}
     states = {}
     for name, prec in (("fp64", A.ADERDG_FP64), ("mixed", A.ADERDG_MIXED_FP32)):
         s, _, st, pr, co = _time_single(A, torch, w, prec, stream, steps, 2, flush, 1, shapes)
@@ -593,6 +600,9 @@ def run_ours(args, w, rank, world):
                                             args.l2_steps, probe, hbm, args.workload))
         if args.elastic_steps > 0 and args.workload != "elastic3d_pulse_64^3_N3":
             variants["elastic3d"] = _elastic(A, torch, stream, flush, args.elastic_steps, shapes)
+        if args.diffuse_steps > 0 and args.workload != "diffuse3d_terrain_80^3_N3":
+            variants["diffuse3d"] = _elastic(A, torch, stream, flush, args.diffuse_steps, shapes,
+                                             "diffuse3d_terrain_80^3_N3")
         if args.batched_solves > 0:
             variants["batched"] = _batched(A, torch, args.batched_steps, args.batched_warmup, args.batched_solves,
                                            shapes)
@@ -657,6 +667,8 @@ def main():
                     help="only the headline path (no mixed/batched/served/equal-L2 runs)")
     ap.add_argument("--l2-steps", type=int, default=100)
     ap.add_argument("--elastic-steps", type=int, default=4)
+    ap.add_argument("--diffuse-steps", type=int, default=3,
+                    help="timed steps of the 3D diffuse-interface variant (0: skip)")
     ap.add_argument("--batched-solves", type=int, default=256)
     ap.add_argument("--batched-steps", type=int, default=200, help="timed window of the batched workload")
     ap.add_argument("--batched-warmup", type=int, default=20)
