@@ -165,6 +165,11 @@ struct PredCfg {
     static constexpr int n = G::n, M = G::M, NS = G::NS, NST = G::NST, NF = G::NF, NREC = G::NREC;
     static constexpr int LAM = G::LAM;
     static constexpr int DIMS = DIM;
+    // values per node in the exchange fields: all m (the flux F_d), or for a
+    // purely non-conservative system the leading ones whose derivatives B
+    // uses -- the evolved variables and alpha (the other material fields
+    // enter only as coefficients)
+    static constexpr int MX = PDE::NCP ? PDE::MEV + 1 : M;
     // per-element shared buffer: DIM space-time flux fields, later
     // qbar | Fbar_d (| face states, where records outnumber threads)
     // Exchange field F_d[t][s][v] of an element: time slices TSL values apart
@@ -173,11 +178,14 @@ struct PredCfg {
     // the conflicting 4-byte bank accesses of the store / contract / gather
     // phases gives 7488 -> 4608 wavefronts per iteration and CTA for m = 9,
     // 4160 -> 3200 for m = 5, 832 -> 640 for m = 1 (no gain for other n).
-    static constexpr bool PAD3 = (DIM == 3 && sizeof(T) == 4 && n == 4);
+    static constexpr bool PAD3 = (DIM == 3 && sizeof(T) == 4 && n == 4 && MX % 2 == 1);  // keeps scalar nodes
     static constexpr int TPAD = PAD3 ? 1 : 0;
-    static constexpr int TSL = NS * M + TPAD;
+    static constexpr int TSL = NS * MX + TPAD;
     static constexpr int FSL = n * TSL;
-    static constexpr int ELEM0 = cmax(DIM * FSL + (PAD3 ? 1 : 0), ((1 + DIM) * NS + (NREC > NS ? NREC : 0)) * M);
+    static constexpr int ELEM0x = cmax(DIM * FSL + (PAD3 ? 1 : 0), ((1 + DIM) * NS + (NREC > NS ? NREC : 0)) * M);
+    // the non-conservative layout's vector nodes (MX even) want every
+    // element buffer 16-byte aligned
+    static constexpr int ELEM0 = PDE::NCP ? round_up(ELEM0x, 4) : ELEM0x;
     // Shared-memory bank layout of the 2D FP32 path with 16-byte nodes
     // (Euler, m = 4), chosen per n from a bank-conflict count of the
     // store / contract / gather phases: bit 0 pads the per-element buffer to
@@ -206,6 +214,13 @@ struct PredCfg {
     // thread of shape 0 (65536 / (THREADS0 MINB0)) is kept
     static constexpr int MINB = cmax(1, cmin(2048 / THREADS, (THREADS0 * MINB0) / THREADS));
     static constexpr int SHARED = round_up(DIM * n * n + 2 * n + 1 + n * n, 4);  // Kw, F0, F1, dt/dx, W
+    // every vector access of a node in the exchange fields and in qbar |
+    // Fbar starts on its vector width
+    static_assert((SHARED * sizeof(T)) % 16 == 0, "shared header alignment");
+    static_assert((ELEM * sizeof(T)) % NodeIO<T, MX>::VB == 0 && (TSL * sizeof(T)) % NodeIO<T, MX>::VB == 0 &&
+                      (FSL * sizeof(T)) % NodeIO<T, MX>::VB == 0,
+                  "exchange-field alignment");
+    static_assert((ELEM * sizeof(T)) % NodeIO<T, M>::VB == 0, "element buffer alignment");
     static constexpr size_t BYTES = sizeof(T) * (size_t)(SHARED + EPB * ELEM);
     // FP32 path: perturbation form about the element's node SREF
     static constexpr bool DELTA = sizeof(T) == 4;
@@ -237,7 +252,7 @@ __device__ __forceinline__ void extrap_weights(const Ops<T> &O, T r, T *W)
 template <class C, int D, typename T>
 __device__ __forceinline__ void contract_pencil(T *Fd, int t, int p, const T *Dm)
 {
-    constexpr int n = C::n, M = C::M;
+    constexpr int n = C::n, M = C::MX;
     constexpr int pd = ipow(n, D);
     using IO = NodeIO<T, M>;
     const int s0 = (p % pd) + (p / pd) * pd * n;
@@ -278,7 +293,7 @@ __device__ __forceinline__ void contract_all(T *ebuf, int t0, int p0, int t, int
 template <class C, typename T>
 __device__ __forceinline__ void contract_item_t0(T *ebuf, int item, const T *Dm)
 {
-    constexpr int n = C::n, M = C::M, NF = C::NF;
+    constexpr int n = C::n, M = C::MX, NF = C::NF;
     const int d = item / (NF * M);
     const int r = item - d * (NF * M);
     const int p = r / M, v = r - p * M;
@@ -425,7 +440,7 @@ k_predictor(const KParams P)
 #pragma unroll
                 for (int d = 0; d < DIM; ++d) {
                     T g[M], b[M];
-                    NodeIO<T, M>::load(ebuf + d * C::FSL + t * C::TSL + s * M, g);
+                    NodeIO<T, C::MX>::load(ebuf + d * C::FSL + t * C::TSL + s * C::MX, g);
                     PDE::bdot(qa, ia, ir, d, g, b);
 #pragma unroll
                     for (int v = 0; v < M; ++v) R[v] = d == 0 ? b[v] : R[v] + ratio[d] * b[v];
@@ -450,11 +465,11 @@ k_predictor(const KParams P)
             xch(w, F);
             if (act) {
 #pragma unroll
-                for (int d = 0; d < DIM; ++d) NodeIO<T, M>::store(ebuf + d * C::FSL + s * M, F[d]);
+                for (int d = 0; d < DIM; ++d) NodeIO<T, C::MX>::store(ebuf + d * C::FSL + s * C::MX, F[d]);
             }
             __syncthreads();
             if (act)
-                for (int item = s; item < DIM * NF * M; item += NS) contract_item_t0<C, T>(ebuf, item, O.Dm[0]);
+                for (int item = s; item < DIM * NF * C::MX; item += NS) contract_item_t0<C, T>(ebuf, item, O.Dm[0]);
             __syncthreads();
             rhs(0, w, R);
             __syncthreads();
@@ -530,7 +545,8 @@ k_predictor(const KParams P)
                 xch(q[t], F);
                 if (act) {
 #pragma unroll
-                    for (int d = 0; d < DIM; ++d) NodeIO<T, M>::store(ebuf + d * C::FSL + t * C::TSL + s * M, F[d]);
+                    for (int d = 0; d < DIM; ++d)
+                        NodeIO<T, C::MX>::store(ebuf + d * C::FSL + t * C::TSL + s * C::MX, F[d]);
                 }
             }
             __syncthreads();
