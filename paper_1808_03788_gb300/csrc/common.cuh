@@ -361,9 +361,11 @@ struct DiffuseElastic {
     static constexpr int IA = MEV, IL = MEV + 1, IM = MEV + 2, IR = MEV + 3;  // alpha lambda mu rho
     static constexpr bool NCP = true, HAS_SRC = false;
     static constexpr int KIND = 4;
-    // per point and direction: 2 reciprocals, a (DIM x 3), stress rows
-    // (~3 NSIG), momentum rows (3 DIM), accumulation (2 MEV)
-    static constexpr int FLUX_FLOPS = DIM * (2 + 3 * DIM + 3 * NSIG + 3 * DIM + 2 * MEV);
+    // B(q) times the derivatives at one point, all directions: 2
+    // reciprocals; per direction the velocity derivative (4 DIM), the stress
+    // rows (~3 NSIG) and the momentum rows (4 DIM); the accumulation over
+    // directions (2 M per direction after the first)
+    static constexpr int FLUX_FLOPS = 2 + DIM * (8 * DIM + 3 * NSIG) + (DIM - 1) * 2 * M;
     static constexpr int EIG_FLOPS = 4;
     template <typename T> using Ref = NoRef<T, M>;
     template <typename T>
@@ -488,6 +490,7 @@ struct KernelSet {
     int flux_flops, eig_flops;  // per point, for the cost model
     int rf;                     // doubles per element of the FP32 reference record (0: none)
     int ncp;                    // 1: purely non-conservative system (no flux in the records)
+    int mx;                     // values per node in the predictor's derivative exchange
     TileShape pshape[NSHAPE_P], pshape_ex[NSHAPE_P], cshape[NSHAPE_C];  // pshape_ex: extrapolation guess
     int pred_shape, corr_shape;  // indices of the shapes in use
 };

@@ -265,8 +265,9 @@ void fill_cost(const aderdg_t *h, aderdg_info_t *info)
 {
     const double n = h->n, M = h->M, NS = h->NS, NST = h->NS * h->n, NF = h->NF, NREC = h->NREC, D = h->dim;
     const double P = h->picard, FF = h->ks->flux_flops, EF = h->ks->eig_flops;
-    const double it1 = NS * FF + D * NF * M * 2 * n * n + NS * M * (D - 1) + n * NS * M * 3;
-    const double itk = NST * FF + D * NS * M * 2 * n * n + NST * M * (D - 1) + NS * M * n * (2 * n + 2);
+    const double MX = h->ks->mx;  // variables whose derivatives are taken (all m, or fewer for B-only systems)
+    const double it1 = NS * FF + D * NF * MX * 2 * n * n + NS * MX * (D - 1) + n * NS * M * 3;
+    const double itk = NST * FF + D * NS * MX * 2 * n * n + NST * MX * (D - 1) + NS * M * n * (2 * n + 2);
     // a purely non-conservative system averages q only and takes its volume
     // term as one more L evaluation on qbar (it1 without the time expansion)
     const double fin = h->ks->ncp ? NST * M * 2 + (it1 - n * NS * M * 3) + NS * M + NREC * M * 2 * n + NREC * EF
