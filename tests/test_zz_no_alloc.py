@@ -21,14 +21,17 @@ CASES = [
     (A.ADERDG_PDE_EULER, 2, (20, 16), 4, (0.0, 0.0), (10.0, 10.0), (1.4,), A.ADERDG_FP64),
     (A.ADERDG_PDE_ELASTICITY, 3, (6, 5, 4), 3, (0.0,) * 3, (1.0,) * 3, (1.0, 2.0, 1.0), A.ADERDG_FP64),
     (A.ADERDG_PDE_EULER, 2, (20, 16), 4, (0.0, 0.0), (10.0, 10.0), (1.4,), A.ADERDG_MIXED_FP32),
+    (A.ADERDG_PDE_DIFFUSE_ELASTICITY, 3, (5, 4, 4), 3, (0.0,) * 3, (1.0,) * 3, (), A.ADERDG_MIXED_FP32),
 ]
 
 
 def _ic(pde, X):
+    if pde == A.ADERDG_PDE_DIFFUSE_ELASTICITY:
+        return inputs.diffuse_terrain(X, width=0.1)
     return inputs.euler_vortex(X) if pde == A.ADERDG_PDE_EULER else inputs.elastic_pulse(X)
 
 
-@pytest.mark.parametrize("case", CASES, ids=["euler2d-fp64", "elastic3d-fp64", "euler2d-mixed"])
+@pytest.mark.parametrize("case", CASES, ids=["euler2d-fp64", "elastic3d-fp64", "euler2d-mixed", "diffuse3d-mixed"])
 def test_noalloc_step_matches_handle_path_twice(case):
     import torch
 
