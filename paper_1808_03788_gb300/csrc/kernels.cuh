@@ -213,9 +213,6 @@ struct PredCfg {
     // resident CTAs per SM for the launch bounds: the register cap per
     // thread of shape 0 (65536 / (THREADS0 MINB0)) is kept
     static constexpr int MINB = cmax(1, cmin(2048 / THREADS, (THREADS0 * MINB0) / THREADS));
-    // the extrapolation-guess variant holds the previous predictor's
-    // weights and stream as well: one resident CTA of shape 0 fewer
-    static constexpr int MINB_EX = cmax(1, cmin(2048 / THREADS, (THREADS0 * cmax(1, MINB0 - 1)) / THREADS));
     static constexpr int SHARED = round_up(DIM * n * n + 2 * n + 1 + n * n, 4);  // Kw, F0, F1, dt/dx, W
     // every vector access of a node in the exchange fields and in qbar |
     // Fbar starts on its vector width
@@ -335,8 +332,7 @@ __device__ __forceinline__ void gather_R(const T *ebuf, int t, int s, const T *r
 // EX: the variant that serves the extrapolation guess (guess 3); solves with
 // other guesses use EX = false, which carries no code (or registers) for it.
 template <class PDE, int DIM, int N, typename T, int TS, bool EX>
-__global__ void __launch_bounds__(PredCfg<PDE, DIM, N, T, TS>::THREADS,
-                                  EX ? PredCfg<PDE, DIM, N, T, TS>::MINB_EX : PredCfg<PDE, DIM, N, T, TS>::MINB)
+__global__ void __launch_bounds__(PredCfg<PDE, DIM, N, T, TS>::THREADS, PredCfg<PDE, DIM, N, T, TS>::MINB)
 k_predictor(const KParams P)
 {
     using C = PredCfg<PDE, DIM, N, T, TS>;

@@ -30,8 +30,6 @@ struct PredXtCfg {
     // shape 0 (about 128 threads): 3 CTAs per SM (168 registers; large planes
     // spill a little); shape 2 (about 256 threads): one CTA, up to 255 registers
     static constexpr int MINB = TS == 2 ? 1 : cmax(1, (3 * 128) / THREADS);
-    // the extrapolation-guess variant: one resident CTA fewer (it spills at 3)
-    static constexpr int MINB_EX = TS == 2 ? 1 : cmax(1, (2 * 128) / THREADS);
     // per element: the F_y / R_y field [t][y][x][v]; its size is padded to
     // 16 mod 128 bytes so that neighbouring elements start on other banks
     static constexpr int ELEM = round_up(NST * M, 32) + 4;
@@ -85,8 +83,7 @@ __device__ __forceinline__ void xt_contract_x(const float (*F)[M], float (*R)[M]
 }
 
 template <class PDE, int N, int TS, bool EX>
-__global__ void __launch_bounds__(PredXtCfg<PDE, N, TS>::THREADS,
-                                  EX ? PredXtCfg<PDE, N, TS>::MINB_EX : PredXtCfg<PDE, N, TS>::MINB)
+__global__ void __launch_bounds__(PredXtCfg<PDE, N, TS>::THREADS, PredXtCfg<PDE, N, TS>::MINB)
 k_predictor_xt(const KParams P)
 {
     using C = PredXtCfg<PDE, N, TS>;
