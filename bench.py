@@ -208,7 +208,7 @@ def _config(args, w, world):
     """The workload description both arms print (same keys and values)."""
     from paper_1808_03788_gb300 import inputs
     alpha = {1: 0.3001, 2: 0.1538, 3: 0.0936, 4: 0.0629, 5: 0.0451, 6: 0.0339, 7: 0.0265}[w["N"]]
-    return {"workload": args.workload, "pde": {1: "advection", 2: "euler", 3: "elasticity"}[w["pde"]],
+    return {"workload": args.workload, "pde": {1: "advection", 2: "euler", 3: "elasticity", 4: "diffuse-interface elasticity"}[w["pde"]],
             "dim": w["dim"], "cells": list(w["cells"]), "N": w["N"], "nvar": inputs.nvar(w["pde"], w["dim"]),
             "dofs": int(w["dofs"]), "precision": args.precision, "picard_iters": w["N"] + 1,
             "cfl_alpha": alpha, "l2": "flushed: 256 MiB written between timed steps",
