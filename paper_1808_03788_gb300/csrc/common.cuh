@@ -378,11 +378,11 @@ struct DiffuseElastic {
         return i > j ? sig(j, i)
                      : (i == j ? i : (DIM == 2 ? 2 : (i == 0 && j == 1 ? 3 : (i == 1 && j == 2 ? 4 : 5))));
     }
-    // out = B_d(q) g for the state q (absolute values) and g = dQ/dx_d, with
-    // the inverses ia = 1/alpha and ir = 1/rho of q precomputed
+    // out = B_d(q) g for the state q (absolute values) and g = dQ/dx_d (its
+    // evolved part; ga = dalpha/dx_d), with the inverses ia = 1/alpha and
+    // ir = 1/rho of q precomputed
     template <typename T>
-    __device__ __forceinline__ static void bdot(const T *q, T ia, T ir, int d, const T *g, T *out) {
-        const T ga = g[IA];
+    __device__ __forceinline__ static void bdot(const T *q, T ia, T ir, int d, const T *g, T ga, T *out) {
         T a[DIM];
 #pragma unroll
         for (int i = 0; i < DIM; ++i) a[i] = (g[NSIG + i] - q[NSIG + i] * ia * ga) * ia;
@@ -425,7 +425,7 @@ struct DiffuseElastic {
             T ps[M], b[M];
 #pragma unroll
             for (int v = 0; v < M; ++v) ps[v] = qL[v] + sg[k] * dq[v];
-            bdot(ps, recip(ps[IA]), recip(ps[IR]), d, dq, b);
+            bdot(ps, recip(ps[IA]), recip(ps[IR]), d, dq, dq[IA], b);
 #pragma unroll
             for (int v = 0; v < MEV; ++v) J[v] += wg[k] * b[v];
         }

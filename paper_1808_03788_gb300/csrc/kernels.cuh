@@ -166,10 +166,12 @@ struct PredCfg {
     static constexpr int LAM = G::LAM;
     static constexpr int DIMS = DIM;
     // values per node in the exchange fields: all m (the flux F_d), or for a
-    // purely non-conservative system the leading ones whose derivatives B
-    // uses -- the evolved variables and alpha (the other material fields
-    // enter only as coefficients)
-    static constexpr int MX = PDE::NCP ? PDE::MEV + 1 : M;
+    // purely non-conservative system its evolved variables (the material
+    // fields enter B as coefficients; alpha's gradient, constant in time, is
+    // taken once per tile)
+    static constexpr int MX = PDE::NCP ? PDE::MEV : M;
+    // variables whose time derivative can be nonzero (the rest keep q = u)
+    static constexpr int MR = PDE::NCP ? PDE::MEV : M;
     // per-element shared buffer: DIM space-time flux fields, later
     // qbar | Fbar_d (| face states, where records outnumber threads)
     // Exchange field F_d[t][s][v] of an element: time slices TSL values apart
@@ -429,6 +431,24 @@ k_predictor(const KParams P)
         };
         T dx0 = T(0);
         if constexpr (PDE::HAS_SRC) dx0 = T(1.0 / S.inv_dx[0]);
+        // purely non-conservative system: -Dhat_d alpha at this node, once per
+        // tile (alpha is constant in time), through ebuf's first NS words
+        T gal[PDE::NCP ? DIM : 1];
+        if constexpr (PDE::NCP) {
+            if (act) ebuf[s] = u[PDE::IA];
+            __syncthreads();
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) {
+                const int pd = ipow(n, d);
+                const int kd = (s / pd) % n;
+                const T *a = ebuf + (s - kd * pd);
+                T acc = O.Dm[0][kd * n] * a[0];
+#pragma unroll
+                for (int j = 1; j < n; ++j) acc += O.Dm[0][kd * n + j] * a[j * pd];
+                gal[d] = acc;
+            }
+            __syncthreads();  // ebuf is the exchange field from here on
+        }
         // R = dx_0 L at (t, s) from the exchanged -Dhat_d derivatives in
         // ebuf: -sum_d (dx_0/dx_d) Dhat_d F_d, or -sum_d (dx_0/dx_d) B_d(q)
         // Dhat_d q; plus dx_0 S(q).  qq is this node's state at time level t.
@@ -439,12 +459,14 @@ k_predictor(const KParams P)
                 const T ia = recip(qa[PDE::IA]), ir = recip(qa[PDE::IR]);
 #pragma unroll
                 for (int d = 0; d < DIM; ++d) {
-                    T g[M], b[M];
+                    T g[C::MX], b[M];
                     NodeIO<T, C::MX>::load(ebuf + d * C::FSL + t * C::TSL + s * C::MX, g);
-                    PDE::bdot(qa, ia, ir, d, g, b);
+                    PDE::bdot(qa, ia, ir, d, g, gal[d], b);
 #pragma unroll
-                    for (int v = 0; v < M; ++v) R[v] = d == 0 ? b[v] : R[v] + ratio[d] * b[v];
+                    for (int v = 0; v < C::MR; ++v) R[v] = d == 0 ? b[v] : R[v] + ratio[d] * b[v];
                 }
+#pragma unroll
+                for (int v = C::MR; v < M; ++v) R[v] = T(0);  // the material fields
             } else {
                 gather_R<C, T>(ebuf, t, s, ratio, R);
             }
@@ -558,7 +580,7 @@ k_predictor(const KParams P)
 #pragma unroll
                 for (int t = 0; t < n; ++t) rhs(t, q[t], R[t]);
 #pragma unroll
-                for (int v = 0; v < M; ++v)
+                for (int v = 0; v < C::MR; ++v)  // rows MR.. have R = 0: q stays u there
 #pragma unroll
                     for (int t = 0; t < n; ++t) {
                         T acc = O.iK1W[t * n] * R[0][v];
