@@ -171,7 +171,7 @@ def test_initial_guesses_match_oracle(guess, picard):
     non-conservative product; the extrapolation guess across steps."""
     dim, N, cells = 2, 3, (6, 5)
     cfg, s = _pair(dim, N, cells, guess=guess, picard=picard)
-    U0 = _di_state(cfg, seed=600)
+    U0 = _di_state(cfg, seed=600, alpha_vac=0.3)  # bounded regime: rounding differences do not grow
     Uo, to, ko, _ = oracle.run(cfg, U0, t_end=0.05)
     s.set_state(U0)
     s.advance(0.05)
