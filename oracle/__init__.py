@@ -103,6 +103,8 @@ def lib():
             L.orc_face_flux.argtypes = [cp, C.c_int, dp, dp, dp, dp, dp, dp]
             L.orc_face_flux.restype = None
             L.orc_nevolved.argtypes = [cp]
+            L.orc_cerk_weights.argtypes = [C.c_double, dp]
+            L.orc_cerk_weights.restype = None
             L.orc_cfl_dt.argtypes = [cp, dp]
             L.orc_cfl_dt.restype = C.c_double
             L.orc_step_ex.argtypes = [cp, dp, C.c_double, dp, dp, dp]
@@ -131,7 +133,7 @@ def nvar(pde: int, dim: int) -> int:
     return lib().orc_nvar(pde, dim)
 
 
-GUESS_TRIVIAL, GUESS_ORDER2, GUESS_ORDER3, GUESS_EXTRAP = 0, 1, 2, 3
+GUESS_TRIVIAL, GUESS_ORDER2, GUESS_ORDER3, GUESS_EXTRAP, GUESS_CERK = 0, 1, 2, 3, 4
 
 
 def make_cfg(dim, cells, lo, hi, N, pde, prm=(), picard=0, alpha=0.0, guess=GUESS_TRIVIAL) -> Cfg:
@@ -229,6 +231,13 @@ def initial_guess(cfg: Cfg, u: np.ndarray, dt: float) -> np.ndarray:
     if lib().orc_initial_guess(C.byref(cfg), _p(u), float(dt), _p(q0)):
         raise RuntimeError("orc_initial_guess failed")
     return q0
+
+
+def cerk_weights(theta: float) -> np.ndarray:
+    """The four cubic weights b_i(theta) of the CERK guess."""
+    out = np.zeros(4)
+    lib().orc_cerk_weights(float(theta), _p(out))
+    return out
 
 
 def initial_guess_extrap(cfg: Cfg, u: np.ndarray, dt: float, qprev: np.ndarray, ratio: float) -> np.ndarray:

@@ -89,7 +89,9 @@ typedef struct {
                          0 trivial q = u(t^n); 1 second order u + tau L(u);
                          2 third order u + tau k1 + tau^2 (k2 - k1) / (2 dt);
                          3 extrapolation of the previous step's predictor
-                           (orc_run; the first step, and single steps, use 2) */
+                           (orc_run; the first step, and single steps, use 2);
+                         4 continuous Runge-Kutta (CERK) dense output of the
+                           classical fourth-order method, a cubic in time */
 } orc_cfg;
 
 /* ------------------------------------------------------------------------ */
@@ -425,7 +427,7 @@ int orc_picard_count(const orc_cfg *c)
 {
     if (c->picard != 0) return c->picard;
     if (c->guess == 3) return 2;  /* a degree-N guess: one iteration, plus one */
-    int P = c->N + 1 - (c->guess == 1 ? 1 : c->guess == 2 ? 2 : 0);
+    int P = c->N + 1 - (c->guess == 1 ? 1 : c->guess == 2 ? 2 : c->guess == 4 ? 3 : 0);
     return P < 1 ? 1 : P;
 }
 
@@ -507,6 +509,24 @@ static void l_operator(const orc_cfg *c, const basis *b, const double *w, double
  * beyond the flux term). */
 static int has_nc_or_source(const orc_cfg *c) { return c->pde == 4 || (c->pde == 1 && c->prm[3] != 0.0); }
 
+/* Weights of the continuous extension of the classical fourth-order
+ * Runge-Kutta method (stages at 0, 1/2, 1/2, 1 with a21 = a32 = 1/2,
+ * a43 = 1): the cubics b_i(th), th = tau / dt, that satisfy the order
+ * conditions of a continuous Runge-Kutta scheme to order 3 for every th,
+ *   sum b_i = th, sum b_i c_i = th^2/2, sum b_i c_i^2 = th^3/3,
+ *   sum b_i a_ij c_j = th^3/6,
+ * and reduce to the method's weights 1/6, 1/3, 1/3, 1/6 at th = 1:
+ *   b1 = th - 3 th^2/2 + 2 th^3/3, b2 = b3 = th^2 - 2 th^3/3,
+ *   b4 = -th^2/2 + 2 th^3/3. */
+void orc_cerk_weights(double th, double *bw)
+{
+    const double t2 = th * th, t3 = t2 * th;
+    bw[0] = th - 1.5 * t2 + 2.0 * t3 / 3.0;
+    bw[1] = t2 - 2.0 * t3 / 3.0;
+    bw[2] = bw[1];
+    bw[3] = -0.5 * t2 + 2.0 * t3 / 3.0;
+}
+
 /* Initial guess q0 at the space-time nodes (t^n + tau_t, x_s),
  * tau_t = xi_t dt (Sec. 2.2, written as a Taylor series in time):
  *   0: q0 = u (the trivial guess)
@@ -518,7 +538,10 @@ static int has_nc_or_source(const orc_cfg *c) { return c->pde == 4 || (c->pde ==
  *      start at u:  q0 = u + qprev(1 + xi_t ratio) - qprev(1), the
  *      polynomials evaluated with the Lagrange basis of the time nodes;
  *      without qprev, guess 2.
- * gw holds (3 + dim) ns m values. */
+ *   4: the CERK guess (Sec. 2.2 names continuous extension Runge-Kutta
+ *      schemes): k1 = L(u), k2 = L(u + dt k1/2), k3 = L(u + dt k2/2),
+ *      k4 = L(u + dt k3), q0 = u + dt sum_i b_i(tau/dt) k_i (orc_cerk_weights)
+ * gw holds (5 + dim) ns m values. */
 static void initial_guess(const orc_cfg *c, const basis *b, const double *u, double dt, double *q,
                           double *gw, const double *qprev, double ratio)
 {
@@ -535,6 +558,24 @@ static void initial_guess(const orc_cfg *c, const basis *b, const double *u, dou
                 for (int k = 0; k < n; ++k) v += (Lt[k] - L1[k]) * qprev[(size_t)k * nsm + i];
                 q[(size_t)t * nsm + i] = v;
             }
+        }
+        return;
+    }
+    if (c->guess == 4) {
+        double *k1 = gw, *k2 = gw + nsm, *k3 = gw + 2 * nsm, *k4 = gw + 3 * nsm, *w = gw + 4 * nsm,
+               *tmp = gw + 5 * nsm;
+        l_operator(c, b, u, k1, tmp);
+        for (size_t i = 0; i < nsm; ++i) w[i] = u[i] + 0.5 * dt * k1[i];
+        l_operator(c, b, w, k2, tmp);
+        for (size_t i = 0; i < nsm; ++i) w[i] = u[i] + 0.5 * dt * k2[i];
+        l_operator(c, b, w, k3, tmp);
+        for (size_t i = 0; i < nsm; ++i) w[i] = u[i] + dt * k3[i];
+        l_operator(c, b, w, k4, tmp);
+        for (int t = 0; t < n; ++t) {
+            double bw[4];
+            orc_cerk_weights(b->x[t], bw);
+            for (size_t i = 0; i < nsm; ++i)
+                q[(size_t)t * nsm + i] = u[i] + dt * (bw[0] * k1[i] + bw[1] * k2[i] + bw[2] * k3[i] + bw[3] * k4[i]);
         }
         return;
     }
@@ -621,7 +662,7 @@ static size_t predictor_work_len(const orc_cfg *c)
 {
     int n = c->N + 1;
     size_t nst = (size_t)ipow(n, c->dim + 1), ns = (size_t)ipow(n, c->dim);
-    return nst * c->m * (3 + c->dim) + ns * c->m * (3 + c->dim);
+    return nst * c->m * (3 + c->dim) + ns * c->m * (5 + c->dim);
 }
 
 /* Volume integral of the corrector (third integral of eq. pde.nc.gw2) divided
@@ -768,7 +809,7 @@ int orc_initial_guess(const orc_cfg *c, const double *u, double dt, double *q0)
 {
     basis b;
     if (make_basis(c->N, &b)) return -1;
-    double *gw = malloc(sizeof(double) * (size_t)ipow(c->N + 1, c->dim) * c->m * (3 + c->dim));
+    double *gw = malloc(sizeof(double) * (size_t)ipow(c->N + 1, c->dim) * c->m * (5 + c->dim));
     if (!gw) return -2;
     initial_guess(c, &b, u, dt, q0, gw, NULL, 1.0);
     free(gw);

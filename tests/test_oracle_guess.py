@@ -232,3 +232,95 @@ def test_extrapolation_guess_vortex_error_matches_trivial():
         U1, t, _, _ = oracle.run(cfg, inputs.euler_vortex(X), t_end=0.5)
         errs.append(l2_abs(cfg, U1, inputs.euler_vortex(X, t=t))[0])
     assert abs(errs[1] - errs[0]) <= 1e-3 * errs[0], errs
+
+
+# ---- continuous Runge-Kutta (CERK) guess (Sec. 2.2) -------------------------
+
+RK_C = np.array([0.0, 0.5, 0.5, 1.0])
+RK_A = np.array([[0, 0, 0, 0], [0.5, 0, 0, 0], [0, 0.5, 0, 0], [0, 0, 1.0, 0]])
+
+
+@pytest.mark.parametrize("theta", [0.0, 0.1, 0.3, 0.5, 0.77, 1.0])
+def test_cerk_weights_satisfy_the_continuous_order_conditions(theta):
+    """The dense-output weights b_i(theta) of the classical fourth-order
+    method meet the order conditions of a continuous Runge-Kutta scheme up to
+    order 3 at every theta, and at theta = 1 are the method's own weights."""
+    b = oracle.cerk_weights(theta)
+    assert abs(b.sum() - theta) < 1e-15
+    assert abs(b @ RK_C - theta ** 2 / 2) < 1e-15
+    assert abs(b @ RK_C ** 2 - theta ** 3 / 3) < 1e-15
+    assert abs(b @ (RK_A @ RK_C) - theta ** 3 / 6) < 1e-15
+    if theta == 1.0:
+        np.testing.assert_allclose(b, [1 / 6, 1 / 3, 1 / 3, 1 / 6], rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("dim,N", [(1, 3), (2, 3), (2, 4), (3, 3)])
+def test_cerk_guess_is_exact_for_cubic_data(dim, N):
+    """Linear advection of a polynomial of total degree <= 3: L^4 u = 0 and
+    the CERK guess reproduces the exact space-time solution."""
+    a = [1.7, -0.6, 0.9][:dim]
+    cfg = oracle.make_cfg(dim, [4] * dim, [0.0] * dim, [1.0] * dim, N, oracle.PDE_ADVECTION, a,
+                          guess=oracle.GUESS_CERK)
+    coef = _poly(dim, 3, seed=50 + 10 * dim + N)
+    dt = 0.05
+    ex, X, _ = _space_time(cfg, coef, a, dt)
+    q0 = oracle.initial_guess(cfg, _eval(coef, X)[:, None], dt)
+    np.testing.assert_allclose(q0, ex, rtol=0, atol=1e-11)
+    cfg.guess = oracle.GUESS_ORDER3  # the third-order guess is not exact here
+    assert np.abs(oracle.initial_guess(cfg, _eval(coef, X)[:, None], dt) - ex).max() > 1e-6
+
+
+def test_cerk_guess_misses_exactly_the_quartic_term():
+    """u0 = x^4: with L = -a d/dx the dense output carries
+    dt^4 b_4(theta) L^4 u / 4 = 6 a^4 dt^4 b_4(theta) where the exact
+    solution has tau^4 L^4 u / 24 = a^4 tau^4: the miss is
+    a^4 dt^4 (6 b_4(theta) - theta^4)."""
+    a, N, dt = 1.3, 4, 0.07
+    cfg = oracle.make_cfg(1, [3], [0.0], [1.0], N, oracle.PDE_ADVECTION, [a], guess=oracle.GUESS_CERK)
+    coef = {(4,): 1.0}
+    ex, X, tau = _space_time(cfg, coef, [a], dt)
+    q0 = oracle.initial_guess(cfg, _eval(coef, X)[:, None], dt)
+    want = np.array([a ** 4 * dt ** 4 * (6 * oracle.cerk_weights(t)[3] - t ** 4) for t in tau])
+    np.testing.assert_allclose((q0 - ex)[:, :, 0], np.broadcast_to(want[:, None], (N + 1, N + 1)),
+                               rtol=1e-9, atol=1e-15)
+
+
+def test_cerk_guess_constant_state_and_picard_count():
+    cfg = euler_cfg((3, 3), N=3)
+    cfg.guess = oracle.GUESS_CERK
+    q = inputs.random_state(oracle.PDE_EULER, 2, 1, 1, seed=4)[0, 0]
+    u = np.tile(q, (16, 1))
+    np.testing.assert_allclose(oracle.initial_guess(cfg, u, 0.02), np.broadcast_to(u, (4, 16, 4)), atol=1e-13)
+    for N in range(1, 8):
+        cfg = euler_cfg((2, 2), N=N)
+        cfg.guess = oracle.GUESS_CERK
+        assert oracle.lib().orc_picard_count(cfg) == max(1, N - 2)
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 5])
+def test_cerk_guess_converged_for_linear_advection(N):
+    """1D linear advection: the guess is exact to third order in time, and
+    each Picard iteration adds one order, so max(1, N-3) iterations reach
+    the converged predictor (the space-time solution of degree N)."""
+    K = 5
+    rng = np.random.default_rng(40 + N)
+    U = rng.standard_normal((K, N + 1, 1))
+    mk = lambda g, P: oracle.make_cfg(1, [K], [0.0], [1.0], N, oracle.PDE_ADVECTION, [1.0], picard=P, guess=g)
+    ref = oracle.step(mk(0, N + 1), U, 0.02)
+    got = oracle.step(mk(oracle.GUESS_CERK, max(1, N - 3)), U, 0.02)
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("N", [3, 4])
+def test_cerk_guess_design_order_with_one_iteration(N):
+    """A guess of degree N-1 (or more) in time needs one Picard iteration
+    (Sec. 2.2): Euler density wave, CERK guess, one iteration per step,
+    design order N+1."""
+    errs = []
+    for c in (8, 16):
+        cfg = euler_cfg((c, c), N=N, L=1.0, picard=1)
+        cfg.guess = oracle.GUESS_CERK
+        X = oracle.node_coords(cfg)
+        U1, t, _, _ = oracle.run(cfg, inputs.euler_density_wave(X, L=1.0), t_end=0.2)
+        errs.append(l2_abs(cfg, U1, inputs.euler_density_wave(X, L=1.0, t=t))[0])
+    assert order(*errs) > N + 1 - 0.5, errs
