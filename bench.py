@@ -302,15 +302,18 @@ def _kernels(info, pred_avg, corr_avg, hbm):
 
 def _guess_variants(A, torch, w, stream, flush, steps, warmup, shapes, l2_steps, probe, hbm, workload):
     """The initial guesses of Sec. 2.2 that cut the Picard iterations: the
-    third-order guess with the paper's N-2 iterations and the extrapolation
-    of the previous step's predictor with one.  Both precisions timed like
-    the headline, and the L2 errors against the exact vortex after `l2_steps`
+    third-order guess with the paper's N-2 iterations, the CERK guess (a
+    cubic, degree N-1 at N = 4) with max(1, N-3), and the extrapolation of
+    the previous step's predictor with one.  Both precisions timed like the
+    headline, and the L2 errors against the exact vortex after `l2_steps`
     steps next to the trivial guess's."""
     import numpy as np
 
     from paper_1808_03788_gb300 import inputs
     guesses = (("guess_order3", "third order (k1 = L(u), k2 = L(u + dt k1))", A.ADERDG_GUESS_ORDER3,
                 max(1, w["N"] - 2)),
+               ("guess_cerk", "CERK: cubic dense output of the classical fourth-order Runge-Kutta method",
+                A.ADERDG_GUESS_CERK, max(1, w["N"] - 3)),
                ("guess_extrap", "extrapolation of the previous step's predictor", A.ADERDG_GUESS_EXTRAP, 1))
     out = {}
     for key, desc, guess, P in guesses:

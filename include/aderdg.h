@@ -104,15 +104,23 @@ extern "C" {
  *          previous predictor (the first after aderdg_set_state, or a
  *          predictor call with an explicit dt) takes ORDER3 with its
  *          default count.  Holds n^(d+1) m values per element more.
+ * CERK     continuous extension of the classical fourth-order Runge-Kutta
+ *          method (a CERK scheme, which Sec. 2.2 names): k1 = L(u),
+ *          k2 = L(u + dt k1/2), k3 = L(u + dt k2/2), k4 = L(u + dt k3),
+ *          q0 = u + dt sum_i b_i(tau/dt) k_i with the cubics
+ *          b1 = th - 3th^2/2 + 2th^3/3, b2 = b3 = th^2 - 2th^3/3,
+ *          b4 = -th^2/2 + 2th^3/3 (uniform order 3, degree 3 in time).
  * with tau = t - t^n and L(w) = -div F(w), the element-local nodal
- * derivative of the flux.  The default Picard count after a guess of
- * degree k in time is max(1, N + 1 - k): N+1 for TRIVIAL, N for ORDER2,
- * N-1 for ORDER3 (the paper notes N - k iterations suffice), and 2 for
- * EXTRAP (degree N). */
+ * derivative of the flux (plus -B(w) grad w + S(w) where the PDE has
+ * them).  The default Picard count after a guess of degree k in time is
+ * max(1, N + 1 - k): N+1 for TRIVIAL, N for ORDER2, N-1 for ORDER3, N-2 for
+ * CERK (the paper notes N - k iterations suffice), and 2 for EXTRAP
+ * (degree N). */
 #define ADERDG_GUESS_TRIVIAL 0
 #define ADERDG_GUESS_ORDER2 1
 #define ADERDG_GUESS_ORDER3 2
 #define ADERDG_GUESS_EXTRAP 3
+#define ADERDG_GUESS_CERK 4
 
 /* ---- tile shapes -------------------------------------------------------
  * The predictor is compiled in ADERDG_NUM_PRED_SHAPES launch variants and

@@ -33,7 +33,7 @@ ADERDG_HOST, ADERDG_DEVICE = 0, 1
 ADERDG_NUM_PRED_SHAPES, ADERDG_NUM_CORR_SHAPES = 5, 3
 ADERDG_SHAPE_DEFAULT, ADERDG_SHAPE_AUTOTUNE = 0, -1
 ADERDG_TUNE_FORCE = 1
-ADERDG_GUESS_TRIVIAL, ADERDG_GUESS_ORDER2, ADERDG_GUESS_ORDER3, ADERDG_GUESS_EXTRAP = 0, 1, 2, 3
+ADERDG_GUESS_TRIVIAL, ADERDG_GUESS_ORDER2, ADERDG_GUESS_ORDER3, ADERDG_GUESS_EXTRAP, ADERDG_GUESS_CERK = 0, 1, 2, 3, 4
 
 
 class AderdgError(RuntimeError):

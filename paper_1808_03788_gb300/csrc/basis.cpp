@@ -158,6 +158,12 @@ void fill_typed(const Basis &b, Ops<T> &o)
         o.inv_w[t] = T(b.inv_w[t]);
         o.xi[t] = T(b.x[t]);
         o.hxi2[t] = T(0.5 * b.x[t] * b.x[t]);
+        {  // CERK weights at xi_t: b1, b2 = b3, b4 (cubics of the dense output)
+            const double th = b.x[t], t2 = th * th, t3 = t2 * th;
+            o.rk[0][t] = T(th - 1.5 * t2 + 2.0 * t3 / 3.0);
+            o.rk[1][t] = T(t2 - 2.0 * t3 / 3.0);
+            o.rk[2][t] = T(-0.5 * t2 + 2.0 * t3 / 3.0);
+        }
         double prod = 1.0;
         for (int j = 0; j < n; ++j)
             if (j != t) prod *= b.x[t] - b.x[j];
@@ -217,7 +223,7 @@ void fill_pde_consts(int kind, PdeParams &P)
 int default_picard(int N, int guess)
 {
     if (guess == 3) return 2;  // a degree-N guess: one iteration, plus one
-    const int k = guess == 1 ? 1 : (guess == 2 ? 2 : 0);
+    const int k = guess == 1 ? 1 : (guess == 2 ? 2 : (guess == 4 ? 3 : 0));
     return N + 1 - k < 1 ? 1 : N + 1 - k;
 }
 

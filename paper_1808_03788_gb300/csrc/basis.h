@@ -7,7 +7,7 @@ int gauss_legendre01(int n, double *x, double *w);
 int build_basis(int N, Basis &b);
 double default_alpha(int N);
 // Picard iterations after an initial guess (0 trivial, 1 second order, 2
-// third order): max(1, N + 1 - degree of the guess in time); 3
+// third order, 4 CERK): max(1, N + 1 - degree of the guess in time); 3
 // (extrapolation, degree N): 2
 int default_picard(int N, int guess);
 // number of variables of PDE kind `kind` in dimension dim (-1: unknown)

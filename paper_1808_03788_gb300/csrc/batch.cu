@@ -124,7 +124,7 @@ int make_slot(const aderdg_solve_spec_t &sp, int prec, int guess, int picard, do
     if (!ks) return fail(ADERDG_E_UNSUPPORTED, "no kernels compiled for this (pde, dim, N)");
     if (sp.pde.kind == ADERDG_PDE_EULER && !(sp.pde.p[0] > 1.0)) return fail(ADERDG_E_INVAL, "gamma must be > 1");
     if (sp.pde.kind == ADERDG_PDE_ADVECTION && !(sp.pde.p[3] >= 0.0)) return fail(ADERDG_E_INVAL, "kappa must be >= 0");
-    if (guess < ADERDG_GUESS_TRIVIAL || guess > ADERDG_GUESS_EXTRAP) return fail(ADERDG_E_INVAL, "bad initial guess");
+    if (guess < ADERDG_GUESS_TRIVIAL || guess > ADERDG_GUESS_CERK) return fail(ADERDG_E_INVAL, "bad initial guess");
     s = Slot();
     s.pde = sp.pde.kind;
     s.dim = m.dim;
@@ -168,7 +168,7 @@ __global__ void k_set_tend(Control *const *ctls, const double *t_end, int count)
 
 struct Group {
     int pde = 0, dim = 0, N = 0, prec = 0;
-    bool extrap = false;  // its solves use the extrapolation guess (predictor variant)
+    bool extrap = false;  // its solves use the extrapolation or CERK guess (predictor variant)
     PdeParams pp{};
     const KernelSet *ks = nullptr;  // compiled kernels of the group
     KernelSet kso{};                // the same with the tile shapes in use
@@ -184,7 +184,8 @@ struct Group {
 bool same_group(const Group &g, const Slot &s)
 {
     return g.ks == s.ks && g.pde == s.pde && g.dim == s.dim && g.N == s.N && g.prec == s.prec &&
-           g.extrap == (s.guess == ADERDG_GUESS_EXTRAP) && std::memcmp(&g.pp, &s.pp, sizeof(PdeParams)) == 0;
+           g.extrap == (s.guess == ADERDG_GUESS_EXTRAP || s.guess == ADERDG_GUESS_CERK) &&
+           std::memcmp(&g.pp, &s.pp, sizeof(PdeParams)) == 0;
 }
 
 class Engine {
@@ -296,7 +297,7 @@ public:
             if (gi < 0) {
                 Group g;
                 g.pde = s->pde; g.dim = s->dim; g.N = s->N; g.prec = s->prec; g.pp = s->pp; g.ks = s->ks;
-                g.extrap = s->guess == ADERDG_GUESS_EXTRAP;
+                g.extrap = s->guess == ADERDG_GUESS_EXTRAP || s->guess == ADERDG_GUESS_CERK;
                 ng.push_back(g);
                 gi = (int)ng.size() - 1;
             }
@@ -808,7 +809,7 @@ int aderdg_server_create(const aderdg_server_config_t *cfg, aderdg_server_t **ou
         return fail(ADERDG_E_INVAL, "bad tile shape request");
     }
     s->guess = cfg ? cfg->initial_guess : ADERDG_GUESS_TRIVIAL;
-    if (s->guess < ADERDG_GUESS_TRIVIAL || s->guess > ADERDG_GUESS_EXTRAP) {
+    if (s->guess < ADERDG_GUESS_TRIVIAL || s->guess > ADERDG_GUESS_CERK) {
         delete s;
         return fail(ADERDG_E_INVAL, "bad initial guess");
     }

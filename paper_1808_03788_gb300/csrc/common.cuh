@@ -84,6 +84,7 @@ struct Ops {
     T xi[NMAX];            // time nodes on [0, 1] (initial guesses)
     T hxi2[NMAX];          // xi^2 / 2
     T bw[NMAX];            // barycentric weights 1 / prod_{j != k} (xi_k - xi_j)
+    T rk[3][NMAX];         // CERK dense-output weights b1, b2 = b3, b4 at xi_t
 };
 
 // One solve of a launch (device memory).  Tiles of EPB consecutive
@@ -97,7 +98,7 @@ struct SolveDesc {
     int picard;        // Picard iterations after the initial guess
     int picard_first;  // extrapolation guess: iterations of a step without a previous predictor
     int guess;         // initial guess: 0 trivial, 1 second order, 2 third order,
-                       // 3 extrapolation of the previous predictor (Sec. 2.2)
+                       // 3 extrapolation of the previous predictor, 4 CERK (Sec. 2.2)
     double inv_dx[3];
     float inv_dx_f[3]; // 1/dx_d and dx_0/dx_d in FP32 (precomputed on the host)
     float ratio_f[3];
@@ -491,7 +492,7 @@ struct KernelSet {
     int rf;                     // doubles per element of the FP32 reference record (0: none)
     int ncp;                    // 1: purely non-conservative system (no flux in the records)
     int mx;                     // values per node in the predictor's derivative exchange
-    TileShape pshape[NSHAPE_P], pshape_ex[NSHAPE_P], cshape[NSHAPE_C];  // pshape_ex: extrapolation guess
+    TileShape pshape[NSHAPE_P], pshape_ex[NSHAPE_P], cshape[NSHAPE_C];  // pshape_ex: extrapolation and CERK guesses
     int pred_shape, corr_shape;  // indices of the shapes in use
 };
 

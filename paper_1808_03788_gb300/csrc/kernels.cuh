@@ -331,8 +331,10 @@ __device__ __forceinline__ void gather_R(const T *ebuf, int t, int s, const T *r
     }
 }
 
-// EX: the variant that serves the extrapolation guess (guess 3); solves with
-// other guesses use EX = false, which carries no code (or registers) for it.
+// EX: the variant that serves the guesses with more state -- the
+// extrapolation of the previous predictor (guess 3) and the CERK guess
+// (guess 4); solves with the other guesses use EX = false, which carries no
+// code (or registers) for them.
 template <class PDE, int DIM, int N, typename T, int TS, bool EX>
 __global__ void __launch_bounds__(PredCfg<PDE, DIM, N, T, TS>::THREADS, PredCfg<PDE, DIM, N, T, TS>::MINB)
 k_predictor(const KParams P)
@@ -548,6 +550,34 @@ k_predictor(const KParams P)
                 for (int t = 0; t < n; ++t)
 #pragma unroll
                     for (int v = 0; v < M; ++v) q[t][v] = u[v] + dtT * (O.xi[t] * R1[v]);
+                it0 = 0;
+            } else if (EX && S.guess == 4) {
+                if constexpr (EX) {
+                    // CERK guess (Sec. 2.2): the cubic dense output of the classical
+                    // fourth-order Runge-Kutta method on q' = L(q), q = u + dt sum_i
+                    // b_i(xi) k_i, k2 = L(u + dt k1/2), k3 = L(u + dt k2/2),
+                    // k4 = L(u + dt k3); accumulated stage by stage
+                    T w[M], Rk[M];
+#pragma unroll
+                    for (int t = 0; t < n; ++t)
+#pragma unroll
+                        for (int v = 0; v < M; ++v) q[t][v] = u[v] + dtT * (O.rk[0][t] * R1[v]);
+#pragma unroll
+                    for (int v = 0; v < M; ++v) w[v] = u[v] + T(0.5) * dtT * R1[v];
+#pragma unroll 1
+                    for (int st = 1; st < 4; ++st) {
+                        spatial_R(w, Rk);
+#pragma unroll
+                        for (int t = 0; t < n; ++t) {
+                            const T bt = st == 3 ? O.rk[2][t] : O.rk[1][t];  // constant-bank reads, then a select
+#pragma unroll
+                            for (int v = 0; v < M; ++v) q[t][v] += dtT * (bt * Rk[v]);
+                        }
+                        const T cs = st == 1 ? T(0.5) : T(1);
+#pragma unroll
+                        for (int v = 0; v < M; ++v) w[v] = u[v] + cs * dtT * Rk[v];
+                    }
+                }
                 it0 = 0;
             } else {
                 // trivial guess q = u: its first Picard iteration, taken on

@@ -242,6 +242,39 @@ k_predictor_xt(const KParams P)
 #pragma unroll
                         for (int v = 0; v < M; ++v) A[t][x][v] = u[x][v] + dtT * (O.xi[t] * R1[x][v]);
                 it0 = 0;
+            } else if (EX && S.guess == 4) {
+                if constexpr (EX) {
+                    // CERK guess (Sec. 2.2), stage by stage as in k_predictor
+                    float w[n][M], Rk[n][M];
+#pragma unroll
+                    for (int t = 0; t < n; ++t)
+#pragma unroll
+                        for (int x = 0; x < n; ++x)
+#pragma unroll
+                            for (int v = 0; v < M; ++v) A[t][x][v] = u[x][v] + dtT * (O.rk[0][t] * R1[x][v]);
+#pragma unroll
+                    for (int x = 0; x < n; ++x)
+#pragma unroll
+                        for (int v = 0; v < M; ++v) w[x][v] = u[x][v] + 0.5f * dtT * R1[x][v];
+#pragma unroll 1
+                    for (int st = 1; st < 4; ++st) {
+                        spatial_R(w, Rk);
+#pragma unroll
+                        for (int t = 0; t < n; ++t) {
+                            const float bt = st == 3 ? O.rk[2][t] : O.rk[1][t];
+#pragma unroll
+                            for (int x = 0; x < n; ++x)
+#pragma unroll
+                                for (int v = 0; v < M; ++v) A[t][x][v] += dtT * (bt * Rk[x][v]);
+                        }
+                        const float cs = st == 1 ? 0.5f : 1.0f;
+#pragma unroll
+                        for (int x = 0; x < n; ++x)
+#pragma unroll
+                            for (int v = 0; v < M; ++v) w[x][v] = u[x][v] + cs * dtT * Rk[x][v];
+                    }
+                }
+                it0 = 0;
             } else {
 #pragma unroll
                 for (int t = 0; t < n; ++t)

@@ -275,6 +275,7 @@ void fill_cost(const aderdg_t *h, aderdg_info_t *info)
                                         NREC * EF;
     double pred;
     if (h->guess == 3) pred = NST * M * 2 * n + P * itk + fin;  // steady state (a previous predictor)
+    else if (h->guess == 4) pred = 4 * it1 + 6 * NS * M + P * itk + fin;  // four stages, three stage states
     else if (h->guess == 2) pred = 2 * it1 + 2 * NS * M + P * itk + fin;  // it1 counts 3 flops per q value, the
                                                                      // Taylor form 6 over two evaluations
     else if (h->guess == 1) pred = it1 + P * itk + fin;
@@ -352,7 +353,7 @@ int aderdg_create(const aderdg_mesh_t *mesh, int N, int nVar, const aderdg_pde_t
     h->pde = pde->kind;
     h->precision = prec;
     h->guess = cfg ? cfg->initial_guess : ADERDG_GUESS_TRIVIAL;
-    if (h->guess < ADERDG_GUESS_TRIVIAL || h->guess > ADERDG_GUESS_EXTRAP) {
+    if (h->guess < ADERDG_GUESS_TRIVIAL || h->guess > ADERDG_GUESS_CERK) {
         delete h;
         return fail(ADERDG_E_INVAL, "bad initial guess");
     }
@@ -368,7 +369,7 @@ int aderdg_create(const aderdg_mesh_t *mesh, int N, int nVar, const aderdg_pde_t
         fill_pde_consts(pde->kind, pp);
         const int rc = resolve_shapes(ks, pde->kind, mesh->dim, N, prec, pp, cfg ? cfg->pred_shape : 0,
                                       cfg ? cfg->corr_shape : 0, cfg ? cfg->tune_cache : nullptr,
-                                      h->guess == ADERDG_GUESS_EXTRAP, &h->kso);
+                                      h->guess == ADERDG_GUESS_EXTRAP || h->guess == ADERDG_GUESS_CERK, &h->kso);
         if (rc) { delete h; return rc; }
     }
     h->ks = ks = &h->kso;

@@ -20,8 +20,8 @@ const KernelSet *lookup_kernels(int pde, int dim, int N, int prec);
 // current device: from the process-wide table, else from the text file
 // `cache` (may be NULL), else by timing every shape (and appending the
 // result to `cache`).  Opts the chosen kernels in to their dynamic shared
-// memory.  extrap selects the predictor variant of the extrapolation guess
-// (same shapes).  Returns an ADERDG_* status.
+// memory.  extrap selects the predictor variant of the extrapolation and
+// CERK guesses (same shapes).  Returns an ADERDG_* status.
 int resolve_shapes(const KernelSet *ks, int pde, int dim, int N, int prec, const PdeParams &pp, int pred_req,
                    int corr_req, const char *cache, bool extrap, KernelSet *out);
 

@@ -1,5 +1,6 @@
-"""Parity of the CUDA path with the oracle for the second- and third-order
-initial guesses of the Picard iteration (Sec. 2.2), through the C ABI.
+"""Parity of the CUDA path with the oracle for the initial guesses of the
+Picard iteration (Sec. 2.2: second and third order, extrapolation of the
+previous predictor, CERK), through the C ABI.
 Same tolerances as the trivial guess: one predictor call within 1e-12 of
 the data scale, full runs within 1e-11 relative L2 in FP64 and 1e-6 in the
 mixed path; batched solves equal the same solves alone bitwise."""
@@ -15,7 +16,7 @@ pytestmark = pytest.mark.gpu
 
 GAMMA = 1.4
 EL = (1.0, 2.0, 1.0)
-GUESSES = [A.ADERDG_GUESS_ORDER2, A.ADERDG_GUESS_ORDER3, A.ADERDG_GUESS_EXTRAP]
+GUESSES = [A.ADERDG_GUESS_ORDER2, A.ADERDG_GUESS_ORDER3, A.ADERDG_GUESS_EXTRAP, A.ADERDG_GUESS_CERK]
 
 # (pde, dim, N, cells, L, params)
 CASES = (
@@ -176,7 +177,40 @@ def test_extrapolation_restarts_after_set_state():
     np.testing.assert_array_equal(a, s2.get_state()[0])
 
 
-@pytest.mark.parametrize("guess", [A.ADERDG_GUESS_ORDER3, A.ADERDG_GUESS_EXTRAP])
+@pytest.mark.parametrize("picard", [0, 1])
+def test_full_run_euler_vortex_cerk_guess(picard):
+    """FP64 and mixed full runs with the CERK guess: default count (N-2)
+    and one Picard iteration (a degree N-1 guess for N = 4)."""
+    case = (2, 2, 4, (24, 20), 10.0, (GAMMA,))
+    for prec, tol in ((A.ADERDG_FP64, 1e-11), (A.ADERDG_MIXED_FP32, 1e-6)):
+        cfg, s = _pair(*case, guess=A.ADERDG_GUESS_CERK, picard=picard, precision=prec)
+        U0 = inputs.euler_vortex(oracle.node_coords(cfg))
+        Uo, to, ko, _ = oracle.run(cfg, U0, t_end=0.4)
+        s.set_state(U0)
+        s.advance(0.4)
+        Ug, t, k = s.get_state()
+        assert (t, k) == (to, ko) and k > 2
+        assert l2_rel(cfg, Ug, Uo) <= tol
+
+
+@pytest.mark.parametrize("shapes", [(3, 0), (4, 1)])
+def test_cerk_guess_plane_kernel(shapes):
+    """The plane-owning 2D FP32 predictor with the CERK guess."""
+    case = (2, 2, 2, (12, 10), 10.0, (GAMMA,))
+    cfg = oracle.make_cfg(2, case[3], [0, 0], [10, 10], 2, 2, case[5], picard=1, guess=oracle.GUESS_CERK)
+    U0 = inputs.euler_vortex(oracle.node_coords(cfg))
+    Uo, to, ko, _ = oracle.run(cfg, U0, t_end=0.3)
+    with A.Solver(2, 2, case[3], (0, 0), (10, 10), 2, case[5], precision=A.ADERDG_MIXED_FP32, picard=1,
+                  guess=A.ADERDG_GUESS_CERK, shapes=shapes) as s:
+        s.set_state(U0)
+        s.advance(0.3)
+        Ug, t, k = s.get_state()
+        assert s.info()["pred_shape"] == shapes[0]
+    assert t == to and abs(k - ko) <= 1
+    assert l2_rel(cfg, Ug, Uo) <= 1e-6
+
+
+@pytest.mark.parametrize("guess", [A.ADERDG_GUESS_ORDER3, A.ADERDG_GUESS_EXTRAP, A.ADERDG_GUESS_CERK])
 def test_batch_with_guess_equals_alone(guess):
     mix = [(2, 2, (6, 5), (0, 0), (10, 10), 2, (GAMMA,)), (2, 2, (8, 8), (0, 0), (10, 10), 4, (GAMMA,)),
            (3, 3, (3, 3, 2), (0, 0, 0), (1, 1, 1), 3, EL)]
