@@ -54,6 +54,7 @@ class Cfg(C.Structure):
         ("picard", C.c_int),
         ("alpha", C.c_double),
         ("guess", C.c_int),
+        ("limiter", C.c_int),
     ]
 
 
@@ -105,6 +106,8 @@ def lib():
             L.orc_nevolved.argtypes = [cp]
             L.orc_cerk_weights.argtypes = [C.c_double, dp]
             L.orc_cerk_weights.restype = None
+            L.orc_step_limited.argtypes = [cp, dp, C.c_double, C.POINTER(C.c_int), C.POINTER(C.c_long)]
+            L.orc_subcell_ops.argtypes = [C.c_int, dp, dp]
             L.orc_cfl_dt.argtypes = [cp, dp]
             L.orc_cfl_dt.restype = C.c_double
             L.orc_step_ex.argtypes = [cp, dp, C.c_double, dp, dp, dp]
@@ -136,7 +139,7 @@ def nvar(pde: int, dim: int) -> int:
 GUESS_TRIVIAL, GUESS_ORDER2, GUESS_ORDER3, GUESS_EXTRAP, GUESS_CERK = 0, 1, 2, 3, 4
 
 
-def make_cfg(dim, cells, lo, hi, N, pde, prm=(), picard=0, alpha=0.0, guess=GUESS_TRIVIAL) -> Cfg:
+def make_cfg(dim, cells, lo, hi, N, pde, prm=(), picard=0, alpha=0.0, guess=GUESS_TRIVIAL, limiter=0) -> Cfg:
     c = Cfg()
     c.dim = dim
     for d in range(3):
@@ -151,6 +154,7 @@ def make_cfg(dim, cells, lo, hi, N, pde, prm=(), picard=0, alpha=0.0, guess=GUES
     c.picard = picard
     c.alpha = alpha
     c.guess = guess
+    c.limiter = limiter
     return c
 
 
@@ -342,6 +346,30 @@ def step(cfg: Cfg, U: np.ndarray, dt: float, with_parts: bool = False):
     if rc:
         raise RuntimeError("orc_step failed: %d" % rc)
     return (out, V, qf, ff) if with_parts else out
+
+
+def step_limited(cfg: Cfg, U: np.ndarray, dt: float):
+    """One step with the subcell limiter: (u^{n+1}, troubled[E] flags, count)."""
+    out = np.array(U, dtype=np.float64, copy=True, order="C")
+    E = n_elems(cfg)
+    flags = np.zeros(E, dtype=np.int32)
+    cnt = C.c_long(0)
+    rc = lib().orc_step_limited(C.byref(cfg), _p(out), float(dt), flags.ctypes.data_as(C.POINTER(C.c_int)),
+                                C.byref(cnt))
+    if rc:
+        raise RuntimeError("orc_step_limited failed: %d" % rc)
+    return out, flags, cnt.value
+
+
+def subcell_ops(N: int):
+    """1D subcell operators: Pr[(2N+1), N+1] (subcell averages of the nodal
+    basis) and Rc[N+1, 2N+1] (least-squares reconstruction)."""
+    n, S = N + 1, 2 * N + 1
+    Pr = np.zeros((S, n))
+    Rc = np.zeros((n, S))
+    if lib().orc_subcell_ops(N, _p(Pr), _p(Rc)):
+        raise RuntimeError("orc_subcell_ops failed")
+    return Pr, Rc
 
 
 def run(cfg: Cfg, U: np.ndarray, t_end: float, t0: float = 0.0, max_steps: int = 10**9):

@@ -20,6 +20,12 @@
  *     with the straight-segment path and a three-point Gauss-Legendre rule
  *     for the path integral, eq. rusanov) on time-averaged traces
  *   - CFL time step dt = alpha / sum_d lambda_d^max / dx_d (Sec. 3, CFL eq.)
+ *   - the a posteriori subcell finite-volume limiter (Sec. 2.3): detection
+ *     on the candidate (non-finite values, Euler positivity, a relaxed
+ *     discrete maximum principle on subcell averages), a second-order
+ *     finite-volume step of the troubled elements on (2N+1)^d subcells,
+ *     least-squares reconstruction of the DG polynomial, and the matching
+ *     face fluxes in the unlimited neighbours (readings R25-R28)
  *   - PDEs: linear advection with an optional linear reaction source
  *     S = -kappa q, Euler (Sec. 3.1, eq. euler, ideal gas), the
  *     velocity-stress linear elasticity system obtained from Sec. 3.2 with
@@ -54,6 +60,22 @@
  *      R5); the lower element of a face receives
  *      (fL + fR)/2 - Theta (qR - qL)/2 + J/2 and the upper one the same
  *      with -J/2, J = int_0^1 B_d(psi(s)) ds (qR - qL)
+ *   R25 detection: a candidate element is troubled if a value is not
+ *      finite, if (Euler) density or pressure is not positive at a node or
+ *      in a subcell average, or if a subcell average leaves
+ *      [lo - delta, hi + delta], lo / hi the extreme subcell averages of
+ *      u^n over the element and its 2d face neighbours,
+ *      delta = max(1e-4, 1e-3 (hi - lo))
+ *   R26 the subcell scheme: MUSCL-Hancock with minmod slopes and the
+ *      Rusanov flux, direction by direction (each face flux uses the two
+ *      adjacent subcells' values and normal slopes, with the half-step
+ *      evolution along that direction), ghost data two subcells deep from
+ *      the face neighbours' u^n
+ *   R27 an unlimited neighbour of a troubled element takes, on their common
+ *      face, the subcell fluxes projected onto its face nodes
+ *      (F(p) = sum_seg F_seg int_seg phi_p / w_p) instead of its DG flux
+ *   R28 reconstruction: least squares from the (2N+1)^d subcell averages;
+ *      with equal subcells it keeps the element's mass
  *
  * Layout: u[e][s][v] with v fastest, then x, y, z (s = sx + n*sy + n^2*sz);
  * space-time qhat[t][s][v] with time slowest (the AoS layout of Sec. 2.2).
@@ -92,6 +114,8 @@ typedef struct {
                            (orc_run; the first step, and single steps, use 2);
                          4 continuous Runge-Kutta (CERK) dense output of the
                            classical fourth-order method, a cubic in time */
+    int limiter;      /* 1: a posteriori subcell finite-volume limiter
+                         (Sec. 2.3) after every step */
 } orc_cfg;
 
 /* ------------------------------------------------------------------------ */
@@ -833,6 +857,115 @@ int orc_traces(const orc_cfg *c, const double *qbar, const double *Fbar, double 
 }
 
 /* ------------------------------------------------------------------------ */
+/* Subcell operators of the limiter (Sec. 2.3)                               */
+/* ------------------------------------------------------------------------ */
+
+/* 1D: S = 2N+1 equal subcells of [0,1].
+ *   Pr[j][k] = average of phi_k over subcell j (n-point GL per subcell:
+ *              exact, the integrand has degree N)
+ *   Rc[k][j] = least-squares reconstruction (Pr^T Pr)^{-1} Pr^T
+ *   Sg[k][j] = int over subcell j of phi_k = Pr[j][k] / S */
+typedef struct {
+    int n, S;
+    double Pr[(2 * ORC_MAXN - 1) * ORC_MAXN], Rc[ORC_MAXN * (2 * ORC_MAXN - 1)];
+} subcell_ops;
+
+static int make_subcell_ops(const basis *b, subcell_ops *o)
+{
+    const int n = b->n, S = 2 * n - 1;
+    o->n = n;
+    o->S = S;
+    double xq[ORC_MAXN], wq[ORC_MAXN], phi[ORC_MAXN];
+    if (orc_gauss_legendre(n, xq, wq)) return -1;
+    for (int j = 0; j < S; ++j) {
+        for (int k = 0; k < n; ++k) o->Pr[j * n + k] = 0.0;
+        for (int q = 0; q < n; ++q) {
+            orc_lagrange_eval(n, b->x, (j + xq[q]) / S, phi);
+            for (int k = 0; k < n; ++k) o->Pr[j * n + k] += wq[q] * phi[k];
+        }
+    }
+    /* normal equations: (Pr^T Pr) Rc = Pr^T */
+    double A[ORC_MAXN * ORC_MAXN];
+    int piv[ORC_MAXN];
+    for (int k = 0; k < n; ++k)
+        for (int l = 0; l < n; ++l) {
+            double a = 0.0;
+            for (int j = 0; j < S; ++j) a += o->Pr[j * n + k] * o->Pr[j * n + l];
+            A[k * n + l] = a;
+        }
+    if (lu_factor(n, A, piv)) return -1;
+    for (int j = 0; j < S; ++j) {
+        double col[ORC_MAXN];
+        for (int k = 0; k < n; ++k) col[k] = o->Pr[j * n + k];
+        lu_solve(n, A, piv, col);
+        for (int k = 0; k < n; ++k) o->Rc[k * S + j] = col[k];
+    }
+    return 0;
+}
+
+/* Subcell averages of one element's nodal state: avg[sub][v] =
+ * sum_s prod_d Pr[sub_d][s_d] u[s][v] (S^d x m). */
+static void subcell_averages(const orc_cfg *c, const subcell_ops *o, const double *u, double *avg)
+{
+    const int n = o->n, S = o->S, dim = c->dim, m = c->m, ns = ipow(n, dim), nsub = ipow(S, dim);
+    for (int a = 0; a < nsub; ++a)
+        for (int v = 0; v < m; ++v) {
+            double acc = 0.0;
+            for (int s = 0; s < ns; ++s) {
+                double wgt = 1.0;
+                for (int d = 0; d < dim; ++d) wgt *= o->Pr[digit(a, S, d) * n + digit(s, n, d)];
+                acc += wgt * u[(size_t)s * m + v];
+            }
+            avg[(size_t)a * m + v] = acc;
+        }
+}
+
+/* Nodal state from subcell averages by least squares (R28). */
+static void subcell_reconstruct(const orc_cfg *c, const subcell_ops *o, const double *avg, double *u)
+{
+    const int n = o->n, S = o->S, dim = c->dim, m = c->m, ns = ipow(n, dim), nsub = ipow(S, dim);
+    for (int s = 0; s < ns; ++s)
+        for (int v = 0; v < m; ++v) {
+            double acc = 0.0;
+            for (int a = 0; a < nsub; ++a) {
+                double wgt = 1.0;
+                for (int d = 0; d < dim; ++d) wgt *= o->Rc[digit(s, n, d) * S + digit(a, S, d)];
+                acc += wgt * avg[(size_t)a * m + v];
+            }
+            u[(size_t)s * m + v] = acc;
+        }
+}
+
+/* Euler admissibility: positive density and pressure. */
+static int euler_admissible(const orc_cfg *c, const double *q)
+{
+    if (c->pde != 2) return 1;
+    const double rho = q[0];
+    double kin = 0.0;
+    for (int k = 0; k < c->dim; ++k) kin += q[1 + k] * q[1 + k];
+    const double p = (c->prm[0] - 1.0) * (q[c->dim + 1] - 0.5 * kin / rho);
+    return rho > 0.0 && p > 0.0;
+}
+
+static double minmod(double a, double b)
+{
+    if (a * b <= 0.0) return 0.0;
+    return fabs(a) < fabs(b) ? a : b;
+}
+
+/* Exported for the pins: the 1D subcell operators of degree N
+ * (Pr: (2N+1) x (N+1), Rc: (N+1) x (2N+1)). */
+int orc_subcell_ops(int N, double *Pr, double *Rc)
+{
+    basis b;
+    subcell_ops o;
+    if (make_basis(N, &b) || make_subcell_ops(&b, &o)) return -1;
+    memcpy(Pr, o.Pr, sizeof(double) * o.S * o.n);
+    memcpy(Rc, o.Rc, sizeof(double) * o.n * o.S);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Whole-mesh operations on the periodic Cartesian grid                      */
 /* ------------------------------------------------------------------------ */
 
@@ -879,6 +1012,208 @@ double orc_cfl_dt(const orc_cfg *c, const double *U)
     return orc_alpha(c) / S;
 }
 
+/* The a posteriori subcell limiter (Sec. 2.3) on a candidate U (in place),
+ * from the state U0 at t^n and the candidate's traces qf / ff:
+ *   1. extreme subcell averages of U0 per element and variable;
+ *   2. detection (R25) -> troubled[e] (may be NULL);
+ *   3. troubled elements: MUSCL-Hancock on their subcells from U0 (R26),
+ *      least-squares reconstruction (R28), boundary subcell fluxes kept;
+ *   4. unlimited face neighbours of troubled elements: their DG face flux on
+ *      the common face replaced by the projected subcell fluxes (R27).
+ * Returns the number of troubled elements, or < 0 on failure. */
+static long apply_limiter(const orc_cfg *c, const basis *b, const double *U0, double *U, const double *qf,
+                          const double *ff, double dt, int *troubled)
+{
+    subcell_ops o;
+    if (make_subcell_ops(b, &o)) return -1;
+    const int n = b->n, S = o.S, dim = c->dim, m = c->m;
+    const int ns = ipow(n, dim), nf = ipow(n, dim - 1), nsub = ipow(S, dim), nline = ipow(S, dim - 1);
+    const long E = n_elems(c);
+    const size_t fsz = (size_t)2 * dim * nf * m;
+    double *mm = malloc(sizeof(double) * (size_t)E * m * 2);          /* [e][v][min|max] of U0 */
+    int *bad = malloc(sizeof(int) * (size_t)E);
+    double *Unew = malloc(sizeof(double) * (size_t)E * ns * m);
+    double *Fb = malloc(sizeof(double) * (size_t)E * dim * 2 * nline * m); /* [e][d][side][line][v] */
+    if (!mm || !bad || !Unew || !Fb) { free(mm); free(bad); free(Unew); free(Fb); return -2; }
+    long count = 0;
+
+    /* 1. extreme subcell averages of u^n */
+#pragma omp parallel
+    {
+        double *avg = malloc(sizeof(double) * (size_t)nsub * m);
+#pragma omp for schedule(static)
+        for (long e = 0; e < E; ++e) {
+            subcell_averages(c, &o, &U0[(size_t)e * ns * m], avg);
+            for (int v = 0; v < m; ++v) {
+                double lo = avg[v], hi = avg[v];
+                for (int a = 1; a < nsub; ++a) {
+                    const double x = avg[(size_t)a * m + v];
+                    lo = x < lo ? x : lo;
+                    hi = x > hi ? x : hi;
+                }
+                mm[((size_t)e * m + v) * 2] = lo;
+                mm[((size_t)e * m + v) * 2 + 1] = hi;
+            }
+        }
+        free(avg);
+    }
+    /* 2. detection on the candidate */
+#pragma omp parallel
+    {
+        double *avg = malloc(sizeof(double) * (size_t)nsub * m);
+#pragma omp for schedule(static) reduction(+ : count)
+        for (long e = 0; e < E; ++e) {
+            const double *u = &U[(size_t)e * ns * m];
+            int t = 0;
+            for (size_t i = 0; i < (size_t)ns * m; ++i) t |= !isfinite(u[i]);
+            for (int s = 0; s < ns && !t; ++s) t |= !euler_admissible(c, &u[(size_t)s * m]);
+            if (!t) {
+                subcell_averages(c, &o, u, avg);
+                for (int a = 0; a < nsub && !t; ++a) t |= !euler_admissible(c, &avg[(size_t)a * m]);
+                for (int v = 0; v < m && !t; ++v) {
+                    double lo = mm[((size_t)e * m + v) * 2], hi = mm[((size_t)e * m + v) * 2 + 1];
+                    for (int d = 0; d < dim; ++d)
+                        for (int off = -1; off <= 1; off += 2) {
+                            const long nb = neighbour(c, e, d, off);
+                            lo = fmin(lo, mm[((size_t)nb * m + v) * 2]);
+                            hi = fmax(hi, mm[((size_t)nb * m + v) * 2 + 1]);
+                        }
+                    const double delta = fmax(1e-4, 1e-3 * (hi - lo));
+                    for (int a = 0; a < nsub && !t; ++a) {
+                        const double x = avg[(size_t)a * m + v];
+                        t |= x < lo - delta || x > hi + delta;
+                    }
+                }
+            }
+            bad[e] = t;
+            count += t;
+        }
+        free(avg);
+    }
+    /* 3. subcell finite-volume step of the troubled elements */
+#pragma omp parallel
+    {
+        double *avg = malloc(sizeof(double) * (size_t)(1 + 2 * dim) * nsub * m);
+        double *dq = malloc(sizeof(double) * (size_t)nsub * m);
+#pragma omp for schedule(dynamic)
+        for (long e = 0; e < E; ++e) {
+            if (!bad[e]) continue;
+            /* slot 0: e; 1 + 2d + (0|1): the neighbour -1 / +1 along d */
+            subcell_averages(c, &o, &U0[(size_t)e * ns * m], avg);
+            for (int d = 0; d < dim; ++d)
+                for (int sd = 0; sd < 2; ++sd)
+                    subcell_averages(c, &o, &U0[(size_t)neighbour(c, e, d, sd ? 1 : -1) * ns * m],
+                                     &avg[(size_t)(1 + 2 * d + sd) * nsub * m]);
+            for (size_t i = 0; i < (size_t)nsub * m; ++i) dq[i] = 0.0;
+            for (int d = 0; d < dim; ++d) {
+                const double h = cell_dx(c, d) / S, r = dt / h;
+                for (int l = 0; l < nline; ++l) {
+                    /* the line of subcells along d through transverse index l */
+                    int base = 0, pw = 1, rem = l;
+                    for (int k = 0; k < dim; ++k) {
+                        if (k != d) { base += (rem % S) * pw; rem /= S; }
+                        pw *= S;
+                    }
+                    const int st = ipow(S, d);
+                    double line[2 * ORC_MAXN + 3][ORC_MAXM];  /* cells -2 .. S+1 */
+                    for (int i = -2; i <= S + 1; ++i) {
+                        const double *src;
+                        if (i < 0) src = &avg[((size_t)(1 + 2 * d) * nsub + base + (S + i) * st) * m];
+                        else if (i >= S) src = &avg[((size_t)(2 + 2 * d) * nsub + base + (i - S) * st) * m];
+                        else src = &avg[((size_t)base + i * st) * m];
+                        memcpy(line[i + 2], src, sizeof(double) * m);
+                    }
+                    double qm[2 * ORC_MAXN + 1][ORC_MAXM], qp[2 * ORC_MAXN + 1][ORC_MAXM];  /* cells -1 .. S */
+                    for (int i = -1; i <= S; ++i) {
+                        double lo[ORC_MAXM], hi[ORC_MAXM], fl[ORC_MAXM], fh[ORC_MAXM];
+                        for (int v = 0; v < m; ++v) {
+                            const double sl = minmod(line[i + 2][v] - line[i + 1][v], line[i + 3][v] - line[i + 2][v]);
+                            lo[v] = line[i + 2][v] - 0.5 * sl;
+                            hi[v] = line[i + 2][v] + 0.5 * sl;
+                        }
+                        orc_flux(c, lo, d, fl);
+                        orc_flux(c, hi, d, fh);
+                        for (int v = 0; v < m; ++v) {
+                            qm[i + 1][v] = lo[v] - 0.5 * r * (fh[v] - fl[v]);
+                            qp[i + 1][v] = hi[v] - 0.5 * r * (fh[v] - fl[v]);
+                        }
+                    }
+                    double Fh[2 * ORC_MAXN + 1][ORC_MAXM];  /* faces 0 .. S (face f: cells f-1 | f) */
+                    for (int f = 0; f <= S; ++f) {
+                        double fl[ORC_MAXM], fr[ORC_MAXM];
+                        orc_flux(c, qp[f], d, fl);
+                        orc_flux(c, qm[f + 1], d, fr);
+                        orc_rusanov(c, d, qp[f], fl, qm[f + 1], fr, Fh[f]);
+                    }
+                    for (int i = 0; i < S; ++i)
+                        for (int v = 0; v < m; ++v) dq[((size_t)base + i * st) * m + v] -= r * (Fh[i + 1][v] - Fh[i][v]);
+                    for (int v = 0; v < m; ++v) {
+                        Fb[((((size_t)e * dim + d) * 2 + 0) * nline + l) * m + v] = Fh[0][v];
+                        Fb[((((size_t)e * dim + d) * 2 + 1) * nline + l) * m + v] = Fh[S][v];
+                    }
+                }
+            }
+            for (size_t i = 0; i < (size_t)nsub * m; ++i) dq[i] += avg[i];
+            subcell_reconstruct(c, &o, dq, &Unew[(size_t)e * ns * m]);
+        }
+        free(avg);
+        free(dq);
+    }
+    /* 4. unlimited neighbours: projected subcell fluxes on the common faces */
+#pragma omp parallel for schedule(static)
+    for (long e = 0; e < E; ++e) {
+        if (bad[e]) continue;
+        for (int d = 0; d < dim; ++d)
+            for (int side = 0; side < 2; ++side) {
+                const long nb = neighbour(c, e, d, side ? 1 : -1);
+                if (!bad[nb]) continue;
+                /* the troubled neighbour's boundary fluxes on this face: its
+                 * side 0 face if e is below it (side 1 of e), else side 1 */
+                const double *Fs = &Fb[(((size_t)nb * dim + d) * 2 + (side ? 0 : 1)) * nline * m];
+                for (int p = 0; p < nf; ++p) {
+                    /* the face node's transverse indices */
+                    int pk[3], rem = p, kk = 0;
+                    for (int k = 0; k < dim; ++k) {
+                        if (k == d) continue;
+                        pk[kk++] = rem % n;
+                        rem /= n;
+                    }
+                    double Ft[ORC_MAXM];
+                    for (int v = 0; v < m; ++v) Ft[v] = 0.0;
+                    for (int l = 0; l < nline; ++l) {
+                        double wgt = 1.0;
+                        int lr = l;
+                        for (int k = 0; k < dim - 1; ++k) {
+                            const int j = lr % S;
+                            lr /= S;
+                            wgt *= o.Pr[j * n + pk[k]] / S / b->w[pk[k]];
+                        }
+                        for (int v = 0; v < m; ++v) Ft[v] += wgt * Fs[(size_t)l * m + v];
+                    }
+                    /* the DG flux this element used on the face */
+                    double lower[ORC_MAXM], upper[ORC_MAXM];
+                    const long el = side ? e : nb, eu = side ? nb : e;
+                    const size_t oL = (size_t)el * fsz + (((size_t)d * 2 + 1) * nf + p) * m;
+                    const size_t oR = (size_t)eu * fsz + (((size_t)d * 2 + 0) * nf + p) * m;
+                    orc_face_flux(c, d, &qf[oL], &ff[oL], &qf[oR], &ff[oR], lower, upper);
+                    const double *Fdg = side ? lower : upper;
+                    for (int s = 0; s < ns; ++s) {
+                        if (face_index(s, n, dim, d) != p) continue;
+                        const int sd = digit(s, n, d);
+                        const double lift = (side ? b->F1[sd] : -b->F0[sd]) / (cell_dx(c, d) * b->w[sd]);
+                        for (int v = 0; v < m; ++v) U[((size_t)e * ns + s) * m + v] -= dt * lift * (Ft[v] - Fdg[v]);
+                    }
+                }
+            }
+    }
+    for (long e = 0; e < E; ++e) {
+        if (bad[e]) memcpy(&U[(size_t)e * ns * m], &Unew[(size_t)e * ns * m], sizeof(double) * ns * m);
+        if (troubled) troubled[e] = bad[e];
+    }
+    free(mm); free(bad); free(Unew); free(Fb);
+    return count;
+}
+
 /* One ADER-DG step with the given dt: predictor on every element, Rusanov
  * on every face, corrector (eq. pde.nc.gw2).  U is overwritten with u^{n+1}.
  * If V_out/qf_out/ff_out are non-NULL, the per-element volume terms and
@@ -892,10 +1227,13 @@ typedef struct {
 } history;
 
 static int step_impl(const orc_cfg *c, double *U, double dt, double *V_out, double *qf_out, double *ff_out,
-                     history *h)
+                     history *h, int *troubled, long *ntroubled)
 {
     basis b;
     if (make_basis(c->N, &b)) return -1;
+    /* the limiter's subcell scheme covers conservative systems without a
+     * source, and needs every step's predictor fresh (no extrapolation) */
+    if (c->limiter && (c->pde == 4 || (c->pde == 1 && c->prm[3] != 0.0) || c->guess == 3)) return -3;
     const int n = b.n, dim = c->dim, m = c->m;
     const int ns = ipow(n, dim), nf = ipow(n, dim - 1);
     const long E = n_elems(c);
@@ -903,7 +1241,9 @@ static int step_impl(const orc_cfg *c, double *U, double dt, double *V_out, doub
     double *V = malloc(sizeof(double) * (size_t)E * ns * m);
     double *qf = malloc(sizeof(double) * (size_t)E * fsz);
     double *ff = malloc(sizeof(double) * (size_t)E * fsz);
-    if (!V || !qf || !ff) { free(V); free(qf); free(ff); return -2; }
+    double *U0 = c->limiter ? malloc(sizeof(double) * (size_t)E * ns * m) : NULL;
+    if (!V || !qf || !ff || (c->limiter && !U0)) { free(V); free(qf); free(ff); free(U0); return -2; }
+    if (U0) memcpy(U0, U, sizeof(double) * (size_t)E * ns * m);
     int err = 0;
 
 #pragma omp parallel
@@ -959,19 +1299,30 @@ static int step_impl(const orc_cfg *c, double *U, double dt, double *V_out, doub
                 U[i] = U[i] + dt * (V[i] - surf);
             }
     }
+    if (c->limiter) {
+        const long cnt = apply_limiter(c, &b, U0, U, qf, ff, dt, troubled);
+        if (cnt < 0) err = (int)cnt;
+        if (ntroubled) *ntroubled = cnt;
+    }
     if (V_out) memcpy(V_out, V, sizeof(double) * (size_t)E * ns * m);
     if (qf_out) memcpy(qf_out, qf, sizeof(double) * (size_t)E * fsz);
     if (ff_out) memcpy(ff_out, ff, sizeof(double) * (size_t)E * fsz);
-    free(V); free(qf); free(ff);
-    return 0;
+    free(V); free(qf); free(ff); free(U0);
+    return err;
 }
 
 int orc_step_ex(const orc_cfg *c, double *U, double dt, double *V_out, double *qf_out, double *ff_out)
 {
-    return step_impl(c, U, dt, V_out, qf_out, ff_out, NULL);
+    return step_impl(c, U, dt, V_out, qf_out, ff_out, NULL, NULL, NULL);
 }
 
 int orc_step(const orc_cfg *c, double *U, double dt) { return orc_step_ex(c, U, dt, NULL, NULL, NULL); }
+
+/* One step with the limiter's outcome: troubled[e] (E ints) and their count. */
+int orc_step_limited(const orc_cfg *c, double *U, double dt, int *troubled, long *ntroubled)
+{
+    return step_impl(c, U, dt, NULL, NULL, NULL, NULL, troubled, ntroubled);
+}
 
 /* Time loop with the CFL step and the clip to t_end:
  *   dtc = orc_cfl_dt(U);  if t + dtc >= t_end: dt = t_end - t, t = t_end
@@ -995,7 +1346,7 @@ int orc_run(const orc_cfg *c, double *U, double t0, double t_end, long max_steps
         double dt, tn;
         if (t + dtc >= t_end) { dt = t_end - t; tn = t_end; }
         else { dt = dtc; tn = t + dtc; }
-        int rc = step_impl(c, U, dt, NULL, NULL, NULL, h);
+        int rc = step_impl(c, U, dt, NULL, NULL, NULL, h, NULL, NULL);
         if (rc) { if (h) { free(hist.prev); free(hist.next); } return rc; }
         if (h) {
             double *tmp = hist.prev; hist.prev = hist.next; hist.next = tmp;
