@@ -173,6 +173,14 @@ typedef struct {
     const char *tune_cache;     /* text file of autotuned shapes, read and
                                    appended; NULL -> process memory only */
     int initial_guess;          /* ADERDG_GUESS_* (0: trivial) */
+    int limiter;                /* 1: the a posteriori subcell finite-volume
+                                   limiter (Sec. 2.3) after every aderdg_step /
+                                   aderdg_advance step: FP64 precision,
+                                   conservative systems without a source
+                                   (advection, Euler, elasticity), not with the
+                                   EXTRAP guess; ADERDG_E_UNSUPPORTED for an
+                                   instance whose subcell arrays do not fit
+                                   a CTA (3D elasticity N = 4) */
 } aderdg_config_t;
 
 typedef struct aderdg_s aderdg_t;
@@ -252,6 +260,12 @@ int aderdg_corrector(aderdg_t *h, double dt);
  * Any pointer may be NULL.  Synchronising. */
 int aderdg_get_predictor_outputs(aderdg_t *h, double *volume, double *qface, double *fface,
                                  int where);
+
+/* Troubled elements of the last limited step (Sec. 2.3): flags[e] = 1 for
+ * an element that the subcell scheme replaced (host array of E ints, may be
+ * NULL), *count their number (may be NULL).  ADERDG_E_INVAL on a handle
+ * without the limiter.  Synchronising. */
+int aderdg_troubled(aderdg_t *h, int *flags, int64_t *count);
 
 /* One full step: dt from the CFL condition on the current state, clipped so
  * that t does not pass t_end (the clipped step sets t = t_end exactly),

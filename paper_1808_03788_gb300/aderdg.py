@@ -62,7 +62,7 @@ class aderdg_config_t(C.Structure):
     _fields_ = [("precision", C.c_int), ("picard_iters", C.c_int), ("cfl_alpha", C.c_double),
                 ("cuda_stream", C.c_void_p), ("alloc", C.POINTER(aderdg_alloc_t)),
                 ("pred_shape", C.c_int), ("corr_shape", C.c_int), ("tune_cache", C.c_char_p),
-                ("initial_guess", C.c_int)]
+                ("initial_guess", C.c_int), ("limiter", C.c_int)]
 
 
 class aderdg_info_t(C.Structure):
@@ -117,6 +117,7 @@ _SIGS = {
     "aderdg_predictor": (C.c_int, [_H, C.c_double]),
     "aderdg_corrector": (C.c_int, [_H, C.c_double]),
     "aderdg_get_predictor_outputs": (C.c_int, [_H, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    "aderdg_troubled": (C.c_int, [_H, C.c_void_p, C.POINTER(C.c_int64)]),
     "aderdg_step": (C.c_int, [_H, C.c_double, _DP]),
     "aderdg_advance": (C.c_int, [_H, C.c_double, C.c_int64]),
     "aderdg_cfl_dt": (C.c_int, [_H, _DP]),
@@ -244,7 +245,7 @@ class Solver:
     def __init__(self, pde: int, dim: int, cells, lo, hi, N: int, params=(),
                  precision: int = ADERDG_FP64, picard: int = 0, alpha: float = 0.0,
                  stream=None, torch_alloc: bool = True, shapes=(0, 0), tune_cache=None,
-                 guess: int = ADERDG_GUESS_TRIVIAL):
+                 guess: int = ADERDG_GUESS_TRIVIAL, limiter: bool = False):
         L = load()
         self.dim, self.N, self.pde = dim, N, pde
         self.m = nvar(pde, dim)
@@ -267,6 +268,7 @@ class Solver:
         cfg.picard_iters = picard
         cfg.cfl_alpha = alpha
         cfg.initial_guess = guess
+        cfg.limiter = 1 if limiter else 0
         _set_shapes(cfg, shapes, tune_cache)
         self._alloc = None
         if stream is not None:
@@ -336,6 +338,13 @@ class Solver:
 
     def corrector(self, dt: float):
         _check(self._L.aderdg_corrector(self._h, float(dt)))
+
+    def troubled(self):
+        """(flags[E], count) of the last limited step."""
+        flags = np.zeros(self.E, dtype=np.int32)
+        cnt = C.c_int64(0)
+        _check(self._L.aderdg_troubled(self._h, flags.ctypes.data, C.byref(cnt)))
+        return flags, cnt.value
 
     def predictor_outputs(self):
         nf = self.n ** (self.dim - 1)

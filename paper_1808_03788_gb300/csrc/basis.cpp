@@ -172,10 +172,60 @@ void fill_typed(const Basis &b, Ops<T> &o)
 }
 }  // namespace
 
+// Subcell operators of the limiter for n = N+1 nodes and S = 2N+1 equal
+// subcells of [0, 1]: pr[j][k] = average over subcell j of the k-th nodal
+// basis polynomial (n-point Gauss rule on the subcell, exact for degree N),
+// rc = (pr^T pr)^{-1} pr^T (least squares), by Gauss-Jordan elimination.
+void fill_subcell_ops(const Basis &b, double *pr, double *rc)
+{
+    const int n = b.n, S = 2 * n - 1;
+    double xq[NMAX], wq[NMAX], bwt[NMAX];
+    gauss_legendre01(n, xq, wq);
+    for (int k = 0; k < n; ++k) {
+        double prod = 1.0;
+        for (int j = 0; j < n; ++j)
+            if (j != k) prod *= b.x[k] - b.x[j];
+        bwt[k] = 1.0 / prod;
+    }
+    for (int j = 0; j < S; ++j)
+        for (int k = 0; k < n; ++k) {
+            double acc = 0.0;
+            for (int q = 0; q < n; ++q) {
+                const double x = (j + xq[q]) / S;
+                double phi = bwt[k];  // Lagrange polynomial k at x (product form)
+                for (int i = 0; i < n; ++i)
+                    if (i != k) phi *= x - b.x[i];
+                acc += wq[q] * phi;
+            }
+            pr[j * n + k] = acc;
+        }
+    double A[NMAX][NMAX + 2 * NMAX - 1];
+    for (int k = 0; k < n; ++k) {
+        for (int l = 0; l < n; ++l) {
+            double a = 0.0;
+            for (int j = 0; j < S; ++j) a += pr[j * n + k] * pr[j * n + l];
+            A[k][l] = a;
+        }
+        for (int j = 0; j < S; ++j) A[k][n + j] = pr[j * n + k];
+    }
+    for (int c = 0; c < n; ++c) {  // the normal matrix is symmetric positive definite: no pivoting
+        const double inv = 1.0 / A[c][c];
+        for (int j = 0; j < n + S; ++j) A[c][j] *= inv;
+        for (int r = 0; r < n; ++r) {
+            if (r == c) continue;
+            const double f = A[r][c];
+            for (int j = 0; j < n + S; ++j) A[r][j] -= f * A[c][j];
+        }
+    }
+    for (int k = 0; k < n; ++k)
+        for (int j = 0; j < S; ++j) rc[k * S + j] = A[k][n + j];
+}
+
 void fill_ops(KParams &kp)
 {
     fill_typed<double>(kp.b, kp.od);
     fill_typed<float>(kp.b, kp.of);
+    fill_subcell_ops(kp.b, kp.lim_pr, kp.lim_rc);
 }
 
 // 0.9 x the von Neumann stability limit of the scheme for 1D linear

@@ -109,6 +109,11 @@ struct SolveDesc {
     double *ref;       // FP32 path: reference state per element [E][M]; unused in FP64
     void *qprev;       // extrapolation guess: last predictor [E][n][NS][M] of T
     Control *ctl;
+    // subcell limiter (FP64 handles): u^n saved before the corrector, the
+    // extreme subcell averages of u^n [E][M][2] and the troubled flags [E]
+    const double *u_prev;
+    double *lim_mm;
+    int *lim_flags;
 };
 
 inline void fill_desc_spacing(SolveDesc &d)
@@ -130,6 +135,10 @@ struct KParams {
     Basis b;
     Ops<double> od;
     Ops<float> of;
+    // subcell limiter operators (2N+1 subcells): averages of the nodal
+    // basis [j][k] and the least-squares reconstruction [k][j]
+    double lim_pr[(2 * NMAX - 1) * NMAX];
+    double lim_rc[NMAX * (2 * NMAX - 1)];
 };
 
 template <typename T> __host__ __device__ inline const Ops<T> &ops_of(const KParams &P);
@@ -492,6 +501,13 @@ struct KernelSet {
     int rf;                     // doubles per element of the FP32 reference record (0: none)
     int ncp;                    // 1: purely non-conservative system (no flux in the records)
     int mx;                     // values per node in the predictor's derivative exchange
+    // subcell limiter kernels (FP64 instances of conservative systems whose
+    // subcell arrays fit one CTA's shared memory; NULL otherwise), 128 threads
+    void (*lim_minmax)(KParams);
+    void (*lim_detect)(KParams);
+    void (*lim_fv)(KParams);
+    void (*lim_couple)(KParams);
+    size_t lim_smem;
     TileShape pshape[NSHAPE_P], pshape_ex[NSHAPE_P], cshape[NSHAPE_C];  // pshape_ex: extrapolation and CERK guesses
     int pred_shape, corr_shape;  // indices of the shapes in use
 };

@@ -1179,6 +1179,24 @@ __global__ void __launch_bounds__(256) k_cfl(const KParams P)
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(&S.ctl->flags, FLAG_NONFINITE);
 }
 
+#include "limiter.cuh"
+
+// The limiter's kernels of one (PDE, d, N), referenced by the FP64 instance
+// only (so that each is compiled once); K: 0 minmax, 1 detect, 2 fv, 3 couple.
+using KernelFn = void (*)(KParams);
+template <class PDE, int DIM, int N, typename T, int K>
+constexpr KernelFn lim_kernel()
+{
+    if constexpr (sizeof(T) == 8 && LimCfg<PDE, DIM, N>::OK) {
+        if constexpr (K == 0) return &k_lim_minmax<PDE, DIM, N>;
+        else if constexpr (K == 1) return &k_lim_detect<PDE, DIM, N>;
+        else if constexpr (K == 2) return &k_lim_fv<PDE, DIM, N>;
+        else return &k_lim_couple<PDE, DIM, N>;
+    } else {
+        return nullptr;
+    }
+}
+
 template <class PDE, int DIM, int N, typename T>
 struct KS {
     static const KernelSet value;
@@ -1219,6 +1237,8 @@ const KernelSet KS<PDE, DIM, N, T>::value = {
     &k_cfl<PDE, DIM, N, T>,
     Geom<PDE, DIM, N>::M, Geom<PDE, DIM, N>::RS, (int)sizeof(T), PDE::FLUX_FLOPS, PDE::EIG_FLOPS,
     PredCfg<PDE, DIM, N, T>::DELTA ? PredCfg<PDE, DIM, N, T>::RF : 0, PDE::NCP ? 1 : 0, PredCfg<PDE, DIM, N, T>::MX,
+    lim_kernel<PDE, DIM, N, T, 0>(), lim_kernel<PDE, DIM, N, T, 1>(), lim_kernel<PDE, DIM, N, T, 2>(),
+    lim_kernel<PDE, DIM, N, T, 3>(), LimCfg<PDE, DIM, N>::BYTES,
     {pred_shape<PDE, DIM, N, T, 0>(), pred_shape<PDE, DIM, N, T, 1>(), pred_shape<PDE, DIM, N, T, 2>(),
      pred_shape<PDE, DIM, N, T, 3>(), pred_shape<PDE, DIM, N, T, 4>()},
     {pred_shape<PDE, DIM, N, T, 0, true>(), pred_shape<PDE, DIM, N, T, 1, true>(),

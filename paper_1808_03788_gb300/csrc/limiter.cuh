@@ -1,0 +1,448 @@
+// A posteriori subcell finite-volume limiter (Sec. 2.3) of the FP64 path.
+//
+// After the unlimited step has produced a candidate u* (in place of u^n,
+// which the step saved to u_prev):
+//   k_lim_minmax  extreme subcell averages of u^n per element and variable
+//   k_lim_detect  troubled elements: non-finite values, Euler positivity at
+//                 the nodes and in the subcell averages, or a subcell average
+//                 of u* outside the relaxed discrete maximum principle
+//                 [lo - delta, hi + delta] of u^n over the element and its
+//                 2d face neighbours, delta = max(1e-4, 1e-3 (hi - lo))
+//   k_lim_fv      troubled elements: MUSCL-Hancock with minmod slopes and
+//                 Rusanov fluxes on (2N+1)^d subcells of u^n (direction by
+//                 direction, ghost subcells two deep from the face
+//                 neighbours), then least-squares reconstruction
+//   k_lim_couple  unlimited elements next to troubled ones: the DG face
+//                 flux the corrector applied on the common face is replaced
+//                 by the subcell fluxes projected onto the face nodes
+// Both sides of a face between a troubled and an unlimited element, and of
+// a face between two troubled ones, evaluate its subcell fluxes with the
+// same function on the same subcell averages, so the scheme stays
+// conservative.  Each CTA owns one element at a time (grid-stride loop).
+// Included by kernels.cuh inside namespace aderdg.
+#pragma once
+
+template <class PDE, int DIM, int N>
+struct LimCfg {
+    static constexpr int n = N + 1, S = 2 * N + 1, M = PDE::M;
+    static constexpr int NS = ipow(n, DIM), NSUB = ipow(S, DIM), NF = ipow(n, DIM - 1), NLINE = ipow(S, DIM - 1);
+    static constexpr int THREADS = 128;
+    // largest intermediate of a sum-factorised projection or reconstruction
+    static constexpr int TMP = cmax(cmax(S * ipow(n, DIM - 1), ipow(S, DIM - 1) * n),
+                                    DIM == 3 ? cmax(S * S * n, n * n * S) : 0) * M;
+    static constexpr int OPS = round_up(2 * S * n, 2);
+    static constexpr int GHOST = 2 * DIM * 2 * NLINE * M;  // [d][side][layer][line][v]
+    // doubles: operators, staged nodes, own averages, a neighbour's averages,
+    // ghost layers, increments, two projection buffers
+    static constexpr size_t DOUBLES = OPS + round_up(NS * M, 2) + 3 * (size_t)NSUB * M + GHOST + 2 * TMP;
+    static constexpr size_t BYTES = sizeof(double) * DOUBLES;
+    static constexpr bool FITS = BYTES <= 227 * 1024;
+    static constexpr bool OK = FITS && !PDE::NCP;
+};
+
+// out = (Op (x) ... (x) Op) in along the DIM directions, Op an R x C matrix
+// in shared memory ([r][c]); in has C points per direction (x fastest,
+// M values per point), out R.  Every thread of the CTA calls it.
+template <int DIM, int M>
+__device__ void lim_tensor(const double *in, double *out, double *ta, double *tb, const double *Op, int R, int C)
+{
+    const double *src = in;
+    for (int d = 0; d < DIM; ++d) {
+        double *dst = d == DIM - 1 ? out : ((d & 1) ? tb : ta);
+        int lo = 1, hi = 1;
+        for (int k = 0; k < d; ++k) lo *= R;
+        for (int k = d + 1; k < DIM; ++k) hi *= C;
+        const int total = lo * R * hi * M;
+        for (int i = threadIdx.x; i < total; i += blockDim.x) {
+            const int v = i % M;
+            int r = i / M;
+            const int al = r % lo;
+            r /= lo;
+            const int ad = r % R, ah = r / R;
+            double acc = 0.0;
+            for (int j = 0; j < C; ++j) acc += Op[ad * C + j] * src[(al + lo * (j + C * ah)) * M + v];
+            dst[i] = acc;
+        }
+        __syncthreads();
+        src = dst;
+    }
+}
+
+template <class PDE>
+__device__ __forceinline__ bool lim_admissible(const PdeParams &P, const double *q)
+{
+    if constexpr (PDE::KIND == 2) {  // Euler: positive density and pressure
+        constexpr int D = PDE::M - 2;
+        double kin = 0.0;
+#pragma unroll
+        for (int k = 0; k < D; ++k) kin += q[1 + k] * q[1 + k];
+        const double p = pconst<double>(P, 0) * (q[D + 1] - 0.5 * kin / q[0]);
+        return q[0] > 0.0 && p > 0.0;
+    } else {
+        return true;
+    }
+}
+
+__device__ __forceinline__ double lim_minmod(double a, double b)
+{
+    if (a * b <= 0.0) return 0.0;
+    return fabs(a) < fabs(b) ? a : b;
+}
+
+// Subcell flux across the face between cells b and c of a line along d
+// (a, b, c, e: four consecutive subcell averages; r = dt / subcell width):
+// minmod slopes, half-step evolution of the two face extrapolations along
+// d (MUSCL-Hancock), Rusanov flux.  The one routine every face uses.
+template <class PDE, int DIM>
+__device__ void lim_face(const PdeParams &P, const double *a, const double *b, const double *c, const double *e, int d,
+                         double r, double *F)
+{
+    constexpr int M = PDE::M;
+    double lo[M], hi[M], qp[M], qm[M], fl[DIM][M], fh[DIM][M];
+#pragma unroll
+    for (int v = 0; v < M; ++v) {
+        const double s = lim_minmod(b[v] - a[v], c[v] - b[v]);
+        lo[v] = b[v] - 0.5 * s;
+        hi[v] = b[v] + 0.5 * s;
+    }
+    PDE::flux(P, lo, fl);
+    PDE::flux(P, hi, fh);
+#pragma unroll
+    for (int v = 0; v < M; ++v) {
+        double df = fh[0][v] - fl[0][v];
+#pragma unroll
+        for (int k = 1; k < DIM; ++k) df = d == k ? fh[k][v] - fl[k][v] : df;
+        qp[v] = hi[v] - 0.5 * r * df;
+    }
+#pragma unroll
+    for (int v = 0; v < M; ++v) {
+        const double s = lim_minmod(c[v] - b[v], e[v] - c[v]);
+        lo[v] = c[v] - 0.5 * s;
+        hi[v] = c[v] + 0.5 * s;
+    }
+    PDE::flux(P, lo, fl);
+    PDE::flux(P, hi, fh);
+#pragma unroll
+    for (int v = 0; v < M; ++v) {
+        double df = fh[0][v] - fl[0][v];
+#pragma unroll
+        for (int k = 1; k < DIM; ++k) df = d == k ? fh[k][v] - fl[k][v] : df;
+        qm[v] = lo[v] - 0.5 * r * df;
+    }
+    PDE::flux(P, qp, fl);
+    PDE::flux(P, qm, fh);
+    const double sl = PDE::max_eig(P, qp, d), sr = PDE::max_eig(P, qm, d);
+    const double smax = sl > sr ? sl : sr;
+#pragma unroll
+    for (int v = 0; v < M; ++v) {
+        double fsum = fl[0][v] + fh[0][v];
+#pragma unroll
+        for (int k = 1; k < DIM; ++k) fsum = d == k ? fl[k][v] + fh[k][v] : fsum;
+        F[v] = 0.5 * fsum - 0.5 * smax * (qm[v] - qp[v]);
+    }
+}
+
+// index of the subcell at position i along d on line l (the other indices
+// of l in increasing direction order)
+template <int DIM, int S>
+__device__ __forceinline__ int lim_cell(int d, int l, int i)
+{
+    int idx = 0, pw = 1, rem = l;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+        int x;
+        if (k == d) {
+            x = i;
+        } else {
+            x = rem % S;
+            rem /= S;
+        }
+        idx += x * pw;
+        pw *= S;
+    }
+    return idx;
+}
+
+// Shared-memory layout of the limiter kernels.
+template <class L>
+struct LimSmem {
+    double *Pr, *Rc, *u, *avg, *nb, *ghost, *dq, *ta, *tb;
+    __device__ explicit LimSmem(double *base)
+    {
+        Pr = base;
+        Rc = Pr + L::S * L::n;
+        u = base + L::OPS;
+        avg = u + round_up(L::NS * L::M, 2);
+        nb = avg + (size_t)L::NSUB * L::M;
+        ghost = nb + (size_t)L::NSUB * L::M;
+        dq = ghost + L::GHOST;
+        ta = dq + (size_t)L::NSUB * L::M;
+        tb = ta + L::TMP;
+    }
+};
+
+template <class L>
+__device__ void lim_load_ops(const KParams &P, LimSmem<L> &sm)
+{
+    for (int i = threadIdx.x; i < L::S * L::n; i += blockDim.x) {
+        sm.Pr[i] = P.lim_pr[i];
+        sm.Rc[i] = P.lim_rc[i];
+    }
+    __syncthreads();
+}
+
+// subcell averages of element e's nodal state src into dst
+template <class L, int DIM>
+__device__ void lim_averages(const double *src, long long e, LimSmem<L> &sm, double *dst)
+{
+    for (int i = threadIdx.x; i < L::NS * L::M; i += blockDim.x) sm.u[i] = src[e * (L::NS * L::M) + i];
+    __syncthreads();
+    lim_tensor<DIM, L::M>(sm.u, dst, sm.ta, sm.tb, sm.Pr, L::S, L::n);
+}
+
+// the two subcell layers of averages a next to face (d, side) into
+// ghost slot g[layer][line][v]: side 0 -> layers 0, 1; side 1 -> S-2, S-1
+template <class L, int DIM>
+__device__ void lim_layers(const double *a, int d, int side, double *g)
+{
+    for (int i = threadIdx.x; i < 2 * L::NLINE * L::M; i += blockDim.x) {
+        const int v = i % L::M, r = i / L::M, l = r % L::NLINE, layer = r / L::NLINE;
+        const int pos = side ? L::S - 2 + layer : layer;
+        g[i] = a[lim_cell<DIM, L::S>(d, l, pos) * L::M + v];
+    }
+}
+
+template <class PDE, int DIM, int N>
+__global__ void __launch_bounds__(128) k_lim_minmax(const KParams P)
+{
+    using L = LimCfg<PDE, DIM, N>;
+    if constexpr (L::OK) {
+        extern __shared__ __align__(16) unsigned char smem_raw[];
+        LimSmem<L> sm(reinterpret_cast<double *>(smem_raw));
+        lim_load_ops<L>(P, sm);
+        const SolveDesc &S = P.solves[0];
+        for (long long e = blockIdx.x; e < S.E; e += gridDim.x) {
+            lim_averages<L, DIM>(S.u_prev, e, sm, sm.avg);
+            if (threadIdx.x < L::M) {
+                const int v = threadIdx.x;
+                double lo = sm.avg[v], hi = sm.avg[v];
+                for (int a = 1; a < L::NSUB; ++a) {
+                    const double x = sm.avg[a * L::M + v];
+                    lo = x < lo ? x : lo;
+                    hi = x > hi ? x : hi;
+                }
+                S.lim_mm[(e * L::M + v) * 2] = lo;
+                S.lim_mm[(e * L::M + v) * 2 + 1] = hi;
+            }
+            __syncthreads();
+        }
+    }
+}
+
+template <class PDE, int DIM, int N>
+__global__ void __launch_bounds__(128) k_lim_detect(const KParams P)
+{
+    using L = LimCfg<PDE, DIM, N>;
+    if constexpr (L::OK) {
+        extern __shared__ __align__(16) unsigned char smem_raw[];
+        LimSmem<L> sm(reinterpret_cast<double *>(smem_raw));
+        lim_load_ops<L>(P, sm);
+        const SolveDesc &S = P.solves[0];
+        for (long long e = blockIdx.x; e < S.E; e += gridDim.x) {
+            const double *u = S.u_out + e * (L::NS * L::M);  // the candidate
+            int bad = 0;
+            for (int s = threadIdx.x; s < L::NS; s += blockDim.x) {
+                double q[L::M];
+                bool fin = true;
+#pragma unroll
+                for (int v = 0; v < L::M; ++v) {
+                    q[v] = u[s * L::M + v];
+                    fin = fin && !dbl_nonfinite(q[v]);
+                }
+                bad |= !fin || !lim_admissible<PDE>(P.pde, q);
+            }
+            bad = __syncthreads_or(bad);
+            if (!bad) {
+                lim_averages<L, DIM>(S.u_out, e, sm, sm.avg);
+                for (int i = threadIdx.x; i < L::NSUB * L::M; i += blockDim.x) {
+                    const int v = i % L::M, a = i / L::M;
+                    if (v == 0) bad |= !lim_admissible<PDE>(P.pde, sm.avg + a * L::M);
+                    double lo = S.lim_mm[(e * L::M + v) * 2], hi = S.lim_mm[(e * L::M + v) * 2 + 1];
+#pragma unroll
+                    for (int d = 0; d < DIM; ++d)
+#pragma unroll
+                        for (int side = 0; side < 2; ++side) {
+                            const long long nb = neighbour((int)e, S.cells[0], S.cells[1], S.cells[2], d, side ? 1 : -1);
+                            lo = fmin(lo, S.lim_mm[(nb * L::M + v) * 2]);
+                            hi = fmax(hi, S.lim_mm[(nb * L::M + v) * 2 + 1]);
+                        }
+                    const double delta = fmax(1e-4, 1e-3 * (hi - lo));
+                    const double x = sm.avg[i];
+                    bad |= x < lo - delta || x > hi + delta;
+                }
+                bad = __syncthreads_or(bad);
+            }
+            if (threadIdx.x == 0) S.lim_flags[e] = bad;
+            __syncthreads();
+        }
+    }
+}
+
+template <class PDE, int DIM, int N>
+__global__ void __launch_bounds__(128) k_lim_fv(const KParams P)
+{
+    using L = LimCfg<PDE, DIM, N>;
+    if constexpr (L::OK) {
+        constexpr int M = L::M, S_ = L::S;
+        extern __shared__ __align__(16) unsigned char smem_raw[];
+        LimSmem<L> sm(reinterpret_cast<double *>(smem_raw));
+        lim_load_ops<L>(P, sm);
+        const SolveDesc &S = P.solves[0];
+        const double dt = solve_dt(P, S);
+        if (!(dt > 0.0)) return;
+        for (long long e = blockIdx.x; e < S.E; e += gridDim.x) {
+            if (!S.lim_flags[e]) continue;  // uniform over the CTA
+            lim_averages<L, DIM>(S.u_prev, e, sm, sm.avg);
+#pragma unroll 1
+            for (int d = 0; d < DIM; ++d)
+#pragma unroll 1
+                for (int side = 0; side < 2; ++side) {
+                    const long long nb = neighbour((int)e, S.cells[0], S.cells[1], S.cells[2], d, side ? 1 : -1);
+                    lim_averages<L, DIM>(S.u_prev, nb, sm, sm.nb);
+                    // ghost cells -2, -1 from the lower neighbour's last
+                    // layers; S, S+1 from the upper neighbour's first ones
+                    lim_layers<L, DIM>(sm.nb, d, side ? 0 : 1, sm.ghost + (size_t)(d * 2 + side) * 2 * L::NLINE * M);
+                    __syncthreads();
+                }
+            for (int i = threadIdx.x; i < L::NSUB * M; i += blockDim.x) sm.dq[i] = 0.0;
+            __syncthreads();
+#pragma unroll 1
+            for (int d = 0; d < DIM; ++d) {
+                const double r = dt * S.inv_dx[d] * S_;  // dt / subcell width
+                for (int l = threadIdx.x; l < L::NLINE; l += blockDim.x) {
+                    auto cell = [&](int i) -> const double * {
+                        if (i < 0) return sm.ghost + ((size_t)((d * 2 + 0) * 2 + (i + 2)) * L::NLINE + l) * M;
+                        if (i >= S_) return sm.ghost + ((size_t)((d * 2 + 1) * 2 + (i - S_)) * L::NLINE + l) * M;
+                        return sm.avg + lim_cell<DIM, S_>(d, l, i) * M;
+                    };
+                    double Fprev[M];
+                    lim_face<PDE, DIM>(P.pde, cell(-2), cell(-1), cell(0), cell(1), d, r, Fprev);
+                    for (int f = 1; f <= S_; ++f) {
+                        double F[M];
+                        lim_face<PDE, DIM>(P.pde, cell(f - 2), cell(f - 1), cell(f), cell(f + 1), d, r, F);
+                        double *o = sm.dq + lim_cell<DIM, S_>(d, l, f - 1) * M;
+#pragma unroll
+                        for (int v = 0; v < M; ++v) {
+                            o[v] -= r * (F[v] - Fprev[v]);
+                            Fprev[v] = F[v];
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+            for (int i = threadIdx.x; i < L::NSUB * M; i += blockDim.x) sm.dq[i] += sm.avg[i];
+            __syncthreads();
+            lim_tensor<DIM, M>(sm.dq, sm.u, sm.ta, sm.tb, sm.Rc, L::n, S_);
+            for (int i = threadIdx.x; i < L::NS * M; i += blockDim.x) S.u_out[e * (L::NS * M) + i] = sm.u[i];
+            __syncthreads();
+        }
+    }
+}
+
+template <class PDE, int DIM, int N>
+__global__ void __launch_bounds__(128) k_lim_couple(const KParams P)
+{
+    using L = LimCfg<PDE, DIM, N>;
+    if constexpr (L::OK) {
+        constexpr int M = L::M, S_ = L::S, n = L::n, NF = L::NF, RS = Geom<PDE, DIM, N>::RS;
+        constexpr int NFACE = 2 * DIM * NF;
+        extern __shared__ __align__(16) unsigned char smem_raw[];
+        LimSmem<L> sm(reinterpret_cast<double *>(smem_raw));
+        lim_load_ops<L>(P, sm);
+        const SolveDesc &S = P.solves[0];
+        const double dt = solve_dt(P, S);
+        if (!(dt > 0.0)) return;
+        const double *tr = reinterpret_cast<const double *>(S.tr);
+        for (long long e = blockIdx.x; e < S.E; e += gridDim.x) {
+            if (S.lim_flags[e]) continue;
+            int any = 0;
+#pragma unroll
+            for (int d = 0; d < DIM; ++d)
+#pragma unroll
+                for (int side = 0; side < 2; ++side)
+                    any |= S.lim_flags[neighbour((int)e, S.cells[0], S.cells[1], S.cells[2], d, side ? 1 : -1)];
+            if (!any) continue;  // uniform over the CTA
+            lim_averages<L, DIM>(S.u_prev, e, sm, sm.avg);
+#pragma unroll 1
+            for (int d = 0; d < DIM; ++d)
+#pragma unroll 1
+                for (int side = 0; side < 2; ++side) {
+                    const long long nb = neighbour((int)e, S.cells[0], S.cells[1], S.cells[2], d, side ? 1 : -1);
+                    if (!S.lim_flags[nb]) continue;
+                    lim_averages<L, DIM>(S.u_prev, nb, sm, sm.nb);
+                    // the face's four cell layers: lower element's last two,
+                    // upper element's first two
+                    double *gl = sm.ghost, *gu = sm.ghost + 2 * L::NLINE * M;
+                    lim_layers<L, DIM>(side ? sm.avg : sm.nb, d, 1, gl);
+                    lim_layers<L, DIM>(side ? sm.nb : sm.avg, d, 0, gu);
+                    __syncthreads();
+                    double *Fl = sm.dq;  // subcell fluxes on the face [line][v]
+                    const double r = dt * S.inv_dx[d] * S_;
+                    for (int l = threadIdx.x; l < L::NLINE; l += blockDim.x)
+                        lim_face<PDE, DIM>(P.pde, gl + (size_t)l * M, gl + (size_t)(L::NLINE + l) * M,
+                                           gu + (size_t)l * M, gu + (size_t)(L::NLINE + l) * M, d, r,
+                                           Fl + (size_t)l * M);
+                    __syncthreads();
+                    // per face node: projected subcell flux minus the DG flux
+                    double *dF = sm.dq + (size_t)L::NLINE * M;  // [p][v]
+                    for (int i = threadIdx.x; i < NF * M; i += blockDim.x) {
+                        const int v = i % M, p = i / M;
+                        int pk[3], rem = p;
+#pragma unroll
+                        for (int k = 0; k < DIM - 1; ++k) {
+                            pk[k] = rem % n;
+                            rem /= n;
+                        }
+                        double Ft = 0.0;
+                        for (int l = 0; l < L::NLINE; ++l) {
+                            double wgt = 1.0;
+                            int lr = l;
+#pragma unroll
+                            for (int k = 0; k < DIM - 1; ++k) {
+                                const int j = lr % S_;
+                                lr /= S_;
+                                wgt *= sm.Pr[j * n + pk[k]] / S_ / P.b.w[pk[k]];
+                            }
+                            Ft += wgt * Fl[(size_t)l * M + v];
+                        }
+                        // the corrector's Rusanov flux on this face node (lower | upper)
+                        const long long el = side ? e : nb, eu = side ? nb : e;
+                        const double *Lr = tr + (el * NFACE + (d * 2 + 1) * NF + p) * RS;
+                        const double *Rr = tr + (eu * NFACE + (d * 2 + 0) * NF + p) * RS;
+                        const double smax = tmax(Lr[2 * M], Rr[2 * M]);
+                        const double Fdg = 0.5 * (Lr[M + v] + Rr[M + v]) - 0.5 * smax * (Rr[v] - Lr[v]);
+                        dF[i] = Ft - Fdg;
+                    }
+                    __syncthreads();
+                    for (int i = threadIdx.x; i < L::NS * M; i += blockDim.x) {
+                        const int v = i % M, s = i / M;
+                        int sd = 0, p = 0, pw = 1, rem = s;
+#pragma unroll
+                        for (int k = 0; k < DIM; ++k) {
+                            const int x = rem % n;
+                            rem /= n;
+                            if (k == d) {
+                                sd = x;
+                            } else {
+                                p += x * pw;
+                                pw *= n;
+                            }
+                        }
+                        const double lift = (side ? P.b.F1[sd] : -P.b.F0[sd]) * S.inv_dx[d] * P.b.inv_w[sd];
+                        S.u_out[e * (L::NS * M) + i] -= dt * lift * dF[p * M + v];
+                    }
+                    __syncthreads();
+                }
+        }
+    }
+}

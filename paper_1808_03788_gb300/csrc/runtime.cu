@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include <cuda_runtime.h>
 
@@ -159,6 +160,10 @@ struct aderdg_s {
     double *scratch = nullptr;  // mass partials + small outputs
     double *ref = nullptr;      // FP32 path: per-element reference records
     void *qprev = nullptr;      // extrapolation guess: last predictor [E][n][NS][M]
+    bool limiter = false;       // subcell limiter after every step
+    double *u_prev = nullptr;   // limiter: u^n saved before the corrector
+    double *lim_mm = nullptr;   // limiter: extreme subcell averages [E][M][2]
+    int *lim_flags = nullptr;   // limiter: troubled elements of the last step [E]
     double *host_pinned = nullptr;
     KParams kp{};
     Basis basis{};
@@ -214,10 +219,41 @@ int launch_corrector(aderdg_t *h, int use_ctl, double dt)
     return ADERDG_OK;
 }
 
+// Clears the step's wave-speed maxima and non-finite flag before they are
+// taken again from the limited state.
+__global__ void k_lim_reset(Control *c)
+{
+    if (threadIdx.x < 3) c->lam_acc[threadIdx.x] = 0ull;
+    if (threadIdx.x == 0) c->flags &= ~FLAG_NONFINITE;
+}
+
+// The subcell limiter on the candidate the corrector left in u (Sec. 2.3):
+// detection, subcell finite-volume update of the troubled elements,
+// coupling of their unlimited neighbours, and the wave-speed maxima of the
+// limited state for the next CFL step.
+int launch_limiter(aderdg_t *h)
+{
+    const KernelSet *ks = h->ks;
+    KParams kp = h->kp;
+    kp.use_ctl_dt = 1;
+    const unsigned grid = (unsigned)std::min<long long>(h->E, 152LL * 16);
+    ks->lim_minmax<<<grid, 128, ks->lim_smem, h->stream>>>(kp);
+    ks->lim_detect<<<grid, 128, ks->lim_smem, h->stream>>>(kp);
+    ks->lim_fv<<<grid, 128, ks->lim_smem, h->stream>>>(kp);
+    ks->lim_couple<<<grid, 128, ks->lim_smem, h->stream>>>(kp);
+    k_lim_reset<<<1, 32, 0, h->stream>>>(h->ctl);
+    ks->cfl<<<(unsigned)std::min<long long>(4 * 152, (h->E * h->NS + 255) / 256), 256, 0, h->stream>>>(kp);
+    CK(cudaGetLastError());
+    return ADERDG_OK;
+}
+
 int enqueue_step(aderdg_t *h)
 {
     k_dt<<<1, 32, 0, h->stream>>>(h->ctl);
     CK(cudaGetLastError());
+    if (h->limiter)
+        CK(cudaMemcpyAsync(h->u_prev, h->u, (size_t)h->E * h->NS * h->M * sizeof(double), cudaMemcpyDeviceToDevice,
+                           h->stream));
     if (h->profiling) CK(cudaEventRecord(h->ev[0], h->stream));
     int rc = launch_predictor(h, 1, 0.0);
     if (rc) return rc;
@@ -225,6 +261,7 @@ int enqueue_step(aderdg_t *h)
     rc = launch_corrector(h, 1, 0.0);
     if (rc) return rc;
     if (h->profiling) CK(cudaEventRecord(h->ev[2], h->stream));
+    if (h->limiter) return launch_limiter(h);
     return ADERDG_OK;
 }
 
@@ -357,6 +394,25 @@ int aderdg_create(const aderdg_mesh_t *mesh, int N, int nVar, const aderdg_pde_t
         delete h;
         return fail(ADERDG_E_INVAL, "bad initial guess");
     }
+    h->limiter = cfg && cfg->limiter;
+    if (h->limiter) {
+        const char *why = prec != ADERDG_FP64                                       ? "the subcell limiter runs on the FP64 path"
+                          : !ks->lim_fv                                               ? "no subcell limiter for this (pde, dim, N)"
+                          : h->guess == ADERDG_GUESS_EXTRAP                           ? "the subcell limiter needs a fresh predictor per step (no EXTRAP guess)"
+                          : (pde->kind == ADERDG_PDE_ADVECTION && pde->p[3] != 0.0) ? "the subcell limiter covers systems without a source"
+                                                                                      : nullptr;
+        if (why) {
+            delete h;
+            return fail(ADERDG_E_UNSUPPORTED, why);
+        }
+        for (void (*k)(KParams) : {ks->lim_minmax, ks->lim_detect, ks->lim_fv, ks->lim_couple})
+            if (ks->lim_smem > 48 * 1024 &&
+                cudaFuncSetAttribute((const void *)k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ks->lim_smem) !=
+                    cudaSuccess) {
+                delete h;
+                return fail(ADERDG_E_CUDA, "shared memory opt-in of the limiter failed");
+            }
+    }
     h->picard = (cfg && cfg->picard_iters > 0) ? cfg->picard_iters : default_picard(N, h->guess);
     h->alpha = (cfg && cfg->cfl_alpha > 0) ? cfg->cfl_alpha : default_alpha(N);
     h->E = E;
@@ -402,8 +458,14 @@ int aderdg_create(const aderdg_mesh_t *mesh, int N, int nVar, const aderdg_pde_t
     h->d_desc = (SolveDesc *)dev_alloc(h, sizeof(SolveDesc));
     if (ks->rf > 0) h->ref = (double *)dev_alloc(h, sizeof(double) * (size_t)E * ks->rf);
     if (h->guess == ADERDG_GUESS_EXTRAP) h->qprev = dev_alloc(h, nstate * h->n * ks->elem_bytes);
+    if (h->limiter) {
+        h->u_prev = (double *)dev_alloc(h, nstate * sizeof(double));
+        h->lim_mm = (double *)dev_alloc(h, sizeof(double) * (size_t)E * m * 2);
+        h->lim_flags = (int *)dev_alloc(h, sizeof(int) * (size_t)E);
+    }
     if (!h->u || !h->V || !h->tr || !h->ctl || !h->scratch || !h->d_desc || (ks->rf > 0 && !h->ref) ||
-        (h->guess == ADERDG_GUESS_EXTRAP && !h->qprev)) {
+        (h->guess == ADERDG_GUESS_EXTRAP && !h->qprev) ||
+        (h->limiter && (!h->u_prev || !h->lim_mm || !h->lim_flags))) {
         aderdg_destroy(h);
         return fail(ADERDG_E_NOMEM, "device allocation failed");
     }
@@ -432,6 +494,9 @@ int aderdg_create(const aderdg_mesh_t *mesh, int N, int nVar, const aderdg_pde_t
     sd.tr = h->tr;
     sd.ref = h->ref;
     sd.ctl = h->ctl;
+    sd.u_prev = h->u_prev;
+    sd.lim_mm = h->lim_mm;
+    sd.lim_flags = h->lim_flags;
     KParams &kp = h->kp;
     std::memset(&kp, 0, sizeof(kp));
     kp.solves = h->d_desc;
@@ -449,6 +514,7 @@ int aderdg_create(const aderdg_mesh_t *mesh, int N, int nVar, const aderdg_pde_t
     c.t_end = 0.0;
     if (cudaMemcpyAsync(h->d_desc, &sd, sizeof(sd), cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
         cudaMemsetAsync(h->u, 0, nstate * sizeof(double), h->stream) != cudaSuccess ||
+        (h->limiter && cudaMemsetAsync(h->lim_flags, 0, sizeof(int) * (size_t)E, h->stream) != cudaSuccess) ||
         cudaMemcpyAsync(h->ctl, &c, sizeof(c), cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
         cudaStreamSynchronize(h->stream) != cudaSuccess) {
         aderdg_destroy(h);
@@ -464,6 +530,9 @@ int aderdg_destroy(aderdg_t *h)
     if (h->stream) cudaStreamSynchronize(h->stream);
     if (h->graph) cudaGraphExecDestroy(h->graph);
     dev_free(h, h->u);
+    dev_free(h, h->u_prev);
+    dev_free(h, h->lim_mm);
+    dev_free(h, h->lim_flags);
     dev_free(h, h->V);
     dev_free(h, h->tr);
     dev_free(h, h->ctl);
@@ -552,6 +621,20 @@ int aderdg_corrector(aderdg_t *h, double dt)
     if (!(dt > 0.0) || !std::isfinite(dt)) return fail(ADERDG_E_INVAL, "dt must be positive and finite");
     CK(cudaMemsetAsync(h->ctl->lam_acc, 0, sizeof(h->ctl->lam_acc), h->stream));
     return launch_corrector(h, 0, dt);
+}
+
+int aderdg_troubled(aderdg_t *h, int *flags, int64_t *count)
+{
+    if (!h) return fail(ADERDG_E_INVAL, "NULL handle");
+    if (!h->limiter) return fail(ADERDG_E_INVAL, "the handle has no limiter");
+    std::vector<int> f((size_t)h->E);
+    CK(cudaMemcpyAsync(f.data(), h->lim_flags, sizeof(int) * (size_t)h->E, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    int64_t c = 0;
+    for (long long e = 0; e < h->E; ++e) c += f[(size_t)e] != 0;
+    if (flags) std::memcpy(flags, f.data(), sizeof(int) * (size_t)h->E);
+    if (count) *count = c;
+    return ADERDG_OK;
 }
 
 int aderdg_get_predictor_outputs(aderdg_t *h, double *volume, double *qface, double *fface, int where)

@@ -1,0 +1,100 @@
+"""Parity of the CUDA subcell limiter (Sec. 2.3) with the oracle, through
+the C ABI: the troubled elements of every step agree exactly (both sides
+decide in FP64), limited states within the FP64 tolerance, total mass
+conserved on the device, smooth data untouched (bitwise the unlimited
+step), and the combinations the limiter does not cover are refused."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1808_03788_gb300 import aderdg as A
+from helpers import l2_rel
+
+pytestmark = pytest.mark.gpu
+
+
+def _sod(nx=64, N=3):
+    c = oracle.make_cfg(2, (nx, 1), [0, 0], [1.0, 1.0 / nx], N, oracle.PDE_EULER, [1.4], limiter=1)
+    x = oracle.node_coords(c)[..., 0]
+    high = (x > 0.25) & (x < 0.75)
+    rho = np.where(high, 1.0, 0.125)
+    p = np.where(high, 1.0, 0.1)
+    return c, np.stack([rho, 0 * rho, 0 * rho, p / 0.4], axis=-1)
+
+
+def _explosion(dim=2, cells=(16, 16), N=3):
+    c = oracle.make_cfg(dim, cells, [0] * dim, [1] * dim, N, oracle.PDE_EULER, [1.4], limiter=1)
+    X = oracle.node_coords(c)
+    r2 = sum((X[..., d] - 0.5) ** 2 for d in range(dim))
+    inside = r2 < 0.2 ** 2
+    rho = np.where(inside, 1.0, 0.125)
+    p = np.where(inside, 1.0, 0.1)
+    z = 0 * rho
+    return c, np.stack([rho] + [z] * dim + [p / 0.4], axis=-1)
+
+
+def _solver(c, **kw):
+    dim = c.dim
+    return A.Solver(c.pde, dim, [c.cells[d] for d in range(dim)], [c.lo[d] for d in range(dim)],
+                    [c.hi[d] for d in range(dim)], c.N, [c.prm[0]], limiter=True, **kw)
+
+
+@pytest.mark.parametrize("make", [_sod, _explosion, lambda: _explosion(3, (6, 6, 6), 2)],
+                         ids=["sod", "explosion2d", "explosion3d"])
+def test_limited_steps_match_oracle(make):
+    c, U = make()
+    s = _solver(c)
+    s.set_state(U)
+    Uo = U.copy()
+    seen = 0
+    for _ in range(12):
+        dt = s.step(1e30, sync_dt=True)
+        assert abs(dt - oracle.cfl_dt(c, Uo)) <= 1e-13 * dt
+        Uo, flags_o, cnt_o = oracle.step_limited(c, Uo, dt)
+        flags, cnt = s.troubled()
+        np.testing.assert_array_equal(flags, flags_o)
+        seen = max(seen, cnt)
+        Ug = s.get_state()[0]
+        assert np.abs(Ug - Uo).max() <= 1e-11 * max(1.0, np.abs(Uo).max())
+    s.close()
+    assert seen > 0
+
+
+def test_limited_sod_run_and_mass_on_the_device():
+    c, U = _sod()
+    with _solver(c) as s:
+        s.set_state(U)
+        M0 = s.mass()
+        s.advance(0.1)
+        Ug, t, k = s.get_state()
+        M1 = s.mass()
+    Uo, to, ko, _ = oracle.run(c, U, 0.1)
+    assert (t, k) == (to, ko)
+    assert np.isfinite(Ug).all() and Ug[..., 0].min() > 0
+    np.testing.assert_allclose(M1, M0, rtol=0, atol=1e-14)
+    assert l2_rel(c, Ug, Uo) <= 1e-10
+
+
+def test_smooth_data_limited_equals_unlimited():
+    from paper_1808_03788_gb300 import inputs
+    c = oracle.make_cfg(2, (10, 10), [0, 0], [10, 10], 3, oracle.PDE_EULER, [1.4])
+    U = inputs.euler_density_wave(oracle.node_coords(c), L=10.0)
+    out = []
+    for lim in (False, True):
+        with A.Solver(2, 2, (10, 10), (0, 0), (10, 10), 3, (1.4,), limiter=lim) as s:
+            s.set_state(U)
+            s.advance(1e30, max_steps=5)
+            out.append(s.get_state()[0])
+            if lim:
+                assert s.troubled()[1] == 0
+    np.testing.assert_array_equal(out[0], out[1])
+
+
+@pytest.mark.parametrize("kw", [dict(precision=A.ADERDG_MIXED_FP32), dict(guess=A.ADERDG_GUESS_EXTRAP)])
+def test_limiter_refuses_what_it_does_not_cover(kw):
+    with pytest.raises(A.AderdgError) as ei:
+        A.Solver(2, 2, (4, 4), (0, 0), (1, 1), 3, (1.4,), limiter=True, **kw)
+    assert ei.value.code == A.ADERDG_E_UNSUPPORTED
+    with pytest.raises(A.AderdgError) as ei:
+        A.Solver(A.ADERDG_PDE_DIFFUSE_ELASTICITY, 2, (4, 4), (0, 0), (1, 1), 3, (), limiter=True)
+    assert ei.value.code == A.ADERDG_E_UNSUPPORTED
