@@ -23,12 +23,15 @@ def _sod(nx=64, N=3):
 
 
 def _explosion(dim=2, cells=(16, 16), N=3):
+    """A blast (rho, p = 1 inside r = 0.2, 0.125 and 0.1 outside) with a tanh
+    edge of width 0.03: subcell averages of the nodal data stay admissible
+    (the limiter projects u^n afresh every step)."""
+    from paper_1808_03788_gb300 import inputs
     c = oracle.make_cfg(dim, cells, [0] * dim, [1] * dim, N, oracle.PDE_EULER, [1.4], limiter=1)
     X = oracle.node_coords(c)
-    r2 = sum((X[..., d] - 0.5) ** 2 for d in range(dim))
-    inside = r2 < 0.2 ** 2
-    rho = np.where(inside, 1.0, 0.125)
-    p = np.where(inside, 1.0, 0.1)
+    r = np.sqrt(sum((X[..., d] - 0.5) ** 2 for d in range(dim)))
+    rho = inputs.smooth_step(r, 0.2, 0.03, 1.0, 0.125)
+    p = inputs.smooth_step(r, 0.2, 0.03, 1.0, 0.1)
     z = 0 * rho
     return c, np.stack([rho] + [z] * dim + [p / 0.4], axis=-1)
 

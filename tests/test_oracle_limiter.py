@@ -132,12 +132,12 @@ def test_limited_sod_follows_the_exact_solution():
 
 
 def _explosion(cells=(16, 16), N=3):
+    """Blast with a tanh edge of width 0.03 (admissible subcell averages)."""
     c = oracle.make_cfg(2, cells, [0, 0], [1, 1], N, oracle.PDE_EULER, [1.4], limiter=1)
     X = oracle.node_coords(c)
-    r2 = (X[..., 0] - 0.5) ** 2 + (X[..., 1] - 0.5) ** 2
-    inside = r2 < 0.2 ** 2
-    rho = np.where(inside, 1.0, 0.125)
-    p = np.where(inside, 1.0, 0.1)
+    r = np.sqrt((X[..., 0] - 0.5) ** 2 + (X[..., 1] - 0.5) ** 2)
+    rho = inputs.smooth_step(r, 0.2, 0.03, 1.0, 0.125)
+    p = inputs.smooth_step(r, 0.2, 0.03, 1.0, 0.1)
     return c, np.stack([rho, 0 * rho, 0 * rho, p / 0.4], axis=-1)
 
 
