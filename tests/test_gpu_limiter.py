@@ -75,7 +75,9 @@ def test_limited_sod_run_and_mass_on_the_device():
     assert (t, k) == (to, ko)
     assert np.isfinite(Ug).all() and Ug[..., 0].min() > 0
     np.testing.assert_allclose(M1, M0, rtol=0, atol=1e-14)
-    assert l2_rel(c, Ug, Uo) <= 1e-10
+    live = [0, 1, 3]  # the y momentum stays at rounding level (~1e-16) on both sides
+    assert l2_rel(c, Ug[..., live], Uo[..., live]) <= 1e-10
+    assert np.abs(Ug[..., 2]).max() < 1e-12
 
 
 def test_smooth_data_limited_equals_unlimited():
