@@ -353,6 +353,48 @@ def _guess_variants(A, torch, w, stream, flush, steps, warmup, shapes, l2_steps,
     return out
 
 
+def _limiter(A, torch, w, stream, flush, steps, warmup):
+    """The a posteriori subcell limiter (Sec. 2.3) on the headline mesh, FP64:
+    the vortex (smooth: detection only) and a blast (rho, p = 1 inside
+    r = 2, 0.125 / 0.1 outside, tanh edge of width 0.3, centred in the box),
+    each timed like the headline, with the troubled elements of the last step."""
+    import numpy as np
+
+    from paper_1808_03788_gb300 import inputs
+    out = {"precision": "fp64"}
+    for name in ("vortex", "blast"):
+        s = A.Solver(w["pde"], w["dim"], w["cells"], w["lo"], w["hi"], w["N"], w["params"], stream=stream.cuda_stream,
+                     limiter=True)
+        X = s.node_coords(w["lo"], w["hi"])
+        if name == "vortex":
+            U0 = inputs.euler_vortex(X, lo=w["lo"], hi=w["hi"])
+        else:
+            r = np.sqrt((X[..., 0] - 5.0) ** 2 + (X[..., 1] - 5.0) ** 2)
+            rho = inputs.smooth_step(r, 2.0, 0.3, 1.0, 0.125)
+            p = inputs.smooth_step(r, 2.0, 0.3, 1.0, 0.1)
+            U0 = np.stack([rho, 0 * rho, 0 * rho, p / 0.4], axis=-1)
+        s.set_state(np.ascontiguousarray(U0))
+        with torch.cuda.stream(stream):
+            for _ in range(warmup):
+                flush.zero_()
+                s.step(1e30)
+            torch.cuda.synchronize()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+            for a, b in ev:
+                flush.zero_()
+                a.record(stream)
+                s.step(1e30)
+                b.record(stream)
+            torch.cuda.synchronize()
+        ms = [a.elapsed_time(b) for a, b in ev]
+        flags, cnt = s.troubled()
+        info = s.info()
+        s.close()
+        out[name] = {"value": info["dofs"] * steps / (sum(ms) / 1e3), "ms_per_step": sum(ms) / steps,
+                     "troubled_last_step": int(cnt), "elements": int(info["elements"])}
+    return out
+
+
 def _equal_l2(A, w, steps):
     """Advance the FP64 and the mixed path `steps` CFL steps from the same
     initial state; relative L2 distance of the two and each one's L2 error
@@ -598,6 +640,8 @@ def run_ours(args, w, rank, world):
                            "roofline": _roofline(i2, p2, other, probe, args.workload),
                            "kernels": _kernels(i2, p2, c2, hbm)}
         variants["equal_l2"] = _equal_l2(A, w, args.l2_steps)
+        if args.limiter_steps > 0 and w["pde"] == 2:
+            variants["limiter"] = _limiter(A, torch, w, stream, flush, args.limiter_steps, args.warmup)
         if args.guess_variant:
             variants.update(_guess_variants(A, torch, w, stream, flush, args.steps, args.warmup, shapes,
                                             args.l2_steps, probe, hbm, args.workload))
@@ -670,6 +714,8 @@ def main():
                     help="only the headline path (no mixed/batched/served/equal-L2 runs)")
     ap.add_argument("--l2-steps", type=int, default=100)
     ap.add_argument("--elastic-steps", type=int, default=4)
+    ap.add_argument("--limiter-steps", type=int, default=10,
+                    help="timed steps of the subcell-limiter variant (0: skip)")
     ap.add_argument("--diffuse-steps", type=int, default=3,
                     help="timed steps of the 3D diffuse-interface variant (0: skip)")
     ap.add_argument("--batched-solves", type=int, default=256)
