@@ -507,7 +507,8 @@ struct KernelSet {
     void (*lim_detect)(KParams);
     void (*lim_fv)(KParams);
     void (*lim_couple)(KParams);
-    size_t lim_smem;
+    size_t lim_smem;    // k_lim_fv / k_lim_couple (one element per CTA)
+    size_t lim_smem_w;  // k_lim_minmax / k_lim_detect (one element per warp)
     TileShape pshape[NSHAPE_P], pshape_ex[NSHAPE_P], cshape[NSHAPE_C];  // pshape_ex: extrapolation and CERK guesses
     int pred_shape, corr_shape;  // indices of the shapes in use
 };

@@ -1238,7 +1238,7 @@ const KernelSet KS<PDE, DIM, N, T>::value = {
     Geom<PDE, DIM, N>::M, Geom<PDE, DIM, N>::RS, (int)sizeof(T), PDE::FLUX_FLOPS, PDE::EIG_FLOPS,
     PredCfg<PDE, DIM, N, T>::DELTA ? PredCfg<PDE, DIM, N, T>::RF : 0, PDE::NCP ? 1 : 0, PredCfg<PDE, DIM, N, T>::MX,
     lim_kernel<PDE, DIM, N, T, 0>(), lim_kernel<PDE, DIM, N, T, 1>(), lim_kernel<PDE, DIM, N, T, 2>(),
-    lim_kernel<PDE, DIM, N, T, 3>(), LimCfg<PDE, DIM, N>::BYTES,
+    lim_kernel<PDE, DIM, N, T, 3>(), LimCfg<PDE, DIM, N>::BYTES, LimWarp<LimCfg<PDE, DIM, N>>::BYTES,
     {pred_shape<PDE, DIM, N, T, 0>(), pred_shape<PDE, DIM, N, T, 1>(), pred_shape<PDE, DIM, N, T, 2>(),
      pred_shape<PDE, DIM, N, T, 3>(), pred_shape<PDE, DIM, N, T, 4>()},
     {pred_shape<PDE, DIM, N, T, 0, true>(), pred_shape<PDE, DIM, N, T, 1, true>(),

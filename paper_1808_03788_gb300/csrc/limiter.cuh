@@ -42,9 +42,11 @@ struct LimCfg {
 
 // out = (Op (x) ... (x) Op) in along the DIM directions, Op an R x C matrix
 // in shared memory ([r][c]); in has C points per direction (x fastest,
-// M values per point), out R.  Every thread of the CTA calls it.
-template <int DIM, int M>
-__device__ void lim_tensor(const double *in, double *out, double *ta, double *tb, const double *Op, int R, int C)
+// M values per point), out R.  The team -- a CTA or one warp -- is the
+// threads tid = 0 .. nt-1, all of which call it; sync() joins them.
+template <int DIM, int M, class Sync>
+__device__ void lim_tensor_team(const double *in, double *out, double *ta, double *tb, const double *Op, int R, int C,
+                                int tid, int nt, Sync sync)
 {
     const double *src = in;
     for (int d = 0; d < DIM; ++d) {
@@ -53,7 +55,7 @@ __device__ void lim_tensor(const double *in, double *out, double *ta, double *tb
         for (int k = 0; k < d; ++k) lo *= R;
         for (int k = d + 1; k < DIM; ++k) hi *= C;
         const int total = lo * R * hi * M;
-        for (int i = threadIdx.x; i < total; i += blockDim.x) {
+        for (int i = tid; i < total; i += nt) {
             const int v = i % M;
             int r = i / M;
             const int al = r % lo;
@@ -63,9 +65,15 @@ __device__ void lim_tensor(const double *in, double *out, double *ta, double *tb
             for (int j = 0; j < C; ++j) acc += Op[ad * C + j] * src[(al + lo * (j + C * ah)) * M + v];
             dst[i] = acc;
         }
-        __syncthreads();
+        sync();
         src = dst;
     }
+}
+
+template <int DIM, int M>
+__device__ void lim_tensor(const double *in, double *out, double *ta, double *tb, const double *Op, int R, int C)
+{
+    lim_tensor_team<DIM, M>(in, out, ta, tb, Op, R, C, threadIdx.x, blockDim.x, [] { __syncthreads(); });
 }
 
 template <class PDE>
@@ -212,29 +220,60 @@ __device__ void lim_layers(const double *a, int d, int side, double *g)
     }
 }
 
+// Per-warp shared memory of the element-per-warp kernels (minmax, detect):
+// staged nodes, subcell averages, two projection buffers.
+template <class L>
+struct LimWarp {
+    static constexpr size_t DOUBLES = round_up(L::NS * L::M, 2) + (size_t)L::NSUB * L::M + 2 * L::TMP;
+    static constexpr int WARPS = cmax(1, cmin(4, (int)((200 * 1024) / (8 * DOUBLES))));
+    static constexpr size_t BYTES = sizeof(double) * (round_up(2 * L::S * L::n, 2) + WARPS * DOUBLES);
+};
+
+// subcell averages of element e's nodal state src, by one warp into avg
+template <class L, int DIM>
+__device__ void lim_averages_warp(const double *src, long long e, const double *Pr, double *u, double *avg, double *ta,
+                                  double *tb, int lane)
+{
+    for (int i = lane; i < L::NS * L::M; i += 32) u[i] = src[e * (L::NS * L::M) + i];
+    __syncwarp();
+    lim_tensor_team<DIM, L::M>(u, avg, ta, tb, Pr, L::S, L::n, lane, 32, [] { __syncwarp(); });
+}
+
 template <class PDE, int DIM, int N>
 __global__ void __launch_bounds__(128) k_lim_minmax(const KParams P)
 {
     using L = LimCfg<PDE, DIM, N>;
+    using W = LimWarp<L>;
     if constexpr (L::OK) {
         extern __shared__ __align__(16) unsigned char smem_raw[];
-        LimSmem<L> sm(reinterpret_cast<double *>(smem_raw));
-        lim_load_ops<L>(P, sm);
+        double *Pr = reinterpret_cast<double *>(smem_raw);
+        for (int i = threadIdx.x; i < L::S * L::n; i += blockDim.x) Pr[i] = P.lim_pr[i];
+        __syncthreads();
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        if (warp >= W::WARPS) return;
+        double *u = Pr + round_up(2 * L::S * L::n, 2) + warp * W::DOUBLES;
+        double *avg = u + round_up(L::NS * L::M, 2), *ta = avg + (size_t)L::NSUB * L::M, *tb = ta + L::TMP;
         const SolveDesc &S = P.solves[0];
-        for (long long e = blockIdx.x; e < S.E; e += gridDim.x) {
-            lim_averages<L, DIM>(S.u_prev, e, sm, sm.avg);
-            if (threadIdx.x < L::M) {
-                const int v = threadIdx.x;
-                double lo = sm.avg[v], hi = sm.avg[v];
-                for (int a = 1; a < L::NSUB; ++a) {
-                    const double x = sm.avg[a * L::M + v];
+        for (long long e = (long long)blockIdx.x * W::WARPS + warp; e < S.E; e += (long long)gridDim.x * W::WARPS) {
+            lim_averages_warp<L, DIM>(S.u_prev, e, Pr, u, avg, ta, tb, lane);
+            for (int v = 0; v < L::M; ++v) {
+                double lo = avg[v], hi = avg[v];
+                for (int a = lane; a < L::NSUB; a += 32) {
+                    const double x = avg[a * L::M + v];
                     lo = x < lo ? x : lo;
                     hi = x > hi ? x : hi;
                 }
-                S.lim_mm[(e * L::M + v) * 2] = lo;
-                S.lim_mm[(e * L::M + v) * 2 + 1] = hi;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+                    hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+                }
+                if (lane == 0) {
+                    S.lim_mm[(e * L::M + v) * 2] = lo;
+                    S.lim_mm[(e * L::M + v) * 2 + 1] = hi;
+                }
             }
-            __syncthreads();
+            __syncwarp();
         }
     }
 }
@@ -243,30 +282,36 @@ template <class PDE, int DIM, int N>
 __global__ void __launch_bounds__(128) k_lim_detect(const KParams P)
 {
     using L = LimCfg<PDE, DIM, N>;
+    using W = LimWarp<L>;
     if constexpr (L::OK) {
         extern __shared__ __align__(16) unsigned char smem_raw[];
-        LimSmem<L> sm(reinterpret_cast<double *>(smem_raw));
-        lim_load_ops<L>(P, sm);
+        double *Pr = reinterpret_cast<double *>(smem_raw);
+        for (int i = threadIdx.x; i < L::S * L::n; i += blockDim.x) Pr[i] = P.lim_pr[i];
+        __syncthreads();
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        if (warp >= W::WARPS) return;
+        double *u = Pr + round_up(2 * L::S * L::n, 2) + warp * W::DOUBLES;
+        double *avg = u + round_up(L::NS * L::M, 2), *ta = avg + (size_t)L::NSUB * L::M, *tb = ta + L::TMP;
         const SolveDesc &S = P.solves[0];
-        for (long long e = blockIdx.x; e < S.E; e += gridDim.x) {
-            const double *u = S.u_out + e * (L::NS * L::M);  // the candidate
+        for (long long e = (long long)blockIdx.x * W::WARPS + warp; e < S.E; e += (long long)gridDim.x * W::WARPS) {
+            const double *uc = S.u_out + e * (L::NS * L::M);  // the candidate
             int bad = 0;
-            for (int s = threadIdx.x; s < L::NS; s += blockDim.x) {
+            for (int s = lane; s < L::NS; s += 32) {
                 double q[L::M];
                 bool fin = true;
 #pragma unroll
                 for (int v = 0; v < L::M; ++v) {
-                    q[v] = u[s * L::M + v];
+                    q[v] = uc[s * L::M + v];
                     fin = fin && !dbl_nonfinite(q[v]);
                 }
                 bad |= !fin || !lim_admissible<PDE>(P.pde, q);
             }
-            bad = __syncthreads_or(bad);
+            bad = __any_sync(0xffffffffu, bad);
             if (!bad) {
-                lim_averages<L, DIM>(S.u_out, e, sm, sm.avg);
-                for (int i = threadIdx.x; i < L::NSUB * L::M; i += blockDim.x) {
-                    const int v = i % L::M, a = i / L::M;
-                    if (v == 0) bad |= !lim_admissible<PDE>(P.pde, sm.avg + a * L::M);
+                lim_averages_warp<L, DIM>(S.u_out, e, Pr, u, avg, ta, tb, lane);
+                for (int a = lane; a < L::NSUB; a += 32) bad |= !lim_admissible<PDE>(P.pde, avg + a * L::M);
+                for (int v = 0; v < L::M; ++v) {
+                    // the relaxed maximum principle of u^n over the element and its face neighbours
                     double lo = S.lim_mm[(e * L::M + v) * 2], hi = S.lim_mm[(e * L::M + v) * 2 + 1];
 #pragma unroll
                     for (int d = 0; d < DIM; ++d)
@@ -277,13 +322,15 @@ __global__ void __launch_bounds__(128) k_lim_detect(const KParams P)
                             hi = fmax(hi, S.lim_mm[(nb * L::M + v) * 2 + 1]);
                         }
                     const double delta = fmax(1e-4, 1e-3 * (hi - lo));
-                    const double x = sm.avg[i];
-                    bad |= x < lo - delta || x > hi + delta;
+                    for (int a = lane; a < L::NSUB; a += 32) {
+                        const double x = avg[a * L::M + v];
+                        bad |= x < lo - delta || x > hi + delta;
+                    }
                 }
-                bad = __syncthreads_or(bad);
+                bad = __any_sync(0xffffffffu, bad);
             }
-            if (threadIdx.x == 0) S.lim_flags[e] = bad;
-            __syncthreads();
+            if (lane == 0) S.lim_flags[e] = bad;
+            __syncwarp();
         }
     }
 }

@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -237,8 +238,8 @@ int launch_limiter(aderdg_t *h)
     KParams kp = h->kp;
     kp.use_ctl_dt = 1;
     const unsigned grid = (unsigned)std::min<long long>(h->E, 152LL * 16);
-    ks->lim_minmax<<<grid, 128, ks->lim_smem, h->stream>>>(kp);
-    ks->lim_detect<<<grid, 128, ks->lim_smem, h->stream>>>(kp);
+    ks->lim_minmax<<<grid, 128, ks->lim_smem_w, h->stream>>>(kp);
+    ks->lim_detect<<<grid, 128, ks->lim_smem_w, h->stream>>>(kp);
     ks->lim_fv<<<grid, 128, ks->lim_smem, h->stream>>>(kp);
     ks->lim_couple<<<grid, 128, ks->lim_smem, h->stream>>>(kp);
     k_lim_reset<<<1, 32, 0, h->stream>>>(h->ctl);
@@ -405,9 +406,12 @@ int aderdg_create(const aderdg_mesh_t *mesh, int N, int nVar, const aderdg_pde_t
             delete h;
             return fail(ADERDG_E_UNSUPPORTED, why);
         }
-        for (void (*k)(KParams) : {ks->lim_minmax, ks->lim_detect, ks->lim_fv, ks->lim_couple})
-            if (ks->lim_smem > 48 * 1024 &&
-                cudaFuncSetAttribute((const void *)k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ks->lim_smem) !=
+        const std::pair<void (*)(KParams), size_t> lk[4] = {
+            {ks->lim_minmax, ks->lim_smem_w}, {ks->lim_detect, ks->lim_smem_w}, {ks->lim_fv, ks->lim_smem},
+            {ks->lim_couple, ks->lim_smem}};
+        for (const auto &k : lk)
+            if (k.second > 48 * 1024 &&
+                cudaFuncSetAttribute((const void *)k.first, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.second) !=
                     cudaSuccess) {
                 delete h;
                 return fail(ADERDG_E_CUDA, "shared memory opt-in of the limiter failed");
