@@ -32,9 +32,10 @@ struct LimCfg {
                                     DIM == 3 ? cmax(S * S * n, n * n * S) : 0) * M;
     static constexpr int OPS = round_up(2 * S * n, 2);
     static constexpr int GHOST = 2 * DIM * 2 * NLINE * M;  // [d][side][layer][line][v]
+    static constexpr int FACES = (S + 1) * NLINE * M;      // subcell face fluxes of one direction
     // doubles: operators, staged nodes, own averages, a neighbour's averages,
-    // ghost layers, increments, two projection buffers
-    static constexpr size_t DOUBLES = OPS + round_up(NS * M, 2) + 3 * (size_t)NSUB * M + GHOST + 2 * TMP;
+    // ghost layers, increments, two projection buffers, face fluxes
+    static constexpr size_t DOUBLES = OPS + round_up(NS * M, 2) + 3 * (size_t)NSUB * M + GHOST + 2 * TMP + FACES;
     static constexpr size_t BYTES = sizeof(double) * DOUBLES;
     static constexpr bool FITS = BYTES <= 227 * 1024;
     static constexpr bool OK = FITS && !PDE::NCP;
@@ -174,7 +175,7 @@ __device__ __forceinline__ int lim_cell(int d, int l, int i)
 // Shared-memory layout of the limiter kernels.
 template <class L>
 struct LimSmem {
-    double *Pr, *Rc, *u, *avg, *nb, *ghost, *dq, *ta, *tb;
+    double *Pr, *Rc, *u, *avg, *nb, *ghost, *dq, *ta, *tb, *fb;
     __device__ explicit LimSmem(double *base)
     {
         Pr = base;
@@ -186,6 +187,7 @@ struct LimSmem {
         dq = ghost + L::GHOST;
         ta = dq + (size_t)L::NSUB * L::M;
         tb = ta + L::TMP;
+        fb = tb + L::TMP;
     }
 };
 
@@ -366,24 +368,25 @@ __global__ void __launch_bounds__(128) k_lim_fv(const KParams P)
 #pragma unroll 1
             for (int d = 0; d < DIM; ++d) {
                 const double r = dt * S.inv_dx[d] * S_;  // dt / subcell width
-                for (int l = threadIdx.x; l < L::NLINE; l += blockDim.x) {
-                    auto cell = [&](int i) -> const double * {
-                        if (i < 0) return sm.ghost + ((size_t)((d * 2 + 0) * 2 + (i + 2)) * L::NLINE + l) * M;
-                        if (i >= S_) return sm.ghost + ((size_t)((d * 2 + 1) * 2 + (i - S_)) * L::NLINE + l) * M;
-                        return sm.avg + lim_cell<DIM, S_>(d, l, i) * M;
-                    };
-                    double Fprev[M];
-                    lim_face<PDE, DIM>(P.pde, cell(-2), cell(-1), cell(0), cell(1), d, r, Fprev);
-                    for (int f = 1; f <= S_; ++f) {
-                        double F[M];
-                        lim_face<PDE, DIM>(P.pde, cell(f - 2), cell(f - 1), cell(f), cell(f + 1), d, r, F);
-                        double *o = sm.dq + lim_cell<DIM, S_>(d, l, f - 1) * M;
+                // cell i of line l along d: ghost layers below 0 and from S on
+                auto cell = [&](int l, int i) -> const double * {
+                    if (i < 0) return sm.ghost + ((size_t)((d * 2 + 0) * 2 + (i + 2)) * L::NLINE + l) * M;
+                    if (i >= S_) return sm.ghost + ((size_t)((d * 2 + 1) * 2 + (i - S_)) * L::NLINE + l) * M;
+                    return sm.avg + lim_cell<DIM, S_>(d, l, i) * M;
+                };
+                // every face flux of this direction (face f between cells f-1 and f)
+                for (int it = threadIdx.x; it < (S_ + 1) * L::NLINE; it += blockDim.x) {
+                    const int f = it % (S_ + 1), l = it / (S_ + 1);
+                    lim_face<PDE, DIM>(P.pde, cell(l, f - 2), cell(l, f - 1), cell(l, f), cell(l, f + 1), d, r,
+                                       sm.fb + (size_t)it * M);
+                }
+                __syncthreads();
+                for (int it = threadIdx.x; it < S_ * L::NLINE; it += blockDim.x) {
+                    const int i = it % S_, l = it / S_;
+                    const double *F0 = sm.fb + (size_t)(l * (S_ + 1) + i) * M, *F1 = F0 + M;
+                    double *o = sm.dq + lim_cell<DIM, S_>(d, l, i) * M;
 #pragma unroll
-                        for (int v = 0; v < M; ++v) {
-                            o[v] -= r * (F[v] - Fprev[v]);
-                            Fprev[v] = F[v];
-                        }
-                    }
+                    for (int v = 0; v < M; ++v) o[v] -= r * (F1[v] - F0[v]);
                 }
                 __syncthreads();
             }
