@@ -320,3 +320,29 @@ def test_mixed_mass_conservation():
     s.advance(1e30, max_steps=64)
     # FP32 rounding of the reference differences across faces: ~1e-11 per 64 steps
     np.testing.assert_allclose(s.mass(), M0, rtol=1e-9, atol=1e-9)
+
+
+@pytest.mark.parametrize("precision,limiter", [(A.ADERDG_FP64, False), (A.ADERDG_MIXED_FP32, False),
+                                               (A.ADERDG_FP64, True)])
+def test_checkpoint_and_resume_is_bitwise(precision, limiter):
+    """Checkpoint = (state, time) read back to the host; a fresh handle that
+    resumes from it continues bitwise like the uninterrupted run (every step
+    depends only on u^n and t; the step counter restarts)."""
+    case = (2, 2, 3, (12, 10), 10.0, (GAMMA,))
+    cfg = oracle.make_cfg(2, case[3], [0, 0], [10, 10], 3, 2, case[5])
+    U0 = inputs.euler_vortex(oracle.node_coords(cfg))
+    kw = dict(precision=precision, limiter=limiter)
+    with A.Solver(2, 2, case[3], (0, 0), (10, 10), 3, case[5], **kw) as s:
+        s.set_state(U0)
+        s.advance(0.5)
+        ref, t_ref, k_ref = s.get_state()
+    with A.Solver(2, 2, case[3], (0, 0), (10, 10), 3, case[5], **kw) as s:
+        s.set_state(U0)
+        s.advance(0.2)
+        ck, t_ck, k_ck = s.get_state()  # the checkpoint
+    with A.Solver(2, 2, case[3], (0, 0), (10, 10), 3, case[5], **kw) as s:
+        s.set_state(ck, t=t_ck)
+        s.advance(0.5)
+        got, t, k = s.get_state()
+    assert t == t_ref and k_ck + k == k_ref
+    np.testing.assert_array_equal(got, ref)
