@@ -65,3 +65,44 @@ def test_max_over_ranks_with_two_gloo_processes():
         assert p.exitcode == 0
     got = dict(q.get(timeout=5) for _ in range(2))
     assert got == {0: 17.0, 1: 17.0}
+
+
+def _rank_failing(rank, world, port, q):
+    """Rank 1 fails before the collective; rank 0 must get an error from the
+    process group's timeout instead of waiting forever."""
+    import datetime
+
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=5))
+    if rank == 1:
+        q.put((1, "raised"))
+        raise SystemExit(3)  # the failing rank leaves between steps
+    import bench
+    try:
+        bench._max_over_ranks(1.0, world, device="cpu")
+        q.put((0, "returned"))
+    except Exception as e:  # the collective fails on the host, nothing hangs
+        q.put((0, "error: " + type(e).__name__))
+
+
+def test_a_failing_rank_surfaces_as_an_error_not_a_hang():
+    import multiprocessing as mp
+    import socket
+    import time
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    ps = [ctx.Process(target=_rank_failing, args=(r, 2, port, q)) for r in range(2)]
+    t0 = time.time()
+    for p in ps:
+        p.start()
+    for p in ps:
+        p.join(120)
+    got = dict(q.get(timeout=5) for _ in range(2))
+    assert ps[1].exitcode == 3
+    assert got[1] == "raised" and got[0].startswith("error"), got
+    assert time.time() - t0 < 100
