@@ -338,11 +338,11 @@ def test_checkpoint_and_resume_is_bitwise(precision, limiter):
         ref, t_ref, k_ref = s.get_state()
     with A.Solver(2, 2, case[3], (0, 0), (10, 10), 3, case[5], **kw) as s:
         s.set_state(U0)
-        s.advance(0.2)
+        s.advance(0.5, max_steps=20)  # stop after 20 steps (a stop at a time would clip one step)
         ck, t_ck, k_ck = s.get_state()  # the checkpoint
     with A.Solver(2, 2, case[3], (0, 0), (10, 10), 3, case[5], **kw) as s:
         s.set_state(ck, t=t_ck)
         s.advance(0.5)
         got, t, k = s.get_state()
-    assert t == t_ref and k_ck + k == k_ref
+    assert k_ck == 20 and t == t_ref and k_ck + k == k_ref
     np.testing.assert_array_equal(got, ref)
