@@ -103,3 +103,35 @@ def test_limiter_refuses_what_it_does_not_cover(kw):
     with pytest.raises(A.AderdgError) as ei:
         A.Solver(A.ADERDG_PDE_DIFFUSE_ELASTICITY, 2, (4, 4), (0, 0), (1, 1), 3, (), limiter=True)
     assert ei.value.code == A.ADERDG_E_UNSUPPORTED
+
+
+@pytest.mark.parametrize("pde", [oracle.PDE_ADVECTION, oracle.PDE_ELASTICITY])
+def test_limiter_on_advection_and_elasticity(pde):
+    """The limiter on the other conservative systems: a square wave of
+    advection (2D) and a velocity slab of elasticity (3D), discontinuities on
+    element faces; troubled sets and states against the oracle."""
+    if pde == oracle.PDE_ADVECTION:
+        c = oracle.make_cfg(2, (16, 8), [0, 0], [1, 1], 3, pde, [1.0, 0.5], limiter=1)
+        x = oracle.node_coords(c)[..., 0]
+        U = np.where((x > 0.25) & (x < 0.5), 1.0, 0.0)[..., None]
+        params = (1.0, 0.5)
+    else:
+        c = oracle.make_cfg(3, (8, 3, 3), [0, 0, 0], [1, 1, 1], 2, pde, [1.0, 2.0, 1.0], limiter=1)
+        x = oracle.node_coords(c)[..., 0]
+        U = np.zeros(x.shape + (9,))
+        U[..., 6] = np.where((x > 0.25) & (x < 0.5), 1.0, 0.0)
+        params = (1.0, 2.0, 1.0)
+    dim = c.dim
+    s = A.Solver(pde, dim, [c.cells[d] for d in range(dim)], [0.0] * dim, [1.0] * dim, c.N, params, limiter=True)
+    s.set_state(U)
+    Uo = U.copy()
+    seen = 0
+    for _ in range(8):
+        dt = s.step(1e30, sync_dt=True)
+        Uo, flags_o, cnt = oracle.step_limited(c, Uo, dt)
+        flags, _ = s.troubled()
+        np.testing.assert_array_equal(flags, flags_o)
+        seen = max(seen, cnt)
+        assert np.abs(s.get_state()[0] - Uo).max() <= 1e-11 * max(1.0, np.abs(Uo).max())
+    s.close()
+    assert seen > 0

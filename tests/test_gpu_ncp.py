@@ -245,3 +245,42 @@ def test_reaction_plane_kernel_matches_oracle(shapes):
         assert s.info()["pred_shape"] == shapes[0]
     assert (t, k) == (to, ko)
     assert l2_rel(cfg, Ug, Uo) <= 1e-6
+
+
+def test_server_serves_the_non_conservative_system_and_cerk_requests():
+    """Requests of the diffuse-interface system (FP64 and mixed) and an Euler
+    request with the CERK guess, served together: each result bitwise equal
+    to the same solve alone."""
+    import time
+    cfg = oracle.make_cfg(2, (6, 4), [0, 0], [1, 1], 3, oracle.PDE_DIFFUSE_ELASTICITY, [])
+    ud = _di_state(cfg, seed=900, alpha_vac=0.3)
+    ue = inputs.euler_vortex(oracle.node_coords(oracle.make_cfg(2, (8, 8), [0, 0], [10, 10], 4, 2, [1.4])))
+    reqs = [(A.make_spec(DI, 2, (6, 4), (0, 0), (1, 1), 3, ()), ud, 0.05, A.ADERDG_FP64, 0),
+            (A.make_spec(DI, 2, (6, 4), (0, 0), (1, 1), 3, ()), ud, 0.05, A.ADERDG_MIXED_FP32, 0),
+            (A.make_spec(2, 2, (8, 8), (0, 0), (10, 10), 4, (1.4,)), ue, 0.2, A.ADERDG_MIXED_FP32,
+             A.ADERDG_GUESS_CERK)]
+    srv = A.Server(precision=A.ADERDG_FP64, steps_per_round=4)
+    tickets = [srv.submit(sp, u0, te, precision=prec, guess=g) for sp, u0, te, prec, g in reqs]
+    res = {}
+    t0 = time.time()
+    while len(res) < len(tickets) and time.time() - t0 < 120:
+        for tk in tickets:
+            if tk not in res:
+                r = srv.poll(tk)
+                if r is not None:
+                    res[tk] = r
+        time.sleep(0.002)
+    assert len(res) == len(tickets)
+    for tk, (sp, u0, te, prec, g) in zip(tickets, reqs):
+        assert res[tk]["status"] == A.ADERDG_OK
+        dim = sp.mesh.dim
+        with A.Solver(sp.pde.kind, dim, [sp.mesh.cells[d] for d in range(dim)], [sp.mesh.lo[d] for d in range(dim)],
+                      [sp.mesh.hi[d] for d in range(dim)], sp.N, tuple(sp.pde.p[:1]) if sp.pde.kind == 2 else (),
+                      precision=prec, guess=g) as s:
+            s.set_state(u0)
+            s.advance(te)
+            alone, t, k = s.get_state()
+        assert res[tk]["steps"] == k and res[tk]["t"] == t
+        np.testing.assert_array_equal(res[tk]["u"], alone.reshape(-1))
+        srv.release(tk)
+    srv.close()
