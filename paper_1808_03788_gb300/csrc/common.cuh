@@ -46,7 +46,7 @@ struct Control {
     double lam_used[3];             // maxima the last dt was computed from
     long long step;
     unsigned int flags;
-    unsigned int pad1;
+    unsigned int lim_fresh;  // subcell limiter: lim_mmc holds the candidate extremes of the state's last step
 };
 
 // PDE parameters as given (aderdg_pde_t) and constants derived from them
@@ -110,9 +110,11 @@ struct SolveDesc {
     void *qprev;       // extrapolation guess: last predictor [E][n][NS][M] of T
     Control *ctl;
     // subcell limiter (FP64 handles): u^n saved before the corrector, the
-    // extreme subcell averages of u^n [E][M][2] and the troubled flags [E]
+    // extreme subcell averages of u^n and of the candidate [E][M][2], and
+    // the troubled flags [E]
     const double *u_prev;
     double *lim_mm;
+    double *lim_mmc;
     int *lim_flags;
 };
 

@@ -3,6 +3,7 @@
 // After the unlimited step has produced a candidate u* (in place of u^n,
 // which the step saved to u_prev):
 //   k_lim_minmax  extreme subcell averages of u^n per element and variable
+//                 (copied from the last detection where u^n is its candidate)
 //   k_lim_detect  troubled elements: non-finite values, Euler positivity at
 //                 the nodes and in the subcell averages, or a subcell average
 //                 of u* outside the relaxed discrete maximum principle
@@ -41,40 +42,68 @@ struct LimCfg {
     static constexpr bool OK = FITS && !PDE::NCP;
 };
 
+// One direction of a tensor-product application: LO points before the
+// direction (R of them already transformed), HI after it (C untransformed),
+// M values per point; each output is one C-term sum, accumulated in j order.
+template <int M, int R, int C, int LO, int HI>
+__device__ __forceinline__ void lim_pass(const double *src, double *dst, const double *Op, int tid, int nt)
+{
+    constexpr int total = LO * R * HI * M;
+    for (int i = tid; i < total; i += nt) {
+        const int v = i % M, r = i / M, al = r % LO, ad = (r / LO) % R, ah = r / (LO * R);
+        const double *x = src + (al + LO * C * ah) * M + v;
+        double acc = 0.0;
+#pragma unroll
+        for (int j = 0; j < C; ++j) acc += Op[ad * C + j] * x[j * LO * M];
+        dst[i] = acc;
+    }
+}
+
 // out = (Op (x) ... (x) Op) in along the DIM directions, Op an R x C matrix
 // in shared memory ([r][c]); in has C points per direction (x fastest,
 // M values per point), out R.  The team -- a CTA or one warp -- is the
 // threads tid = 0 .. nt-1, all of which call it; sync() joins them.
-template <int DIM, int M, class Sync>
-__device__ void lim_tensor_team(const double *in, double *out, double *ta, double *tb, const double *Op, int R, int C,
-                                int tid, int nt, Sync sync)
+template <int DIM, int M, int R, int C, class Sync>
+__device__ void lim_tensor_team(const double *in, double *out, double *ta, double *tb, const double *Op, int tid,
+                                int nt, Sync sync)
 {
-    const double *src = in;
-    for (int d = 0; d < DIM; ++d) {
-        double *dst = d == DIM - 1 ? out : ((d & 1) ? tb : ta);
-        int lo = 1, hi = 1;
-        for (int k = 0; k < d; ++k) lo *= R;
-        for (int k = d + 1; k < DIM; ++k) hi *= C;
-        const int total = lo * R * hi * M;
-        for (int i = tid; i < total; i += nt) {
-            const int v = i % M;
-            int r = i / M;
-            const int al = r % lo;
-            r /= lo;
-            const int ad = r % R, ah = r / R;
-            double acc = 0.0;
-            for (int j = 0; j < C; ++j) acc += Op[ad * C + j] * src[(al + lo * (j + C * ah)) * M + v];
-            dst[i] = acc;
-        }
+    if constexpr (DIM == 1) {
+        lim_pass<M, R, C, 1, 1>(in, out, Op, tid, nt);
         sync();
-        src = dst;
+    } else if constexpr (DIM == 2) {
+        lim_pass<M, R, C, 1, C>(in, ta, Op, tid, nt);
+        sync();
+        lim_pass<M, R, C, R, 1>(ta, out, Op, tid, nt);
+        sync();
+    } else {
+        lim_pass<M, R, C, 1, C * C>(in, ta, Op, tid, nt);
+        sync();
+        lim_pass<M, R, C, R, C>(ta, tb, Op, tid, nt);
+        sync();
+        lim_pass<M, R, C, R * R, 1>(tb, out, Op, tid, nt);
+        sync();
     }
 }
 
-template <int DIM, int M>
-__device__ void lim_tensor(const double *in, double *out, double *ta, double *tb, const double *Op, int R, int C)
+template <int DIM, int M, int R, int C>
+__device__ void lim_tensor(const double *in, double *out, double *ta, double *tb, const double *Op)
 {
-    lim_tensor_team<DIM, M>(in, out, ta, tb, Op, R, C, threadIdx.x, blockDim.x, [] { __syncthreads(); });
+    lim_tensor_team<DIM, M, R, C>(in, out, ta, tb, Op, threadIdx.x, blockDim.x, [] { __syncthreads(); });
+}
+
+// Order-preserving integer key of a double that is not NaN (-0 and +0 both
+// map to 0): x < y exactly when lim_key(x) < lim_key(y).  Extremes and
+// bound tests run on the integer pipe with it; the FP64 pipe, this GPU's
+// scarce one, carries only the projections and the admissibility tests.
+__device__ __forceinline__ long long lim_key(double x)
+{
+    const long long b = __double_as_longlong(x);
+    return b < 0 ? -(b & 0x7fffffffffffffffLL) : b;
+}
+
+__device__ __forceinline__ double lim_unkey(long long k)
+{
+    return k < 0 ? __longlong_as_double((-k) | (long long)0x8000000000000000ULL) : __longlong_as_double(k);
 }
 
 template <class PDE>
@@ -207,7 +236,7 @@ __device__ void lim_averages(const double *src, long long e, LimSmem<L> &sm, dou
 {
     for (int i = threadIdx.x; i < L::NS * L::M; i += blockDim.x) sm.u[i] = src[e * (L::NS * L::M) + i];
     __syncthreads();
-    lim_tensor<DIM, L::M>(sm.u, dst, sm.ta, sm.tb, sm.Pr, L::S, L::n);
+    lim_tensor<DIM, L::M, L::S, L::n>(sm.u, dst, sm.ta, sm.tb, sm.Pr);
 }
 
 // the two subcell layers of averages a next to face (d, side) into
@@ -238,9 +267,40 @@ __device__ void lim_averages_warp(const double *src, long long e, const double *
 {
     for (int i = lane; i < L::NS * L::M; i += 32) u[i] = src[e * (L::NS * L::M) + i];
     __syncwarp();
-    lim_tensor_team<DIM, L::M>(u, avg, ta, tb, Pr, L::S, L::n, lane, 32, [] { __syncwarp(); });
+    lim_tensor_team<DIM, L::M, L::S, L::n>(u, avg, ta, tb, Pr, lane, 32, [] { __syncwarp(); });
 }
 
+// extreme subcell averages of one element (warp-wide), written to
+// mm[v][lo, hi]; the same routine for u^n and for the candidate, so that a
+// candidate's extremes can stand for the next step's u^n bit for bit
+template <class L>
+__device__ void lim_extremes_warp(const double *avg, int lane, double *mm)
+{
+    for (int v = 0; v < L::M; ++v) {
+        long long lo = lim_key(avg[v]), hi = lo;
+        for (int a = lane; a < L::NSUB; a += 32) {
+            const long long k = lim_key(avg[a * L::M + v]);
+            lo = k < lo ? k : lo;
+            hi = k > hi ? k : hi;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const long long ol = __shfl_xor_sync(0xffffffffu, lo, o), oh = __shfl_xor_sync(0xffffffffu, hi, o);
+            lo = ol < lo ? ol : lo;
+            hi = oh > hi ? oh : hi;
+        }
+        if (lane == 0) {
+            mm[v * 2] = lim_unkey(lo);
+            mm[v * 2 + 1] = lim_unkey(hi);
+        }
+    }
+}
+
+// Extremes of u^n.  After a limited step on the same state (ctl->lim_fresh),
+// an element that was not troubled and had no troubled face neighbour
+// still holds the candidate the detection projected, so its extremes are
+// copied from there; the others (and all after a state upload or an
+// explicit corrector call) are projected afresh.
 template <class PDE, int DIM, int N>
 __global__ void __launch_bounds__(128) k_lim_minmax(const KParams P)
 {
@@ -256,25 +316,24 @@ __global__ void __launch_bounds__(128) k_lim_minmax(const KParams P)
         double *u = Pr + round_up(2 * L::S * L::n, 2) + warp * W::DOUBLES;
         double *avg = u + round_up(L::NS * L::M, 2), *ta = avg + (size_t)L::NSUB * L::M, *tb = ta + L::TMP;
         const SolveDesc &S = P.solves[0];
+        const bool fresh = S.ctl->lim_fresh != 0;
         for (long long e = (long long)blockIdx.x * W::WARPS + warp; e < S.E; e += (long long)gridDim.x * W::WARPS) {
-            lim_averages_warp<L, DIM>(S.u_prev, e, Pr, u, avg, ta, tb, lane);
-            for (int v = 0; v < L::M; ++v) {
-                double lo = avg[v], hi = avg[v];
-                for (int a = lane; a < L::NSUB; a += 32) {
-                    const double x = avg[a * L::M + v];
-                    lo = x < lo ? x : lo;
-                    hi = x > hi ? x : hi;
-                }
+            bool reuse = fresh;
+            if (reuse) {
+                int touched = S.lim_flags[e];
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
-                    hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
-                }
-                if (lane == 0) {
-                    S.lim_mm[(e * L::M + v) * 2] = lo;
-                    S.lim_mm[(e * L::M + v) * 2 + 1] = hi;
-                }
+                for (int d = 0; d < DIM; ++d)
+#pragma unroll
+                    for (int side = 0; side < 2; ++side)
+                        touched |= S.lim_flags[neighbour((int)e, S.cells[0], S.cells[1], S.cells[2], d, side ? 1 : -1)];
+                reuse = !touched;
             }
+            if (reuse) {  // uniform over the warp
+                if (lane < 2 * L::M) S.lim_mm[e * (2 * L::M) + lane] = S.lim_mmc[e * (2 * L::M) + lane];
+                continue;
+            }
+            lim_averages_warp<L, DIM>(S.u_prev, e, Pr, u, avg, ta, tb, lane);
+            lim_extremes_warp<L>(avg, lane, S.lim_mm + e * (2 * L::M));
             __syncwarp();
         }
     }
@@ -311,22 +370,29 @@ __global__ void __launch_bounds__(128) k_lim_detect(const KParams P)
             bad = __any_sync(0xffffffffu, bad);
             if (!bad) {
                 lim_averages_warp<L, DIM>(S.u_out, e, Pr, u, avg, ta, tb, lane);
+                // the candidate's extremes, the next step's u^n extremes if
+                // this element stays untouched
+                lim_extremes_warp<L>(avg, lane, S.lim_mmc + e * (2 * L::M));
                 for (int a = lane; a < L::NSUB; a += 32) bad |= !lim_admissible<PDE>(P.pde, avg + a * L::M);
                 for (int v = 0; v < L::M; ++v) {
                     // the relaxed maximum principle of u^n over the element and its face neighbours
-                    double lo = S.lim_mm[(e * L::M + v) * 2], hi = S.lim_mm[(e * L::M + v) * 2 + 1];
+                    long long klo = lim_key(S.lim_mm[(e * L::M + v) * 2]), khi = lim_key(S.lim_mm[(e * L::M + v) * 2 + 1]);
 #pragma unroll
                     for (int d = 0; d < DIM; ++d)
 #pragma unroll
                         for (int side = 0; side < 2; ++side) {
                             const long long nb = neighbour((int)e, S.cells[0], S.cells[1], S.cells[2], d, side ? 1 : -1);
-                            lo = fmin(lo, S.lim_mm[(nb * L::M + v) * 2]);
-                            hi = fmax(hi, S.lim_mm[(nb * L::M + v) * 2 + 1]);
+                            const long long kl = lim_key(S.lim_mm[(nb * L::M + v) * 2]);
+                            const long long kh = lim_key(S.lim_mm[(nb * L::M + v) * 2 + 1]);
+                            klo = kl < klo ? kl : klo;
+                            khi = kh > khi ? kh : khi;
                         }
+                    const double lo = lim_unkey(klo), hi = lim_unkey(khi);
                     const double delta = fmax(1e-4, 1e-3 * (hi - lo));
+                    const long long blo = lim_key(lo - delta), bhi = lim_key(hi + delta);
                     for (int a = lane; a < L::NSUB; a += 32) {
-                        const double x = avg[a * L::M + v];
-                        bad |= x < lo - delta || x > hi + delta;
+                        const long long k = lim_key(avg[a * L::M + v]);
+                        bad |= k < blo || k > bhi;
                     }
                 }
                 bad = __any_sync(0xffffffffu, bad);
@@ -392,7 +458,7 @@ __global__ void __launch_bounds__(128) k_lim_fv(const KParams P)
             }
             for (int i = threadIdx.x; i < L::NSUB * M; i += blockDim.x) sm.dq[i] += sm.avg[i];
             __syncthreads();
-            lim_tensor<DIM, M>(sm.dq, sm.u, sm.ta, sm.tb, sm.Rc, L::n, S_);
+            lim_tensor<DIM, M, L::n, S_>(sm.dq, sm.u, sm.ta, sm.tb, sm.Rc);
             for (int i = threadIdx.x; i < L::NS * M; i += blockDim.x) S.u_out[e * (L::NS * M) + i] = sm.u[i];
             __syncthreads();
         }

@@ -163,7 +163,8 @@ struct aderdg_s {
     void *qprev = nullptr;      // extrapolation guess: last predictor [E][n][NS][M]
     bool limiter = false;       // subcell limiter after every step
     double *u_prev = nullptr;   // limiter: u^n saved before the corrector
-    double *lim_mm = nullptr;   // limiter: extreme subcell averages [E][M][2]
+    double *lim_mm = nullptr;   // limiter: extreme subcell averages of u^n [E][M][2]
+    double *lim_mmc = nullptr;  // limiter: those of the candidate, kept for the next step
     int *lim_flags = nullptr;   // limiter: troubled elements of the last step [E]
     double *host_pinned = nullptr;
     KParams kp{};
@@ -221,11 +222,15 @@ int launch_corrector(aderdg_t *h, int use_ctl, double dt)
 }
 
 // Clears the step's wave-speed maxima and non-finite flag before they are
-// taken again from the limited state.
+// taken again from the limited state, and marks the candidate extremes as
+// those of the new state (where the limiter left an element untouched).
 __global__ void k_lim_reset(Control *c)
 {
     if (threadIdx.x < 3) c->lam_acc[threadIdx.x] = 0ull;
-    if (threadIdx.x == 0) c->flags &= ~FLAG_NONFINITE;
+    if (threadIdx.x == 0) {
+        c->flags &= ~FLAG_NONFINITE;
+        c->lim_fresh = 1u;
+    }
 }
 
 // The subcell limiter on the candidate the corrector left in u (Sec. 2.3):
@@ -465,11 +470,12 @@ int aderdg_create(const aderdg_mesh_t *mesh, int N, int nVar, const aderdg_pde_t
     if (h->limiter) {
         h->u_prev = (double *)dev_alloc(h, nstate * sizeof(double));
         h->lim_mm = (double *)dev_alloc(h, sizeof(double) * (size_t)E * m * 2);
+        h->lim_mmc = (double *)dev_alloc(h, sizeof(double) * (size_t)E * m * 2);
         h->lim_flags = (int *)dev_alloc(h, sizeof(int) * (size_t)E);
     }
     if (!h->u || !h->V || !h->tr || !h->ctl || !h->scratch || !h->d_desc || (ks->rf > 0 && !h->ref) ||
         (h->guess == ADERDG_GUESS_EXTRAP && !h->qprev) ||
-        (h->limiter && (!h->u_prev || !h->lim_mm || !h->lim_flags))) {
+        (h->limiter && (!h->u_prev || !h->lim_mm || !h->lim_mmc || !h->lim_flags))) {
         aderdg_destroy(h);
         return fail(ADERDG_E_NOMEM, "device allocation failed");
     }
@@ -500,6 +506,7 @@ int aderdg_create(const aderdg_mesh_t *mesh, int N, int nVar, const aderdg_pde_t
     sd.ctl = h->ctl;
     sd.u_prev = h->u_prev;
     sd.lim_mm = h->lim_mm;
+    sd.lim_mmc = h->lim_mmc;
     sd.lim_flags = h->lim_flags;
     KParams &kp = h->kp;
     std::memset(&kp, 0, sizeof(kp));
@@ -536,6 +543,7 @@ int aderdg_destroy(aderdg_t *h)
     dev_free(h, h->u);
     dev_free(h, h->u_prev);
     dev_free(h, h->lim_mm);
+    dev_free(h, h->lim_mmc);
     dev_free(h, h->lim_flags);
     dev_free(h, h->V);
     dev_free(h, h->tr);
@@ -624,6 +632,8 @@ int aderdg_corrector(aderdg_t *h, double dt)
     if (!h) return fail(ADERDG_E_INVAL, "NULL handle");
     if (!(dt > 0.0) || !std::isfinite(dt)) return fail(ADERDG_E_INVAL, "dt must be positive and finite");
     CK(cudaMemsetAsync(h->ctl->lam_acc, 0, sizeof(h->ctl->lam_acc), h->stream));
+    // the state changes without the limiter: its kept extremes are stale
+    CK(cudaMemsetAsync(&h->ctl->lim_fresh, 0, sizeof(h->ctl->lim_fresh), h->stream));
     return launch_corrector(h, 0, dt);
 }
 

@@ -135,3 +135,38 @@ def test_limiter_on_advection_and_elasticity(pde):
         assert np.abs(s.get_state()[0] - Uo).max() <= 1e-11 * max(1.0, np.abs(Uo).max())
     s.close()
     assert seen > 0
+
+
+def _limited_run(c, U, steps, upload_between, explicit_first=False):
+    s = _solver(c)
+    s.set_state(U)
+    if explicit_first:  # one unlimited step through the explicit entry points
+        dt = 0.5 * oracle.cfl_dt(c, U)
+        s.predictor(dt)
+        s.corrector(dt)
+    flags = []
+    for k in range(steps):
+        if upload_between and (k or explicit_first):
+            Ug, t, _ = s.get_state()
+            s.set_state(Ug, t)
+        s.step(1e30, sync_dt=True)
+        flags.append(s.troubled()[0])
+    Ug = s.get_state()[0]
+    s.close()
+    return Ug, flags
+
+
+@pytest.mark.parametrize("explicit_first", [False, True], ids=["steps", "after_explicit_corrector"])
+def test_kept_extremes_equal_fresh_projections(explicit_first):
+    """The detection keeps each candidate's extreme subcell averages, and the
+    next step reuses them for every element the limiter left untouched
+    (neither troubled nor next to a troubled one).  A state upload before
+    each step, or an explicit corrector call, makes every element project
+    u^n afresh instead; the two runs agree bit for bit."""
+    c, U = _explosion()
+    Ua, fa = _limited_run(c, U, 10, False, explicit_first)
+    Ub, fb = _limited_run(c, U, 10, True, explicit_first)
+    np.testing.assert_array_equal(Ua, Ub)
+    for a, b in zip(fa, fb):
+        np.testing.assert_array_equal(a, b)
+    assert any(f.any() for f in fa) and not all(f.all() for f in fa)
