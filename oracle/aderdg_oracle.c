@@ -25,7 +25,8 @@
  *     discrete maximum principle on subcell averages), a second-order
  *     finite-volume step of the troubled elements on (2N+1)^d subcells,
  *     least-squares reconstruction of the DG polynomial, and the matching
- *     face fluxes in the unlimited neighbours (readings R25-R28)
+ *     face fluxes in the unlimited neighbours (readings R25-R29; with
+ *     non-conservative products and sources, eq. pde.nc.fv)
  *   - PDEs: linear advection with an optional linear reaction source
  *     S = -kappa q, Euler (Sec. 3.1, eq. euler, ideal gas), the
  *     velocity-stress linear elasticity system obtained from Sec. 3.2 with
@@ -76,6 +77,19 @@
  *      (F(p) = sum_seg F_seg int_seg phi_p / w_p) instead of its DG flux
  *   R28 reconstruction: least squares from the (2N+1)^d subcell averages;
  *      with equal subcells it keeps the element's mass
+ *   R29 the subcell scheme with B(Q) grad Q and S(Q) (eq. pde.nc.fv): the
+ *      half-step of each face value adds -(dt/2h) B_d(w) s and (dt/2) S(w)
+ *      (w the subcell average, s its minmod slope); a face gives the lower
+ *      subcell the path-conservative fluctuation of the DG faces (R20) with
+ *      +J/2 and the upper one that with -J/2; inside the subcell
+ *      -(dt/h) B_d(w~) s is added, w~ the half-step centre along d; the
+ *      source enters as dt S(w*), w* = w + the half-step changes of all
+ *      directions + (dt/2) S(w); the material fields are kept as they were
+ *   R30 coupling with B(Q) grad Q: an unlimited neighbour takes, per face
+ *      node, the projected subcell fluctuation it receives plus the path
+ *      integral J from its own DG trace to its own subcell state at that
+ *      subcell face (with B the Jacobian of a flux this is R27: the flux
+ *      difference between the two states of its own side)
  *
  * Layout: u[e][s][v] with v fastest, then x, y, z (s = sx + n*sy + n^2*sz);
  * space-time qhat[t][s][v] with time slowest (the AoS layout of Sec. 2.2).
@@ -1016,8 +1030,9 @@ double orc_cfl_dt(const orc_cfg *c, const double *U)
  * from the state U0 at t^n and the candidate's traces qf / ff:
  *   1. extreme subcell averages of U0 per element and variable;
  *   2. detection (R25) -> troubled[e] (may be NULL);
- *   3. troubled elements: MUSCL-Hancock on their subcells from U0 (R26),
- *      least-squares reconstruction (R28), boundary subcell fluxes kept;
+ *   3. troubled elements: MUSCL-Hancock on their subcells from U0 (R26,
+ *      R29), least-squares reconstruction (R28), boundary subcell
+ *      fluctuations kept (the one each face neighbour receives);
  *   4. unlimited face neighbours of troubled elements: their DG face flux on
  *      the common face replaced by the projected subcell fluxes (R27).
  * Returns the number of troubled elements, or < 0 on failure. */
@@ -1030,10 +1045,13 @@ static long apply_limiter(const orc_cfg *c, const basis *b, const double *U0, do
     const int ns = ipow(n, dim), nf = ipow(n, dim - 1), nsub = ipow(S, dim), nline = ipow(S, dim - 1);
     const long E = n_elems(c);
     const size_t fsz = (size_t)2 * dim * nf * m;
+    const int ncp = c->pde == 4, src = c->pde == 1, mev = orc_nevolved(c);
     double *mm = malloc(sizeof(double) * (size_t)E * m * 2);          /* [e][v][min|max] of U0 */
     int *bad = malloc(sizeof(int) * (size_t)E);
     double *Unew = malloc(sizeof(double) * (size_t)E * ns * m);
-    double *Fb = malloc(sizeof(double) * (size_t)E * dim * 2 * nline * m); /* [e][d][side][line][v] */
+    /* [e][d][side][line][2m]: the boundary fluctuation a face neighbour
+     * receives, then that neighbour's own subcell state at the face */
+    double *Fb = malloc(sizeof(double) * (size_t)E * dim * 2 * nline * 2 * m);
     if (!mm || !bad || !Unew || !Fb) { free(mm); free(bad); free(Unew); free(Fb); return -2; }
     long count = 0;
 
@@ -1095,6 +1113,7 @@ static long apply_limiter(const orc_cfg *c, const basis *b, const double *U0, do
     {
         double *avg = malloc(sizeof(double) * (size_t)(1 + 2 * dim) * nsub * m);
         double *dq = malloc(sizeof(double) * (size_t)nsub * m);
+        double *ctr = malloc(sizeof(double) * (size_t)nsub * m);  /* sum over d of the half-step changes */
 #pragma omp for schedule(dynamic)
         for (long e = 0; e < E; ++e) {
             if (!bad[e]) continue;
@@ -1104,7 +1123,7 @@ static long apply_limiter(const orc_cfg *c, const basis *b, const double *U0, do
                 for (int sd = 0; sd < 2; ++sd)
                     subcell_averages(c, &o, &U0[(size_t)neighbour(c, e, d, sd ? 1 : -1) * ns * m],
                                      &avg[(size_t)(1 + 2 * d + sd) * nsub * m]);
-            for (size_t i = 0; i < (size_t)nsub * m; ++i) dq[i] = 0.0;
+            for (size_t i = 0; i < (size_t)nsub * m; ++i) dq[i] = ctr[i] = 0.0;
             for (int d = 0; d < dim; ++d) {
                 const double h = cell_dx(c, d) / S, r = dt / h;
                 for (int l = 0; l < nline; ++l) {
@@ -1124,40 +1143,90 @@ static long apply_limiter(const orc_cfg *c, const basis *b, const double *U0, do
                         memcpy(line[i + 2], src, sizeof(double) * m);
                     }
                     double qm[2 * ORC_MAXN + 1][ORC_MAXM], qp[2 * ORC_MAXN + 1][ORC_MAXM];  /* cells -1 .. S */
+                    double cs[2 * ORC_MAXN + 1][ORC_MAXM], cw[2 * ORC_MAXN + 1][ORC_MAXM];  /* cells 0 .. S-1: */
+                    double cc[2 * ORC_MAXN + 1][ORC_MAXM];  /* slope, half-step centre, its change without S */
                     for (int i = -1; i <= S; ++i) {
-                        double lo[ORC_MAXM], hi[ORC_MAXM], fl[ORC_MAXM], fh[ORC_MAXM];
+                        double lo[ORC_MAXM], hi[ORC_MAXM], fl[ORC_MAXM], fh[ORC_MAXM], sl[ORC_MAXM];
+                        double Bs[ORC_MAXM], Sv[ORC_MAXM];
                         for (int v = 0; v < m; ++v) {
-                            const double sl = minmod(line[i + 2][v] - line[i + 1][v], line[i + 3][v] - line[i + 2][v]);
-                            lo[v] = line[i + 2][v] - 0.5 * sl;
-                            hi[v] = line[i + 2][v] + 0.5 * sl;
+                            sl[v] = minmod(line[i + 2][v] - line[i + 1][v], line[i + 3][v] - line[i + 2][v]);
+                            lo[v] = line[i + 2][v] - 0.5 * sl[v];
+                            hi[v] = line[i + 2][v] + 0.5 * sl[v];
                         }
                         orc_flux(c, lo, d, fl);
                         orc_flux(c, hi, d, fh);
+                        if (ncp) orc_ncp(c, line[i + 2], d, sl, Bs);          /* B_d(w) times the slope */
+                        if (src) orc_source(c, line[i + 2], Sv);
                         for (int v = 0; v < m; ++v) {
-                            qm[i + 1][v] = lo[v] - 0.5 * r * (fh[v] - fl[v]);
-                            qp[i + 1][v] = hi[v] - 0.5 * r * (fh[v] - fl[v]);
+                            const double df = ncp ? fh[v] - fl[v] + Bs[v] : fh[v] - fl[v];
+                            qm[i + 1][v] = lo[v] - 0.5 * r * df;
+                            qp[i + 1][v] = hi[v] - 0.5 * r * df;
+                            if (src) {
+                                qm[i + 1][v] += 0.5 * dt * Sv[v];
+                                qp[i + 1][v] += 0.5 * dt * Sv[v];
+                            }
+                            if (i >= 0 && i < S) {
+                                cs[i][v] = sl[v];
+                                cc[i][v] = -0.5 * r * df;
+                                cw[i][v] = line[i + 2][v] + cc[i][v] + (src ? 0.5 * dt * Sv[v] : 0.0);
+                            }
                         }
                     }
-                    double Fh[2 * ORC_MAXN + 1][ORC_MAXM];  /* faces 0 .. S (face f: cells f-1 | f) */
+                    /* faces 0 .. S (face f: cells f-1 | f); the lower cell
+                     * receives Fl, the upper one Fu (equal without B) */
+                    double Fl[2 * ORC_MAXN + 1][ORC_MAXM], Fu[2 * ORC_MAXN + 1][ORC_MAXM];
                     for (int f = 0; f <= S; ++f) {
                         double fl[ORC_MAXM], fr[ORC_MAXM];
                         orc_flux(c, qp[f], d, fl);
                         orc_flux(c, qm[f + 1], d, fr);
-                        orc_rusanov(c, d, qp[f], fl, qm[f + 1], fr, Fh[f]);
+                        if (ncp) {
+                            orc_face_flux(c, d, qp[f], fl, qm[f + 1], fr, Fl[f], Fu[f]);
+                        } else {
+                            orc_rusanov(c, d, qp[f], fl, qm[f + 1], fr, Fl[f]);
+                            memcpy(Fu[f], Fl[f], sizeof(double) * m);
+                        }
                     }
-                    for (int i = 0; i < S; ++i)
-                        for (int v = 0; v < m; ++v) dq[((size_t)base + i * st) * m + v] -= r * (Fh[i + 1][v] - Fh[i][v]);
+                    for (int i = 0; i < S; ++i) {
+                        double Bc[ORC_MAXM];
+                        /* the smooth part of B(q) grad q inside the subcell, at the half-step centre */
+                        if (ncp) orc_ncp(c, cw[i], d, cs[i], Bc);
+                        for (int v = 0; v < m; ++v) {
+                            const size_t k = ((size_t)base + i * st) * m + v;
+                            dq[k] -= r * (Fl[i + 1][v] - Fu[i][v]);
+                            if (ncp) dq[k] -= r * Bc[v];
+                            if (src) ctr[k] += cc[i][v];
+                        }
+                    }
                     for (int v = 0; v < m; ++v) {
-                        Fb[((((size_t)e * dim + d) * 2 + 0) * nline + l) * m + v] = Fh[0][v];
-                        Fb[((((size_t)e * dim + d) * 2 + 1) * nline + l) * m + v] = Fh[S][v];
+                        double *b0 = &Fb[((((size_t)e * dim + d) * 2 + 0) * nline + l) * 2 * m];
+                        double *b1 = &Fb[((((size_t)e * dim + d) * 2 + 1) * nline + l) * 2 * m];
+                        b0[v] = Fl[0][v];
+                        b0[m + v] = qp[0][v];
+                        b1[v] = Fu[S][v];
+                        b1[m + v] = qm[S + 1][v];
                     }
+                }
+            }
+            if (src) {
+                /* the source at the half-step centre of all directions (second order in time) */
+                for (int a = 0; a < nsub; ++a) {
+                    double S0[ORC_MAXM], S1[ORC_MAXM], w[ORC_MAXM];
+                    orc_source(c, &avg[(size_t)a * m], S0);
+                    for (int v = 0; v < m; ++v) w[v] = avg[(size_t)a * m + v] + ctr[(size_t)a * m + v] + 0.5 * dt * S0[v];
+                    orc_source(c, w, S1);
+                    for (int v = 0; v < m; ++v) dq[(size_t)a * m + v] += dt * S1[v];
                 }
             }
             for (size_t i = 0; i < (size_t)nsub * m; ++i) dq[i] += avg[i];
             subcell_reconstruct(c, &o, dq, &Unew[(size_t)e * ns * m]);
+            /* the material fields obey q_t = 0: kept as they were */
+            for (int s2 = 0; s2 < ns; ++s2)
+                for (int v = mev; v < m; ++v)
+                    Unew[((size_t)e * ns + s2) * m + v] = U0[((size_t)e * ns + s2) * m + v];
         }
         free(avg);
         free(dq);
+        free(ctr);
     }
     /* 4. unlimited neighbours: projected subcell fluxes on the common faces */
 #pragma omp parallel for schedule(static)
@@ -1169,7 +1238,7 @@ static long apply_limiter(const orc_cfg *c, const basis *b, const double *U0, do
                 if (!bad[nb]) continue;
                 /* the troubled neighbour's boundary fluxes on this face: its
                  * side 0 face if e is below it (side 1 of e), else side 1 */
-                const double *Fs = &Fb[(((size_t)nb * dim + d) * 2 + (side ? 0 : 1)) * nline * m];
+                const double *Fs = &Fb[(((size_t)nb * dim + d) * 2 + (side ? 0 : 1)) * nline * 2 * m];
                 for (int p = 0; p < nf; ++p) {
                     /* the face node's transverse indices */
                     int pk[3], rem = p, kk = 0;
@@ -1178,6 +1247,14 @@ static long apply_limiter(const orc_cfg *c, const basis *b, const double *U0, do
                         pk[kk++] = rem % n;
                         rem /= n;
                     }
+                    /* the DG flux this element used on the face */
+                    double lower[ORC_MAXM], upper[ORC_MAXM];
+                    const long el = side ? e : nb, eu = side ? nb : e;
+                    const size_t oL = (size_t)el * fsz + (((size_t)d * 2 + 1) * nf + p) * m;
+                    const size_t oR = (size_t)eu * fsz + (((size_t)d * 2 + 0) * nf + p) * m;
+                    orc_face_flux(c, d, &qf[oL], &ff[oL], &qf[oR], &ff[oR], lower, upper);
+                    const double *Fdg = side ? lower : upper;
+                    const double *qown = side ? &qf[oL] : &qf[oR];
                     double Ft[ORC_MAXM];
                     for (int v = 0; v < m; ++v) Ft[v] = 0.0;
                     for (int l = 0; l < nline; ++l) {
@@ -1188,15 +1265,17 @@ static long apply_limiter(const orc_cfg *c, const basis *b, const double *U0, do
                             lr /= S;
                             wgt *= o.Pr[j * n + pk[k]] / S / b->w[pk[k]];
                         }
-                        for (int v = 0; v < m; ++v) Ft[v] += wgt * Fs[(size_t)l * m + v];
+                        const double *fs = &Fs[(size_t)l * 2 * m];
+                        if (ncp) {
+                            /* R30: plus the path integral from this element's
+                             * own DG trace to its own subcell state at the face */
+                            double J[ORC_MAXM];
+                            orc_path_jump(c, d, qown, fs + m, J);
+                            for (int v = 0; v < m; ++v) Ft[v] += wgt * (fs[v] + J[v]);
+                        } else {
+                            for (int v = 0; v < m; ++v) Ft[v] += wgt * fs[v];
+                        }
                     }
-                    /* the DG flux this element used on the face */
-                    double lower[ORC_MAXM], upper[ORC_MAXM];
-                    const long el = side ? e : nb, eu = side ? nb : e;
-                    const size_t oL = (size_t)el * fsz + (((size_t)d * 2 + 1) * nf + p) * m;
-                    const size_t oR = (size_t)eu * fsz + (((size_t)d * 2 + 0) * nf + p) * m;
-                    orc_face_flux(c, d, &qf[oL], &ff[oL], &qf[oR], &ff[oR], lower, upper);
-                    const double *Fdg = side ? lower : upper;
                     for (int s = 0; s < ns; ++s) {
                         if (face_index(s, n, dim, d) != p) continue;
                         const int sd = digit(s, n, d);
@@ -1231,9 +1310,8 @@ static int step_impl(const orc_cfg *c, double *U, double dt, double *V_out, doub
 {
     basis b;
     if (make_basis(c->N, &b)) return -1;
-    /* the limiter's subcell scheme covers conservative systems without a
-     * source, and needs every step's predictor fresh (no extrapolation) */
-    if (c->limiter && (c->pde == 4 || (c->pde == 1 && c->prm[3] != 0.0) || c->guess == 3)) return -3;
+    /* the limiter needs every step's predictor fresh (no extrapolation) */
+    if (c->limiter && c->guess == 3) return -3;
     const int n = b.n, dim = c->dim, m = c->m;
     const int ns = ipow(n, dim), nf = ipow(n, dim - 1);
     const long E = n_elems(c);

@@ -14,6 +14,10 @@
   couplings, and the x <-> y mirror symmetry of the data kept to rounding
   (a wrong index or orientation in the subcell sweeps or the face coupling
   breaks it).
+- Non-conservative products and sources (eq. pde.nc.fv): with alpha = 1 the
+  diffuse-interface subcell scheme is the conservative elasticity one; a
+  soft inclusion keeps the mirror symmetry; the reaction source on uniform
+  data gives the second-order Taylor step in closed form.
 """
 import math
 
@@ -157,10 +161,92 @@ def test_limited_explosion_conserves_and_keeps_symmetry():
 
 
 def test_limiter_rejects_what_it_does_not_cover():
-    c = oracle.make_cfg(2, (4, 4), [0, 0], [1, 1], 2, oracle.PDE_DIFFUSE_ELASTICITY, [], limiter=1)
-    with pytest.raises(RuntimeError):
-        oracle.step_limited(c, np.ones((16, 9, 9)), 1e-3)
     c = oracle.make_cfg(2, (4, 4), [0, 0], [1, 1], 2, oracle.PDE_EULER, [1.4], limiter=1,
                         guess=oracle.GUESS_EXTRAP)
     with pytest.raises(RuntimeError):
         oracle.step_limited(c, np.ones((16, 9, 4)), 1e-3)
+
+
+def test_limited_diffuse_interface_with_alpha_one_equals_limited_elasticity():
+    """alpha = 1 and constant material: the path-conservative subcell scheme
+    (fluctuations +-J/2 at subcell faces, B(w~) s inside the subcells,
+    B_d(w) s in the half-step) is the conservative MUSCL-Hancock scheme of
+    the elasticity flux, since B_d is then that flux's constant Jacobian;
+    and the unlimited neighbours' coupled fluctuations are the conservative
+    fluxes (R30: the path integral between the two states of the unlimited
+    element's side is then their flux difference).  Limited runs agree to
+    rounding with equal troubled sets; the material fields stay bitwise
+    constant."""
+    cells, N = (12, 2, 2), 2
+    ce = oracle.make_cfg(3, cells, [0] * 3, [1] * 3, N, oracle.PDE_ELASTICITY, [1.0, 2.0, 1.0], limiter=1)
+    cd = oracle.make_cfg(3, cells, [0] * 3, [1] * 3, N, oracle.PDE_DIFFUSE_ELASTICITY, [], limiter=1)
+    X = oracle.node_coords(ce)
+    v = np.where((X[..., 0] > 1 / 3) & (X[..., 0] < 2 / 3), 1.0, 0.0)
+    z = 0 * v
+    U9 = np.stack([z] * 6 + [v, 0.5 * v, z], axis=-1)
+    U13 = inputs.diffuse_pack(3, [U9[..., i] for i in range(6)], [U9[..., 6 + i] for i in range(3)], 1.0, 2.0, 1.0,
+                              1.0)
+    seen = 0
+    for _ in range(6):
+        dt = oracle.cfl_dt(ce, U9)
+        assert dt == oracle.cfl_dt(cd, U13)
+        U9, fe, ne = oracle.step_limited(ce, U9, dt)
+        Ud, fd, nd = oracle.step_limited(cd, U13, dt)
+        np.testing.assert_array_equal(fe, fd)
+        assert np.array_equal(Ud[..., 9:], U13[..., 9:])
+        U13 = Ud
+        seen = max(seen, ne)
+        assert np.abs(U13[..., :9] - U9).max() <= 1e-13 * np.abs(U9).max()
+    assert 0 < seen < 48  # limited and unlimited elements side by side
+
+
+def _mirror2d(U, cells, n):
+    """x <-> y mirror of a 2D diffuse-interface state [e][s][v]: the element
+    and node grids transposed, sigma_xx <-> sigma_yy, w_x <-> w_y."""
+    E = U.reshape(cells[1], cells[0], n, n, -1)
+    return E.transpose(1, 0, 3, 2, 4)[..., [1, 0, 2, 4, 3, 5, 6, 7, 8]].reshape(U.shape)
+
+
+def test_limited_diffuse_interface_keeps_mirror_symmetry():
+    """A soft inclusion (alpha from 1 to 0.3 across r = 0.25) hit by two
+    mirrored velocity boxes: the limited run keeps the x <-> y mirror
+    symmetry of the data to rounding (a wrong index, orientation or sign of
+    the alpha-gradient terms in the subcell sweeps or the coupling breaks
+    it) and the material fields bitwise."""
+    cells, N = (12, 12), 3
+    c = oracle.make_cfg(2, cells, [0, 0], [1, 1], N, oracle.PDE_DIFFUSE_ELASTICITY, [], limiter=1)
+    X = oracle.node_coords(c)
+    x, y = X[..., 0], X[..., 1]
+    r = np.sqrt((x - 0.5) ** 2 + (y - 0.5) ** 2)
+    alpha = inputs.smooth_step(r, 0.25, 0.04, 0.3, 1.0)
+    box = lambda a, b: np.where((a > 0.1) & (a < 0.3) & (b > 0.3) & (b < 0.6), 1.0, 0.0)
+    z = 0 * x
+    U = inputs.diffuse_pack(2, [z, z, z], [alpha * box(x, y), alpha * box(y, x)], alpha, 2.0, 1.0, 1.0)
+    assert np.abs(U - _mirror2d(U, cells, N + 1)).max() == 0
+    U0 = U.copy()
+    seen = 0
+    for _ in range(15):
+        U, flags, cnt = oracle.step_limited(c, U, oracle.cfl_dt(c, U))
+        seen = max(seen, cnt)
+    assert 0 < seen < 144
+    assert np.isfinite(U).all()
+    assert np.abs(U - _mirror2d(U, cells, N + 1)).max() < 1e-13 * np.abs(U).max()
+    assert np.array_equal(U[..., 5:], U0[..., 5:])
+
+
+def test_limited_reaction_on_uniform_data_is_the_second_order_taylor_step():
+    """Advection with the reaction S = -kappa q on uniform data: the decay
+    leaves the relaxed maximum principle, so every element is troubled; with
+    no gradients the subcell scheme reduces to the source at the half-step
+    centre, u (1 - z + z^2 / 2), z = kappa dt, at every node (the DG step
+    alone gives the subdiagonal Pade value instead)."""
+    kappa = 2.0
+    c = oracle.make_cfg(2, (4, 4), [0, 0], [1, 1], 3, oracle.PDE_ADVECTION, [1.0, 0.5, 0.0, kappa], limiter=1)
+    U = np.full((16, 16, 1), 0.8)
+    dt = oracle.cfl_dt(c, U)
+    Ul, flags, cnt = oracle.step_limited(c, U, dt)
+    assert cnt == 16 and flags.all()
+    zt = kappa * dt
+    np.testing.assert_allclose(Ul, 0.8 * (1 - zt + zt * zt / 2), rtol=1e-14)
+    c.limiter = 0
+    assert np.abs(oracle.step(c, U, dt) - 0.8 * (1 - zt + zt * zt / 2)).max() > 1e-6
