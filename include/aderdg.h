@@ -174,13 +174,14 @@ typedef struct {
                                    appended; NULL -> process memory only */
     int initial_guess;          /* ADERDG_GUESS_* (0: trivial) */
     int limiter;                /* 1: the a posteriori subcell finite-volume
-                                   limiter (Sec. 2.3) after every aderdg_step /
-                                   aderdg_advance step: FP64 precision,
-                                   conservative systems without a source
-                                   (advection, Euler, elasticity), not with the
-                                   EXTRAP guess; ADERDG_E_UNSUPPORTED for an
-                                   instance whose subcell arrays do not fit
-                                   a CTA (3D elasticity N = 4) */
+                                   limiter (Sec. 2.3, eq. pde.nc.fv) after
+                                   every aderdg_step / aderdg_advance step:
+                                   FP64 precision, every PDE (non-conservative
+                                   products and sources included), not with
+                                   the EXTRAP guess; ADERDG_E_UNSUPPORTED for
+                                   an instance whose subcell arrays do not fit
+                                   a CTA (3D elasticity N = 4, 3D
+                                   diffuse-interface elasticity N = 3) */
 } aderdg_config_t;
 
 typedef struct aderdg_s aderdg_t;

@@ -33,13 +33,15 @@ struct LimCfg {
                                     DIM == 3 ? cmax(S * S * n, n * n * S) : 0) * M;
     static constexpr int OPS = round_up(2 * S * n, 2);
     static constexpr int GHOST = 2 * DIM * 2 * NLINE * M;  // [d][side][layer][line][v]
-    static constexpr int FACES = (S + 1) * NLINE * M;      // subcell face fluxes of one direction
+    // subcell face fluxes of one direction (non-conservative systems: the
+    // fluctuations of the lower and of the upper subcell)
+    static constexpr int FACES = (S + 1) * NLINE * M * (PDE::NCP ? 2 : 1);
     // doubles: operators, staged nodes, own averages, a neighbour's averages,
     // ghost layers, increments, two projection buffers, face fluxes
     static constexpr size_t DOUBLES = OPS + round_up(NS * M, 2) + 3 * (size_t)NSUB * M + GHOST + 2 * TMP + FACES;
     static constexpr size_t BYTES = sizeof(double) * DOUBLES;
     static constexpr bool FITS = BYTES <= 227 * 1024;
-    static constexpr bool OK = FITS && !PDE::NCP;
+    static constexpr bool OK = FITS;
 };
 
 // One direction of a tensor-product application: LO points before the
@@ -133,10 +135,10 @@ __device__ __forceinline__ double lim_minmod(double a, double b)
 // d (MUSCL-Hancock), Rusanov flux.  The one routine every face uses.
 template <class PDE, int DIM>
 __device__ void lim_face(const PdeParams &P, const double *a, const double *b, const double *c, const double *e, int d,
-                         double r, double *F)
+                         double r, double dt, double *F)
 {
     constexpr int M = PDE::M;
-    double lo[M], hi[M], qp[M], qm[M], fl[DIM][M], fh[DIM][M];
+    double lo[M], hi[M], qp[M], qm[M], fl[DIM][M], fh[DIM][M], Sv[M];
 #pragma unroll
     for (int v = 0; v < M; ++v) {
         const double s = lim_minmod(b[v] - a[v], c[v] - b[v]);
@@ -145,12 +147,14 @@ __device__ void lim_face(const PdeParams &P, const double *a, const double *b, c
     }
     PDE::flux(P, lo, fl);
     PDE::flux(P, hi, fh);
+    if constexpr (PDE::HAS_SRC) PDE::source(P, b, Sv);
 #pragma unroll
     for (int v = 0; v < M; ++v) {
         double df = fh[0][v] - fl[0][v];
 #pragma unroll
         for (int k = 1; k < DIM; ++k) df = d == k ? fh[k][v] - fl[k][v] : df;
         qp[v] = hi[v] - 0.5 * r * df;
+        if constexpr (PDE::HAS_SRC) qp[v] += 0.5 * dt * Sv[v];
     }
 #pragma unroll
     for (int v = 0; v < M; ++v) {
@@ -160,12 +164,14 @@ __device__ void lim_face(const PdeParams &P, const double *a, const double *b, c
     }
     PDE::flux(P, lo, fl);
     PDE::flux(P, hi, fh);
+    if constexpr (PDE::HAS_SRC) PDE::source(P, c, Sv);
 #pragma unroll
     for (int v = 0; v < M; ++v) {
         double df = fh[0][v] - fl[0][v];
 #pragma unroll
         for (int k = 1; k < DIM; ++k) df = d == k ? fh[k][v] - fl[k][v] : df;
         qm[v] = lo[v] - 0.5 * r * df;
+        if constexpr (PDE::HAS_SRC) qm[v] += 0.5 * dt * Sv[v];
     }
     PDE::flux(P, qp, fl);
     PDE::flux(P, qm, fh);
@@ -177,6 +183,84 @@ __device__ void lim_face(const PdeParams &P, const double *a, const double *b, c
 #pragma unroll
         for (int k = 1; k < DIM; ++k) fsum = d == k ? fl[k][v] + fh[k][v] : fsum;
         F[v] = 0.5 * fsum - 0.5 * smax * (qm[v] - qp[v]);
+    }
+}
+
+// B_d(q) g of a non-conservative system (zero otherwise)
+template <class PDE>
+__device__ __forceinline__ void lim_bdot(const double *q, int d, const double *g, double *out)
+{
+    if constexpr (PDE::NCP) {
+        PDE::bdot(q, recip(q[PDE::IA]), recip(q[PDE::IR]), d, g, g[PDE::IA], out);
+    } else {
+#pragma unroll
+        for (int v = 0; v < PDE::M; ++v) out[v] = 0.0;
+    }
+}
+
+// MUSCL-Hancock half-step of subcell b (neighbours a, c along d; r = dt /
+// subcell width): minmod slope s, the two face values evolved by
+// -(r/2) (F_d(hi) - F_d(lo) + B_d(b) s) + (dt/2) S(b) into qlo / qhi, and
+// that change without the source into chc (any output may be null)
+template <class PDE, int DIM>
+__device__ void lim_half(const PdeParams &P, const double *a, const double *b, const double *c, int d, double r,
+                         double dt, double *s, double *qlo, double *qhi, double *chc)
+{
+    constexpr int M = PDE::M;
+    double sl[M], lo[M], hi[M], fl[DIM][M], fh[DIM][M], Bs[M], Sv[M];
+#pragma unroll
+    for (int v = 0; v < M; ++v) {
+        sl[v] = lim_minmod(b[v] - a[v], c[v] - b[v]);
+        lo[v] = b[v] - 0.5 * sl[v];
+        hi[v] = b[v] + 0.5 * sl[v];
+    }
+    PDE::flux(P, lo, fl);
+    PDE::flux(P, hi, fh);
+    if constexpr (PDE::NCP) lim_bdot<PDE>(b, d, sl, Bs);
+    if constexpr (PDE::HAS_SRC) PDE::source(P, b, Sv);
+#pragma unroll
+    for (int v = 0; v < M; ++v) {
+        double df = fh[0][v] - fl[0][v];
+#pragma unroll
+        for (int k = 1; k < DIM; ++k) df = d == k ? fh[k][v] - fl[k][v] : df;
+        if constexpr (PDE::NCP) df += Bs[v];
+        double ql = lo[v] - 0.5 * r * df, qh = hi[v] - 0.5 * r * df;
+        if constexpr (PDE::HAS_SRC) {
+            ql += 0.5 * dt * Sv[v];
+            qh += 0.5 * dt * Sv[v];
+        }
+        if (s) s[v] = sl[v];
+        if (qlo) qlo[v] = ql;
+        if (qhi) qhi[v] = qh;
+        if (chc) chc[v] = -0.5 * r * df;
+    }
+}
+
+// Path-conservative subcell face along d between cells b and c (a, b, c, e
+// consecutive): the lower cell receives Fl = -s_max dq/2 + J/2, the upper
+// one Fu = -s_max dq/2 - J/2 (s_max dq on the evolved variables only), dq
+// and J between the evolved face values qb (upper value of b) and qc
+// (lower value of c), which are returned too (any of them may be null)
+template <class PDE, int DIM>
+__device__ void lim_face_nc(const PdeParams &P, const double *a, const double *b, const double *c, const double *e,
+                            int d, double r, double dt, double *Fl, double *Fu, double *qb_out, double *qc_out)
+{
+    constexpr int M = PDE::M;
+    double qb[M], qc[M], dq[M], J[M];
+    lim_half<PDE, DIM>(P, a, b, c, d, r, dt, nullptr, nullptr, qb, nullptr);
+    lim_half<PDE, DIM>(P, b, c, e, d, r, dt, nullptr, qc, nullptr, nullptr);
+#pragma unroll
+    for (int v = 0; v < M; ++v) dq[v] = qc[v] - qb[v];
+    PDE::path_jump(qb, dq, d, J);
+    const double sl = PDE::max_eig(P, qb, d), sr = PDE::max_eig(P, qc, d);
+    const double smax = sl > sr ? sl : sr;
+#pragma unroll
+    for (int v = 0; v < M; ++v) {
+        const double f = v < PDE::MEV ? -(0.5 * smax * dq[v]) : 0.0;
+        if (Fl) Fl[v] = f + 0.5 * J[v];
+        if (Fu) Fu[v] = f - 0.5 * J[v];
+        if (qb_out) qb_out[v] = qb[v];
+        if (qc_out) qc_out[v] = qc[v];
     }
 }
 
@@ -429,7 +513,10 @@ __global__ void __launch_bounds__(128) k_lim_fv(const KParams P)
                     lim_layers<L, DIM>(sm.nb, d, side ? 0 : 1, sm.ghost + (size_t)(d * 2 + side) * 2 * L::NLINE * M);
                     __syncthreads();
                 }
-            for (int i = threadIdx.x; i < L::NSUB * M; i += blockDim.x) sm.dq[i] = 0.0;
+            // sm.nb is free from here on: the source's sum over directions of
+            // the half-step changes
+            double *ctr = sm.nb;
+            for (int i = threadIdx.x; i < L::NSUB * M; i += blockDim.x) sm.dq[i] = ctr[i] = 0.0;
             __syncthreads();
 #pragma unroll 1
             for (int d = 0; d < DIM; ++d) {
@@ -440,26 +527,75 @@ __global__ void __launch_bounds__(128) k_lim_fv(const KParams P)
                     if (i >= S_) return sm.ghost + ((size_t)((d * 2 + 1) * 2 + (i - S_)) * L::NLINE + l) * M;
                     return sm.avg + lim_cell<DIM, S_>(d, l, i) * M;
                 };
-                // every face flux of this direction (face f between cells f-1 and f)
+                // every face of this direction (face f between cells f-1 and f):
+                // the flux, or the two fluctuations [lower | upper]
+                constexpr int FW = PDE::NCP ? 2 * M : M;
                 for (int it = threadIdx.x; it < (S_ + 1) * L::NLINE; it += blockDim.x) {
                     const int f = it % (S_ + 1), l = it / (S_ + 1);
-                    lim_face<PDE, DIM>(P.pde, cell(l, f - 2), cell(l, f - 1), cell(l, f), cell(l, f + 1), d, r,
-                                       sm.fb + (size_t)it * M);
+                    double *fo = sm.fb + (size_t)it * FW;
+                    if constexpr (PDE::NCP)
+                        lim_face_nc<PDE, DIM>(P.pde, cell(l, f - 2), cell(l, f - 1), cell(l, f), cell(l, f + 1), d, r,
+                                              dt, fo, fo + M, nullptr, nullptr);
+                    else
+                        lim_face<PDE, DIM>(P.pde, cell(l, f - 2), cell(l, f - 1), cell(l, f), cell(l, f + 1), d, r, dt,
+                                           fo);
                 }
                 __syncthreads();
                 for (int it = threadIdx.x; it < S_ * L::NLINE; it += blockDim.x) {
                     const int i = it % S_, l = it / S_;
-                    const double *F0 = sm.fb + (size_t)(l * (S_ + 1) + i) * M, *F1 = F0 + M;
-                    double *o = sm.dq + lim_cell<DIM, S_>(d, l, i) * M;
+                    const double *F0 = sm.fb + (size_t)(l * (S_ + 1) + i) * FW, *F1 = F0 + FW;
+                    const int k = lim_cell<DIM, S_>(d, l, i);
+                    double *o = sm.dq + k * M;
+                    if constexpr (PDE::NCP) {
+                        // F1: the lower cell's fluctuation of face i+1; F0 + M:
+                        // the upper cell's of face i; then the smooth part of
+                        // B(q) grad q inside the subcell at its half-step centre
+                        double sl[M], chc[M], cw[M], Bc[M];
+                        const double *w = cell(l, i);
+                        lim_half<PDE, DIM>(P.pde, cell(l, i - 1), w, cell(l, i + 1), d, r, dt, sl, nullptr, nullptr,
+                                           chc);
 #pragma unroll
-                    for (int v = 0; v < M; ++v) o[v] -= r * (F1[v] - F0[v]);
+                        for (int v = 0; v < M; ++v) cw[v] = w[v] + chc[v];
+                        lim_bdot<PDE>(cw, d, sl, Bc);
+#pragma unroll
+                        for (int v = 0; v < M; ++v) {
+                            o[v] -= r * (F1[v] - F0[M + v]);
+                            o[v] -= r * Bc[v];
+                        }
+                    } else {
+#pragma unroll
+                        for (int v = 0; v < M; ++v) o[v] -= r * (F1[v] - F0[v]);
+                    }
+                    if constexpr (PDE::HAS_SRC) {
+                        double chc[M];
+                        lim_half<PDE, DIM>(P.pde, cell(l, i - 1), cell(l, i), cell(l, i + 1), d, r, dt, nullptr,
+                                           nullptr, nullptr, chc);
+#pragma unroll
+                        for (int v = 0; v < M; ++v) ctr[k * M + v] += chc[v];
+                    }
+                }
+                __syncthreads();
+            }
+            if constexpr (PDE::HAS_SRC) {
+                // the source at the half-step centre of all directions
+                for (int a = threadIdx.x; a < L::NSUB; a += blockDim.x) {
+                    double S0[M], S1[M], w[M];
+                    const double *av = sm.avg + a * M;
+                    PDE::source(P.pde, av, S0);
+#pragma unroll
+                    for (int v = 0; v < M; ++v) w[v] = av[v] + ctr[a * M + v] + 0.5 * dt * S0[v];
+                    PDE::source(P.pde, w, S1);
+#pragma unroll
+                    for (int v = 0; v < M; ++v) sm.dq[a * M + v] += dt * S1[v];
                 }
                 __syncthreads();
             }
             for (int i = threadIdx.x; i < L::NSUB * M; i += blockDim.x) sm.dq[i] += sm.avg[i];
             __syncthreads();
             lim_tensor<DIM, M, L::n, S_>(sm.dq, sm.u, sm.ta, sm.tb, sm.Rc);
-            for (int i = threadIdx.x; i < L::NS * M; i += blockDim.x) S.u_out[e * (L::NS * M) + i] = sm.u[i];
+            // the material fields (q_t = 0) are kept as they were
+            for (int i = threadIdx.x; i < L::NS * M; i += blockDim.x)
+                S.u_out[e * (L::NS * M) + i] = (i % M) < PDE::MEV ? sm.u[i] : S.u_prev[e * (L::NS * M) + i];
             __syncthreads();
         }
     }
@@ -502,44 +638,104 @@ __global__ void __launch_bounds__(128) k_lim_couple(const KParams P)
                     lim_layers<L, DIM>(side ? sm.avg : sm.nb, d, 1, gl);
                     lim_layers<L, DIM>(side ? sm.nb : sm.avg, d, 0, gu);
                     __syncthreads();
-                    double *Fl = sm.dq;  // subcell fluxes on the face [line][v]
                     const double r = dt * S.inv_dx[d] * S_;
-                    for (int l = threadIdx.x; l < L::NLINE; l += blockDim.x)
-                        lim_face<PDE, DIM>(P.pde, gl + (size_t)l * M, gl + (size_t)(L::NLINE + l) * M,
-                                           gu + (size_t)l * M, gu + (size_t)(L::NLINE + l) * M, d, r,
-                                           Fl + (size_t)l * M);
-                    __syncthreads();
+                    const long long el = side ? e : nb, eu = side ? nb : e;
                     // per face node: projected subcell flux minus the DG flux
-                    double *dF = sm.dq + (size_t)L::NLINE * M;  // [p][v]
-                    for (int i = threadIdx.x; i < NF * M; i += blockDim.x) {
-                        const int v = i % M, p = i / M;
-                        int pk[3], rem = p;
-#pragma unroll
-                        for (int k = 0; k < DIM - 1; ++k) {
-                            pk[k] = rem % n;
-                            rem /= n;
+                    if constexpr (PDE::NCP) {
+                        // per line: the fluctuation this element receives and
+                        // its own subcell state at the face [line][2M]
+                        double *Fl = sm.dq, *dF = sm.dq + (size_t)L::NLINE * 2 * M;  // dF: [p][v]
+                        for (int l = threadIdx.x; l < L::NLINE; l += blockDim.x) {
+                            double *o = Fl + (size_t)l * 2 * M;
+                            const double *a0 = gl + (size_t)l * M, *a1 = gl + (size_t)(L::NLINE + l) * M;
+                            const double *b0 = gu + (size_t)l * M, *b1 = gu + (size_t)(L::NLINE + l) * M;
+                            if (side)  // this element is the lower one
+                                lim_face_nc<PDE, DIM>(P.pde, a0, a1, b0, b1, d, r, dt, o, nullptr, o + M, nullptr);
+                            else
+                                lim_face_nc<PDE, DIM>(P.pde, a0, a1, b0, b1, d, r, dt, nullptr, o, nullptr, o + M);
                         }
-                        double Ft = 0.0;
-                        for (int l = 0; l < L::NLINE; ++l) {
-                            double wgt = 1.0;
-                            int lr = l;
+                        __syncthreads();
+                        for (int p = threadIdx.x; p < NF; p += blockDim.x) {
+                            int pk[3], rem = p;
 #pragma unroll
                             for (int k = 0; k < DIM - 1; ++k) {
-                                const int j = lr % S_;
-                                lr /= S_;
-                                wgt *= sm.Pr[j * n + pk[k]] / S_ / P.b.w[pk[k]];
+                                pk[k] = rem % n;
+                                rem /= n;
                             }
-                            Ft += wgt * Fl[(size_t)l * M + v];
+                            const double *Lr = tr + (el * NFACE + (d * 2 + 1) * NF + p) * RS;
+                            const double *Rr = tr + (eu * NFACE + (d * 2 + 0) * NF + p) * RS;
+                            const double *qown = side ? Lr : Rr;
+                            double Ft[M], dq[M], J[M];
+#pragma unroll
+                            for (int v = 0; v < M; ++v) Ft[v] = 0.0;
+                            for (int l = 0; l < L::NLINE; ++l) {
+                                double wgt = 1.0;
+                                int lr = l;
+#pragma unroll
+                                for (int k = 0; k < DIM - 1; ++k) {
+                                    const int j = lr % S_;
+                                    lr /= S_;
+                                    wgt *= sm.Pr[j * n + pk[k]] / S_ / P.b.w[pk[k]];
+                                }
+                                // the projected fluctuation plus the path
+                                // integral from this element's DG trace to its
+                                // subcell state at the face
+                                const double *fs = Fl + (size_t)l * 2 * M;
+#pragma unroll
+                                for (int v = 0; v < M; ++v) dq[v] = fs[M + v] - qown[v];
+                                PDE::path_jump(qown, dq, d, J);
+#pragma unroll
+                                for (int v = 0; v < M; ++v) Ft[v] += wgt * (fs[v] + J[v]);
+                            }
+                            // the corrector's path-conservative fluctuation on this face node
+                            const double smax = tmax(Lr[Geom<PDE, DIM, N>::LAM], Rr[Geom<PDE, DIM, N>::LAM]);
+#pragma unroll
+                            for (int v = 0; v < M; ++v) dq[v] = Rr[v] - Lr[v];
+                            PDE::path_jump(Lr, dq, d, J);
+                            const double hs = side ? 0.5 : -0.5;
+#pragma unroll
+                            for (int v = 0; v < M; ++v)
+                                dF[p * M + v] = Ft[v] - (v < PDE::MEV ? hs * J[v] - 0.5 * smax * dq[v] : 0.0);
                         }
-                        // the corrector's Rusanov flux on this face node (lower | upper)
-                        const long long el = side ? e : nb, eu = side ? nb : e;
-                        const double *Lr = tr + (el * NFACE + (d * 2 + 1) * NF + p) * RS;
-                        const double *Rr = tr + (eu * NFACE + (d * 2 + 0) * NF + p) * RS;
-                        const double smax = tmax(Lr[2 * M], Rr[2 * M]);
-                        const double Fdg = 0.5 * (Lr[M + v] + Rr[M + v]) - 0.5 * smax * (Rr[v] - Lr[v]);
-                        dF[i] = Ft - Fdg;
+                        __syncthreads();
+                    } else {
+                        double *Fl = sm.dq;  // subcell fluxes on the face [line][v]
+                        for (int l = threadIdx.x; l < L::NLINE; l += blockDim.x)
+                            lim_face<PDE, DIM>(P.pde, gl + (size_t)l * M, gl + (size_t)(L::NLINE + l) * M,
+                                               gu + (size_t)l * M, gu + (size_t)(L::NLINE + l) * M, d, r, dt,
+                                               Fl + (size_t)l * M);
+                        __syncthreads();
+                        double *dF = sm.dq + (size_t)L::NLINE * M;  // [p][v]
+                        for (int i = threadIdx.x; i < NF * M; i += blockDim.x) {
+                            const int v = i % M, p = i / M;
+                            int pk[3], rem = p;
+#pragma unroll
+                            for (int k = 0; k < DIM - 1; ++k) {
+                                pk[k] = rem % n;
+                                rem /= n;
+                            }
+                            double Ft = 0.0;
+                            for (int l = 0; l < L::NLINE; ++l) {
+                                double wgt = 1.0;
+                                int lr = l;
+#pragma unroll
+                                for (int k = 0; k < DIM - 1; ++k) {
+                                    const int j = lr % S_;
+                                    lr /= S_;
+                                    wgt *= sm.Pr[j * n + pk[k]] / S_ / P.b.w[pk[k]];
+                                }
+                                Ft += wgt * Fl[(size_t)l * M + v];
+                            }
+                            // the corrector's Rusanov flux on this face node (lower | upper)
+                            const double *Lr = tr + (el * NFACE + (d * 2 + 1) * NF + p) * RS;
+                            const double *Rr = tr + (eu * NFACE + (d * 2 + 0) * NF + p) * RS;
+                            const double smax = tmax(Lr[Geom<PDE, DIM, N>::LAM], Rr[Geom<PDE, DIM, N>::LAM]);
+                            const double Fdg = 0.5 * (Lr[M + v] + Rr[M + v]) - 0.5 * smax * (Rr[v] - Lr[v]);
+                            dF[i] = Ft - Fdg;
+                        }
+                        __syncthreads();
                     }
-                    __syncthreads();
+                    const double *dF = sm.dq + (size_t)L::NLINE * M * (PDE::NCP ? 2 : 1);
                     for (int i = threadIdx.x; i < L::NS * M; i += blockDim.x) {
                         const int v = i % M, s = i / M;
                         int sd = 0, p = 0, pw = 1, rem = s;

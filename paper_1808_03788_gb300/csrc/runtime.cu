@@ -402,11 +402,10 @@ int aderdg_create(const aderdg_mesh_t *mesh, int N, int nVar, const aderdg_pde_t
     }
     h->limiter = cfg && cfg->limiter;
     if (h->limiter) {
-        const char *why = prec != ADERDG_FP64                                       ? "the subcell limiter runs on the FP64 path"
-                          : !ks->lim_fv                                               ? "no subcell limiter for this (pde, dim, N)"
-                          : h->guess == ADERDG_GUESS_EXTRAP                           ? "the subcell limiter needs a fresh predictor per step (no EXTRAP guess)"
-                          : (pde->kind == ADERDG_PDE_ADVECTION && pde->p[3] != 0.0) ? "the subcell limiter covers systems without a source"
-                                                                                      : nullptr;
+        const char *why = prec != ADERDG_FP64             ? "the subcell limiter runs on the FP64 path"
+                          : !ks->lim_fv                     ? "no subcell limiter for this (pde, dim, N): its shared memory does not fit"
+                          : h->guess == ADERDG_GUESS_EXTRAP ? "the subcell limiter needs a fresh predictor per step (no EXTRAP guess)"
+                                                            : nullptr;
         if (why) {
             delete h;
             return fail(ADERDG_E_UNSUPPORTED, why);
