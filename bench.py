@@ -356,23 +356,36 @@ def _guess_variants(A, torch, w, stream, flush, steps, warmup, shapes, l2_steps,
 def _limiter(A, torch, w, stream, flush, steps, warmup):
     """The a posteriori subcell limiter (Sec. 2.3) on the headline mesh, FP64:
     the vortex (smooth: detection only) and a blast (rho, p = 1 inside
-    r = 2, 0.125 / 0.1 outside, tanh edge of width 0.3, centred in the box),
-    each timed like the headline, with the troubled elements of the last step."""
+    r = 2, 0.125 / 0.1 outside, tanh edge of width 0.3, centred in the box);
+    and the path-conservative subcell scheme (eq. pde.nc.fv) on the
+    diffuse-interface system: a soft inclusion (alpha 1 -> 0.3 across r = 2.5,
+    tanh width 0.3, lambda = 2, mu = rho = 1) hit by two mirrored velocity
+    boxes, limited and unlimited.  Each is timed like the headline, with the
+    troubled elements of the last step."""
     import numpy as np
 
     from paper_1808_03788_gb300 import inputs
     out = {"precision": "fp64"}
-    for name in ("vortex", "blast"):
-        s = A.Solver(w["pde"], w["dim"], w["cells"], w["lo"], w["hi"], w["N"], w["params"], stream=stream.cuda_stream,
-                     limiter=True)
+    for name in ("vortex", "blast", "inclusion", "inclusion_unlimited"):
+        dim_pde = name.startswith("inclusion")
+        pde, params = (A.ADERDG_PDE_DIFFUSE_ELASTICITY, ()) if dim_pde else (w["pde"], w["params"])
+        lim = name != "inclusion_unlimited"
+        s = A.Solver(pde, w["dim"], w["cells"], w["lo"], w["hi"], w["N"], params, stream=stream.cuda_stream,
+                     limiter=lim)
         X = s.node_coords(w["lo"], w["hi"])
+        x, y = X[..., 0], X[..., 1]
         if name == "vortex":
             U0 = inputs.euler_vortex(X, lo=w["lo"], hi=w["hi"])
-        else:
-            r = np.sqrt((X[..., 0] - 5.0) ** 2 + (X[..., 1] - 5.0) ** 2)
+        elif name == "blast":
+            r = np.sqrt((x - 5.0) ** 2 + (y - 5.0) ** 2)
             rho = inputs.smooth_step(r, 2.0, 0.3, 1.0, 0.125)
             p = inputs.smooth_step(r, 2.0, 0.3, 1.0, 0.1)
             U0 = np.stack([rho, 0 * rho, 0 * rho, p / 0.4], axis=-1)
+        else:
+            alpha = inputs.smooth_step(np.sqrt((x - 5.0) ** 2 + (y - 5.0) ** 2), 2.5, 0.3, 0.3, 1.0)
+            box = lambda a, b: np.where((a > 1.0) & (a < 3.0) & (b > 3.0) & (b < 6.0), 1.0, 0.0)
+            z = 0 * x
+            U0 = inputs.diffuse_pack(2, [z, z, z], [alpha * box(x, y), alpha * box(y, x)], alpha, 2.0, 1.0, 1.0)
         s.set_state(np.ascontiguousarray(U0))
         with torch.cuda.stream(stream):
             for _ in range(warmup):
@@ -387,7 +400,7 @@ def _limiter(A, torch, w, stream, flush, steps, warmup):
                 b.record(stream)
             torch.cuda.synchronize()
         ms = [a.elapsed_time(b) for a, b in ev]
-        flags, cnt = s.troubled()
+        cnt = s.troubled()[1] if lim else 0
         info = s.info()
         s.close()
         out[name] = {"value": info["dofs"] * steps / (sum(ms) / 1e3), "ms_per_step": sum(ms) / steps,

@@ -655,38 +655,47 @@ __global__ void __launch_bounds__(128) k_lim_couple(const KParams P)
                                 lim_face_nc<PDE, DIM>(P.pde, a0, a1, b0, b1, d, r, dt, nullptr, o, nullptr, o + M);
                         }
                         __syncthreads();
-                        for (int p = threadIdx.x; p < NF; p += blockDim.x) {
+                        // per (face node, line): the projected fluctuation plus
+                        // the path integral from this element's DG trace to its
+                        // subcell state at the face, into sm.fb [p][line][v]
+                        static_assert((size_t)NF * L::NLINE * M <= (size_t)L::FACES, "coupling terms exceed sm.fb");
+                        double *Cp = sm.fb;
+                        for (int it = threadIdx.x; it < NF * L::NLINE; it += blockDim.x) {
+                            const int l = it % L::NLINE, p = it / L::NLINE;
                             int pk[3], rem = p;
 #pragma unroll
                             for (int k = 0; k < DIM - 1; ++k) {
                                 pk[k] = rem % n;
                                 rem /= n;
                             }
+                            double wgt = 1.0;
+                            int lr = l;
+#pragma unroll
+                            for (int k = 0; k < DIM - 1; ++k) {
+                                const int j = lr % S_;
+                                lr /= S_;
+                                wgt *= sm.Pr[j * n + pk[k]] / S_ / P.b.w[pk[k]];
+                            }
+                            const double *qown = side ? tr + (el * NFACE + (d * 2 + 1) * NF + p) * RS
+                                                      : tr + (eu * NFACE + (d * 2 + 0) * NF + p) * RS;
+                            const double *fs = Fl + (size_t)l * 2 * M;
+                            double dq[M], J[M];
+#pragma unroll
+                            for (int v = 0; v < M; ++v) dq[v] = fs[M + v] - qown[v];
+                            PDE::path_jump(qown, dq, d, J);
+#pragma unroll
+                            for (int v = 0; v < M; ++v) Cp[(size_t)it * M + v] = wgt * (fs[v] + J[v]);
+                        }
+                        __syncthreads();
+                        for (int p = threadIdx.x; p < NF; p += blockDim.x) {
                             const double *Lr = tr + (el * NFACE + (d * 2 + 1) * NF + p) * RS;
                             const double *Rr = tr + (eu * NFACE + (d * 2 + 0) * NF + p) * RS;
-                            const double *qown = side ? Lr : Rr;
                             double Ft[M], dq[M], J[M];
 #pragma unroll
                             for (int v = 0; v < M; ++v) Ft[v] = 0.0;
-                            for (int l = 0; l < L::NLINE; ++l) {
-                                double wgt = 1.0;
-                                int lr = l;
+                            for (int l = 0; l < L::NLINE; ++l)
 #pragma unroll
-                                for (int k = 0; k < DIM - 1; ++k) {
-                                    const int j = lr % S_;
-                                    lr /= S_;
-                                    wgt *= sm.Pr[j * n + pk[k]] / S_ / P.b.w[pk[k]];
-                                }
-                                // the projected fluctuation plus the path
-                                // integral from this element's DG trace to its
-                                // subcell state at the face
-                                const double *fs = Fl + (size_t)l * 2 * M;
-#pragma unroll
-                                for (int v = 0; v < M; ++v) dq[v] = fs[M + v] - qown[v];
-                                PDE::path_jump(qown, dq, d, J);
-#pragma unroll
-                                for (int v = 0; v < M; ++v) Ft[v] += wgt * (fs[v] + J[v]);
-                            }
+                                for (int v = 0; v < M; ++v) Ft[v] += Cp[((size_t)p * L::NLINE + l) * M + v];
                             // the corrector's path-conservative fluctuation on this face node
                             const double smax = tmax(Lr[Geom<PDE, DIM, N>::LAM], Rr[Geom<PDE, DIM, N>::LAM]);
 #pragma unroll
