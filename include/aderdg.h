@@ -315,7 +315,8 @@ typedef struct {
 
 /* Create a batch of `count` solves (state zero, t = 0).  cfg applies to all
  * of them (precision, initial guess, Picard count: 0 -> the default rule per
- * solve's N, CFL alpha: 0 -> default per N, stream, allocator, tile shapes). */
+ * solve's N, CFL alpha: 0 -> default per N, stream, allocator, tile shapes,
+ * the subcell limiter). */
 int aderdg_batch_create(const aderdg_solve_spec_t *specs, int count, const aderdg_config_t *cfg,
                         aderdg_batch_t **out);
 int aderdg_batch_destroy(aderdg_batch_t *b);
@@ -336,6 +337,12 @@ int aderdg_batch_advance(aderdg_batch_t *b, const double *t_end, int64_t max_ste
 
 /* Totals: DOFs (sum over solves of E (N+1)^d), device bytes, groups. */
 int aderdg_batch_info(const aderdg_batch_t *b, int64_t *dofs, size_t *device_bytes, int *groups);
+
+/* Troubled elements of solve i in the last limited step (a batch created
+ * with cfg->limiter: every solve runs the subcell limiter; the rules of the
+ * single-solve handle apply).  flags: E host ints or NULL, *count or NULL.
+ * ADERDG_E_INVAL for a batch without the limiter.  Synchronising. */
+int aderdg_batch_troubled(aderdg_batch_t *b, int i, int *flags, int64_t *count);
 
 /* Per-solve status after a synchronising call: 0 running, 1 done (t >=
  * t_end), ADERDG_E_NONFINITE.  status: `count` ints (host). */

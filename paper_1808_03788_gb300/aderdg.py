@@ -137,6 +137,7 @@ _SIGS = {
     "aderdg_batch_advance": (C.c_int, [_H, _DP, C.c_int64]),
     "aderdg_batch_info": (C.c_int, [_H, C.POINTER(C.c_int64), C.POINTER(C.c_size_t), C.POINTER(C.c_int)]),
     "aderdg_batch_status": (C.c_int, [_H, C.POINTER(C.c_int)]),
+    "aderdg_batch_troubled": (C.c_int, [_H, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int64)]),
     "aderdg_server_create": (C.c_int, [C.POINTER(aderdg_server_config_t), C.POINTER(_H)]),
     "aderdg_server_destroy": (C.c_int, [_H]),
     "aderdg_submit": (C.c_int, [_H, C.POINTER(aderdg_request_t), C.POINTER(C.c_uint64)]),
@@ -536,7 +537,7 @@ class Batch:
 
     def __init__(self, specs, precision: int = ADERDG_FP64, picard: int = 0, alpha: float = 0.0,
                  stream=None, torch_alloc: bool = True, shapes=(0, 0), tune_cache=None,
-                 guess: int = ADERDG_GUESS_TRIVIAL):
+                 guess: int = ADERDG_GUESS_TRIVIAL, limiter: bool = False):
         L = load()
         self._L = L
         self.specs = list(specs)
@@ -546,6 +547,7 @@ class Batch:
         cfg.picard_iters = picard
         cfg.cfl_alpha = alpha
         cfg.initial_guess = guess
+        cfg.limiter = 1 if limiter else 0
         _set_shapes(cfg, shapes, tune_cache)
         if stream is not None:
             cfg.cuda_stream = C.c_void_p(int(stream))
@@ -604,6 +606,17 @@ class Batch:
         st = (C.c_int * len(self))()
         _check(self._L.aderdg_batch_status(self._h, st))
         return list(st)
+
+    def troubled(self, i: int):
+        """(flags[E], count) of solve i's last limited step."""
+        E = 1
+        m = self.specs[i].mesh
+        for d in range(m.dim):
+            E *= m.cells[d]
+        flags = np.zeros(E, dtype=np.int32)
+        cnt = C.c_int64(0)
+        _check(self._L.aderdg_batch_troubled(self._h, i, flags.ctypes.data_as(C.POINTER(C.c_int)), C.byref(cnt)))
+        return flags, cnt.value
 
     def info(self):
         d, b, g = C.c_int64(0), C.c_size_t(0), C.c_int(0)

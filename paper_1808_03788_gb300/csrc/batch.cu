@@ -102,19 +102,31 @@ struct Slot {
     void *V = nullptr, *tr = nullptr;
     double *ref = nullptr;
     void *qprev = nullptr;     // extrapolation guess: last predictor
+    // subcell limiter (FP64): u^n, extremes of u^n and of the candidate, flags
+    bool limiter = false;
+    double *u_prev = nullptr, *lim_mm = nullptr, *lim_mmc = nullptr;
+    int *lim_flags = nullptr;
     int ctl_index = -1;
     // placement in the current group arrays (for k_cfl)
     int group = -1, member = -1;
 };
 
+size_t lim_bytes(const Slot &s)
+{
+    const size_t ns = (size_t)s.E * s.NS * s.M;
+    return s.limiter ? a256(ns * 8) + 2 * a256((size_t)s.E * s.M * 2 * 8) + a256((size_t)s.E * 4) : 0;
+}
+
 size_t slot_bytes(const Slot &s)
 {
     const size_t ns = (size_t)s.E * s.NS * s.M;
     return a256(ns * 8) + a256(ns * s.ks->elem_bytes) + a256((size_t)s.E * s.NREC * s.ks->rs * s.ks->elem_bytes) +
-           a256((size_t)s.E * s.ks->rf * 8) + (s.guess == ADERDG_GUESS_EXTRAP ? a256(ns * (s.N + 1) * s.ks->elem_bytes) : 0);
+           a256((size_t)s.E * s.ks->rf * 8) + (s.guess == ADERDG_GUESS_EXTRAP ? a256(ns * (s.N + 1) * s.ks->elem_bytes) : 0) +
+           lim_bytes(s);
 }
 
-int make_slot(const aderdg_solve_spec_t &sp, int prec, int guess, int picard, double alpha, Slot &s)
+int make_slot(const aderdg_solve_spec_t &sp, int prec, int guess, int picard, double alpha, Slot &s,
+              bool limiter = false)
 {
     const aderdg_mesh_t &m = sp.mesh;
     if (m.dim < 2 || m.dim > 3) return fail(ADERDG_E_INVAL, "dim must be 2 or 3");
@@ -125,7 +137,23 @@ int make_slot(const aderdg_solve_spec_t &sp, int prec, int guess, int picard, do
     if (sp.pde.kind == ADERDG_PDE_EULER && !(sp.pde.p[0] > 1.0)) return fail(ADERDG_E_INVAL, "gamma must be > 1");
     if (sp.pde.kind == ADERDG_PDE_ADVECTION && !(sp.pde.p[3] >= 0.0)) return fail(ADERDG_E_INVAL, "kappa must be >= 0");
     if (guess < ADERDG_GUESS_TRIVIAL || guess > ADERDG_GUESS_CERK) return fail(ADERDG_E_INVAL, "bad initial guess");
+    if (limiter) {
+        if (prec != ADERDG_FP64) return fail(ADERDG_E_UNSUPPORTED, "the subcell limiter runs on the FP64 path");
+        if (!ks->lim_fv)
+            return fail(ADERDG_E_UNSUPPORTED, "no subcell limiter for this (pde, dim, N): its shared memory does not fit");
+        if (guess == ADERDG_GUESS_EXTRAP)
+            return fail(ADERDG_E_UNSUPPORTED, "the subcell limiter needs a fresh predictor per step (no EXTRAP guess)");
+        const std::pair<void (*)(KParams), size_t> lk[4] = {
+            {ks->lim_minmax, ks->lim_smem_w}, {ks->lim_detect, ks->lim_smem_w}, {ks->lim_fv, ks->lim_smem},
+            {ks->lim_couple, ks->lim_smem}};
+        for (const auto &k : lk)
+            if (k.second > 48 * 1024 && cudaFuncSetAttribute((const void *)k.first,
+                                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                             (int)k.second) != cudaSuccess)
+                return fail(ADERDG_E_CUDA, "shared memory opt-in of the limiter failed");
+    }
     s = Slot();
+    s.limiter = limiter;
     s.pde = sp.pde.kind;
     s.dim = m.dim;
     s.N = sp.N;
@@ -160,6 +188,8 @@ __global__ void k_dt_batch(Control *const *ctls, int count)
     if (i < count) dt_update(ctls[i]);
 }
 
+__global__ void k_lim_reset_one(Control *c) { lim_reset(c); }
+
 __global__ void k_set_tend(Control *const *ctls, const double *t_end, int count)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -169,6 +199,8 @@ __global__ void k_set_tend(Control *const *ctls, const double *t_end, int count)
 struct Group {
     int pde = 0, dim = 0, N = 0, prec = 0;
     bool extrap = false;  // its solves use the extrapolation or CERK guess (predictor variant)
+    bool limiter = false;  // its solves run the subcell limiter
+    long long elems = 0;   // elements of all its solves
     PdeParams pp{};
     const KernelSet *ks = nullptr;  // compiled kernels of the group
     KernelSet kso{};                // the same with the tile shapes in use
@@ -184,7 +216,7 @@ struct Group {
 bool same_group(const Group &g, const Slot &s)
 {
     return g.ks == s.ks && g.pde == s.pde && g.dim == s.dim && g.N == s.N && g.prec == s.prec &&
-           g.extrap == (s.guess == ADERDG_GUESS_EXTRAP || s.guess == ADERDG_GUESS_CERK) &&
+           g.extrap == (s.guess == ADERDG_GUESS_EXTRAP || s.guess == ADERDG_GUESS_CERK) && g.limiter == s.limiter &&
            std::memcmp(&g.pp, &s.pp, sizeof(PdeParams)) == 0;
 }
 
@@ -258,6 +290,14 @@ public:
                              a256((size_t)s->E * s->NREC * s->ks->rs * s->ks->elem_bytes);
         s->ref = s->ks->rf > 0 ? reinterpret_cast<double *>(b + o_ref) : nullptr;
         s->qprev = s->guess == ADERDG_GUESS_EXTRAP ? b + o_ref + a256((size_t)s->E * s->ks->rf * 8) : nullptr;
+        if (s->limiter) {
+            unsigned char *l = b + s->bytes - lim_bytes(*s);
+            s->u_prev = reinterpret_cast<double *>(l);
+            s->lim_mm = reinterpret_cast<double *>(l + a256(ns * 8));
+            s->lim_mmc = reinterpret_cast<double *>(l + a256(ns * 8) + a256((size_t)s->E * s->M * 2 * 8));
+            s->lim_flags = reinterpret_cast<int *>(l + a256(ns * 8) + 2 * a256((size_t)s->E * s->M * 2 * 8));
+            CKB(cudaMemsetAsync(s->lim_flags, 0, sizeof(int) * (size_t)s->E, st));
+        }
         s->ctl_index = ctl_free.back();
         ctl_free.pop_back();
         Control c;
@@ -298,12 +338,14 @@ public:
                 Group g;
                 g.pde = s->pde; g.dim = s->dim; g.N = s->N; g.prec = s->prec; g.pp = s->pp; g.ks = s->ks;
                 g.extrap = s->guess == ADERDG_GUESS_EXTRAP || s->guess == ADERDG_GUESS_CERK;
+                g.limiter = s->limiter;
                 ng.push_back(g);
                 gi = (int)ng.size() - 1;
             }
             s->group = gi;
             s->member = (int)ng[gi].members.size();
             ng[gi].members.push_back(s);
+            ng[gi].elems += s->E;
         }
         // tile shapes per group (may autotune on first use of a key)
         for (Group &g : ng) {
@@ -338,6 +380,10 @@ public:
                 d.tr = s->tr;
                 d.ref = s->ref;
                 d.ctl = ctl_of(s);
+                d.u_prev = s->u_prev;
+                d.lim_mm = s->lim_mm;
+                d.lim_mmc = s->lim_mmc;
+                d.lim_flags = s->lim_flags;
             }
             g.ntp = tp;
             g.ntc = tc;
@@ -416,10 +462,31 @@ public:
         CKB(cudaGetLastError());
         for (Group &g : groups) {
             KParams kp = g.kp;
+            if (g.limiter)  // u^n for the limiter, before the corrector overwrites it
+                for (const Slot *m : g.members)
+                    CKB(cudaMemcpyAsync(m->u_prev, m->u, (size_t)m->E * m->NS * m->M * sizeof(double),
+                                        cudaMemcpyDeviceToDevice, st));
             kp.ntiles = g.ntp;
             g.kso.predictor<<<(unsigned)g.ntp, g.kso.pred_threads, g.kso.pred_smem, st>>>(kp);
             kp.ntiles = g.ntc;
             g.kso.corrector<<<(unsigned)g.ntc, g.kso.corr_threads, g.kso.corr_smem, st>>>(kp);
+            if (g.limiter) {
+                // one launch of each limiter kernel for all solves of the group
+                const KernelSet *ks = g.ks;
+                const unsigned grid = (unsigned)std::min<long long>(g.elems, 152LL * 16);
+                ks->lim_minmax<<<grid, 128, ks->lim_smem_w, st>>>(kp);
+                ks->lim_detect<<<grid, 128, ks->lim_smem_w, st>>>(kp);
+                ks->lim_fv<<<grid, 128, ks->lim_smem, st>>>(kp);
+                ks->lim_couple<<<grid, 128, ks->lim_smem, st>>>(kp);
+                for (const Slot *m : g.members) {
+                    k_lim_reset_one<<<1, 32, 0, st>>>(ctl_of(m));
+                    KParams k1 = g.kp;
+                    k1.solves = g.d_desc + m->member;
+                    k1.nsolves = 1;
+                    k1.use_ctl_dt = 1;
+                    ks->cfl<<<(unsigned)std::min<long long>(4 * 152, (m->E * m->NS + 255) / 256), 256, 0, st>>>(k1);
+                }
+            }
         }
         CKB(cudaGetLastError());
         return ADERDG_OK;
@@ -495,7 +562,7 @@ int aderdg_batch_create(const aderdg_solve_spec_t *specs, int count, const aderd
     std::vector<Slot> tmp(count);
     for (int i = 0; i < count; ++i) {
         int rc = make_slot(specs[i], prec, cfg ? cfg->initial_guess : 0, cfg ? cfg->picard_iters : 0,
-                           cfg ? cfg->cfl_alpha : 0.0, tmp[i]);
+                           cfg ? cfg->cfl_alpha : 0.0, tmp[i], cfg && cfg->limiter);
         if (rc) return rc;
     }
     int ndev = 0;
@@ -622,6 +689,21 @@ int aderdg_batch_info(const aderdg_batch_t *b, int64_t *dofs, size_t *device_byt
     if (dofs) *dofs = b->dofs;
     if (device_bytes) *device_bytes = b->eng.mem.in_use;
     if (groups) *groups = (int)b->eng.groups.size();
+    return ADERDG_OK;
+}
+
+int aderdg_batch_troubled(aderdg_batch_t *b, int i, int *flags, int64_t *count)
+{
+    if (!b || i < 0 || i >= (int)b->slots.size()) return fail(ADERDG_E_INVAL, "bad batch index");
+    const Slot *s = b->slots[i];
+    if (!s->limiter) return fail(ADERDG_E_INVAL, "the batch has no limiter");
+    std::vector<int> f((size_t)s->E);
+    CKB(cudaMemcpyAsync(f.data(), s->lim_flags, sizeof(int) * (size_t)s->E, cudaMemcpyDeviceToHost, b->eng.st));
+    CKB(cudaStreamSynchronize(b->eng.st));
+    int64_t c = 0;
+    for (long long e = 0; e < s->E; ++e) c += f[(size_t)e] != 0;
+    if (flags) std::memcpy(flags, f.data(), sizeof(int) * (size_t)s->E);
+    if (count) *count = c;
     return ADERDG_OK;
 }
 

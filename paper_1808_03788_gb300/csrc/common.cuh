@@ -49,6 +49,21 @@ struct Control {
     unsigned int lim_fresh;  // subcell limiter: lim_mmc holds the candidate extremes of the state's last step
 };
 
+// After the subcell limiter: the step's wave-speed maxima and non-finite
+// flag are cleared before they are taken again from the limited state, and
+// the candidate extremes the detection kept become those of the new state
+// (for the elements the limiter left untouched).
+#ifdef __CUDACC__
+__device__ __forceinline__ void lim_reset(Control *c)
+{
+    if (threadIdx.x < 3) c->lam_acc[threadIdx.x] = 0ull;
+    if (threadIdx.x == 0) {
+        c->flags &= ~FLAG_NONFINITE;
+        c->lim_fresh = 1u;
+    }
+}
+#endif
+
 // PDE parameters as given (aderdg_pde_t) and constants derived from them
 // on the host (fill_pde_consts), in double and rounded to float, so that
 // the kernels do no per-call parameter arithmetic or double->float

@@ -19,7 +19,9 @@
 // Both sides of a face between a troubled and an unlimited element, and of
 // a face between two troubled ones, evaluate its subcell fluxes with the
 // same function on the same subcell averages, so the scheme stays
-// conservative.  Each CTA owns one element at a time (grid-stride loop).
+// conservative.  Each CTA owns one element at a time (grid-stride loop);
+// a launch covers every solve of its descriptor list that has the limiter
+// (u_prev set), one after the other.
 // Included by kernels.cuh inside namespace aderdg.
 #pragma once
 
@@ -399,26 +401,30 @@ __global__ void __launch_bounds__(128) k_lim_minmax(const KParams P)
         if (warp >= W::WARPS) return;
         double *u = Pr + round_up(2 * L::S * L::n, 2) + warp * W::DOUBLES;
         double *avg = u + round_up(L::NS * L::M, 2), *ta = avg + (size_t)L::NSUB * L::M, *tb = ta + L::TMP;
-        const SolveDesc &S = P.solves[0];
-        const bool fresh = S.ctl->lim_fresh != 0;
-        for (long long e = (long long)blockIdx.x * W::WARPS + warp; e < S.E; e += (long long)gridDim.x * W::WARPS) {
-            bool reuse = fresh;
-            if (reuse) {
-                int touched = S.lim_flags[e];
+        for (int si = 0; si < P.nsolves; ++si) {
+            const SolveDesc &S = P.solves[si];
+            if (!S.u_prev) continue;  // a solve without the limiter
+            const bool fresh = S.ctl->lim_fresh != 0;
+            for (long long e = (long long)blockIdx.x * W::WARPS + warp; e < S.E; e += (long long)gridDim.x * W::WARPS) {
+                bool reuse = fresh;
+                if (reuse) {
+                    int touched = S.lim_flags[e];
 #pragma unroll
-                for (int d = 0; d < DIM; ++d)
+                    for (int d = 0; d < DIM; ++d)
 #pragma unroll
-                    for (int side = 0; side < 2; ++side)
-                        touched |= S.lim_flags[neighbour((int)e, S.cells[0], S.cells[1], S.cells[2], d, side ? 1 : -1)];
-                reuse = !touched;
+                        for (int side = 0; side < 2; ++side)
+                            touched |=
+                                S.lim_flags[neighbour((int)e, S.cells[0], S.cells[1], S.cells[2], d, side ? 1 : -1)];
+                    reuse = !touched;
+                }
+                if (reuse) {  // uniform over the warp
+                    if (lane < 2 * L::M) S.lim_mm[e * (2 * L::M) + lane] = S.lim_mmc[e * (2 * L::M) + lane];
+                    continue;
+                }
+                lim_averages_warp<L, DIM>(S.u_prev, e, Pr, u, avg, ta, tb, lane);
+                lim_extremes_warp<L>(avg, lane, S.lim_mm + e * (2 * L::M));
+                __syncwarp();
             }
-            if (reuse) {  // uniform over the warp
-                if (lane < 2 * L::M) S.lim_mm[e * (2 * L::M) + lane] = S.lim_mmc[e * (2 * L::M) + lane];
-                continue;
-            }
-            lim_averages_warp<L, DIM>(S.u_prev, e, Pr, u, avg, ta, tb, lane);
-            lim_extremes_warp<L>(avg, lane, S.lim_mm + e * (2 * L::M));
-            __syncwarp();
         }
     }
 }
@@ -437,52 +443,57 @@ __global__ void __launch_bounds__(128) k_lim_detect(const KParams P)
         if (warp >= W::WARPS) return;
         double *u = Pr + round_up(2 * L::S * L::n, 2) + warp * W::DOUBLES;
         double *avg = u + round_up(L::NS * L::M, 2), *ta = avg + (size_t)L::NSUB * L::M, *tb = ta + L::TMP;
-        const SolveDesc &S = P.solves[0];
-        for (long long e = (long long)blockIdx.x * W::WARPS + warp; e < S.E; e += (long long)gridDim.x * W::WARPS) {
-            const double *uc = S.u_out + e * (L::NS * L::M);  // the candidate
-            int bad = 0;
-            for (int s = lane; s < L::NS; s += 32) {
-                double q[L::M];
-                bool fin = true;
+        for (int si = 0; si < P.nsolves; ++si) {
+            const SolveDesc &S = P.solves[si];
+            if (!S.u_prev) continue;
+            for (long long e = (long long)blockIdx.x * W::WARPS + warp; e < S.E; e += (long long)gridDim.x * W::WARPS) {
+                const double *uc = S.u_out + e * (L::NS * L::M);  // the candidate
+                int bad = 0;
+                for (int s = lane; s < L::NS; s += 32) {
+                    double q[L::M];
+                    bool fin = true;
 #pragma unroll
-                for (int v = 0; v < L::M; ++v) {
-                    q[v] = uc[s * L::M + v];
-                    fin = fin && !dbl_nonfinite(q[v]);
-                }
-                bad |= !fin || !lim_admissible<PDE>(P.pde, q);
-            }
-            bad = __any_sync(0xffffffffu, bad);
-            if (!bad) {
-                lim_averages_warp<L, DIM>(S.u_out, e, Pr, u, avg, ta, tb, lane);
-                // the candidate's extremes, the next step's u^n extremes if
-                // this element stays untouched
-                lim_extremes_warp<L>(avg, lane, S.lim_mmc + e * (2 * L::M));
-                for (int a = lane; a < L::NSUB; a += 32) bad |= !lim_admissible<PDE>(P.pde, avg + a * L::M);
-                for (int v = 0; v < L::M; ++v) {
-                    // the relaxed maximum principle of u^n over the element and its face neighbours
-                    long long klo = lim_key(S.lim_mm[(e * L::M + v) * 2]), khi = lim_key(S.lim_mm[(e * L::M + v) * 2 + 1]);
-#pragma unroll
-                    for (int d = 0; d < DIM; ++d)
-#pragma unroll
-                        for (int side = 0; side < 2; ++side) {
-                            const long long nb = neighbour((int)e, S.cells[0], S.cells[1], S.cells[2], d, side ? 1 : -1);
-                            const long long kl = lim_key(S.lim_mm[(nb * L::M + v) * 2]);
-                            const long long kh = lim_key(S.lim_mm[(nb * L::M + v) * 2 + 1]);
-                            klo = kl < klo ? kl : klo;
-                            khi = kh > khi ? kh : khi;
-                        }
-                    const double lo = lim_unkey(klo), hi = lim_unkey(khi);
-                    const double delta = fmax(1e-4, 1e-3 * (hi - lo));
-                    const long long blo = lim_key(lo - delta), bhi = lim_key(hi + delta);
-                    for (int a = lane; a < L::NSUB; a += 32) {
-                        const long long k = lim_key(avg[a * L::M + v]);
-                        bad |= k < blo || k > bhi;
+                    for (int v = 0; v < L::M; ++v) {
+                        q[v] = uc[s * L::M + v];
+                        fin = fin && !dbl_nonfinite(q[v]);
                     }
+                    bad |= !fin || !lim_admissible<PDE>(P.pde, q);
                 }
                 bad = __any_sync(0xffffffffu, bad);
+                if (!bad) {
+                    lim_averages_warp<L, DIM>(S.u_out, e, Pr, u, avg, ta, tb, lane);
+                    // the candidate's extremes, the next step's u^n extremes if
+                    // this element stays untouched
+                    lim_extremes_warp<L>(avg, lane, S.lim_mmc + e * (2 * L::M));
+                    for (int a = lane; a < L::NSUB; a += 32) bad |= !lim_admissible<PDE>(P.pde, avg + a * L::M);
+                    for (int v = 0; v < L::M; ++v) {
+                        // the relaxed maximum principle of u^n over the element and its face neighbours
+                        long long klo = lim_key(S.lim_mm[(e * L::M + v) * 2]);
+                        long long khi = lim_key(S.lim_mm[(e * L::M + v) * 2 + 1]);
+#pragma unroll
+                        for (int d = 0; d < DIM; ++d)
+#pragma unroll
+                            for (int side = 0; side < 2; ++side) {
+                                const long long nb =
+                                    neighbour((int)e, S.cells[0], S.cells[1], S.cells[2], d, side ? 1 : -1);
+                                const long long kl = lim_key(S.lim_mm[(nb * L::M + v) * 2]);
+                                const long long kh = lim_key(S.lim_mm[(nb * L::M + v) * 2 + 1]);
+                                klo = kl < klo ? kl : klo;
+                                khi = kh > khi ? kh : khi;
+                            }
+                        const double lo = lim_unkey(klo), hi = lim_unkey(khi);
+                        const double delta = fmax(1e-4, 1e-3 * (hi - lo));
+                        const long long blo = lim_key(lo - delta), bhi = lim_key(hi + delta);
+                        for (int a = lane; a < L::NSUB; a += 32) {
+                            const long long k = lim_key(avg[a * L::M + v]);
+                            bad |= k < blo || k > bhi;
+                        }
+                    }
+                    bad = __any_sync(0xffffffffu, bad);
+                }
+                if (lane == 0) S.lim_flags[e] = bad;
+                __syncwarp();
             }
-            if (lane == 0) S.lim_flags[e] = bad;
-            __syncwarp();
         }
     }
 }
@@ -496,107 +507,111 @@ __global__ void __launch_bounds__(128) k_lim_fv(const KParams P)
         extern __shared__ __align__(16) unsigned char smem_raw[];
         LimSmem<L> sm(reinterpret_cast<double *>(smem_raw));
         lim_load_ops<L>(P, sm);
-        const SolveDesc &S = P.solves[0];
-        const double dt = solve_dt(P, S);
-        if (!(dt > 0.0)) return;
-        for (long long e = blockIdx.x; e < S.E; e += gridDim.x) {
-            if (!S.lim_flags[e]) continue;  // uniform over the CTA
-            lim_averages<L, DIM>(S.u_prev, e, sm, sm.avg);
+        for (int si = 0; si < P.nsolves; ++si) {
+            const SolveDesc &S = P.solves[si];
+            if (!S.u_prev) continue;
+            const double dt = solve_dt(P, S);
+            if (!(dt > 0.0)) continue;
+            for (long long e = blockIdx.x; e < S.E; e += gridDim.x) {
+                if (!S.lim_flags[e]) continue;  // uniform over the CTA
+                lim_averages<L, DIM>(S.u_prev, e, sm, sm.avg);
 #pragma unroll 1
-            for (int d = 0; d < DIM; ++d)
+                for (int d = 0; d < DIM; ++d)
 #pragma unroll 1
-                for (int side = 0; side < 2; ++side) {
-                    const long long nb = neighbour((int)e, S.cells[0], S.cells[1], S.cells[2], d, side ? 1 : -1);
-                    lim_averages<L, DIM>(S.u_prev, nb, sm, sm.nb);
-                    // ghost cells -2, -1 from the lower neighbour's last
-                    // layers; S, S+1 from the upper neighbour's first ones
-                    lim_layers<L, DIM>(sm.nb, d, side ? 0 : 1, sm.ghost + (size_t)(d * 2 + side) * 2 * L::NLINE * M);
+                    for (int side = 0; side < 2; ++side) {
+                        const long long nb = neighbour((int)e, S.cells[0], S.cells[1], S.cells[2], d, side ? 1 : -1);
+                        lim_averages<L, DIM>(S.u_prev, nb, sm, sm.nb);
+                        // ghost cells -2, -1 from the lower neighbour's last
+                        // layers; S, S+1 from the upper neighbour's first ones
+                        lim_layers<L, DIM>(sm.nb, d, side ? 0 : 1,
+                                           sm.ghost + (size_t)(d * 2 + side) * 2 * L::NLINE * M);
+                        __syncthreads();
+                    }
+                // sm.nb is free from here on: the source's sum over directions of
+                // the half-step changes
+                double *ctr = sm.nb;
+                for (int i = threadIdx.x; i < L::NSUB * M; i += blockDim.x) sm.dq[i] = ctr[i] = 0.0;
+                __syncthreads();
+#pragma unroll 1
+                for (int d = 0; d < DIM; ++d) {
+                    const double r = dt * S.inv_dx[d] * S_;  // dt / subcell width
+                    // cell i of line l along d: ghost layers below 0 and from S on
+                    auto cell = [&](int l, int i) -> const double * {
+                        if (i < 0) return sm.ghost + ((size_t)((d * 2 + 0) * 2 + (i + 2)) * L::NLINE + l) * M;
+                        if (i >= S_) return sm.ghost + ((size_t)((d * 2 + 1) * 2 + (i - S_)) * L::NLINE + l) * M;
+                        return sm.avg + lim_cell<DIM, S_>(d, l, i) * M;
+                    };
+                    // every face of this direction (face f between cells f-1 and f):
+                    // the flux, or the two fluctuations [lower | upper]
+                    constexpr int FW = PDE::NCP ? 2 * M : M;
+                    for (int it = threadIdx.x; it < (S_ + 1) * L::NLINE; it += blockDim.x) {
+                        const int f = it % (S_ + 1), l = it / (S_ + 1);
+                        double *fo = sm.fb + (size_t)it * FW;
+                        if constexpr (PDE::NCP)
+                            lim_face_nc<PDE, DIM>(P.pde, cell(l, f - 2), cell(l, f - 1), cell(l, f), cell(l, f + 1),
+                                                  d, r, dt, fo, fo + M, nullptr, nullptr);
+                        else
+                            lim_face<PDE, DIM>(P.pde, cell(l, f - 2), cell(l, f - 1), cell(l, f), cell(l, f + 1), d, r,
+                                               dt, fo);
+                    }
+                    __syncthreads();
+                    for (int it = threadIdx.x; it < S_ * L::NLINE; it += blockDim.x) {
+                        const int i = it % S_, l = it / S_;
+                        const double *F0 = sm.fb + (size_t)(l * (S_ + 1) + i) * FW, *F1 = F0 + FW;
+                        const int k = lim_cell<DIM, S_>(d, l, i);
+                        double *o = sm.dq + k * M;
+                        if constexpr (PDE::NCP) {
+                            // F1: the lower cell's fluctuation of face i+1; F0 + M:
+                            // the upper cell's of face i; then the smooth part of
+                            // B(q) grad q inside the subcell at its half-step centre
+                            double sl[M], chc[M], cw[M], Bc[M];
+                            const double *w = cell(l, i);
+                            lim_half<PDE, DIM>(P.pde, cell(l, i - 1), w, cell(l, i + 1), d, r, dt, sl, nullptr, nullptr,
+                                               chc);
+#pragma unroll
+                            for (int v = 0; v < M; ++v) cw[v] = w[v] + chc[v];
+                            lim_bdot<PDE>(cw, d, sl, Bc);
+#pragma unroll
+                            for (int v = 0; v < M; ++v) {
+                                o[v] -= r * (F1[v] - F0[M + v]);
+                                o[v] -= r * Bc[v];
+                            }
+                        } else {
+#pragma unroll
+                            for (int v = 0; v < M; ++v) o[v] -= r * (F1[v] - F0[v]);
+                        }
+                        if constexpr (PDE::HAS_SRC) {
+                            double chc[M];
+                            lim_half<PDE, DIM>(P.pde, cell(l, i - 1), cell(l, i), cell(l, i + 1), d, r, dt, nullptr,
+                                               nullptr, nullptr, chc);
+#pragma unroll
+                            for (int v = 0; v < M; ++v) ctr[k * M + v] += chc[v];
+                        }
+                    }
                     __syncthreads();
                 }
-            // sm.nb is free from here on: the source's sum over directions of
-            // the half-step changes
-            double *ctr = sm.nb;
-            for (int i = threadIdx.x; i < L::NSUB * M; i += blockDim.x) sm.dq[i] = ctr[i] = 0.0;
-            __syncthreads();
-#pragma unroll 1
-            for (int d = 0; d < DIM; ++d) {
-                const double r = dt * S.inv_dx[d] * S_;  // dt / subcell width
-                // cell i of line l along d: ghost layers below 0 and from S on
-                auto cell = [&](int l, int i) -> const double * {
-                    if (i < 0) return sm.ghost + ((size_t)((d * 2 + 0) * 2 + (i + 2)) * L::NLINE + l) * M;
-                    if (i >= S_) return sm.ghost + ((size_t)((d * 2 + 1) * 2 + (i - S_)) * L::NLINE + l) * M;
-                    return sm.avg + lim_cell<DIM, S_>(d, l, i) * M;
-                };
-                // every face of this direction (face f between cells f-1 and f):
-                // the flux, or the two fluctuations [lower | upper]
-                constexpr int FW = PDE::NCP ? 2 * M : M;
-                for (int it = threadIdx.x; it < (S_ + 1) * L::NLINE; it += blockDim.x) {
-                    const int f = it % (S_ + 1), l = it / (S_ + 1);
-                    double *fo = sm.fb + (size_t)it * FW;
-                    if constexpr (PDE::NCP)
-                        lim_face_nc<PDE, DIM>(P.pde, cell(l, f - 2), cell(l, f - 1), cell(l, f), cell(l, f + 1), d, r,
-                                              dt, fo, fo + M, nullptr, nullptr);
-                    else
-                        lim_face<PDE, DIM>(P.pde, cell(l, f - 2), cell(l, f - 1), cell(l, f), cell(l, f + 1), d, r, dt,
-                                           fo);
+                if constexpr (PDE::HAS_SRC) {
+                    // the source at the half-step centre of all directions
+                    for (int a = threadIdx.x; a < L::NSUB; a += blockDim.x) {
+                        double S0[M], S1[M], w[M];
+                        const double *av = sm.avg + a * M;
+                        PDE::source(P.pde, av, S0);
+#pragma unroll
+                        for (int v = 0; v < M; ++v) w[v] = av[v] + ctr[a * M + v] + 0.5 * dt * S0[v];
+                        PDE::source(P.pde, w, S1);
+#pragma unroll
+                        for (int v = 0; v < M; ++v) sm.dq[a * M + v] += dt * S1[v];
+                    }
+                    __syncthreads();
                 }
+                for (int i = threadIdx.x; i < L::NSUB * M; i += blockDim.x) sm.dq[i] += sm.avg[i];
                 __syncthreads();
-                for (int it = threadIdx.x; it < S_ * L::NLINE; it += blockDim.x) {
-                    const int i = it % S_, l = it / S_;
-                    const double *F0 = sm.fb + (size_t)(l * (S_ + 1) + i) * FW, *F1 = F0 + FW;
-                    const int k = lim_cell<DIM, S_>(d, l, i);
-                    double *o = sm.dq + k * M;
-                    if constexpr (PDE::NCP) {
-                        // F1: the lower cell's fluctuation of face i+1; F0 + M:
-                        // the upper cell's of face i; then the smooth part of
-                        // B(q) grad q inside the subcell at its half-step centre
-                        double sl[M], chc[M], cw[M], Bc[M];
-                        const double *w = cell(l, i);
-                        lim_half<PDE, DIM>(P.pde, cell(l, i - 1), w, cell(l, i + 1), d, r, dt, sl, nullptr, nullptr,
-                                           chc);
-#pragma unroll
-                        for (int v = 0; v < M; ++v) cw[v] = w[v] + chc[v];
-                        lim_bdot<PDE>(cw, d, sl, Bc);
-#pragma unroll
-                        for (int v = 0; v < M; ++v) {
-                            o[v] -= r * (F1[v] - F0[M + v]);
-                            o[v] -= r * Bc[v];
-                        }
-                    } else {
-#pragma unroll
-                        for (int v = 0; v < M; ++v) o[v] -= r * (F1[v] - F0[v]);
-                    }
-                    if constexpr (PDE::HAS_SRC) {
-                        double chc[M];
-                        lim_half<PDE, DIM>(P.pde, cell(l, i - 1), cell(l, i), cell(l, i + 1), d, r, dt, nullptr,
-                                           nullptr, nullptr, chc);
-#pragma unroll
-                        for (int v = 0; v < M; ++v) ctr[k * M + v] += chc[v];
-                    }
-                }
+                lim_tensor<DIM, M, L::n, S_>(sm.dq, sm.u, sm.ta, sm.tb, sm.Rc);
+                // the material fields (q_t = 0) are kept as they were
+                for (int i = threadIdx.x; i < L::NS * M; i += blockDim.x)
+                    S.u_out[e * (L::NS * M) + i] = (i % M) < PDE::MEV ? sm.u[i] : S.u_prev[e * (L::NS * M) + i];
                 __syncthreads();
             }
-            if constexpr (PDE::HAS_SRC) {
-                // the source at the half-step centre of all directions
-                for (int a = threadIdx.x; a < L::NSUB; a += blockDim.x) {
-                    double S0[M], S1[M], w[M];
-                    const double *av = sm.avg + a * M;
-                    PDE::source(P.pde, av, S0);
-#pragma unroll
-                    for (int v = 0; v < M; ++v) w[v] = av[v] + ctr[a * M + v] + 0.5 * dt * S0[v];
-                    PDE::source(P.pde, w, S1);
-#pragma unroll
-                    for (int v = 0; v < M; ++v) sm.dq[a * M + v] += dt * S1[v];
-                }
-                __syncthreads();
-            }
-            for (int i = threadIdx.x; i < L::NSUB * M; i += blockDim.x) sm.dq[i] += sm.avg[i];
-            __syncthreads();
-            lim_tensor<DIM, M, L::n, S_>(sm.dq, sm.u, sm.ta, sm.tb, sm.Rc);
-            // the material fields (q_t = 0) are kept as they were
-            for (int i = threadIdx.x; i < L::NS * M; i += blockDim.x)
-                S.u_out[e * (L::NS * M) + i] = (i % M) < PDE::MEV ? sm.u[i] : S.u_prev[e * (L::NS * M) + i];
-            __syncthreads();
         }
     }
 }
@@ -611,120 +626,65 @@ __global__ void __launch_bounds__(128) k_lim_couple(const KParams P)
         extern __shared__ __align__(16) unsigned char smem_raw[];
         LimSmem<L> sm(reinterpret_cast<double *>(smem_raw));
         lim_load_ops<L>(P, sm);
-        const SolveDesc &S = P.solves[0];
-        const double dt = solve_dt(P, S);
-        if (!(dt > 0.0)) return;
-        const double *tr = reinterpret_cast<const double *>(S.tr);
-        for (long long e = blockIdx.x; e < S.E; e += gridDim.x) {
-            if (S.lim_flags[e]) continue;
-            int any = 0;
+        for (int si = 0; si < P.nsolves; ++si) {
+            const SolveDesc &S = P.solves[si];
+            if (!S.u_prev) continue;
+            const double dt = solve_dt(P, S);
+            if (!(dt > 0.0)) continue;
+            const double *tr = reinterpret_cast<const double *>(S.tr);
+            for (long long e = blockIdx.x; e < S.E; e += gridDim.x) {
+                if (S.lim_flags[e]) continue;
+                int any = 0;
 #pragma unroll
-            for (int d = 0; d < DIM; ++d)
+                for (int d = 0; d < DIM; ++d)
 #pragma unroll
-                for (int side = 0; side < 2; ++side)
-                    any |= S.lim_flags[neighbour((int)e, S.cells[0], S.cells[1], S.cells[2], d, side ? 1 : -1)];
-            if (!any) continue;  // uniform over the CTA
-            lim_averages<L, DIM>(S.u_prev, e, sm, sm.avg);
+                    for (int side = 0; side < 2; ++side)
+                        any |= S.lim_flags[neighbour((int)e, S.cells[0], S.cells[1], S.cells[2], d, side ? 1 : -1)];
+                if (!any) continue;  // uniform over the CTA
+                lim_averages<L, DIM>(S.u_prev, e, sm, sm.avg);
 #pragma unroll 1
-            for (int d = 0; d < DIM; ++d)
+                for (int d = 0; d < DIM; ++d)
 #pragma unroll 1
-                for (int side = 0; side < 2; ++side) {
-                    const long long nb = neighbour((int)e, S.cells[0], S.cells[1], S.cells[2], d, side ? 1 : -1);
-                    if (!S.lim_flags[nb]) continue;
-                    lim_averages<L, DIM>(S.u_prev, nb, sm, sm.nb);
-                    // the face's four cell layers: lower element's last two,
-                    // upper element's first two
-                    double *gl = sm.ghost, *gu = sm.ghost + 2 * L::NLINE * M;
-                    lim_layers<L, DIM>(side ? sm.avg : sm.nb, d, 1, gl);
-                    lim_layers<L, DIM>(side ? sm.nb : sm.avg, d, 0, gu);
-                    __syncthreads();
-                    const double r = dt * S.inv_dx[d] * S_;
-                    const long long el = side ? e : nb, eu = side ? nb : e;
-                    // per face node: projected subcell flux minus the DG flux
-                    if constexpr (PDE::NCP) {
-                        // per line: the fluctuation this element receives and
-                        // its own subcell state at the face [line][2M]
-                        double *Fl = sm.dq, *dF = sm.dq + (size_t)L::NLINE * 2 * M;  // dF: [p][v]
-                        for (int l = threadIdx.x; l < L::NLINE; l += blockDim.x) {
-                            double *o = Fl + (size_t)l * 2 * M;
-                            const double *a0 = gl + (size_t)l * M, *a1 = gl + (size_t)(L::NLINE + l) * M;
-                            const double *b0 = gu + (size_t)l * M, *b1 = gu + (size_t)(L::NLINE + l) * M;
-                            if (side)  // this element is the lower one
-                                lim_face_nc<PDE, DIM>(P.pde, a0, a1, b0, b1, d, r, dt, o, nullptr, o + M, nullptr);
-                            else
-                                lim_face_nc<PDE, DIM>(P.pde, a0, a1, b0, b1, d, r, dt, nullptr, o, nullptr, o + M);
-                        }
+                    for (int side = 0; side < 2; ++side) {
+                        const long long nb = neighbour((int)e, S.cells[0], S.cells[1], S.cells[2], d, side ? 1 : -1);
+                        if (!S.lim_flags[nb]) continue;
+                        lim_averages<L, DIM>(S.u_prev, nb, sm, sm.nb);
+                        // the face's four cell layers: lower element's last two,
+                        // upper element's first two
+                        double *gl = sm.ghost, *gu = sm.ghost + 2 * L::NLINE * M;
+                        lim_layers<L, DIM>(side ? sm.avg : sm.nb, d, 1, gl);
+                        lim_layers<L, DIM>(side ? sm.nb : sm.avg, d, 0, gu);
                         __syncthreads();
-                        // per (face node, line): the projected fluctuation plus
-                        // the path integral from this element's DG trace to its
-                        // subcell state at the face, into sm.fb [p][line][v]
-                        static_assert((size_t)NF * L::NLINE * M <= (size_t)L::FACES, "coupling terms exceed sm.fb");
-                        double *Cp = sm.fb;
-                        for (int it = threadIdx.x; it < NF * L::NLINE; it += blockDim.x) {
-                            const int l = it % L::NLINE, p = it / L::NLINE;
-                            int pk[3], rem = p;
-#pragma unroll
-                            for (int k = 0; k < DIM - 1; ++k) {
-                                pk[k] = rem % n;
-                                rem /= n;
+                        const double r = dt * S.inv_dx[d] * S_;
+                        const long long el = side ? e : nb, eu = side ? nb : e;
+                        // per face node: projected subcell flux minus the DG flux
+                        if constexpr (PDE::NCP) {
+                            // per line: the fluctuation this element receives and
+                            // its own subcell state at the face [line][2M]
+                            double *Fl = sm.dq, *dF = sm.dq + (size_t)L::NLINE * 2 * M;  // dF: [p][v]
+                            for (int l = threadIdx.x; l < L::NLINE; l += blockDim.x) {
+                                double *o = Fl + (size_t)l * 2 * M;
+                                const double *a0 = gl + (size_t)l * M, *a1 = gl + (size_t)(L::NLINE + l) * M;
+                                const double *b0 = gu + (size_t)l * M, *b1 = gu + (size_t)(L::NLINE + l) * M;
+                                if (side)  // this element is the lower one
+                                    lim_face_nc<PDE, DIM>(P.pde, a0, a1, b0, b1, d, r, dt, o, nullptr, o + M, nullptr);
+                                else
+                                    lim_face_nc<PDE, DIM>(P.pde, a0, a1, b0, b1, d, r, dt, nullptr, o, nullptr, o + M);
                             }
-                            double wgt = 1.0;
-                            int lr = l;
+                            __syncthreads();
+                            // per (face node, line): the projected fluctuation plus
+                            // the path integral from this element's DG trace to its
+                            // subcell state at the face, into sm.fb [p][line][v]
+                            static_assert((size_t)NF * L::NLINE * M <= (size_t)L::FACES, "coupling terms exceed sm.fb");
+                            double *Cp = sm.fb;
+                            for (int it = threadIdx.x; it < NF * L::NLINE; it += blockDim.x) {
+                                const int l = it % L::NLINE, p = it / L::NLINE;
+                                int pk[3], rem = p;
 #pragma unroll
-                            for (int k = 0; k < DIM - 1; ++k) {
-                                const int j = lr % S_;
-                                lr /= S_;
-                                wgt *= sm.Pr[j * n + pk[k]] / S_ / P.b.w[pk[k]];
-                            }
-                            const double *qown = side ? tr + (el * NFACE + (d * 2 + 1) * NF + p) * RS
-                                                      : tr + (eu * NFACE + (d * 2 + 0) * NF + p) * RS;
-                            const double *fs = Fl + (size_t)l * 2 * M;
-                            double dq[M], J[M];
-#pragma unroll
-                            for (int v = 0; v < M; ++v) dq[v] = fs[M + v] - qown[v];
-                            PDE::path_jump(qown, dq, d, J);
-#pragma unroll
-                            for (int v = 0; v < M; ++v) Cp[(size_t)it * M + v] = wgt * (fs[v] + J[v]);
-                        }
-                        __syncthreads();
-                        for (int p = threadIdx.x; p < NF; p += blockDim.x) {
-                            const double *Lr = tr + (el * NFACE + (d * 2 + 1) * NF + p) * RS;
-                            const double *Rr = tr + (eu * NFACE + (d * 2 + 0) * NF + p) * RS;
-                            double Ft[M], dq[M], J[M];
-#pragma unroll
-                            for (int v = 0; v < M; ++v) Ft[v] = 0.0;
-                            for (int l = 0; l < L::NLINE; ++l)
-#pragma unroll
-                                for (int v = 0; v < M; ++v) Ft[v] += Cp[((size_t)p * L::NLINE + l) * M + v];
-                            // the corrector's path-conservative fluctuation on this face node
-                            const double smax = tmax(Lr[Geom<PDE, DIM, N>::LAM], Rr[Geom<PDE, DIM, N>::LAM]);
-#pragma unroll
-                            for (int v = 0; v < M; ++v) dq[v] = Rr[v] - Lr[v];
-                            PDE::path_jump(Lr, dq, d, J);
-                            const double hs = side ? 0.5 : -0.5;
-#pragma unroll
-                            for (int v = 0; v < M; ++v)
-                                dF[p * M + v] = Ft[v] - (v < PDE::MEV ? hs * J[v] - 0.5 * smax * dq[v] : 0.0);
-                        }
-                        __syncthreads();
-                    } else {
-                        double *Fl = sm.dq;  // subcell fluxes on the face [line][v]
-                        for (int l = threadIdx.x; l < L::NLINE; l += blockDim.x)
-                            lim_face<PDE, DIM>(P.pde, gl + (size_t)l * M, gl + (size_t)(L::NLINE + l) * M,
-                                               gu + (size_t)l * M, gu + (size_t)(L::NLINE + l) * M, d, r, dt,
-                                               Fl + (size_t)l * M);
-                        __syncthreads();
-                        double *dF = sm.dq + (size_t)L::NLINE * M;  // [p][v]
-                        for (int i = threadIdx.x; i < NF * M; i += blockDim.x) {
-                            const int v = i % M, p = i / M;
-                            int pk[3], rem = p;
-#pragma unroll
-                            for (int k = 0; k < DIM - 1; ++k) {
-                                pk[k] = rem % n;
-                                rem /= n;
-                            }
-                            double Ft = 0.0;
-                            for (int l = 0; l < L::NLINE; ++l) {
+                                for (int k = 0; k < DIM - 1; ++k) {
+                                    pk[k] = rem % n;
+                                    rem /= n;
+                                }
                                 double wgt = 1.0;
                                 int lr = l;
 #pragma unroll
@@ -733,37 +693,95 @@ __global__ void __launch_bounds__(128) k_lim_couple(const KParams P)
                                     lr /= S_;
                                     wgt *= sm.Pr[j * n + pk[k]] / S_ / P.b.w[pk[k]];
                                 }
-                                Ft += wgt * Fl[(size_t)l * M + v];
+                                const double *qown = side ? tr + (el * NFACE + (d * 2 + 1) * NF + p) * RS
+                                                          : tr + (eu * NFACE + (d * 2 + 0) * NF + p) * RS;
+                                const double *fs = Fl + (size_t)l * 2 * M;
+                                double dq[M], J[M];
+#pragma unroll
+                                for (int v = 0; v < M; ++v) dq[v] = fs[M + v] - qown[v];
+                                PDE::path_jump(qown, dq, d, J);
+#pragma unroll
+                                for (int v = 0; v < M; ++v) Cp[(size_t)it * M + v] = wgt * (fs[v] + J[v]);
                             }
-                            // the corrector's Rusanov flux on this face node (lower | upper)
-                            const double *Lr = tr + (el * NFACE + (d * 2 + 1) * NF + p) * RS;
-                            const double *Rr = tr + (eu * NFACE + (d * 2 + 0) * NF + p) * RS;
-                            const double smax = tmax(Lr[Geom<PDE, DIM, N>::LAM], Rr[Geom<PDE, DIM, N>::LAM]);
-                            const double Fdg = 0.5 * (Lr[M + v] + Rr[M + v]) - 0.5 * smax * (Rr[v] - Lr[v]);
-                            dF[i] = Ft - Fdg;
+                            __syncthreads();
+                            for (int p = threadIdx.x; p < NF; p += blockDim.x) {
+                                const double *Lr = tr + (el * NFACE + (d * 2 + 1) * NF + p) * RS;
+                                const double *Rr = tr + (eu * NFACE + (d * 2 + 0) * NF + p) * RS;
+                                double Ft[M], dq[M], J[M];
+#pragma unroll
+                                for (int v = 0; v < M; ++v) Ft[v] = 0.0;
+                                for (int l = 0; l < L::NLINE; ++l)
+#pragma unroll
+                                    for (int v = 0; v < M; ++v) Ft[v] += Cp[((size_t)p * L::NLINE + l) * M + v];
+                                // the corrector's path-conservative fluctuation on this face node
+                                const double smax = tmax(Lr[Geom<PDE, DIM, N>::LAM], Rr[Geom<PDE, DIM, N>::LAM]);
+#pragma unroll
+                                for (int v = 0; v < M; ++v) dq[v] = Rr[v] - Lr[v];
+                                PDE::path_jump(Lr, dq, d, J);
+                                const double hs = side ? 0.5 : -0.5;
+#pragma unroll
+                                for (int v = 0; v < M; ++v)
+                                    dF[p * M + v] = Ft[v] - (v < PDE::MEV ? hs * J[v] - 0.5 * smax * dq[v] : 0.0);
+                            }
+                            __syncthreads();
+                        } else {
+                            double *Fl = sm.dq;  // subcell fluxes on the face [line][v]
+                            for (int l = threadIdx.x; l < L::NLINE; l += blockDim.x)
+                                lim_face<PDE, DIM>(P.pde, gl + (size_t)l * M, gl + (size_t)(L::NLINE + l) * M,
+                                                   gu + (size_t)l * M, gu + (size_t)(L::NLINE + l) * M, d, r, dt,
+                                                   Fl + (size_t)l * M);
+                            __syncthreads();
+                            double *dF = sm.dq + (size_t)L::NLINE * M;  // [p][v]
+                            for (int i = threadIdx.x; i < NF * M; i += blockDim.x) {
+                                const int v = i % M, p = i / M;
+                                int pk[3], rem = p;
+#pragma unroll
+                                for (int k = 0; k < DIM - 1; ++k) {
+                                    pk[k] = rem % n;
+                                    rem /= n;
+                                }
+                                double Ft = 0.0;
+                                for (int l = 0; l < L::NLINE; ++l) {
+                                    double wgt = 1.0;
+                                    int lr = l;
+#pragma unroll
+                                    for (int k = 0; k < DIM - 1; ++k) {
+                                        const int j = lr % S_;
+                                        lr /= S_;
+                                        wgt *= sm.Pr[j * n + pk[k]] / S_ / P.b.w[pk[k]];
+                                    }
+                                    Ft += wgt * Fl[(size_t)l * M + v];
+                                }
+                                // the corrector's Rusanov flux on this face node (lower | upper)
+                                const double *Lr = tr + (el * NFACE + (d * 2 + 1) * NF + p) * RS;
+                                const double *Rr = tr + (eu * NFACE + (d * 2 + 0) * NF + p) * RS;
+                                const double smax = tmax(Lr[Geom<PDE, DIM, N>::LAM], Rr[Geom<PDE, DIM, N>::LAM]);
+                                const double Fdg = 0.5 * (Lr[M + v] + Rr[M + v]) - 0.5 * smax * (Rr[v] - Lr[v]);
+                                dF[i] = Ft - Fdg;
+                            }
+                            __syncthreads();
+                        }
+                        const double *dF = sm.dq + (size_t)L::NLINE * M * (PDE::NCP ? 2 : 1);
+                        for (int i = threadIdx.x; i < L::NS * M; i += blockDim.x) {
+                            const int v = i % M, s = i / M;
+                            int sd = 0, p = 0, pw = 1, rem = s;
+#pragma unroll
+                            for (int k = 0; k < DIM; ++k) {
+                                const int x = rem % n;
+                                rem /= n;
+                                if (k == d) {
+                                    sd = x;
+                                } else {
+                                    p += x * pw;
+                                    pw *= n;
+                                }
+                            }
+                            const double lift = (side ? P.b.F1[sd] : -P.b.F0[sd]) * S.inv_dx[d] * P.b.inv_w[sd];
+                            S.u_out[e * (L::NS * M) + i] -= dt * lift * dF[p * M + v];
                         }
                         __syncthreads();
                     }
-                    const double *dF = sm.dq + (size_t)L::NLINE * M * (PDE::NCP ? 2 : 1);
-                    for (int i = threadIdx.x; i < L::NS * M; i += blockDim.x) {
-                        const int v = i % M, s = i / M;
-                        int sd = 0, p = 0, pw = 1, rem = s;
-#pragma unroll
-                        for (int k = 0; k < DIM; ++k) {
-                            const int x = rem % n;
-                            rem /= n;
-                            if (k == d) {
-                                sd = x;
-                            } else {
-                                p += x * pw;
-                                pw *= n;
-                            }
-                        }
-                        const double lift = (side ? P.b.F1[sd] : -P.b.F0[sd]) * S.inv_dx[d] * P.b.inv_w[sd];
-                        S.u_out[e * (L::NS * M) + i] -= dt * lift * dF[p * M + v];
-                    }
-                    __syncthreads();
-                }
+            }
         }
     }
 }

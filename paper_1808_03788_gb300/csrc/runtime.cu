@@ -221,17 +221,7 @@ int launch_corrector(aderdg_t *h, int use_ctl, double dt)
     return ADERDG_OK;
 }
 
-// Clears the step's wave-speed maxima and non-finite flag before they are
-// taken again from the limited state, and marks the candidate extremes as
-// those of the new state (where the limiter left an element untouched).
-__global__ void k_lim_reset(Control *c)
-{
-    if (threadIdx.x < 3) c->lam_acc[threadIdx.x] = 0ull;
-    if (threadIdx.x == 0) {
-        c->flags &= ~FLAG_NONFINITE;
-        c->lim_fresh = 1u;
-    }
-}
+__global__ void k_lim_reset(Control *c) { lim_reset(c); }
 
 // The subcell limiter on the candidate the corrector left in u (Sec. 2.3):
 // detection, subcell finite-volume update of the troubled elements,

@@ -232,3 +232,75 @@ def test_kept_extremes_equal_fresh_projections(explicit_first):
     for a, b in zip(fa, fb):
         np.testing.assert_array_equal(a, b)
     assert any(f.any() for f in fa) and not all(f.all() for f in fa)
+
+
+def _blast2d(cells, N, lo=(0, 0), hi=(1, 1)):
+    from paper_1808_03788_gb300 import inputs
+    c = oracle.make_cfg(2, cells, list(lo), list(hi), N, oracle.PDE_EULER, [1.4], limiter=1)
+    X = oracle.node_coords(c)
+    r = np.sqrt((X[..., 0] - 0.45) ** 2 + (X[..., 1] - 0.5) ** 2)
+    rho = inputs.smooth_step(r, 0.2, 0.03, 1.0, 0.125)
+    p = inputs.smooth_step(r, 0.2, 0.03, 1.0, 0.1)
+    z = 0 * rho
+    return (A.ADERDG_PDE_EULER, 2, cells, lo, hi, N, (1.4,)), np.stack([rho, z, z, p / 0.4], axis=-1)
+
+
+def _inclusion2d(cells, N):
+    from paper_1808_03788_gb300 import inputs
+    c = oracle.make_cfg(2, cells, [0, 0], [1, 1], N, oracle.PDE_DIFFUSE_ELASTICITY, [], limiter=1)
+    X = oracle.node_coords(c)
+    x, y = X[..., 0], X[..., 1]
+    alpha = inputs.smooth_step(np.sqrt((x - 0.5) ** 2 + (y - 0.5) ** 2), 0.25, 0.04, 0.3, 1.0)
+    box = lambda a, b: np.where((a > 0.1) & (a < 0.3) & (b > 0.3) & (b < 0.6), 1.0, 0.0)
+    z = 0 * x
+    U = inputs.diffuse_pack(2, [z, z, z], [alpha * box(x, y), alpha * box(y, x)], alpha, 2.0, 1.0, 1.0)
+    return (A.ADERDG_PDE_DIFFUSE_ELASTICITY, 2, cells, (0, 0), (1, 1), N, ()), U
+
+
+def test_limited_batch_equals_solves_alone():
+    """The limiter in a batch: one launch of each limiter kernel covers every
+    solve of a (PDE, d, N) group (here two Euler N = 3 solves of different
+    sizes share one), and each solve's states and troubled sets are bitwise
+    those it gets alone on a limited handle."""
+    cases = [_blast2d((16, 16), 3), _blast2d((12, 20), 3, hi=(1, 1.5)), _blast2d((10, 10), 2),
+             _inclusion2d((12, 12), 3)]
+    b = A.Batch([A.make_spec(*c) for c, _ in cases], limiter=True)
+    assert b.info()["groups"] == 3
+    for i, (_, U) in enumerate(cases):
+        b.set_state(i, U)
+    singles = []
+    for c, U in cases:
+        s = A.Solver(*c, limiter=True)
+        s.set_state(U)
+        singles.append(s)
+    seen = [0] * len(cases)
+    for _ in range(8):
+        b.step(1e30)
+        for i, s in enumerate(singles):
+            s.step(1e30)
+            fb, cb = b.troubled(i)
+            fs, cs = s.troubled()
+            np.testing.assert_array_equal(fb, fs)
+            seen[i] = max(seen[i], cb)
+    for i, s in enumerate(singles):
+        Ub, tb, kb = b.get_state(i)
+        Us, ts, ks = s.get_state()
+        assert (tb, kb) == (ts, ks) == (ts, 8)
+        np.testing.assert_array_equal(Ub, Us.reshape(-1))
+        s.close()
+    b.close()
+    assert all(x > 0 for x in seen)
+
+
+def test_limited_batch_refuses_what_the_limiter_does_not_cover():
+    c, _ = _blast2d((4, 4), 3)
+    with pytest.raises(A.AderdgError) as ei:
+        A.Batch([A.make_spec(*c)], limiter=True, precision=A.ADERDG_MIXED_FP32)
+    assert ei.value.code == A.ADERDG_E_UNSUPPORTED
+    with pytest.raises(A.AderdgError) as ei:
+        A.Batch([A.make_spec(*c)], limiter=True, guess=A.ADERDG_GUESS_EXTRAP)
+    assert ei.value.code == A.ADERDG_E_UNSUPPORTED
+    b = A.Batch([A.make_spec(*c)])
+    with pytest.raises(A.AderdgError):
+        b.troubled(0)
+    b.close()
