@@ -105,7 +105,7 @@ struct Slot {
     // subcell limiter (FP64): u^n, extremes of u^n and of the candidate, flags
     bool limiter = false;
     double *u_prev = nullptr, *lim_mm = nullptr, *lim_mmc = nullptr;
-    int *lim_flags = nullptr;
+    int *lim_flags = nullptr, *lim_list = nullptr;
     int ctl_index = -1;
     // placement in the current group arrays (for k_cfl)
     int group = -1, member = -1;
@@ -114,7 +114,7 @@ struct Slot {
 size_t lim_bytes(const Slot &s)
 {
     const size_t ns = (size_t)s.E * s.NS * s.M;
-    return s.limiter ? a256(ns * 8) + 2 * a256((size_t)s.E * s.M * 2 * 8) + a256((size_t)s.E * 4) : 0;
+    return s.limiter ? a256(ns * 8) + 2 * a256((size_t)s.E * s.M * 2 * 8) + 2 * a256((size_t)s.E * 4) : 0;
 }
 
 size_t slot_bytes(const Slot &s)
@@ -296,6 +296,8 @@ public:
             s->lim_mm = reinterpret_cast<double *>(l + a256(ns * 8));
             s->lim_mmc = reinterpret_cast<double *>(l + a256(ns * 8) + a256((size_t)s->E * s->M * 2 * 8));
             s->lim_flags = reinterpret_cast<int *>(l + a256(ns * 8) + 2 * a256((size_t)s->E * s->M * 2 * 8));
+            s->lim_list = reinterpret_cast<int *>(reinterpret_cast<unsigned char *>(s->lim_flags) +
+                                                  a256((size_t)s->E * 4));
             CKB(cudaMemsetAsync(s->lim_flags, 0, sizeof(int) * (size_t)s->E, st));
         }
         s->ctl_index = ctl_free.back();
@@ -384,6 +386,7 @@ public:
                 d.lim_mm = s->lim_mm;
                 d.lim_mmc = s->lim_mmc;
                 d.lim_flags = s->lim_flags;
+                d.lim_list = s->lim_list;
             }
             g.ntp = tp;
             g.ntc = tc;

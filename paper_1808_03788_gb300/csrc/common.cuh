@@ -47,6 +47,8 @@ struct Control {
     long long step;
     unsigned int flags;
     unsigned int lim_fresh;  // subcell limiter: lim_mmc holds the candidate extremes of the state's last step
+    unsigned int lim_count;  // subcell limiter: troubled elements listed in lim_list this step
+    unsigned int pad2;
 };
 
 // After the subcell limiter: the step's wave-speed maxima and non-finite
@@ -60,6 +62,7 @@ __device__ __forceinline__ void lim_reset(Control *c)
     if (threadIdx.x == 0) {
         c->flags &= ~FLAG_NONFINITE;
         c->lim_fresh = 1u;
+        c->lim_count = 0u;
     }
 }
 #endif
@@ -131,6 +134,7 @@ struct SolveDesc {
     double *lim_mm;
     double *lim_mmc;
     int *lim_flags;
+    int *lim_list;  // the troubled elements of the step, in detection order [ctl->lim_count]
 };
 
 inline void fill_desc_spacing(SolveDesc &d)

@@ -8,7 +8,8 @@
 //                 the nodes and in the subcell averages, or a subcell average
 //                 of u* outside the relaxed discrete maximum principle
 //                 [lo - delta, hi + delta] of u^n over the element and its
-//                 2d face neighbours, delta = max(1e-4, 1e-3 (hi - lo))
+//                 2d face neighbours, delta = max(1e-4, 1e-3 (hi - lo));
+//                 flags and a compact list of them
 //   k_lim_fv      troubled elements: MUSCL-Hancock with minmod slopes and
 //                 Rusanov fluxes on (2N+1)^d subcells of u^n (direction by
 //                 direction, ghost subcells two deep from the face
@@ -491,7 +492,10 @@ __global__ void __launch_bounds__(128) k_lim_detect(const KParams P)
                     }
                     bad = __any_sync(0xffffffffu, bad);
                 }
-                if (lane == 0) S.lim_flags[e] = bad;
+                if (lane == 0) {
+                    S.lim_flags[e] = bad;
+                    if (bad) S.lim_list[atomicAdd(&S.ctl->lim_count, 1u)] = (int)e;
+                }
                 __syncwarp();
             }
         }
@@ -512,8 +516,11 @@ __global__ void __launch_bounds__(128) k_lim_fv(const KParams P)
             if (!S.u_prev) continue;
             const double dt = solve_dt(P, S);
             if (!(dt > 0.0)) continue;
-            for (long long e = blockIdx.x; e < S.E; e += gridDim.x) {
-                if (!S.lim_flags[e]) continue;  // uniform over the CTA
+            // the troubled elements, one per CTA (their order does not
+            // matter: each is computed on its own)
+            const unsigned ntroubled = S.ctl->lim_count;
+            for (unsigned k = blockIdx.x; k < ntroubled; k += gridDim.x) {
+                const long long e = S.lim_list[k];
                 lim_averages<L, DIM>(S.u_prev, e, sm, sm.avg);
 #pragma unroll 1
                 for (int d = 0; d < DIM; ++d)

@@ -166,6 +166,7 @@ struct aderdg_s {
     double *lim_mm = nullptr;   // limiter: extreme subcell averages of u^n [E][M][2]
     double *lim_mmc = nullptr;  // limiter: those of the candidate, kept for the next step
     int *lim_flags = nullptr;   // limiter: troubled elements of the last step [E]
+    int *lim_list = nullptr;    // limiter: their indices, in detection order [E]
     double *host_pinned = nullptr;
     KParams kp{};
     Basis basis{};
@@ -461,10 +462,11 @@ int aderdg_create(const aderdg_mesh_t *mesh, int N, int nVar, const aderdg_pde_t
         h->lim_mm = (double *)dev_alloc(h, sizeof(double) * (size_t)E * m * 2);
         h->lim_mmc = (double *)dev_alloc(h, sizeof(double) * (size_t)E * m * 2);
         h->lim_flags = (int *)dev_alloc(h, sizeof(int) * (size_t)E);
+        h->lim_list = (int *)dev_alloc(h, sizeof(int) * (size_t)E);
     }
     if (!h->u || !h->V || !h->tr || !h->ctl || !h->scratch || !h->d_desc || (ks->rf > 0 && !h->ref) ||
         (h->guess == ADERDG_GUESS_EXTRAP && !h->qprev) ||
-        (h->limiter && (!h->u_prev || !h->lim_mm || !h->lim_mmc || !h->lim_flags))) {
+        (h->limiter && (!h->u_prev || !h->lim_mm || !h->lim_mmc || !h->lim_flags || !h->lim_list))) {
         aderdg_destroy(h);
         return fail(ADERDG_E_NOMEM, "device allocation failed");
     }
@@ -497,6 +499,7 @@ int aderdg_create(const aderdg_mesh_t *mesh, int N, int nVar, const aderdg_pde_t
     sd.lim_mm = h->lim_mm;
     sd.lim_mmc = h->lim_mmc;
     sd.lim_flags = h->lim_flags;
+    sd.lim_list = h->lim_list;
     KParams &kp = h->kp;
     std::memset(&kp, 0, sizeof(kp));
     kp.solves = h->d_desc;
@@ -534,6 +537,7 @@ int aderdg_destroy(aderdg_t *h)
     dev_free(h, h->lim_mm);
     dev_free(h, h->lim_mmc);
     dev_free(h, h->lim_flags);
+    dev_free(h, h->lim_list);
     dev_free(h, h->V);
     dev_free(h, h->tr);
     dev_free(h, h->ctl);
