@@ -494,7 +494,11 @@ __global__ void __launch_bounds__(128) k_lim_detect(const KParams P)
                 }
                 if (lane == 0) {
                     S.lim_flags[e] = bad;
-                    if (bad) S.lim_list[atomicAdd(&S.ctl->lim_count, 1u)] = (int)e;
+                    if (bad) {
+                        // at most E entries a step (the reset after the limiter empties it)
+                        const unsigned k = atomicAdd(&S.ctl->lim_count, 1u);
+                        if (k < (unsigned)S.E) S.lim_list[k] = (int)e;
+                    }
                 }
                 __syncwarp();
             }
@@ -518,7 +522,7 @@ __global__ void __launch_bounds__(128) k_lim_fv(const KParams P)
             if (!(dt > 0.0)) continue;
             // the troubled elements, one per CTA (their order does not
             // matter: each is computed on its own)
-            const unsigned ntroubled = S.ctl->lim_count;
+            const unsigned ntroubled = min(S.ctl->lim_count, (unsigned)S.E);
             for (unsigned k = blockIdx.x; k < ntroubled; k += gridDim.x) {
                 const long long e = S.lim_list[k];
                 lim_averages<L, DIM>(S.u_prev, e, sm, sm.avg);
