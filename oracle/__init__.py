@@ -361,6 +361,19 @@ def step_limited(cfg: Cfg, U: np.ndarray, dt: float):
     return out, flags, cnt.value
 
 
+def detect(cfg: Cfg, U0: np.ndarray, U: np.ndarray):
+    """The limiter's detection alone (Sec. 2.3, R25): (troubled[E] flags,
+    count) of the candidate U against the state U0 at t^n."""
+    U0 = np.ascontiguousarray(U0, dtype=np.float64)
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    flags = np.zeros(n_elems(cfg), dtype=np.int32)
+    lib().orc_detect.restype = C.c_long
+    cnt = lib().orc_detect(C.byref(cfg), _p(U0), _p(U), flags.ctypes.data_as(C.POINTER(C.c_int)))
+    if cnt < 0:
+        raise RuntimeError("orc_detect failed: %d" % cnt)
+    return flags, int(cnt)
+
+
 def subcell_ops(N: int):
     """1D subcell operators: Pr[(2N+1), N+1] (subcell averages of the nodal
     basis) and Rc[N+1, 2N+1] (least-squares reconstruction)."""

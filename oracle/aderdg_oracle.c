@@ -1026,33 +1026,17 @@ double orc_cfl_dt(const orc_cfg *c, const double *U)
     return orc_alpha(c) / S;
 }
 
-/* The a posteriori subcell limiter (Sec. 2.3) on a candidate U (in place),
- * from the state U0 at t^n and the candidate's traces qf / ff:
- *   1. extreme subcell averages of U0 per element and variable;
- *   2. detection (R25) -> troubled[e] (may be NULL);
- *   3. troubled elements: MUSCL-Hancock on their subcells from U0 (R26,
- *      R29), least-squares reconstruction (R28), boundary subcell
- *      fluctuations kept (the one each face neighbour receives);
- *   4. unlimited face neighbours of troubled elements: their DG face flux on
- *      the common face replaced by the projected subcell fluxes (R27).
- * Returns the number of troubled elements, or < 0 on failure. */
-static long apply_limiter(const orc_cfg *c, const basis *b, const double *U0, double *U, const double *qf,
-                          const double *ff, double dt, int *troubled)
+/* Steps 1 and 2 of the limiter (R25): extreme subcell averages of the
+ * state U0 at t^n per element and variable, then the troubled elements of
+ * the candidate U -> bad[e].  Returns their number, or < 0 on failure. */
+static long detect_troubled(const orc_cfg *c, const subcell_ops *so, const double *U0, const double *U, int *bad)
 {
-    subcell_ops o;
-    if (make_subcell_ops(b, &o)) return -1;
-    const int n = b->n, S = o.S, dim = c->dim, m = c->m;
-    const int ns = ipow(n, dim), nf = ipow(n, dim - 1), nsub = ipow(S, dim), nline = ipow(S, dim - 1);
+    const subcell_ops o = *so;
+    const int n = o.n, dim = c->dim, m = c->m;
+    const int ns = ipow(n, dim), nsub = ipow(o.S, dim);
     const long E = n_elems(c);
-    const size_t fsz = (size_t)2 * dim * nf * m;
-    const int ncp = c->pde == 4, src = c->pde == 1, mev = orc_nevolved(c);
     double *mm = malloc(sizeof(double) * (size_t)E * m * 2);          /* [e][v][min|max] of U0 */
-    int *bad = malloc(sizeof(int) * (size_t)E);
-    double *Unew = malloc(sizeof(double) * (size_t)E * ns * m);
-    /* [e][d][side][line][2m]: the boundary fluctuation a face neighbour
-     * receives, then that neighbour's own subcell state at the face */
-    double *Fb = malloc(sizeof(double) * (size_t)E * dim * 2 * nline * 2 * m);
-    if (!mm || !bad || !Unew || !Fb) { free(mm); free(bad); free(Unew); free(Fb); return -2; }
+    if (!mm) return -2;
     long count = 0;
 
     /* 1. extreme subcell averages of u^n */
@@ -1108,6 +1092,39 @@ static long apply_limiter(const orc_cfg *c, const basis *b, const double *U0, do
         }
         free(avg);
     }
+    free(mm);
+    return count;
+}
+
+/* The a posteriori subcell limiter (Sec. 2.3) on a candidate U (in place),
+ * from the state U0 at t^n and the candidate's traces qf / ff:
+ *   1. extreme subcell averages of U0 per element and variable;
+ *   2. detection (R25) -> troubled[e] (may be NULL);
+ *   3. troubled elements: MUSCL-Hancock on their subcells from U0 (R26,
+ *      R29), least-squares reconstruction (R28), boundary subcell
+ *      fluctuations kept (the one each face neighbour receives);
+ *   4. unlimited face neighbours of troubled elements: their DG face flux on
+ *      the common face replaced by the projected subcell fluxes (R27).
+ * Returns the number of troubled elements, or < 0 on failure. */
+static long apply_limiter(const orc_cfg *c, const basis *b, const double *U0, double *U, const double *qf,
+                          const double *ff, double dt, int *troubled)
+{
+    subcell_ops o;
+    if (make_subcell_ops(b, &o)) return -1;
+    const int n = b->n, S = o.S, dim = c->dim, m = c->m;
+    const int ns = ipow(n, dim), nf = ipow(n, dim - 1), nsub = ipow(S, dim), nline = ipow(S, dim - 1);
+    const long E = n_elems(c);
+    const size_t fsz = (size_t)2 * dim * nf * m;
+    const int ncp = c->pde == 4, src = c->pde == 1, mev = orc_nevolved(c);
+    int *bad = malloc(sizeof(int) * (size_t)E);
+    double *Unew = malloc(sizeof(double) * (size_t)E * ns * m);
+    /* [e][d][side][line][2m]: the boundary fluctuation a face neighbour
+     * receives, then that neighbour's own subcell state at the face */
+    double *Fb = malloc(sizeof(double) * (size_t)E * dim * 2 * nline * 2 * m);
+    if (!bad || !Unew || !Fb) { free(bad); free(Unew); free(Fb); return -2; }
+    const long count = detect_troubled(c, &o, U0, U, bad);
+    if (count < 0) { free(bad); free(Unew); free(Fb); return count; }
+
     /* 3. subcell finite-volume step of the troubled elements */
 #pragma omp parallel
     {
@@ -1289,7 +1306,7 @@ static long apply_limiter(const orc_cfg *c, const basis *b, const double *U0, do
         if (bad[e]) memcpy(&U[(size_t)e * ns * m], &Unew[(size_t)e * ns * m], sizeof(double) * ns * m);
         if (troubled) troubled[e] = bad[e];
     }
-    free(mm); free(bad); free(Unew); free(Fb);
+    free(bad); free(Unew); free(Fb);
     return count;
 }
 
@@ -1397,6 +1414,16 @@ int orc_step_ex(const orc_cfg *c, double *U, double dt, double *V_out, double *q
 int orc_step(const orc_cfg *c, double *U, double dt) { return orc_step_ex(c, U, dt, NULL, NULL, NULL); }
 
 /* One step with the limiter's outcome: troubled[e] (E ints) and their count. */
+/* The limiter's detection alone (R25): troubled[e] of the candidate U
+ * against the state U0 at t^n; returns their number, or < 0. */
+long orc_detect(const orc_cfg *c, const double *U0, const double *U, int *troubled)
+{
+    basis b;
+    subcell_ops o;
+    if (make_basis(c->N, &b) || make_subcell_ops(&b, &o)) return -1;
+    return detect_troubled(c, &o, U0, U, troubled);
+}
+
 int orc_step_limited(const orc_cfg *c, double *U, double dt, int *troubled, long *ntroubled)
 {
     return step_impl(c, U, dt, NULL, NULL, NULL, NULL, troubled, ntroubled);

@@ -14,6 +14,9 @@
   couplings, and the x <-> y mirror symmetry of the data kept to rounding
   (a wrong index or orientation in the subcell sweeps or the face coupling
   breaks it).
+- Detection (R25) against closed-form flip points: the floor delta = 1e-4
+  on uniform data, delta = 1e-3 (hi - lo) over the face neighbours (not the
+  diagonal ones), non-finite values, negative pressure within the bounds.
 - Non-conservative products and sources (eq. pde.nc.fv): with alpha = 1 the
   diffuse-interface subcell scheme is the conservative elasticity one; a
   soft inclusion keeps the mirror symmetry; the reaction source on uniform
@@ -250,3 +253,75 @@ def test_limited_reaction_on_uniform_data_is_the_second_order_taylor_step():
     np.testing.assert_allclose(Ul, 0.8 * (1 - zt + zt * zt / 2), rtol=1e-14)
     c.limiter = 0
     assert np.abs(oracle.step(c, U, dt) - 0.8 * (1 - zt + zt * zt / 2)).max() > 1e-6
+
+
+def _grid_index(cells, i, j):
+    return j * cells[0] + i
+
+
+@pytest.mark.parametrize("eps, flagged", [(0.9e-4, False), (1.1e-4, True), (-1.1e-4, True)])
+def test_detection_floor_of_the_relaxed_maximum_principle(eps, flagged):
+    """Uniform u^n (range 0): the relaxed bounds are [c - 1e-4, c + 1e-4]
+    (delta = max(1e-4, 1e-3 * 0)).  A candidate element shifted by eps has
+    every subcell average at c + eps (the averages of a constant are that
+    constant), so it is troubled exactly when |eps| > 1e-4, and no other
+    element is."""
+    cells = (6, 6)
+    c = oracle.make_cfg(2, cells, [0, 0], [1, 1], 3, oracle.PDE_ADVECTION, [1.0, 0.5], limiter=1)
+    U0 = np.full((36, 16, 1), 0.7)
+    U = U0.copy()
+    k = _grid_index(cells, 2, 3)
+    U[k] += eps
+    flags, cnt = oracle.detect(c, U0, U)
+    assert cnt == int(flagged) and bool(flags[k]) == flagged
+
+
+@pytest.mark.parametrize("eps, flagged", [(0.9e-3, False), (1.1e-3, True)])
+def test_detection_bounds_span_the_face_neighbours(eps, flagged):
+    """u^n = c except one element j at c + 1: every face neighbour k of j
+    has bounds [c - delta, c + 1 + delta] with delta = 1e-3 * 1, so a
+    candidate k at c + 1 + eps is troubled exactly when eps > 1e-3.  A
+    diagonal neighbour of j does not see j (face neighbours only): shifted
+    by 5e-4 it is troubled (its delta is 1e-4)."""
+    cells = (6, 6)
+    c = oracle.make_cfg(2, cells, [0, 0], [1, 1], 3, oracle.PDE_ADVECTION, [1.0, 0.5], limiter=1)
+    U0 = np.full((36, 16, 1), 0.7)
+    j = _grid_index(cells, 2, 2)
+    U0[j] += 1.0
+    for k in (_grid_index(cells, 3, 2), _grid_index(cells, 2, 1), _grid_index(cells, 1, 2), _grid_index(cells, 2, 3)):
+        U = U0.copy()
+        U[k] = 0.7 + 1.0 + eps
+        flags, cnt = oracle.detect(c, U0, U)
+        assert cnt == int(flagged) and bool(flags[k]) == flagged
+    U = U0.copy()
+    d = _grid_index(cells, 3, 3)
+    U[d] += 5e-4
+    flags, cnt = oracle.detect(c, U0, U)
+    assert cnt == 1 and flags[d] == 1
+
+
+def test_detection_flags_non_finite_and_negative_pressure():
+    """Non-finite values flag an element; so does negative pressure where
+    the maximum principle alone would not: u^n holds a moving element (rho
+    1, momentum 3, rho E 10) next to resting ones (rho E 2.5), and a
+    candidate element with momentum 3 and rho E 2.5 stays within every
+    variable's bounds but has p = 0.4 (2.5 - 4.5) < 0."""
+    cells = (4, 4)
+    c = oracle.make_cfg(2, cells, [0, 0], [1, 1], 2, oracle.PDE_EULER, [1.4], limiter=1)
+    U0 = np.zeros((16, 9, 4))
+    U0[..., 0] = 1.0
+    U0[..., 3] = 2.5
+    j, k = _grid_index(cells, 1, 1), _grid_index(cells, 2, 1)
+    U0[j, :, 1] = 3.0
+    U0[j, :, 3] = 10.0
+    assert oracle.detect(c, U0, U0.copy())[1] == 0
+    U = U0.copy()
+    U[5, 4, 0] = np.nan
+    flags, cnt = oracle.detect(c, U0, U)
+    assert cnt == 1 and flags[5] == 1
+    U = U0.copy()
+    U[k, :, 1] = 3.0  # rho E stays 2.5
+    flags, cnt = oracle.detect(c, U0, U)
+    assert cnt == 1 and flags[k] == 1
+    U[k, :, 3] = 10.0  # the same momentum with enough energy: admissible, within bounds
+    assert oracle.detect(c, U0, U)[1] == 0
