@@ -97,6 +97,8 @@ def lib():
             L.orc_rusanov.restype = None
             L.orc_ncp.argtypes = [cp, dp, C.c_int, dp, dp]
             L.orc_ncp.restype = None
+            L.orc_detect.argtypes = [cp, dp, dp, C.POINTER(C.c_int)]
+            L.orc_detect.restype = C.c_long
             L.orc_source.argtypes = [cp, dp, dp]
             L.orc_source.restype = None
             L.orc_path_jump.argtypes = [cp, C.c_int, dp, dp, dp]
@@ -367,7 +369,6 @@ def detect(cfg: Cfg, U0: np.ndarray, U: np.ndarray):
     U0 = np.ascontiguousarray(U0, dtype=np.float64)
     U = np.ascontiguousarray(U, dtype=np.float64)
     flags = np.zeros(n_elems(cfg), dtype=np.int32)
-    lib().orc_detect.restype = C.c_long
     cnt = lib().orc_detect(C.byref(cfg), _p(U0), _p(U), flags.ctypes.data_as(C.POINTER(C.c_int)))
     if cnt < 0:
         raise RuntimeError("orc_detect failed: %d" % cnt)
