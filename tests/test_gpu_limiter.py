@@ -304,3 +304,25 @@ def test_limited_batch_refuses_what_the_limiter_does_not_cover():
     with pytest.raises(A.AderdgError):
         b.troubled(0)
     b.close()
+
+
+def test_limited_batch_graph_replay_equals_solves_alone():
+    """Limited batch steps replayed as CUDA graphs (aderdg_batch_advance, in
+    chunks of captured steps) give each solve the states it gets alone on a
+    limited handle advanced with its own graphs."""
+    cases = [_blast2d((16, 16), 3), _inclusion2d((10, 10), 2)]
+    b = A.Batch([A.make_spec(*c) for c, _ in cases], limiter=True)
+    for i, (_, U) in enumerate(cases):
+        b.set_state(i, U)
+    b.advance(1e30, max_steps=19)
+    for i, (c, U) in enumerate(cases):
+        with A.Solver(*c, limiter=True) as s:
+            s.set_state(U)
+            s.advance(1e30, max_steps=19)
+            Us, ts, ks = s.get_state()
+            fs = s.troubled()[0]
+        Ub, tb, kb = b.get_state(i)
+        assert (tb, kb) == (ts, ks) and kb == 19
+        np.testing.assert_array_equal(Ub, Us.reshape(-1))
+        np.testing.assert_array_equal(b.troubled(i)[0], fs)
+    b.close()
