@@ -326,3 +326,31 @@ def test_limited_batch_graph_replay_equals_solves_alone():
         np.testing.assert_array_equal(Ub, Us.reshape(-1))
         np.testing.assert_array_equal(b.troubled(i)[0], fs)
     b.close()
+
+
+@pytest.mark.parametrize("case", ["blast", "inclusion"])
+def test_limited_step_at_the_bench_size_matches_oracle(case):
+    """The limiter rows of bench.py at their full size (200 x 200 elements,
+    N = 4, the same inputs), two limited steps: troubled sets equal, every
+    node within the FP64 tolerance."""
+    from paper_1808_03788_gb300 import inputs
+    cells, lo, hi, N = (200, 200), (0.0, 0.0), (10.0, 10.0), 4
+    if case == "blast":
+        pde, params = oracle.PDE_EULER, [1.4]
+    else:
+        pde, params = oracle.PDE_DIFFUSE_ELASTICITY, []
+    c = oracle.make_cfg(2, cells, list(lo), list(hi), N, pde, params, limiter=1)
+    X = oracle.node_coords(c)
+    x, y = X[..., 0], X[..., 1]
+    r = np.sqrt((x - 5.0) ** 2 + (y - 5.0) ** 2)
+    if case == "blast":
+        rho = inputs.smooth_step(r, 2.0, 0.3, 1.0, 0.125)
+        p = inputs.smooth_step(r, 2.0, 0.3, 1.0, 0.1)
+        U = np.stack([rho, 0 * rho, 0 * rho, p / 0.4], axis=-1)
+    else:
+        alpha = inputs.smooth_step(r, 2.5, 0.3, 0.3, 1.0)
+        box = lambda a, b: np.where((a > 1.0) & (a < 3.0) & (b > 3.0) & (b < 6.0), 1.0, 0.0)
+        z = 0 * x
+        U = inputs.diffuse_pack(2, [z, z, z], [alpha * box(x, y), alpha * box(y, x)], alpha, 2.0, 1.0, 1.0)
+    _, counts = _run_against_oracle(c, U, tuple(params), 2)
+    assert min(counts) > 0
