@@ -360,23 +360,25 @@ def _limiter(A, torch, w, stream, flush, steps, warmup):
     and the path-conservative subcell scheme (eq. pde.nc.fv) on the
     diffuse-interface system: a soft inclusion (alpha 1 -> 0.3 across r = 2.5,
     tanh width 0.3, lambda = 2, mu = rho = 1) hit by two mirrored velocity
-    boxes, limited and unlimited.  Each is timed like the headline, with the
-    troubled elements of the last step."""
+    boxes, limited and unlimited; the vortex and the blast again on the FP32
+    path.  Each is timed like the headline, with the troubled elements of
+    the last step."""
     import numpy as np
 
     from paper_1808_03788_gb300 import inputs
-    out = {"precision": "fp64"}
-    for name in ("vortex", "blast", "inclusion", "inclusion_unlimited"):
+    out = {"precision": "fp64 (the *_mixed cases: the FP32 path)"}
+    for name in ("vortex", "blast", "inclusion", "inclusion_unlimited", "vortex_mixed", "blast_mixed"):
         dim_pde = name.startswith("inclusion")
         pde, params = (A.ADERDG_PDE_DIFFUSE_ELASTICITY, ()) if dim_pde else (w["pde"], w["params"])
         lim = name != "inclusion_unlimited"
+        prec = A.ADERDG_MIXED_FP32 if name.endswith("_mixed") else A.ADERDG_FP64
         s = A.Solver(pde, w["dim"], w["cells"], w["lo"], w["hi"], w["N"], params, stream=stream.cuda_stream,
-                     limiter=lim)
+                     limiter=lim, precision=prec)
         X = s.node_coords(w["lo"], w["hi"])
         x, y = X[..., 0], X[..., 1]
-        if name == "vortex":
+        if name.startswith("vortex"):
             U0 = inputs.euler_vortex(X, lo=w["lo"], hi=w["hi"])
-        elif name == "blast":
+        elif name.startswith("blast"):
             r = np.sqrt((x - 5.0) ** 2 + (y - 5.0) ** 2)
             rho = inputs.smooth_step(r, 2.0, 0.3, 1.0, 0.125)
             p = inputs.smooth_step(r, 2.0, 0.3, 1.0, 0.1)

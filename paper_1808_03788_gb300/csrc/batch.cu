@@ -104,6 +104,7 @@ struct Slot {
     void *qprev = nullptr;     // extrapolation guess: last predictor
     // subcell limiter (FP64): u^n, extremes of u^n and of the candidate, flags
     bool limiter = false;
+    LimKernels lk{};
     double *u_prev = nullptr, *lim_mm = nullptr, *lim_mmc = nullptr;
     int *lim_flags = nullptr, *lim_list = nullptr;
     int ctl_index = -1;
@@ -137,23 +138,15 @@ int make_slot(const aderdg_solve_spec_t &sp, int prec, int guess, int picard, do
     if (sp.pde.kind == ADERDG_PDE_EULER && !(sp.pde.p[0] > 1.0)) return fail(ADERDG_E_INVAL, "gamma must be > 1");
     if (sp.pde.kind == ADERDG_PDE_ADVECTION && !(sp.pde.p[3] >= 0.0)) return fail(ADERDG_E_INVAL, "kappa must be >= 0");
     if (guess < ADERDG_GUESS_TRIVIAL || guess > ADERDG_GUESS_CERK) return fail(ADERDG_E_INVAL, "bad initial guess");
+    LimKernels lk{};
     if (limiter) {
-        if (prec != ADERDG_FP64) return fail(ADERDG_E_UNSUPPORTED, "the subcell limiter runs on the FP64 path");
-        if (!ks->lim_fv)
-            return fail(ADERDG_E_UNSUPPORTED, "no subcell limiter for this (pde, dim, N): its shared memory does not fit");
-        if (guess == ADERDG_GUESS_EXTRAP)
-            return fail(ADERDG_E_UNSUPPORTED, "the subcell limiter needs a fresh predictor per step (no EXTRAP guess)");
-        const std::pair<void (*)(KParams), size_t> lk[4] = {
-            {ks->lim_minmax, ks->lim_smem_w}, {ks->lim_detect, ks->lim_smem_w}, {ks->lim_fv, ks->lim_smem},
-            {ks->lim_couple, ks->lim_smem}};
-        for (const auto &k : lk)
-            if (k.second > 48 * 1024 && cudaFuncSetAttribute((const void *)k.first,
-                                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                             (int)k.second) != cudaSuccess)
-                return fail(ADERDG_E_CUDA, "shared memory opt-in of the limiter failed");
+        const char *why = nullptr;
+        const int rc = limiter_kernels(sp.pde.kind, m.dim, sp.N, prec, guess, &lk, &why);
+        if (rc) return fail(rc, why);
     }
     s = Slot();
     s.limiter = limiter;
+    s.lk = lk;
     s.pde = sp.pde.kind;
     s.dim = m.dim;
     s.N = sp.N;
@@ -476,11 +469,12 @@ public:
             if (g.limiter) {
                 // one launch of each limiter kernel for all solves of the group
                 const KernelSet *ks = g.ks;
+                const LimKernels &lk = g.members[0]->lk;  // one (PDE, d, N, precision) per group
                 const unsigned grid = (unsigned)std::min<long long>(g.elems, 152LL * 16);
-                ks->lim_minmax<<<grid, 128, ks->lim_smem_w, st>>>(kp);
-                ks->lim_detect<<<grid, 128, ks->lim_smem_w, st>>>(kp);
-                ks->lim_fv<<<grid, 128, ks->lim_smem, st>>>(kp);
-                ks->lim_couple<<<grid, 128, ks->lim_smem, st>>>(kp);
+                lk.minmax<<<grid, 128, lk.smem_w, st>>>(kp);
+                lk.detect<<<grid, 128, lk.smem_w, st>>>(kp);
+                lk.fv<<<grid, 128, lk.smem, st>>>(kp);
+                lk.couple<<<grid, 128, lk.smem, st>>>(kp);
                 for (const Slot *m : g.members) {
                     k_lim_reset_one<<<1, 32, 0, st>>>(ctl_of(m));
                     KParams k1 = g.kp;

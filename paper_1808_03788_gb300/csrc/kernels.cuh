@@ -1181,17 +1181,23 @@ __global__ void __launch_bounds__(256) k_cfl(const KParams P)
 
 #include "limiter.cuh"
 
-// The limiter's kernels of one (PDE, d, N), referenced by the FP64 instance
-// only (so that each is compiled once); K: 0 minmax, 1 detect, 2 fv, 3 couple.
+// The limiter's kernels of one (PDE, d, N); K: 0 minmax, 1 detect, 2 fv,
+// 3 couple.  Detection and the subcell scheme work on the FP64 state in
+// both precisions and are referenced by the FP64 instance only (so that
+// each is compiled once; an FP32-path handle takes them from there); the
+// coupling replaces the face fluxes of the step's own precision (the FP32
+// path: conservative systems).
 using KernelFn = void (*)(KParams);
 template <class PDE, int DIM, int N, typename T, int K>
 constexpr KernelFn lim_kernel()
 {
-    if constexpr (sizeof(T) == 8 && LimCfg<PDE, DIM, N>::OK) {
+    if constexpr (LimCfg<PDE, DIM, N>::OK && sizeof(T) == 8) {
         if constexpr (K == 0) return &k_lim_minmax<PDE, DIM, N>;
         else if constexpr (K == 1) return &k_lim_detect<PDE, DIM, N>;
         else if constexpr (K == 2) return &k_lim_fv<PDE, DIM, N>;
-        else return &k_lim_couple<PDE, DIM, N>;
+        else return &k_lim_couple<PDE, DIM, N, T>;
+    } else if constexpr (LimCfg<PDE, DIM, N>::OK && !PDE::NCP && K == 3) {
+        return &k_lim_couple<PDE, DIM, N, T>;
     } else {
         return nullptr;
     }

@@ -627,7 +627,10 @@ __global__ void __launch_bounds__(128) k_lim_fv(const KParams P)
     }
 }
 
-template <class PDE, int DIM, int N>
+// T: the compute type of the step whose face fluxes are replaced (double:
+// FP64 trace records; float: the FP32 path's perturbation records about
+// each element's reference state, conservative systems only).
+template <class PDE, int DIM, int N, typename T = double>
 __global__ void __launch_bounds__(128) k_lim_couple(const KParams P)
 {
     using L = LimCfg<PDE, DIM, N>;
@@ -733,6 +736,71 @@ __global__ void __launch_bounds__(128) k_lim_couple(const KParams P)
 #pragma unroll
                                 for (int v = 0; v < M; ++v)
                                     dF[p * M + v] = Ft[v] - (v < PDE::MEV ? hs * J[v] - 0.5 * smax * dq[v] : 0.0);
+                            }
+                            __syncthreads();
+                        } else if constexpr (sizeof(T) == 4) {
+                            double *Fl = sm.dq;  // subcell fluxes on the face [line][v]
+                            for (int l = threadIdx.x; l < L::NLINE; l += blockDim.x)
+                                lim_face<PDE, DIM>(P.pde, gl + (size_t)l * M, gl + (size_t)(L::NLINE + l) * M,
+                                                   gu + (size_t)l * M, gu + (size_t)(L::NLINE + l) * M, d, r, dt,
+                                                   Fl + (size_t)l * M);
+                            __syncthreads();
+                            double *dF = sm.dq + (size_t)L::NLINE * M;  // [p][v]
+                            const T *trf = reinterpret_cast<const T *>(S.tr);
+                            constexpr int LAM = Geom<PDE, DIM, N>::LAM;
+                            for (int p = threadIdx.x; p < NF; p += blockDim.x) {
+                                int pk[3], rem = p;
+#pragma unroll
+                                for (int k = 0; k < DIM - 1; ++k) {
+                                    pk[k] = rem % n;
+                                    rem /= n;
+                                }
+                                // the corrector's FP32 Rusanov flux of this element on this face
+                                // node, formed as the corrector forms it: perturbation traces plus
+                                // the reference differences across the face
+                                const T *Lq = trf + (el * NFACE + (d * 2 + 1) * NF + p) * RS;
+                                const T *Rq = trf + (eu * NFACE + (d * 2 + 0) * NF + p) * RS;
+                                const T smax = tmax(Lq[LAM], Rq[LAM]);
+                                const double *ro = S.ref + e * M, *rn = S.ref + nb * M;
+                                T qf[M], dq[M], dFr[DIM][M];
+#pragma unroll
+                                for (int v = 0; v < M; ++v) {
+                                    qf[v] = narrow<T>(ro[v]);
+                                    dq[v] = narrow<T>(rn[v] - ro[v]);
+                                }
+                                typename PDE::template Ref<T> rr;
+                                PDE::make_ref(P.pde, qf, rr);
+                                PDE::flux_delta(P.pde, rr, dq, dFr);
+                                // plus the element's reference flux, which the perturbation form
+                                // leaves out of both its volume and its surface terms
+                                double Fref[DIM][M];
+                                PDE::flux(P.pde, ro, Fref);
+                                const T sg = side ? T(1) : T(-1);
+#pragma unroll
+                                for (int v = 0; v < M; ++v) {
+                                    T df = dFr[0][v];
+                                    double fr = Fref[0][v];
+#pragma unroll
+                                    for (int k = 1; k < DIM; ++k) {
+                                        df = d == k ? dFr[k][v] : df;
+                                        fr = d == k ? Fref[k][v] : fr;
+                                    }
+                                    T f = T(0.5) * (Lq[M + v] + Rq[M + v]) - T(0.5) * smax * (Rq[v] - Lq[v]);
+                                    f += (side ? T(0.5) : T(-0.5)) * (sg * df) - T(0.5) * smax * (sg * dq[v]);
+                                    double Ft = 0.0;
+                                    for (int l = 0; l < L::NLINE; ++l) {
+                                        double wgt = 1.0;
+                                        int lr = l;
+#pragma unroll
+                                        for (int k = 0; k < DIM - 1; ++k) {
+                                            const int j = lr % S_;
+                                            lr /= S_;
+                                            wgt *= sm.Pr[j * n + pk[k]] / S_ / P.b.w[pk[k]];
+                                        }
+                                        Ft += wgt * Fl[(size_t)l * M + v];
+                                    }
+                                    dF[p * M + v] = Ft - (widen<T>(f) + fr);
+                                }
                             }
                             __syncthreads();
                         } else {

@@ -162,6 +162,7 @@ struct aderdg_s {
     double *ref = nullptr;      // FP32 path: per-element reference records
     void *qprev = nullptr;      // extrapolation guess: last predictor [E][n][NS][M]
     bool limiter = false;       // subcell limiter after every step
+    LimKernels lk{};            // its kernels
     double *u_prev = nullptr;   // limiter: u^n saved before the corrector
     double *lim_mm = nullptr;   // limiter: extreme subcell averages of u^n [E][M][2]
     double *lim_mmc = nullptr;  // limiter: those of the candidate, kept for the next step
@@ -233,11 +234,12 @@ int launch_limiter(aderdg_t *h)
     const KernelSet *ks = h->ks;
     KParams kp = h->kp;
     kp.use_ctl_dt = 1;
+    const LimKernels &lk = h->lk;
     const unsigned grid = (unsigned)std::min<long long>(h->E, 152LL * 16);
-    ks->lim_minmax<<<grid, 128, ks->lim_smem_w, h->stream>>>(kp);
-    ks->lim_detect<<<grid, 128, ks->lim_smem_w, h->stream>>>(kp);
-    ks->lim_fv<<<grid, 128, ks->lim_smem, h->stream>>>(kp);
-    ks->lim_couple<<<grid, 128, ks->lim_smem, h->stream>>>(kp);
+    lk.minmax<<<grid, 128, lk.smem_w, h->stream>>>(kp);
+    lk.detect<<<grid, 128, lk.smem_w, h->stream>>>(kp);
+    lk.fv<<<grid, 128, lk.smem, h->stream>>>(kp);
+    lk.couple<<<grid, 128, lk.smem, h->stream>>>(kp);
     k_lim_reset<<<1, 32, 0, h->stream>>>(h->ctl);
     ks->cfl<<<(unsigned)std::min<long long>(4 * 152, (h->E * h->NS + 255) / 256), 256, 0, h->stream>>>(kp);
     CK(cudaGetLastError());
@@ -393,24 +395,12 @@ int aderdg_create(const aderdg_mesh_t *mesh, int N, int nVar, const aderdg_pde_t
     }
     h->limiter = cfg && cfg->limiter;
     if (h->limiter) {
-        const char *why = prec != ADERDG_FP64             ? "the subcell limiter runs on the FP64 path"
-                          : !ks->lim_fv                     ? "no subcell limiter for this (pde, dim, N): its shared memory does not fit"
-                          : h->guess == ADERDG_GUESS_EXTRAP ? "the subcell limiter needs a fresh predictor per step (no EXTRAP guess)"
-                                                            : nullptr;
-        if (why) {
+        const char *why = nullptr;
+        const int rc = limiter_kernels(pde->kind, mesh->dim, N, prec, h->guess, &h->lk, &why);
+        if (rc) {
             delete h;
-            return fail(ADERDG_E_UNSUPPORTED, why);
+            return fail(rc, why);
         }
-        const std::pair<void (*)(KParams), size_t> lk[4] = {
-            {ks->lim_minmax, ks->lim_smem_w}, {ks->lim_detect, ks->lim_smem_w}, {ks->lim_fv, ks->lim_smem},
-            {ks->lim_couple, ks->lim_smem}};
-        for (const auto &k : lk)
-            if (k.second > 48 * 1024 &&
-                cudaFuncSetAttribute((const void *)k.first, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.second) !=
-                    cudaSuccess) {
-                delete h;
-                return fail(ADERDG_E_CUDA, "shared memory opt-in of the limiter failed");
-            }
     }
     h->picard = (cfg && cfg->picard_iters > 0) ? cfg->picard_iters : default_picard(N, h->guess);
     h->alpha = (cfg && cfg->cfl_alpha > 0) ? cfg->cfl_alpha : default_alpha(N);

@@ -14,6 +14,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <utility>
 
 #include <cuda_runtime.h>
 
@@ -45,6 +46,35 @@ const KernelSet *lookup_kernels(int pde, int dim, int N, int prec)
     ADERDG_INSTANCES(ADERDG_MATCH)
 #undef ADERDG_MATCH
     return nullptr;
+}
+
+int limiter_kernels(int pde, int dim, int N, int prec, int guess, LimKernels *out, const char **why)
+{
+    const KernelSet *k64 = lookup_kernels(pde, dim, N, ADERDG_FP64);
+    const KernelSet *ks = lookup_kernels(pde, dim, N, prec);
+    *why = nullptr;
+    if (guess == ADERDG_GUESS_EXTRAP) {
+        *why = "the subcell limiter needs a fresh predictor per step (no EXTRAP guess)";
+        return ADERDG_E_UNSUPPORTED;
+    }
+    if (!ks || !k64 || !k64->lim_fv) {
+        *why = "no subcell limiter for this (pde, dim, N): its shared memory does not fit";
+        return ADERDG_E_UNSUPPORTED;
+    }
+    if (!ks->lim_couple) {
+        *why = "the subcell limiter on the FP32 path covers conservative systems";
+        return ADERDG_E_UNSUPPORTED;
+    }
+    *out = LimKernels{k64->lim_minmax, k64->lim_detect, k64->lim_fv, ks->lim_couple, k64->lim_smem, k64->lim_smem_w};
+    const std::pair<void (*)(KParams), size_t> lk[4] = {
+        {out->minmax, out->smem_w}, {out->detect, out->smem_w}, {out->fv, out->smem}, {out->couple, out->smem}};
+    for (const auto &k : lk)
+        if (k.second > 48 * 1024 && cudaFuncSetAttribute((const void *)k.first, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                         (int)k.second) != cudaSuccess) {
+            *why = "shared memory opt-in of the limiter failed";
+            return ADERDG_E_CUDA;
+        }
+    return ADERDG_OK;
 }
 }  // namespace aderdg
 

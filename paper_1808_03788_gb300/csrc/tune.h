@@ -25,4 +25,15 @@ const KernelSet *lookup_kernels(int pde, int dim, int N, int prec);
 int resolve_shapes(const KernelSet *ks, int pde, int dim, int N, int prec, const PdeParams &pp, int pred_req,
                    int corr_req, const char *cache, bool extrap, KernelSet *out);
 
+// The subcell limiter's kernels for a step of precision prec (Sec. 2.3):
+// detection and the subcell scheme of the FP64 instance (they work on the
+// FP64 state in both precisions) and the coupling of the step's own
+// precision, with their dynamic shared memory opted in.  Returns ADERDG_OK,
+// or an ADERDG_* status with *why set to the reason.
+struct LimKernels {
+    void (*minmax)(KParams), (*detect)(KParams), (*fv)(KParams), (*couple)(KParams);
+    size_t smem, smem_w;  // per CTA: fv / couple, and minmax / detect
+};
+int limiter_kernels(int pde, int dim, int N, int prec, int guess, LimKernels *out, const char **why);
+
 }  // namespace aderdg

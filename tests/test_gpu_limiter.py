@@ -95,10 +95,14 @@ def test_smooth_data_limited_equals_unlimited():
     np.testing.assert_array_equal(out[0], out[1])
 
 
-@pytest.mark.parametrize("kw", [dict(precision=A.ADERDG_MIXED_FP32), dict(guess=A.ADERDG_GUESS_EXTRAP)])
-def test_limiter_refuses_what_it_does_not_cover(kw):
+def test_limiter_refuses_what_it_does_not_cover():
     with pytest.raises(A.AderdgError) as ei:
-        A.Solver(2, 2, (4, 4), (0, 0), (1, 1), 3, (1.4,), limiter=True, **kw)
+        A.Solver(2, 2, (4, 4), (0, 0), (1, 1), 3, (1.4,), limiter=True, guess=A.ADERDG_GUESS_EXTRAP)
+    assert ei.value.code == A.ADERDG_E_UNSUPPORTED
+    # the FP32 path's coupling covers conservative systems
+    with pytest.raises(A.AderdgError) as ei:
+        A.Solver(A.ADERDG_PDE_DIFFUSE_ELASTICITY, 2, (4, 4), (0, 0), (1, 1), 3, (), limiter=True,
+                 precision=A.ADERDG_MIXED_FP32)
     assert ei.value.code == A.ADERDG_E_UNSUPPORTED
     # subcell arrays beyond a CTA's shared memory
     with pytest.raises(A.AderdgError) as ei:
@@ -294,8 +298,9 @@ def test_limited_batch_equals_solves_alone():
 
 def test_limited_batch_refuses_what_the_limiter_does_not_cover():
     c, _ = _blast2d((4, 4), 3)
+    ci, _ = _inclusion2d((4, 4), 3)
     with pytest.raises(A.AderdgError) as ei:
-        A.Batch([A.make_spec(*c)], limiter=True, precision=A.ADERDG_MIXED_FP32)
+        A.Batch([A.make_spec(*ci)], limiter=True, precision=A.ADERDG_MIXED_FP32)
     assert ei.value.code == A.ADERDG_E_UNSUPPORTED
     with pytest.raises(A.AderdgError) as ei:
         A.Batch([A.make_spec(*c)], limiter=True, guess=A.ADERDG_GUESS_EXTRAP)
@@ -354,3 +359,63 @@ def test_limited_step_at_the_bench_size_matches_oracle(case):
         U = inputs.diffuse_pack(2, [z, z, z], [alpha * box(x, y), alpha * box(y, x)], alpha, 2.0, 1.0, 1.0)
     _, counts = _run_against_oracle(c, U, tuple(params), 2)
     assert min(counts) > 0
+
+
+@pytest.mark.parametrize("make", [_sod, _explosion, lambda: _explosion(3, (6, 6, 6), 2)],
+                         ids=["sod", "explosion2d", "explosion3d"])
+def test_mixed_limited_steps_match_oracle(make):
+    """The limiter on the FP32 path: detection, the subcell scheme and the
+    update work on the FP64 state; the coupling replaces the FP32 path's
+    perturbation-form face fluxes.  Troubled sets equal the FP64 oracle's
+    every step, states within the mixed path's tolerance (relative L2
+    1e-6), mass conserved as on the unlimited FP32 path."""
+    c, U = make()
+    s = _solver(c, precision=A.ADERDG_MIXED_FP32)
+    s.set_state(U)
+    M0 = s.mass()
+    Uo = U.copy()
+    seen = 0
+    for _ in range(10):
+        dt = s.step(1e30, sync_dt=True)
+        Uo, flags_o, cnt_o = oracle.step_limited(c, Uo, dt)
+        flags, cnt = s.troubled()
+        np.testing.assert_array_equal(flags, flags_o)
+        seen = max(seen, cnt)
+        Ug = s.get_state()[0]
+        live = [v for v in range(Uo.shape[-1]) if np.abs(Uo[..., v]).max() > 1e-8]
+        assert l2_rel(c, Ug[..., live], Uo[..., live]) <= 1e-6
+    # the FP32 path's own conservation: FP32 rounding of the reference differences across faces
+    np.testing.assert_allclose(s.mass(), M0, rtol=1e-9, atol=1e-9)
+    s.close()
+    assert seen > 0
+
+
+def test_mixed_limited_reaction_and_elasticity_match_oracle():
+    for pde in (oracle.PDE_ADVECTION, oracle.PDE_ELASTICITY):
+        if pde == oracle.PDE_ADVECTION:
+            c = oracle.make_cfg(2, (16, 8), [0, 0], [1, 1], 3, pde, [1.0, 0.5, 0.0, 1.5], limiter=1)
+            x = oracle.node_coords(c)[..., 0]
+            U = (0.2 + np.where((x > 0.25) & (x < 0.5), 1.0, 0.0))[..., None]
+            params = (1.0, 0.5, 0.0, 1.5)
+        else:
+            c = oracle.make_cfg(3, (8, 3, 3), [0, 0, 0], [1, 1, 1], 2, pde, [1.0, 2.0, 1.0], limiter=1)
+            x = oracle.node_coords(c)[..., 0]
+            U = np.zeros(x.shape + (9,))
+            U[..., 6] = np.where((x > 0.25) & (x < 0.5), 1.0, 0.0)
+            params = (1.0, 2.0, 1.0)
+        dim = c.dim
+        s = A.Solver(pde, dim, [c.cells[d] for d in range(dim)], [0.0] * dim, [1.0] * dim, c.N, params,
+                     limiter=True, precision=A.ADERDG_MIXED_FP32)
+        s.set_state(U)
+        Uo = U.copy()
+        seen = 0
+        for _ in range(8):
+            dt = s.step(1e30, sync_dt=True)
+            Uo, flags_o, cnt = oracle.step_limited(c, Uo, dt)
+            np.testing.assert_array_equal(s.troubled()[0], flags_o)
+            seen = max(seen, cnt)
+            Ug = s.get_state()[0]
+            live = [v for v in range(Uo.shape[-1]) if np.abs(Uo[..., v]).max() > 1e-8]
+            assert l2_rel(c, Ug[..., live], Uo[..., live]) <= 1e-6
+        s.close()
+        assert seen > 0
