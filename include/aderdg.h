@@ -176,13 +176,12 @@ typedef struct {
     int limiter;                /* 1: the a posteriori subcell finite-volume
                                    limiter (Sec. 2.3, eq. pde.nc.fv) after
                                    every aderdg_step / aderdg_advance step:
-                                   FP64 precision for every PDE
+                                   both precisions, every PDE
                                    (non-conservative products and sources
-                                   included), the mixed precision for the
-                                   conservative ones; not with the EXTRAP
-                                   guess; ADERDG_E_UNSUPPORTED otherwise and
-                                   for an instance whose subcell arrays do
-                                   not fit a CTA (3D elasticity N = 4, 3D
+                                   included); not with the EXTRAP guess;
+                                   ADERDG_E_UNSUPPORTED for that and for an
+                                   instance whose subcell arrays do not fit
+                                   a CTA (3D elasticity N = 4, 3D
                                    diffuse-interface elasticity N = 3) */
 } aderdg_config_t;
 

@@ -1185,8 +1185,7 @@ __global__ void __launch_bounds__(256) k_cfl(const KParams P)
 // 3 couple.  Detection and the subcell scheme work on the FP64 state in
 // both precisions and are referenced by the FP64 instance only (so that
 // each is compiled once; an FP32-path handle takes them from there); the
-// coupling replaces the face fluxes of the step's own precision (the FP32
-// path: conservative systems).
+// coupling replaces the face fluxes of the step's own precision.
 using KernelFn = void (*)(KParams);
 template <class PDE, int DIM, int N, typename T, int K>
 constexpr KernelFn lim_kernel()
@@ -1196,7 +1195,7 @@ constexpr KernelFn lim_kernel()
         else if constexpr (K == 1) return &k_lim_detect<PDE, DIM, N>;
         else if constexpr (K == 2) return &k_lim_fv<PDE, DIM, N>;
         else return &k_lim_couple<PDE, DIM, N, T>;
-    } else if constexpr (LimCfg<PDE, DIM, N>::OK && !PDE::NCP && K == 3) {
+    } else if constexpr (LimCfg<PDE, DIM, N>::OK && K == 3) {
         return &k_lim_couple<PDE, DIM, N, T>;
     } else {
         return nullptr;

@@ -629,7 +629,7 @@ __global__ void __launch_bounds__(128) k_lim_fv(const KParams P)
 
 // T: the compute type of the step whose face fluxes are replaced (double:
 // FP64 trace records; float: the FP32 path's perturbation records about
-// each element's reference state, conservative systems only).
+// each element's reference state).
 template <class PDE, int DIM, int N, typename T = double>
 __global__ void __launch_bounds__(128) k_lim_couple(const KParams P)
 {
@@ -707,8 +707,17 @@ __global__ void __launch_bounds__(128) k_lim_couple(const KParams P)
                                     lr /= S_;
                                     wgt *= sm.Pr[j * n + pk[k]] / S_ / P.b.w[pk[k]];
                                 }
-                                const double *qown = side ? tr + (el * NFACE + (d * 2 + 1) * NF + p) * RS
-                                                          : tr + (eu * NFACE + (d * 2 + 0) * NF + p) * RS;
+                                const long long orec = side ? (el * NFACE + (d * 2 + 1) * NF + p) * RS
+                                                            : (eu * NFACE + (d * 2 + 0) * NF + p) * RS;
+                                double qown[M];  // this element's DG trace
+                                if constexpr (sizeof(T) == 4) {  // perturbation about its reference
+                                    const T *qd = reinterpret_cast<const T *>(S.tr) + orec;
+#pragma unroll
+                                    for (int v = 0; v < M; ++v) qown[v] = widen<T>(qd[v]) + S.ref[e * M + v];
+                                } else {
+#pragma unroll
+                                    for (int v = 0; v < M; ++v) qown[v] = tr[orec + v];
+                                }
                                 const double *fs = Fl + (size_t)l * 2 * M;
                                 double dq[M], J[M];
 #pragma unroll
@@ -719,8 +728,6 @@ __global__ void __launch_bounds__(128) k_lim_couple(const KParams P)
                             }
                             __syncthreads();
                             for (int p = threadIdx.x; p < NF; p += blockDim.x) {
-                                const double *Lr = tr + (el * NFACE + (d * 2 + 1) * NF + p) * RS;
-                                const double *Rr = tr + (eu * NFACE + (d * 2 + 0) * NF + p) * RS;
                                 double Ft[M], dq[M], J[M];
 #pragma unroll
                                 for (int v = 0; v < M; ++v) Ft[v] = 0.0;
@@ -728,14 +735,44 @@ __global__ void __launch_bounds__(128) k_lim_couple(const KParams P)
 #pragma unroll
                                     for (int v = 0; v < M; ++v) Ft[v] += Cp[((size_t)p * L::NLINE + l) * M + v];
                                 // the corrector's path-conservative fluctuation on this face node
-                                const double smax = tmax(Lr[Geom<PDE, DIM, N>::LAM], Rr[Geom<PDE, DIM, N>::LAM]);
+                                if constexpr (sizeof(T) == 4) {
+                                    // as the FP32 corrector forms it: perturbation records
+                                    // about each element's reference, the lower state and
+                                    // the jump made absolute with the reference difference
+                                    const T *trf = reinterpret_cast<const T *>(S.tr);
+                                    const T *Lq = trf + (el * NFACE + (d * 2 + 1) * NF + p) * RS;
+                                    const T *Rq = trf + (eu * NFACE + (d * 2 + 0) * NF + p) * RS;
+                                    const T smax = tmax(Lq[Geom<PDE, DIM, N>::LAM], Rq[Geom<PDE, DIM, N>::LAM]);
+                                    const double *ro = S.ref + e * M, *rn = S.ref + nb * M;
+                                    const T sg = side ? T(1) : T(-1);
+                                    T dqf[M], qa[M], Jf[M];
 #pragma unroll
-                                for (int v = 0; v < M; ++v) dq[v] = Rr[v] - Lr[v];
-                                PDE::path_jump(Lr, dq, d, J);
-                                const double hs = side ? 0.5 : -0.5;
+                                    for (int v = 0; v < M; ++v) {
+                                        const T dlq = sg * narrow<T>(rn[v] - ro[v]);
+                                        dqf[v] = Rq[v] - Lq[v];
+                                        qa[v] = Lq[v];
+                                        dqf[v] += dlq;
+                                        qa[v] += narrow<T>(ro[v]) - (side ? T(0) : dlq);
+                                    }
+                                    PDE::path_jump(qa, dqf, d, Jf);
+                                    const T hs = side ? T(0.5) : T(-0.5);
 #pragma unroll
-                                for (int v = 0; v < M; ++v)
-                                    dF[p * M + v] = Ft[v] - (v < PDE::MEV ? hs * J[v] - 0.5 * smax * dq[v] : 0.0);
+                                    for (int v = 0; v < M; ++v) {
+                                        const T f = hs * Jf[v] - T(0.5) * smax * dqf[v];
+                                        dF[p * M + v] = Ft[v] - (v < PDE::MEV ? widen<T>(f) : 0.0);
+                                    }
+                                } else {
+                                    const double *Lr = tr + (el * NFACE + (d * 2 + 1) * NF + p) * RS;
+                                    const double *Rr = tr + (eu * NFACE + (d * 2 + 0) * NF + p) * RS;
+                                    const double smax = tmax(Lr[Geom<PDE, DIM, N>::LAM], Rr[Geom<PDE, DIM, N>::LAM]);
+#pragma unroll
+                                    for (int v = 0; v < M; ++v) dq[v] = Rr[v] - Lr[v];
+                                    PDE::path_jump(Lr, dq, d, J);
+                                    const double hs = side ? 0.5 : -0.5;
+#pragma unroll
+                                    for (int v = 0; v < M; ++v)
+                                        dF[p * M + v] = Ft[v] - (v < PDE::MEV ? hs * J[v] - 0.5 * smax * dq[v] : 0.0);
+                                }
                             }
                             __syncthreads();
                         } else if constexpr (sizeof(T) == 4) {

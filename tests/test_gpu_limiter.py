@@ -99,11 +99,6 @@ def test_limiter_refuses_what_it_does_not_cover():
     with pytest.raises(A.AderdgError) as ei:
         A.Solver(2, 2, (4, 4), (0, 0), (1, 1), 3, (1.4,), limiter=True, guess=A.ADERDG_GUESS_EXTRAP)
     assert ei.value.code == A.ADERDG_E_UNSUPPORTED
-    # the FP32 path's coupling covers conservative systems
-    with pytest.raises(A.AderdgError) as ei:
-        A.Solver(A.ADERDG_PDE_DIFFUSE_ELASTICITY, 2, (4, 4), (0, 0), (1, 1), 3, (), limiter=True,
-                 precision=A.ADERDG_MIXED_FP32)
-    assert ei.value.code == A.ADERDG_E_UNSUPPORTED
     # subcell arrays beyond a CTA's shared memory
     with pytest.raises(A.AderdgError) as ei:
         A.Solver(A.ADERDG_PDE_DIFFUSE_ELASTICITY, 3, (2, 2, 2), (0, 0, 0), (1, 1, 1), 3, (), limiter=True)
@@ -298,10 +293,6 @@ def test_limited_batch_equals_solves_alone():
 
 def test_limited_batch_refuses_what_the_limiter_does_not_cover():
     c, _ = _blast2d((4, 4), 3)
-    ci, _ = _inclusion2d((4, 4), 3)
-    with pytest.raises(A.AderdgError) as ei:
-        A.Batch([A.make_spec(*ci)], limiter=True, precision=A.ADERDG_MIXED_FP32)
-    assert ei.value.code == A.ADERDG_E_UNSUPPORTED
     with pytest.raises(A.AderdgError) as ei:
         A.Batch([A.make_spec(*c)], limiter=True, guess=A.ADERDG_GUESS_EXTRAP)
     assert ei.value.code == A.ADERDG_E_UNSUPPORTED
@@ -419,3 +410,27 @@ def test_mixed_limited_reaction_and_elasticity_match_oracle():
             assert l2_rel(c, Ug[..., live], Uo[..., live]) <= 1e-6
         s.close()
         assert seen > 0
+
+
+def test_mixed_limited_diffuse_interface_matches_oracle():
+    """The path-conservative limiter on the FP32 path: the coupling rebuilds
+    the FP32 corrector's fluctuation (perturbation records made absolute
+    with the reference differences) and takes each element's trace as its
+    reference plus the perturbation.  Troubled sets equal the FP64 oracle's
+    every step, states within 1e-6 relative L2, material fields bitwise."""
+    c = oracle.make_cfg(2, (12, 12), [0, 0], [1, 1], 3, oracle.PDE_DIFFUSE_ELASTICITY, [], limiter=1)
+    (spec, U) = _inclusion2d((12, 12), 3)
+    s = A.Solver(*spec, limiter=True, precision=A.ADERDG_MIXED_FP32)
+    s.set_state(U)
+    Uo = U.copy()
+    seen = 0
+    for _ in range(10):
+        dt = s.step(1e30, sync_dt=True)
+        Uo, flags_o, cnt = oracle.step_limited(c, Uo, dt)
+        np.testing.assert_array_equal(s.troubled()[0], flags_o)
+        seen = max(seen, cnt)
+        Ug = s.get_state()[0]
+        assert l2_rel(c, Ug[..., :5], Uo[..., :5]) <= 1e-6
+    assert np.array_equal(Ug[..., 5:], U[..., 5:])
+    s.close()
+    assert seen > 0
