@@ -142,11 +142,18 @@ def _gpu_id():
 
 
 def _kernel_source_hash() -> str:
+    """Hash of the CUDA/C++ sources with comments removed and whitespace
+    collapsed: committed DRAM counters stay tied to the code they were taken
+    on, not to its comments or layout."""
+    import re
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1808_03788_gb300", "csrc")
     for f in sorted(os.listdir(csrc)):
         if f.endswith((".cu", ".cuh", ".h", ".cpp")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+            src = open(os.path.join(csrc, f), encoding="utf-8").read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            src = re.sub(r"//[^\n]*", "", src)
+            h.update(" ".join(src.split()).encode())  # layout-independent
     return h.hexdigest()[:16]
 
 

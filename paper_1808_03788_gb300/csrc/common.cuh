@@ -127,9 +127,9 @@ struct SolveDesc {
     double *ref;       // FP32 path: reference state per element [E][M]; unused in FP64
     void *qprev;       // extrapolation guess: last predictor [E][n][NS][M] of T
     Control *ctl;
-    // subcell limiter (FP64 handles): u^n saved before the corrector, the
-    // extreme subcell averages of u^n and of the candidate [E][M][2], and
-    // the troubled flags [E]
+    // subcell limiter (either precision; the state is FP64): u^n saved
+    // before the corrector, the extreme subcell averages of u^n and of the
+    // candidate [E][M][2], and the troubled flags [E]
     const double *u_prev;
     double *lim_mm;
     double *lim_mmc;
@@ -522,8 +522,9 @@ struct KernelSet {
     int rf;                     // doubles per element of the FP32 reference record (0: none)
     int ncp;                    // 1: purely non-conservative system (no flux in the records)
     int mx;                     // values per node in the predictor's derivative exchange
-    // subcell limiter kernels (FP64 instances of conservative systems whose
-    // subcell arrays fit one CTA's shared memory; NULL otherwise), 128 threads
+    // subcell limiter kernels of instances whose subcell arrays fit one CTA's
+    // shared memory (NULL otherwise), 128 threads: minmax, detect and fv in
+    // the FP64 instance only, couple in both (its own precision's fluxes)
     void (*lim_minmax)(KParams);
     void (*lim_detect)(KParams);
     void (*lim_fv)(KParams);
