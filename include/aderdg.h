@@ -221,9 +221,16 @@ double aderdg_default_alpha(int N);
 
 /* Create a solver for one periodic mesh, degree N, nVar variables.
  * Supported: d = 2 with N = 1..7 for ADVECTION and EULER; d = 3 with
- * N = 1..4 for ADVECTION, EULER and ELASTICITY.  nVar must equal the PDE's
- * m.  The state is zero and t = 0 until aderdg_set_state.  On failure *out
- * is set to NULL. */
+ * N = 1..4 for ADVECTION, EULER and ELASTICITY; DIFFUSE_ELASTICITY with
+ * N = 2..4 in 2D and N = 2, 3 in 3D (other (PDE, d, N): ADERDG_E_UNSUPPORTED).
+ * The subcell limiter (cfg->limiter) is available for all of them except
+ * 3D ELASTICITY N = 4 and 3D DIFFUSE_ELASTICITY N = 3, whose subcell
+ * arrays do not fit a CTA, and not with the EXTRAP guess.  Limits:
+ * 1 <= cells[d] <= 2^30, E = prod cells[d] <= 2^31, hi > lo, and the
+ * parameter ranges above (Euler gamma > 1; elasticity rho > 0, mu > 0,
+ * lambda + 2 mu > 0; advection kappa >= 0): ADERDG_E_INVAL otherwise.
+ * nVar must equal the PDE's m.  The state is zero and t = 0 until
+ * aderdg_set_state.  On failure *out is set to NULL. */
 int aderdg_create(const aderdg_mesh_t *mesh, int N, int nVar, const aderdg_pde_t *pde,
                   const aderdg_config_t *cfg, aderdg_t **out);
 
@@ -411,24 +418,27 @@ int aderdg_server_stats(aderdg_server_t *s, int64_t *queued, int64_t *active, in
  * from u_in to u_out, caller-owned device buffers in the state layout above
  * (they may be the same buffer).  No handle is created.
  *
- * For callers that cannot call cudaMalloc: code that runs inside a CUDA
- * graph capture or a stream-ordered region where an allocation would
- * synchronise the device or is not permitted, frameworks whose memory must
- * all come from their own allocator, and real-time or embedded hosts that
- * forbid allocation after start-up.  This call allocates no memory at all:
- * the volume term, the face traces and the control block live in one fixed
- * device array of ADERDG_NOALLOC_SCRATCH_BYTES (32 MiB), part of the
- * library module, which every GPU that loads the library holds until the
- * process exits.  Meshes whose scratch would exceed it are rejected with
- * ADERDG_E_INVAL (message gives the size needed).
+ * For callers that cannot call cudaMalloc: frameworks whose device memory
+ * must all come from their own allocator, code paths where cudaMalloc's
+ * implicit device synchronisation is not acceptable, and real-time or
+ * embedded hosts that forbid allocation after start-up.  This call
+ * allocates no memory at all: the volume term, the face traces, the FP32
+ * path's reference states, the step's descriptor and its control block
+ * live in one fixed device array of ADERDG_NOALLOC_SCRATCH_BYTES (32 MiB),
+ * part of the library module, which every GPU that loads the library
+ * holds until the process exits.  The mesh and PDE limits of
+ * aderdg_create apply (ADERDG_E_INVAL); meshes whose scratch would exceed
+ * the array are rejected with ADERDG_E_INVAL too (the message gives the
+ * size needed).
  *
  * The first call on a device looks the array's device address up
  * (cudaGetSymbolAddress, once per device, with that device current); make
  * that first call before any stream capture.  All calls share the array
- * and it keeps the last call's contents: calls whose work overlaps on the
- * GPU (other streams, other host threads) race on it, so serialise them.
- * Work is queued on cuda_stream (NULL: the legacy stream); the call does
- * not synchronise and does not check for non-finite values.  Errors are
+ * and it keeps the last call's contents (each call clears the parts that
+ * must start at zero): calls whose work overlaps on the GPU (other
+ * streams, other host threads) race on it, so serialise them.  Work is
+ * queued on cuda_stream (NULL: the legacy stream); the call does not
+ * synchronise and does not check for non-finite values.  Errors are
  * reported through aderdg_last_error. */
 #define ADERDG_NOALLOC_SCRATCH_BYTES (32u << 20)
 int aderdg_step_noalloc(const aderdg_mesh_t *mesh, int N, int nVar, const aderdg_pde_t *pde,

@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstring>
 
+#include "../../include/aderdg.h"
 #include "basis.h"
 
 namespace aderdg {
@@ -268,6 +269,43 @@ void fill_pde_consts(int kind, PdeParams &P)
         P.c[4] = std::sqrt((P.p[1] + 2.0 * P.p[2]) / P.p[0]);
     }
     for (int i = 0; i < 8; ++i) P.cf[i] = (float)P.c[i];
+}
+
+int check_mesh(const aderdg_mesh_t &mesh, int kind, long long *E, const char **why)
+{
+    auto bad = [&](const char *m) { *why = m; return ADERDG_E_INVAL; };
+    if (mesh.dim < 2 || mesh.dim > 3) return bad("dim must be 2 or 3");
+    if (pde_nvar(kind, mesh.dim) < 0) return bad("unknown pde kind for this dimension");
+    long long e = 1;
+    for (int d = 0; d < mesh.dim; ++d) {
+        // each factor <= 2^30 and the running product <= 2^31: no overflow
+        if (mesh.cells[d] <= 0 || mesh.cells[d] > (1LL << 30)) return bad("bad cell count (1 .. 2^30 per direction)");
+        if (!(mesh.hi[d] > mesh.lo[d]) || !std::isfinite(mesh.hi[d] - mesh.lo[d])) return bad("hi must exceed lo");
+        e *= mesh.cells[d];
+        if (e > (1LL << 31)) return bad("too many elements (at most 2^31)");
+    }
+    *E = e;
+    return ADERDG_OK;
+}
+
+int check_pde_params(const aderdg_pde_t &pde, const char **why)
+{
+    auto bad = [&](const char *m) { *why = m; return ADERDG_E_INVAL; };
+    const double *p = pde.p;
+    if (pde.kind == 1 && !(std::isfinite(p[0]) && std::isfinite(p[1]) && std::isfinite(p[2]) && p[3] >= 0.0 &&
+                           std::isfinite(p[3])))
+        return bad("advection: finite velocity and kappa >= 0 required");
+    if (pde.kind == 2 && !(p[0] > 1.0 && std::isfinite(p[0]))) return bad("gamma must be > 1");
+    if (pde.kind == 3 && !(p[0] > 0 && p[2] > 0 && p[1] + 2 * p[2] > 0 && std::isfinite(p[0]) &&
+                           std::isfinite(p[1]) && std::isfinite(p[2])))
+        return bad("bad elastic parameters (rho > 0, mu > 0, lambda + 2 mu > 0)");
+    return ADERDG_OK;
+}
+
+int check_problem(const aderdg_mesh_t &mesh, const aderdg_pde_t &pde, long long *E, const char **why)
+{
+    const int rc = check_mesh(mesh, pde.kind, E, why);
+    return rc ? rc : check_pde_params(pde, why);
 }
 
 int default_picard(int N, int guess)

@@ -1,5 +1,6 @@
 // Host-side basis construction (see basis.cpp).
 #pragma once
+#include "../../include/aderdg.h"
 #include "common.cuh"
 
 namespace aderdg {
@@ -12,6 +13,16 @@ double default_alpha(int N);
 int default_picard(int N, int guess);
 // number of variables of PDE kind `kind` in dimension dim (-1: unknown)
 int pde_nvar(int kind, int dim);
+// Checks of a problem before any kernel sees it, shared by every entry
+// point that takes a mesh.  check_mesh: dim 2 or 3, a PDE kind defined in
+// that dimension, 1 <= cells[d] <= 2^30 and E = prod cells[d] <= 2^31
+// (checked factor by factor, so the product cannot overflow), hi > lo;
+// sets *E.  check_pde_params: Euler gamma > 1; elasticity rho > 0, mu > 0,
+// lambda + 2 mu > 0; advection kappa >= 0 (all finite).  check_problem:
+// both.  Each returns ADERDG_OK, or ADERDG_E_INVAL with *why set.
+int check_mesh(const aderdg_mesh_t &mesh, int kind, long long *E, const char **why);
+int check_pde_params(const aderdg_pde_t &pde, const char **why);
+int check_problem(const aderdg_mesh_t &mesh, const aderdg_pde_t &pde, long long *E, const char **why);
 // derived constants P.c / P.cf of PDE kind `kind` from P.p (see PdeParams)
 void fill_pde_consts(int kind, PdeParams &P);
 // fill kp.od / kp.of from kp.b

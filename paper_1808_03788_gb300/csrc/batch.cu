@@ -130,17 +130,16 @@ int make_slot(const aderdg_solve_spec_t &sp, int prec, int guess, int picard, do
               bool limiter = false)
 {
     const aderdg_mesh_t &m = sp.mesh;
-    if (m.dim < 2 || m.dim > 3) return fail(ADERDG_E_INVAL, "dim must be 2 or 3");
+    long long E = 0;
+    const char *why = nullptr;
+    if (check_mesh(m, sp.pde.kind, &E, &why)) return fail(ADERDG_E_INVAL, why);
     const int M = nvar_of(sp.pde.kind, m.dim);
-    if (M < 0) return fail(ADERDG_E_INVAL, "unknown pde kind");
     const KernelSet *ks = kernels_for(sp.pde.kind, m.dim, sp.N, prec);
     if (!ks) return fail(ADERDG_E_UNSUPPORTED, "no kernels compiled for this (pde, dim, N)");
-    if (sp.pde.kind == ADERDG_PDE_EULER && !(sp.pde.p[0] > 1.0)) return fail(ADERDG_E_INVAL, "gamma must be > 1");
-    if (sp.pde.kind == ADERDG_PDE_ADVECTION && !(sp.pde.p[3] >= 0.0)) return fail(ADERDG_E_INVAL, "kappa must be >= 0");
+    if (check_pde_params(sp.pde, &why)) return fail(ADERDG_E_INVAL, why);
     if (guess < ADERDG_GUESS_TRIVIAL || guess > ADERDG_GUESS_CERK) return fail(ADERDG_E_INVAL, "bad initial guess");
     LimKernels lk{};
     if (limiter) {
-        const char *why = nullptr;
         const int rc = limiter_kernels(sp.pde.kind, m.dim, sp.N, prec, guess, &lk, &why);
         if (rc) return fail(rc, why);
     }
@@ -159,16 +158,13 @@ int make_slot(const aderdg_solve_spec_t &sp, int prec, int guess, int picard, do
     s.picard = picard > 0 ? picard : default_picard(sp.N, guess);
     s.alpha = alpha > 0 ? alpha : default_alpha(sp.N);
     s.ks = ks;
-    s.E = 1;
+    s.E = E;
     for (int d = 0; d < m.dim; ++d) {
-        if (m.cells[d] <= 0 || m.cells[d] > (1 << 30) || !(m.hi[d] > m.lo[d])) return fail(ADERDG_E_INVAL, "bad mesh");
         s.cells[d] = (int)m.cells[d];
         const double dx = (m.hi[d] - m.lo[d]) / m.cells[d];
         s.inv_dx[d] = 1.0 / dx;
         s.vol *= dx;
-        s.E *= m.cells[d];
     }
-    if (s.E > (1LL << 31)) return fail(ADERDG_E_INVAL, "too many elements");
     for (int i = 0; i < 8; ++i) s.pp.p[i] = sp.pde.p[i];
     fill_pde_consts(s.pde, s.pp);
     s.bytes = slot_bytes(s);

@@ -1,19 +1,20 @@
 // aderdg_step_noalloc: one ADER-DG step (predictor + corrector, given dt)
 // on caller-owned device buffers, with no device allocation at all.
 //
-// Who needs it: callers that cannot call cudaMalloc -- code running inside
-// a CUDA-graph capture or a stream-ordered region where an allocation
-// would synchronise or be illegal, hosts whose memory is owned by another
-// allocator that must see every byte, and embedded/real-time callers that
-// forbid allocation after start-up.  The regular handle API allocates its
-// volume-term and face-trace buffers at aderdg_create; this entry point
-// keeps them in one fixed, file-scope device array instead.
+// Who needs it: callers that cannot call cudaMalloc -- hosts whose device
+// memory is owned by another allocator that must account for every byte,
+// code paths where cudaMalloc's implicit device synchronisation is not
+// acceptable, and embedded or real-time callers that forbid allocation
+// after start-up.  The regular handle API allocates its volume-term and
+// face-trace buffers at aderdg_create; this entry point keeps them in one
+// fixed, file-scope device array instead.
 //
 // The scratch array below (ADERDG_NOALLOC_SCRATCH_BYTES = 32 MiB) is part
 // of the module: every GPU that loads the library holds it until the
 // process exits.  All calls share it and it keeps the last call's
 // contents, so two calls whose work overlaps on the GPU (different streams,
 // or different host threads) race on it; serialise them.
+#include <cmath>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -58,6 +59,19 @@ const KernelSet *kernels_for(int pde, int dim, int N, int prec)
     return lookup_kernels(pde, dim, N, prec);
 }
 
+// Puts the step's descriptor into the scratch (it arrives by value as a
+// kernel argument, so no host buffer has to outlive the call) and clears
+// the control block: the corrector max-reduces wave speeds and ORs flags
+// into it, so it must start at zero on every call.
+static_assert(sizeof(Control) % sizeof(unsigned int) == 0, "control block is cleared word by word");
+__global__ void k_noalloc_setup(const SolveDesc sd, SolveDesc *d_desc, Control *ctl)
+{
+    if (blockIdx.x != 0) return;
+    if (threadIdx.x == 0) *d_desc = sd;
+    unsigned int *c = reinterpret_cast<unsigned int *>(ctl);
+    for (int i = threadIdx.x; i < (int)(sizeof(Control) / sizeof(unsigned int)); i += blockDim.x) c[i] = 0u;
+}
+
 // Device address of the scratch on the current device; looked up once per
 // device (with that device current) and cached.
 int scratch_address(void **out)
@@ -85,18 +99,18 @@ extern "C" int aderdg_step_noalloc(const aderdg_mesh_t *mesh, int N, int nVar, c
                                    double dt, void *cuda_stream)
 {
     if (!mesh || !pde || !u_in || !u_out) return fail(ADERDG_E_INVAL, "NULL argument");
-    if (mesh->dim < 2 || mesh->dim > 3) return fail(ADERDG_E_INVAL, "dim must be 2 or 3");
+    // the same mesh and parameter limits as aderdg_create (cells[d] <= 2^30,
+    // E <= 2^31, PDE parameter ranges), before any size is computed from them
+    long long E = 0;
+    const char *why = nullptr;
+    if (check_mesh(*mesh, pde->kind, &E, &why)) return fail(ADERDG_E_INVAL, why);
     const int m = pde_nvar(pde->kind, mesh->dim);
-    if (m < 0 || nVar != m) return fail(ADERDG_E_INVAL, "unknown pde or nVar mismatch");
+    if (nVar != m) return fail(ADERDG_E_INVAL, "nVar does not match the PDE");
     if (precision != ADERDG_FP64 && precision != ADERDG_MIXED_FP32) return fail(ADERDG_E_INVAL, "bad precision");
-    if (!(dt > 0.0)) return fail(ADERDG_E_INVAL, "dt must be positive");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(ADERDG_E_INVAL, "dt must be positive and finite");
     const KernelSet *ks = (N >= 1 && N <= 9) ? kernels_for(pde->kind, mesh->dim, N, precision) : nullptr;
     if (!ks) return fail(ADERDG_E_UNSUPPORTED, "no kernels compiled for this (pde, dim, N)");
-    long long E = 1;
-    for (int d = 0; d < mesh->dim; ++d) {
-        if (mesh->cells[d] <= 0 || !(mesh->hi[d] > mesh->lo[d])) return fail(ADERDG_E_INVAL, "bad mesh");
-        E *= mesh->cells[d];
-    }
+    if (check_pde_params(*pde, &why)) return fail(ADERDG_E_INVAL, why);
     const int n = N + 1;
     const int NS = ipow(n, mesh->dim), NF = ipow(n, mesh->dim - 1), NREC = mesh->dim * 2 * NF;
     const size_t v_bytes = align256((size_t)E * NS * m * ks->elem_bytes);
@@ -154,19 +168,12 @@ extern "C" int aderdg_step_noalloc(const aderdg_mesh_t *mesh, int N, int nVar, c
                              (int)ks->corr_smem) != cudaSuccess)
         return fail(ADERDG_E_CUDA, "corrector shared-memory opt-in failed");
 
-    // the corrector max-reduces wave speeds and ORs flags into the control
-    // block: it must start at zero on every call
-    cudaError_t e = cudaMemsetAsync(ctl, 0, sizeof(Control), st);
-    if (e != cudaSuccess) return fail(ADERDG_E_CUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
-    // the descriptor is a copy into the scratch, not an allocation; the
-    // pageable source is consumed before cudaMemcpyAsync returns
-    e = cudaMemcpyAsync(d_desc, &sd, sizeof(sd), cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return fail(ADERDG_E_CUDA, std::string("cudaMemcpyAsync: ") + cudaGetErrorString(e));
+    k_noalloc_setup<<<1, 32, 0, st>>>(sd, d_desc, ctl);
     kp.ntiles = (E + ks->pred_epb - 1) / ks->pred_epb;
     ks->predictor<<<(unsigned)kp.ntiles, ks->pred_threads, ks->pred_smem, st>>>(kp);
     kp.ntiles = (E + ks->corr_epb - 1) / ks->corr_epb;
     ks->corrector<<<(unsigned)kp.ntiles, ks->corr_threads, ks->corr_smem, st>>>(kp);
-    e = cudaGetLastError();
+    const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(ADERDG_E_CUDA, std::string("launch: ") + cudaGetErrorString(e));
     return ADERDG_OK;
 }

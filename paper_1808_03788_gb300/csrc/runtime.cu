@@ -353,26 +353,17 @@ int aderdg_create(const aderdg_mesh_t *mesh, int N, int nVar, const aderdg_pde_t
     if (!out) return fail(ADERDG_E_INVAL, "out is NULL");
     *out = nullptr;
     if (!mesh || !pde) return fail(ADERDG_E_INVAL, "mesh/pde is NULL");
-    if (mesh->dim < 2 || mesh->dim > 3) return fail(ADERDG_E_INVAL, "dim must be 2 or 3");
+    long long E = 0;
+    const char *why = nullptr;
+    if (check_mesh(*mesh, pde->kind, &E, &why)) return fail(ADERDG_E_INVAL, why);
     const int m = pde_nvar(pde->kind, mesh->dim);
-    if (m < 0) return fail(ADERDG_E_INVAL, "unknown pde kind");
     if (nVar != m) return fail(ADERDG_E_INVAL, "nVar does not match the PDE");
     if (N < 1 || N > 9) return fail(ADERDG_E_INVAL, "N must be in 1..9");
-    long long E = 1;
-    for (int d = 0; d < mesh->dim; ++d) {
-        if (mesh->cells[d] <= 0 || mesh->cells[d] > (1 << 30)) return fail(ADERDG_E_INVAL, "bad cell count");
-        if (!(mesh->hi[d] > mesh->lo[d])) return fail(ADERDG_E_INVAL, "hi must exceed lo");
-        E *= mesh->cells[d];
-    }
-    if (E > (1LL << 31)) return fail(ADERDG_E_INVAL, "too many elements");
     const int prec = cfg ? cfg->precision : ADERDG_FP64;
     if (prec != ADERDG_FP64 && prec != ADERDG_MIXED_FP32) return fail(ADERDG_E_INVAL, "bad precision");
     const KernelSet *ks = find_kernels(pde->kind, mesh->dim, N, prec);
     if (!ks) return fail(ADERDG_E_UNSUPPORTED, "no kernels compiled for this (pde, dim, N)");
-    if (pde->kind == ADERDG_PDE_EULER && !(pde->p[0] > 1.0)) return fail(ADERDG_E_INVAL, "gamma must be > 1");
-    if (pde->kind == ADERDG_PDE_ELASTICITY && !(pde->p[0] > 0 && pde->p[2] > 0 && pde->p[1] + 2 * pde->p[2] > 0))
-        return fail(ADERDG_E_INVAL, "bad elastic parameters");
-    if (pde->kind == ADERDG_PDE_ADVECTION && !(pde->p[3] >= 0.0)) return fail(ADERDG_E_INVAL, "kappa must be >= 0");
+    if (check_pde_params(*pde, &why)) return fail(ADERDG_E_INVAL, why);
 
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
@@ -395,7 +386,6 @@ int aderdg_create(const aderdg_mesh_t *mesh, int N, int nVar, const aderdg_pde_t
     }
     h->limiter = cfg && cfg->limiter;
     if (h->limiter) {
-        const char *why = nullptr;
         const int rc = limiter_kernels(pde->kind, mesh->dim, N, prec, h->guess, &h->lk, &why);
         if (rc) {
             delete h;

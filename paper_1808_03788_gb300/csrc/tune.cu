@@ -61,8 +61,8 @@ int limiter_kernels(int pde, int dim, int N, int prec, int guess, LimKernels *ou
         *why = "no subcell limiter for this (pde, dim, N): its shared memory does not fit";
         return ADERDG_E_UNSUPPORTED;
     }
-    if (!ks->lim_couple) {
-        *why = "the subcell limiter on the FP32 path covers conservative systems";
+    if (!ks->lim_couple) {  // both instances come from the same LimCfg: not expected to happen
+        *why = "no coupling kernel compiled for this precision of the subcell limiter";
         return ADERDG_E_UNSUPPORTED;
     }
     *out = LimKernels{k64->lim_minmax, k64->lim_detect, k64->lim_fv, ks->lim_couple, k64->lim_smem, k64->lim_smem_w};

@@ -1,10 +1,13 @@
 """The step entry point that allocates nothing (aderdg_step_noalloc), for
-callers that cannot call cudaMalloc (graph capture, foreign allocators,
-allocation-free hosts).  Called through the C ABI on caller-owned device
-buffers, it must give the same state as the handle path
-(aderdg_predictor + aderdg_corrector with the same dt), on two calls in a
-row -- the second reusing the fixed scratch the first one left behind --
-and must refuse meshes whose scratch exceeds its fixed size.
+callers that cannot call cudaMalloc: frameworks whose device memory must
+all come from their own allocator, code that cannot take cudaMalloc's
+implicit device synchronisation, and hosts that forbid allocation after
+start-up.  Called through the C ABI on caller-owned device buffers, it must
+give the same state as the handle path (aderdg_predictor + aderdg_corrector
+with the same dt; the same kernels and shapes, so bit for bit), on two
+calls in a row -- the second reusing the fixed scratch the first one left
+behind -- and must refuse meshes whose scratch exceeds its fixed size and
+meshes or parameters that aderdg_create refuses.
 
 This file is collected last so that a stop at its first failure has
 already run every other test."""
@@ -62,9 +65,9 @@ def test_noalloc_step_matches_handle_path_twice(case):
     torch.cuda.synchronize()
     V1 = u_mid.cpu().numpy()
     V2 = u_out.cpu().numpy()
-    scale = max(1.0, float(np.abs(U2).max()))
-    assert np.abs(V1 - U1).max() <= 1e-12 * scale
-    assert np.abs(V2 - U2).max() <= 1e-12 * scale
+    # the same kernels, shapes and operands as the handle path: bit for bit
+    np.testing.assert_array_equal(V1, U1)
+    np.testing.assert_array_equal(V2, U2)
     # the input buffer is left untouched
     np.testing.assert_array_equal(u_in.cpu().numpy(), U0)
 
@@ -79,3 +82,37 @@ def test_noalloc_rejects_meshes_beyond_the_scratch():
     assert ei.value.code == A.ADERDG_E_INVAL
     assert "too large for the static scratch" in str(ei.value)
     assert str(A.ADERDG_NOALLOC_SCRATCH_BYTES) in str(ei.value)
+
+
+@pytest.mark.parametrize("cells", [
+    (7, 0x6DB6DB6DB6DB6DB7),   # the int64 product wraps to 1
+    (1 << 31, 1),              # one direction beyond 2^30
+    (1 << 16, 1 << 16),        # E = 2^32 > 2^31
+    (0, 4),
+])
+def test_noalloc_rejects_the_mesh_limits_of_create(cells):
+    import torch
+
+    u = torch.zeros(1, dtype=torch.float64, device="cuda")
+    with pytest.raises(A.AderdgError) as ei:
+        A.aderdg_step_noalloc(A.ADERDG_PDE_EULER, 2, cells, (0, 0), (1, 1), 2, (1.4,), u, u, 1e-3)
+    assert ei.value.code == A.ADERDG_E_INVAL
+    assert "scratch" not in str(ei.value)  # refused before any scratch size is formed
+
+
+@pytest.mark.parametrize("pde,dim,params", [
+    (A.ADERDG_PDE_EULER, 2, (1.0,)),               # gamma must exceed 1
+    (A.ADERDG_PDE_ELASTICITY, 3, (1.0, 2.0, 0.0)),  # mu must be positive
+    (A.ADERDG_PDE_ADVECTION, 2, (1.0, 1.0, 0.0, -0.5)),  # kappa must be >= 0
+])
+def test_noalloc_rejects_the_parameters_create_rejects(pde, dim, params):
+    import torch
+
+    u = torch.zeros(1, dtype=torch.float64, device="cuda")
+    cells = (4,) * dim
+    with pytest.raises(A.AderdgError) as ei:
+        A.aderdg_step_noalloc(pde, dim, cells, (0,) * dim, (1,) * dim, 2, params, u, u, 1e-3)
+    assert ei.value.code == A.ADERDG_E_INVAL
+    with pytest.raises(A.AderdgError) as ec:
+        A.Solver(pde, dim, cells, (0,) * dim, (1,) * dim, 2, params)
+    assert ec.value.code == A.ADERDG_E_INVAL
