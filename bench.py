@@ -142,18 +142,24 @@ def _gpu_id():
 
 
 def _kernel_source_hash() -> str:
-    """Hash of the CUDA/C++ sources with comments removed and whitespace
-    collapsed: committed DRAM counters stay tied to the code they were taken
-    on, not to its comments or layout."""
+    """Hash of what the kernels are built from -- the CUDA/C++ sources and the
+    public header with comments removed and whitespace collapsed, and the
+    compiler flags of the build -- so that committed DRAM counters stay tied
+    to the code they were taken on, not to its comments or layout."""
     import re
+
+    from paper_1808_03788_gb300 import build as _b
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1808_03788_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h", ".cpp")):
-            src = open(os.path.join(csrc, f), encoding="utf-8").read()
-            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-            src = re.sub(r"//[^\n]*", "", src)
-            h.update(" ".join(src.split()).encode())  # layout-independent
+    files = [os.path.join(csrc, f) for f in sorted(os.listdir(csrc)) if f.endswith((".cu", ".cuh", ".h", ".cpp"))]
+    files.append(os.path.join(ROOT, "include", "aderdg.h"))
+    for path in files:
+        src = open(path, encoding="utf-8").read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        h.update(" ".join(src.split()).encode())  # layout-independent
+    flags = [f for f in _b.NVFLAGS + _b.CXXFLAGS if not os.path.isabs(f)]  # machine paths excluded
+    h.update(" ".join(flags).encode())
     return h.hexdigest()[:16]
 
 
@@ -454,6 +460,53 @@ def _equal_l2(A, w, steps):
     return out
 
 
+def _end_time(A, torch, vortex_t_end=10.0, elastic_t_end=0.25, shapes=(0, 0)):
+    """The configured end-time runs, FP64 and mixed from the same initial
+    state: the 200^2 N = 4 vortex to t = 10 (its exact solution is the
+    initial state again), with each path's L2 error of rho against the
+    exact vortex and the mixed-vs-FP64 relative L2; and the 64^3 N = 3
+    elastic pulse to t = 0.25, mixed against FP64 (no exact solution).
+    Whole runs through aderdg_advance (graph-replayed steps)."""
+    import numpy as np
+
+    from paper_1808_03788_gb300 import inputs
+    out = {}
+    for key, wname, t_end in (("vortex_t10", "euler2d_vortex_200x200_N4", vortex_t_end),
+                              ("elastic_t0.25", "elastic3d_pulse_64^3_N3", elastic_t_end)):
+        if t_end <= 0:
+            continue
+        w = WORKLOADS[wname]
+        res = {}
+        for name, prec in (("fp64", A.ADERDG_FP64), ("mixed", A.ADERDG_MIXED_FP32)):
+            with A.Solver(w["pde"], w["dim"], w["cells"], w["lo"], w["hi"], w["N"], w["params"], precision=prec,
+                          shapes=shapes) as s:
+                X = s.node_coords(w["lo"], w["hi"])
+                s.set_state(np.ascontiguousarray(_initial_state(w, X)))
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                s.advance(t_end)
+                U, t, k = s.get_state()
+                res[name] = (U, t, k, time.perf_counter() - t0)
+        _, wq = A.aderdg_gl_nodes(w["N"])
+        wn = np.ones(1)
+        for _ in range(w["dim"]):
+            wn = np.kron(wq, wn)
+        vol = np.prod([(w["hi"][d] - w["lo"][d]) / w["cells"][d] for d in range(w["dim"])])
+        W = (vol * wn)[None, :, None]
+        l2 = lambda a: np.sqrt(np.sum(W * a * a, axis=(0, 1)))
+        (U64, t64, k64, s64), (Umx, tmx, kmx, smx) = res["fp64"], res["mixed"]
+        den = l2(U64)
+        rel = l2(Umx - U64) / np.where(den > 0, den, 1.0)
+        o = {"workload": wname, "t_end": t_end, "fp64": {"t": t64, "steps": k64, "wall_s": s64},
+             "mixed": {"t": tmx, "steps": kmx, "wall_s": smx},
+             "mixed_vs_fp64_rel_l2": float(np.max(rel)), "equal_at_1e-6": bool(np.max(rel) <= 1e-6)}
+        if w["ic"] == "vortex":  # X: the node coordinates of the runs above
+            o["fp64"]["l2_err_vs_exact_rho"] = float(l2(U64 - inputs.euler_vortex(X, t=t64))[0])
+            o["mixed"]["l2_err_vs_exact_rho"] = float(l2(Umx - inputs.euler_vortex(X, t=tmx))[0])
+        out[key] = o
+    return out
+
+
 def _elastic(A, torch, stream, flush, steps, shapes=(0, 0), workload="elastic3d_pulse_64^3_N3"):
     """A 3D elasticity workload -- the conservative system (64^3 elements,
     N = 3, 9 variables, Gaussian velocity pulse) or the diffuse-interface
@@ -559,7 +612,10 @@ def _served(A, requests, rate, seed=1808, shapes=(0, 0)):
     work = sum(r["steps"] * d for r, d in results.values())
     ok = sum(1 for r, _ in results.values() if r["status"] == 0)
     return {"requests": len(tickets), "ok": ok, "rate_per_s": rate, "p50_latency_s": float(np.percentile(lat, 50)),
-            "p99_latency_s": float(np.percentile(lat, 99)), "mean_queue_s":
+            "p99_latency_s": float(np.percentile(lat, 99)), "latency_samples": int(lat.size),
+            "p99_note": ("a tail estimate over %d samples" % lat.size) if lat.size >= 100 else
+                        ("= the maximum of %d samples, not a tail estimate" % lat.size),
+            "mean_queue_s":
                 float(np.mean([r["queue_s"] for r, _ in results.values()])),
             "makespan_s": makespan, "dof_updates": work, "value": work / makespan, "unit": UNIT,
             "dtype": "f32+f64"}
@@ -662,6 +718,8 @@ def run_ours(args, w, rank, world):
                            "roofline": _roofline(i2, p2, other, probe, args.workload),
                            "kernels": _kernels(i2, p2, c2, hbm)}
         variants["equal_l2"] = _equal_l2(A, w, args.l2_steps)
+        if args.end_time:
+            variants["end_time"] = _end_time(A, torch, shapes=shapes)
         if args.limiter_steps > 0 and w["pde"] == 2:
             variants["limiter"] = _limiter(A, torch, w, stream, flush, args.limiter_steps, args.warmup)
         if args.guess_variant:
@@ -747,6 +805,8 @@ def main():
     ap.add_argument("--served-rate", type=float, default=200.0)
     ap.add_argument("--served-scaled", type=int, default=12,
                     help="requests of a second served run at 80 %% of the measured capacity (0: skip)")
+    ap.add_argument("--no-end-time", dest="end_time", action="store_false",
+                    help="skip the configured end-time runs (vortex to t = 10, elastic pulse to t = 0.25)")
     ap.add_argument("--no-guess-variant", dest="guess_variant", action="store_false",
                     help="skip the initial-guess variants (third order, extrapolation)")
     ap.add_argument("--shapes", default="auto",

@@ -290,6 +290,47 @@ def test_mixed_full_run_euler_vortex():
     assert l2_rel(cfg, Ug, Uo) <= 1e-6
 
 
+def test_mixed_full_run_advection_config():
+    """The advection configuration (16x16, N = 3, a = (1, 1)) to t = 1 on
+    the FP32 path: the same 342 steps as the oracle and within the mixed
+    tolerance of its FP64 result."""
+    case = (1, 2, 3, (16, 16), 1.0, (1.0, 1.0))
+    cfg, s = _pair(*case, precision=A.ADERDG_MIXED_FP32)
+    U0 = inputs.advection_sine(oracle.node_coords(cfg))
+    Uo, to, ko, _ = oracle.run(cfg, U0, t_end=1.0)
+    s.set_state(U0)
+    s.advance(1.0)
+    Ug, t, k = s.get_state()
+    assert (t, k) == (to, ko) == (1.0, 342)
+    assert l2_rel(cfg, Ug, Uo) <= 1e-6
+
+
+def test_mixed_and_fp64_vortex_to_the_end_time():
+    """The vortex to t = 10 (a full period: the exact solution is the
+    initial state again) on 40^2 elements, N = 4: the FP32 path stays within
+    1e-6 relative L2 of the FP64 path over the whole run (about 3.6k steps),
+    and the two L2 errors of rho against the exact solution differ by less
+    than that tolerance times the norm of the exact rho (at this resolution
+    the error is ~9e-7 and the FP32 rounding of 3.6k steps adds ~3e-7)."""
+    from helpers import l2_abs
+    cells, N = (40, 40), 4
+    res = {}
+    for prec in (A.ADERDG_FP64, A.ADERDG_MIXED_FP32):
+        cfg, s = _pair(2, 2, N, cells, 10.0, (GAMMA,), precision=prec)
+        X = oracle.node_coords(cfg)
+        s.set_state(inputs.euler_vortex(X))
+        s.advance(10.0)
+        res[prec] = s.get_state()
+    (U64, t64, k64), (Umx, tmx, kmx) = res[A.ADERDG_FP64], res[A.ADERDG_MIXED_FP32]
+    assert t64 == tmx == 10.0 and k64 > 3000 and abs(k64 - kmx) <= 1
+    assert l2_rel(cfg, Umx, U64) <= 1e-6
+    e64 = l2_abs(cfg, U64, inputs.euler_vortex(X, t=t64))[0]
+    emx = l2_abs(cfg, Umx, inputs.euler_vortex(X, t=tmx))[0]
+    rho_norm = l2_abs(cfg, inputs.euler_vortex(X, t=t64), 0 * U64)[0]
+    assert abs(emx - e64) <= 1e-6 * rho_norm, (e64, emx, rho_norm)
+    assert e64 < 1e-5 and emx < 1e-5, (e64, emx)
+
+
 def test_mixed_tracks_fp64_over_a_long_run():
     """The FP32 predictor works on perturbations about a per-element FP64
     reference, so its rounding stays far below the discretisation error:
