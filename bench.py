@@ -507,6 +507,47 @@ def _end_time(A, torch, vortex_t_end=10.0, elastic_t_end=0.25, shapes=(0, 0)):
     return out
 
 
+def _partitioned(A, torch, w, stream, flush, steps, warmup, parts=(2, 2), shapes=(0, 0)):
+    """The headline mesh split into parts blocks on this GPU (the
+    distributed-memory step of Sec. 2.2: boundary predictor first, face
+    traces exchanged while the interior predictor runs, one wave-speed
+    reduction): ms per step next to the undivided solver's, both timed like
+    the headline, and whether the two states are bitwise equal after the
+    same steps."""
+    import numpy as np
+    out = {"parts": list(parts)}
+    states = {}
+    for name, prec in (("fp64", A.ADERDG_FP64), ("mixed", A.ADERDG_MIXED_FP32)):
+        for kind in ("single", "partitioned"):
+            extra = {"parts": parts} if kind == "partitioned" else {}
+            cls = A.Partitioned if kind == "partitioned" else A.Solver
+            with cls(w["pde"], w["dim"], w["cells"], w["lo"], w["hi"], w["N"], w["params"], precision=prec,
+                     stream=stream.cuda_stream, shapes=shapes, **extra) as s:
+                X = s.node_coords(w["lo"], w["hi"])
+                s.set_state(np.ascontiguousarray(_initial_state(w, X)))
+                with torch.cuda.stream(stream):
+                    for _ in range(warmup):
+                        flush.zero_()
+                        s.step(1e30)
+                    torch.cuda.synchronize()
+                    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                          for _ in range(steps)]
+                    for a, b in ev:
+                        flush.zero_()
+                        a.record(stream)
+                        s.step(1e30)
+                        b.record(stream)
+                    torch.cuda.synchronize()
+                ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+                states[(name, kind)] = s.get_state()[0]
+                rec = {"ms_per_step": ms, "value": w["dofs"] / (ms / 1e3)}
+                if kind == "partitioned":
+                    rec.update(s.dd_info())
+                out.setdefault(name, {})[kind] = rec
+        out[name]["bitwise_equal"] = bool(np.array_equal(states[(name, "single")], states[(name, "partitioned")]))
+    return out
+
+
 def _elastic(A, torch, stream, flush, steps, shapes=(0, 0), workload="elastic3d_pulse_64^3_N3"):
     """A 3D elasticity workload -- the conservative system (64^3 elements,
     N = 3, 9 variables, Gaussian velocity pulse) or the diffuse-interface
@@ -720,6 +761,9 @@ def run_ours(args, w, rank, world):
         variants["equal_l2"] = _equal_l2(A, w, args.l2_steps)
         if args.end_time:
             variants["end_time"] = _end_time(A, torch, shapes=shapes)
+        if args.dd_steps > 0:
+            variants["partitioned"] = _partitioned(A, torch, w, stream, flush, args.dd_steps, args.warmup,
+                                                   shapes=shapes)
         if args.limiter_steps > 0 and w["pde"] == 2:
             variants["limiter"] = _limiter(A, torch, w, stream, flush, args.limiter_steps, args.warmup)
         if args.guess_variant:
@@ -805,6 +849,8 @@ def main():
     ap.add_argument("--served-rate", type=float, default=200.0)
     ap.add_argument("--served-scaled", type=int, default=12,
                     help="requests of a second served run at 80 %% of the measured capacity (0: skip)")
+    ap.add_argument("--dd-steps", type=int, default=20,
+                    help="timed steps of the partitioned (2 x 2 blocks) variant (0: skip)")
     ap.add_argument("--no-end-time", dest="end_time", action="store_false",
                     help="skip the configured end-time runs (vortex to t = 10, elastic pulse to t = 0.25)")
     ap.add_argument("--no-guess-variant", dest="guess_variant", action="store_false",

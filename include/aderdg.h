@@ -128,12 +128,16 @@ extern "C" {
  * Shapes 0-2 of both are CTA sizes (default, half, double).  Predictor
  * shapes 3 and 4 are, for 2D FP32 solves whose n x n x m space-time plane
  * fits the registers, a kernel in which each thread owns that plane (about
- * 128 and 256 threads per CTA); elsewhere they repeat shapes 0 and 2.  For
- * a given (PDE, d, N, precision) every shape computes bit-identical results
- * except that the two predictor kernels round differently (both within
- * the path's tolerance); only the speed differs.  ADERDG_SHAPE_AUTOTUNE
- * picks the shapes measured fastest on the current device. */
-#define ADERDG_NUM_PRED_SHAPES 5
+ * 128 and 256 threads per CTA); elsewhere they repeat shapes 0 and 2.
+ * Predictor shapes 5 and 6 are shapes 0 and 1 with the derivative
+ * contractions of the Picard iterations on the tensor cores (mma.sync
+ * TF32 with three split products, FP32 accumulation) on the FP32 path; in
+ * FP64 they repeat shapes 0 and 1.  For a given (PDE, d, N, precision)
+ * every shape computes bit-identical results within each of these three
+ * kernel families; the families round differently (all within the path's
+ * tolerance); only the speed differs.  ADERDG_SHAPE_AUTOTUNE picks the
+ * shapes measured fastest on the current device. */
+#define ADERDG_NUM_PRED_SHAPES 7
 #define ADERDG_NUM_CORR_SHAPES 3
 #define ADERDG_SHAPE_DEFAULT 0
 #define ADERDG_SHAPE_AUTOTUNE (-1)
@@ -409,6 +413,71 @@ int aderdg_cancel(aderdg_server_t *s, uint64_t ticket);
 /* Server counters: queued, active, finished, device bytes in use. */
 int aderdg_server_stats(aderdg_server_t *s, int64_t *queued, int64_t *active, int64_t *finished,
                         size_t *bytes_in_use);
+
+/* ---- domain decomposition --------------------------------------------------
+ * The distributed-memory structure of the scheme (Sec. 2.2, the closing
+ * remarks on MPI; Sec. 4): the periodic mesh is split into a
+ * parts[0] x parts[1] (x parts[2]) grid of blocks; each step, every block
+ * runs the predictor on its boundary elements first (those with a face on
+ * a split block boundary), sends their time-averaged face traces to the
+ * neighbouring blocks while the predictor of its interior elements runs,
+ * and then runs the corrector on the received traces; the time step comes
+ * from one global max-reduction of the per-direction wave speeds, so every
+ * block takes the dt of the undivided mesh.
+ *
+ * Plan (host logic, no device needed).  Blocks are numbered x-fastest over
+ * the block grid; along a direction of C cells and p blocks, the first
+ * C mod p blocks take one cell more.  1 <= parts[d] <= cells[d], at most
+ * 4096 blocks.  Elements inside a block are numbered x-fastest. */
+typedef struct {
+    int rank;                 /* block index */
+    int coords[3];            /* position in the block grid */
+    int64_t offset[3];        /* first global cell per direction */
+    int64_t cells[3];         /* cells per direction (1 beyond dim) */
+    int neighbour[3][2];      /* block across face (d, side: 0 lower, 1 upper);
+                                 -1 if direction d is not split (it then wraps
+                                 periodically inside the block) */
+    int64_t elements;         /* cells[0] cells[1] cells[2] */
+    int64_t boundary_elements;/* elements with a face on a split boundary */
+    int64_t face_chunks[3][2];/* face-trace chunks sent across (and received
+                                 on) face (d, side): elements / cells[d], or 0 */
+} aderdg_dd_block_t;
+
+int aderdg_dd_plan(const aderdg_mesh_t *mesh, const int parts[3], int rank, aderdg_dd_block_t *block);
+
+/* The elements of block `rank` on its face (d, side), in the order of the
+ * chunks it sends across that face: j = the element's index over the other
+ * directions, lowest fastest (the receiver stores chunk j at the same
+ * transverse position).  elements: face_chunks[d][side] entries (host). */
+int aderdg_dd_face_elements(const aderdg_mesh_t *mesh, const int parts[3], int rank, int d, int side,
+                            int64_t *elements);
+
+/* The boundary elements (boundary_elements entries) and the interior ones
+ * (elements - boundary_elements) of block `rank`, each increasing; either
+ * pointer may be NULL (host). */
+int aderdg_dd_element_lists(const aderdg_mesh_t *mesh, const int parts[3], int rank, int64_t *boundary,
+                            int64_t *interior);
+
+/* A partitioned solver with every block on the current GPU: the exchange
+ * stores each block's boundary chunks into its neighbours' halo buffers
+ * (on a second stream that overlaps the interior predictor) and the
+ * reduction runs over the blocks' control blocks.  The results are bitwise
+ * those of aderdg_create + aderdg_step on the undivided mesh.  Arguments as
+ * for aderdg_create (cfg->limiter: ADERDG_E_UNSUPPORTED); states are passed
+ * in the global layout and scattered to / gathered from the blocks. */
+typedef struct aderdg_dd_s aderdg_dd_t;
+int aderdg_dd_create(const aderdg_mesh_t *mesh, int N, int nVar, const aderdg_pde_t *pde,
+                     const aderdg_config_t *cfg, const int parts[3], aderdg_dd_t **out);
+int aderdg_dd_destroy(aderdg_dd_t *dd);
+int aderdg_dd_set_state(aderdg_dd_t *dd, const double *u, int where, double t);
+int aderdg_dd_get_state(aderdg_dd_t *dd, double *u, int where, double *t, int64_t *step);
+/* as aderdg_step / aderdg_advance on the undivided mesh */
+int aderdg_dd_step(aderdg_dd_t *dd, double t_end, double *dt_taken);
+int aderdg_dd_advance(aderdg_dd_t *dd, double t_end, int64_t max_steps);
+/* blocks, boundary elements over all blocks, bytes exchanged per step,
+ * device bytes held; any pointer may be NULL */
+int aderdg_dd_info(const aderdg_dd_t *dd, int *blocks, int64_t *boundary_elements, size_t *halo_bytes_per_step,
+                   size_t *device_bytes);
 
 /* ---- a step that allocates nothing ---------------------------------------
  * The paper has no counterpart; this is an integration aid of the library.

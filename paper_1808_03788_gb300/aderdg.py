@@ -30,7 +30,7 @@ ADERDG_E_CANCELLED = -8
 ADERDG_PDE_ADVECTION, ADERDG_PDE_EULER, ADERDG_PDE_ELASTICITY, ADERDG_PDE_DIFFUSE_ELASTICITY = 1, 2, 3, 4
 ADERDG_FP64, ADERDG_MIXED_FP32 = 0, 1
 ADERDG_HOST, ADERDG_DEVICE = 0, 1
-ADERDG_NUM_PRED_SHAPES, ADERDG_NUM_CORR_SHAPES = 5, 3
+ADERDG_NUM_PRED_SHAPES, ADERDG_NUM_CORR_SHAPES = 7, 3
 ADERDG_SHAPE_DEFAULT, ADERDG_SHAPE_AUTOTUNE = 0, -1
 ADERDG_TUNE_FORCE = 1
 ADERDG_GUESS_TRIVIAL, ADERDG_GUESS_ORDER2, ADERDG_GUESS_ORDER3, ADERDG_GUESS_EXTRAP, ADERDG_GUESS_CERK = 0, 1, 2, 3, 4
@@ -74,6 +74,12 @@ class aderdg_info_t(C.Structure):
                 ("pred_shape", C.c_int), ("pred_threads", C.c_int), ("pred_epb", C.c_int),
                 ("corr_shape", C.c_int), ("corr_threads", C.c_int), ("corr_epb", C.c_int),
                 ("initial_guess", C.c_int)]
+
+
+class aderdg_dd_block_t(C.Structure):
+    _fields_ = [("rank", C.c_int), ("coords", C.c_int * 3), ("offset", C.c_int64 * 3), ("cells", C.c_int64 * 3),
+                ("neighbour", (C.c_int * 2) * 3), ("elements", C.c_int64), ("boundary_elements", C.c_int64),
+                ("face_chunks", (C.c_int64 * 2) * 3)]
 
 
 class aderdg_solve_spec_t(C.Structure):
@@ -148,6 +154,21 @@ _SIGS = {
                                       C.POINTER(C.c_size_t)]),
     "aderdg_step_noalloc": (C.c_int, [C.POINTER(aderdg_mesh_t), C.c_int, C.c_int, C.POINTER(aderdg_pde_t),
                                       C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_double, C.c_void_p]),
+    "aderdg_dd_plan": (C.c_int, [C.POINTER(aderdg_mesh_t), C.POINTER(C.c_int), C.c_int,
+                                 C.POINTER(aderdg_dd_block_t)]),
+    "aderdg_dd_face_elements": (C.c_int, [C.POINTER(aderdg_mesh_t), C.POINTER(C.c_int), C.c_int, C.c_int, C.c_int,
+                                          C.c_void_p]),
+    "aderdg_dd_element_lists": (C.c_int, [C.POINTER(aderdg_mesh_t), C.POINTER(C.c_int), C.c_int, C.c_void_p,
+                                          C.c_void_p]),
+    "aderdg_dd_create": (C.c_int, [C.POINTER(aderdg_mesh_t), C.c_int, C.c_int, C.POINTER(aderdg_pde_t),
+                                   C.POINTER(aderdg_config_t), C.POINTER(C.c_int), C.POINTER(_H)]),
+    "aderdg_dd_destroy": (C.c_int, [_H]),
+    "aderdg_dd_set_state": (C.c_int, [_H, C.c_void_p, C.c_int, C.c_double]),
+    "aderdg_dd_get_state": (C.c_int, [_H, C.c_void_p, C.c_int, _DP, C.POINTER(C.c_int64)]),
+    "aderdg_dd_step": (C.c_int, [_H, C.c_double, _DP]),
+    "aderdg_dd_advance": (C.c_int, [_H, C.c_double, C.c_int64]),
+    "aderdg_dd_info": (C.c_int, [_H, C.POINTER(C.c_int), C.POINTER(C.c_int64), C.POINTER(C.c_size_t),
+                                 C.POINTER(C.c_size_t)]),
 }
 
 
@@ -506,6 +527,143 @@ def aderdg_step_noalloc(pde: int, dim: int, cells, lo, hi, N: int, params, u_in,
     _check(load().aderdg_step_noalloc(C.byref(mesh), N, nvar(pde, dim), C.byref(p), precision, picard,
                                       C.c_void_p(u_in.data_ptr()), C.c_void_p(u_out.data_ptr()),
                                       float(dt), C.c_void_p(int(stream) if stream else 0)))
+
+
+# ---- domain decomposition --------------------------------------------------------
+
+def _mesh(dim, cells, lo, hi) -> aderdg_mesh_t:
+    mesh = aderdg_mesh_t()
+    mesh.dim = dim
+    for d in range(3):
+        mesh.cells[d] = int(cells[d]) if d < dim else 1
+        mesh.lo[d] = float(lo[d]) if d < dim else 0.0
+        mesh.hi[d] = float(hi[d]) if d < dim else 1.0
+    return mesh
+
+
+def _parts(parts):
+    a = (C.c_int * 3)()
+    for d in range(3):
+        a[d] = int(parts[d]) if d < len(parts) else 1
+    return a
+
+
+def aderdg_dd_plan(dim: int, cells, parts, rank: int) -> dict:
+    """Block `rank` of the partition (host logic; no device needed)."""
+    b = aderdg_dd_block_t()
+    _check(load().aderdg_dd_plan(C.byref(_mesh(dim, cells, (0,) * 3, (1,) * 3)), _parts(parts), rank, C.byref(b)))
+    return {"rank": b.rank, "coords": list(b.coords), "offset": list(b.offset), "cells": list(b.cells),
+            "neighbour": [list(b.neighbour[d]) for d in range(3)], "elements": b.elements,
+            "boundary_elements": b.boundary_elements, "face_chunks": [list(b.face_chunks[d]) for d in range(3)]}
+
+
+def aderdg_dd_face_elements(dim: int, cells, parts, rank: int, d: int, side: int) -> np.ndarray:
+    """Block-local elements on face (d, side), in the order of the chunks sent across it."""
+    n = aderdg_dd_plan(dim, cells, parts, rank)["face_chunks"][d][side]
+    out = np.zeros(max(1, n), dtype=np.int64)
+    _check(load().aderdg_dd_face_elements(C.byref(_mesh(dim, cells, (0,) * 3, (1,) * 3)), _parts(parts), rank, d,
+                                          side, out.ctypes.data))
+    return out[:n]
+
+
+def aderdg_dd_element_lists(dim: int, cells, parts, rank: int):
+    """(boundary, interior) block-local element lists of block `rank`."""
+    b = aderdg_dd_plan(dim, cells, parts, rank)
+    bl = np.zeros(max(1, b["boundary_elements"]), dtype=np.int64)
+    il = np.zeros(max(1, b["elements"] - b["boundary_elements"]), dtype=np.int64)
+    _check(load().aderdg_dd_element_lists(C.byref(_mesh(dim, cells, (0,) * 3, (1,) * 3)), _parts(parts), rank,
+                                          bl.ctypes.data, il.ctypes.data))
+    return bl[:b["boundary_elements"]], il[:b["elements"] - b["boundary_elements"]]
+
+
+class Partitioned(Solver):
+    """One solve on a mesh split into parts[0] x parts[1] (x parts[2]) blocks
+    (aderdg_dd_* of the C ABI): boundary-first predictor, face-trace
+    exchange overlapping the interior predictor, global wave-speed
+    reduction.  States are in the global layout, as for Solver."""
+
+    def __init__(self, pde: int, dim: int, cells, lo, hi, N: int, params=(), parts=(2, 2, 1),
+                 precision: int = ADERDG_FP64, picard: int = 0, alpha: float = 0.0, stream=None,
+                 torch_alloc: bool = True, shapes=(0, 0), tune_cache=None, guess: int = ADERDG_GUESS_TRIVIAL):
+        L = load()
+        self.dim, self.N, self.pde = dim, N, pde
+        self.m = nvar(pde, dim)
+        self.n = N + 1
+        self.ns = self.n ** dim
+        self.cells = tuple(int(c) for c in cells[:dim])
+        self.E = int(np.prod(self.cells))
+        self.parts = tuple(int(p) for p in parts[:dim])
+        mesh = _mesh(dim, cells, lo, hi)
+        p = aderdg_pde_t()
+        p.kind = pde
+        for i, v in enumerate(params):
+            p.p[i] = float(v)
+        cfg = aderdg_config_t()
+        cfg.precision = precision
+        cfg.picard_iters = picard
+        cfg.cfl_alpha = alpha
+        cfg.initial_guess = guess
+        _set_shapes(cfg, shapes, tune_cache)
+        self._alloc = None
+        if stream is not None:
+            cfg.cuda_stream = C.c_void_p(int(stream))
+        if torch_alloc:
+            self._alloc = _TorchAllocator()
+            cfg.alloc = C.pointer(self._alloc.struct)
+        self._h = _H()
+        _check(L.aderdg_dd_create(C.byref(mesh), N, self.m, C.byref(p), C.byref(cfg), _parts(parts),
+                                  C.byref(self._h)))
+        self._L = L
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._L.aderdg_dd_destroy(self._h)
+            self._h = _H()
+
+    def set_state(self, u, t: float = 0.0):
+        if hasattr(u, "data_ptr"):
+            assert u.dtype.itemsize == 8 and u.is_contiguous() and u.numel() == self.E * self.ns * self.m
+            _torch_ready()
+            _check(self._L.aderdg_dd_set_state(self._h, C.c_void_p(u.data_ptr()), ADERDG_DEVICE, float(t)))
+            return
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        assert u.size == self.E * self.ns * self.m
+        _check(self._L.aderdg_dd_set_state(self._h, u.ctypes.data, ADERDG_HOST, float(t)))
+
+    def get_state(self, out=None, check=True):
+        t = C.c_double(0)
+        k = C.c_int64(0)
+        u = np.empty((self.E, self.ns, self.m)) if out is None else out
+        if hasattr(u, "data_ptr"):
+            rc = self._L.aderdg_dd_get_state(self._h, C.c_void_p(u.data_ptr()), ADERDG_DEVICE, C.byref(t), C.byref(k))
+        else:
+            rc = self._L.aderdg_dd_get_state(self._h, u.ctypes.data, ADERDG_HOST, C.byref(t), C.byref(k))
+        if check:
+            _check(rc)
+        return u, t.value, k.value
+
+    def step(self, t_end: float, sync_dt: bool = False):
+        if sync_dt:
+            dt = C.c_double(0)
+            _check(self._L.aderdg_dd_step(self._h, float(t_end), C.byref(dt)))
+            return dt.value
+        _check(self._L.aderdg_dd_step(self._h, float(t_end), None))
+        return None
+
+    def advance(self, t_end: float, max_steps: int = 2 ** 62):
+        _check(self._L.aderdg_dd_advance(self._h, float(t_end), int(max_steps)))
+
+    def dd_info(self) -> dict:
+        k, nb, hb, db = C.c_int(0), C.c_int64(0), C.c_size_t(0), C.c_size_t(0)
+        _check(self._L.aderdg_dd_info(self._h, C.byref(k), C.byref(nb), C.byref(hb), C.byref(db)))
+        return {"blocks": k.value, "boundary_elements": nb.value, "halo_bytes_per_step": hb.value,
+                "device_bytes": db.value}
+
+    def _unsupported(self, *a, **k):
+        raise AderdgError(ADERDG_E_UNSUPPORTED, "not available on a partitioned solver")
+
+    predictor = corrector = troubled = predictor_outputs = cfl_dt = mass = sync = _unsupported
+    profile = profile_read = info = _unsupported
 
 
 # ---- batched solves -------------------------------------------------------------

@@ -135,6 +135,17 @@ struct SolveDesc {
     double *lim_mmc;
     int *lim_flags;
     int *lim_list;  // the troubled elements of the step, in detection order [ctl->lim_count]
+    // domain decomposition (a block of a partitioned mesh, see partition.cu):
+    // elist: the predictor's elements, E indices into the block (its
+    // boundary or its interior elements); NULL: elements 0 .. E-1.
+    // halo_tr[d][side]: for the corrector, the face chunks [j][NF][RS] of the
+    // neighbouring block across this block's face (d, side), j the element's
+    // index over the other directions (lowest fastest), and halo_ref[d][side]
+    // their FP32-path reference states [j][M]; NULL: the direction is not
+    // split and wraps periodically inside the block.
+    const int *elist;
+    const void *halo_tr[3][2];
+    const double *halo_ref[3][2];
 };
 
 inline void fill_desc_spacing(SolveDesc &d)
@@ -503,7 +514,7 @@ struct TileShape {
 
 // Number of compiled shapes of the predictor and the corrector (shape 0 is
 // the default).
-constexpr int NSHAPE_P = 5;
+constexpr int NSHAPE_P = 7;
 constexpr int NSHAPE_C = 3;
 
 // Host-visible description of the compiled kernels of one (PDE, d, N,

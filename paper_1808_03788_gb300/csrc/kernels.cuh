@@ -207,7 +207,11 @@ struct PredCfg {
     static constexpr int TARGET0 = sizeof(T) == 8 ? 128 : 256;
     static constexpr int MINB0 = PDE::NCP ? (sizeof(T) == 8 ? 1 : 2)
                                  : sizeof(T) == 8 ? (n * M < 24 ? 3 : 2) : ((n * M <= 20 || (M == 9 && n <= 4)) ? 3 : 2);
-    static constexpr int TARGET = TS == 1 ? TARGET0 / 2 : (TS == 2 ? TARGET0 * 2 : TARGET0);
+    // shapes 5 and 6: the CTA geometry of shapes 0 and 1 with the derivative
+    // contractions on the tensor cores (FP32 path only; see contract_all_mma)
+    static constexpr int TSG = TS >= 5 ? TS - 5 : TS;
+    static constexpr bool TC = TS >= 5 && sizeof(T) == 4 && n <= 8;
+    static constexpr int TARGET = TSG == 1 ? TARGET0 / 2 : (TSG == 2 ? TARGET0 * 2 : TARGET0);
     static constexpr int EPB_S = cmax(1, (int)((110 * 1024) / (ELEM * sizeof(T))));
     static constexpr int EPB = cmin(cmax(1, TARGET / NS), EPB_S);
     static constexpr int THREADS = round_up(EPB * NS, 32);
@@ -287,6 +291,120 @@ __device__ __forceinline__ void contract_all(T *ebuf, int t0, int p0, int t, int
     }
 }
 
+// ---------------------------------------------------------------------------
+// Derivative contractions on the tensor cores (FP32 path).  For direction
+// d the exchange field holds, per element, NS MX "rows" (time level t,
+// pencil p across d, variable v), each a pencil of n values along d.  A
+// warp takes 16 rows as the A operand of mma.m16n8k8 (TF32, FP32
+// accumulate), with the pencil index as K, and -Dhat (transposed) as the B
+// operand, so D[row][i] = sum_j -Dhat[i][j] x_row[j].  K position k holds
+// pencil node tau(k) = 2k (k < 4) or 2(k - 4) + 1 (k >= 4): a lane then
+// loads nodes 2c and 2c + 1 of its two rows (c = lane mod 4) and receives
+// the outputs at the same two nodes of the same rows, so the result goes
+// back in place with no exchange between lanes.  FP32 accuracy comes from
+// three TF32 products, x_hi B_hi + x_hi B_lo + x_lo B_hi, with x = x_hi +
+// x_lo split by round-to-nearest TF32 conversions (B split once).
+// ---------------------------------------------------------------------------
+#ifdef __CUDACC__
+__device__ __forceinline__ unsigned to_tf32(float x)
+{
+    unsigned r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1)
+{
+    asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                 "{%0,%1,%2,%3};\n"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+#endif
+
+// This lane's B fragment of -Dhat: b0 = B[k = c][i] = -Dhat[i][2c],
+// b1 = B[k = c + 4][i] = -Dhat[i][2c + 1], i = lane / 4 (zero outside
+// n x n), split into TF32 hi and lo parts.  Compile-time indices into the
+// operator table, selected by lane.
+struct TcOp {
+    unsigned h0, h1, l0, l1;
+};
+
+template <int n>
+__device__ __forceinline__ TcOp tc_operator(const float *Dm)
+{
+    const int lane = threadIdx.x & 31, i = lane >> 2, j = 2 * (lane & 3);
+    float b0 = 0.f, b1 = 0.f;
+#pragma unroll
+    for (int ii = 0; ii < n; ++ii)
+#pragma unroll
+        for (int jj = 0; jj < n; ++jj) {
+            b0 = (ii == i && jj == j) ? Dm[ii * n + jj] : b0;
+            b1 = (ii == i && jj == j + 1) ? Dm[ii * n + jj] : b1;
+        }
+    TcOp o;
+    o.h0 = to_tf32(b0);
+    o.h1 = to_tf32(b1);
+    o.l0 = to_tf32(b0 - __uint_as_float(o.h0));
+    o.l1 = to_tf32(b1 - __uint_as_float(o.h1));
+    return o;
+}
+
+// Every direction's contraction of every element of the CTA, in place
+// (all threads of the CTA take part, warp by warp; elements start at
+// sbase, ELEM values apart).
+template <class C>
+__device__ __forceinline__ void contract_all_mma(float *sbase, const TcOp &op)
+{
+    constexpr int n = C::n, MX = C::MX, NS = C::NS, NP = NS / n;
+    constexpr int ROWS = NS * MX;  // rows per element and direction
+    constexpr int R = C::EPB * ROWS;
+    constexpr int TILES = (R + 15) / 16;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int j0 = 2 * (lane & 3);
+#pragma unroll 1
+    for (int item = warp; item < C::DIMS * TILES; item += nw) {
+        const int d = item / TILES, tile = item - d * TILES;
+        const int pd = d == 0 ? 1 : (d == 1 ? n : n * n);
+        const int js = pd * MX;  // stride of a pencil's nodes
+        float *rp[2];
+        bool ok[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int r = tile * 16 + (lane >> 2) + 8 * h;
+            ok[h] = r < R;
+            const int rr = ok[h] ? r : 0;
+            const int g = rr / ROWS, rem = rr - g * ROWS;
+            const int v = rem % MX, q = rem / MX;
+            const int p = q % NP, t = q / NP;
+            const int s0 = (p % pd) + (p / pd) * pd * n;
+            rp[h] = sbase + g * C::ELEM + d * C::FSL + t * C::TSL + s0 * MX + v;
+        }
+        // A fragment: a0 (row 0, node j0), a1 (row 1, j0), a2 (row 0, j0+1), a3 (row 1, j0+1)
+        const bool in0 = j0 < n, in1 = j0 + 1 < n;
+        float x[4];
+        x[0] = (ok[0] && in0) ? rp[0][j0 * js] : 0.f;
+        x[1] = (ok[1] && in0) ? rp[1][j0 * js] : 0.f;
+        x[2] = (ok[0] && in1) ? rp[0][(j0 + 1) * js] : 0.f;
+        x[3] = (ok[1] && in1) ? rp[1][(j0 + 1) * js] : 0.f;
+        unsigned hi[4], lo[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            hi[k] = to_tf32(x[k]);
+            lo[k] = to_tf32(x[k] - __uint_as_float(hi[k]));
+        }
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        mma_tf32(acc, lo, op.h0, op.h1);  // small terms first
+        mma_tf32(acc, hi, op.l0, op.l1);
+        mma_tf32(acc, hi, op.h0, op.h1);
+        // D fragment: c0 (row 0, node j0), c1 (row 0, j0+1), c2 (row 1, j0), c3 (row 1, j0+1)
+        if (ok[0] && in0) rp[0][j0 * js] = acc[0];
+        if (ok[0] && in1) rp[0][(j0 + 1) * js] = acc[1];
+        if (ok[1] && in0) rp[1][j0 * js] = acc[2];
+        if (ok[1] && in1) rp[1][(j0 + 1) * js] = acc[3];
+    }
+}
+
 // -Dhat F_d on one variable v of the t = 0 pencil p along d, in place; item
 // = (d, p, v) with v fastest, so that the DIM NF M items of an element
 // spread over all its threads (the time-constant L evaluations of the
@@ -360,6 +478,8 @@ k_predictor(const KParams P)
     T *sQ = ebuf;                             // qbar[s][v]
     T *sFb = ebuf + NS * M;                   // Fbar[d][s][v]
 
+    TcOp tcop{};
+    if constexpr (C::TC) tcop = tc_operator<n>(reinterpret_cast<const float *>(O.Dm[0]));
     for (int i = tid; i < DIM * n * n; i += blockDim.x) sKw[i] = O.Kv[i / (n * n)][i % (n * n)];
     for (int i = tid; i < n; i += blockDim.x) {
         sF0[i] = O.F0[i];
@@ -387,7 +507,8 @@ k_predictor(const KParams P)
 
         const long long e = (tile - S.tile0_p) * EPB + g;
         const bool valid = act && e < S.E;
-        const long long ec = e < S.E ? e : S.E - 1;  // tail groups recompute the last element
+        const long long el = e < S.E ? e : S.E - 1;  // tail groups recompute the last element
+        const long long ec = S.elist ? (long long)S.elist[el] : el;  // a listed subset of a block, or all
         // FP32 path: perturbations about the element's reference node
         typename PDE::template Ref<T> ref;
         double uref[M];
@@ -602,7 +723,8 @@ k_predictor(const KParams P)
                 }
             }
             __syncthreads();
-            if (act) contract_all<C, T>(ebuf, tk0, pk0, tk, pk, O);
+            if constexpr (C::TC) contract_all_mma<C>(reinterpret_cast<float *>(smem_raw) + C::SHARED, tcop);
+            else if (act) contract_all<C, T>(ebuf, tk0, pk0, tk, pk, O);
             __syncthreads();
             {
                 const T dtT = sDt[0];
@@ -901,6 +1023,21 @@ __device__ __forceinline__ int neighbour(int e, int cx, int cy, int cz, int d, i
     return ix + cx * (iy + cy * iz);
 }
 
+// Neighbour of element e of a block across its face (d, side): the block
+// element (>= 0), or -(1 + j) for chunk j of the halo that another block of
+// a partitioned mesh filled (j: the element's index over the other
+// directions, lowest fastest).  Sg is the descriptor in device memory (its
+// halo pointers are read with runtime indices).
+__device__ __forceinline__ int neighbour_or_halo(int e, const SolveDesc *Sg, int cx, int cy, int cz, int d, int side)
+{
+    const int ix = e % cx, r = e / cx, iy = r % cy, iz = r / cy;
+    const int k = d == 0 ? ix : (d == 1 ? iy : iz);
+    const int cd = d == 0 ? cx : (d == 1 ? cy : cz);
+    if ((side ? k == cd - 1 : k == 0) && Sg->halo_tr[d][side] != nullptr)
+        return -1 - (d == 0 ? iy + cy * iz : (d == 1 ? ix + cx * iz : ix + cx * iy));
+    return neighbour(e, cx, cy, cz, d, side ? 1 : -1);
+}
+
 template <class PDE, int DIM, int N, typename T, int TS>
 __global__ void __launch_bounds__(CorrCfg<PDE, DIM, N, T, TS>::THREADS)
 k_corrector(const KParams P)
@@ -933,7 +1070,7 @@ k_corrector(const KParams P)
         // ---- stage everything -----------------------------------------------
         for (int c = threadIdx.x; c < ne * 2 * DIM; c += blockDim.x) {
             const int el = c / (2 * DIM), d = (c / 2) % DIM, side = c & 1;
-            sNbIdx[c] = neighbour(e0 + el, S.cells[0], S.cells[1], S.cells[2], d, side ? 1 : -1);
+            sNbIdx[c] = neighbour_or_halo(e0 + el, P.solves + si, S.cells[0], S.cells[1], S.cells[2], d, side);
         }
         for (int i = threadIdx.x; i < DIM * n; i += blockDim.x) {
             const int d = i / n, k = i % n;
@@ -954,7 +1091,10 @@ k_corrector(const KParams P)
                 const int c = i / units;  // chunk (element, d, side)
                 const int d = (c / 2) % DIM;
                 const int side = c & 1;
-                const T *src = tr + (((long long)sNbIdx[c] * DIM + d) * 2 + (1 - side)) * NF * RS;
+                const int nb = sNbIdx[c];
+                const T *src = nb >= 0 ? tr + (((long long)nb * DIM + d) * 2 + (1 - side)) * NF * RS
+                                       : reinterpret_cast<const T *>(P.solves[si].halo_tr[d][side]) +
+                                             (long long)(-1 - nb) * NF * RS;
                 unsigned char *dst = reinterpret_cast<unsigned char *>(sNb + (size_t)c * NF * RS);
                 cp_async(dst + u_ * C::G_NB, reinterpret_cast<const unsigned char *>(src) + u_ * C::G_NB, C::G_NB);
             }
@@ -967,7 +1107,9 @@ k_corrector(const KParams P)
             for (int c = threadIdx.x; c < ne * 2 * DIM; c += blockDim.x) {
                 const int el = c / (2 * DIM), d = (c / 2) % DIM, side = c & 1;
                 const double *ro = S.ref + (long long)(e0 + el) * C::RF;
-                const double *rn = S.ref + (long long)sNbIdx[c] * C::RF;
+                const int nb = sNbIdx[c];
+                const double *rn = nb >= 0 ? S.ref + (long long)nb * C::RF
+                                           : P.solves[si].halo_ref[d][side] + (long long)(-1 - nb) * C::RF;
                 double qo[M];
                 T dq[M];
 #pragma unroll
@@ -1213,7 +1355,14 @@ struct KS {
 template <class PDE, int DIM, int N, typename T, int TS, bool EX = false>
 constexpr TileShape pred_shape()
 {
-    if constexpr (TS >= 3) {
+    if constexpr (TS >= 5) {
+        if constexpr (PredCfg<PDE, DIM, N, T, TS>::TC) {
+            using C = PredCfg<PDE, DIM, N, T, TS>;  // shapes 0 / 1 with tensor-core contractions (FP32)
+            return TileShape{&k_predictor<PDE, DIM, N, T, TS, EX>, C::THREADS, C::EPB, C::BYTES};
+        } else {
+            return pred_shape<PDE, DIM, N, T, TS - 5, EX>();  // FP64: repeats of shapes 0 and 1
+        }
+    } else if constexpr (TS >= 3) {
         if constexpr (DIM == 2 && sizeof(T) == 4 && use_xt<PDE, N>()) {
             using C = PredXtCfg<PDE, N, TS == 3 ? 0 : 2>;
             return TileShape{&k_predictor_xt<PDE, N, TS == 3 ? 0 : 2, EX>, C::THREADS, C::EPB, C::BYTES};
@@ -1245,10 +1394,12 @@ const KernelSet KS<PDE, DIM, N, T>::value = {
     lim_kernel<PDE, DIM, N, T, 0>(), lim_kernel<PDE, DIM, N, T, 1>(), lim_kernel<PDE, DIM, N, T, 2>(),
     lim_kernel<PDE, DIM, N, T, 3>(), LimCfg<PDE, DIM, N>::BYTES, LimWarp<LimCfg<PDE, DIM, N>>::BYTES,
     {pred_shape<PDE, DIM, N, T, 0>(), pred_shape<PDE, DIM, N, T, 1>(), pred_shape<PDE, DIM, N, T, 2>(),
-     pred_shape<PDE, DIM, N, T, 3>(), pred_shape<PDE, DIM, N, T, 4>()},
+     pred_shape<PDE, DIM, N, T, 3>(), pred_shape<PDE, DIM, N, T, 4>(), pred_shape<PDE, DIM, N, T, 5>(),
+     pred_shape<PDE, DIM, N, T, 6>()},
     {pred_shape<PDE, DIM, N, T, 0, true>(), pred_shape<PDE, DIM, N, T, 1, true>(),
      pred_shape<PDE, DIM, N, T, 2, true>(), pred_shape<PDE, DIM, N, T, 3, true>(),
-     pred_shape<PDE, DIM, N, T, 4, true>()},
+     pred_shape<PDE, DIM, N, T, 4, true>(), pred_shape<PDE, DIM, N, T, 5, true>(),
+     pred_shape<PDE, DIM, N, T, 6, true>()},
     {corr_shape<PDE, DIM, N, T, 0>(), corr_shape<PDE, DIM, N, T, 1>(), corr_shape<PDE, DIM, N, T, 2>()},
     0, 0};
 

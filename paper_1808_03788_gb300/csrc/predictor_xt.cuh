@@ -124,7 +124,8 @@ k_predictor_xt(const KParams P)
 
         const long long e = (tile - S.tile0_p) * EPB + g;
         const bool valid = act && e < S.E;
-        const long long ec = e < S.E ? e : S.E - 1;
+        const long long el = e < S.E ? e : S.E - 1;
+        const long long ec = S.elist ? (long long)S.elist[el] : el;  // a listed subset of a block, or all
 
         // reference state (node SREF) and the perturbations u - u_ref of this
         // thread's row of nodes (x, y)

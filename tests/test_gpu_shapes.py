@@ -1,8 +1,8 @@
 """Tile shapes and the autotuner: every CTA-size shape of the predictor and
 the corrector gives a result bitwise equal to the default shape's (the
 per-element arithmetic does not depend on how elements are grouped into
-CTAs); the plane-owning predictor variant agrees within the mixed
-tolerance; the autotuner returns valid shapes, keeps them in its cache file
+CTAs); the plane-owning predictor variant and the tensor-core one agree
+within the mixed tolerance (each bitwise across its own shapes); the autotuner returns valid shapes, keeps them in its cache file
 and reads them back; autotuned batches equal the same solves alone."""
 import numpy as np
 import pytest
@@ -45,6 +45,13 @@ def _run(case, shapes, precision):
     return U, k, info
 
 
+def _tc_applies(case, precision):
+    """Predictor shapes 5-6 take the derivative contractions on the tensor
+    cores on the FP32 path (they round differently from shapes 0-2); in
+    FP64 they repeat shapes 0 and 1."""
+    return precision == A.ADERDG_MIXED_FP32 and case[5] + 1 <= 8
+
+
 def _xt_applies(case, precision):
     """Predictor shapes 3-4 are the plane-owning kernel for 2D FP32 solves
     with n^2 m <= 100 (they round differently from shapes 0-2)."""
@@ -64,7 +71,9 @@ def test_every_shape_is_bitwise_the_default(case, precision):
     assert k0 > 0
     assert info0["pred_shape"] == 0 and info0["corr_shape"] == 0
     xt = _xt_applies(case, precision)
+    tc = _tc_applies(case, precision)
     U3 = _run(case, (3, 0), precision)[0] if xt else U0
+    U5 = _run(case, (5, 0), precision)[0] if tc else U0
     seen = set()
     for ps in range(A.ADERDG_NUM_PRED_SHAPES):
         for cs in range(A.ADERDG_NUM_CORR_SHAPES):
@@ -74,12 +83,15 @@ def test_every_shape_is_bitwise_the_default(case, precision):
             assert (info["pred_shape"], info["corr_shape"]) == (ps, cs)
             seen.add((info["pred_threads"], info["pred_epb"], info["corr_threads"], info["corr_epb"]))
             assert k == k0
-            ref = U3 if (xt and ps >= 3) else U0
+            ref = U5 if (tc and ps >= 5) else (U3 if (xt and ps in (3, 4)) else U0)
             np.testing.assert_array_equal(U, ref, err_msg="shapes %d/%d" % (ps, cs))
-    if xt:
-        num = np.sqrt(np.sum((U3 - U0) ** 2, axis=(0, 1)))
-        den = np.maximum(np.sqrt(np.sum(U0 ** 2, axis=(0, 1))), 1e-300)
-        assert float(np.max(num / den)) <= 1e-6
+    for other, applies in ((U3, xt), (U5, tc)):
+        if applies:
+            num = np.sqrt(np.sum((other - U0) ** 2, axis=(0, 1)))
+            den = np.maximum(np.sqrt(np.sum(U0 ** 2, axis=(0, 1))), 1e-300)
+            assert float(np.max(num / den)) <= 1e-6
+    if tc:
+        assert not np.array_equal(U5, U0)  # the tensor-core kernel really ran
     assert len(seen) >= 2  # the shapes really differ
 
 
