@@ -303,7 +303,7 @@ __device__ __forceinline__ void contract_all(T *ebuf, int t0, int p0, int t, int
 // the outputs at the same two nodes of the same rows, so the result goes
 // back in place with no exchange between lanes.  FP32 accuracy comes from
 // three TF32 products, x_hi B_hi + x_hi B_lo + x_lo B_hi, with x = x_hi +
-// x_lo split by round-to-nearest TF32 conversions (B split once).
+// x_lo split by masking (B split once, by round-to-nearest conversions).
 // ---------------------------------------------------------------------------
 #ifdef __CUDACC__
 __device__ __forceinline__ unsigned to_tf32(float x)
@@ -387,11 +387,13 @@ __device__ __forceinline__ void contract_all_mma(float *sbase, const TcOp &op)
         x[1] = (ok[1] && in0) ? rp[1][j0 * js] : 0.f;
         x[2] = (ok[0] && in1) ? rp[0][(j0 + 1) * js] : 0.f;
         x[3] = (ok[1] && in1) ? rp[1][(j0 + 1) * js] : 0.f;
+        // split on the integer pipe: hi keeps the TF32 bits of x (x - hi is
+        // then exact in FP32), lo goes in as it is (the MMA reads its TF32 bits)
         unsigned hi[4], lo[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            hi[k] = to_tf32(x[k]);
-            lo[k] = to_tf32(x[k] - __uint_as_float(hi[k]));
+            hi[k] = __float_as_uint(x[k]) & 0xffffe000u;
+            lo[k] = __float_as_uint(x[k] - __uint_as_float(hi[k]));
         }
         float acc[4] = {0.f, 0.f, 0.f, 0.f};
         mma_tf32(acc, lo, op.h0, op.h1);  // small terms first
@@ -955,12 +957,12 @@ __device__ __forceinline__ void cp_async_wait_all()
 }
 
 template <int GRAN>
-__device__ __forceinline__ void stage(void *dst, const void *src, int bytes)
+__device__ __forceinline__ void stage(void *dst, const void *src, int bytes, int tid, int nthr)
 {
     const int units = bytes / GRAN;
     unsigned char *d = static_cast<unsigned char *>(dst);
     const unsigned char *s = static_cast<const unsigned char *>(src);
-    for (int i = threadIdx.x; i < units; i += blockDim.x) cp_async(d + i * GRAN, s + i * GRAN, GRAN);
+    for (int i = tid; i < units; i += nthr) cp_async(d + i * GRAN, s + i * GRAN, GRAN);
 }
 
 template <class PDE, int DIM, int N, typename T, int TS = 0>
@@ -981,11 +983,14 @@ struct CorrCfg {
         sizeof(T) == 4 || align16(OWN) + align16(NB) + align16(UB) + align16(VB) <= 8192;
     static constexpr size_t PER_ELEM =
         align16(OWN) + align16(NB) + (STAGE_UV ? align16(UB) + align16(VB) : 0) + align16(FS);
-    // shapes 0, 1, 2: 256-, 128- and 512-thread CTAs
-    static constexpr int THREADS = TS == 1 ? 128 : (TS == 2 ? 512 : 256);
-    static constexpr int EPB_T = cmax(1, THREADS / NS);
+    // shapes 0, 1, 2: 256-, 128- and 512-thread CTAs; shape 3: every warp
+    // takes one element of the tile on its own (its own shared-memory
+    // slice, warp-level synchronisation only), NW warps per CTA
+    static constexpr bool WM = TS == 3;
+    static constexpr int THREADS_CTA = TS == 1 ? 128 : (TS == 2 ? 512 : 256);
+    static constexpr int EPB_T = cmax(1, THREADS_CTA / NS);
     static constexpr int EPB_S = cmax(1, (int)((110 * 1024) / PER_ELEM));
-    static constexpr int EPB = cmin(EPB_T, EPB_S);
+    static constexpr int EPB = WM ? 1 : cmin(EPB_T, EPB_S);  // elements per shared-memory unit
     static constexpr size_t O_OWN = 0;
     static constexpr size_t O_NB = align16(EPB * OWN);
     static constexpr size_t O_U = O_NB + align16(EPB * NB);
@@ -1001,7 +1006,11 @@ struct CorrCfg {
     // (the path integral needs absolute face states)
     static constexpr size_t O_REFO = O_DEL + (DELTA ? align16(sizeof(T) * EPB * 2 * DIM * 2 * M) : 0);
     static constexpr size_t O_RED = O_REFO + (DELTA && PDE::NCP ? align16(sizeof(T) * EPB * M) : 0);
-    static constexpr size_t BYTES = O_RED + 64 * sizeof(double);
+    static constexpr size_t BYTES = O_RED + 64 * sizeof(double);  // one unit (the CTA, or a warp)
+    static constexpr int NW = WM ? cmax(1, cmin(8, (int)((200 * 1024) / BYTES))) : 1;
+    static constexpr int THREADS = WM ? 32 * NW : THREADS_CTA;
+    static constexpr int EPB_TILE = WM ? NW : EPB;  // elements per tile of the launch
+    static constexpr size_t CTA_BYTES = NW * BYTES;
     // copy granules (bytes): the largest of 16/8/4 dividing offsets and sizes
     static constexpr int G_OWN = cgcd((int)OWN, 16);
     static constexpr int G_NB = cgcd((int)(sizeof(T) * RS), 16);
@@ -1043,19 +1052,55 @@ __global__ void __launch_bounds__(CorrCfg<PDE, DIM, N, T, TS>::THREADS)
 k_corrector(const KParams P)
 {
     using C = CorrCfg<PDE, DIM, N, T, TS>;
-    constexpr int n = C::n, M = C::M, NS = C::NS, NF = C::NF, NREC = C::NREC, RS = C::RS, EPB = C::EPB;
+    constexpr int n = C::n, M = C::M, NS = C::NS, NF = C::NF, NREC = C::NREC, RS = C::RS;
+    constexpr int EPT = C::EPB_TILE;
 
+    // the unit that shares a shared-memory slice and synchronises: the CTA,
+    // or (shape 3) each warp with its own slice and element
+    const int wid = threadIdx.x >> 5;
+    const int tid = C::WM ? (int)(threadIdx.x & 31) : (int)threadIdx.x;
+    const int nthr = C::WM ? 32 : (int)blockDim.x;
+    auto usync = [&]() {
+        if constexpr (C::WM) __syncwarp();
+        else __syncthreads();
+    };
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *sOwn = reinterpret_cast<T *>(smem_raw + C::O_OWN);
-    T *sNb = reinterpret_cast<T *>(smem_raw + C::O_NB);
-    double *sU = reinterpret_cast<double *>(smem_raw + C::O_U);
-    T *sV = reinterpret_cast<T *>(smem_raw + C::O_V);
-    T *sFs = reinterpret_cast<T *>(smem_raw + C::O_FS);
-    T *sL = reinterpret_cast<T *>(smem_raw + C::O_LIFT);  // [side][d][k]
-    int *sNbIdx = reinterpret_cast<int *>(smem_raw + C::O_NBIDX);
-    T *sDel = reinterpret_cast<T *>(smem_raw + C::O_DEL);  // [el][d][side][dF | dq][M]
-    T *sRefO = reinterpret_cast<T *>(smem_raw + C::O_REFO);  // [el][M]
-    double *red = reinterpret_cast<double *>(smem_raw + C::O_RED);
+    unsigned char *sb = smem_raw + (C::WM ? wid * C::BYTES : 0);
+    T *sOwn = reinterpret_cast<T *>(sb + C::O_OWN);
+    T *sNb = reinterpret_cast<T *>(sb + C::O_NB);
+    double *sU = reinterpret_cast<double *>(sb + C::O_U);
+    T *sV = reinterpret_cast<T *>(sb + C::O_V);
+    T *sFs = reinterpret_cast<T *>(sb + C::O_FS);
+    T *sL = reinterpret_cast<T *>(sb + C::O_LIFT);  // [side][d][k]
+    int *sNbIdx = reinterpret_cast<int *>(sb + C::O_NBIDX);
+    T *sDel = reinterpret_cast<T *>(sb + C::O_DEL);  // [el][d][side][dF | dq][M]
+    T *sRefO = reinterpret_cast<T *>(sb + C::O_REFO);  // [el][M]
+    double *red = reinterpret_cast<double *>(sb + C::O_RED);
+    // shape 3: each lane's wave-speed maxima and non-finite flag, gathered
+    // over the warp's elements of one solve and flushed when the solve changes
+    T acc_l[DIM];
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) acc_l[d] = T(0);
+    bool acc_bad = false;
+    Control *acc_ctl = nullptr;
+    auto flush = [&]() {  // warp-uniform
+        if (acc_ctl == nullptr) return;
+        const unsigned anyb = __any_sync(0xffffffffu, acc_bad);
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) {
+            T x = acc_l[d];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const T y = __shfl_xor_sync(0xffffffffu, x, o);
+                x = y > x ? y : x;
+            }
+            if ((threadIdx.x & 31) == 0)
+                atomicMax(&acc_ctl->lam_acc[d], (unsigned long long)__double_as_longlong(double(x)));
+            acc_l[d] = T(0);
+        }
+        if ((threadIdx.x & 31) == 0 && anyb) atomicOr(&acc_ctl->flags, FLAG_NONFINITE);
+        acc_bad = false;
+    };
 
     for (long long tile = blockIdx.x; tile < P.ntiles; tile += gridDim.x) {
         const int si = find_solve(P.solves, P.nsolves, tile, 1);
@@ -1063,30 +1108,33 @@ k_corrector(const KParams P)
         const double dt = solve_dt(P, S);
         if (!(dt > 0.0)) continue;  // uniform over the CTA
 
-        const int e0 = (int)((tile - S.tile0_c) * EPB);
-        const int ne = (S.E - e0) < EPB ? (int)(S.E - e0) : EPB;
+        const int et = (int)((tile - S.tile0_c) * EPT);              // the tile's first element
+        const int nt = (S.E - et) < EPT ? (int)(S.E - et) : EPT;     // and its element count
+        const int e0 = C::WM ? et + wid : et;                        // this unit's first element
+        const int ne = C::WM ? (wid < nt ? 1 : 0) : nt;
+        if (C::WM && ne == 0) continue;  // uniform over the warp
         const T *tr = reinterpret_cast<const T *>(S.tr);
 
         // ---- stage everything -----------------------------------------------
-        for (int c = threadIdx.x; c < ne * 2 * DIM; c += blockDim.x) {
+        for (int c = tid; c < ne * 2 * DIM; c += nthr) {
             const int el = c / (2 * DIM), d = (c / 2) % DIM, side = c & 1;
             sNbIdx[c] = neighbour_or_halo(e0 + el, P.solves + si, S.cells[0], S.cells[1], S.cells[2], d, side);
         }
-        for (int i = threadIdx.x; i < DIM * n; i += blockDim.x) {
+        for (int i = tid; i < DIM * n; i += nthr) {
             const int d = i / n, k = i % n;
             const double idx = P.solves[si].inv_dx[d];  // runtime index: read from global
             sL[(0 * 3 + d) * NMAX + k] = T(idx * P.b.inv_w[k] * P.b.F0[k]);
             sL[(1 * 3 + d) * NMAX + k] = T(idx * P.b.inv_w[k] * P.b.F1[k]);
         }
-        stage<C::G_OWN>(sOwn, tr + (long long)e0 * NREC * RS, ne * (int)C::OWN);
+        stage<C::G_OWN>(sOwn, tr + (long long)e0 * NREC * RS, ne * (int)C::OWN, tid, nthr);
         if constexpr (C::STAGE_UV) {
-            stage<C::G_U>(sU, S.u + (long long)e0 * NS * M, ne * (int)C::UB);
-            stage<C::G_V>(sV, reinterpret_cast<const T *>(S.V) + (long long)e0 * NS * M, ne * (int)C::VB);
+            stage<C::G_U>(sU, S.u + (long long)e0 * NS * M, ne * (int)C::UB, tid, nthr);
+            stage<C::G_V>(sV, reinterpret_cast<const T *>(S.V) + (long long)e0 * NS * M, ne * (int)C::VB, tid, nthr);
         }
-        __syncthreads();  // neighbour indices
+        usync();  // neighbour indices
         {
             constexpr int units = (int)(sizeof(T) * NF * RS) / C::G_NB;
-            for (int i = threadIdx.x; i < ne * 2 * DIM * units; i += blockDim.x) {
+            for (int i = tid; i < ne * 2 * DIM * units; i += nthr) {
                 const int u_ = i % units;
                 const int c = i / units;  // chunk (element, d, side)
                 const int d = (c / 2) % DIM;
@@ -1104,7 +1152,7 @@ k_corrector(const KParams P)
             // xi_d = 1 face and -1 on the xi_d = 0 face:  dq = q_ref(nb) -
             // q_ref(own) formed in FP64 and rounded (it is O(h)), and
             // dF = F_d(q_ref(nb)) - F_d(q_ref(own)) by the perturbation flux
-            for (int c = threadIdx.x; c < ne * 2 * DIM; c += blockDim.x) {
+            for (int c = tid; c < ne * 2 * DIM; c += nthr) {
                 const int el = c / (2 * DIM), d = (c / 2) % DIM, side = c & 1;
                 const double *ro = S.ref + (long long)(e0 + el) * C::RF;
                 const int nb = sNbIdx[c];
@@ -1144,10 +1192,10 @@ k_corrector(const KParams P)
             }
         }
         cp_async_wait_all();
-        __syncthreads();
+        usync();
 
         // ---- Rusanov flux per (element, face record), all variables --------
-        for (int i = threadIdx.x; i < ne * NREC; i += blockDim.x) {
+        for (int i = tid; i < ne * NREC; i += nthr) {
             const int el = i / NREC;
             const int rec = i - el * NREC;
             const int d = rec / (2 * NF);
@@ -1194,7 +1242,7 @@ k_corrector(const KParams P)
 #pragma unroll
             for (int v = 0; v < M; ++v) sFs[(el * NREC + rec) * M + v] = f[v];
         }
-        __syncthreads();
+        usync();
 
         // ---- per node: surface lift, update u^{n+1} = u^n + dt (V - surface),
         // ---- then the wave speeds of u^{n+1} and the non-finite check -------
@@ -1204,7 +1252,7 @@ k_corrector(const KParams P)
 #pragma unroll
         for (int d = 0; d < DIM; ++d) lmax[d] = T(0);
         bool bad = false;
-        for (int i = threadIdx.x; i < ne * NS; i += blockDim.x) {
+        for (int i = tid; i < ne * NS; i += nthr) {
             const int el = i / NS;
             const int sn = i - el * NS;
             int kk[DIM], pp[DIM];
@@ -1248,37 +1296,48 @@ k_corrector(const KParams P)
                 lmax[d] = lam > lmax[d] ? lam : lmax[d];
             }
         }
-#pragma unroll
-        for (int d = 0; d < DIM; ++d) {
-            T x = lmax[d];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const T y = __shfl_xor_sync(0xffffffffu, x, o);
-                x = y > x ? y : x;
+        if constexpr (C::WM) {
+            if (S.ctl != acc_ctl) {  // warp-uniform: a new solve
+                flush();
+                acc_ctl = S.ctl;
             }
-            lmax[d] = x;
-        }
-        const unsigned anybad = __any_sync(0xffffffffu, bad);
-        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        if (lane == 0) {
 #pragma unroll
-            for (int d = 0; d < DIM; ++d) red[warp * 4 + d] = double(lmax[d]);
-            red[warp * 4 + 3] = anybad ? 1.0 : 0.0;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            const int nw = blockDim.x >> 5;
-            double b = 0.0;
+            for (int d = 0; d < DIM; ++d) acc_l[d] = lmax[d] > acc_l[d] ? lmax[d] : acc_l[d];
+            acc_bad |= bad;
+        } else {
+#pragma unroll
             for (int d = 0; d < DIM; ++d) {
-                double x = 0.0;
-                for (int w = 0; w < nw; ++w) x = fmax(x, red[w * 4 + d]);
-                atomicMax(&S.ctl->lam_acc[d], (unsigned long long)__double_as_longlong(x));
+                T x = lmax[d];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const T y = __shfl_xor_sync(0xffffffffu, x, o);
+                    x = y > x ? y : x;
+                }
+                lmax[d] = x;
             }
-            for (int w = 0; w < nw; ++w) b = fmax(b, red[w * 4 + 3]);
-            if (b > 0.0) atomicOr(&S.ctl->flags, FLAG_NONFINITE);
+            const unsigned anybad = __any_sync(0xffffffffu, bad);
+            const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+            if (lane == 0) {
+#pragma unroll
+                for (int d = 0; d < DIM; ++d) red[warp * 4 + d] = double(lmax[d]);
+                red[warp * 4 + 3] = anybad ? 1.0 : 0.0;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                const int nw = blockDim.x >> 5;
+                double b = 0.0;
+                for (int d = 0; d < DIM; ++d) {
+                    double x = 0.0;
+                    for (int w = 0; w < nw; ++w) x = fmax(x, red[w * 4 + d]);
+                    atomicMax(&S.ctl->lam_acc[d], (unsigned long long)__double_as_longlong(x));
+                }
+                for (int w = 0; w < nw; ++w) b = fmax(b, red[w * 4 + 3]);
+                if (b > 0.0) atomicOr(&S.ctl->flags, FLAG_NONFINITE);
+            }
         }
-        __syncthreads();  // shared buffers are reused by the next tile
+        usync();  // shared buffers are reused by the next tile
     }
+    if constexpr (C::WM) flush();
 }
 
 // Wave-speed maxima of the current state of solve 0 of the launch (the CFL
@@ -1379,7 +1438,7 @@ template <class PDE, int DIM, int N, typename T, int TS>
 constexpr TileShape corr_shape()
 {
     using C = CorrCfg<PDE, DIM, N, T, TS>;
-    return TileShape{&k_corrector<PDE, DIM, N, T, TS>, C::THREADS, C::EPB, C::BYTES};
+    return TileShape{&k_corrector<PDE, DIM, N, T, TS>, C::THREADS, C::EPB_TILE, C::CTA_BYTES};
 }
 
 template <class PDE, int DIM, int N, typename T>
@@ -1400,7 +1459,8 @@ const KernelSet KS<PDE, DIM, N, T>::value = {
      pred_shape<PDE, DIM, N, T, 2, true>(), pred_shape<PDE, DIM, N, T, 3, true>(),
      pred_shape<PDE, DIM, N, T, 4, true>(), pred_shape<PDE, DIM, N, T, 5, true>(),
      pred_shape<PDE, DIM, N, T, 6, true>()},
-    {corr_shape<PDE, DIM, N, T, 0>(), corr_shape<PDE, DIM, N, T, 1>(), corr_shape<PDE, DIM, N, T, 2>()},
+    {corr_shape<PDE, DIM, N, T, 0>(), corr_shape<PDE, DIM, N, T, 1>(), corr_shape<PDE, DIM, N, T, 2>(),
+     corr_shape<PDE, DIM, N, T, 3>()},
     0, 0};
 
 }  // namespace aderdg
