@@ -542,6 +542,11 @@ struct KernelSet {
     void (*lim_couple)(KParams);
     size_t lim_smem;    // k_lim_fv / k_lim_couple (one element per CTA)
     size_t lim_smem_w;  // k_lim_minmax / k_lim_detect (one element per warp)
+    // the FP32 path's extremes and detection (FP32 projections, FP64 where
+    // a decision is too close to call), in the FP64 instance only
+    void (*lim_minmax32)(KParams);
+    void (*lim_detect32)(KParams);
+    size_t lim_smem_w32;
     TileShape pshape[NSHAPE_P], pshape_ex[NSHAPE_P], cshape[NSHAPE_C];  // pshape_ex: extrapolation and CERK guesses
     int pred_shape, corr_shape;  // indices of the shapes in use
 };

@@ -1395,6 +1395,8 @@ constexpr KernelFn lim_kernel()
         if constexpr (K == 0) return &k_lim_minmax<PDE, DIM, N>;
         else if constexpr (K == 1) return &k_lim_detect<PDE, DIM, N>;
         else if constexpr (K == 2) return &k_lim_fv<PDE, DIM, N>;
+        else if constexpr (K == 4) return &k_lim_minmax32<PDE, DIM, N>;
+        else if constexpr (K == 5) return &k_lim_detect32<PDE, DIM, N>;
         else return &k_lim_couple<PDE, DIM, N, T>;
     } else if constexpr (LimCfg<PDE, DIM, N>::OK && K == 3) {
         return &k_lim_couple<PDE, DIM, N, T>;
@@ -1452,6 +1454,7 @@ const KernelSet KS<PDE, DIM, N, T>::value = {
     PredCfg<PDE, DIM, N, T>::DELTA ? PredCfg<PDE, DIM, N, T>::RF : 0, PDE::NCP ? 1 : 0, PredCfg<PDE, DIM, N, T>::MX,
     lim_kernel<PDE, DIM, N, T, 0>(), lim_kernel<PDE, DIM, N, T, 1>(), lim_kernel<PDE, DIM, N, T, 2>(),
     lim_kernel<PDE, DIM, N, T, 3>(), LimCfg<PDE, DIM, N>::BYTES, LimWarp<LimCfg<PDE, DIM, N>>::BYTES,
+    lim_kernel<PDE, DIM, N, T, 4>(), lim_kernel<PDE, DIM, N, T, 5>(), LimWarp32<LimCfg<PDE, DIM, N>>::BYTES,
     {pred_shape<PDE, DIM, N, T, 0>(), pred_shape<PDE, DIM, N, T, 1>(), pred_shape<PDE, DIM, N, T, 2>(),
      pred_shape<PDE, DIM, N, T, 3>(), pred_shape<PDE, DIM, N, T, 4>(), pred_shape<PDE, DIM, N, T, 5>(),
      pred_shape<PDE, DIM, N, T, 6>()},

@@ -50,14 +50,14 @@ struct LimCfg {
 // One direction of a tensor-product application: LO points before the
 // direction (R of them already transformed), HI after it (C untransformed),
 // M values per point; each output is one C-term sum, accumulated in j order.
-template <int M, int R, int C, int LO, int HI>
-__device__ __forceinline__ void lim_pass(const double *src, double *dst, const double *Op, int tid, int nt)
+template <int M, int R, int C, int LO, int HI, typename V>
+__device__ __forceinline__ void lim_pass(const V *src, V *dst, const V *Op, int tid, int nt)
 {
     constexpr int total = LO * R * HI * M;
     for (int i = tid; i < total; i += nt) {
         const int v = i % M, r = i / M, al = r % LO, ad = (r / LO) % R, ah = r / (LO * R);
-        const double *x = src + (al + LO * C * ah) * M + v;
-        double acc = 0.0;
+        const V *x = src + (al + LO * C * ah) * M + v;
+        V acc = V(0);
 #pragma unroll
         for (int j = 0; j < C; ++j) acc += Op[ad * C + j] * x[j * LO * M];
         dst[i] = acc;
@@ -68,9 +68,8 @@ __device__ __forceinline__ void lim_pass(const double *src, double *dst, const d
 // in shared memory ([r][c]); in has C points per direction (x fastest,
 // M values per point), out R.  The team -- a CTA or one warp -- is the
 // threads tid = 0 .. nt-1, all of which call it; sync() joins them.
-template <int DIM, int M, int R, int C, class Sync>
-__device__ void lim_tensor_team(const double *in, double *out, double *ta, double *tb, const double *Op, int tid,
-                                int nt, Sync sync)
+template <int DIM, int M, int R, int C, typename V, class Sync>
+__device__ void lim_tensor_team(const V *in, V *out, V *ta, V *tb, const V *Op, int tid, int nt, Sync sync)
 {
     if constexpr (DIM == 1) {
         lim_pass<M, R, C, 1, 1>(in, out, Op, tid, nt);
@@ -488,6 +487,302 @@ __global__ void __launch_bounds__(128) k_lim_detect(const KParams P)
                         for (int a = lane; a < L::NSUB; a += 32) {
                             const long long k = lim_key(avg[a * L::M + v]);
                             bad |= k < blo || k > bhi;
+                        }
+                    }
+                    bad = __any_sync(0xffffffffu, bad);
+                }
+                if (lane == 0) {
+                    S.lim_flags[e] = bad;
+                    if (bad) {
+                        // at most E entries a step (the reset after the limiter empties it)
+                        const unsigned k = atomicAdd(&S.ctl->lim_count, 1u);
+                        if (k < (unsigned)S.E) S.lim_list[k] = (int)e;
+                    }
+                }
+                __syncwarp();
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Detection on the FP32 path (Sec. 2.3).  The subcell averages are projected
+// in FP32 from the perturbations dq = u - u_ref of the element's nodes
+// (u_ref: its first node, in FP64), so that their rounding scales with the
+// element's variation, not with the state.  Every decision that an FP32
+// value is too close to call is taken again in FP64: a subcell average within
+// the error bound of a maximum-principle bound is recomputed from the FP64
+// nodes and compared with the FP64 bound, and an Euler subcell whose FP32
+// density or pressure is within its error bound of zero has its averages
+// recomputed in FP64 and tested exactly.  The error bound of an average of
+// variable v is TOLC eps32 rho^d max_s |dq_sv| (rho = the largest absolute
+// row sum of the projection; TOLC covers the d passes of n-term sums, the
+// narrowing of dq and of the operator, with a factor 2 to spare), plus eps32
+// times the bound itself.  The extremes the detection keeps for the next
+// step (and the ones k_lim_minmax32 computes) are u_ref plus the FP32
+// extremes, the same routine for the state and for the candidate.
+// ---------------------------------------------------------------------------
+template <class L>
+struct LimWarp32 {
+    // floats per warp: node perturbations, subcell averages, two projection buffers
+    static constexpr size_t FLOATS =
+        (size_t)round_up(L::NS * L::M, 4) + round_up(L::NSUB * L::M, 4) + 2 * (size_t)round_up(L::TMP, 4);
+    static constexpr int WARPS = cmax(1, cmin(4, (int)((200 * 1024) / (4 * FLOATS))));
+    static constexpr int PR64 = round_up(L::S * L::n, 2);  // doubles: the FP64 operator (rechecks)
+    static constexpr int PR32 = round_up(L::S * L::n, 4);  // floats: the FP32 operator
+    static constexpr size_t BYTES = 8 * (size_t)PR64 + 4 * (size_t)PR32 + 4 * WARPS * FLOATS;
+    static constexpr float TOLC = 2.0f * (L::n + 2) * 3 + 8.0f;  // d (n + 2) + 4, doubled, for d <= 3
+};
+
+// The FP64 subcell average a of variable v from the FP64 nodes x of one
+// element (one lane; the tensor sums of the projection, innermost x).
+template <class L, int DIM>
+__device__ double lim_average64(const double *x, const double *Pr, int a, int v)
+{
+    constexpr int n = L::n, S = L::S, M = L::M;
+    const int ax = a % S, ay = (a / S) % S, az = a / (S * S);
+    double acc = 0.0;
+    for (int jz = 0; jz < (DIM == 3 ? n : 1); ++jz) {
+        double accy = 0.0;
+        for (int jy = 0; jy < n; ++jy) {
+            double accx = 0.0;
+            for (int jx = 0; jx < n; ++jx) accx += Pr[ax * n + jx] * x[((jz * n + jy) * n + jx) * M + v];
+            accy += Pr[ay * n + jy] * accx;
+        }
+        acc = DIM == 3 ? acc + Pr[az * n + jz] * accy : accy;
+    }
+    return acc;
+}
+
+// FP32 subcell averages of element e of src (warp-wide): ref = its first
+// node, u = narrowed perturbations, avg = their averages, am[v] = max |dq|
+// of variable v (every lane gets ref and am).
+template <class L, int DIM>
+__device__ __forceinline__ void lim_averages32_warp(const double *src, long long e, const float *Pr32, float *u, float *avg, float *ta,
+                                    float *tb, int lane, double *ref, float *am)
+{
+    constexpr int M = L::M;
+    const double *x = src + e * (L::NS * M);
+#pragma unroll
+    for (int v = 0; v < M; ++v) {
+        ref[v] = x[v];
+        am[v] = 0.f;
+    }
+    for (int s = lane; s < L::NS; s += 32) {
+#pragma unroll
+        for (int v = 0; v < M; ++v) {
+            const float d = dbl_to_flt_rn(x[s * M + v] - ref[v]);
+            u[s * M + v] = d;
+            am[v] = fmaxf(am[v], fabsf(d));
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < M; ++v)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) am[v] = fmaxf(am[v], __shfl_xor_sync(0xffffffffu, am[v], o));
+    __syncwarp();
+    lim_tensor_team<DIM, M, L::S, L::n>(u, avg, ta, tb, Pr32, lane, 32, [] { __syncwarp(); });
+}
+
+// Extremes of the FP32 averages (warp-wide), kept as ref + widened value.
+template <class L>
+__device__ __forceinline__ void lim_extremes32_warp(const float *avg, const double *ref, int lane, double *mm)
+{
+#pragma unroll
+    for (int v = 0; v < L::M; ++v) {
+        float lo = avg[v], hi = lo;
+        for (int a = lane; a < L::NSUB; a += 32) {
+            lo = fminf(lo, avg[a * L::M + v]);
+            hi = fmaxf(hi, avg[a * L::M + v]);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+            hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        }
+        if (lane == 0) {
+            mm[v * 2] = ref[v] + flt_to_dbl(lo);
+            mm[v * 2 + 1] = ref[v] + flt_to_dbl(hi);
+        }
+    }
+}
+
+// Shared layout of the FP32-path kernels: FP64 operator, FP32 operator,
+// then per warp its buffers; returns this warp's first buffer, sets rhoD.
+template <class L, int DIM>
+__device__ __forceinline__ float *lim32_setup(const KParams &P, unsigned char *smem, double **Pr64, float **Pr32, float *rhoD)
+{
+    using W = LimWarp32<L>;
+    double *p64 = reinterpret_cast<double *>(smem);
+    float *p32 = reinterpret_cast<float *>(p64 + W::PR64);
+    for (int i = threadIdx.x; i < L::S * L::n; i += blockDim.x) {
+        p64[i] = P.lim_pr[i];
+        p32[i] = dbl_to_flt_rn(P.lim_pr[i]);
+    }
+    __syncthreads();
+    float rho = 0.f;
+    for (int a = 0; a < L::S; ++a) {
+        float r = 0.f;
+        for (int j = 0; j < L::n; ++j) r += fabsf(p32[a * L::n + j]);
+        rho = fmaxf(rho, r);
+    }
+    float rd = 1.f;
+    for (int d = 0; d < DIM; ++d) rd *= rho * 1.001f;
+    *rhoD = rd;
+    *Pr64 = p64;
+    *Pr32 = p32;
+    return p32 + W::PR32 + (size_t)(threadIdx.x >> 5) * W::FLOATS;
+}
+
+// Extremes of u^n on the FP32 path (as k_lim_minmax, FP32 projections).
+template <class PDE, int DIM, int N>
+__global__ void __launch_bounds__(128) k_lim_minmax32(const KParams P)
+{
+    using L = LimCfg<PDE, DIM, N>;
+    using W = LimWarp32<L>;
+    if constexpr (L::OK) {
+        extern __shared__ __align__(16) unsigned char smem_raw[];
+        double *Pr64;
+        float *Pr32, rhoD;
+        float *u = lim32_setup<L, DIM>(P, smem_raw, &Pr64, &Pr32, &rhoD);
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        if (warp >= W::WARPS) return;
+        float *avg = u + round_up(L::NS * L::M, 4), *ta = avg + round_up(L::NSUB * L::M, 4),
+              *tb = ta + round_up(L::TMP, 4);
+        for (int si = 0; si < P.nsolves; ++si) {
+            const SolveDesc &S = P.solves[si];
+            if (!S.u_prev) continue;  // a solve without the limiter
+            const bool fresh = S.ctl->lim_fresh != 0;
+            for (long long e = (long long)blockIdx.x * W::WARPS + warp; e < S.E; e += (long long)gridDim.x * W::WARPS) {
+                bool reuse = fresh;
+                if (reuse) {
+                    int touched = S.lim_flags[e];
+#pragma unroll
+                    for (int d = 0; d < DIM; ++d)
+#pragma unroll
+                        for (int side = 0; side < 2; ++side)
+                            touched |=
+                                S.lim_flags[neighbour((int)e, S.cells[0], S.cells[1], S.cells[2], d, side ? 1 : -1)];
+                    reuse = !touched;
+                }
+                if (reuse) {  // uniform over the warp
+                    if (lane < 2 * L::M) S.lim_mm[e * (2 * L::M) + lane] = S.lim_mmc[e * (2 * L::M) + lane];
+                    continue;
+                }
+                double ref[L::M];
+                float am[L::M];
+                lim_averages32_warp<L, DIM>(S.u_prev, e, Pr32, u, avg, ta, tb, lane, ref, am);
+                lim_extremes32_warp<L>(avg, ref, lane, S.lim_mm + e * (2 * L::M));
+                __syncwarp();
+            }
+        }
+    }
+}
+
+// Euler admissibility of one FP32 subcell average (absolute state ref +
+// avg): 1 admissible, 0 not, -1 too close to call in FP32.
+template <class PDE>
+__device__ __forceinline__ int lim_admissible32(const PdeParams &P, const double *ref, const float *avg)
+{
+    if constexpr (PDE::KIND == 2) {
+        constexpr int D = PDE::M - 2;
+        float q[PDE::M];
+        float mag = 0.f;
+#pragma unroll
+        for (int v = 0; v < PDE::M; ++v) {
+            q[v] = dbl_to_flt_rn(ref[v]) + avg[v];
+            mag = fmaxf(mag, fabsf(q[v]));
+        }
+        if (q[0] <= 1e-6f * mag) return q[0] < -1e-6f * mag ? 0 : -1;
+        float kin = 0.f;
+#pragma unroll
+        for (int k = 0; k < D; ++k) kin += q[1 + k] * q[1 + k];
+        const float e2 = 0.5f * kin / q[0];
+        const float p = pconst<float>(P, 0) * (q[D + 1] - e2);
+        const float err = 1e-5f * (fabsf(q[D + 1]) + e2) * pconst<float>(P, 0);
+        return p > err ? 1 : (p < -err ? 0 : -1);
+    } else {
+        return 1;
+    }
+}
+
+template <class PDE, int DIM, int N>
+__global__ void __launch_bounds__(128) k_lim_detect32(const KParams P)
+{
+    using L = LimCfg<PDE, DIM, N>;
+    using W = LimWarp32<L>;
+    if constexpr (L::OK) {
+        extern __shared__ __align__(16) unsigned char smem_raw[];
+        double *Pr64;
+        float *Pr32, rhoD;
+        float *u = lim32_setup<L, DIM>(P, smem_raw, &Pr64, &Pr32, &rhoD);
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        if (warp >= W::WARPS) return;
+        float *avg = u + round_up(L::NS * L::M, 4), *ta = avg + round_up(L::NSUB * L::M, 4),
+              *tb = ta + round_up(L::TMP, 4);
+        constexpr float EPS = 5.9604645e-08f;  // 2^-24
+        for (int si = 0; si < P.nsolves; ++si) {
+            const SolveDesc &S = P.solves[si];
+            if (!S.u_prev) continue;
+            for (long long e = (long long)blockIdx.x * W::WARPS + warp; e < S.E; e += (long long)gridDim.x * W::WARPS) {
+                const double *uc = S.u_out + e * (L::NS * L::M);  // the candidate
+                int bad = 0;
+                for (int s = lane; s < L::NS; s += 32) {
+                    double q[L::M];
+                    bool fin = true;
+#pragma unroll
+                    for (int v = 0; v < L::M; ++v) {
+                        q[v] = uc[s * L::M + v];
+                        fin = fin && !dbl_nonfinite(q[v]);
+                    }
+                    bad |= !fin || !lim_admissible<PDE>(P.pde, q);
+                }
+                bad = __any_sync(0xffffffffu, bad);
+                if (!bad) {
+                    double ref[L::M];
+                    float am[L::M];
+                    lim_averages32_warp<L, DIM>(S.u_out, e, Pr32, u, avg, ta, tb, lane, ref, am);
+                    lim_extremes32_warp<L>(avg, ref, lane, S.lim_mmc + e * (2 * L::M));
+                    for (int a = lane; a < L::NSUB; a += 32) {
+                        int ok = lim_admissible32<PDE>(P.pde, ref, avg + a * L::M);
+                        if (ok < 0) {  // too close to call: the subcell's FP64 averages
+                            double q[L::M];
+#pragma unroll
+                            for (int v = 0; v < L::M; ++v) q[v] = lim_average64<L, DIM>(uc, Pr64, a, v);
+                            ok = lim_admissible<PDE>(P.pde, q) ? 1 : 0;
+                        }
+                        bad |= ok == 0;
+                    }
+#pragma unroll
+                    for (int v = 0; v < L::M; ++v) {
+                        // the relaxed maximum principle of u^n over the element and its face neighbours
+                        long long klo = lim_key(S.lim_mm[(e * L::M + v) * 2]);
+                        long long khi = lim_key(S.lim_mm[(e * L::M + v) * 2 + 1]);
+#pragma unroll
+                        for (int d = 0; d < DIM; ++d)
+#pragma unroll
+                            for (int side = 0; side < 2; ++side) {
+                                const long long nb =
+                                    neighbour((int)e, S.cells[0], S.cells[1], S.cells[2], d, side ? 1 : -1);
+                                const long long kl = lim_key(S.lim_mm[(nb * L::M + v) * 2]);
+                                const long long kh = lim_key(S.lim_mm[(nb * L::M + v) * 2 + 1]);
+                                klo = kl < klo ? kl : klo;
+                                khi = kh > khi ? kh : khi;
+                            }
+                        const double lo = lim_unkey(klo), hi = lim_unkey(khi);
+                        const double delta = fmax(1e-4, 1e-3 * (hi - lo));
+                        const double blo = lo - delta, bhi = hi + delta;
+                        const float rlo = dbl_to_flt_rn(blo - ref[v]), rhi = dbl_to_flt_rn(bhi - ref[v]);
+                        const float tol = W::TOLC * EPS * rhoD * am[v] + 2.f * EPS * fmaxf(fabsf(rlo), fabsf(rhi)) +
+                                          1e-30f;
+                        for (int a = lane; a < L::NSUB; a += 32) {
+                            const float x = avg[a * L::M + v];
+                            if (x < rlo - tol || x > rhi + tol) {
+                                bad = 1;
+                            } else if (x < rlo + tol || x > rhi - tol) {  // too close to call in FP32
+                                const double x64 = lim_average64<L, DIM>(uc, Pr64, a, v);
+                                bad |= x64 < blo || x64 > bhi;
+                            }
                         }
                     }
                     bad = __any_sync(0xffffffffu, bad);

@@ -65,7 +65,11 @@ int limiter_kernels(int pde, int dim, int N, int prec, int guess, LimKernels *ou
         *why = "no coupling kernel compiled for this precision of the subcell limiter";
         return ADERDG_E_UNSUPPORTED;
     }
-    *out = LimKernels{k64->lim_minmax, k64->lim_detect, k64->lim_fv, ks->lim_couple, k64->lim_smem, k64->lim_smem_w};
+    // the FP32 path projects its subcell averages in FP32 (FP64 only for
+    // decisions too close to call)
+    const bool f32 = prec == ADERDG_MIXED_FP32;
+    *out = LimKernels{f32 ? k64->lim_minmax32 : k64->lim_minmax, f32 ? k64->lim_detect32 : k64->lim_detect,
+                      k64->lim_fv, ks->lim_couple, k64->lim_smem, f32 ? k64->lim_smem_w32 : k64->lim_smem_w};
     const std::pair<void (*)(KParams), size_t> lk[4] = {
         {out->minmax, out->smem_w}, {out->detect, out->smem_w}, {out->fv, out->smem}, {out->couple, out->smem}};
     for (const auto &k : lk)

@@ -1,6 +1,8 @@
 """Parity of the CUDA subcell limiter (Sec. 2.3) with the oracle, through
 the C ABI: the troubled elements of every step agree exactly (both sides
-decide in FP64), limited states within the FP64 tolerance, total mass
+decide in FP64; the FP32 path screens its FP32 subcell averages against
+an error bound and takes every decision too close to call in FP64),
+limited states within the FP64 tolerance, total mass
 conserved on the device, smooth data untouched (bitwise the unlimited
 step), and the combinations the limiter does not cover are refused."""
 import numpy as np
@@ -198,8 +200,8 @@ def test_limiter_on_advection_and_elasticity(pde):
     assert seen > 0
 
 
-def _limited_run(c, U, steps, upload_between, explicit_first=False):
-    s = _solver(c)
+def _limited_run(c, U, steps, upload_between, explicit_first=False, precision=A.ADERDG_FP64):
+    s = _solver(c, precision=precision)
     s.set_state(U)
     if explicit_first:  # one unlimited step through the explicit entry points
         dt = 0.5 * oracle.cfl_dt(c, U)
@@ -217,16 +219,17 @@ def _limited_run(c, U, steps, upload_between, explicit_first=False):
     return Ug, flags
 
 
+@pytest.mark.parametrize("precision", [A.ADERDG_FP64, A.ADERDG_MIXED_FP32], ids=["fp64", "mixed"])
 @pytest.mark.parametrize("explicit_first", [False, True], ids=["steps", "after_explicit_corrector"])
-def test_kept_extremes_equal_fresh_projections(explicit_first):
+def test_kept_extremes_equal_fresh_projections(explicit_first, precision):
     """The detection keeps each candidate's extreme subcell averages, and the
     next step reuses them for every element the limiter left untouched
     (neither troubled nor next to a troubled one).  A state upload before
     each step, or an explicit corrector call, makes every element project
     u^n afresh instead; the two runs agree bit for bit."""
     c, U = _explosion()
-    Ua, fa = _limited_run(c, U, 10, False, explicit_first)
-    Ub, fb = _limited_run(c, U, 10, True, explicit_first)
+    Ua, fa = _limited_run(c, U, 10, False, explicit_first, precision)
+    Ub, fb = _limited_run(c, U, 10, True, explicit_first, precision)
     np.testing.assert_array_equal(Ua, Ub)
     for a, b in zip(fa, fb):
         np.testing.assert_array_equal(a, b)
