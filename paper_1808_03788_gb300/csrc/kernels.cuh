@@ -1341,14 +1341,15 @@ k_corrector(const KParams P)
 }
 
 // Wave-speed maxima of the current state of solve 0 of the launch (the CFL
-// input of the first step after an upload): grid-stride over all nodes,
-// one atomic per warp.
+// input of the first step after an upload, and after a limited step that
+// changed the state): grid-stride over all nodes, one atomic per warp.
 template <class PDE, int DIM, int N, typename T>
 __global__ void __launch_bounds__(256) k_cfl(const KParams P)
 {
     using G = Geom<PDE, DIM, N>;
     constexpr int M = G::M;
     const SolveDesc &S = P.solves[0];
+    if (S.ctl->lim_keep) return;  // a limited step that changed nothing: the corrector's maxima stand
     const long long total = S.E * G::NS;
     double lmax[DIM];
 #pragma unroll

@@ -728,14 +728,10 @@ __global__ void __launch_bounds__(128) k_lim_detect32(const KParams P)
                 const double *uc = S.u_out + e * (L::NS * L::M);  // the candidate
                 int bad = 0;
                 for (int s = lane; s < L::NS; s += 32) {
-                    double q[L::M];
                     bool fin = true;
 #pragma unroll
-                    for (int v = 0; v < L::M; ++v) {
-                        q[v] = uc[s * L::M + v];
-                        fin = fin && !dbl_nonfinite(q[v]);
-                    }
-                    bad |= !fin || !lim_admissible<PDE>(P.pde, q);
+                    for (int v = 0; v < L::M; ++v) fin = fin && !dbl_nonfinite(uc[s * L::M + v]);
+                    bad |= !fin;
                 }
                 bad = __any_sync(0xffffffffu, bad);
                 if (!bad) {
@@ -743,6 +739,13 @@ __global__ void __launch_bounds__(128) k_lim_detect32(const KParams P)
                     float am[L::M];
                     lim_averages32_warp<L, DIM>(S.u_out, e, Pr32, u, avg, ta, tb, lane, ref, am);
                     lim_extremes32_warp<L>(avg, ref, lane, S.lim_mmc + e * (2 * L::M));
+                    // admissibility at the nodes: FP32 on ref + perturbation, FP64
+                    // where that is too close to call
+                    for (int s = lane; s < L::NS; s += 32) {
+                        int ok = lim_admissible32<PDE>(P.pde, ref, u + s * L::M);
+                        if (ok < 0) ok = lim_admissible<PDE>(P.pde, uc + s * L::M) ? 1 : 0;
+                        bad |= ok == 0;
+                    }
                     for (int a = lane; a < L::NSUB; a += 32) {
                         int ok = lim_admissible32<PDE>(P.pde, ref, avg + a * L::M);
                         if (ok < 0) {  // too close to call: the subcell's FP64 averages
@@ -940,6 +943,7 @@ __global__ void __launch_bounds__(128) k_lim_couple(const KParams P)
             if (!S.u_prev) continue;
             const double dt = solve_dt(P, S);
             if (!(dt > 0.0)) continue;
+            if (S.ctl->lim_count == 0u) continue;  // no troubled element this step: nothing to couple
             const double *tr = reinterpret_cast<const double *>(S.tr);
             for (long long e = blockIdx.x; e < S.E; e += gridDim.x) {
                 if (S.lim_flags[e]) continue;
