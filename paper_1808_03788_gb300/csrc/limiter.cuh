@@ -555,14 +555,18 @@ __device__ double lim_average64(const double *x, const double *Pr, int a, int v)
 }
 
 // FP32 subcell averages of element e of src (warp-wide): ref = its first
-// node, u = narrowed perturbations, avg = their averages, am[v] = max |dq|
-// of variable v (every lane gets ref and am).
+// node (every lane), u = narrowed perturbations, avg = their averages; lane
+// v < M also gets its variable's reference ref_l and largest perturbation
+// am_l (the per-variable FP64 work then runs once per warp instruction,
+// one variable per lane).
 template <class L, int DIM>
-__device__ __forceinline__ void lim_averages32_warp(const double *src, long long e, const float *Pr32, float *u, float *avg, float *ta,
-                                    float *tb, int lane, double *ref, float *am)
+__device__ __forceinline__ void lim_averages32_warp(const double *src, long long e, const float *Pr32, float *u, float *avg,
+                                                    float *ta, float *tb, int lane, double *ref, double &ref_l,
+                                                    float &am_l)
 {
     constexpr int M = L::M;
     const double *x = src + e * (L::NS * M);
+    float am[M];
 #pragma unroll
     for (int v = 0; v < M; ++v) {
         ref[v] = x[v];
@@ -576,18 +580,25 @@ __device__ __forceinline__ void lim_averages32_warp(const double *src, long long
             am[v] = fmaxf(am[v], fabsf(d));
         }
     }
+    ref_l = 0.0;
+    am_l = 0.f;
 #pragma unroll
-    for (int v = 0; v < M; ++v)
+    for (int v = 0; v < M; ++v) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) am[v] = fmaxf(am[v], __shfl_xor_sync(0xffffffffu, am[v], o));
+        am_l = lane == v ? am[v] : am_l;
+        ref_l = lane == v ? ref[v] : ref_l;
+    }
     __syncwarp();
     lim_tensor_team<DIM, M, L::S, L::n>(u, avg, ta, tb, Pr32, lane, 32, [] { __syncwarp(); });
 }
 
-// Extremes of the FP32 averages (warp-wide), kept as ref + widened value.
+// Extremes of the FP32 averages (warp-wide), kept as ref + widened value;
+// lane v < M writes variable v's pair.
 template <class L>
-__device__ __forceinline__ void lim_extremes32_warp(const float *avg, const double *ref, int lane, double *mm)
+__device__ __forceinline__ void lim_extremes32_warp(const float *avg, double ref_l, int lane, double *mm)
 {
+    float lo_l = 0.f, hi_l = 0.f;
 #pragma unroll
     for (int v = 0; v < L::M; ++v) {
         float lo = avg[v], hi = lo;
@@ -600,10 +611,12 @@ __device__ __forceinline__ void lim_extremes32_warp(const float *avg, const doub
             lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
             hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
         }
-        if (lane == 0) {
-            mm[v * 2] = ref[v] + flt_to_dbl(lo);
-            mm[v * 2 + 1] = ref[v] + flt_to_dbl(hi);
-        }
+        lo_l = lane == v ? lo : lo_l;
+        hi_l = lane == v ? hi : hi_l;
+    }
+    if (lane < L::M) {
+        mm[lane * 2] = ref_l + flt_to_dbl(lo_l);
+        mm[lane * 2 + 1] = ref_l + flt_to_dbl(hi_l);
     }
 }
 
@@ -669,10 +682,10 @@ __global__ void __launch_bounds__(128) k_lim_minmax32(const KParams P)
                     if (lane < 2 * L::M) S.lim_mm[e * (2 * L::M) + lane] = S.lim_mmc[e * (2 * L::M) + lane];
                     continue;
                 }
-                double ref[L::M];
-                float am[L::M];
-                lim_averages32_warp<L, DIM>(S.u_prev, e, Pr32, u, avg, ta, tb, lane, ref, am);
-                lim_extremes32_warp<L>(avg, ref, lane, S.lim_mm + e * (2 * L::M));
+                double ref[L::M], ref_l;
+                float am_l;
+                lim_averages32_warp<L, DIM>(S.u_prev, e, Pr32, u, avg, ta, tb, lane, ref, ref_l, am_l);
+                lim_extremes32_warp<L>(avg, ref_l, lane, S.lim_mm + e * (2 * L::M));
                 __syncwarp();
             }
         }
@@ -735,10 +748,10 @@ __global__ void __launch_bounds__(128) k_lim_detect32(const KParams P)
                 }
                 bad = __any_sync(0xffffffffu, bad);
                 if (!bad) {
-                    double ref[L::M];
-                    float am[L::M];
-                    lim_averages32_warp<L, DIM>(S.u_out, e, Pr32, u, avg, ta, tb, lane, ref, am);
-                    lim_extremes32_warp<L>(avg, ref, lane, S.lim_mmc + e * (2 * L::M));
+                    double ref[L::M], ref_l;
+                    float am_l;
+                    lim_averages32_warp<L, DIM>(S.u_out, e, Pr32, u, avg, ta, tb, lane, ref, ref_l, am_l);
+                    lim_extremes32_warp<L>(avg, ref_l, lane, S.lim_mmc + e * (2 * L::M));
                     // admissibility at the nodes: FP32 on ref + perturbation, FP64
                     // where that is too close to call
                     for (int s = lane; s < L::NS; s += 32) {
@@ -756,9 +769,12 @@ __global__ void __launch_bounds__(128) k_lim_detect32(const KParams P)
                         }
                         bad |= ok == 0;
                     }
-#pragma unroll
-                    for (int v = 0; v < L::M; ++v) {
-                        // the relaxed maximum principle of u^n over the element and its face neighbours
+                    // the relaxed maximum principle of u^n over the element and
+                    // its face neighbours: lane v forms variable v's bounds
+                    double blo_l = 0.0, bhi_l = 0.0;
+                    float rlo_l = 0.f, rhi_l = 0.f, tol_l = 0.f;
+                    if (lane < L::M) {
+                        const int v = lane;
                         long long klo = lim_key(S.lim_mm[(e * L::M + v) * 2]);
                         long long khi = lim_key(S.lim_mm[(e * L::M + v) * 2 + 1]);
 #pragma unroll
@@ -774,10 +790,17 @@ __global__ void __launch_bounds__(128) k_lim_detect32(const KParams P)
                             }
                         const double lo = lim_unkey(klo), hi = lim_unkey(khi);
                         const double delta = fmax(1e-4, 1e-3 * (hi - lo));
-                        const double blo = lo - delta, bhi = hi + delta;
-                        const float rlo = dbl_to_flt_rn(blo - ref[v]), rhi = dbl_to_flt_rn(bhi - ref[v]);
-                        const float tol = W::TOLC * EPS * rhoD * am[v] + 2.f * EPS * fmaxf(fabsf(rlo), fabsf(rhi)) +
-                                          1e-30f;
+                        blo_l = lo - delta;
+                        bhi_l = hi + delta;
+                        rlo_l = dbl_to_flt_rn(blo_l - ref_l);
+                        rhi_l = dbl_to_flt_rn(bhi_l - ref_l);
+                        tol_l = W::TOLC * EPS * rhoD * am_l + 2.f * EPS * fmaxf(fabsf(rlo_l), fabsf(rhi_l)) + 1e-30f;
+                    }
+#pragma unroll
+                    for (int v = 0; v < L::M; ++v) {
+                        const float rlo = __shfl_sync(0xffffffffu, rlo_l, v), rhi = __shfl_sync(0xffffffffu, rhi_l, v);
+                        const float tol = __shfl_sync(0xffffffffu, tol_l, v);
+                        const double blo = __shfl_sync(0xffffffffu, blo_l, v), bhi = __shfl_sync(0xffffffffu, bhi_l, v);
                         for (int a = lane; a < L::NSUB; a += 32) {
                             const float x = avg[a * L::M + v];
                             if (x < rlo - tol || x > rhi + tol) {
