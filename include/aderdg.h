@@ -135,12 +135,16 @@ extern "C" {
  * Predictor shapes 5 and 6 are shapes 0 and 1 with the derivative
  * contractions of the Picard iterations on the tensor cores (mma.sync
  * TF32 with three split products, FP32 accumulation) on the FP32 path; in
- * FP64 they repeat shapes 0 and 1.  For a given (PDE, d, N, precision)
- * every shape computes bit-identical results within each of these three
- * kernel families; the families round differently (all within the path's
- * tolerance); only the speed differs.  ADERDG_SHAPE_AUTOTUNE picks the
+ * FP64 they repeat shapes 0 and 1.  Predictor shapes 7 and 8 are shapes 0
+ * and 1 on the FP32 path of a conservative system with the state, not the
+ * fluxes, exchanged through shared memory (each pencil owner evaluates its
+ * flux component); bit-identical to shapes 0-2; elsewhere repeats of
+ * shapes 0 and 1.  For a given (PDE, d, N, precision) every shape computes
+ * bit-identical results within each of the three kernel families (shapes
+ * 0-2 and 7-8, 3-4, 5-6); the families round differently (all within the
+ * path's tolerance); only the speed differs.  ADERDG_SHAPE_AUTOTUNE picks the
  * shapes measured fastest on the current device. */
-#define ADERDG_NUM_PRED_SHAPES 7
+#define ADERDG_NUM_PRED_SHAPES 9
 #define ADERDG_NUM_CORR_SHAPES 4
 #define ADERDG_SHAPE_DEFAULT 0
 #define ADERDG_SHAPE_AUTOTUNE (-1)

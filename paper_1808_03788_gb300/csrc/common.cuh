@@ -527,7 +527,7 @@ struct TileShape {
 
 // Number of compiled shapes of the predictor and the corrector (shape 0 is
 // the default).
-constexpr int NSHAPE_P = 7;
+constexpr int NSHAPE_P = 9;
 constexpr int NSHAPE_C = 4;
 
 // Host-visible description of the compiled kernels of one (PDE, d, N,

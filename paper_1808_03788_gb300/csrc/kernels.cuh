@@ -184,7 +184,12 @@ struct PredCfg {
     static constexpr int TPAD = PAD3 ? 1 : 0;
     static constexpr int TSL = NS * MX + TPAD;
     static constexpr int FSL = n * TSL;
-    static constexpr int ELEM0x = cmax(DIM * FSL + (PAD3 ? 1 : 0), ((1 + DIM) * NS + (NREC > NS ? NREC : 0)) * M);
+    // shapes 7 and 8 (FP32, conservative systems): the state q goes through
+    // shared memory once (one more field) and each d-pencil owner takes F_d
+    // of its own pencil, instead of every flux field going through it
+    static constexpr bool QX = TS >= 7 && sizeof(T) == 4 && !PDE::NCP;
+    static constexpr int ELEM0x =
+        cmax((DIM + (QX ? 1 : 0)) * FSL + (PAD3 ? 1 : 0), ((1 + DIM) * NS + (NREC > NS ? NREC : 0)) * M);
     // the non-conservative layout's vector nodes (MX even) want every
     // element buffer 16-byte aligned
     static constexpr int ELEM0 = PDE::NCP ? round_up(ELEM0x, 4) : ELEM0x;
@@ -209,8 +214,8 @@ struct PredCfg {
                                  : sizeof(T) == 8 ? (n * M < 24 ? 3 : 2) : ((n * M <= 20 || (M == 9 && n <= 4)) ? 3 : 2);
     // shapes 5 and 6: the CTA geometry of shapes 0 and 1 with the derivative
     // contractions on the tensor cores (FP32 path only; see contract_all_mma)
-    static constexpr int TSG = TS >= 5 ? TS - 5 : TS;
-    static constexpr bool TC = TS >= 5 && sizeof(T) == 4 && n <= 8;
+    static constexpr int TSG = TS >= 7 ? TS - 7 : (TS >= 5 ? TS - 5 : TS);
+    static constexpr bool TC = TS >= 5 && TS <= 6 && sizeof(T) == 4 && n <= 8;
     static constexpr int TARGET = TSG == 1 ? TARGET0 / 2 : (TSG == 2 ? TARGET0 * 2 : TARGET0);
     static constexpr int EPB_S = cmax(1, (int)((110 * 1024) / (ELEM * sizeof(T))));
     static constexpr int EPB = cmin(cmax(1, TARGET / NS), EPB_S);
@@ -288,6 +293,52 @@ __device__ __forceinline__ void contract_all(T *ebuf, int t0, int p0, int t, int
         if constexpr (D == 0) contract_pencil<C, D, T>(ebuf, t0, p0, O.Dm[D]);
         else contract_pencil<C, D, T>(ebuf + D * C::FSL, t, p, O.Dm[D]);
         contract_all<C, T, D + 1>(ebuf, t0, p0, t, p, O);
+    }
+}
+
+// -Dhat F_d along direction D on pencil (t, p) from the state field: the
+// pencil's n nodes of q (field DIM), the flux F_D at each (the flux functor
+// gives every direction; the others are dead code once it is inlined), the
+// contraction, and the result into field D -- the same values as
+// contract_pencil on the flux field.
+template <class C, int D, typename T, class Flux>
+__device__ __forceinline__ void contract_pencil_qx(T *ebuf, int t, int p, const T *Dm, Flux &flx)
+{
+    constexpr int n = C::n, M = C::M;
+    constexpr int pd = ipow(n, D);
+    const int s0 = (p % pd) + (p / pd) * pd * n;
+    const T *qb = ebuf + C::DIMS * C::FSL + t * C::TSL + s0 * M;
+    T f[n][M];
+#pragma unroll
+    for (int j = 0; j < n; ++j) {
+        T x[M], F[C::DIMS][M];
+        NodeIO<T, M>::load(qb + j * pd * M, x);
+        flx(x, F);
+#pragma unroll
+        for (int v = 0; v < M; ++v) f[j][v] = F[D][v];
+    }
+    T *base = ebuf + D * C::FSL + t * C::TSL + s0 * M;
+#pragma unroll
+    for (int i = 0; i < n; ++i) {
+        T y[M];
+#pragma unroll
+        for (int v = 0; v < M; ++v) {
+            T acc = Dm[i * n] * f[0][v];
+#pragma unroll
+            for (int j = 1; j < n; ++j) acc += Dm[i * n + j] * f[j][v];
+            y[v] = acc;
+        }
+        NodeIO<T, M>::store(base + i * pd * M, y);
+    }
+}
+
+template <class C, typename T, class Flux, int D = 0>
+__device__ __forceinline__ void contract_all_qx(T *ebuf, int t0, int p0, int t, int p, const Ops<T> &O, Flux &flx)
+{
+    if constexpr (D < C::DIMS) {
+        if constexpr (D == 0) contract_pencil_qx<C, D, T>(ebuf, t0, p0, O.Dm[D], flx);
+        else contract_pencil_qx<C, D, T>(ebuf, t, p, O.Dm[D], flx);
+        contract_all_qx<C, T, Flux, D + 1>(ebuf, t0, p0, t, p, O, flx);
     }
 }
 
@@ -714,19 +765,29 @@ k_predictor(const KParams P)
         }
         // ---- Picard iterations of eq. pde.st2 ------------------------------
         for (int it = it0; it < P_it; ++it) {
-#pragma unroll
-            for (int t = 0; t < n; ++t) {
-                T F[DIM][M];
-                xch(q[t], F);
+            if constexpr (C::QX) {
+                // the state through shared memory; each pencil owner forms its F_d
                 if (act) {
 #pragma unroll
-                    for (int d = 0; d < DIM; ++d)
-                        NodeIO<T, C::MX>::store(ebuf + d * C::FSL + t * C::TSL + s * C::MX, F[d]);
+                    for (int t = 0; t < n; ++t) NodeIO<T, M>::store(ebuf + DIM * C::FSL + t * C::TSL + s * M, q[t]);
                 }
+                __syncthreads();
+                if (act) contract_all_qx<C, T>(ebuf, tk0, pk0, tk, pk, O, flx);
+            } else {
+#pragma unroll
+                for (int t = 0; t < n; ++t) {
+                    T F[DIM][M];
+                    xch(q[t], F);
+                    if (act) {
+#pragma unroll
+                        for (int d = 0; d < DIM; ++d)
+                            NodeIO<T, C::MX>::store(ebuf + d * C::FSL + t * C::TSL + s * C::MX, F[d]);
+                    }
+                }
+                __syncthreads();
+                if constexpr (C::TC) contract_all_mma<C>(reinterpret_cast<float *>(smem_raw) + C::SHARED, tcop);
+                else if (act) contract_all<C, T>(ebuf, tk0, pk0, tk, pk, O);
             }
-            __syncthreads();
-            if constexpr (C::TC) contract_all_mma<C>(reinterpret_cast<float *>(smem_raw) + C::SHARED, tcop);
-            else if (act) contract_all<C, T>(ebuf, tk0, pk0, tk, pk, O);
             __syncthreads();
             {
                 const T dtT = sDt[0];
@@ -1417,7 +1478,14 @@ struct KS {
 template <class PDE, int DIM, int N, typename T, int TS, bool EX = false>
 constexpr TileShape pred_shape()
 {
-    if constexpr (TS >= 5) {
+    if constexpr (TS >= 7) {
+        if constexpr (PredCfg<PDE, DIM, N, T, TS>::QX) {
+            using C = PredCfg<PDE, DIM, N, T, TS>;  // shapes 0 / 1 exchanging the state (FP32, conservative)
+            return TileShape{&k_predictor<PDE, DIM, N, T, TS, EX>, C::THREADS, C::EPB, C::BYTES};
+        } else {
+            return pred_shape<PDE, DIM, N, T, TS - 7, EX>();  // repeats of shapes 0 and 1
+        }
+    } else if constexpr (TS >= 5) {
         if constexpr (PredCfg<PDE, DIM, N, T, TS>::TC) {
             using C = PredCfg<PDE, DIM, N, T, TS>;  // shapes 0 / 1 with tensor-core contractions (FP32)
             return TileShape{&k_predictor<PDE, DIM, N, T, TS, EX>, C::THREADS, C::EPB, C::BYTES};
@@ -1458,11 +1526,12 @@ const KernelSet KS<PDE, DIM, N, T>::value = {
     lim_kernel<PDE, DIM, N, T, 4>(), lim_kernel<PDE, DIM, N, T, 5>(), LimWarp32<LimCfg<PDE, DIM, N>>::BYTES,
     {pred_shape<PDE, DIM, N, T, 0>(), pred_shape<PDE, DIM, N, T, 1>(), pred_shape<PDE, DIM, N, T, 2>(),
      pred_shape<PDE, DIM, N, T, 3>(), pred_shape<PDE, DIM, N, T, 4>(), pred_shape<PDE, DIM, N, T, 5>(),
-     pred_shape<PDE, DIM, N, T, 6>()},
+     pred_shape<PDE, DIM, N, T, 6>(), pred_shape<PDE, DIM, N, T, 7>(), pred_shape<PDE, DIM, N, T, 8>()},
     {pred_shape<PDE, DIM, N, T, 0, true>(), pred_shape<PDE, DIM, N, T, 1, true>(),
      pred_shape<PDE, DIM, N, T, 2, true>(), pred_shape<PDE, DIM, N, T, 3, true>(),
      pred_shape<PDE, DIM, N, T, 4, true>(), pred_shape<PDE, DIM, N, T, 5, true>(),
-     pred_shape<PDE, DIM, N, T, 6, true>()},
+     pred_shape<PDE, DIM, N, T, 6, true>(), pred_shape<PDE, DIM, N, T, 7, true>(),
+     pred_shape<PDE, DIM, N, T, 8, true>()},
     {corr_shape<PDE, DIM, N, T, 0>(), corr_shape<PDE, DIM, N, T, 1>(), corr_shape<PDE, DIM, N, T, 2>(),
      corr_shape<PDE, DIM, N, T, 3>()},
     0, 0};

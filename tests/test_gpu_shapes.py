@@ -83,7 +83,7 @@ def test_every_shape_is_bitwise_the_default(case, precision):
             assert (info["pred_shape"], info["corr_shape"]) == (ps, cs)
             seen.add((info["pred_threads"], info["pred_epb"], info["corr_threads"], info["corr_epb"]))
             assert k == k0
-            ref = U5 if (tc and ps >= 5) else (U3 if (xt and ps in (3, 4)) else U0)
+            ref = U5 if (tc and ps in (5, 6)) else (U3 if (xt and ps in (3, 4)) else U0)
             np.testing.assert_array_equal(U, ref, err_msg="shapes %d/%d" % (ps, cs))
     for other, applies in ((U3, xt), (U5, tc)):
         if applies:
