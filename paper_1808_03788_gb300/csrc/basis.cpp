@@ -308,6 +308,18 @@ int check_problem(const aderdg_mesh_t &mesh, const aderdg_pde_t &pde, long long 
     return rc ? rc : check_pde_params(pde, why);
 }
 
+void fill_desc_lift(SolveDesc &sd, int N)
+{
+    Basis b;
+    std::memset(&b, 0, sizeof(b));
+    if (build_basis(N, b)) return;
+    for (int d = 0; d < 3; ++d)
+        for (int k = 0; k < NMAX; ++k) {
+            sd.lift_f[0][d][k] = k < b.n ? (float)(sd.inv_dx[d] * b.inv_w[k] * b.F0[k]) : 0.f;
+            sd.lift_f[1][d][k] = k < b.n ? (float)(sd.inv_dx[d] * b.inv_w[k] * b.F1[k]) : 0.f;
+        }
+}
+
 int default_picard(int N, int guess)
 {
     if (guess == 3) return 2;  // a degree-N guess: one iteration, plus one

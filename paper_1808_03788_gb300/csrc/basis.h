@@ -23,6 +23,9 @@ int pde_nvar(int kind, int dim);
 int check_mesh(const aderdg_mesh_t &mesh, int kind, long long *E, const char **why);
 int check_pde_params(const aderdg_pde_t &pde, const char **why);
 int check_problem(const aderdg_mesh_t &mesh, const aderdg_pde_t &pde, long long *E, const char **why);
+// The FP32 lift coefficients of d (from its inv_dx and the degree-N basis),
+// the same values as float(inv_dx[d] * inv_w[k] * F0|F1[k]) in double.
+void fill_desc_lift(SolveDesc &d, int N);
 // derived constants P.c / P.cf of PDE kind `kind` from P.p (see PdeParams)
 void fill_pde_consts(int kind, PdeParams &P);
 // fill kp.od / kp.of from kp.b

@@ -361,6 +361,7 @@ public:
                 tc += (s->E + g.kso.corr_epb - 1) / g.kso.corr_epb;
                 for (int k = 0; k < 3; ++k) { d.cells[k] = s->cells[k]; d.inv_dx[k] = s->inv_dx[k]; }
                 fill_desc_spacing(d);
+                fill_desc_lift(d, s->N);
                 d.picard = s->picard;
                 d.guess = s->guess;
                 d.picard_first = default_picard(s->N, ADERDG_GUESS_ORDER3);

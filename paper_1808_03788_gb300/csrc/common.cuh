@@ -159,6 +159,9 @@ struct SolveDesc {
     const int *elist;
     const void *halo_tr[3][2];
     const double *halo_ref[3][2];
+    // FP32 path: the corrector's lift coefficients (1/dx_d) F_{0|1}[k] / w_k
+    // rounded to float, [side][d][k] (fill_desc_lift)
+    float lift_f[2][3][NMAX];
 };
 
 inline void fill_desc_spacing(SolveDesc &d)

@@ -1067,7 +1067,8 @@ struct CorrCfg {
     // (the path integral needs absolute face states)
     static constexpr size_t O_REFO = O_DEL + (DELTA ? align16(sizeof(T) * EPB * 2 * DIM * 2 * M) : 0);
     static constexpr size_t O_RED = O_REFO + (DELTA && PDE::NCP ? align16(sizeof(T) * EPB * M) : 0);
-    static constexpr size_t BYTES = O_RED + 64 * sizeof(double);  // one unit (the CTA, or a warp)
+    // the CTA reduction: 16 warps x 4 values, then 16 flags
+    static constexpr size_t BYTES = O_RED + 64 * sizeof(double) + 16 * sizeof(int);  // one unit (the CTA, or a warp)
     static constexpr int NW = WM ? cmax(1, cmin(8, (int)((200 * 1024) / BYTES))) : 1;
     static constexpr int THREADS = WM ? 32 * NW : THREADS_CTA;
     static constexpr int EPB_TILE = WM ? NW : EPB;  // elements per tile of the launch
@@ -1183,9 +1184,14 @@ k_corrector(const KParams P)
         }
         for (int i = tid; i < DIM * n; i += nthr) {
             const int d = i / n, k = i % n;
-            const double idx = P.solves[si].inv_dx[d];  // runtime index: read from global
-            sL[(0 * 3 + d) * NMAX + k] = T(idx * P.b.inv_w[k] * P.b.F0[k]);
-            sL[(1 * 3 + d) * NMAX + k] = T(idx * P.b.inv_w[k] * P.b.F1[k]);
+            if constexpr (sizeof(T) == 4) {  // precomputed on the host: no FP64 work here
+                sL[(0 * 3 + d) * NMAX + k] = P.solves[si].lift_f[0][d][k];
+                sL[(1 * 3 + d) * NMAX + k] = P.solves[si].lift_f[1][d][k];
+            } else {
+                const double idx = P.solves[si].inv_dx[d];  // runtime index: read from global
+                sL[(0 * 3 + d) * NMAX + k] = T(idx * P.b.inv_w[k] * P.b.F0[k]);
+                sL[(1 * 3 + d) * NMAX + k] = T(idx * P.b.inv_w[k] * P.b.F1[k]);
+            }
         }
         stage<C::G_OWN>(sOwn, tr + (long long)e0 * NREC * RS, ne * (int)C::OWN, tid, nthr);
         if constexpr (C::STAGE_UV) {
@@ -1378,22 +1384,27 @@ k_corrector(const KParams P)
             }
             const unsigned anybad = __any_sync(0xffffffffu, bad);
             const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+            // the CTA's maxima in the compute type (on the FP32 path no FP64
+            // instruction: one costs the whole warp's FP64 issue slot however
+            // few lanes it has); widened once for the atomic
+            T *redT = reinterpret_cast<T *>(red);
+            int *redB = reinterpret_cast<int *>(red + 64);
             if (lane == 0) {
 #pragma unroll
-                for (int d = 0; d < DIM; ++d) red[warp * 4 + d] = double(lmax[d]);
-                red[warp * 4 + 3] = anybad ? 1.0 : 0.0;
+                for (int d = 0; d < DIM; ++d) redT[warp * 4 + d] = lmax[d];
+                redB[warp] = anybad ? 1 : 0;
             }
             __syncthreads();
             if (threadIdx.x == 0) {
                 const int nw = blockDim.x >> 5;
-                double b = 0.0;
+                int b = 0;
                 for (int d = 0; d < DIM; ++d) {
-                    double x = 0.0;
-                    for (int w = 0; w < nw; ++w) x = fmax(x, red[w * 4 + d]);
-                    atomicMax(&S.ctl->lam_acc[d], (unsigned long long)__double_as_longlong(x));
+                    T x = T(0);
+                    for (int w = 0; w < nw; ++w) x = tmax(x, redT[w * 4 + d]);
+                    atomicMax(&S.ctl->lam_acc[d], (unsigned long long)__double_as_longlong(double(x)));
                 }
-                for (int w = 0; w < nw; ++w) b = fmax(b, red[w * 4 + 3]);
-                if (b > 0.0) atomicOr(&S.ctl->flags, FLAG_NONFINITE);
+                for (int w = 0; w < nw; ++w) b |= redB[w];
+                if (b) atomicOr(&S.ctl->flags, FLAG_NONFINITE);
             }
         }
         usync();  // shared buffers are reused by the next tile

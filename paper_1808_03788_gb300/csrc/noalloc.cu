@@ -137,6 +137,7 @@ extern "C" int aderdg_step_noalloc(const aderdg_mesh_t *mesh, int N, int nVar, c
         sd.inv_dx[d] = d < mesh->dim ? 1.0 / ((mesh->hi[d] - mesh->lo[d]) / mesh->cells[d]) : 1.0;
     }
     fill_desc_spacing(sd);
+    fill_desc_lift(sd, N);
     sd.picard = picard_iters > 0 ? picard_iters : N + 1;
     sd.u = u_in;
     sd.u_out = u_out;

@@ -591,6 +591,7 @@ extern "C" int aderdg_dd_create(const aderdg_mesh_t *mesh, int N, int nVar, cons
             base.inv_dx[d] = h->inv_dx[d];
         }
         fill_desc_spacing(base);
+        fill_desc_lift(base, N);
         base.picard = h->picard;
         base.guess = h->guess;
         base.picard_first = default_picard(N, ADERDG_GUESS_ORDER3);

@@ -465,6 +465,7 @@ int aderdg_create(const aderdg_mesh_t *mesh, int N, int nVar, const aderdg_pde_t
         sd.inv_dx[d] = h->inv_dx[d];
     }
     fill_desc_spacing(sd);
+    fill_desc_lift(sd, N);
     sd.picard = h->picard;
     sd.guess = h->guess;
     sd.picard_first = default_picard(N, ADERDG_GUESS_ORDER3);

@@ -246,6 +246,7 @@ int measure(const KernelSet *ks, int pde, int dim, int N, int m, const PdeParams
         sd.inv_dx[d] = d < dim ? (double)k : 1.0;  // unit box
     }
     fill_desc_spacing(sd);
+    fill_desc_lift(sd, N);
     sd.picard = n;
     sd.u = u;
     sd.u_out = uo;
