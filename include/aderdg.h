@@ -104,18 +104,21 @@ extern "C" {
  *          previous predictor (the first after aderdg_set_state, or a
  *          predictor call with an explicit dt) takes ORDER3 with its
  *          default count.  Holds n^(d+1) m values per element more.
- * CERK     continuous extension of the classical fourth-order Runge-Kutta
- *          method (a CERK scheme, which Sec. 2.2 names): k1 = L(u),
- *          k2 = L(u + dt k1/2), k3 = L(u + dt k2/2), k4 = L(u + dt k3),
- *          q0 = u + dt sum_i b_i(tau/dt) k_i with the cubics
+ * CERK     dense output of a continuous explicit Runge-Kutta scheme (the
+ *          CERK schemes Sec. 2.2 names): k_i = L(u + dt sum_{j<i} a_ij k_j),
+ *          q0 = u + dt sum_i b_i(tau/dt) k_i, of uniform order k in time.
+ *          N <= 4: the classical fourth-order method (k2 = L(u + dt k1/2),
+ *          k3 = L(u + dt k2/2), k4 = L(u + dt k3)) with the cubics
  *          b1 = th - 3th^2/2 + 2th^3/3, b2 = b3 = th^2 - 2th^3/3,
- *          b4 = -th^2/2 + 2th^3/3 (uniform order 3, degree 3 in time).
+ *          b4 = -th^2/2 + 2th^3/3 (k = 3).  N >= 5: a six-stage scheme
+ *          with quartic weights (k = 4: degree N - 1 at N = 5, where one
+ *          Picard iteration suffices).
  * with tau = t - t^n and L(w) = -div F(w), the element-local nodal
  * derivative of the flux (plus -B(w) grad w + S(w) where the PDE has
  * them).  The default Picard count after a guess of degree k in time is
- * max(1, N + 1 - k): N+1 for TRIVIAL, N for ORDER2, N-1 for ORDER3, N-2 for
- * CERK (the paper notes N - k iterations suffice), and 2 for EXTRAP
- * (degree N). */
+ * max(1, N + 1 - k): N+1 for TRIVIAL, N for ORDER2, N-1 for ORDER3, N-2
+ * (N <= 4) or N-3 (N >= 5) for CERK (the paper notes N - k iterations
+ * suffice), and 2 for EXTRAP (degree N). */
 #define ADERDG_GUESS_TRIVIAL 0
 #define ADERDG_GUESS_ORDER2 1
 #define ADERDG_GUESS_ORDER3 2
@@ -545,6 +548,16 @@ int aderdg_autotune(const aderdg_solve_spec_t *spec, int precision, const char *
  * (DFMA), kind 1: FP32 (FFMA).  Synchronising; runs for ~0.1 s.  Used as
  * the denominator of the ALU rooflines. */
 int aderdg_peak_tflops(int kind, double *tflops);
+
+/* Check utility: y[i] = 1 / x[i] as the kernels compute it on the device
+ * (the flux's reciprocal of the density and of volume fractions, in the
+ * compute type: precision ADERDG_FP64, or ADERDG_MIXED_FP32 for the FP32
+ * path, where x is rounded to float and the result widened).  x and y are
+ * n doubles in host memory (caller-owned, n <= 2^26); x must hold normal,
+ * finite, nonzero numbers.  The result is within one ulp of the correctly
+ * rounded 1/x in the compute type.  Synchronising; allocates and frees
+ * 16 n bytes of device memory.  ADERDG_E_INVAL on bad arguments. */
+int aderdg_device_recip(const double *x, double *y, long long n, int precision);
 
 #ifdef __cplusplus
 }

@@ -106,8 +106,10 @@ def lib():
             L.orc_face_flux.argtypes = [cp, C.c_int, dp, dp, dp, dp, dp, dp]
             L.orc_face_flux.restype = None
             L.orc_nevolved.argtypes = [cp]
-            L.orc_cerk_weights.argtypes = [C.c_double, dp]
+            L.orc_cerk_weights.argtypes = [C.c_int, C.c_double, dp]
             L.orc_cerk_weights.restype = None
+            L.orc_cerk_scheme.argtypes = [C.c_int, dp, dp, C.POINTER(C.c_int)]
+            L.orc_cerk_scheme.restype = C.c_int
             L.orc_step_limited.argtypes = [cp, dp, C.c_double, C.POINTER(C.c_int), C.POINTER(C.c_long)]
             L.orc_subcell_ops.argtypes = [C.c_int, dp, dp]
             L.orc_cfl_dt.argtypes = [cp, dp]
@@ -239,11 +241,22 @@ def initial_guess(cfg: Cfg, u: np.ndarray, dt: float) -> np.ndarray:
     return q0
 
 
-def cerk_weights(theta: float) -> np.ndarray:
-    """The four cubic weights b_i(theta) of the CERK guess."""
-    out = np.zeros(4)
-    lib().orc_cerk_weights(float(theta), _p(out))
-    return out
+def cerk_scheme(N: int):
+    """The continuous Runge-Kutta scheme of the CERK guess for degree N:
+    (A [s, s] strictly lower triangular, beta [s, p]) with the dense-output
+    weights b_i(theta) = sum_k beta[i, k] theta^(k+1); p is its order."""
+    a = np.zeros(100)
+    beta = np.zeros(60)
+    p = C.c_int()
+    s = lib().orc_cerk_scheme(int(N), _p(a), _p(beta), C.byref(p))
+    return a[:s * s].reshape(s, s).copy(), beta[:s * p.value].reshape(s, p.value).copy()
+
+
+def cerk_weights(theta: float, N: int = 4) -> np.ndarray:
+    """The dense-output weights b_i(theta) of the CERK guess for degree N."""
+    out = np.zeros(10)
+    lib().orc_cerk_weights(int(N), float(theta), _p(out))
+    return out[:cerk_scheme(N)[0].shape[0]].copy()
 
 
 def initial_guess_extrap(cfg: Cfg, u: np.ndarray, dt: float, qprev: np.ndarray, ratio: float) -> np.ndarray:

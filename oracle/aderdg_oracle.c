@@ -126,8 +126,8 @@ typedef struct {
                          2 third order u + tau k1 + tau^2 (k2 - k1) / (2 dt);
                          3 extrapolation of the previous step's predictor
                            (orc_run; the first step, and single steps, use 2);
-                         4 continuous Runge-Kutta (CERK) dense output of the
-                           classical fourth-order method, a cubic in time */
+                         4 continuous Runge-Kutta (CERK) dense output, a
+                           polynomial of degree max(3, N - 1) in time */
     int limiter;      /* 1: a posteriori subcell finite-volume limiter
                          (Sec. 2.3) after every step */
 } orc_cfg;
@@ -461,11 +461,13 @@ static int make_basis(int N, basis *b)
  * paper's sufficiency rule (a degree N-1 guess needs one iteration, Sec.
  * 2.2) corresponds to N-k; the default keeps the one extra iteration the
  * trivial guess has. */
+static int cerk_order(int N);
+
 int orc_picard_count(const orc_cfg *c)
 {
     if (c->picard != 0) return c->picard;
     if (c->guess == 3) return 2;  /* a degree-N guess: one iteration, plus one */
-    int P = c->N + 1 - (c->guess == 1 ? 1 : c->guess == 2 ? 2 : c->guess == 4 ? 3 : 0);
+    int P = c->N + 1 - (c->guess == 1 ? 1 : c->guess == 2 ? 2 : c->guess == 4 ? cerk_order(c->N) : 0);
     return P < 1 ? 1 : P;
 }
 
@@ -547,22 +549,94 @@ static void l_operator(const orc_cfg *c, const basis *b, const double *w, double
  * beyond the flux term). */
 static int has_nc_or_source(const orc_cfg *c) { return c->pde == 4 || (c->pde == 1 && c->prm[3] != 0.0); }
 
-/* Weights of the continuous extension of the classical fourth-order
- * Runge-Kutta method (stages at 0, 1/2, 1/2, 1 with a21 = a32 = 1/2,
- * a43 = 1): the cubics b_i(th), th = tau / dt, that satisfy the order
- * conditions of a continuous Runge-Kutta scheme to order 3 for every th,
- *   sum b_i = th, sum b_i c_i = th^2/2, sum b_i c_i^2 = th^3/3,
- *   sum b_i a_ij c_j = th^3/6,
- * and reduce to the method's weights 1/6, 1/3, 1/3, 1/6 at th = 1:
- *   b1 = th - 3 th^2/2 + 2 th^3/3, b2 = b3 = th^2 - 2 th^3/3,
- *   b4 = -th^2/2 + 2 th^3/3. */
-void orc_cerk_weights(double th, double *bw)
+/* Continuous explicit Runge-Kutta (CERK) schemes for the CERK guess
+ * (Sec. 2.2 names the continuous extensions of Owren and Zennaro and prints
+ * no coefficients).  A scheme of s stages takes k_i = L(u + dt sum_{j<i}
+ * a_ij k_j) and has the dense output u(t^n + th dt) ~ u + dt sum_i b_i(th)
+ * k_i with polynomial weights b_i(th) = sum_k beta_ik th^(k+1) (no constant
+ * term).  It has uniform order p when, for every rooted tree t of order
+ * |t| <= p with elementary weights Phi_i(t) and density gamma(t),
+ *   sum_i b_i(th) Phi_i(t) = th^|t| / gamma(t)   for every th in [0, 1],
+ * so the dense output is a polynomial of degree p in time whose error is
+ * O(dt^(p+1)) uniformly in th.
+ *   order 3: the classical fourth-order method (stages at 0, 1/2, 1/2, 1,
+ *     a21 = a32 = 1/2, a43 = 1) with the cubic dense output that ends in its
+ *     weights 1/6, 1/3, 1/3, 1/6 at th = 1:
+ *     b1 = th - 3 th^2/2 + 2 th^3/3, b2 = b3 = th^2 - 2 th^3/3,
+ *     b4 = -th^2/2 + 2 th^3/3;
+ *   order 4: six stages with quartic weights.  Five stages do not reach
+ *     uniform order 4; this six-stage tableau was found by a numerical
+ *     search over the stage coefficients, minimising max |b_i(th)| on
+ *     [0, 1] (0.35) with nodes c_i in [0, 1], then solved to 40 digits by
+ *     Newton's method on the eight order conditions.
+ * The values below are those digits rounded to 20; the order conditions
+ * hold to rounding (pinned in the tests). */
+#define ORC_CERK_SMAX 10
+typedef struct {
+    int s, p;
+    double a[ORC_CERK_SMAX][ORC_CERK_SMAX];
+    double beta[ORC_CERK_SMAX][6];
+} cerk_scheme;
+
+static const cerk_scheme cerk_order3 = {
+    4, 3,
+    {{0}, {0.5}, {0.0, 0.5}, {0.0, 0.0, 1.0}},
+    {{1.0, -1.5, 2.0 / 3.0}, {0.0, 1.0, -2.0 / 3.0}, {0.0, 1.0, -2.0 / 3.0}, {0.0, -0.5, 2.0 / 3.0}},
+};
+
+static const cerk_scheme cerk_order4 = {
+    6, 4,
+    {{0},
+     {0.50849583384840113958},
+     {0.046949965621769603951, 0.4819237260551746206},
+     {0.16975684152901151769, 0.071063883183927482688, -0.028300707574148454932},
+     {-0.076143308578057834897, -0.14017373747662979618, 0.048722116369755792049, 0.50735746259681266958},
+     {0.12216705712724082426, 0.12299809408491295783, 0.48070156394276517752, 0.02616528026761548546,
+      0.093926602975396757805}},
+    {{1.0, -3.9153671327673924417, 5.9934951934142588637, -3.0269093126242169958},
+     {0.0, -0.80100882679982742762, 2.6530980786357989255, -1.7516658795402877462},
+     {0.0, -0.89842534403733875434, 2.9131919603555952085, -1.8758298804924840825},
+     {0.0, 5.3725609369242888065, -13.195842800637089784, 8.1610686740032049053},
+     {0.0, -0.070646768460630971334, 2.90293867489981116, -2.8111171676340170791},
+     {0.0, 0.31288713514090078845, -1.2668811066683743739, 1.3044535662878009984}},
+};
+
+/* The scheme of the CERK guess for degree N: the paper's rule wants a guess
+ * of degree N - 1 in time (one Picard iteration then suffices), so order
+ * N - 1, at least 3 and at most the highest order built. */
+static const cerk_scheme *cerk_for(int N)
 {
-    const double t2 = th * th, t3 = t2 * th;
-    bw[0] = th - 1.5 * t2 + 2.0 * t3 / 3.0;
-    bw[1] = t2 - 2.0 * t3 / 3.0;
-    bw[2] = bw[1];
-    bw[3] = -0.5 * t2 + 2.0 * t3 / 3.0;
+    return N >= 5 ? &cerk_order4 : &cerk_order3;
+}
+
+static int cerk_order(int N) { return cerk_for(N)->p; }
+
+/* Tableau of the CERK guess for degree N: a[i * s + j] (row-major s x s,
+ * zero on and above the diagonal) and beta[i * p + k] (b_i(th) = sum_k
+ * beta_ik th^(k+1)).  Returns s; *p receives the order. */
+int orc_cerk_scheme(int N, double *a, double *beta, int *p)
+{
+    const cerk_scheme *cs = cerk_for(N);
+    for (int i = 0; i < cs->s; ++i) {
+        for (int j = 0; j < cs->s; ++j) a[i * cs->s + j] = j < i ? cs->a[i][j] : 0.0;
+        for (int k = 0; k < cs->p; ++k) beta[i * cs->p + k] = cs->beta[i][k];
+    }
+    *p = cs->p;
+    return cs->s;
+}
+
+/* b_i(th) of the CERK guess for degree N (s values). */
+void orc_cerk_weights(int N, double th, double *bw)
+{
+    const cerk_scheme *cs = cerk_for(N);
+    for (int i = 0; i < cs->s; ++i) {
+        double v = 0.0, thk = th;
+        for (int k = 0; k < cs->p; ++k) {
+            v += cs->beta[i][k] * thk;
+            thk *= th;
+        }
+        bw[i] = v;
+    }
 }
 
 /* Initial guess q0 at the space-time nodes (t^n + tau_t, x_s),
@@ -577,9 +651,14 @@ void orc_cerk_weights(double th, double *bw)
  *      polynomials evaluated with the Lagrange basis of the time nodes;
  *      without qprev, guess 2.
  *   4: the CERK guess (Sec. 2.2 names continuous extension Runge-Kutta
- *      schemes): k1 = L(u), k2 = L(u + dt k1/2), k3 = L(u + dt k2/2),
- *      k4 = L(u + dt k3), q0 = u + dt sum_i b_i(tau/dt) k_i (orc_cerk_weights)
- * gw holds (5 + dim) ns m values. */
+ *      schemes): k_i = L(u + dt sum_{j<i} a_ij k_j), q0 = u + dt sum_i
+ *      b_i(tau/dt) k_i with the scheme of order max(3, N - 1) (cerk_for)
+ * gw holds guess_work_len(c) values. */
+static size_t guess_work_len(const orc_cfg *c)
+{
+    return (size_t)ipow(c->N + 1, c->dim) * c->m * (ORC_CERK_SMAX + 1 + c->dim);
+}
+
 static void initial_guess(const orc_cfg *c, const basis *b, const double *u, double dt, double *q,
                           double *gw, const double *qprev, double ratio)
 {
@@ -600,20 +679,24 @@ static void initial_guess(const orc_cfg *c, const basis *b, const double *u, dou
         return;
     }
     if (c->guess == 4) {
-        double *k1 = gw, *k2 = gw + nsm, *k3 = gw + 2 * nsm, *k4 = gw + 3 * nsm, *w = gw + 4 * nsm,
-               *tmp = gw + 5 * nsm;
-        l_operator(c, b, u, k1, tmp);
-        for (size_t i = 0; i < nsm; ++i) w[i] = u[i] + 0.5 * dt * k1[i];
-        l_operator(c, b, w, k2, tmp);
-        for (size_t i = 0; i < nsm; ++i) w[i] = u[i] + 0.5 * dt * k2[i];
-        l_operator(c, b, w, k3, tmp);
-        for (size_t i = 0; i < nsm; ++i) w[i] = u[i] + dt * k3[i];
-        l_operator(c, b, w, k4, tmp);
+        const cerk_scheme *cs = cerk_for(c->N);
+        double *k = gw, *w = gw + (size_t)ORC_CERK_SMAX * nsm, *tmp = w + nsm;  /* k_i at k + i nsm */
+        for (int st = 0; st < cs->s; ++st) {
+            for (size_t i = 0; i < nsm; ++i) {
+                double acc = 0.0;
+                for (int j = 0; j < st; ++j) acc += cs->a[st][j] * k[(size_t)j * nsm + i];
+                w[i] = u[i] + dt * acc;
+            }
+            l_operator(c, b, w, k + (size_t)st * nsm, tmp);
+        }
         for (int t = 0; t < n; ++t) {
-            double bw[4];
-            orc_cerk_weights(b->x[t], bw);
-            for (size_t i = 0; i < nsm; ++i)
-                q[(size_t)t * nsm + i] = u[i] + dt * (bw[0] * k1[i] + bw[1] * k2[i] + bw[2] * k3[i] + bw[3] * k4[i]);
+            double bw[ORC_CERK_SMAX];
+            orc_cerk_weights(c->N, b->x[t], bw);
+            for (size_t i = 0; i < nsm; ++i) {
+                double acc = 0.0;
+                for (int st = 0; st < cs->s; ++st) acc += bw[st] * k[(size_t)st * nsm + i];
+                q[(size_t)t * nsm + i] = u[i] + dt * acc;
+            }
         }
         return;
     }
@@ -700,7 +783,8 @@ static size_t predictor_work_len(const orc_cfg *c)
 {
     int n = c->N + 1;
     size_t nst = (size_t)ipow(n, c->dim + 1), ns = (size_t)ipow(n, c->dim);
-    return nst * c->m * (3 + c->dim) + ns * c->m * (5 + c->dim);
+    (void)ns;
+    return nst * c->m * (3 + c->dim) + guess_work_len(c);
 }
 
 /* Volume integral of the corrector (third integral of eq. pde.nc.gw2) divided
@@ -847,7 +931,7 @@ int orc_initial_guess(const orc_cfg *c, const double *u, double dt, double *q0)
 {
     basis b;
     if (make_basis(c->N, &b)) return -1;
-    double *gw = malloc(sizeof(double) * (size_t)ipow(c->N + 1, c->dim) * c->m * (5 + c->dim));
+    double *gw = malloc(sizeof(double) * guess_work_len(c));
     if (!gw) return -2;
     initial_guess(c, &b, u, dt, q0, gw, NULL, 1.0);
     free(gw);

@@ -132,6 +132,7 @@ _SIGS = {
     "aderdg_profile": (C.c_int, [_H, C.c_int]),
     "aderdg_profile_read": (C.c_int, [_H, C.POINTER(C.c_float), C.POINTER(C.c_float)]),
     "aderdg_peak_tflops": (C.c_int, [C.c_int, _DP]),
+    "aderdg_device_recip": (C.c_int, [_DP, _DP, C.c_longlong, C.c_int]),
     "aderdg_autotune": (C.c_int, [C.POINTER(aderdg_solve_spec_t), C.c_int, C.c_char_p, C.c_int,
                                   C.POINTER(C.c_int), C.POINTER(C.c_float)]),
     "aderdg_batch_create": (C.c_int, [C.POINTER(aderdg_solve_spec_t), C.c_int, C.POINTER(aderdg_config_t),
@@ -493,6 +494,14 @@ def aderdg_peak_tflops(kind: int) -> float:
     v = C.c_double(0)
     _check(load().aderdg_peak_tflops(int(kind), C.byref(v)))
     return v.value
+
+
+def aderdg_device_recip(x, precision: int = ADERDG_FP64):
+    """1/x as the kernels compute it on the device (check utility)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.empty_like(x)
+    _check(load().aderdg_device_recip(x.ctypes.data_as(_DP), y.ctypes.data_as(_DP), x.size, int(precision)))
+    return y
 
 
 def aderdg_autotune(spec: aderdg_solve_spec_t, precision: int = ADERDG_MIXED_FP32, tune_cache=None,

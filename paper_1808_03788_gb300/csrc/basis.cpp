@@ -138,6 +138,43 @@ int build_basis(int N, Basis &b)
 }
 
 namespace {
+// Continuous explicit Runge-Kutta schemes of the CERK guess (Sec. 2.2 names
+// those of Owren and Zennaro without coefficients): stages k_i = L(u + dt
+// sum_{j<i} a_ij k_j), dense output u + dt sum_i b_i(th) k_i with b_i(th) =
+// sum_k beta_ik th^(k+1), of uniform order p (every rooted-tree condition
+// sum_i b_i(th) Phi_i(t) = th^|t| / gamma(t), |t| <= p, holds for all th).
+// Order 3: the classical fourth-order method and its cubic dense output.
+// Order 4: a six-stage scheme with quartic weights (five stages cannot reach
+// uniform order 4), from a numerical search over the stage matrix that kept
+// max |b_i(th)| small (0.35), refined to 40 digits by Newton's method on the
+// order conditions; shown here to 20 digits.
+struct CerkScheme {
+    int s, p;
+    double a[CERK_SMAX][CERK_SMAX];
+    double beta[CERK_SMAX][4];
+};
+const CerkScheme kCerkOrder3 = {
+    4, 3,
+    {{0}, {0.5}, {0.0, 0.5}, {0.0, 0.0, 1.0}},
+    {{1.0, -1.5, 2.0 / 3.0}, {0.0, 1.0, -2.0 / 3.0}, {0.0, 1.0, -2.0 / 3.0}, {0.0, -0.5, 2.0 / 3.0}},
+};
+const CerkScheme kCerkOrder4 = {
+    6, 4,
+    {{0},
+     {0.50849583384840113958},
+     {0.046949965621769603951, 0.4819237260551746206},
+     {0.16975684152901151769, 0.071063883183927482688, -0.028300707574148454932},
+     {-0.076143308578057834897, -0.14017373747662979618, 0.048722116369755792049, 0.50735746259681266958},
+     {0.12216705712724082426, 0.12299809408491295783, 0.48070156394276517752, 0.02616528026761548546,
+      0.093926602975396757805}},
+    {{1.0, -3.9153671327673924417, 5.9934951934142588637, -3.0269093126242169958},
+     {0.0, -0.80100882679982742762, 2.6530980786357989255, -1.7516658795402877462},
+     {0.0, -0.89842534403733875434, 2.9131919603555952085, -1.8758298804924840825},
+     {0.0, 5.3725609369242888065, -13.195842800637089784, 8.1610686740032049053},
+     {0.0, -0.070646768460630971334, 2.90293867489981116, -2.8111171676340170791},
+     {0.0, 0.31288713514090078845, -1.2668811066683743739, 1.3044535662878009984}},
+};
+
 template <typename T>
 void fill_typed(const Basis &b, Ops<T> &o)
 {
@@ -159,16 +196,26 @@ void fill_typed(const Basis &b, Ops<T> &o)
         o.inv_w[t] = T(b.inv_w[t]);
         o.xi[t] = T(b.x[t]);
         o.hxi2[t] = T(0.5 * b.x[t] * b.x[t]);
-        {  // CERK weights at xi_t: b1, b2 = b3, b4 (cubics of the dense output)
-            const double th = b.x[t], t2 = th * th, t3 = t2 * th;
-            o.rk[0][t] = T(th - 1.5 * t2 + 2.0 * t3 / 3.0);
-            o.rk[1][t] = T(t2 - 2.0 * t3 / 3.0);
-            o.rk[2][t] = T(-0.5 * t2 + 2.0 * t3 / 3.0);
+        {  // CERK dense-output weights at xi_t
+            const CerkScheme &cs = cerk_stages(n - 1) == 6 ? kCerkOrder4 : kCerkOrder3;
+            for (int i = 0; i < cs.s; ++i) {
+                double v = 0.0, thk = b.x[t];
+                for (int k = 0; k < cs.p; ++k) {
+                    v += cs.beta[i][k] * thk;
+                    thk *= b.x[t];
+                }
+                o.ck_b[i][t] = T(v);
+            }
         }
         double prod = 1.0;
         for (int j = 0; j < n; ++j)
             if (j != t) prod *= b.x[t] - b.x[j];
         o.bw[t] = T(1.0 / prod);
+    }
+    {
+        const CerkScheme &cs = cerk_stages(n - 1) == 6 ? kCerkOrder4 : kCerkOrder3;
+        for (int i = 0; i < cs.s; ++i)
+            for (int j = 0; j < i; ++j) o.ck_a[i][j] = T(cs.a[i][j]);
     }
 }
 }  // namespace
@@ -323,7 +370,7 @@ void fill_desc_lift(SolveDesc &sd, int N)
 int default_picard(int N, int guess)
 {
     if (guess == 3) return 2;  // a degree-N guess: one iteration, plus one
-    const int k = guess == 1 ? 1 : (guess == 2 ? 2 : (guess == 4 ? 3 : 0));
+    const int k = guess == 1 ? 1 : (guess == 2 ? 2 : (guess == 4 ? cerk_order(N) : 0));
     return N + 1 - k < 1 ? 1 : N + 1 - k;
 }
 

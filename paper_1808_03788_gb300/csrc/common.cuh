@@ -101,6 +101,14 @@ __host__ __device__ __forceinline__ double pconst<double>(const PdeParams &P, in
 template <>
 __host__ __device__ __forceinline__ float pconst<float>(const PdeParams &P, int i) { return P.cf[i]; }
 
+// The continuous Runge-Kutta scheme of the CERK guess (Sec. 2.2) for
+// degree N: the classical fourth-order method with its cubic dense output
+// up to N = 4, a six-stage scheme with quartic weights from N = 5 (the
+// degree N - 1 that one Picard iteration wants at N = 5).
+constexpr int CERK_SMAX = 6;
+__host__ __device__ constexpr int cerk_stages(int N) { return N >= 5 ? 6 : 4; }
+__host__ __device__ constexpr int cerk_order(int N) { return N >= 5 ? 4 : 3; }
+
 // Operators in the compute type (filled on the host by fill_ops).  Indexed
 // with compile-time constants inside unrolled loops, they are read straight
 // from the kernel-parameter constant bank.  They do not depend on the mesh
@@ -115,7 +123,8 @@ struct Ops {
     T xi[NMAX];            // time nodes on [0, 1] (initial guesses)
     T hxi2[NMAX];          // xi^2 / 2
     T bw[NMAX];            // barycentric weights 1 / prod_{j != k} (xi_k - xi_j)
-    T rk[3][NMAX];         // CERK dense-output weights b1, b2 = b3, b4 at xi_t
+    T ck_b[CERK_SMAX][NMAX];        // CERK dense-output weights b_i(xi_t)
+    T ck_a[CERK_SMAX][CERK_SMAX];   // CERK stage matrix (strictly lower triangular)
 };
 
 // One solve of a launch (device memory).  Tiles of EPB consecutive
@@ -216,14 +225,34 @@ struct NoRef {
     T q[M];
 };
 
-// 1/x in the compute type: the correctly rounded reciprocal intrinsic for
-// double (cheaper on the FP64 pipe than a full division), plain for float.
+// 1/x in the compute type, within one ulp (not correctly rounded).  The
+// seed is the hardware reciprocal approximation (rcp.approx.ftz: for double
+// it reads the leading 32 bits of x, relative error below 2^-19; for float
+// about 2^-23), refined by the Newton-Raphson iteration for 1/x, e = 1 - x r,
+// r <- r + r e, which squares the relative error, or for double by its
+// third-order form r <- r + r (e + e^2), which cubes it (see Muller et al.,
+// Handbook of Floating-Point Arithmetic, ch. on Newton-Raphson division).
+// Double: 3 FMAs on the FP64 pipe; float: 2 FFMAs.  x is a normal, finite,
+// nonzero number wherever the kernels take a reciprocal (densities, volume
+// fractions); its result is tested against 1/x (aderdg_device_recip).
 #ifdef __CUDACC__
-__device__ __forceinline__ double recip(double x) { return __drcp_rn(x); }
+__device__ __forceinline__ double recip(double x)
+{
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+    const double e = fma(-x, r, 1.0);
+    return fma(r, fma(e, e, e), r);
+}
+__device__ __forceinline__ float recip(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return fmaf(r, fmaf(-x, r, 1.0f), r);
+}
 #else
 inline double recip(double x) { return 1.0 / x; }
+inline float recip(float x) { return 1.0f / x; }
 #endif
-__host__ __device__ __forceinline__ float recip(float x) { return 1.0f / x; }
 
 // Every PDE states: M variables, of which the leading MEV evolve (the rest
 // obey q_t = 0); NCP: the system is purely non-conservative (F = 0, all

@@ -224,7 +224,7 @@ struct PredCfg {
     // resident CTAs per SM for the launch bounds: the register cap per
     // thread of shape 0 (65536 / (THREADS0 MINB0)) is kept
     static constexpr int MINB = cmax(1, cmin(2048 / THREADS, (THREADS0 * MINB0) / THREADS));
-    static constexpr int SHARED = round_up(DIM * n * n + 2 * n + 1 + n * n, 4);  // Kw, F0, F1, dt/dx, W
+    static constexpr int SHARED = round_up(DIM * n * n + 2 * n + 1 + 2 * n * n, 4);  // Kw, F0, F1, dt/dx, W, iK1W dt/dx
     // every vector access of a node in the exchange fields and in qbar |
     // Fbar starts on its vector width
     static_assert((SHARED * sizeof(T)) % 16 == 0, "shared header alignment");
@@ -521,6 +521,7 @@ k_predictor(const KParams P)
     T *sF1 = sF0 + n;
     T *sDt = sF1 + n;                          // dt / dx_0 of the current tile
     T *sW = sDt + 1;                           // extrapolation weights [t][k] of the tile
+    T *sIW = sW + n * n;                       // (dt / dx_0) iK1W of the tile
     const int tid = threadIdx.x;
     const bool act = tid < EPB * NS;
     const int g = act ? tid / NS : 0;
@@ -546,6 +547,10 @@ k_predictor(const KParams P)
         const double dt = solve_dt(P, S);
         if (!(dt > 0.0)) continue;  // uniform over the CTA: this solve takes no step
         if (tid == 0) sDt[0] = T(dt * S.inv_dx[0]);  // dt / dx_0 (see gather_R), read after a barrier
+        // FP64: the time solve's operator scaled by dt / dx_0 (read after a
+        // barrier), so that q[t] = u + sum_t' sIW[t][t'] R[t'] takes n FMAs per value
+        if constexpr (sizeof(T) == 8)
+            for (int i = tid; i < n * n; i += blockDim.x) sIW[i] = T(dt * S.inv_dx[0]) * O.iK1W[i];
         T idx[DIM], ratio[DIM];
 #pragma unroll
         for (int d = 0; d < DIM; ++d) {
@@ -727,29 +732,66 @@ k_predictor(const KParams P)
                 it0 = 0;
             } else if (EX && S.guess == 4) {
                 if constexpr (EX) {
-                    // CERK guess (Sec. 2.2): the cubic dense output of the classical
-                    // fourth-order Runge-Kutta method on q' = L(q), q = u + dt sum_i
-                    // b_i(xi) k_i, k2 = L(u + dt k1/2), k3 = L(u + dt k2/2),
-                    // k4 = L(u + dt k3); accumulated stage by stage
+                    // CERK guess (Sec. 2.2): q = u + dt sum_i b_i(xi) k_i with
+                    // k_i = L(u + dt sum_{j<i} a_ij k_j), the scheme of
+                    // cerk_stages(N) stages (Ops::ck_a, ck_b); accumulated stage
+                    // by stage
+                    constexpr int CS = cerk_stages(N);
                     T w[M], Rk[M];
 #pragma unroll
                     for (int t = 0; t < n; ++t)
 #pragma unroll
-                        for (int v = 0; v < M; ++v) q[t][v] = u[v] + dtT * (O.rk[0][t] * R1[v]);
+                        for (int v = 0; v < M; ++v) q[t][v] = u[v] + dtT * (O.ck_b[0][t] * R1[v]);
+                    if constexpr (CS == 4) {
+                        // the classical method: each stage state from the previous k
 #pragma unroll
-                    for (int v = 0; v < M; ++v) w[v] = u[v] + T(0.5) * dtT * R1[v];
+                        for (int v = 0; v < M; ++v) w[v] = u[v] + T(0.5) * dtT * R1[v];
 #pragma unroll 1
-                    for (int st = 1; st < 4; ++st) {
-                        spatial_R(w, Rk);
+                        for (int st = 1; st < 4; ++st) {
+                            spatial_R(w, Rk);
 #pragma unroll
-                        for (int t = 0; t < n; ++t) {
-                            const T bt = st == 3 ? O.rk[2][t] : O.rk[1][t];  // constant-bank reads, then a select
+                            for (int t = 0; t < n; ++t) {
+                                const T bt = st == 3 ? O.ck_b[3][t] : O.ck_b[1][t];  // b2 = b3
 #pragma unroll
-                            for (int v = 0; v < M; ++v) q[t][v] += dtT * (bt * Rk[v]);
+                                for (int v = 0; v < M; ++v) q[t][v] += dtT * (bt * Rk[v]);
+                            }
+                            const T cs = st == 1 ? T(0.5) : T(1);
+#pragma unroll
+                            for (int v = 0; v < M; ++v) w[v] = u[v] + cs * dtT * Rk[v];
                         }
-                        const T cs = st == 1 ? T(0.5) : T(1);
+                    } else {
+                        // the earlier stages' k of this thread's node wait in the
+                        // exchange field's time slices t >= 1 (only the t = 0
+                        // slices serve the L evaluations); the variables past MX
+                        // have k = 0
+                        static_assert(CS - 1 <= DIM * (n - 1), "CERK stage slots");
+                        auto kslot = [&](int j) {
+                            return ebuf + (j / (n - 1)) * C::FSL + (1 + j % (n - 1)) * C::TSL + s * C::MX;
+                        };
+                        if (act) NodeIO<T, C::MX>::store(kslot(0), R1);
+#pragma unroll 1
+                        for (int st = 1; st < CS; ++st) {
 #pragma unroll
-                        for (int v = 0; v < M; ++v) w[v] = u[v] + cs * dtT * Rk[v];
+                            for (int v = 0; v < M; ++v) w[v] = T(0);
+#pragma unroll 1
+                            for (int j = 0; j < st; ++j) {
+                                T kj[C::MX];
+                                NodeIO<T, C::MX>::load(kslot(j), kj);
+                                const T a = O.ck_a[st][j];
+#pragma unroll
+                                for (int v = 0; v < C::MX; ++v) w[v] += a * kj[v];
+                            }
+#pragma unroll
+                            for (int v = 0; v < M; ++v) w[v] = u[v] + dtT * w[v];
+                            spatial_R(w, Rk);
+#pragma unroll
+                            for (int t = 0; t < n; ++t) {
+                                const T bt = O.ck_b[st][t];
+#pragma unroll
+                                for (int v = 0; v < M; ++v) q[t][v] += dtT * (bt * Rk[v]);
+                            }
+                            if (act && st < CS - 1) NodeIO<T, C::MX>::store(kslot(st), Rk);
+                        }
                     }
                 }
                 it0 = 0;
@@ -790,18 +832,28 @@ k_predictor(const KParams P)
             }
             __syncthreads();
             {
-                const T dtT = sDt[0];
                 T R[n][M];
 #pragma unroll
                 for (int t = 0; t < n; ++t) rhs(t, q[t], R[t]);
+                // FP64: the scaled operator from shared memory, n FMAs per value
+                // (the FP64 pipe bounds the kernel: 8 % faster than the
+                // constant-bank operator times dt/dx_0); FP32: the constant-bank
+                // operator (shared-memory bandwidth bounds that kernel)
 #pragma unroll
                 for (int v = 0; v < C::MR; ++v)  // rows MR.. have R = 0: q stays u there
 #pragma unroll
                     for (int t = 0; t < n; ++t) {
-                        T acc = O.iK1W[t * n] * R[0][v];
+                        if constexpr (sizeof(T) == 8) {
+                            T acc = u[v];
 #pragma unroll
-                        for (int tp = 1; tp < n; ++tp) acc += O.iK1W[t * n + tp] * R[tp][v];
-                        q[t][v] = u[v] + dtT * acc;
+                            for (int tp = 0; tp < n; ++tp) acc += sIW[t * n + tp] * R[tp][v];
+                            q[t][v] = acc;
+                        } else {
+                            T acc = O.iK1W[t * n] * R[0][v];
+#pragma unroll
+                            for (int tp = 1; tp < n; ++tp) acc += O.iK1W[t * n + tp] * R[tp][v];
+                            q[t][v] = u[v] + sDt[0] * acc;
+                        }
                     }
             }
             __syncthreads();

@@ -1,9 +1,11 @@
 // Arithmetic peak probes: many independent FMA chains per thread, timed
 // with CUDA events.  They give the FP64 (DFMA) and FP32 (FFMA) rates this
 // GPU sustains, the denominators of the ALU rooflines of the kernels.
+// Also the check of the device reciprocal the flux kernels use.
 #include <cuda_runtime.h>
 
 #include "../../include/aderdg.h"
+#include "common.cuh"
 
 namespace {
 
@@ -51,7 +53,32 @@ int run(int iters, double *tflops)
     return ADERDG_OK;
 }
 
+__global__ void k_recip(const double *x, double *y, long long n, int single)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = single ? (double)aderdg::recip((float)x[i]) : aderdg::recip(x[i]);
+}
+
 }  // namespace
+
+extern "C" int aderdg_device_recip(const double *x, double *y, long long n, int precision)
+{
+    if (n < 0 || (n > 0 && (!x || !y)) || (precision != ADERDG_FP64 && precision != ADERDG_MIXED_FP32))
+        return ADERDG_E_INVAL;
+    if (n == 0) return ADERDG_OK;
+    if (n > (1ll << 26)) return ADERDG_E_INVAL;
+    double *d = nullptr;
+    if (cudaMalloc(&d, 2 * n * sizeof(double)) != cudaSuccess) return ADERDG_E_NOMEM;
+    cudaError_t e = cudaMemcpy(d, x, n * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        k_recip<<<(int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096), 256>>>(d, d + n, n,
+                                                                             precision == ADERDG_MIXED_FP32);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(y, d + n, n * sizeof(double), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    return e == cudaSuccess ? ADERDG_OK : ADERDG_E_CUDA;
+}
 
 extern "C" int aderdg_peak_tflops(int kind, double *tflops)
 {

@@ -246,33 +246,71 @@ k_predictor_xt(const KParams P)
             } else if (EX && S.guess == 4) {
                 if constexpr (EX) {
                     // CERK guess (Sec. 2.2), stage by stage as in k_predictor
+                    constexpr int CS = cerk_stages(N);
                     float w[n][M], Rk[n][M];
 #pragma unroll
                     for (int t = 0; t < n; ++t)
 #pragma unroll
                         for (int x = 0; x < n; ++x)
 #pragma unroll
-                            for (int v = 0; v < M; ++v) A[t][x][v] = u[x][v] + dtT * (O.rk[0][t] * R1[x][v]);
-#pragma unroll
-                    for (int x = 0; x < n; ++x)
-#pragma unroll
-                        for (int v = 0; v < M; ++v) w[x][v] = u[x][v] + 0.5f * dtT * R1[x][v];
-#pragma unroll 1
-                    for (int st = 1; st < 4; ++st) {
-                        spatial_R(w, Rk);
-#pragma unroll
-                        for (int t = 0; t < n; ++t) {
-                            const float bt = st == 3 ? O.rk[2][t] : O.rk[1][t];
-#pragma unroll
-                            for (int x = 0; x < n; ++x)
-#pragma unroll
-                                for (int v = 0; v < M; ++v) A[t][x][v] += dtT * (bt * Rk[x][v]);
-                        }
-                        const float cs = st == 1 ? 0.5f : 1.0f;
+                            for (int v = 0; v < M; ++v) A[t][x][v] = u[x][v] + dtT * (O.ck_b[0][t] * R1[x][v]);
+                    if constexpr (CS == 4) {
 #pragma unroll
                         for (int x = 0; x < n; ++x)
 #pragma unroll
-                            for (int v = 0; v < M; ++v) w[x][v] = u[x][v] + cs * dtT * Rk[x][v];
+                            for (int v = 0; v < M; ++v) w[x][v] = u[x][v] + 0.5f * dtT * R1[x][v];
+#pragma unroll 1
+                        for (int st = 1; st < 4; ++st) {
+                            spatial_R(w, Rk);
+#pragma unroll
+                            for (int t = 0; t < n; ++t) {
+                                const float bt = st == 3 ? O.ck_b[3][t] : O.ck_b[1][t];  // b2 = b3
+#pragma unroll
+                                for (int x = 0; x < n; ++x)
+#pragma unroll
+                                    for (int v = 0; v < M; ++v) A[t][x][v] += dtT * (bt * Rk[x][v]);
+                            }
+                            const float cs = st == 1 ? 0.5f : 1.0f;
+#pragma unroll
+                            for (int x = 0; x < n; ++x)
+#pragma unroll
+                                for (int v = 0; v < M; ++v) w[x][v] = u[x][v] + cs * dtT * Rk[x][v];
+                        }
+                    } else {
+                        // the earlier stages' k of the row in registers (this
+                        // kernel serves small rows: n^2 m <= 100)
+                        float K[CS - 1][n][M];
+#pragma unroll
+                        for (int x = 0; x < n; ++x)
+#pragma unroll
+                            for (int v = 0; v < M; ++v) K[0][x][v] = R1[x][v];
+#pragma unroll
+                        for (int st = 1; st < CS; ++st) {
+#pragma unroll
+                            for (int x = 0; x < n; ++x)
+#pragma unroll
+                                for (int v = 0; v < M; ++v) {
+                                    float acc = 0.f;
+#pragma unroll
+                                    for (int j = 0; j < st; ++j) acc += O.ck_a[st][j] * K[j][x][v];
+                                    w[x][v] = u[x][v] + dtT * acc;
+                                }
+                            spatial_R(w, Rk);
+#pragma unroll
+                            for (int t = 0; t < n; ++t) {
+                                const float bt = O.ck_b[st][t];
+#pragma unroll
+                                for (int x = 0; x < n; ++x)
+#pragma unroll
+                                    for (int v = 0; v < M; ++v) A[t][x][v] += dtT * (bt * Rk[x][v]);
+                            }
+                            if (st < CS - 1) {
+#pragma unroll
+                                for (int x = 0; x < n; ++x)
+#pragma unroll
+                                    for (int v = 0; v < M; ++v) K[st][x][v] = Rk[x][v];
+                            }
+                        }
                     }
                 }
                 it0 = 0;

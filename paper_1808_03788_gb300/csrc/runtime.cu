@@ -311,7 +311,10 @@ void fill_cost(const aderdg_t *h, aderdg_info_t *info)
                                         NREC * EF;
     double pred;
     if (h->guess == 3) pred = NST * M * 2 * n + P * itk + fin;  // steady state (a previous predictor)
-    else if (h->guess == 4) pred = 4 * it1 + 6 * NS * M + P * itk + fin;  // four stages, three stage states
+    else if (h->guess == 4) {  // S stages; the classical method forms each stage state with one product
+        const double S = cerk_stages(h->N);
+        pred = S * it1 + (S == 4 ? 6.0 : S * (S - 1)) * NS * M + P * itk + fin;
+    }
     else if (h->guess == 2) pred = 2 * it1 + 2 * NS * M + P * itk + fin;  // it1 counts 3 flops per q value, the
                                                                      // Taylor form 6 over two evaluations
     else if (h->guess == 1) pred = it1 + P * itk + fin;

@@ -179,8 +179,9 @@ def test_extrapolation_restarts_after_set_state():
 
 @pytest.mark.parametrize("picard", [0, 1])
 def test_full_run_euler_vortex_cerk_guess(picard):
-    """FP64 and mixed full runs with the CERK guess: default count (N-2)
-    and one Picard iteration (a degree N-1 guess for N = 4)."""
+    """FP64 and mixed full runs with the CERK guess (the classical
+    method's cubic dense output at N = 4): default count (N-2) and one
+    Picard iteration (a degree N-1 guess for N = 4)."""
     case = (2, 2, 4, (24, 20), 10.0, (GAMMA,))
     for prec, tol in ((A.ADERDG_FP64, 1e-11), (A.ADERDG_MIXED_FP32, 1e-6)):
         cfg, s = _pair(*case, guess=A.ADERDG_GUESS_CERK, picard=picard, precision=prec)
@@ -191,6 +192,64 @@ def test_full_run_euler_vortex_cerk_guess(picard):
         Ug, t, k = s.get_state()
         assert (t, k) == (to, ko) and k > 2
         assert l2_rel(cfg, Ug, Uo) <= tol
+
+
+@pytest.mark.parametrize("N", [5, 6])
+def test_full_run_euler_vortex_order4_cerk_guess(N):
+    """The six-stage scheme with quartic weights (N >= 5): a degree N-1
+    guess at N = 5, so one Picard iteration; FP64 and mixed full runs against
+    the oracle, and the default count N + 1 - 4."""
+    case = (2, 2, N, (14, 12), 10.0, (GAMMA,))
+    for picard in (0, 1):
+        for prec, tol in ((A.ADERDG_FP64, 1e-11), (A.ADERDG_MIXED_FP32, 1e-6)):
+            cfg, s = _pair(*case, guess=A.ADERDG_GUESS_CERK, picard=picard, precision=prec)
+            assert s.info()["picard_iters"] == (picard or N + 1 - 4)
+            U0 = inputs.euler_vortex(oracle.node_coords(cfg))
+            Uo, to, ko, _ = oracle.run(cfg, U0, t_end=0.3)
+            s.set_state(U0)
+            s.advance(0.3)
+            Ug, t, k = s.get_state()
+            s.close()
+            assert (t, k) == (to, ko) and k > 2
+            assert l2_rel(cfg, Ug, Uo) <= tol
+
+
+@pytest.mark.parametrize("shapes", [(0, 0), (1, 1), (2, 2), (7, 3), (8, 0)])
+def test_order4_cerk_guess_every_predictor_shape(shapes):
+    """Each predictor shape of the FP32 path holds the earlier stages in its
+    exchange field's free time slices (its own layout per shape): within
+    the mixed tolerance of the oracle."""
+    cfg = oracle.make_cfg(2, (9, 7), [0, 0], [10, 10], 5, 2, (GAMMA,), picard=1, guess=oracle.GUESS_CERK)
+    U0 = inputs.euler_vortex(oracle.node_coords(cfg))
+    Uo, to, ko, _ = oracle.run(cfg, U0, t_end=0.2)
+    with A.Solver(2, 2, (9, 7), (0, 0), (10, 10), 5, (GAMMA,), precision=A.ADERDG_MIXED_FP32, picard=1,
+                  guess=A.ADERDG_GUESS_CERK, shapes=shapes) as s:
+        s.set_state(U0)
+        s.advance(0.2)
+        Ug, t, k = s.get_state()
+        assert s.info()["pred_shape"] == shapes[0]
+    assert (t, k) == (to, ko)
+    assert l2_rel(cfg, Ug, Uo) <= 1e-6
+
+
+@pytest.mark.parametrize("N,shapes", [(5, (3, 0)), (6, (4, 1)), (5, (0, 0))])
+def test_order4_cerk_guess_advection_plane_kernel(N, shapes):
+    """2D advection with the order-4 scheme on the plane-owning FP32 kernel
+    (the stages' k in registers) and on k_predictor: one Picard iteration,
+    against the oracle."""
+    a = (0.7, -1.1)
+    cfg = oracle.make_cfg(2, (6, 5), [0, 0], [1, 1], N, 1, a, picard=1, guess=oracle.GUESS_CERK)
+    X = oracle.node_coords(cfg)
+    U0 = inputs.smooth_random_state(1, X, [1.0, 1.0], seed=9)
+    Uo, to, ko, _ = oracle.run(cfg, U0, t_end=0.05)
+    with A.Solver(1, 2, (6, 5), (0, 0), (1, 1), N, a, precision=A.ADERDG_MIXED_FP32, picard=1,
+                  guess=A.ADERDG_GUESS_CERK, shapes=shapes) as s:
+        s.set_state(U0)
+        s.advance(0.05)
+        Ug, t, k = s.get_state()
+        assert s.info()["pred_shape"] == shapes[0]
+    assert (t, k) == (to, ko)
+    assert l2_rel(cfg, Ug, Uo) <= 1e-6
 
 
 @pytest.mark.parametrize("shapes", [(3, 0), (4, 1)])

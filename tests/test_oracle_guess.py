@@ -235,33 +235,78 @@ def test_extrapolation_guess_vortex_error_matches_trivial():
 
 
 # ---- continuous Runge-Kutta (CERK) guess (Sec. 2.2) -------------------------
+#
+# The guess for degree N uses a continuous explicit Runge-Kutta scheme of
+# order p = max(3, N - 1), capped at the highest order built: the classical
+# fourth-order method with its cubic dense output (p = 3) up to N = 4, a
+# six-stage scheme with quartic weights (p = 4) from N = 5.
 
 RK_C = np.array([0.0, 0.5, 0.5, 1.0])
 RK_A = np.array([[0, 0, 0, 0], [0.5, 0, 0, 0], [0, 0.5, 0, 0], [0, 0, 1.0, 0]])
+CERK_ORDER = {1: 3, 2: 3, 3: 3, 4: 3, 5: 4, 6: 4, 7: 4}
 
 
+def _trees(A, p):
+    """(order, gamma, elementary weight vector) of every rooted tree of order
+    <= p for the stage matrix A (Butcher's trees; c = A 1)."""
+    one = np.ones(A.shape[0])
+    c = A @ one
+    Ac = A @ c
+    T = [(1, 1, one), (2, 2, c), (3, 3, c ** 2), (3, 6, Ac),
+         (4, 4, c ** 3), (4, 8, c * Ac), (4, 12, A @ c ** 2), (4, 24, A @ Ac)]
+    if p >= 5:
+        T += [(5, 5, c ** 4), (5, 10, c ** 2 * Ac), (5, 15, c * (A @ c ** 2)), (5, 30, c * (A @ Ac)),
+              (5, 20, Ac * Ac), (5, 20, A @ c ** 3), (5, 40, A @ (c * Ac)), (5, 60, A @ (A @ c ** 2)),
+              (5, 120, A @ (A @ Ac))]
+    return [t for t in T if t[0] <= p]
+
+
+def test_cerk_schemes_have_the_orders_the_guess_needs():
+    for N, p in CERK_ORDER.items():
+        A, beta = oracle.cerk_scheme(N)
+        assert beta.shape[1] == p and A.shape == (beta.shape[0],) * 2
+        assert np.all(np.triu(A) == 0)  # explicit
+    np.testing.assert_array_equal(oracle.cerk_scheme(4)[0], RK_A)  # the classical method
+
+
+@pytest.mark.parametrize("N", [4, 5])
 @pytest.mark.parametrize("theta", [0.0, 0.1, 0.3, 0.5, 0.77, 1.0])
-def test_cerk_weights_satisfy_the_continuous_order_conditions(theta):
-    """The dense-output weights b_i(theta) of the classical fourth-order
-    method meet the order conditions of a continuous Runge-Kutta scheme up to
-    order 3 at every theta, and at theta = 1 are the method's own weights."""
-    b = oracle.cerk_weights(theta)
-    assert abs(b.sum() - theta) < 1e-15
-    assert abs(b @ RK_C - theta ** 2 / 2) < 1e-15
-    assert abs(b @ RK_C ** 2 - theta ** 3 / 3) < 1e-15
-    assert abs(b @ (RK_A @ RK_C) - theta ** 3 / 6) < 1e-15
-    if theta == 1.0:
-        np.testing.assert_allclose(b, [1 / 6, 1 / 3, 1 / 3, 1 / 6], rtol=0, atol=1e-15)
+def test_cerk_weights_satisfy_the_continuous_order_conditions(theta, N):
+    """The dense-output weights b_i(theta) meet every order condition of a
+    continuous Runge-Kutta scheme up to its order p at each theta,
+    sum_i b_i(theta) Phi_i(t) = theta^|t| / gamma(t); the weights of the
+    classical method end in 1/6, 1/3, 1/3, 1/6."""
+    A, beta = oracle.cerk_scheme(N)
+    p = CERK_ORDER[N]
+    b = oracle.cerk_weights(theta, N)
+    np.testing.assert_allclose(b, beta @ theta ** np.arange(1, p + 1), rtol=0, atol=1e-15)
+    for order_, gamma, phi in _trees(A, p):
+        assert abs(b @ phi - theta ** order_ / gamma) < 2e-15, (order_, gamma)
+    if N <= 4:
+        for order_, gamma, phi in _trees(RK_A, 3):
+            assert abs(b @ phi - theta ** order_ / gamma) < 1e-15
+        if theta == 1.0:
+            np.testing.assert_allclose(b, [1 / 6, 1 / 3, 1 / 3, 1 / 6], rtol=0, atol=1e-15)
 
 
-@pytest.mark.parametrize("dim,N", [(1, 3), (2, 3), (2, 4), (3, 3)])
-def test_cerk_guess_is_exact_for_cubic_data(dim, N):
-    """Linear advection of a polynomial of total degree <= 3: L^4 u = 0 and
-    the CERK guess reproduces the exact space-time solution."""
+def test_cerk_order4_scheme_misses_an_order5_condition():
+    """The order-4 scheme is not of order 5 (so the quintic test below
+    measures a real miss)."""
+    A, _ = oracle.cerk_scheme(5)
+    b = oracle.cerk_weights(1.0, 5)
+    misses = [abs(b @ phi - 1 / g) for o, g, phi in _trees(A, 5) if o == 5]
+    assert max(misses) > 1e-4
+
+
+@pytest.mark.parametrize("dim,N", [(1, 3), (2, 3), (2, 4), (3, 3), (1, 5), (2, 5), (2, 6)])
+def test_cerk_guess_is_exact_for_data_of_its_order(dim, N):
+    """Linear advection of a polynomial of total degree <= p: L^(p+1) u = 0
+    and the CERK guess reproduces the exact space-time solution."""
+    p = CERK_ORDER[N]
     a = [1.7, -0.6, 0.9][:dim]
     cfg = oracle.make_cfg(dim, [4] * dim, [0.0] * dim, [1.0] * dim, N, oracle.PDE_ADVECTION, a,
                           guess=oracle.GUESS_CERK)
-    coef = _poly(dim, 3, seed=50 + 10 * dim + N)
+    coef = _poly(dim, p, seed=50 + 10 * dim + N)
     dt = 0.05
     ex, X, _ = _space_time(cfg, coef, a, dt)
     q0 = oracle.initial_guess(cfg, _eval(coef, X)[:, None], dt)
@@ -270,19 +315,30 @@ def test_cerk_guess_is_exact_for_cubic_data(dim, N):
     assert np.abs(oracle.initial_guess(cfg, _eval(coef, X)[:, None], dt) - ex).max() > 1e-6
 
 
-def test_cerk_guess_misses_exactly_the_quartic_term():
-    """u0 = x^4: with L = -a d/dx the dense output carries
-    dt^4 b_4(theta) L^4 u / 4 = 6 a^4 dt^4 b_4(theta) where the exact
-    solution has tau^4 L^4 u / 24 = a^4 tau^4: the miss is
-    a^4 dt^4 (6 b_4(theta) - theta^4)."""
-    a, N, dt = 1.3, 4, 0.07
+@pytest.mark.parametrize("N", [4, 5])
+def test_cerk_guess_misses_exactly_the_next_taylor_term(N):
+    """u0 = x^(p+1), L = -a d/dx: the stages give k = sum_j dt^j A^j 1
+    L^(j+1) u, so the dense output carries dt^(p+1) (b(theta) . A^p 1)
+    L^(p+1) u where the exact solution has (theta dt)^(p+1) L^(p+1) u /
+    (p+1)!; with L^(p+1) u = (-a)^(p+1) (p+1)! the miss is
+    (-a)^(p+1) dt^(p+1) ((p+1)! b(theta) . A^p 1 - theta^(p+1))."""
+    p = CERK_ORDER[N]
+    a, dt = 1.3, 0.07
+    A, _ = oracle.cerk_scheme(N)
+    chain = np.linalg.matrix_power(A, p) @ np.ones(A.shape[0])
     cfg = oracle.make_cfg(1, [3], [0.0], [1.0], N, oracle.PDE_ADVECTION, [a], guess=oracle.GUESS_CERK)
-    coef = {(4,): 1.0}
+    coef = {(p + 1,): 1.0}
     ex, X, tau = _space_time(cfg, coef, [a], dt)
     q0 = oracle.initial_guess(cfg, _eval(coef, X)[:, None], dt)
-    want = np.array([a ** 4 * dt ** 4 * (6 * oracle.cerk_weights(t)[3] - t ** 4) for t in tau])
+    fact = float(np.prod(np.arange(1, p + 2)))
+    want = np.array([(-a) ** (p + 1) * dt ** (p + 1) * (fact * (oracle.cerk_weights(t, N) @ chain) - t ** (p + 1))
+                     for t in tau])
+    if N == 4:  # the classical method: A^3 1 = (0, 0, 0, 1/4), the miss a^4 dt^4 (6 b_4 - theta^4)
+        np.testing.assert_allclose(want, [a ** 4 * dt ** 4 * (6 * oracle.cerk_weights(t, 4)[3] - t ** 4)
+                                          for t in tau], rtol=1e-12)
+    assert np.abs(want).max() > 1e-9
     np.testing.assert_allclose((q0 - ex)[:, :, 0], np.broadcast_to(want[:, None], (N + 1, N + 1)),
-                               rtol=1e-9, atol=1e-15)
+                               rtol=1e-8, atol=1e-15)
 
 
 def test_cerk_guess_constant_state_and_picard_count():
@@ -294,24 +350,29 @@ def test_cerk_guess_constant_state_and_picard_count():
     for N in range(1, 8):
         cfg = euler_cfg((2, 2), N=N)
         cfg.guess = oracle.GUESS_CERK
-        assert oracle.lib().orc_picard_count(cfg) == max(1, N - 2)
+        assert oracle.lib().orc_picard_count(cfg) == max(1, N + 1 - CERK_ORDER[N])
 
 
-@pytest.mark.parametrize("N", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 5, 6])
 def test_cerk_guess_converged_for_linear_advection(N):
-    """1D linear advection: the guess is exact to third order in time, and
-    each Picard iteration adds one order, so max(1, N-3) iterations reach
-    the converged predictor (the space-time solution of degree N)."""
+    """1D linear advection: the guess is exact to order p in time, and each
+    Picard iteration adds one order, so max(1, N - p) iterations reach the
+    converged predictor (the space-time solution of degree N)."""
     K = 5
+    p = CERK_ORDER[N]
     rng = np.random.default_rng(40 + N)
     U = rng.standard_normal((K, N + 1, 1))
     mk = lambda g, P: oracle.make_cfg(1, [K], [0.0], [1.0], N, oracle.PDE_ADVECTION, [1.0], picard=P, guess=g)
     ref = oracle.step(mk(0, N + 1), U, 0.02)
-    got = oracle.step(mk(oracle.GUESS_CERK, max(1, N - 3)), U, 0.02)
+    got = oracle.step(mk(oracle.GUESS_CERK, max(1, N - p)), U, 0.02)
     np.testing.assert_allclose(got, ref, rtol=0, atol=1e-13)
+    if N - p >= 1:  # one iteration fewer does not converge
+        short = oracle.step(mk(oracle.GUESS_CERK, N - p - 1), U, 0.02) if N - p >= 2 else None
+        if short is not None:
+            assert np.abs(short - ref).max() > 1e-12
 
 
-@pytest.mark.parametrize("N", [3, 4])
+@pytest.mark.parametrize("N", [3, 4, 5])
 def test_cerk_guess_design_order_with_one_iteration(N):
     """A guess of degree N-1 (or more) in time needs one Picard iteration
     (Sec. 2.2): Euler density wave, CERK guess, one iteration per step,
