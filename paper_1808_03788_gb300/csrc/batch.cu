@@ -468,7 +468,7 @@ public:
                 const KernelSet *ks = g.ks;
                 const LimKernels &lk = g.members[0]->lk;  // one (PDE, d, N, precision) per group
                 const unsigned grid = (unsigned)std::min<long long>(g.elems, 152LL * 16);
-                lk.minmax<<<grid, 128, lk.smem_w, st>>>(kp);
+                lk.minmax<<<lk.minmax_grid(g.elems), 128, lk.smem_w, st>>>(kp);
                 lk.detect<<<grid, 128, lk.smem_w, st>>>(kp);
                 lk.fv<<<grid, 128, lk.smem, st>>>(kp);
                 lk.couple<<<grid, 128, lk.smem, st>>>(kp);

@@ -12,6 +12,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 namespace aderdg {
@@ -127,6 +128,33 @@ struct Ops {
     T ck_a[CERK_SMAX][CERK_SMAX];   // CERK stage matrix (strictly lower triangular)
 };
 
+// Unsigned division by a divisor fixed for a solve (its cell counts) as a
+// multiply-high and two shifts, Granlund and Montgomery, "Division by
+// invariant integers using multiplication" (PLDI 1994, fig. 4.1): with
+// l = ceil(log2 d), m = floor(2^32 (2^l - d) / d) + 1, t = mulhi(m, n),
+// n / d = (t + ((n - t) >> min(l, 1))) >> max(l - 1, 0) for every 32-bit n.
+struct FastDiv {
+    unsigned m;
+    unsigned s1, s2;
+};
+inline FastDiv make_fastdiv(unsigned d)
+{
+    unsigned l = 0;
+    while (l < 32 && (1ull << l) < d) ++l;
+    FastDiv f;
+    f.m = (unsigned)((((1ull << l) - d) << 32) / d + 1);
+    f.s1 = l < 1 ? l : 1;
+    f.s2 = l > 1 ? l - 1 : 0;
+    return f;
+}
+#ifdef __CUDACC__
+__device__ __forceinline__ unsigned fdiv(unsigned n, const FastDiv &f)
+{
+    const unsigned t = __umulhi(n, f.m);
+    return (t + ((n - t) >> f.s1)) >> f.s2;
+}
+#endif
+
 // One solve of a launch (device memory).  Tiles of EPB consecutive
 // elements are numbered solve after solve: this solve owns tiles
 // [tile0_p, tile0_p + ceil(E / EPB_predictor)) of the predictor launch and
@@ -171,14 +199,19 @@ struct SolveDesc {
     // FP32 path: the corrector's lift coefficients (1/dx_d) F_{0|1}[k] / w_k
     // rounded to float, [side][d][k] (fill_desc_lift)
     float lift_f[2][3][NMAX];
+    // element index -> cell: divisions by cells[0] and cells[1]
+    FastDiv div_cx, div_cy;
 };
 
+// the per-solve constants derived from cells and inv_dx
 inline void fill_desc_spacing(SolveDesc &d)
 {
     for (int k = 0; k < 3; ++k) {
         d.inv_dx_f[k] = (float)d.inv_dx[k];
         d.ratio_f[k] = (float)(d.inv_dx[k] / d.inv_dx[0]);
     }
+    d.div_cx = make_fastdiv((unsigned)d.cells[0]);
+    d.div_cy = make_fastdiv((unsigned)d.cells[1]);
 }
 
 // Kernel parameter block (passed by value).
@@ -560,7 +593,7 @@ struct TileShape {
 // Number of compiled shapes of the predictor and the corrector (shape 0 is
 // the default).
 constexpr int NSHAPE_P = 9;
-constexpr int NSHAPE_C = 4;
+constexpr int NSHAPE_C = 5;
 
 // Host-visible description of the compiled kernels of one (PDE, d, N,
 // precision).  predictor/corrector and their sizes are the shapes in use;

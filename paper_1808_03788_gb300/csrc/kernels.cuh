@@ -1096,11 +1096,11 @@ struct CorrCfg {
         sizeof(T) == 4 || align16(OWN) + align16(NB) + align16(UB) + align16(VB) <= 8192;
     static constexpr size_t PER_ELEM =
         align16(OWN) + align16(NB) + (STAGE_UV ? align16(UB) + align16(VB) : 0) + align16(FS);
-    // shapes 0, 1, 2: 256-, 128- and 512-thread CTAs; shape 3: every warp
-    // takes one element of the tile on its own (its own shared-memory
+    // shapes 0, 1, 2, 4: 256-, 128-, 512- and 64-thread CTAs; shape 3: every
+    // warp takes one element of the tile on its own (its own shared-memory
     // slice, warp-level synchronisation only), NW warps per CTA
     static constexpr bool WM = TS == 3;
-    static constexpr int THREADS_CTA = TS == 1 ? 128 : (TS == 2 ? 512 : 256);
+    static constexpr int THREADS_CTA = TS == 1 ? 128 : (TS == 2 ? 512 : (TS == 4 ? 64 : 256));
     static constexpr int EPB_T = cmax(1, THREADS_CTA / NS);
     static constexpr int EPB_S = cmax(1, (int)((110 * 1024) / PER_ELEM));
     static constexpr int EPB = WM ? 1 : cmin(EPB_T, EPB_S);  // elements per shared-memory unit
@@ -1110,8 +1110,7 @@ struct CorrCfg {
     static constexpr size_t O_V = O_U + (STAGE_UV ? align16(EPB * UB) : 0);
     static constexpr size_t O_FS = O_V + (STAGE_UV ? align16(EPB * VB) : 0);
     static constexpr size_t O_LIFT = O_FS + align16(EPB * FS);
-    static constexpr size_t O_NBIDX = O_LIFT + align16(sizeof(T) * 2 * 3 * NMAX);
-    static constexpr size_t O_DEL = O_NBIDX + align16(sizeof(int) * EPB * 2 * DIM);
+    static constexpr size_t O_DEL = O_LIFT + align16(sizeof(T) * 2 * 3 * NMAX);
     static constexpr bool DELTA = sizeof(T) == 4;
     static constexpr int RF = M;
     static constexpr int LAM = G::LAM;
@@ -1132,33 +1131,36 @@ struct CorrCfg {
     static constexpr int G_V = cgcd((int)VB, 16);
 };
 
-// neighbour of element e (x-fastest numbering, cells cx, cy, cz) along d,
-// periodic
-__device__ __forceinline__ int neighbour(int e, int cx, int cy, int cz, int d, int off)
+// neighbour of element e of solve S (x-fastest numbering over S.cells)
+// along d, periodic; the divisions by the cell counts are multiply-highs
+__device__ __forceinline__ int neighbour_of(const SolveDesc &S, int e, int d, int off)
 {
-    int ix = e % cx;
-    const int r = e / cx;
-    int iy = r % cy;
-    int iz = r / cy;
+    const int cx = S.cells[0], cy = S.cells[1], cz = S.cells[2];
+    const unsigned q0 = fdiv((unsigned)e, S.div_cx), q1 = fdiv(q0, S.div_cy);
+    int ix = e - (int)q0 * cx, iy = (int)(q0 - q1 * (unsigned)cy), iz = (int)q1;
     if (d == 0) ix = ix + off < 0 ? cx - 1 : (ix + off >= cx ? 0 : ix + off);
     else if (d == 1) iy = iy + off < 0 ? cy - 1 : (iy + off >= cy ? 0 : iy + off);
     else iz = iz + off < 0 ? cz - 1 : (iz + off >= cz ? 0 : iz + off);
     return ix + cx * (iy + cy * iz);
 }
 
-// Neighbour of element e of a block across its face (d, side): the block
-// element (>= 0), or -(1 + j) for chunk j of the halo that another block of
-// a partitioned mesh filled (j: the element's index over the other
-// directions, lowest fastest).  Sg is the descriptor in device memory (its
-// halo pointers are read with runtime indices).
-__device__ __forceinline__ int neighbour_or_halo(int e, const SolveDesc *Sg, int cx, int cy, int cz, int d, int side)
+// Neighbour of element e (at cell (ix, iy, iz); no divisions) of a block
+// across its face (d, side): the block element (>= 0, periodic), or -(1 + j)
+// for chunk j of the halo that another block of a partitioned mesh filled
+// (j: the element's index over the other directions, lowest fastest).  Sg
+// is the descriptor in device memory (its halo pointers are read with
+// runtime indices).
+__device__ __forceinline__ int neighbour_or_halo_at(int e, int ix, int iy, int iz, const SolveDesc *Sg, int cx, int cy,
+                                                    int cz, int d, int side)
 {
-    const int ix = e % cx, r = e / cx, iy = r % cy, iz = r / cy;
     const int k = d == 0 ? ix : (d == 1 ? iy : iz);
     const int cd = d == 0 ? cx : (d == 1 ? cy : cz);
-    if ((side ? k == cd - 1 : k == 0) && Sg->halo_tr[d][side] != nullptr)
+    const int stride = d == 0 ? 1 : (d == 1 ? cx : cx * cy);
+    const bool edge = side ? k == cd - 1 : k == 0;
+    if (edge && Sg->halo_tr[d][side] != nullptr)
         return -1 - (d == 0 ? iy + cy * iz : (d == 1 ? ix + cx * iz : ix + cx * iy));
-    return neighbour(e, cx, cy, cz, d, side ? 1 : -1);
+    if (edge) return side ? e - (cd - 1) * stride : e + (cd - 1) * stride;  // periodic
+    return side ? e + stride : e - stride;
 }
 
 template <class PDE, int DIM, int N, typename T, int TS>
@@ -1186,7 +1188,6 @@ k_corrector(const KParams P)
     T *sV = reinterpret_cast<T *>(sb + C::O_V);
     T *sFs = reinterpret_cast<T *>(sb + C::O_FS);
     T *sL = reinterpret_cast<T *>(sb + C::O_LIFT);  // [side][d][k]
-    int *sNbIdx = reinterpret_cast<int *>(sb + C::O_NBIDX);
     T *sDel = reinterpret_cast<T *>(sb + C::O_DEL);  // [el][d][side][dF | dq][M]
     T *sRefO = reinterpret_cast<T *>(sb + C::O_REFO);  // [el][M]
     double *red = reinterpret_cast<double *>(sb + C::O_RED);
@@ -1229,11 +1230,24 @@ k_corrector(const KParams P)
         if (C::WM && ne == 0) continue;  // uniform over the warp
         const T *tr = reinterpret_cast<const T *>(S.tr);
 
-        // ---- stage everything -----------------------------------------------
-        for (int c = tid; c < ne * 2 * DIM; c += nthr) {
+        // ---- stage everything (one round of loads: the neighbour indices are
+        // ---- formed where they are used, not published through a barrier) --
+        const int cx = S.cells[0], cy = S.cells[1], cz = S.cells[2];
+        // the unit's first cell (divisions by multiply-high)
+        const unsigned q0 = fdiv((unsigned)e0, S.div_cx), q1 = fdiv(q0, S.div_cy);
+        const int ix0 = e0 - (int)q0 * cx, iy0 = (int)(q0 - q1 * (unsigned)cy), iz0 = (int)q1;
+        auto nb_of = [&](int c) {
             const int el = c / (2 * DIM), d = (c / 2) % DIM, side = c & 1;
-            sNbIdx[c] = neighbour_or_halo(e0 + el, P.solves + si, S.cells[0], S.cells[1], S.cells[2], d, side);
-        }
+            int ix = ix0 + el, iy = iy0, iz = iz0;
+            while (ix >= cx) {  // el < EPB: a few rows at most
+                ix -= cx;
+                if (++iy == cy) {
+                    iy = 0;
+                    ++iz;
+                }
+            }
+            return neighbour_or_halo_at(e0 + el, ix, iy, iz, P.solves + si, cx, cy, cz, d, side);
+        };
         for (int i = tid; i < DIM * n; i += nthr) {
             const int d = i / n, k = i % n;
             if constexpr (sizeof(T) == 4) {  // precomputed on the host: no FP64 work here
@@ -1250,20 +1264,25 @@ k_corrector(const KParams P)
             stage<C::G_U>(sU, S.u + (long long)e0 * NS * M, ne * (int)C::UB, tid, nthr);
             stage<C::G_V>(sV, reinterpret_cast<const T *>(S.V) + (long long)e0 * NS * M, ne * (int)C::VB, tid, nthr);
         }
-        usync();  // neighbour indices
         {
+            // the neighbour chunks: tpc consecutive threads per chunk (element,
+            // d, side), which forms its neighbour index once; ng = nthr / tpc
+            // >= nch groups whenever tpc > 1, so every chunk has one group
             constexpr int units = (int)(sizeof(T) * NF * RS) / C::G_NB;
-            for (int i = tid; i < ne * 2 * DIM * units; i += nthr) {
-                const int u_ = i % units;
-                const int c = i / units;  // chunk (element, d, side)
+            const int nch = ne * 2 * DIM;
+            const int tpc = nthr >= 2 * nch ? nthr / nch : 1;
+            const int ng = nthr / tpc;
+            for (int c = tid / tpc; c < nch && tid < ng * tpc; c += ng) {
                 const int d = (c / 2) % DIM;
                 const int side = c & 1;
-                const int nb = sNbIdx[c];
+                const int nb = nb_of(c);
                 const T *src = nb >= 0 ? tr + (((long long)nb * DIM + d) * 2 + (1 - side)) * NF * RS
                                        : reinterpret_cast<const T *>(P.solves[si].halo_tr[d][side]) +
                                              (long long)(-1 - nb) * NF * RS;
                 unsigned char *dst = reinterpret_cast<unsigned char *>(sNb + (size_t)c * NF * RS);
-                cp_async(dst + u_ * C::G_NB, reinterpret_cast<const unsigned char *>(src) + u_ * C::G_NB, C::G_NB);
+                for (int u_ = tid % tpc; u_ < units; u_ += tpc)
+                    cp_async(dst + u_ * C::G_NB, reinterpret_cast<const unsigned char *>(src) + u_ * C::G_NB,
+                             C::G_NB);
             }
         }
         if constexpr (C::DELTA) {
@@ -1274,7 +1293,7 @@ k_corrector(const KParams P)
             for (int c = tid; c < ne * 2 * DIM; c += nthr) {
                 const int el = c / (2 * DIM), d = (c / 2) % DIM, side = c & 1;
                 const double *ro = S.ref + (long long)(e0 + el) * C::RF;
-                const int nb = sNbIdx[c];
+                const int nb = nb_of(c);
                 const double *rn = nb >= 0 ? S.ref + (long long)nb * C::RF
                                            : P.solves[si].halo_ref[d][side] + (long long)(-1 - nb) * C::RF;
                 double qo[M];
@@ -1596,7 +1615,7 @@ const KernelSet KS<PDE, DIM, N, T>::value = {
      pred_shape<PDE, DIM, N, T, 6, true>(), pred_shape<PDE, DIM, N, T, 7, true>(),
      pred_shape<PDE, DIM, N, T, 8, true>()},
     {corr_shape<PDE, DIM, N, T, 0>(), corr_shape<PDE, DIM, N, T, 1>(), corr_shape<PDE, DIM, N, T, 2>(),
-     corr_shape<PDE, DIM, N, T, 3>()},
+     corr_shape<PDE, DIM, N, T, 3>(), corr_shape<PDE, DIM, N, T, 4>()},
     0, 0};
 
 }  // namespace aderdg

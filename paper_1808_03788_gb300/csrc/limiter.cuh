@@ -64,6 +64,31 @@ __device__ __forceinline__ void lim_pass(const V *src, V *dst, const V *Op, int 
     }
 }
 
+// The same pass by lines: each item is one line (al, ah, v) whose C inputs
+// are read once and give its R outputs, each the same C-term sum in j order
+// as lim_pass (bitwise the same results, fewer loads and index divisions;
+// used by the one-warp FP32 teams, where the FMA pipe is not the limit).
+template <int M, int R, int C, int LO, int HI, typename V>
+__device__ __forceinline__ void lim_pass_lines(const V *src, V *dst, const V *Op, int tid, int nt)
+{
+    constexpr int lines = LO * HI * M;
+    for (int i = tid; i < lines; i += nt) {
+        const int v = i % M, r = i / M, al = r % LO, ah = r / LO;
+        const V *x = src + (al + LO * C * ah) * M + v;
+        V xin[C];
+#pragma unroll
+        for (int j = 0; j < C; ++j) xin[j] = x[j * LO * M];
+        V *y = dst + (al + LO * R * ah) * M + v;
+#pragma unroll
+        for (int ad = 0; ad < R; ++ad) {
+            V acc = V(0);
+#pragma unroll
+            for (int j = 0; j < C; ++j) acc += Op[ad * C + j] * xin[j];
+            y[ad * LO * M] = acc;
+        }
+    }
+}
+
 // out = (Op (x) ... (x) Op) in along the DIM directions, Op an R x C matrix
 // in shared memory ([r][c]); in has C points per direction (x fastest,
 // M values per point), out R.  The team -- a CTA or one warp -- is the
@@ -71,20 +96,28 @@ __device__ __forceinline__ void lim_pass(const V *src, V *dst, const V *Op, int 
 template <int DIM, int M, int R, int C, typename V, class Sync>
 __device__ void lim_tensor_team(const V *in, V *out, V *ta, V *tb, const V *Op, int tid, int nt, Sync sync)
 {
+    auto pass = [&](auto lo, auto hi, const V *src, V *dst) {
+        constexpr int LO = decltype(lo)::value, HI = decltype(hi)::value;
+        if constexpr (sizeof(V) == 4) lim_pass_lines<M, R, C, LO, HI>(src, dst, Op, tid, nt);
+        else lim_pass<M, R, C, LO, HI>(src, dst, Op, tid, nt);
+    };
+    using I1 = std::integral_constant<int, 1>;
+    using IC = std::integral_constant<int, C>;
+    using IR = std::integral_constant<int, R>;
     if constexpr (DIM == 1) {
-        lim_pass<M, R, C, 1, 1>(in, out, Op, tid, nt);
+        pass(I1{}, I1{}, in, out);
         sync();
     } else if constexpr (DIM == 2) {
-        lim_pass<M, R, C, 1, C>(in, ta, Op, tid, nt);
+        pass(I1{}, IC{}, in, ta);
         sync();
-        lim_pass<M, R, C, R, 1>(ta, out, Op, tid, nt);
+        pass(IR{}, I1{}, ta, out);
         sync();
     } else {
-        lim_pass<M, R, C, 1, C * C>(in, ta, Op, tid, nt);
+        pass(I1{}, std::integral_constant<int, C * C>{}, in, ta);
         sync();
-        lim_pass<M, R, C, R, C>(ta, tb, Op, tid, nt);
+        pass(IR{}, IC{}, ta, tb);
         sync();
-        lim_pass<M, R, C, R * R, 1>(tb, out, Op, tid, nt);
+        pass(std::integral_constant<int, R * R>{}, I1{}, tb, out);
         sync();
     }
 }
@@ -306,6 +339,17 @@ struct LimSmem {
     }
 };
 
+// whether a limited solve of the launch has a troubled element this step
+// (the subcell scheme and the coupling have nothing to do otherwise)
+__device__ __forceinline__ bool lim_any_troubled(const KParams &P)
+{
+    for (int si = 0; si < P.nsolves; ++si) {
+        const SolveDesc &S = P.solves[si];
+        if (S.u_prev && S.ctl->lim_count != 0u) return true;
+    }
+    return false;
+}
+
 template <class L>
 __device__ void lim_load_ops(const KParams &P, LimSmem<L> &sm)
 {
@@ -414,7 +458,7 @@ __global__ void __launch_bounds__(128) k_lim_minmax(const KParams P)
 #pragma unroll
                         for (int side = 0; side < 2; ++side)
                             touched |=
-                                S.lim_flags[neighbour((int)e, S.cells[0], S.cells[1], S.cells[2], d, side ? 1 : -1)];
+                                S.lim_flags[neighbour_of(S, (int)e, d, side ? 1 : -1)];
                     reuse = !touched;
                 }
                 if (reuse) {  // uniform over the warp
@@ -475,7 +519,7 @@ __global__ void __launch_bounds__(128) k_lim_detect(const KParams P)
 #pragma unroll
                             for (int side = 0; side < 2; ++side) {
                                 const long long nb =
-                                    neighbour((int)e, S.cells[0], S.cells[1], S.cells[2], d, side ? 1 : -1);
+                                    neighbour_of(S, (int)e, d, side ? 1 : -1);
                                 const long long kl = lim_key(S.lim_mm[(nb * L::M + v) * 2]);
                                 const long long kh = lim_key(S.lim_mm[(nb * L::M + v) * 2 + 1]);
                                 klo = kl < klo ? kl : klo;
@@ -532,6 +576,7 @@ struct LimWarp32 {
     static constexpr int PR32 = round_up(L::S * L::n, 4);  // floats: the FP32 operator
     static constexpr size_t BYTES = 8 * (size_t)PR64 + 4 * (size_t)PR32 + 4 * WARPS * FLOATS;
     static constexpr float TOLC = 2.0f * (L::n + 2) * 3 + 8.0f;  // d (n + 2) + 4, doubled, for d <= 3
+    static_assert(round_up(L::TMP, 4) >= 4 * L::M, "the detection keeps 2 M doubles of bounds in ta");
 };
 
 // The FP64 subcell average a of variable v from the FP64 nodes x of one
@@ -598,21 +643,29 @@ __device__ __forceinline__ void lim_averages32_warp(const double *src, long long
 template <class L>
 __device__ __forceinline__ void lim_extremes32_warp(const float *avg, double ref_l, int lane, double *mm)
 {
+    float lo[L::M], hi[L::M];
+    NodeIO<float, L::M>::load(avg, lo);  // subcell 0 seeds every lane
+#pragma unroll
+    for (int v = 0; v < L::M; ++v) hi[v] = lo[v];
+    for (int a = lane; a < L::NSUB; a += 32) {  // each subcell's averages in one vector read
+        float x[L::M];
+        NodeIO<float, L::M>::load(avg + a * L::M, x);
+#pragma unroll
+        for (int v = 0; v < L::M; ++v) {
+            lo[v] = fminf(lo[v], x[v]);
+            hi[v] = fmaxf(hi[v], x[v]);
+        }
+    }
     float lo_l = 0.f, hi_l = 0.f;
 #pragma unroll
     for (int v = 0; v < L::M; ++v) {
-        float lo = avg[v], hi = lo;
-        for (int a = lane; a < L::NSUB; a += 32) {
-            lo = fminf(lo, avg[a * L::M + v]);
-            hi = fmaxf(hi, avg[a * L::M + v]);
-        }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
-            hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+            lo[v] = fminf(lo[v], __shfl_xor_sync(0xffffffffu, lo[v], o));
+            hi[v] = fmaxf(hi[v], __shfl_xor_sync(0xffffffffu, hi[v], o));
         }
-        lo_l = lane == v ? lo : lo_l;
-        hi_l = lane == v ? hi : hi_l;
+        lo_l = lane == v ? lo[v] : lo_l;
+        hi_l = lane == v ? hi[v] : hi_l;
     }
     if (lane < L::M) {
         mm[lane * 2] = ref_l + flt_to_dbl(lo_l);
@@ -666,36 +719,47 @@ __global__ void __launch_bounds__(128) k_lim_minmax32(const KParams P)
             const SolveDesc &S = P.solves[si];
             if (!S.u_prev) continue;  // a solve without the limiter
             const bool fresh = S.ctl->lim_fresh != 0;
-            for (long long e = (long long)blockIdx.x * W::WARPS + warp; e < S.E; e += (long long)gridDim.x * W::WARPS) {
-                bool reuse = fresh;
-                if (reuse) {
-                    int touched = S.lim_flags[e];
+            // 32 elements per warp at a time: each lane decides for its own
+            // element and copies the kept extremes; the warp then projects
+            // the elements that need it, one after the other
+            for (long long e0 = ((long long)blockIdx.x * W::WARPS + warp) * 32; e0 < S.E;
+                 e0 += (long long)gridDim.x * W::WARPS * 32) {
+                const long long el = e0 + lane;
+                bool need = el < S.E;
+                if (need && fresh) {
+                    int touched = S.lim_flags[el];
 #pragma unroll
                     for (int d = 0; d < DIM; ++d)
 #pragma unroll
                         for (int side = 0; side < 2; ++side)
                             touched |=
-                                S.lim_flags[neighbour((int)e, S.cells[0], S.cells[1], S.cells[2], d, side ? 1 : -1)];
-                    reuse = !touched;
+                                S.lim_flags[neighbour_of(S, (int)el, d, side ? 1 : -1)];
+                    if (!touched) {
+#pragma unroll
+                        for (int k = 0; k < 2 * L::M; ++k) S.lim_mm[el * (2 * L::M) + k] = S.lim_mmc[el * (2 * L::M) + k];
+                        need = false;
+                    }
                 }
-                if (reuse) {  // uniform over the warp
-                    if (lane < 2 * L::M) S.lim_mm[e * (2 * L::M) + lane] = S.lim_mmc[e * (2 * L::M) + lane];
-                    continue;
+                unsigned todo = __ballot_sync(0xffffffffu, need);
+                while (todo) {  // uniform over the warp
+                    const long long e = e0 + (__ffs(todo) - 1);
+                    todo &= todo - 1;
+                    double ref[L::M], ref_l;
+                    float am_l;
+                    lim_averages32_warp<L, DIM>(S.u_prev, e, Pr32, u, avg, ta, tb, lane, ref, ref_l, am_l);
+                    lim_extremes32_warp<L>(avg, ref_l, lane, S.lim_mm + e * (2 * L::M));
+                    __syncwarp();
                 }
-                double ref[L::M], ref_l;
-                float am_l;
-                lim_averages32_warp<L, DIM>(S.u_prev, e, Pr32, u, avg, ta, tb, lane, ref, ref_l, am_l);
-                lim_extremes32_warp<L>(avg, ref_l, lane, S.lim_mm + e * (2 * L::M));
-                __syncwarp();
             }
         }
     }
 }
 
-// Euler admissibility of one FP32 subcell average (absolute state ref +
-// avg): 1 admissible, 0 not, -1 too close to call in FP32.
+// Euler admissibility of one FP32 subcell average (absolute state refF +
+// avg, refF the element's reference rounded to float once): 1 admissible,
+// 0 not, -1 too close to call in FP32.
 template <class PDE>
-__device__ __forceinline__ int lim_admissible32(const PdeParams &P, const double *ref, const float *avg)
+__device__ __forceinline__ int lim_admissible32(const PdeParams &P, const float *refF, const float *avg)
 {
     if constexpr (PDE::KIND == 2) {
         constexpr int D = PDE::M - 2;
@@ -703,14 +767,14 @@ __device__ __forceinline__ int lim_admissible32(const PdeParams &P, const double
         float mag = 0.f;
 #pragma unroll
         for (int v = 0; v < PDE::M; ++v) {
-            q[v] = dbl_to_flt_rn(ref[v]) + avg[v];
+            q[v] = refF[v] + avg[v];
             mag = fmaxf(mag, fabsf(q[v]));
         }
         if (q[0] <= 1e-6f * mag) return q[0] < -1e-6f * mag ? 0 : -1;
         float kin = 0.f;
 #pragma unroll
         for (int k = 0; k < D; ++k) kin += q[1 + k] * q[1 + k];
-        const float e2 = 0.5f * kin / q[0];
+        const float e2 = 0.5f * kin * recip(q[0]);  // within 1 ulp: far inside the 1e-5 band
         const float p = pconst<float>(P, 0) * (q[D + 1] - e2);
         const float err = 1e-5f * (fabsf(q[D + 1]) + e2) * pconst<float>(P, 0);
         return p > err ? 1 : (p < -err ? 0 : -1);
@@ -754,13 +818,16 @@ __global__ void __launch_bounds__(128) k_lim_detect32(const KParams P)
                     lim_extremes32_warp<L>(avg, ref_l, lane, S.lim_mmc + e * (2 * L::M));
                     // admissibility at the nodes: FP32 on ref + perturbation, FP64
                     // where that is too close to call
+                    float refF[L::M];
+#pragma unroll
+                    for (int v = 0; v < L::M; ++v) refF[v] = PDE::KIND == 2 ? dbl_to_flt_rn(ref[v]) : 0.f;
                     for (int s = lane; s < L::NS; s += 32) {
-                        int ok = lim_admissible32<PDE>(P.pde, ref, u + s * L::M);
+                        int ok = lim_admissible32<PDE>(P.pde, refF, u + s * L::M);
                         if (ok < 0) ok = lim_admissible<PDE>(P.pde, uc + s * L::M) ? 1 : 0;
                         bad |= ok == 0;
                     }
                     for (int a = lane; a < L::NSUB; a += 32) {
-                        int ok = lim_admissible32<PDE>(P.pde, ref, avg + a * L::M);
+                        int ok = lim_admissible32<PDE>(P.pde, refF, avg + a * L::M);
                         if (ok < 0) {  // too close to call: the subcell's FP64 averages
                             double q[L::M];
 #pragma unroll
@@ -782,7 +849,7 @@ __global__ void __launch_bounds__(128) k_lim_detect32(const KParams P)
 #pragma unroll
                             for (int side = 0; side < 2; ++side) {
                                 const long long nb =
-                                    neighbour((int)e, S.cells[0], S.cells[1], S.cells[2], d, side ? 1 : -1);
+                                    neighbour_of(S, (int)e, d, side ? 1 : -1);
                                 const long long kl = lim_key(S.lim_mm[(nb * L::M + v) * 2]);
                                 const long long kh = lim_key(S.lim_mm[(nb * L::M + v) * 2 + 1]);
                                 klo = kl < klo ? kl : klo;
@@ -796,17 +863,43 @@ __global__ void __launch_bounds__(128) k_lim_detect32(const KParams P)
                         rhi_l = dbl_to_flt_rn(bhi_l - ref_l);
                         tol_l = W::TOLC * EPS * rhoD * am_l + 2.f * EPS * fmaxf(fabsf(rlo_l), fabsf(rhi_l)) + 1e-30f;
                     }
+                    // every lane gets all variables' FP32 bands [lo - tol, lo + tol]
+                    // and [hi - tol, hi + tol] around the bounds; each subcell's
+                    // averages are read once.  The FP64 bounds, for the rare
+                    // rechecks, wait in the projection buffer ta (free by now).
+                    double *bnd = reinterpret_cast<double *>(ta);
+                    if (lane < L::M) {
+                        bnd[2 * lane] = blo_l;
+                        bnd[2 * lane + 1] = bhi_l;
+                    }
+                    __syncwarp();
+                    auto blo_at = [&](int v) { return bnd[2 * v]; };
+                    auto bhi_at = [&](int v) { return bnd[2 * v + 1]; };
+                    float dlo[L::M], ulo[L::M], dhi[L::M], uhi[L::M];
 #pragma unroll
                     for (int v = 0; v < L::M; ++v) {
                         const float rlo = __shfl_sync(0xffffffffu, rlo_l, v), rhi = __shfl_sync(0xffffffffu, rhi_l, v);
                         const float tol = __shfl_sync(0xffffffffu, tol_l, v);
-                        const double blo = __shfl_sync(0xffffffffu, blo_l, v), bhi = __shfl_sync(0xffffffffu, bhi_l, v);
-                        for (int a = lane; a < L::NSUB; a += 32) {
-                            const float x = avg[a * L::M + v];
-                            if (x < rlo - tol || x > rhi + tol) {
-                                bad = 1;
-                            } else if (x < rlo + tol || x > rhi - tol) {  // too close to call in FP32
+                        dlo[v] = rlo - tol;
+                        ulo[v] = rlo + tol;
+                        dhi[v] = rhi - tol;
+                        uhi[v] = rhi + tol;
+                    }
+                    for (int a = lane; a < L::NSUB; a += 32) {
+                        float x[L::M];
+                        NodeIO<float, L::M>::load(avg + a * L::M, x);
+                        int close = 0;
+#pragma unroll
+                        for (int v = 0; v < L::M; ++v) {
+                            bad |= x[v] < dlo[v] || x[v] > uhi[v];
+                            close |= (x[v] < ulo[v] || x[v] > dhi[v]) ? (1 << v) : 0;
+                        }
+                        if (close && !bad) {  // too close to call in FP32: FP64 averages
+#pragma unroll 1
+                            for (int v = 0; v < L::M; ++v) {
+                                if (!((close >> v) & 1)) continue;
                                 const double x64 = lim_average64<L, DIM>(uc, Pr64, a, v);
+                                const double blo = blo_at(v), bhi = bhi_at(v);
                                 bad |= x64 < blo || x64 > bhi;
                             }
                         }
@@ -833,6 +926,7 @@ __global__ void __launch_bounds__(128) k_lim_fv(const KParams P)
     using L = LimCfg<PDE, DIM, N>;
     if constexpr (L::OK) {
         constexpr int M = L::M, S_ = L::S;
+        if (!lim_any_troubled(P)) return;  // uniform over the grid
         extern __shared__ __align__(16) unsigned char smem_raw[];
         LimSmem<L> sm(reinterpret_cast<double *>(smem_raw));
         lim_load_ops<L>(P, sm);
@@ -851,7 +945,7 @@ __global__ void __launch_bounds__(128) k_lim_fv(const KParams P)
                 for (int d = 0; d < DIM; ++d)
 #pragma unroll 1
                     for (int side = 0; side < 2; ++side) {
-                        const long long nb = neighbour((int)e, S.cells[0], S.cells[1], S.cells[2], d, side ? 1 : -1);
+                        const long long nb = neighbour_of(S, (int)e, d, side ? 1 : -1);
                         lim_averages<L, DIM>(S.u_prev, nb, sm, sm.nb);
                         // ghost cells -2, -1 from the lower neighbour's last
                         // layers; S, S+1 from the upper neighbour's first ones
@@ -958,6 +1052,7 @@ __global__ void __launch_bounds__(128) k_lim_couple(const KParams P)
     if constexpr (L::OK) {
         constexpr int M = L::M, S_ = L::S, n = L::n, NF = L::NF, RS = Geom<PDE, DIM, N>::RS;
         constexpr int NFACE = 2 * DIM * NF;
+        if (!lim_any_troubled(P)) return;  // uniform over the grid
         extern __shared__ __align__(16) unsigned char smem_raw[];
         LimSmem<L> sm(reinterpret_cast<double *>(smem_raw));
         lim_load_ops<L>(P, sm);
@@ -975,14 +1070,14 @@ __global__ void __launch_bounds__(128) k_lim_couple(const KParams P)
                 for (int d = 0; d < DIM; ++d)
 #pragma unroll
                     for (int side = 0; side < 2; ++side)
-                        any |= S.lim_flags[neighbour((int)e, S.cells[0], S.cells[1], S.cells[2], d, side ? 1 : -1)];
+                        any |= S.lim_flags[neighbour_of(S, (int)e, d, side ? 1 : -1)];
                 if (!any) continue;  // uniform over the CTA
                 lim_averages<L, DIM>(S.u_prev, e, sm, sm.avg);
 #pragma unroll 1
                 for (int d = 0; d < DIM; ++d)
 #pragma unroll 1
                     for (int side = 0; side < 2; ++side) {
-                        const long long nb = neighbour((int)e, S.cells[0], S.cells[1], S.cells[2], d, side ? 1 : -1);
+                        const long long nb = neighbour_of(S, (int)e, d, side ? 1 : -1);
                         if (!S.lim_flags[nb]) continue;
                         lim_averages<L, DIM>(S.u_prev, nb, sm, sm.nb);
                         // the face's four cell layers: lower element's last two,

@@ -236,7 +236,7 @@ int launch_limiter(aderdg_t *h)
     kp.use_ctl_dt = 1;
     const LimKernels &lk = h->lk;
     const unsigned grid = (unsigned)std::min<long long>(h->E, 152LL * 16);
-    lk.minmax<<<grid, 128, lk.smem_w, h->stream>>>(kp);
+    lk.minmax<<<lk.minmax_grid(h->E), 128, lk.smem_w, h->stream>>>(kp);
     lk.detect<<<grid, 128, lk.smem_w, h->stream>>>(kp);
     lk.fv<<<grid, 128, lk.smem, h->stream>>>(kp);
     lk.couple<<<grid, 128, lk.smem, h->stream>>>(kp);
