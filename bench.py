@@ -301,6 +301,15 @@ def _roofline(info, pred_avg, prec_name, probe, workload):
             "algorithmic_flops_per_launch": info["flops_predictor"], "launch_ms": pred_avg}
 
 
+def _hbm_peak_gbs():
+    """Measured HBM copy bandwidth (MEASURED_PEAKS.json), else the 6.8 TB/s
+    fallback of the profiling recipe."""
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0))
+    except Exception:
+        return 6800.0
+
+
 def _kernels(info, pred_avg, corr_avg, hbm):
     corr_gbs = info["bytes_corrector"] / (corr_avg / 1e3) / 1e9
     return {
@@ -366,7 +375,10 @@ def _guess_variants(A, torch, w, stream, flush, steps, warmup, shapes, l2_steps,
     return out
 
 
-def _limiter(A, torch, w, stream, flush, steps, warmup):
+LIMITER_CASES = ("vortex", "blast", "inclusion", "inclusion_unlimited", "vortex_mixed", "blast_mixed")
+
+
+def _limiter(A, torch, w, stream, flush, steps, warmup, cases=LIMITER_CASES, shapes=(0, 0)):
     """The a posteriori subcell limiter (Sec. 2.3) on the headline mesh, FP64:
     the vortex (smooth: detection only) and a blast (rho, p = 1 inside
     r = 2, 0.125 / 0.1 outside, tanh edge of width 0.3, centred in the box);
@@ -380,13 +392,13 @@ def _limiter(A, torch, w, stream, flush, steps, warmup):
 
     from paper_1808_03788_gb300 import inputs
     out = {"precision": "fp64 (the *_mixed cases: the FP32 path)"}
-    for name in ("vortex", "blast", "inclusion", "inclusion_unlimited", "vortex_mixed", "blast_mixed"):
+    for name in cases:
         dim_pde = name.startswith("inclusion")
         pde, params = (A.ADERDG_PDE_DIFFUSE_ELASTICITY, ()) if dim_pde else (w["pde"], w["params"])
         lim = name != "inclusion_unlimited"
         prec = A.ADERDG_MIXED_FP32 if name.endswith("_mixed") else A.ADERDG_FP64
         s = A.Solver(pde, w["dim"], w["cells"], w["lo"], w["hi"], w["N"], params, stream=stream.cuda_stream,
-                     limiter=lim, precision=prec)
+                     limiter=lim, precision=prec, shapes=shapes)
         X = s.node_coords(w["lo"], w["hi"])
         x, y = X[..., 0], X[..., 1]
         if name.startswith("vortex"):
@@ -419,7 +431,8 @@ def _limiter(A, torch, w, stream, flush, steps, warmup):
         info = s.info()
         s.close()
         out[name] = {"value": info["dofs"] * steps / (sum(ms) / 1e3), "ms_per_step": sum(ms) / steps,
-                     "troubled_last_step": int(cnt), "elements": int(info["elements"])}
+                     "troubled_last_step": int(cnt), "elements": int(info["elements"]),
+                     "tile_shapes": [info["pred_shape"], info["corr_shape"]]}
     return out
 
 
@@ -562,9 +575,12 @@ def _elastic(A, torch, stream, flush, steps, shapes=(0, 0), workload="elastic3d_
         info = s.info()
         states[name] = s.get_state()[0]
         s.close()
+        corr_gbs = info["bytes_corrector"] / (statistics.mean(co) / 1e3) / 1e9
         out[name] = {"value": info["dofs"] * steps / (sum(st) / 1e3), "ms_per_step": sum(st) / steps,
                      "predictor_ms": statistics.mean(pr), "corrector_ms": statistics.mean(co),
-                     "predictor_tflops": info["flops_predictor"] / (statistics.mean(pr) / 1e3) / 1e12}
+                     "predictor_tflops": info["flops_predictor"] / (statistics.mean(pr) / 1e3) / 1e12,
+                     "corrector_gbs": corr_gbs, "corrector_hbm_frac": corr_gbs / _hbm_peak_gbs(),
+                     "tile_shapes": [info["pred_shape"], info["corr_shape"]]}
     a, b = states["mixed"], states["fp64"]
     num = np.sqrt(np.sum((a - b) ** 2, axis=(0, 1)))
     den = np.sqrt(np.sum(b ** 2, axis=(0, 1)))
@@ -735,12 +751,7 @@ def run_ours(args, w, rank, world):
             probe[name] = None if args.no_probe else A.aderdg_peak_tflops(kind)
         except Exception:  # the probe is context only
             probe[name] = None
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        pass
-    hbm = peaks.get("hbm_gbs", 6800.0)
+    hbm = _hbm_peak_gbs()
     pred_avg, corr_avg = statistics.mean(pred_ms), statistics.mean(corr_ms)
     roofline = _roofline(info, pred_avg, args.precision, probe, args.workload)
     kernels = _kernels(info, pred_avg, corr_avg, hbm)
@@ -765,7 +776,8 @@ def run_ours(args, w, rank, world):
             variants["partitioned"] = _partitioned(A, torch, w, stream, flush, args.dd_steps, args.warmup,
                                                    shapes=shapes)
         if args.limiter_steps > 0 and w["pde"] == 2:
-            variants["limiter"] = _limiter(A, torch, w, stream, flush, args.limiter_steps, args.warmup)
+            variants["limiter"] = _limiter(A, torch, w, stream, flush, args.limiter_steps, args.warmup,
+                                           tuple(args.limiter_cases.split(",")), shapes)
         if args.guess_variant:
             variants.update(_guess_variants(A, torch, w, stream, flush, args.steps, args.warmup, shapes,
                                             args.l2_steps, probe, hbm, args.workload))
@@ -840,6 +852,8 @@ def main():
     ap.add_argument("--elastic-steps", type=int, default=4)
     ap.add_argument("--limiter-steps", type=int, default=10,
                     help="timed steps of the subcell-limiter variant (0: skip)")
+    ap.add_argument("--limiter-cases", default=",".join(LIMITER_CASES),
+                    help="comma list of the limiter cases to time (%s)" % ",".join(LIMITER_CASES))
     ap.add_argument("--diffuse-steps", type=int, default=3,
                     help="timed steps of the 3D diffuse-interface variant (0: skip)")
     ap.add_argument("--batched-solves", type=int, default=256)

@@ -177,7 +177,6 @@ __global__ void k_dt_batch(Control *const *ctls, int count)
     if (i < count) dt_update(ctls[i]);
 }
 
-__global__ void k_lim_reset_one(Control *c) { lim_reset(c); }
 
 __global__ void k_set_tend(Control *const *ctls, const double *t_end, int count)
 {
@@ -229,12 +228,19 @@ public:
     bool dirty = true;
     cudaGraphExec_t graph = nullptr;
     int graph_steps = 0;
+    // limited groups: the copies of u^n and their subcell extremes run on a
+    // second stream beside the group's predictor (event fork and join)
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
 
     int init(int capacity, cudaStream_t stream, const aderdg_alloc_t *hook)
     {
         cudaGetDevice(&device);
         st = stream;
         mem.st = stream;
+        CKB(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
+        CKB(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+        CKB(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
         if (hook) { mem.hook = *hook; mem.has_hook = true; }
         ctl_cap = std::max(1, capacity);
         d_ctl = (Control *)mem.get(sizeof(Control) * ctl_cap);
@@ -258,6 +264,12 @@ public:
         mem.put(d_ctl, sizeof(Control) * ctl_cap);
         if (h_ctl) cudaFreeHost(h_ctl);
         if (st) cudaStreamSynchronize(st);
+        if (side) cudaStreamSynchronize(side);
+        if (fork) cudaEventDestroy(fork);
+        if (join) cudaEventDestroy(join);
+        if (side) cudaStreamDestroy(side);
+        fork = join = nullptr;
+        side = nullptr;
         h_ctl = nullptr;
         d_ctl = nullptr;
     }
@@ -455,29 +467,37 @@ public:
         CKB(cudaGetLastError());
         for (Group &g : groups) {
             KParams kp = g.kp;
-            if (g.limiter)  // u^n for the limiter, before the corrector overwrites it
+            const LimKernels *glk = g.limiter ? &g.members[0]->lk : nullptr;  // one (PDE, d, N, precision) per group
+            if (g.limiter) {
+                // u^n for the limiter (before the corrector overwrites it) and
+                // its subcell extremes, on the side stream beside the predictor
+                CKB(cudaEventRecord(fork, st));
+                CKB(cudaStreamWaitEvent(side, fork, 0));
                 for (const Slot *m : g.members)
                     CKB(cudaMemcpyAsync(m->u_prev, m->u, (size_t)m->E * m->NS * m->M * sizeof(double),
-                                        cudaMemcpyDeviceToDevice, st));
+                                        cudaMemcpyDeviceToDevice, side));
+                glk->minmax<<<glk->minmax_grid(g.elems), 128, glk->smem_w, side>>>(kp);
+                CKB(cudaEventRecord(join, side));
+            }
             kp.ntiles = g.ntp;
             g.kso.predictor<<<(unsigned)g.ntp, g.kso.pred_threads, g.kso.pred_smem, st>>>(kp);
+            if (g.limiter) CKB(cudaStreamWaitEvent(st, join, 0));
             kp.ntiles = g.ntc;
             g.kso.corrector<<<(unsigned)g.ntc, g.kso.corr_threads, g.kso.corr_smem, st>>>(kp);
             if (g.limiter) {
                 // one launch of each limiter kernel for all solves of the group
                 const KernelSet *ks = g.ks;
-                const LimKernels &lk = g.members[0]->lk;  // one (PDE, d, N, precision) per group
+                const LimKernels &lk = *glk;
                 const unsigned grid = (unsigned)std::min<long long>(g.elems, 152LL * 16);
-                lk.minmax<<<lk.minmax_grid(g.elems), 128, lk.smem_w, st>>>(kp);
                 lk.detect<<<grid, 128, lk.smem_w, st>>>(kp);
                 lk.fv<<<grid, 128, lk.smem, st>>>(kp);
                 lk.couple<<<grid, 128, lk.smem, st>>>(kp);
                 for (const Slot *m : g.members) {
-                    k_lim_reset_one<<<1, 32, 0, st>>>(ctl_of(m));
                     KParams k1 = g.kp;
                     k1.solves = g.d_desc + m->member;
                     k1.nsolves = 1;
                     k1.use_ctl_dt = 1;
+                    k1.lim_pass = 1;  // the wave speeds of a limited state that changed
                     ks->cfl<<<(unsigned)std::min<long long>(4 * 152, (m->E * m->NS + 255) / 256), 256, 0, st>>>(k1);
                 }
             }

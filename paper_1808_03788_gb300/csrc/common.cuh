@@ -49,37 +49,10 @@ struct Control {
     unsigned int flags;
     unsigned int lim_fresh;  // subcell limiter: lim_mmc holds the candidate extremes of the state's last step
     unsigned int lim_count;  // subcell limiter: troubled elements listed in lim_list this step
-    unsigned int lim_keep;   // subcell limiter: the last step troubled no element, so the corrector's
-                             // wave-speed maxima are those of the state (k_cfl skips)
+                             // (zeroed by the next step's dt_update)
+    unsigned int pad1;
 };
 
-// After the subcell limiter: the step's wave-speed maxima and non-finite
-// flag are cleared before they are taken again from the limited state, and
-// the candidate extremes the detection kept become those of the new state
-// (for the elements the limiter left untouched).  A step that troubled no
-// element leaves the state as the corrector wrote it, so its maxima and
-// flag stand and lim_keep tells k_cfl to skip.  32 threads.
-#ifdef __CUDACC__
-__device__ __forceinline__ void lim_reset(Control *c)
-{
-    const unsigned cnt = c->lim_count;
-    __syncwarp();
-    if (cnt == 0u) {
-        if (threadIdx.x == 0) {
-            c->lim_fresh = 1u;
-            c->lim_keep = 1u;
-        }
-        return;
-    }
-    if (threadIdx.x < 3) c->lam_acc[threadIdx.x] = 0ull;
-    if (threadIdx.x == 0) {
-        c->flags &= ~FLAG_NONFINITE;
-        c->lim_fresh = 1u;
-        c->lim_count = 0u;
-        c->lim_keep = 0u;
-    }
-}
-#endif
 
 // PDE parameters as given (aderdg_pde_t) and constants derived from them
 // on the host (fill_pde_consts), in double and rounded to float, so that
@@ -219,6 +192,7 @@ struct KParams {
     const SolveDesc *solves;  // device array, tile0 ascending
     int nsolves;
     int use_ctl_dt;           // 1: dt of each solve from its ctl->dt, 0: dt_arg
+    int lim_pass;             // k_cfl after the subcell limiter: skip solves with no troubled element
     long long ntiles;         // tiles of this launch (predictor or corrector)
     double dt_arg;
     PdeParams pde;

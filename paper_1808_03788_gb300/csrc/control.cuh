@@ -9,6 +9,7 @@ namespace aderdg {
 
 __device__ __forceinline__ void dt_update(Control *c)
 {
+    c->lim_count = 0u;   // the last step's troubled list is consumed (subcell limiter)
     c->dt_prev = c->dt;  // the step just taken (0 if none)
     const double t = c->t;
     if (!(t < c->t_end) || (c->flags & FLAG_NONFINITE)) {

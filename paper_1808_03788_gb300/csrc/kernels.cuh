@@ -1492,7 +1492,9 @@ __global__ void __launch_bounds__(256) k_cfl(const KParams P)
     using G = Geom<PDE, DIM, N>;
     constexpr int M = G::M;
     const SolveDesc &S = P.solves[0];
-    if (S.ctl->lim_keep) return;  // a limited step that changed nothing: the corrector's maxima stand
+    // after a limited step that troubled no element the state is the
+    // corrector's candidate: its maxima stand
+    if (P.lim_pass && S.ctl->lim_count == 0u) return;
     const long long total = S.E * G::NS;
     double lmax[DIM];
 #pragma unroll

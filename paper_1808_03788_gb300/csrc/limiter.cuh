@@ -490,6 +490,8 @@ __global__ void __launch_bounds__(128) k_lim_detect(const KParams P)
         for (int si = 0; si < P.nsolves; ++si) {
             const SolveDesc &S = P.solves[si];
             if (!S.u_prev) continue;
+            // this launch keeps the candidate's extremes for the next step
+            if (blockIdx.x == 0 && threadIdx.x == 0) S.ctl->lim_fresh = 1u;
             for (long long e = (long long)blockIdx.x * W::WARPS + warp; e < S.E; e += (long long)gridDim.x * W::WARPS) {
                 const double *uc = S.u_out + e * (L::NS * L::M);  // the candidate
                 int bad = 0;
@@ -801,6 +803,8 @@ __global__ void __launch_bounds__(128) k_lim_detect32(const KParams P)
         for (int si = 0; si < P.nsolves; ++si) {
             const SolveDesc &S = P.solves[si];
             if (!S.u_prev) continue;
+            // this launch keeps the candidate's extremes for the next step
+            if (blockIdx.x == 0 && threadIdx.x == 0) S.ctl->lim_fresh = 1u;
             for (long long e = (long long)blockIdx.x * W::WARPS + warp; e < S.E; e += (long long)gridDim.x * W::WARPS) {
                 const double *uc = S.u_out + e * (L::NS * L::M);  // the candidate
                 int bad = 0;
@@ -838,7 +842,7 @@ __global__ void __launch_bounds__(128) k_lim_detect32(const KParams P)
                     }
                     // the relaxed maximum principle of u^n over the element and
                     // its face neighbours: lane v forms variable v's bounds
-                    double blo_l = 0.0, bhi_l = 0.0;
+                    double lo_l = 0.0, hi_l = 0.0;
                     float rlo_l = 0.f, rhi_l = 0.f, tol_l = 0.f;
                     if (lane < L::M) {
                         const int v = lane;
@@ -855,13 +859,18 @@ __global__ void __launch_bounds__(128) k_lim_detect32(const KParams P)
                                 klo = kl < klo ? kl : klo;
                                 khi = kh > khi ? kh : khi;
                             }
-                        const double lo = lim_unkey(klo), hi = lim_unkey(khi);
-                        const double delta = fmax(1e-4, 1e-3 * (hi - lo));
-                        blo_l = lo - delta;
-                        bhi_l = hi + delta;
-                        rlo_l = dbl_to_flt_rn(blo_l - ref_l);
-                        rhi_l = dbl_to_flt_rn(bhi_l - ref_l);
-                        tol_l = W::TOLC * EPS * rhoD * am_l + 2.f * EPS * fmaxf(fabsf(rlo_l), fabsf(rhi_l)) + 1e-30f;
+                        lo_l = lim_unkey(klo);
+                        hi_l = lim_unkey(khi);
+                        // the relaxed bounds lo - delta, hi + delta in FP32 about
+                        // the reference (two FP64 differences): dlo, dhi are
+                        // within eps/2 of exact, delta within a few eps of
+                        // delta, and the band below takes 6 eps of the
+                        // bounds' magnitude for these roundings
+                        const float dlo = dbl_to_flt_rn(lo_l - ref_l), dhi = dbl_to_flt_rn(hi_l - ref_l);
+                        const float delta = fmaxf(1e-4f, 1e-3f * (dhi - dlo));
+                        rlo_l = dlo - delta;
+                        rhi_l = dhi + delta;
+                        tol_l = W::TOLC * EPS * rhoD * am_l + 6.f * EPS * fmaxf(fabsf(rlo_l), fabsf(rhi_l)) + 1e-30f;
                     }
                     // every lane gets all variables' FP32 bands [lo - tol, lo + tol]
                     // and [hi - tol, hi + tol] around the bounds; each subcell's
@@ -869,12 +878,19 @@ __global__ void __launch_bounds__(128) k_lim_detect32(const KParams P)
                     // rechecks, wait in the projection buffer ta (free by now).
                     double *bnd = reinterpret_cast<double *>(ta);
                     if (lane < L::M) {
-                        bnd[2 * lane] = blo_l;
-                        bnd[2 * lane + 1] = bhi_l;
+                        bnd[2 * lane] = lo_l;
+                        bnd[2 * lane + 1] = hi_l;
                     }
                     __syncwarp();
-                    auto blo_at = [&](int v) { return bnd[2 * v]; };
-                    auto bhi_at = [&](int v) { return bnd[2 * v + 1]; };
+                    // the FP64 bounds exactly as the FP64 detection forms them
+                    auto blo_at = [&](int v) {
+                        const double lo = bnd[2 * v], hi = bnd[2 * v + 1];
+                        return lo - fmax(1e-4, 1e-3 * (hi - lo));
+                    };
+                    auto bhi_at = [&](int v) {
+                        const double lo = bnd[2 * v], hi = bnd[2 * v + 1];
+                        return hi + fmax(1e-4, 1e-3 * (hi - lo));
+                    };
                     float dlo[L::M], ulo[L::M], dhi[L::M], uhi[L::M];
 #pragma unroll
                     for (int v = 0; v < L::M; ++v) {
@@ -1062,6 +1078,13 @@ __global__ void __launch_bounds__(128) k_lim_couple(const KParams P)
             const double dt = solve_dt(P, S);
             if (!(dt > 0.0)) continue;
             if (S.ctl->lim_count == 0u) continue;  // no troubled element this step: nothing to couple
+            if (blockIdx.x == 0 && threadIdx.x == 0) {
+                // the limited state's wave-speed maxima and non-finite flag
+                // are taken afresh by k_cfl after this launch (nothing else
+                // touches them meanwhile)
+                for (int d = 0; d < 3; ++d) S.ctl->lam_acc[d] = 0ull;
+                S.ctl->flags &= ~FLAG_NONFINITE;
+            }
             const double *tr = reinterpret_cast<const double *>(S.tr);
             for (long long e = blockIdx.x; e < S.E; e += gridDim.x) {
                 if (S.lim_flags[e]) continue;

@@ -180,6 +180,11 @@ struct aderdg_s {
     int device = 0;
     bool profiling = false;
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    // limiter: the copy of u^n and its subcell extremes run on a second
+    // stream while the predictor runs (forked and joined by events, so a
+    // stream capture takes both branches)
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
 };
 
 namespace {
@@ -223,12 +228,22 @@ int launch_corrector(aderdg_t *h, int use_ctl, double dt)
     return ADERDG_OK;
 }
 
-__global__ void k_lim_reset(Control *c) { lim_reset(c); }
 
 // The subcell limiter on the candidate the corrector left in u (Sec. 2.3):
 // detection, subcell finite-volume update of the troubled elements,
 // coupling of their unlimited neighbours, and the wave-speed maxima of the
 // limited state for the next CFL step.
+// The extremes of u^n's subcell averages (the maximum principle's bounds);
+// they read u_prev only, so the step runs them beside the predictor.
+int launch_lim_minmax(aderdg_t *h, cudaStream_t st)
+{
+    KParams kp = h->kp;
+    kp.use_ctl_dt = 1;
+    h->lk.minmax<<<h->lk.minmax_grid(h->E), 128, h->lk.smem_w, st>>>(kp);
+    CK(cudaGetLastError());
+    return ADERDG_OK;
+}
+
 int launch_limiter(aderdg_t *h)
 {
     const KernelSet *ks = h->ks;
@@ -236,11 +251,10 @@ int launch_limiter(aderdg_t *h)
     kp.use_ctl_dt = 1;
     const LimKernels &lk = h->lk;
     const unsigned grid = (unsigned)std::min<long long>(h->E, 152LL * 16);
-    lk.minmax<<<lk.minmax_grid(h->E), 128, lk.smem_w, h->stream>>>(kp);
     lk.detect<<<grid, 128, lk.smem_w, h->stream>>>(kp);
     lk.fv<<<grid, 128, lk.smem, h->stream>>>(kp);
     lk.couple<<<grid, 128, lk.smem, h->stream>>>(kp);
-    k_lim_reset<<<1, 32, 0, h->stream>>>(h->ctl);
+    kp.lim_pass = 1;  // the wave speeds of the limited state, if it changed
     ks->cfl<<<(unsigned)std::min<long long>(4 * 152, (h->E * h->NS + 255) / 256), 256, 0, h->stream>>>(kp);
     CK(cudaGetLastError());
     return ADERDG_OK;
@@ -250,12 +264,22 @@ int enqueue_step(aderdg_t *h)
 {
     k_dt<<<1, 32, 0, h->stream>>>(h->ctl);
     CK(cudaGetLastError());
-    if (h->limiter)
+    if (h->limiter) {
+        // u^n saved and its subcell extremes formed on the side stream, in
+        // the predictor's shadow (both read u^n, which the predictor does not
+        // write); the corrector, which overwrites u, waits for them
+        CK(cudaEventRecord(h->fork, h->stream));
+        CK(cudaStreamWaitEvent(h->side, h->fork, 0));
         CK(cudaMemcpyAsync(h->u_prev, h->u, (size_t)h->E * h->NS * h->M * sizeof(double), cudaMemcpyDeviceToDevice,
-                           h->stream));
+                           h->side));
+        int rc = launch_lim_minmax(h, h->side);
+        if (rc) return rc;
+        CK(cudaEventRecord(h->join, h->side));
+    }
     if (h->profiling) CK(cudaEventRecord(h->ev[0], h->stream));
     int rc = launch_predictor(h, 1, 0.0);
     if (rc) return rc;
+    if (h->limiter) CK(cudaStreamWaitEvent(h->stream, h->join, 0));
     if (h->profiling) CK(cudaEventRecord(h->ev[1], h->stream));
     rc = launch_corrector(h, 1, 0.0);
     if (rc) return rc;
@@ -458,6 +482,12 @@ int aderdg_create(const aderdg_mesh_t *mesh, int N, int nVar, const aderdg_pde_t
         aderdg_destroy(h);
         return fail(ADERDG_E_NOMEM, "pinned host allocation failed");
     }
+    if (h->limiter && (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
+                       cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming) != cudaSuccess ||
+                       cudaEventCreateWithFlags(&h->join, cudaEventDisableTiming) != cudaSuccess)) {
+        aderdg_destroy(h);
+        return fail(ADERDG_E_CUDA, "limiter stream or events");
+    }
 
     SolveDesc &sd = h->desc;
     std::memset(&sd, 0, sizeof(sd));
@@ -532,6 +562,9 @@ int aderdg_destroy(aderdg_t *h)
     if (h->host_pinned) cudaFreeHost(h->host_pinned);
     for (auto &e : h->ev)
         if (e) cudaEventDestroy(e);
+    if (h->fork) cudaEventDestroy(h->fork);
+    if (h->join) cudaEventDestroy(h->join);
+    if (h->side) cudaStreamDestroy(h->side);
     if (h->own_stream) cudaStreamDestroy(h->stream);
     delete h;
     return ADERDG_OK;
