@@ -132,7 +132,9 @@ extern "C" {
  * shape 3 gives every warp one element of its own (a shared-memory slice
  * per warp and no CTA-wide barrier between the staging, face-flux and
  * update phases); corrector shape 4 is a quarter-size CTA (64 threads:
- * more independent CTAs per SM).  Predictor
+ * more independent CTAs per SM); corrector shape 5 is the half-size CTA
+ * taking four groups of elements per tile, staging the next group's inputs
+ * while it computes the current one.  Predictor
  * shapes 3 and 4 are, for 2D FP32 solves whose n x n x m space-time plane
  * fits the registers, a kernel in which each thread owns that plane (about
  * 128 and 256 threads per CTA); elsewhere they repeat shapes 0 and 2.
@@ -149,7 +151,7 @@ extern "C" {
  * path's tolerance); only the speed differs.  ADERDG_SHAPE_AUTOTUNE picks the
  * shapes measured fastest on the current device. */
 #define ADERDG_NUM_PRED_SHAPES 9
-#define ADERDG_NUM_CORR_SHAPES 5
+#define ADERDG_NUM_CORR_SHAPES 6
 #define ADERDG_SHAPE_DEFAULT 0
 #define ADERDG_SHAPE_AUTOTUNE (-1)
 

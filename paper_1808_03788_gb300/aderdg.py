@@ -30,7 +30,7 @@ ADERDG_E_CANCELLED = -8
 ADERDG_PDE_ADVECTION, ADERDG_PDE_EULER, ADERDG_PDE_ELASTICITY, ADERDG_PDE_DIFFUSE_ELASTICITY = 1, 2, 3, 4
 ADERDG_FP64, ADERDG_MIXED_FP32 = 0, 1
 ADERDG_HOST, ADERDG_DEVICE = 0, 1
-ADERDG_NUM_PRED_SHAPES, ADERDG_NUM_CORR_SHAPES = 9, 5
+ADERDG_NUM_PRED_SHAPES, ADERDG_NUM_CORR_SHAPES = 9, 6
 ADERDG_SHAPE_DEFAULT, ADERDG_SHAPE_AUTOTUNE = 0, -1
 ADERDG_TUNE_FORCE = 1
 ADERDG_GUESS_TRIVIAL, ADERDG_GUESS_ORDER2, ADERDG_GUESS_ORDER3, ADERDG_GUESS_EXTRAP, ADERDG_GUESS_CERK = 0, 1, 2, 3, 4

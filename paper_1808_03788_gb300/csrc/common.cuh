@@ -567,7 +567,7 @@ struct TileShape {
 // Number of compiled shapes of the predictor and the corrector (shape 0 is
 // the default).
 constexpr int NSHAPE_P = 9;
-constexpr int NSHAPE_C = 5;
+constexpr int NSHAPE_C = 6;
 
 // Host-visible description of the compiled kernels of one (PDE, d, N,
 // precision).  predictor/corrector and their sizes are the shapes in use;

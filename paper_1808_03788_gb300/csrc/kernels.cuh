@@ -1064,10 +1064,15 @@ __device__ __forceinline__ void cp_async(void *dst, const void *src, int bytes)
         asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(src));
 }
 
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+
 __device__ __forceinline__ void cp_async_wait_all()
 {
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
+
+// wait for every committed group of this thread's copies but the latest
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
 template <int GRAN>
 __device__ __forceinline__ void stage(void *dst, const void *src, int bytes, int tid, int nthr)
@@ -1098,17 +1103,26 @@ struct CorrCfg {
         align16(OWN) + align16(NB) + (STAGE_UV ? align16(UB) + align16(VB) : 0) + align16(FS);
     // shapes 0, 1, 2, 4: 256-, 128-, 512- and 64-thread CTAs; shape 3: every
     // warp takes one element of the tile on its own (its own shared-memory
-    // slice, warp-level synchronisation only), NW warps per CTA
+    // slice, warp-level synchronisation only), NW warps per CTA; shape 5:
+    // 128-thread CTAs whose tile is SUB consecutive groups of EPB elements,
+    // the next group's inputs staged (double-buffered) while the current
+    // group is computed
     static constexpr bool WM = TS == 3;
-    static constexpr int THREADS_CTA = TS == 1 ? 128 : (TS == 2 ? 512 : (TS == 4 ? 64 : 256));
+    static constexpr int SUB = TS == 5 ? 4 : 1;
+    static constexpr int BUF = SUB > 1 ? 2 : 1;
+    static constexpr int THREADS_CTA = (TS == 1 || TS == 5) ? 128 : (TS == 2 ? 512 : (TS == 4 ? 64 : 256));
     static constexpr int EPB_T = cmax(1, THREADS_CTA / NS);
-    static constexpr int EPB_S = cmax(1, (int)((110 * 1024) / PER_ELEM));
-    static constexpr int EPB = WM ? 1 : cmin(EPB_T, EPB_S);  // elements per shared-memory unit
+    static constexpr size_t STAGED = align16(OWN) + align16(NB) + (STAGE_UV ? align16(UB) + align16(VB) : 0);
+    static constexpr int EPB_S = cmax(1, (int)((110 * 1024) / (PER_ELEM + (BUF - 1) * STAGED)));
+    static constexpr int EPB = WM ? 1 : cmin(EPB_T, EPB_S);  // elements per shared-memory unit (group)
+    // one staging buffer (the group's own records, neighbour chunks, u^n, V);
+    // BUF of them, PB bytes apart
     static constexpr size_t O_OWN = 0;
     static constexpr size_t O_NB = align16(EPB * OWN);
     static constexpr size_t O_U = O_NB + align16(EPB * NB);
     static constexpr size_t O_V = O_U + (STAGE_UV ? align16(EPB * UB) : 0);
-    static constexpr size_t O_FS = O_V + (STAGE_UV ? align16(EPB * VB) : 0);
+    static constexpr size_t PB = O_V + (STAGE_UV ? align16(EPB * VB) : 0);
+    static constexpr size_t O_FS = BUF * PB;
     static constexpr size_t O_LIFT = O_FS + align16(EPB * FS);
     static constexpr size_t O_DEL = O_LIFT + align16(sizeof(T) * 2 * 3 * NMAX);
     static constexpr bool DELTA = sizeof(T) == 4;
@@ -1122,8 +1136,9 @@ struct CorrCfg {
     static constexpr size_t BYTES = O_RED + 64 * sizeof(double) + 16 * sizeof(int);  // one unit (the CTA, or a warp)
     static constexpr int NW = WM ? cmax(1, cmin(8, (int)((200 * 1024) / BYTES))) : 1;
     static constexpr int THREADS = WM ? 32 * NW : THREADS_CTA;
-    static constexpr int EPB_TILE = WM ? NW : EPB;  // elements per tile of the launch
+    static constexpr int EPB_TILE = WM ? NW : EPB * SUB;  // elements per tile of the launch
     static constexpr size_t CTA_BYTES = NW * BYTES;
+    static_assert(CTA_BYTES <= 227 * 1024, "corrector shared memory");
     // copy granules (bytes): the largest of 16/8/4 dividing offsets and sizes
     static constexpr int G_OWN = cgcd((int)OWN, 16);
     static constexpr int G_NB = cgcd((int)(sizeof(T) * RS), 16);
@@ -1182,10 +1197,12 @@ k_corrector(const KParams P)
     };
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char *sb = smem_raw + (C::WM ? wid * C::BYTES : 0);
-    T *sOwn = reinterpret_cast<T *>(sb + C::O_OWN);
-    T *sNb = reinterpret_cast<T *>(sb + C::O_NB);
-    double *sU = reinterpret_cast<double *>(sb + C::O_U);
-    T *sV = reinterpret_cast<T *>(sb + C::O_V);
+    // staging buffer b (BUF of them): the group's own records, neighbour
+    // chunks, u^n and V
+    auto own_of = [&](int b) { return reinterpret_cast<T *>(sb + (size_t)b * C::PB + C::O_OWN); };
+    auto nbr_of = [&](int b) { return reinterpret_cast<T *>(sb + (size_t)b * C::PB + C::O_NB); };
+    auto u_of = [&](int b) { return reinterpret_cast<double *>(sb + (size_t)b * C::PB + C::O_U); };
+    auto v_of = [&](int b) { return reinterpret_cast<T *>(sb + (size_t)b * C::PB + C::O_V); };
     T *sFs = reinterpret_cast<T *>(sb + C::O_FS);
     T *sL = reinterpret_cast<T *>(sb + C::O_LIFT);  // [side][d][k]
     T *sDel = reinterpret_cast<T *>(sb + C::O_DEL);  // [el][d][side][dF | dq][M]
@@ -1225,20 +1242,23 @@ k_corrector(const KParams P)
 
         const int et = (int)((tile - S.tile0_c) * EPT);              // the tile's first element
         const int nt = (S.E - et) < EPT ? (int)(S.E - et) : EPT;     // and its element count
-        const int e0 = C::WM ? et + wid : et;                        // this unit's first element
-        const int ne = C::WM ? (wid < nt ? 1 : 0) : nt;
-        if (C::WM && ne == 0) continue;  // uniform over the warp
+        if (C::WM && wid >= nt) continue;  // uniform over the warp
         const T *tr = reinterpret_cast<const T *>(S.tr);
 
-        // ---- stage everything (one round of loads: the neighbour indices are
-        // ---- formed where they are used, not published through a barrier) --
+        // neighbour (block element, or halo chunk) across face c = (el, d,
+        // side) of the group that starts at element e0g in cell c0: carries
+        // per element from the group's first cell
         const int cx = S.cells[0], cy = S.cells[1], cz = S.cells[2];
-        // the unit's first cell (divisions by multiply-high)
-        const unsigned q0 = fdiv((unsigned)e0, S.div_cx), q1 = fdiv(q0, S.div_cy);
-        const int ix0 = e0 - (int)q0 * cx, iy0 = (int)(q0 - q1 * (unsigned)cy), iz0 = (int)q1;
-        auto nb_of = [&](int c) {
+        struct Cell {
+            int x, y, z;
+        };
+        auto cell_of = [&](int e) {  // by multiply-high divisions
+            const unsigned q0 = fdiv((unsigned)e, S.div_cx), q1 = fdiv(q0, S.div_cy);
+            return Cell{e - (int)q0 * cx, (int)(q0 - q1 * (unsigned)cy), (int)q1};
+        };
+        auto nb_of = [&](int e0g, Cell c0, int c) {
             const int el = c / (2 * DIM), d = (c / 2) % DIM, side = c & 1;
-            int ix = ix0 + el, iy = iy0, iz = iz0;
+            int ix = c0.x + el, iy = c0.y, iz = c0.z;
             while (ix >= cx) {  // el < EPB: a few rows at most
                 ix -= cx;
                 if (++iy == cy) {
@@ -1246,7 +1266,7 @@ k_corrector(const KParams P)
                     ++iz;
                 }
             }
-            return neighbour_or_halo_at(e0 + el, ix, iy, iz, P.solves + si, cx, cy, cz, d, side);
+            return neighbour_or_halo_at(e0g + el, ix, iy, iz, P.solves + si, cx, cy, cz, d, side);
         };
         for (int i = tid; i < DIM * n; i += nthr) {
             const int d = i / n, k = i % n;
@@ -1259,180 +1279,216 @@ k_corrector(const KParams P)
                 sL[(1 * 3 + d) * NMAX + k] = T(idx * P.b.inv_w[k] * P.b.F1[k]);
             }
         }
-        stage<C::G_OWN>(sOwn, tr + (long long)e0 * NREC * RS, ne * (int)C::OWN, tid, nthr);
-        if constexpr (C::STAGE_UV) {
-            stage<C::G_U>(sU, S.u + (long long)e0 * NS * M, ne * (int)C::UB, tid, nthr);
-            stage<C::G_V>(sV, reinterpret_cast<const T *>(S.V) + (long long)e0 * NS * M, ne * (int)C::VB, tid, nthr);
-        }
-        {
-            // the neighbour chunks: tpc consecutive threads per chunk (element,
-            // d, side), which forms its neighbour index once; ng = nthr / tpc
-            // >= nch groups whenever tpc > 1, so every chunk has one group
-            constexpr int units = (int)(sizeof(T) * NF * RS) / C::G_NB;
-            const int nch = ne * 2 * DIM;
-            const int tpc = nthr >= 2 * nch ? nthr / nch : 1;
-            const int ng = nthr / tpc;
-            for (int c = tid / tpc; c < nch && tid < ng * tpc; c += ng) {
-                const int d = (c / 2) % DIM;
-                const int side = c & 1;
-                const int nb = nb_of(c);
-                const T *src = nb >= 0 ? tr + (((long long)nb * DIM + d) * 2 + (1 - side)) * NF * RS
-                                       : reinterpret_cast<const T *>(P.solves[si].halo_tr[d][side]) +
-                                             (long long)(-1 - nb) * NF * RS;
-                unsigned char *dst = reinterpret_cast<unsigned char *>(sNb + (size_t)c * NF * RS);
-                for (int u_ = tid % tpc; u_ < units; u_ += tpc)
-                    cp_async(dst + u_ * C::G_NB, reinterpret_cast<const unsigned char *>(src) + u_ * C::G_NB,
-                             C::G_NB);
-            }
-        }
-        if constexpr (C::DELTA) {
-            // reference differences across every face, sign +1 on the
-            // xi_d = 1 face and -1 on the xi_d = 0 face:  dq = q_ref(nb) -
-            // q_ref(own) formed in FP64 and rounded (it is O(h)), and
-            // dF = F_d(q_ref(nb)) - F_d(q_ref(own)) by the perturbation flux
-            for (int c = tid; c < ne * 2 * DIM; c += nthr) {
-                const int el = c / (2 * DIM), d = (c / 2) % DIM, side = c & 1;
-                const double *ro = S.ref + (long long)(e0 + el) * C::RF;
-                const int nb = nb_of(c);
-                const double *rn = nb >= 0 ? S.ref + (long long)nb * C::RF
-                                           : P.solves[si].halo_ref[d][side] + (long long)(-1 - nb) * C::RF;
-                double qo[M];
-                T dq[M];
-#pragma unroll
-                for (int v = 0; v < M; ++v) {
-                    qo[v] = ro[v];
-                    dq[v] = narrow<T>(rn[v] - qo[v]);
-                }
-                typename PDE::template Ref<T> rr;
-                {
-                    T qf[M];
-#pragma unroll
-                    for (int v = 0; v < M; ++v) qf[v] = narrow<T>(qo[v]);
-                    PDE::make_ref(P.pde, qf, rr);
-                    if constexpr (PDE::NCP) {
-                        if (d == 0 && side == 0) {
-#pragma unroll
-                            for (int v = 0; v < M; ++v) sRefO[el * M + v] = qf[v];
-                        }
-                    }
-                }
-                T dF[DIM][M];
-                PDE::flux_delta(P.pde, rr, dq, dF);
-                const T sg = side ? T(1) : T(-1);
-#pragma unroll
-                for (int v = 0; v < M; ++v) {
-                    T f = dF[0][v];
-#pragma unroll
-                    for (int k = 1; k < DIM; ++k) f = d == k ? dF[k][v] : f;
-                    sDel[(c * 2 + 0) * M + v] = sg * f;
-                    sDel[(c * 2 + 1) * M + v] = sg * dq[v];
-                }
-            }
-        }
-        cp_async_wait_all();
-        usync();
 
-        // ---- Rusanov flux per (element, face record), all variables --------
-        for (int i = tid; i < ne * NREC; i += nthr) {
-            const int el = i / NREC;
-            const int rec = i - el * NREC;
-            const int d = rec / (2 * NF);
-            const int side = (rec / NF) & 1;
-            const int p = rec - (rec / NF) * NF;
-            const T *own = sOwn + (el * NREC + rec) * RS;
-            const T *nb = sNb + ((size_t)(el * DIM + d) * 2 + side) * NF * RS + p * RS;
-            const T *L = side ? own : nb;
-            const T *R = side ? nb : own;
-            const T smax = tmax(L[C::LAM], R[C::LAM]);
-            const T *dl = sDel + ((((el * DIM + d) * 2 + side) * 2) * M);
-            T f[M];
-            if constexpr (PDE::NCP) {
-                // path-conservative Rusanov (eq. pc.scheme, eq. rusanov): the
-                // lower element (side 1) receives -Theta dq/2 + J/2, the upper
-                // one -Theta dq/2 - J/2; Theta = s_max on the evolved variables
-                // only (the material fields obey q_t = 0)
-                T dq[M], qa[M], J[M];
-#pragma unroll
-                for (int v = 0; v < M; ++v) {
-                    dq[v] = R[v] - L[v];
-                    qa[v] = L[v];
-                    if constexpr (C::DELTA) {
-                        // perturbations about each element's own reference
-                        dq[v] += dl[M + v];
-                        qa[v] += sRefO[el * M + v] - (side ? T(0) : dl[M + v]);
-                    }
-                }
-                PDE::path_jump(qa, dq, d, J);
-                const T hs = side ? T(0.5) : T(-0.5);
-#pragma unroll
-                for (int v = 0; v < M; ++v) f[v] = v < PDE::MEV ? hs * J[v] - T(0.5) * smax * dq[v] : T(0);
-            } else {
-#pragma unroll
-                for (int v = 0; v < M; ++v) {
-                    f[v] = T(0.5) * (L[M + v] + R[M + v]) - T(0.5) * smax * (R[v] - L[v]);
-                    if constexpr (C::DELTA) {
-                        // traces are perturbations about each element's own reference:
-                        // add the reference part of the Rusanov flux minus own F_ref
-                        f[v] += (side ? T(0.5) : T(-0.5)) * dl[v] - T(0.5) * smax * dl[M + v];
-                    }
+        // the tile is ngrp groups of EPB elements (one group but for shape 5);
+        // group g is staged into buffer g % BUF, the next one while g is
+        // computed; the staging is one round of loads (the neighbour indices
+        // are formed where they are used, not published through a barrier)
+        const int ngrp = (C::WM || C::SUB == 1) ? 1 : (nt + C::EPB - 1) / C::EPB;
+        auto grp_e0 = [&](int g) { return C::WM ? et + wid : (C::SUB == 1 ? et : et + g * C::EPB); };
+        auto grp_ne = [&](int g) {
+            return C::WM ? 1 : (C::SUB == 1 ? nt : (nt - g * C::EPB < C::EPB ? nt - g * C::EPB : C::EPB));
+        };
+        auto stage_group = [&](int g, int b, const Cell &c0) {  // c0: the group's first cell
+            const int e0 = grp_e0(g), ne = grp_ne(g);
+            T *sNb = nbr_of(b);
+            stage<C::G_OWN>(own_of(b), tr + (long long)e0 * NREC * RS, ne * (int)C::OWN, tid, nthr);
+            if constexpr (C::STAGE_UV) {
+                stage<C::G_U>(u_of(b), S.u + (long long)e0 * NS * M, ne * (int)C::UB, tid, nthr);
+                stage<C::G_V>(v_of(b), reinterpret_cast<const T *>(S.V) + (long long)e0 * NS * M, ne * (int)C::VB,
+                              tid, nthr);
+            }
+            {
+                // the neighbour chunks: tpc consecutive threads per chunk (element,
+                // d, side), which forms its neighbour index once; ng = nthr / tpc
+                // >= nch groups whenever tpc > 1, so every chunk has one group
+                constexpr int units = (int)(sizeof(T) * NF * RS) / C::G_NB;
+                const int nch = ne * 2 * DIM;
+                const int tpc = nthr >= 2 * nch ? nthr / nch : 1;
+                const int ng = nthr / tpc;
+                for (int c = tid / tpc; c < nch && tid < ng * tpc; c += ng) {
+                    const int d = (c / 2) % DIM;
+                    const int side = c & 1;
+                    const int nb = nb_of(e0, c0, c);
+                    const T *src = nb >= 0 ? tr + (((long long)nb * DIM + d) * 2 + (1 - side)) * NF * RS
+                                           : reinterpret_cast<const T *>(P.solves[si].halo_tr[d][side]) +
+                                                 (long long)(-1 - nb) * NF * RS;
+                    unsigned char *dst = reinterpret_cast<unsigned char *>(sNb + (size_t)c * NF * RS);
+                    for (int u_ = tid % tpc; u_ < units; u_ += tpc)
+                        cp_async(dst + u_ * C::G_NB, reinterpret_cast<const unsigned char *>(src) + u_ * C::G_NB,
+                                 C::G_NB);
                 }
             }
-#pragma unroll
-            for (int v = 0; v < M; ++v) sFs[(el * NREC + rec) * M + v] = f[v];
-        }
-        usync();
+        };
 
-        // ---- per node: surface lift, update u^{n+1} = u^n + dt (V - surface),
-        // ---- then the wave speeds of u^{n+1} and the non-finite check -------
-        // (wave speeds in the compute type T; only the per-CTA maxima are widened)
-        double *uo = S.u_out + (long long)e0 * NS * M;
         T lmax[DIM];
 #pragma unroll
         for (int d = 0; d < DIM; ++d) lmax[d] = T(0);
         bool bad = false;
-        for (int i = tid; i < ne * NS; i += nthr) {
-            const int el = i / NS;
-            const int sn = i - el * NS;
-            int kk[DIM], pp[DIM];
-            {
-                int rr = sn;
+        Cell cg = cell_of(grp_e0(0));
+        stage_group(0, 0, cg);
+        if constexpr (C::BUF > 1) cp_async_commit();
+        for (int g = 0; g < ngrp; ++g) {
+            const int b = C::BUF > 1 ? (g & 1) : 0;
+            const Cell c0 = cg;  // this group's first cell
+            if constexpr (C::BUF > 1) {
+                if (g + 1 < ngrp) {
+                    cg = cell_of(grp_e0(g + 1));
+                    stage_group(g + 1, b ^ 1, cg);
+                }
+                cp_async_commit();  // (an empty group when nothing was staged)
+            }
+            const int e0 = grp_e0(g), ne = grp_ne(g);
+            const T *sOwn = own_of(b), *sNb = nbr_of(b);
+            const double *sU = u_of(b);
+            const T *sV = v_of(b);
+            if constexpr (C::DELTA) {
+                // reference differences across every face, sign +1 on the
+                // xi_d = 1 face and -1 on the xi_d = 0 face:  dq = q_ref(nb) -
+                // q_ref(own) formed in FP64 and rounded (it is O(h)), and
+                // dF = F_d(q_ref(nb)) - F_d(q_ref(own)) by the perturbation flux
+                for (int c = tid; c < ne * 2 * DIM; c += nthr) {
+                    const int el = c / (2 * DIM), d = (c / 2) % DIM, side = c & 1;
+                    const double *ro = S.ref + (long long)(e0 + el) * C::RF;
+                    const int nb = nb_of(e0, c0, c);
+                    const double *rn = nb >= 0 ? S.ref + (long long)nb * C::RF
+                                               : P.solves[si].halo_ref[d][side] + (long long)(-1 - nb) * C::RF;
+                    double qo[M];
+                    T dq[M];
 #pragma unroll
-                for (int d = 0; d < DIM; ++d) {
-                    kk[d] = rr % n;
-                    rr /= n;
-                    const int pd = ipow(n, d);
-                    pp[d] = (sn % pd) + (sn / (pd * n)) * pd;
+                    for (int v = 0; v < M; ++v) {
+                        qo[v] = ro[v];
+                        dq[v] = narrow<T>(rn[v] - qo[v]);
+                    }
+                    typename PDE::template Ref<T> rr;
+                    {
+                        T qf[M];
+#pragma unroll
+                        for (int v = 0; v < M; ++v) qf[v] = narrow<T>(qo[v]);
+                        PDE::make_ref(P.pde, qf, rr);
+                        if constexpr (PDE::NCP) {
+                            if (d == 0 && side == 0) {
+#pragma unroll
+                                for (int v = 0; v < M; ++v) sRefO[el * M + v] = qf[v];
+                            }
+                        }
+                    }
+                    T dF[DIM][M];
+                    PDE::flux_delta(P.pde, rr, dq, dF);
+                    const T sg = side ? T(1) : T(-1);
+#pragma unroll
+                    for (int v = 0; v < M; ++v) {
+                        T f = dF[0][v];
+#pragma unroll
+                        for (int k = 1; k < DIM; ++k) f = d == k ? dF[k][v] : f;
+                        sDel[(c * 2 + 0) * M + v] = sg * f;
+                        sDel[(c * 2 + 1) * M + v] = sg * dq[v];
+                    }
                 }
             }
-            double un[M];
-            T vn[M], qs[M];
-            if constexpr (C::STAGE_UV) {
-                NodeIO<double, M>::load(sU + i * M, un);
-                NodeIO<T, M>::load(sV + i * M, vn);
-            } else {
-                NodeIO<double, M>::load(S.u + ((long long)e0 * NS + i) * M, un);
-                NodeIO<T, M>::load(reinterpret_cast<const T *>(S.V) + ((long long)e0 * NS + i) * M, vn);
-            }
+            if constexpr (C::BUF > 1) cp_async_wait_prev();  // this group's copies (all but the latest group)
+            else cp_async_wait_all();
+            usync();
+
+            // ---- Rusanov flux per (element, face record), all variables --------
+            for (int i = tid; i < ne * NREC; i += nthr) {
+                const int el = i / NREC;
+                const int rec = i - el * NREC;
+                const int d = rec / (2 * NF);
+                const int side = (rec / NF) & 1;
+                const int p = rec - (rec / NF) * NF;
+                const T *own = sOwn + (el * NREC + rec) * RS;
+                const T *nb = sNb + ((size_t)(el * DIM + d) * 2 + side) * NF * RS + p * RS;
+                const T *L = side ? own : nb;
+                const T *R = side ? nb : own;
+                const T smax = tmax(L[C::LAM], R[C::LAM]);
+                const T *dl = sDel + ((((el * DIM + d) * 2 + side) * 2) * M);
+                T f[M];
+                if constexpr (PDE::NCP) {
+                    // path-conservative Rusanov (eq. pc.scheme, eq. rusanov): the
+                    // lower element (side 1) receives -Theta dq/2 + J/2, the upper
+                    // one -Theta dq/2 - J/2; Theta = s_max on the evolved variables
+                    // only (the material fields obey q_t = 0)
+                    T dq[M], qa[M], J[M];
 #pragma unroll
-            for (int v = 0; v < M; ++v) {
-                T surf = T(0);
+                    for (int v = 0; v < M; ++v) {
+                        dq[v] = R[v] - L[v];
+                        qa[v] = L[v];
+                        if constexpr (C::DELTA) {
+                            // perturbations about each element's own reference
+                            dq[v] += dl[M + v];
+                            qa[v] += sRefO[el * M + v] - (side ? T(0) : dl[M + v]);
+                        }
+                    }
+                    PDE::path_jump(qa, dq, d, J);
+                    const T hs = side ? T(0.5) : T(-0.5);
+#pragma unroll
+                    for (int v = 0; v < M; ++v) f[v] = v < PDE::MEV ? hs * J[v] - T(0.5) * smax * dq[v] : T(0);
+                } else {
+#pragma unroll
+                    for (int v = 0; v < M; ++v) {
+                        f[v] = T(0.5) * (L[M + v] + R[M + v]) - T(0.5) * smax * (R[v] - L[v]);
+                        if constexpr (C::DELTA) {
+                            // traces are perturbations about each element's own reference:
+                            // add the reference part of the Rusanov flux minus own F_ref
+                            f[v] += (side ? T(0.5) : T(-0.5)) * dl[v] - T(0.5) * smax * dl[M + v];
+                        }
+                    }
+                }
+#pragma unroll
+                for (int v = 0; v < M; ++v) sFs[(el * NREC + rec) * M + v] = f[v];
+            }
+            usync();
+
+            // ---- per node: surface lift, update u^{n+1} = u^n + dt (V - surface),
+            // ---- then the wave speeds of u^{n+1} and the non-finite check -------
+            // (wave speeds in the compute type T; only the per-CTA maxima are widened)
+            double *uo = S.u_out + (long long)e0 * NS * M;
+            for (int i = tid; i < ne * NS; i += nthr) {
+                const int el = i / NS;
+                const int sn = i - el * NS;
+                int kk[DIM], pp[DIM];
+                {
+                    int rr = sn;
+#pragma unroll
+                    for (int d = 0; d < DIM; ++d) {
+                        kk[d] = rr % n;
+                        rr /= n;
+                        const int pd = ipow(n, d);
+                        pp[d] = (sn % pd) + (sn / (pd * n)) * pd;
+                    }
+                }
+                double un[M];
+                T vn[M], qs[M];
+                if constexpr (C::STAGE_UV) {
+                    NodeIO<double, M>::load(sU + i * M, un);
+                    NodeIO<T, M>::load(sV + i * M, vn);
+                } else {
+                    NodeIO<double, M>::load(S.u + ((long long)e0 * NS + i) * M, un);
+                    NodeIO<T, M>::load(reinterpret_cast<const T *>(S.V) + ((long long)e0 * NS + i) * M, vn);
+                }
+#pragma unroll
+                for (int v = 0; v < M; ++v) {
+                    T surf = T(0);
+#pragma unroll
+                    for (int d = 0; d < DIM; ++d) {
+                        const T fp = sFs[(el * NREC + (d * 2 + 1) * NF + pp[d]) * M + v];
+                        const T fm = sFs[(el * NREC + (d * 2 + 0) * NF + pp[d]) * M + v];
+                        surf += sL[(3 + d) * NMAX + kk[d]] * fp - sL[d * NMAX + kk[d]] * fm;
+                    }
+                    un[v] = un[v] + dt * widen<T>(vn[v] - surf);
+                    bad |= dbl_nonfinite(un[v]);
+                    qs[v] = narrow<T>(un[v]);
+                }
+                NodeIO<double, M>::store(uo + i * M, un);
 #pragma unroll
                 for (int d = 0; d < DIM; ++d) {
-                    const T fp = sFs[(el * NREC + (d * 2 + 1) * NF + pp[d]) * M + v];
-                    const T fm = sFs[(el * NREC + (d * 2 + 0) * NF + pp[d]) * M + v];
-                    surf += sL[(3 + d) * NMAX + kk[d]] * fp - sL[d * NMAX + kk[d]] * fm;
+                    const T lam = PDE::max_eig(P.pde, qs, d);
+                    bad |= !(lam >= T(0));
+                    lmax[d] = lam > lmax[d] ? lam : lmax[d];
                 }
-                un[v] = un[v] + dt * widen<T>(vn[v] - surf);
-                bad |= dbl_nonfinite(un[v]);
-                qs[v] = narrow<T>(un[v]);
             }
-            NodeIO<double, M>::store(uo + i * M, un);
-#pragma unroll
-            for (int d = 0; d < DIM; ++d) {
-                const T lam = PDE::max_eig(P.pde, qs, d);
-                bad |= !(lam >= T(0));
-                lmax[d] = lam > lmax[d] ? lam : lmax[d];
-            }
+            if (g + 1 < ngrp) usync();  // buffer b, the face fluxes and the reference differences are reused
         }
         if constexpr (C::WM) {
             if (S.ctl != acc_ctl) {  // warp-uniform: a new solve
@@ -1617,7 +1673,7 @@ const KernelSet KS<PDE, DIM, N, T>::value = {
      pred_shape<PDE, DIM, N, T, 6, true>(), pred_shape<PDE, DIM, N, T, 7, true>(),
      pred_shape<PDE, DIM, N, T, 8, true>()},
     {corr_shape<PDE, DIM, N, T, 0>(), corr_shape<PDE, DIM, N, T, 1>(), corr_shape<PDE, DIM, N, T, 2>(),
-     corr_shape<PDE, DIM, N, T, 3>(), corr_shape<PDE, DIM, N, T, 4>()},
+     corr_shape<PDE, DIM, N, T, 3>(), corr_shape<PDE, DIM, N, T, 4>(), corr_shape<PDE, DIM, N, T, 5>()},
     0, 0};
 
 }  // namespace aderdg
