@@ -62,6 +62,28 @@ def test_partitioned_equals_single_domain_bitwise(case, precision):
     np.testing.assert_array_equal(U2, U1)
 
 
+@pytest.mark.parametrize("precision", [A.ADERDG_FP64, A.ADERDG_MIXED_FP32], ids=["fp64", "mixed"])
+@pytest.mark.parametrize("shapes", [(1, 5), (0, 4), (0, 3)])
+def test_partitioned_corrector_shapes_read_the_halos(shapes, precision):
+    """Every corrector shape reads the neighbouring blocks' traces and (FP32
+    path) reference states from the halos: the pipelined shape 5 stages them
+    with the next group of elements.  Bitwise the undivided mesh's result."""
+    for case in (CASES[0], CASES[4]):
+        pde, dim, cells, L, N, params, parts = case
+        lo, hi = (0.0,) * dim, (L,) * dim
+        cfg = oracle.make_cfg(dim, cells, lo, hi, N, pde, params)
+        U0 = _ic(pde, dim, oracle.node_coords(cfg), L)
+        out = []
+        for cls, extra in ((A.Solver, {}), (A.Partitioned, {"parts": parts, "shapes": shapes})):
+            with cls(pde, dim, cells, lo, hi, N, params, precision=precision, **extra) as s:
+                s.set_state(U0)
+                s.advance(1e30, max_steps=6)
+                out.append(s.get_state())
+        (U1, t1, k1), (U2, t2, k2) = out
+        assert (t1, k1) == (t2, k2)
+        np.testing.assert_array_equal(U2, U1)
+
+
 def test_partitioned_matches_the_oracle():
     pde, dim, cells, L, N, params, parts = CASES[0]
     cfg, U0, (_, (Ug, t, k)) = _pair_run(pde, dim, cells, L, N, params, parts, 8)
