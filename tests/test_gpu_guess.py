@@ -272,8 +272,9 @@ def test_cerk_guess_plane_kernel(shapes):
 @pytest.mark.parametrize("guess", [A.ADERDG_GUESS_ORDER3, A.ADERDG_GUESS_EXTRAP, A.ADERDG_GUESS_CERK])
 def test_batch_with_guess_equals_alone(guess):
     mix = [(2, 2, (6, 5), (0, 0), (10, 10), 2, (GAMMA,)), (2, 2, (8, 8), (0, 0), (10, 10), 4, (GAMMA,)),
-           (3, 3, (3, 3, 2), (0, 0, 0), (1, 1, 1), 3, EL)]
-    t_end = [0.3, 0.2, 0.02]
+           (3, 3, (3, 3, 2), (0, 0, 0), (1, 1, 1), 3, EL),
+           (2, 2, (5, 4), (0, 0), (10, 10), 5, (GAMMA,))]  # N = 5: the six-stage CERK scheme
+    t_end = [0.3, 0.2, 0.02, 0.15]
     ics = []
     for c in mix:
         X = oracle.node_coords(oracle.make_cfg(c[1], c[2], c[3], c[4], c[5], c[0], c[6]))
