@@ -112,6 +112,13 @@ def lib():
             L.orc_cerk_scheme.restype = C.c_int
             L.orc_step_limited.argtypes = [cp, dp, C.c_double, C.POINTER(C.c_int), C.POINTER(C.c_long)]
             L.orc_subcell_ops.argtypes = [C.c_int, dp, dp]
+            ip = C.POINTER(C.c_int)
+            L.orc_step_limited_kept.argtypes = [cp, dp, dp, ip, C.c_double, ip, C.POINTER(C.c_long)]
+            L.orc_cfl_dt_kept.argtypes = [cp, dp, dp, ip]
+            L.orc_cfl_dt_kept.restype = C.c_double
+            L.orc_subcell_init.argtypes = [cp, dp, dp]
+            L.orc_run_kept.argtypes = [cp, dp, dp, ip, C.c_double, C.c_double, C.c_long, dp,
+                                       C.POINTER(C.c_long), dp]
             L.orc_cfl_dt.argtypes = [cp, dp]
             L.orc_cfl_dt.restype = C.c_double
             L.orc_step_ex.argtypes = [cp, dp, C.c_double, dp, dp, dp]
@@ -374,6 +381,69 @@ def step_limited(cfg: Cfg, U: np.ndarray, dt: float):
     if rc:
         raise RuntimeError("orc_step_limited failed: %d" % rc)
     return out, flags, cnt.value
+
+
+class Kept:
+    """The limiter's kept subcell data (R35, limiter mode 2): sub[E, (2N+1)^d,
+    m], the subcell averages of the elements the last step limited, and
+    kept[E], set for those elements."""
+
+    def __init__(self, cfg: Cfg, sub=None, kept=None):
+        E, nsub = n_elems(cfg), (2 * cfg.N + 1) ** cfg.dim
+        self.sub = np.zeros((E, nsub, cfg.m)) if sub is None else np.array(sub, dtype=np.float64, order="C")
+        self.kept = np.zeros(E, dtype=np.int32) if kept is None else np.array(kept, dtype=np.int32, order="C")
+        assert self.sub.size == E * nsub * cfg.m and self.kept.size == E
+
+    def _k(self):
+        return self.kept.ctypes.data_as(C.POINTER(C.c_int))
+
+
+def subcell_init(cfg: Cfg, avg: np.ndarray):
+    """R35: a state given as the subcell averages avg[E, (2N+1)^d, m] of every
+    element: (U, Kept) with U their least-squares reconstruction (R28) and
+    every element carrying avg."""
+    avg = np.ascontiguousarray(avg, dtype=np.float64)
+    E, ns = n_elems(cfg), (cfg.N + 1) ** cfg.dim
+    U = np.zeros((E, ns, cfg.m))
+    if lib().orc_subcell_init(C.byref(cfg), _p(avg), _p(U)):
+        raise RuntimeError("orc_subcell_init failed")
+    return U, Kept(cfg, avg, np.ones(E, dtype=np.int32))
+
+
+def step_limited_kept(cfg: Cfg, U: np.ndarray, kept: Kept, dt: float):
+    """One step with the subcell limiter keeping the limited elements'
+    subcell data (R35): (u^{n+1}, troubled flags, count); kept is updated in
+    place."""
+    out = np.array(U, dtype=np.float64, copy=True, order="C")
+    flags = np.zeros(n_elems(cfg), dtype=np.int32)
+    cnt = C.c_long(0)
+    rc = lib().orc_step_limited_kept(C.byref(cfg), _p(out), _p(kept.sub), kept._k(), float(dt),
+                                     flags.ctypes.data_as(C.POINTER(C.c_int)), C.byref(cnt))
+    if rc:
+        raise RuntimeError("orc_step_limited_kept failed: %d" % rc)
+    return out, flags, cnt.value
+
+
+def cfl_dt_kept(cfg: Cfg, U: np.ndarray, kept: Kept) -> float:
+    """The CFL step with the kept elements' wave speeds from their subcell
+    averages (R35)."""
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    return lib().orc_cfl_dt_kept(C.byref(cfg), _p(U), _p(kept.sub), kept._k())
+
+
+def run_kept(cfg: Cfg, U: np.ndarray, kept: Kept, t_end: float, t0: float = 0.0, max_steps: int = 10**9):
+    """CFL time loop to t_end with the kept subcell data of R35 (updated in
+    place).  Returns (U, t, steps, dt_history)."""
+    out = np.array(U, dtype=np.float64, copy=True, order="C")
+    hist_len = int(min(max_steps, 10**6))
+    hist = np.zeros(hist_len)
+    t = C.c_double(0.0)
+    k = C.c_long(0)
+    rc = lib().orc_run_kept(C.byref(cfg), _p(out), _p(kept.sub), kept._k(), float(t0), float(t_end),
+                            int(hist_len), C.byref(t), C.byref(k), _p(hist))
+    if rc:
+        raise RuntimeError("orc_run_kept failed: %d" % rc)
+    return out, t.value, k.value, hist[: k.value].copy()
 
 
 def detect(cfg: Cfg, U0: np.ndarray, U: np.ndarray):

@@ -129,7 +129,8 @@ typedef struct {
                          4 continuous Runge-Kutta (CERK) dense output, a
                            polynomial of degree max(3, N - 1) in time */
     int limiter;      /* 1: a posteriori subcell finite-volume limiter
-                         (Sec. 2.3) after every step */
+                         (Sec. 2.3) after every step; 2: the same with the
+                         limited elements' subcell averages kept (R35) */
 } orc_cfg;
 
 /* ------------------------------------------------------------------------ */
@@ -1110,10 +1111,26 @@ double orc_cfl_dt(const orc_cfg *c, const double *U)
     return orc_alpha(c) / S;
 }
 
+/* Subcell data of element e at t^n (eq. subcellaverage): the averages of
+ * its nodal state U0, or (R35) the subcell averages it kept from the step
+ * that limited it, sub[e] ([nsub][m]), where kept[e] is set.  sub and kept
+ * may be NULL (nothing kept). */
+static void un_averages(const orc_cfg *c, const subcell_ops *o, const double *U0, const double *sub,
+                        const int *kept, long e, double *avg)
+{
+    const int ns = ipow(o->n, c->dim), nsub = ipow(o->S, c->dim), m = c->m;
+    if (sub && kept && kept[e])
+        memcpy(avg, &sub[(size_t)e * nsub * m], sizeof(double) * (size_t)nsub * m);
+    else
+        subcell_averages(c, o, &U0[(size_t)e * ns * m], avg);
+}
+
 /* Steps 1 and 2 of the limiter (R25): extreme subcell averages of the
- * state U0 at t^n per element and variable, then the troubled elements of
- * the candidate U -> bad[e].  Returns their number, or < 0 on failure. */
-static long detect_troubled(const orc_cfg *c, const subcell_ops *so, const double *U0, const double *U, int *bad)
+ * state U0 at t^n per element and variable (with the kept data of R35
+ * where sub / kept give them), then the troubled elements of the candidate
+ * U -> bad[e].  Returns their number, or < 0 on failure. */
+static long detect_troubled(const orc_cfg *c, const subcell_ops *so, const double *U0, const double *sub,
+                            const int *kept, const double *U, int *bad)
 {
     const subcell_ops o = *so;
     const int n = o.n, dim = c->dim, m = c->m;
@@ -1129,7 +1146,7 @@ static long detect_troubled(const orc_cfg *c, const subcell_ops *so, const doubl
         double *avg = malloc(sizeof(double) * (size_t)nsub * m);
 #pragma omp for schedule(static)
         for (long e = 0; e < E; ++e) {
-            subcell_averages(c, &o, &U0[(size_t)e * ns * m], avg);
+            un_averages(c, &o, U0, sub, kept, e, avg);
             for (int v = 0; v < m; ++v) {
                 double lo = avg[v], hi = avg[v];
                 for (int a = 1; a < nsub; ++a) {
@@ -1191,7 +1208,7 @@ static long detect_troubled(const orc_cfg *c, const subcell_ops *so, const doubl
  *      the common face replaced by the projected subcell fluxes (R27).
  * Returns the number of troubled elements, or < 0 on failure. */
 static long apply_limiter(const orc_cfg *c, const basis *b, const double *U0, double *U, const double *qf,
-                          const double *ff, double dt, int *troubled)
+                          const double *ff, double dt, int *troubled, double *sub, int *kept)
 {
     subcell_ops o;
     if (make_subcell_ops(b, &o)) return -1;
@@ -1205,9 +1222,12 @@ static long apply_limiter(const orc_cfg *c, const basis *b, const double *U0, do
     /* [e][d][side][line][2m]: the boundary fluctuation a face neighbour
      * receives, then that neighbour's own subcell state at the face */
     double *Fb = malloc(sizeof(double) * (size_t)E * dim * 2 * nline * 2 * m);
-    if (!bad || !Unew || !Fb) { free(bad); free(Unew); free(Fb); return -2; }
-    const long count = detect_troubled(c, &o, U0, U, bad);
-    if (count < 0) { free(bad); free(Unew); free(Fb); return count; }
+    /* R35: the troubled elements' new subcell averages, kept for the next
+     * step (written to sub once every element has read its u^n data) */
+    double *Snew = sub ? malloc(sizeof(double) * (size_t)E * nsub * m) : NULL;
+    if (!bad || !Unew || !Fb || (sub && !Snew)) { free(bad); free(Unew); free(Fb); free(Snew); return -2; }
+    const long count = detect_troubled(c, &o, U0, sub, kept, U, bad);
+    if (count < 0) { free(bad); free(Unew); free(Fb); free(Snew); return count; }
 
     /* 3. subcell finite-volume step of the troubled elements */
 #pragma omp parallel
@@ -1219,11 +1239,11 @@ static long apply_limiter(const orc_cfg *c, const basis *b, const double *U0, do
         for (long e = 0; e < E; ++e) {
             if (!bad[e]) continue;
             /* slot 0: e; 1 + 2d + (0|1): the neighbour -1 / +1 along d */
-            subcell_averages(c, &o, &U0[(size_t)e * ns * m], avg);
+            un_averages(c, &o, U0, sub, kept, e, avg);
             for (int d = 0; d < dim; ++d)
                 for (int sd = 0; sd < 2; ++sd)
-                    subcell_averages(c, &o, &U0[(size_t)neighbour(c, e, d, sd ? 1 : -1) * ns * m],
-                                     &avg[(size_t)(1 + 2 * d + sd) * nsub * m]);
+                    un_averages(c, &o, U0, sub, kept, neighbour(c, e, d, sd ? 1 : -1),
+                                &avg[(size_t)(1 + 2 * d + sd) * nsub * m]);
             for (size_t i = 0; i < (size_t)nsub * m; ++i) dq[i] = ctr[i] = 0.0;
             for (int d = 0; d < dim; ++d) {
                 const double h = cell_dx(c, d) / S, r = dt / h;
@@ -1319,6 +1339,7 @@ static long apply_limiter(const orc_cfg *c, const basis *b, const double *U0, do
                 }
             }
             for (size_t i = 0; i < (size_t)nsub * m; ++i) dq[i] += avg[i];
+            if (Snew) memcpy(&Snew[(size_t)e * nsub * m], dq, sizeof(double) * (size_t)nsub * m);
             subcell_reconstruct(c, &o, dq, &Unew[(size_t)e * ns * m]);
             /* the material fields obey q_t = 0: kept as they were */
             for (int s2 = 0; s2 < ns; ++s2)
@@ -1389,8 +1410,10 @@ static long apply_limiter(const orc_cfg *c, const basis *b, const double *U0, do
     for (long e = 0; e < E; ++e) {
         if (bad[e]) memcpy(&U[(size_t)e * ns * m], &Unew[(size_t)e * ns * m], sizeof(double) * ns * m);
         if (troubled) troubled[e] = bad[e];
+        if (Snew && bad[e]) memcpy(&sub[(size_t)e * nsub * m], &Snew[(size_t)e * nsub * m], sizeof(double) * nsub * m);
+        if (kept) kept[e] = bad[e];
     }
-    free(bad); free(Unew); free(Fb);
+    free(bad); free(Unew); free(Fb); free(Snew);
     return count;
 }
 
@@ -1407,7 +1430,7 @@ typedef struct {
 } history;
 
 static int step_impl(const orc_cfg *c, double *U, double dt, double *V_out, double *qf_out, double *ff_out,
-                     history *h, int *troubled, long *ntroubled)
+                     history *h, int *troubled, long *ntroubled, double *sub, int *kept)
 {
     basis b;
     if (make_basis(c->N, &b)) return -1;
@@ -1479,7 +1502,7 @@ static int step_impl(const orc_cfg *c, double *U, double dt, double *V_out, doub
             }
     }
     if (c->limiter) {
-        const long cnt = apply_limiter(c, &b, U0, U, qf, ff, dt, troubled);
+        const long cnt = apply_limiter(c, &b, U0, U, qf, ff, dt, troubled, sub, kept);
         if (cnt < 0) err = (int)cnt;
         if (ntroubled) *ntroubled = cnt;
     }
@@ -1492,7 +1515,7 @@ static int step_impl(const orc_cfg *c, double *U, double dt, double *V_out, doub
 
 int orc_step_ex(const orc_cfg *c, double *U, double dt, double *V_out, double *qf_out, double *ff_out)
 {
-    return step_impl(c, U, dt, V_out, qf_out, ff_out, NULL, NULL, NULL);
+    return step_impl(c, U, dt, V_out, qf_out, ff_out, NULL, NULL, NULL, NULL, NULL);
 }
 
 int orc_step(const orc_cfg *c, double *U, double dt) { return orc_step_ex(c, U, dt, NULL, NULL, NULL); }
@@ -1505,20 +1528,68 @@ long orc_detect(const orc_cfg *c, const double *U0, const double *U, int *troubl
     basis b;
     subcell_ops o;
     if (make_basis(c->N, &b) || make_subcell_ops(&b, &o)) return -1;
-    return detect_troubled(c, &o, U0, U, troubled);
+    return detect_troubled(c, &o, U0, NULL, NULL, U, troubled);
 }
 
 int orc_step_limited(const orc_cfg *c, double *U, double dt, int *troubled, long *ntroubled)
 {
-    return step_impl(c, U, dt, NULL, NULL, NULL, NULL, troubled, ntroubled);
+    return step_impl(c, U, dt, NULL, NULL, NULL, NULL, troubled, ntroubled, NULL, NULL);
+}
+
+/* R35, kept subcell data: one limited step in which an element with
+ * kept[e] set takes sub[e] ([E][(2N+1)^d][m]) as its subcell data at t^n.
+ * On return the troubled elements' new subcell averages are in sub and
+ * kept[e] = troubled[e] (both arrays in and out). */
+int orc_step_limited_kept(const orc_cfg *c, double *U, double *sub, int *kept, double dt, int *troubled,
+                          long *ntroubled)
+{
+    if (!c->limiter || !sub || !kept) return -1;
+    return step_impl(c, U, dt, NULL, NULL, NULL, NULL, troubled, ntroubled, sub, kept);
+}
+
+/* R35: the CFL step of a state whose elements with kept[e] set are limited
+ * ones: their wave speeds are those of their subcell averages sub[e], not
+ * of the nodes of the reconstructed polynomial. */
+double orc_cfl_dt_kept(const orc_cfg *c, const double *U, const double *sub, const int *kept)
+{
+    const long E = n_elems(c);
+    const int ns = ipow(c->N + 1, c->dim), nsub = ipow(2 * c->N + 1, c->dim), m = c->m;
+    double S = 0.0;
+    for (int d = 0; d < c->dim; ++d) {
+        double mx = 0.0;
+        for (long e = 0; e < E; ++e) {
+            const int kept_e = kept && kept[e];
+            const double *q = kept_e ? &sub[(size_t)e * nsub * m] : &U[(size_t)e * ns * m];
+            for (int i = 0; i < (kept_e ? nsub : ns); ++i) {
+                const double l = orc_max_eig(c, &q[(size_t)i * m], d);
+                if (l > mx) mx = l;
+            }
+        }
+        S += mx / cell_dx(c, d);
+    }
+    return orc_alpha(c) / S;
+}
+
+/* R35: a state given by the subcell averages avg of every element
+ * ([E][(2N+1)^d][m]): U = their least-squares reconstruction (R28),
+ * element by element. */
+int orc_subcell_init(const orc_cfg *c, const double *avg, double *U)
+{
+    basis b;
+    subcell_ops o;
+    if (make_basis(c->N, &b) || make_subcell_ops(&b, &o)) return -1;
+    const long E = n_elems(c);
+    const int ns = ipow(o.n, c->dim), nsub = ipow(o.S, c->dim), m = c->m;
+    for (long e = 0; e < E; ++e) subcell_reconstruct(c, &o, &avg[(size_t)e * nsub * m], &U[(size_t)e * ns * m]);
+    return 0;
 }
 
 /* Time loop with the CFL step and the clip to t_end:
  *   dtc = orc_cfl_dt(U);  if t + dtc >= t_end: dt = t_end - t, t = t_end
  *   else dt = dtc, t = t + dt.
  * dt_hist (nullable, length >= max_steps) receives each dt. */
-int orc_run(const orc_cfg *c, double *U, double t0, double t_end, long max_steps,
-            double *t_out, long *steps_out, double *dt_hist)
+static int run_impl(const orc_cfg *c, double *U, double *sub, int *kept, double t0, double t_end, long max_steps,
+                    double *t_out, long *steps_out, double *dt_hist)
 {
     double t = t0;
     long k = 0;
@@ -1531,11 +1602,11 @@ int orc_run(const orc_cfg *c, double *U, double t0, double t_end, long max_steps
         h = &hist;
     }
     while (t < t_end && k < max_steps) {
-        double dtc = orc_cfl_dt(c, U);
+        double dtc = sub ? orc_cfl_dt_kept(c, U, sub, kept) : orc_cfl_dt(c, U);
         double dt, tn;
         if (t + dtc >= t_end) { dt = t_end - t; tn = t_end; }
         else { dt = dtc; tn = t + dtc; }
-        int rc = step_impl(c, U, dt, NULL, NULL, NULL, h, NULL, NULL);
+        int rc = step_impl(c, U, dt, NULL, NULL, NULL, h, NULL, NULL, sub, kept);
         if (rc) { if (h) { free(hist.prev); free(hist.next); } return rc; }
         if (h) {
             double *tmp = hist.prev; hist.prev = hist.next; hist.next = tmp;
@@ -1550,6 +1621,29 @@ int orc_run(const orc_cfg *c, double *U, double t0, double t_end, long max_steps
     if (t_out) *t_out = t;
     if (steps_out) *steps_out = k;
     return 0;
+}
+
+int orc_run(const orc_cfg *c, double *U, double t0, double t_end, long max_steps,
+            double *t_out, long *steps_out, double *dt_hist)
+{
+    if (c->limiter != 2) return run_impl(c, U, NULL, NULL, t0, t_end, max_steps, t_out, steps_out, dt_hist);
+    /* R35 from a nodal state: nothing kept at t0 */
+    const long E = n_elems(c);
+    double *sub = malloc(sizeof(double) * (size_t)E * ipow(2 * c->N + 1, c->dim) * c->m);
+    int *kept = calloc((size_t)E, sizeof(int));
+    if (!sub || !kept) { free(sub); free(kept); return -2; }
+    const int rc = run_impl(c, U, sub, kept, t0, t_end, max_steps, t_out, steps_out, dt_hist);
+    free(sub); free(kept);
+    return rc;
+}
+
+/* orc_run with the kept subcell data of R35 carried in and out (sub, kept
+ * as for orc_step_limited_kept). */
+int orc_run_kept(const orc_cfg *c, double *U, double *sub, int *kept, double t0, double t_end, long max_steps,
+                 double *t_out, long *steps_out, double *dt_hist)
+{
+    if (c->limiter != 2 || !sub || !kept) return -1;
+    return run_impl(c, U, sub, kept, t0, t_end, max_steps, t_out, steps_out, dt_hist);
 }
 
 /* Sampled step: u^{n+1} of the listed elements only (each needs the

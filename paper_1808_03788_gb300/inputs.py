@@ -23,6 +23,10 @@ Fields (X has shape [E, n^d, dim]; results are [E, n^d, m], v fastest):
                           interface profile of the volume fraction or a material
 * ``diffuse_terrain``     3D diffuse-interface workload: solid below a synthetic
                           sinusoidal topography, vacuum above, a velocity pulse
+* ``subcell_means``       a field averaged over the (2N+1)^d equal subcells of
+                          every element (midpoint samples), [E, (2N+1)^d, m]
+* ``euler_sharp_blast``   a discontinuous Euler state at rest (rho, p inside a
+                          ball against outside), for ``subcell_means``
 """
 from __future__ import annotations
 
@@ -313,3 +317,48 @@ def elastic_pulse_torch(X, x0=(0.5, 0.5, 0.5), width=0.01):
     out[..., 7] = g
     out[..., 8] = g
     return out
+
+
+def subcell_means(field, cells, lo, hi, N: int, k: int = 8) -> np.ndarray:
+    """Means of field over the (2N+1)^d equal subcells of every element of
+    the Cartesian mesh (cells, lo, hi), each estimated on k^d midpoint
+    samples: [E, (2N+1)^d, m], subcells x fastest, elements x fastest.
+    field maps coordinates [..., dim] to states [..., m].  This is initial
+    data given as subcell averages (a discontinuous field has no admissible
+    nodal interpolant); the sampling is part of the data's definition."""
+    dim = len(cells)
+    S = 2 * N + 1
+    axes = []
+    for d in range(dim):
+        h = (hi[d] - lo[d]) / (cells[d] * S)
+        fine = np.arange(cells[d] * S)
+        axes.append(lo[d] + (fine[:, None] + (np.arange(k) + 0.5)[None, :] / k) * h)  # [fine, sample]
+    # sample points on the fine grid, reversed axis order (z, y, x) so x is fastest
+    grids = np.meshgrid(*[axes[d].reshape(-1) for d in reversed(range(dim))], indexing="ij")
+    X = np.stack(list(reversed(grids)), axis=-1)
+    F = np.asarray(field(X), dtype=np.float64)
+    m = F.shape[-1]
+    shape = []
+    for d in reversed(range(dim)):
+        shape += [cells[d] * S, k]
+    F = F.reshape(shape + [m]).mean(axis=tuple(range(1, 2 * dim, 2)))  # [fine_z, fine_y, fine_x, m]
+    split = []
+    for d in reversed(range(dim)):
+        split += [cells[d], S]
+    F = F.reshape(split + [m])  # [cz, Sz, cy, Sy, cx, Sx, m]
+    order = list(range(0, 2 * dim, 2)) + list(range(1, 2 * dim, 2)) + [2 * dim]
+    E = int(np.prod(cells))
+    return np.ascontiguousarray(F.transpose(order).reshape(E, S ** dim, m))
+
+
+def euler_sharp_blast(center, radius, inside=(1.0, 1.0), outside=(0.125, 0.1), gamma=1.4):
+    """field(X) of an Euler state at rest, (rho, p) = inside for
+    |x - center| < radius and outside elsewhere, in conserved variables."""
+    def field(X):
+        dim = X.shape[-1]
+        r = np.sqrt(sum((X[..., d] - center[d]) ** 2 for d in range(dim)))
+        inn = r < radius
+        rho = np.where(inn, inside[0], outside[0])
+        p = np.where(inn, inside[1], outside[1])
+        return _euler_conserved(rho, [np.zeros_like(rho)] * dim, p, gamma)
+    return field

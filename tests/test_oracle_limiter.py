@@ -325,3 +325,169 @@ def test_detection_flags_non_finite_and_negative_pressure():
     assert cnt == 1 and flags[k] == 1
     U[k, :, 3] = 10.0  # the same momentum with enough energy: admissible, within bounds
     assert oracle.detect(c, U0, U)[1] == 0
+
+
+# ---------------------------------------------------------------------------
+# Kept subcell data (limiter mode 2, R35): a limited element keeps the subcell
+# averages its subcell scheme produced as its subcell data at t^n, and an
+# initial state can be given as subcell averages.
+
+
+def _mono_avg(a, b, p):
+    """Mean of x^p over [a, b]."""
+    return (b ** (p + 1) - a ** (p + 1)) / ((p + 1) * (b - a))
+
+
+@pytest.mark.parametrize("dim,N,cells", [(2, 3, (3, 2)), (3, 2, (2, 2, 3))])
+def test_subcell_init_reconstructs_polynomials(dim, N, cells):
+    """Subcell averages of a polynomial of degree <= N per direction, in
+    closed form (monomial means over each subcell), give back that
+    polynomial at the nodes: the least-squares reconstruction is exact on
+    the DG space, in every direction and variable."""
+    hi = [1.0, 1.5, 0.7][:dim]
+    c = oracle.make_cfg(dim, cells, [0.0] * dim, hi, N, oracle.PDE_EULER, [1.4], limiter=2)
+    m, S = c.m, 2 * N + 1
+    rng = np.random.default_rng(35)
+    expo = rng.integers(0, N + 1, size=(m, 4, dim))  # four monomials per variable
+    coef = rng.normal(size=(m, 4))
+    X = oracle.node_coords(c)
+    want = np.zeros(X.shape[:-1] + (m,))
+    for v in range(m):
+        for t in range(4):
+            want[..., v] += coef[v, t] * np.prod([X[..., d] ** expo[v, t, d] for d in range(dim)], axis=0)
+    E = int(np.prod(cells))
+    avg = np.zeros((E, S ** dim, m))
+    for e in range(E):
+        ie, r = [], e
+        for d in range(dim):
+            ie.append(r % cells[d]); r //= cells[d]
+        for a in range(S ** dim):
+            ia, r = [], a
+            for d in range(dim):
+                ia.append(r % S); r //= S
+            lo_ = [(ie[d] * S + ia[d]) * hi[d] / (cells[d] * S) for d in range(dim)]
+            hi_ = [(ie[d] * S + ia[d] + 1) * hi[d] / (cells[d] * S) for d in range(dim)]
+            for v in range(m):
+                avg[e, a, v] = sum(coef[v, t] * np.prod([_mono_avg(lo_[d], hi_[d], expo[v, t, d]) for d in range(dim)])
+                                   for t in range(4))
+    U, kept = oracle.subcell_init(c, avg)
+    assert kept.kept.all() and np.array_equal(kept.sub, avg)
+    np.testing.assert_allclose(U, want, rtol=0, atol=1e-12)
+
+
+def test_kept_cfl_takes_the_subcell_averages():
+    """Wave speeds of kept elements come from their subcell averages: a
+    uniform state given as averages gives alpha / sum_d (|v_d| + c) / dx_d
+    in closed form, whatever the kept elements' nodes hold (NaN here); the
+    same nodes without kept data give no finite step."""
+    cells, hi, g = (6, 4), (1.0, 2.0), 1.4
+    c = oracle.make_cfg(2, cells, [0, 0], list(hi), 2, oracle.PDE_EULER, [g], limiter=2)
+    rho, vx, vy, p = 1.3, 0.4, -0.2, 0.9
+    q = np.array([rho, rho * vx, rho * vy, p / (g - 1) + 0.5 * rho * (vx * vx + vy * vy)])
+    E, S = 24, 5
+    avg = np.broadcast_to(q, (E, S * S, 4)).copy()
+    U, kept = oracle.subcell_init(c, avg)
+    cs = math.sqrt(g * p / rho)
+    want = oracle.alpha(c) / ((abs(vx) + cs) / (hi[0] / cells[0]) + (abs(vy) + cs) / (hi[1] / cells[1]))
+    assert abs(oracle.cfl_dt_kept(c, U, kept) - want) <= 1e-14 * want
+    Unan = np.full_like(U, np.nan)
+    assert abs(oracle.cfl_dt_kept(c, Unan, kept) - want) <= 1e-14 * want
+    kept.kept[:12] = 0  # half the elements from their nodes again
+    Uhalf = Unan.copy()
+    Uhalf[:12] = q
+    assert abs(oracle.cfl_dt_kept(c, Uhalf, kept) - want) <= 1e-14 * want
+    kept.kept[:] = 0
+    assert not np.isfinite(oracle.cfl_dt_kept(c, Unan, kept))
+
+
+def test_kept_mode_without_kept_data_is_the_plain_limiter():
+    """From a nodal state (nothing kept) a kept-mode step is the plain
+    limited step bit for bit; it keeps the troubled elements' new subcell
+    averages, whose reconstruction is exactly their new nodal state."""
+    c, U = _explosion()
+    dt = oracle.cfl_dt(c, U)
+    U1, f1, n1 = oracle.step_limited(c, U, dt)
+    c.limiter = 2
+    kept = oracle.Kept(c)
+    U2, f2, n2 = oracle.step_limited_kept(c, U, kept, dt)
+    assert n1 == n2 > 0
+    np.testing.assert_array_equal(U1, U2)
+    np.testing.assert_array_equal(f1, f2)
+    np.testing.assert_array_equal(kept.kept, f2)
+    R, _ = oracle.subcell_init(c, kept.sub)
+    np.testing.assert_array_equal(R[f2 == 1], U2[f2 == 1])
+
+
+def test_sharp_sod_with_kept_subcell_data():
+    """Sod's tubes with the discontinuities inside elements, given as
+    subcell averages: the nodal interpolant of such data is not admissible,
+    but with kept subcell data the run stays positive, conserves mass to
+    rounding and follows the exact Riemann solution (shock position, star
+    plateau)."""
+    nx, N, s = 64, 3, 0.4 / 64
+    c = oracle.make_cfg(2, (nx, 1), [0, 0], [1.0, 1.0 / nx], N, oracle.PDE_EULER, [1.4], limiter=2)
+
+    def tubes(X):
+        x = X[..., 0]
+        high = (x > 0.25 + s) & (x < 0.75 + s)
+        rho = np.where(high, 1.0, 0.125)
+        p = np.where(high, 1.0, 0.1)
+        z = 0 * rho
+        return np.stack([rho, z, z, p / 0.4], axis=-1)
+
+    avg = inputs.subcell_means(tubes, (nx, 1), (0.0, 0.0), (1.0, 1.0 / nx), N, k=5)
+    U0, kept = oracle.subcell_init(c, avg)
+    M0 = oracle.mass(c, U0)
+    np.testing.assert_allclose(M0[0], (0.5 * 1.0 + 0.5 * 0.125) / nx, rtol=1e-13)  # the averages' mass
+    c.limiter = 1  # the plain limiter re-projects the reconstruction, whose subcells are not admissible
+    assert not np.isfinite(oracle.run(c, U0, 0.1)[0]).all()
+    c.limiter = 2
+    U, t, k, _ = oracle.run_kept(c, U0, kept, 0.1)
+    assert t == 0.1 and np.isfinite(U).all()
+    np.testing.assert_allclose(oracle.mass(c, U), M0, rtol=0, atol=1e-14)
+    ks = kept.sub[kept.kept == 1]
+    assert ks.size and ks[..., 0].min() > 0
+    assert (0.4 * (ks[..., 3] - 0.5 * (ks[..., 1] ** 2 + ks[..., 2] ** 2) / ks[..., 0])).min() > 0
+    x = oracle.node_coords(c)[..., 0]
+    rho = U[..., 0]
+    ok = kept.kept == 0  # unlimited elements: their nodes are the solution
+    x0 = 0.75 + s
+    ex_r, star = _sod_exact(x, t, x0)
+    ex_l, _ = _sod_exact(2 * (0.5 + s) - x, t, x0)
+    ex = np.where(x >= 0.5 + s, ex_r, ex_l)
+    l1 = nx * np.sum(node_weights(c) * np.abs(rho - ex))
+    assert l1 < 0.02, l1
+    xs = x0 + star["shock"] * t
+    right = (x > x0 + star["u"] * t + 0.02) & ok[:, None]
+    mid = 0.5 * (star["rho_star_right"] + 0.125)
+    pos = x[right & (rho > mid)].max()
+    assert abs(pos - xs) < 1.5 / nx, (pos, xs)
+    plateau = rho[(x > x0 + star["u"] * t + 0.02) & (x < xs - 0.02) & ok[:, None]]
+    assert np.abs(plateau - star["rho_star_right"]).max() < 0.05 * star["rho_star_right"]
+
+
+def test_sharp_blast_with_kept_subcell_data_keeps_symmetry_and_mass():
+    """A blast with a sharp circular edge (rho 1 / 0.125, p 1 / 0.1) given as
+    subcell averages: 20 limited steps with kept subcell data stay finite,
+    keep the kept averages admissible, conserve mass to rounding and keep
+    the x <-> y mirror symmetry of the data (states and troubled sets)."""
+    C, N = 16, 4
+    c = oracle.make_cfg(2, (C, C), [0, 0], [1, 1], N, oracle.PDE_EULER, [1.4], limiter=2)
+    avg = inputs.subcell_means(inputs.euler_sharp_blast((0.5, 0.5), 0.2), (C, C), (0.0, 0.0), (1.0, 1.0), N)
+    U, kept = oracle.subcell_init(c, avg)
+    M0 = oracle.mass(c, U)
+    seen = 0
+    for _ in range(20):
+        U, flags, cnt = oracle.step_limited_kept(c, U, kept, oracle.cfl_dt_kept(c, U, kept))
+        seen = max(seen, cnt)
+        F = flags.reshape(C, C)
+        assert np.array_equal(F, F.T)
+    assert 0 < seen < C * C
+    assert np.isfinite(U).all()
+    ks = kept.sub[kept.kept == 1]
+    assert ks[..., 0].min() > 0 and (0.4 * (ks[..., 3] - 0.5 * (ks[..., 1] ** 2 + ks[..., 2] ** 2) / ks[..., 0])).min() > 0
+    np.testing.assert_allclose(oracle.mass(c, U), M0, rtol=0, atol=5e-14)
+    n = N + 1
+    Eu = U.reshape(C, C, n, n, 4)  # [ey, ex, sy, sx, v]
+    mirror = Eu.transpose(1, 0, 3, 2, 4)[..., [0, 2, 1, 3]]
+    assert np.abs(Eu - mirror).max() < 1e-12
