@@ -199,7 +199,23 @@ typedef struct {
                                    ADERDG_E_UNSUPPORTED for that and for an
                                    instance whose subcell arrays do not fit
                                    a CTA (3D elasticity N = 4, 3D
-                                   diffuse-interface elasticity N = 3) */
+                                   diffuse-interface elasticity N = 3).
+                                   2: the same limiter with the subcell data
+                                   of limited elements kept between steps:
+                                   an element the last step limited takes
+                                   the subcell averages its subcell scheme
+                                   produced as its subcell data at t^n
+                                   (eq. subcellaverage; not the averages of
+                                   the reconstructed polynomial) for the
+                                   maximum-principle bounds, the subcell
+                                   scheme and the coupling, and its wave
+                                   speeds for the CFL step come from those
+                                   averages; an initial state can be given
+                                   as subcell averages
+                                   (aderdg_set_subcell_state).  Handles
+                                   only: aderdg_batch_create returns
+                                   ADERDG_E_UNSUPPORTED.  Other values:
+                                   ADERDG_E_INVAL */
 } aderdg_config_t;
 
 typedef struct aderdg_s aderdg_t;
@@ -292,6 +308,29 @@ int aderdg_get_predictor_outputs(aderdg_t *h, double *volume, double *qface, dou
  * NULL), *count their number (may be NULL).  ADERDG_E_INVAL on a handle
  * without the limiter.  Synchronising. */
 int aderdg_troubled(aderdg_t *h, int *flags, int64_t *count);
+
+/* Kept subcell data (cfg->limiter = 2; Sec. 2.3, eq. subcellaverage and the
+ * least-squares reconstruction that follows eq. pde.nc.fv).
+ *
+ * aderdg_set_subcell_state sets the state from the subcell averages avg of
+ * every element, avg[e][a][v] ((2N+1)^d subcells a per element, x fastest,
+ * then y, z; E (2N+1)^d nVar doubles), in host or device memory (where),
+ * at time t: each element's nodal state becomes the least-squares
+ * reconstruction of its averages, every element is marked as limited
+ * (aderdg_troubled then reports all of them), so that the next step takes
+ * avg as the subcell data at t^n, and the CFL wave speeds of the state are
+ * those of avg.  A discontinuous initial state given this way needs no
+ * admissible nodal interpolant.  The library copies avg; the caller keeps
+ * ownership.  Synchronising.
+ *
+ * aderdg_get_subcell_state copies out the kept subcell averages in the same
+ * layout: rows of the elements that aderdg_troubled marks hold their
+ * averages; the other rows are unspecified.  Synchronising.
+ *
+ * Both return ADERDG_E_INVAL for a NULL argument, a non-finite t, or a
+ * handle that does not keep subcell data. */
+int aderdg_set_subcell_state(aderdg_t *h, const double *avg, int where, double t);
+int aderdg_get_subcell_state(aderdg_t *h, double *avg, int where);
 
 /* One full step: dt from the CFL condition on the current state, clipped so
  * that t does not pass t_end (the clipped step sets t = t_end exactly),

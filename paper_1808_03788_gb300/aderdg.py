@@ -124,6 +124,8 @@ _SIGS = {
     "aderdg_corrector": (C.c_int, [_H, C.c_double]),
     "aderdg_get_predictor_outputs": (C.c_int, [_H, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "aderdg_troubled": (C.c_int, [_H, C.c_void_p, C.POINTER(C.c_int64)]),
+    "aderdg_set_subcell_state": (C.c_int, [_H, C.c_void_p, C.c_int, C.c_double]),
+    "aderdg_get_subcell_state": (C.c_int, [_H, C.c_void_p, C.c_int]),
     "aderdg_step": (C.c_int, [_H, C.c_double, _DP]),
     "aderdg_advance": (C.c_int, [_H, C.c_double, C.c_int64]),
     "aderdg_cfl_dt": (C.c_int, [_H, _DP]),
@@ -268,7 +270,9 @@ class Solver:
     def __init__(self, pde: int, dim: int, cells, lo, hi, N: int, params=(),
                  precision: int = ADERDG_FP64, picard: int = 0, alpha: float = 0.0,
                  stream=None, torch_alloc: bool = True, shapes=(0, 0), tune_cache=None,
-                 guess: int = ADERDG_GUESS_TRIVIAL, limiter: bool = False):
+                 guess: int = ADERDG_GUESS_TRIVIAL, limiter: int = 0):
+        """limiter: 0 / False none, 1 / True the subcell limiter, 2 the
+        limiter keeping the limited elements' subcell data between steps."""
         L = load()
         self.dim, self.N, self.pde = dim, N, pde
         self.m = nvar(pde, dim)
@@ -291,7 +295,8 @@ class Solver:
         cfg.picard_iters = picard
         cfg.cfl_alpha = alpha
         cfg.initial_guess = guess
-        cfg.limiter = 1 if limiter else 0
+        cfg.limiter = int(limiter)
+        self.nsub = (2 * N + 1) ** dim
         _set_shapes(cfg, shapes, tune_cache)
         self._alloc = None
         if stream is not None:
@@ -368,6 +373,20 @@ class Solver:
         cnt = C.c_int64(0)
         _check(self._L.aderdg_troubled(self._h, flags.ctypes.data, C.byref(cnt)))
         return flags, cnt.value
+
+    def set_subcell_state(self, avg, t: float = 0.0):
+        """The state from the subcell averages avg [E, (2N+1)^d, m] of every
+        element (limiter 2)."""
+        avg = np.ascontiguousarray(avg, dtype=np.float64)
+        assert avg.size == self.E * self.nsub * self.m, (avg.shape, self.E, self.nsub, self.m)
+        _check(self._L.aderdg_set_subcell_state(self._h, avg.ctypes.data, ADERDG_HOST, float(t)))
+
+    def get_subcell_state(self):
+        """The kept subcell averages [E, (2N+1)^d, m] (rows of the elements
+        troubled() marks; the others unspecified)."""
+        avg = np.empty((self.E, self.nsub, self.m))
+        _check(self._L.aderdg_get_subcell_state(self._h, avg.ctypes.data, ADERDG_HOST))
+        return avg
 
     def predictor_outputs(self):
         nf = self.n ** (self.dim - 1)
@@ -714,7 +733,7 @@ class Batch:
         cfg.picard_iters = picard
         cfg.cfl_alpha = alpha
         cfg.initial_guess = guess
-        cfg.limiter = 1 if limiter else 0
+        cfg.limiter = int(limiter)
         _set_shapes(cfg, shapes, tune_cache)
         if stream is not None:
             cfg.cuda_stream = C.c_void_p(int(stream))

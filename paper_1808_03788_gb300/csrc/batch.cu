@@ -573,6 +573,9 @@ int aderdg_batch_create(const aderdg_solve_spec_t *specs, int count, const aderd
     if (prec != ADERDG_FP64 && prec != ADERDG_MIXED_FP32) return fail(ADERDG_E_INVAL, "bad precision");
     if (cfg && !valid_shape_requests(cfg->pred_shape, cfg->corr_shape))
         return fail(ADERDG_E_INVAL, "bad tile shape request");
+    if (cfg && (cfg->limiter < 0 || cfg->limiter > 2)) return fail(ADERDG_E_INVAL, "limiter must be 0, 1 or 2");
+    if (cfg && cfg->limiter == 2)
+        return fail(ADERDG_E_UNSUPPORTED, "kept subcell data (limiter 2) is available on single-solve handles");
     std::vector<Slot> tmp(count);
     for (int i = 0; i < count; ++i) {
         int rc = make_slot(specs[i], prec, cfg ? cfg->initial_guess : 0, cfg ? cfg->picard_iters : 0,

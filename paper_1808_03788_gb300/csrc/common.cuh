@@ -50,7 +50,9 @@ struct Control {
     unsigned int lim_fresh;  // subcell limiter: lim_mmc holds the candidate extremes of the state's last step
     unsigned int lim_count;  // subcell limiter: troubled elements listed in lim_list this step
                              // (zeroed by the next step's dt_update)
-    unsigned int pad1;
+    unsigned int lim_kept_ok;  // kept subcell data: lim_subn holds the subcell averages of the
+                               // elements lim_flags marks (the last limited step, or an upload of
+                               // subcell data) -- cleared by any other change of the state
 };
 
 
@@ -158,6 +160,15 @@ struct SolveDesc {
     double *lim_mmc;
     int *lim_flags;
     int *lim_list;  // the troubled elements of the step, in detection order [ctl->lim_count]
+    // kept subcell data (Sec. 2.3, eq. subcellaverage, for a limited element
+    // the averages its subcell scheme produced; NULL unless the handle keeps
+    // them), each [E][(2N+1)^d][M]: lim_sub the subcell data of u^n of the
+    // elements with lim_kept[e] set, lim_subn the new averages of this step's
+    // troubled elements (k_lim_minmax moves them to lim_sub and sets lim_kept
+    // at the start of the next step)
+    double *lim_sub;
+    double *lim_subn;
+    int *lim_kept;
     // domain decomposition (a block of a partitioned mesh, see partition.cu):
     // elist: the predictor's elements, E indices into the block (its
     // boundary or its interior elements); NULL: elements 0 .. E-1.
@@ -599,6 +610,9 @@ struct KernelSet {
     void (*lim_minmax32)(KParams);
     void (*lim_detect32)(KParams);
     size_t lim_smem_w32;
+    // kept subcell data: the state of uploaded subcell averages (their
+    // least-squares reconstruction), in the FP64 instance only
+    void (*lim_init)(KParams);
     TileShape pshape[NSHAPE_P], pshape_ex[NSHAPE_P], cshape[NSHAPE_C];  // pshape_ex: extrapolation and CERK guesses
     int pred_shape, corr_shape;  // indices of the shapes in use
 };

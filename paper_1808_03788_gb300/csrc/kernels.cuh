@@ -1539,6 +1539,10 @@ k_corrector(const KParams P)
     if constexpr (C::WM) flush();
 }
 
+// the subcell limiter's sizes (limiter.cuh)
+template <class PDE, int DIM, int N>
+struct LimCfg;
+
 // Wave-speed maxima of the current state of solve 0 of the launch (the CFL
 // input of the first step after an upload, and after a limited step that
 // changed the state): grid-stride over all nodes, one atomic per warp.
@@ -1551,17 +1555,20 @@ __global__ void __launch_bounds__(256) k_cfl(const KParams P)
     // after a limited step that troubled no element the state is the
     // corrector's candidate: its maxima stand
     if (P.lim_pass && S.ctl->lim_count == 0u) return;
+    // kept subcell data (Sec. 2.3): the elements lim_flags marks are limited
+    // ones, whose wave speeds are those of their subcell averages (lim_subn,
+    // listed in lim_list), not of the nodes of the reconstructed polynomial
+    const bool kept = S.lim_sub && S.ctl->lim_kept_ok != 0;
     const long long total = S.E * G::NS;
     double lmax[DIM];
 #pragma unroll
     for (int d = 0; d < DIM; ++d) lmax[d] = 0.0;
     bool bad = false;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-         i += (long long)gridDim.x * blockDim.x) {
+    auto take = [&](const double *a) {
         T q[M];
 #pragma unroll
         for (int v = 0; v < M; ++v) {
-            const double x = S.u[i * M + v];
+            const double x = a[v];
             bad |= dbl_nonfinite(x);
             q[v] = narrow<T>(x);
         }
@@ -1570,6 +1577,26 @@ __global__ void __launch_bounds__(256) k_cfl(const KParams P)
             const double lam = double(PDE::max_eig(P.pde, q, d));
             bad |= !(lam >= 0.0);
             lmax[d] = fmax(lmax[d], lam);
+        }
+    };
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        if (kept && S.lim_flags[i / G::NS]) {
+#pragma unroll
+            for (int v = 0; v < M; ++v) bad |= dbl_nonfinite(S.u[i * M + v]);
+            continue;
+        }
+        take(S.u + i * M);
+    }
+    if constexpr (LimCfg<PDE, DIM, N>::OK) {
+        if (kept) {
+            constexpr int NSUB = LimCfg<PDE, DIM, N>::NSUB;
+            const long long nk = (long long)min(S.ctl->lim_count, (unsigned)S.E) * NSUB;
+            for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < nk;
+                 j += (long long)gridDim.x * blockDim.x) {
+                const long long e = S.lim_list[j / NSUB];
+                take(S.lim_subn + (e * NSUB + j % NSUB) * M);
+            }
         }
     }
 #pragma unroll
@@ -1585,7 +1612,8 @@ __global__ void __launch_bounds__(256) k_cfl(const KParams P)
 #include "limiter.cuh"
 
 // The limiter's kernels of one (PDE, d, N); K: 0 minmax, 1 detect, 2 fv,
-// 3 couple.  Detection and the subcell scheme work on the FP64 state in
+// 3 couple, 4 / 5 the FP32 path's minmax / detect, 6 the subcell-data
+// upload.  Detection and the subcell scheme work on the FP64 state in
 // both precisions and are referenced by the FP64 instance only (so that
 // each is compiled once; an FP32-path handle takes them from there); the
 // coupling replaces the face fluxes of the step's own precision.
@@ -1599,6 +1627,7 @@ constexpr KernelFn lim_kernel()
         else if constexpr (K == 2) return &k_lim_fv<PDE, DIM, N>;
         else if constexpr (K == 4) return &k_lim_minmax32<PDE, DIM, N>;
         else if constexpr (K == 5) return &k_lim_detect32<PDE, DIM, N>;
+        else if constexpr (K == 6) return &k_lim_subcell_init<PDE, DIM, N>;
         else return &k_lim_couple<PDE, DIM, N, T>;
     } else if constexpr (LimCfg<PDE, DIM, N>::OK && K == 3) {
         return &k_lim_couple<PDE, DIM, N, T>;
@@ -1664,6 +1693,7 @@ const KernelSet KS<PDE, DIM, N, T>::value = {
     lim_kernel<PDE, DIM, N, T, 0>(), lim_kernel<PDE, DIM, N, T, 1>(), lim_kernel<PDE, DIM, N, T, 2>(),
     lim_kernel<PDE, DIM, N, T, 3>(), LimCfg<PDE, DIM, N>::BYTES, LimWarp<LimCfg<PDE, DIM, N>>::BYTES,
     lim_kernel<PDE, DIM, N, T, 4>(), lim_kernel<PDE, DIM, N, T, 5>(), LimWarp32<LimCfg<PDE, DIM, N>>::BYTES,
+    lim_kernel<PDE, DIM, N, T, 6>(),
     {pred_shape<PDE, DIM, N, T, 0>(), pred_shape<PDE, DIM, N, T, 1>(), pred_shape<PDE, DIM, N, T, 2>(),
      pred_shape<PDE, DIM, N, T, 3>(), pred_shape<PDE, DIM, N, T, 4>(), pred_shape<PDE, DIM, N, T, 5>(),
      pred_shape<PDE, DIM, N, T, 6>(), pred_shape<PDE, DIM, N, T, 7>(), pred_shape<PDE, DIM, N, T, 8>()},

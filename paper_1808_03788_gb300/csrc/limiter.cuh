@@ -369,6 +369,22 @@ __device__ void lim_averages(const double *src, long long e, LimSmem<L> &sm, dou
     lim_tensor<DIM, L::M, L::S, L::n>(sm.u, dst, sm.ta, sm.tb, sm.Pr);
 }
 
+// Subcell data of element e at t^n (eq. subcellaverage): where the solve
+// keeps subcell data and lim_kept[e] is set (the step that produced u^n
+// limited e), the averages that step's subcell scheme gave it; else the
+// averages of its nodal state u_prev.  The CTA works on one element.
+template <class L, int DIM>
+__device__ void lim_un_averages(const SolveDesc &S, long long e, LimSmem<L> &sm, double *dst)
+{
+    if (S.lim_sub && S.lim_kept[e]) {  // uniform over the CTA
+        const double *src = S.lim_sub + e * (L::NSUB * L::M);
+        for (int i = threadIdx.x; i < L::NSUB * L::M; i += blockDim.x) dst[i] = src[i];
+        __syncthreads();
+    } else {
+        lim_averages<L, DIM>(S.u_prev, e, sm, dst);
+    }
+}
+
 // the two subcell layers of averages a next to face (d, side) into
 // ghost slot g[layer][line][v]: side 0 -> layers 0, 1; side 1 -> S-2, S-1
 template <class L, int DIM>
@@ -430,7 +446,11 @@ __device__ void lim_extremes_warp(const double *avg, int lane, double *mm)
 // an element that was not troubled and had no troubled face neighbour
 // still holds the candidate the detection projected, so its extremes are
 // copied from there; the others (and all after a state upload or an
-// explicit corrector call) are projected afresh.
+// explicit corrector call) are projected afresh.  Where the solve keeps
+// subcell data (ctl->lim_kept_ok), an element the last limited step
+// treated takes the subcell averages that step gave it (lim_subn) as its
+// subcell data at t^n: they move to lim_sub, lim_kept[e] is set, and they
+// give its extremes; lim_kept is cleared for every other element.
 template <class PDE, int DIM, int N>
 __global__ void __launch_bounds__(128) k_lim_minmax(const KParams P)
 {
@@ -449,7 +469,19 @@ __global__ void __launch_bounds__(128) k_lim_minmax(const KParams P)
             const SolveDesc &S = P.solves[si];
             if (!S.u_prev) continue;  // a solve without the limiter
             const bool fresh = S.ctl->lim_fresh != 0;
+            const bool kept_ok = S.lim_sub && S.ctl->lim_kept_ok != 0;
             for (long long e = (long long)blockIdx.x * W::WARPS + warp; e < S.E; e += (long long)gridDim.x * W::WARPS) {
+                if (S.lim_sub) {
+                    const int kept = kept_ok && S.lim_flags[e] != 0;
+                    if (lane == 0) S.lim_kept[e] = kept;
+                    if (kept) {  // uniform over the warp
+                        const double *src = S.lim_subn + e * (L::NSUB * L::M);
+                        double *dst = S.lim_sub + e * (L::NSUB * L::M);
+                        for (int i = lane; i < L::NSUB * L::M; i += 32) dst[i] = src[i];
+                        lim_extremes_warp<L>(src, lane, S.lim_mm + e * (2 * L::M));
+                        continue;
+                    }
+                }
                 bool reuse = fresh;
                 if (reuse) {
                     int touched = S.lim_flags[e];
@@ -491,7 +523,12 @@ __global__ void __launch_bounds__(128) k_lim_detect(const KParams P)
             const SolveDesc &S = P.solves[si];
             if (!S.u_prev) continue;
             // this launch keeps the candidate's extremes for the next step
-            if (blockIdx.x == 0 && threadIdx.x == 0) S.ctl->lim_fresh = 1u;
+            // (and, with kept subcell data, the subcell scheme of this step
+            // leaves the troubled elements' averages in lim_subn)
+            if (blockIdx.x == 0 && threadIdx.x == 0) {
+                S.ctl->lim_fresh = 1u;
+                S.ctl->lim_kept_ok = 1u;
+            }
             for (long long e = (long long)blockIdx.x * W::WARPS + warp; e < S.E; e += (long long)gridDim.x * W::WARPS) {
                 const double *uc = S.u_out + e * (L::NS * L::M);  // the candidate
                 int bad = 0;
@@ -721,14 +758,21 @@ __global__ void __launch_bounds__(128) k_lim_minmax32(const KParams P)
             const SolveDesc &S = P.solves[si];
             if (!S.u_prev) continue;  // a solve without the limiter
             const bool fresh = S.ctl->lim_fresh != 0;
+            const bool kept_ok = S.lim_sub && S.ctl->lim_kept_ok != 0;
             // 32 elements per warp at a time: each lane decides for its own
             // element and copies the kept extremes; the warp then projects
-            // the elements that need it, one after the other
+            // the elements that need it (or moves their kept subcell data,
+            // as k_lim_minmax does), one after the other
             for (long long e0 = ((long long)blockIdx.x * W::WARPS + warp) * 32; e0 < S.E;
                  e0 += (long long)gridDim.x * W::WARPS * 32) {
                 const long long el = e0 + lane;
-                bool need = el < S.E;
-                if (need && fresh) {
+                bool need = el < S.E, kept = false;
+                if (need && S.lim_sub) {
+                    kept = kept_ok && S.lim_flags[el] != 0;
+                    S.lim_kept[el] = kept;
+                }
+                const unsigned kmask = __ballot_sync(0xffffffffu, kept);
+                if (need && fresh && !kept) {
                     int touched = S.lim_flags[el];
 #pragma unroll
                     for (int d = 0; d < DIM; ++d)
@@ -744,8 +788,16 @@ __global__ void __launch_bounds__(128) k_lim_minmax32(const KParams P)
                 }
                 unsigned todo = __ballot_sync(0xffffffffu, need);
                 while (todo) {  // uniform over the warp
-                    const long long e = e0 + (__ffs(todo) - 1);
+                    const int j = __ffs(todo) - 1;
+                    const long long e = e0 + j;
                     todo &= todo - 1;
+                    if ((kmask >> j) & 1u) {
+                        const double *src = S.lim_subn + e * (L::NSUB * L::M);
+                        double *dst = S.lim_sub + e * (L::NSUB * L::M);
+                        for (int i = lane; i < L::NSUB * L::M; i += 32) dst[i] = src[i];
+                        lim_extremes_warp<L>(src, lane, S.lim_mm + e * (2 * L::M));
+                        continue;
+                    }
                     double ref[L::M], ref_l;
                     float am_l;
                     lim_averages32_warp<L, DIM>(S.u_prev, e, Pr32, u, avg, ta, tb, lane, ref, ref_l, am_l);
@@ -804,7 +856,12 @@ __global__ void __launch_bounds__(128) k_lim_detect32(const KParams P)
             const SolveDesc &S = P.solves[si];
             if (!S.u_prev) continue;
             // this launch keeps the candidate's extremes for the next step
-            if (blockIdx.x == 0 && threadIdx.x == 0) S.ctl->lim_fresh = 1u;
+            // (and, with kept subcell data, the subcell scheme of this step
+            // leaves the troubled elements' averages in lim_subn)
+            if (blockIdx.x == 0 && threadIdx.x == 0) {
+                S.ctl->lim_fresh = 1u;
+                S.ctl->lim_kept_ok = 1u;
+            }
             for (long long e = (long long)blockIdx.x * W::WARPS + warp; e < S.E; e += (long long)gridDim.x * W::WARPS) {
                 const double *uc = S.u_out + e * (L::NS * L::M);  // the candidate
                 int bad = 0;
@@ -956,13 +1013,13 @@ __global__ void __launch_bounds__(128) k_lim_fv(const KParams P)
             const unsigned ntroubled = min(S.ctl->lim_count, (unsigned)S.E);
             for (unsigned k = blockIdx.x; k < ntroubled; k += gridDim.x) {
                 const long long e = S.lim_list[k];
-                lim_averages<L, DIM>(S.u_prev, e, sm, sm.avg);
+                lim_un_averages<L, DIM>(S, e, sm, sm.avg);
 #pragma unroll 1
                 for (int d = 0; d < DIM; ++d)
 #pragma unroll 1
                     for (int side = 0; side < 2; ++side) {
                         const long long nb = neighbour_of(S, (int)e, d, side ? 1 : -1);
-                        lim_averages<L, DIM>(S.u_prev, nb, sm, sm.nb);
+                        lim_un_averages<L, DIM>(S, nb, sm, sm.nb);
                         // ghost cells -2, -1 from the lower neighbour's last
                         // layers; S, S+1 from the upper neighbour's first ones
                         lim_layers<L, DIM>(sm.nb, d, side ? 0 : 1,
@@ -1048,6 +1105,9 @@ __global__ void __launch_bounds__(128) k_lim_fv(const KParams P)
                 }
                 for (int i = threadIdx.x; i < L::NSUB * M; i += blockDim.x) sm.dq[i] += sm.avg[i];
                 __syncthreads();
+                if (S.lim_subn)  // kept: the next step's subcell data of e
+                    for (int i = threadIdx.x; i < L::NSUB * M; i += blockDim.x)
+                        S.lim_subn[e * (L::NSUB * M) + i] = sm.dq[i];
                 lim_tensor<DIM, M, L::n, S_>(sm.dq, sm.u, sm.ta, sm.tb, sm.Rc);
                 // the material fields (q_t = 0) are kept as they were
                 for (int i = threadIdx.x; i < L::NS * M; i += blockDim.x)
@@ -1095,14 +1155,14 @@ __global__ void __launch_bounds__(128) k_lim_couple(const KParams P)
                     for (int side = 0; side < 2; ++side)
                         any |= S.lim_flags[neighbour_of(S, (int)e, d, side ? 1 : -1)];
                 if (!any) continue;  // uniform over the CTA
-                lim_averages<L, DIM>(S.u_prev, e, sm, sm.avg);
+                lim_un_averages<L, DIM>(S, e, sm, sm.avg);
 #pragma unroll 1
                 for (int d = 0; d < DIM; ++d)
 #pragma unroll 1
                     for (int side = 0; side < 2; ++side) {
                         const long long nb = neighbour_of(S, (int)e, d, side ? 1 : -1);
                         if (!S.lim_flags[nb]) continue;
-                        lim_averages<L, DIM>(S.u_prev, nb, sm, sm.nb);
+                        lim_un_averages<L, DIM>(S, nb, sm, sm.nb);
                         // the face's four cell layers: lower element's last two,
                         // upper element's first two
                         double *gl = sm.ghost, *gu = sm.ghost + 2 * L::NLINE * M;
@@ -1338,6 +1398,42 @@ __global__ void __launch_bounds__(128) k_lim_couple(const KParams P)
                         __syncthreads();
                     }
             }
+        }
+    }
+}
+
+// Kept subcell data: a state given as the subcell averages of every element
+// (uploaded to lim_subn).  Each element's nodal state becomes their
+// least-squares reconstruction (R28) and every element is marked as limited,
+// so that the next step takes the averages as its subcell data at t^n and
+// the wave speeds of the state (k_cfl) come from them.  One solve, one
+// element per CTA.
+template <class PDE, int DIM, int N>
+__global__ void __launch_bounds__(128) k_lim_subcell_init(const KParams P)
+{
+    using L = LimCfg<PDE, DIM, N>;
+    if constexpr (L::OK) {
+        constexpr int M = L::M;
+        extern __shared__ __align__(16) unsigned char smem_raw[];
+        LimSmem<L> sm(reinterpret_cast<double *>(smem_raw));
+        lim_load_ops<L>(P, sm);
+        const SolveDesc &S = P.solves[0];
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            S.ctl->lim_count = (unsigned)S.E;
+            S.ctl->lim_kept_ok = 1u;
+            S.ctl->lim_fresh = 0u;
+        }
+        for (long long e = blockIdx.x; e < S.E; e += gridDim.x) {
+            const double *src = S.lim_subn + e * (L::NSUB * M);
+            for (int i = threadIdx.x; i < L::NSUB * M; i += blockDim.x) sm.dq[i] = src[i];
+            __syncthreads();
+            lim_tensor<DIM, M, L::n, L::S>(sm.dq, sm.u, sm.ta, sm.tb, sm.Rc);
+            for (int i = threadIdx.x; i < L::NS * M; i += blockDim.x) S.u_out[e * (L::NS * M) + i] = sm.u[i];
+            if (threadIdx.x == 0) {
+                S.lim_flags[e] = 1;
+                S.lim_list[e] = (int)e;
+            }
+            __syncthreads();
         }
     }
 }

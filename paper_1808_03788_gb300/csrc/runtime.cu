@@ -168,6 +168,11 @@ struct aderdg_s {
     double *lim_mmc = nullptr;  // limiter: those of the candidate, kept for the next step
     int *lim_flags = nullptr;   // limiter: troubled elements of the last step [E]
     int *lim_list = nullptr;    // limiter: their indices, in detection order [E]
+    bool lim_keep = false;      // limiter: subcell data of limited elements kept between steps
+    int NSUB = 0;               // subcells per element, (2N+1)^d
+    double *lim_sub = nullptr;  // kept: subcell data of u^n [E][NSUB][M]
+    double *lim_subn = nullptr; // kept: new averages of the step's troubled elements [E][NSUB][M]
+    int *lim_kept = nullptr;    // kept: lim_sub[e] holds e's subcell data of u^n [E]
     double *host_pinned = nullptr;
     KParams kp{};
     Basis basis{};
@@ -411,7 +416,12 @@ int aderdg_create(const aderdg_mesh_t *mesh, int N, int nVar, const aderdg_pde_t
         delete h;
         return fail(ADERDG_E_INVAL, "bad initial guess");
     }
+    if (cfg && (cfg->limiter < 0 || cfg->limiter > 2)) {
+        delete h;
+        return fail(ADERDG_E_INVAL, "limiter must be 0, 1 or 2");
+    }
     h->limiter = cfg && cfg->limiter;
+    h->lim_keep = cfg && cfg->limiter == 2;
     if (h->limiter) {
         const int rc = limiter_kernels(pde->kind, mesh->dim, N, prec, h->guess, &h->lk, &why);
         if (rc) {
@@ -471,9 +481,16 @@ int aderdg_create(const aderdg_mesh_t *mesh, int N, int nVar, const aderdg_pde_t
         h->lim_flags = (int *)dev_alloc(h, sizeof(int) * (size_t)E);
         h->lim_list = (int *)dev_alloc(h, sizeof(int) * (size_t)E);
     }
+    h->NSUB = ipow(2 * N + 1, h->dim);
+    if (h->lim_keep) {
+        h->lim_sub = (double *)dev_alloc(h, sizeof(double) * (size_t)E * h->NSUB * m);
+        h->lim_subn = (double *)dev_alloc(h, sizeof(double) * (size_t)E * h->NSUB * m);
+        h->lim_kept = (int *)dev_alloc(h, sizeof(int) * (size_t)E);
+    }
     if (!h->u || !h->V || !h->tr || !h->ctl || !h->scratch || !h->d_desc || (ks->rf > 0 && !h->ref) ||
         (h->guess == ADERDG_GUESS_EXTRAP && !h->qprev) ||
-        (h->limiter && (!h->u_prev || !h->lim_mm || !h->lim_mmc || !h->lim_flags || !h->lim_list))) {
+        (h->limiter && (!h->u_prev || !h->lim_mm || !h->lim_mmc || !h->lim_flags || !h->lim_list)) ||
+        (h->lim_keep && (!h->lim_sub || !h->lim_subn || !h->lim_kept))) {
         aderdg_destroy(h);
         return fail(ADERDG_E_NOMEM, "device allocation failed");
     }
@@ -514,6 +531,9 @@ int aderdg_create(const aderdg_mesh_t *mesh, int N, int nVar, const aderdg_pde_t
     sd.lim_mmc = h->lim_mmc;
     sd.lim_flags = h->lim_flags;
     sd.lim_list = h->lim_list;
+    sd.lim_sub = h->lim_sub;
+    sd.lim_subn = h->lim_subn;
+    sd.lim_kept = h->lim_kept;
     KParams &kp = h->kp;
     std::memset(&kp, 0, sizeof(kp));
     kp.solves = h->d_desc;
@@ -552,6 +572,9 @@ int aderdg_destroy(aderdg_t *h)
     dev_free(h, h->lim_mmc);
     dev_free(h, h->lim_flags);
     dev_free(h, h->lim_list);
+    dev_free(h, h->lim_sub);
+    dev_free(h, h->lim_subn);
+    dev_free(h, h->lim_kept);
     dev_free(h, h->V);
     dev_free(h, h->tr);
     dev_free(h, h->ctl);
@@ -642,9 +665,49 @@ int aderdg_corrector(aderdg_t *h, double dt)
     if (!h) return fail(ADERDG_E_INVAL, "NULL handle");
     if (!(dt > 0.0) || !std::isfinite(dt)) return fail(ADERDG_E_INVAL, "dt must be positive and finite");
     CK(cudaMemsetAsync(h->ctl->lam_acc, 0, sizeof(h->ctl->lam_acc), h->stream));
-    // the state changes without the limiter: its kept extremes are stale
+    // the state changes without the limiter: its kept extremes and subcell
+    // data are stale
     CK(cudaMemsetAsync(&h->ctl->lim_fresh, 0, sizeof(h->ctl->lim_fresh), h->stream));
+    CK(cudaMemsetAsync(&h->ctl->lim_kept_ok, 0, sizeof(h->ctl->lim_kept_ok), h->stream));
     return launch_corrector(h, 0, dt);
+}
+
+int aderdg_set_subcell_state(aderdg_t *h, const double *avg, int where, double t)
+{
+    if (!h || !avg) return fail(ADERDG_E_INVAL, "NULL argument");
+    if (!h->lim_keep) return fail(ADERDG_E_INVAL, "the handle does not keep subcell data (limiter 2)");
+    if (!std::isfinite(t)) return fail(ADERDG_E_INVAL, "t must be finite");
+    const size_t bytes = (size_t)h->E * h->NSUB * h->M * sizeof(double);
+    CK(cudaMemcpyAsync(h->lim_subn, avg, bytes,
+                       where == ADERDG_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+    Control c;
+    std::memset(&c, 0, sizeof(c));
+    c.t = t;
+    c.t_end = t;
+    c.alpha = h->alpha;
+    c.dim = h->dim;
+    for (int d = 0; d < 3; ++d) c.inv_dx[d] = h->inv_dx[d];
+    std::memcpy(h->host_pinned, &c, sizeof(c));
+    CK(cudaMemcpyAsync(h->ctl, h->host_pinned, sizeof(c), cudaMemcpyHostToDevice, h->stream));
+    // the reconstruction of every element, all marked limited, then the
+    // wave speeds of the subcell averages
+    h->lk.init<<<(unsigned)std::min<long long>(h->E, 152LL * 16), 128, h->lk.smem, h->stream>>>(h->kp);
+    CK(cudaGetLastError());
+    h->ks->cfl<<<(unsigned)std::min<long long>(4 * 152, (h->E * h->NS + 255) / 256), 256, 0, h->stream>>>(h->kp);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(h->stream));  // the pinned staging buffer is reused
+    return ADERDG_OK;
+}
+
+int aderdg_get_subcell_state(aderdg_t *h, double *avg, int where)
+{
+    if (!h || !avg) return fail(ADERDG_E_INVAL, "NULL argument");
+    if (!h->lim_keep) return fail(ADERDG_E_INVAL, "the handle does not keep subcell data (limiter 2)");
+    const size_t bytes = (size_t)h->E * h->NSUB * h->M * sizeof(double);
+    CK(cudaMemcpyAsync(avg, h->lim_subn, bytes,
+                       where == ADERDG_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return ADERDG_OK;
 }
 
 int aderdg_troubled(aderdg_t *h, int *flags, int64_t *count)

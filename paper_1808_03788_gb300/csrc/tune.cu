@@ -70,9 +70,12 @@ int limiter_kernels(int pde, int dim, int N, int prec, int guess, LimKernels *ou
     const bool f32 = prec == ADERDG_MIXED_FP32;
     *out = LimKernels{f32 ? k64->lim_minmax32 : k64->lim_minmax, f32 ? k64->lim_detect32 : k64->lim_detect,
                       k64->lim_fv, ks->lim_couple, k64->lim_smem, f32 ? k64->lim_smem_w32 : k64->lim_smem_w,
-                      f32 ? 32 : 1};
-    const std::pair<void (*)(KParams), size_t> lk[4] = {
-        {out->minmax, out->smem_w}, {out->detect, out->smem_w}, {out->fv, out->smem}, {out->couple, out->smem}};
+                      f32 ? 32 : 1, k64->lim_init};
+    const std::pair<void (*)(KParams), size_t> lk[5] = {{out->minmax, out->smem_w},
+                                                        {out->detect, out->smem_w},
+                                                        {out->fv, out->smem},
+                                                        {out->couple, out->smem},
+                                                        {out->init, out->smem}};
     for (const auto &k : lk)
         if (k.second > 48 * 1024 && cudaFuncSetAttribute((const void *)k.first, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                          (int)k.second) != cudaSuccess) {

@@ -34,13 +34,14 @@ int resolve_shapes(const KernelSet *ks, int pde, int dim, int N, int prec, const
 // or an ADERDG_* status with *why set to the reason.
 struct LimKernels {
     void (*minmax)(KParams), (*detect)(KParams), (*fv)(KParams), (*couple)(KParams);
-    size_t smem, smem_w;  // per CTA: fv / couple, and minmax / detect
+    size_t smem, smem_w;  // per CTA: fv / couple / init, and minmax / detect
     int mm_epw;           // elements per warp and pass of minmax (grid: elements / (4 mm_epw))
     unsigned minmax_grid(long long elems) const
     {
         const long long per_cta = 4LL * mm_epw;
         return (unsigned)std::min<long long>((elems + per_cta - 1) / per_cta, 152LL * 16);
     }
+    void (*init)(KParams);  // kept subcell data: the state of uploaded subcell averages
 };
 int limiter_kernels(int pde, int dim, int N, int prec, int guess, LimKernels *out, const char **why);
 

@@ -437,3 +437,108 @@ def test_mixed_limited_diffuse_interface_matches_oracle():
     assert np.array_equal(Ug[..., 5:], U[..., 5:])
     s.close()
     assert seen > 0
+
+
+# ---------------------------------------------------------------------------
+# Kept subcell data (limiter 2): limited elements keep their subcell averages
+# between steps, and a state can be uploaded as subcell averages.
+
+
+def _sharp_blast(dim, C, N, precision=A.ADERDG_FP64):
+    from paper_1808_03788_gb300 import inputs
+    c = oracle.make_cfg(dim, (C,) * dim, [0] * dim, [1] * dim, N, oracle.PDE_EULER, [1.4], limiter=2)
+    avg = inputs.subcell_means(inputs.euler_sharp_blast((0.45, 0.5, 0.5)[:dim], 0.2), (C,) * dim, (0.0,) * dim,
+                               (1.0,) * dim, N, k=8 if dim == 2 else 4)
+    s = A.Solver(A.ADERDG_PDE_EULER, dim, (C,) * dim, (0,) * dim, (1,) * dim, N, (1.4,), limiter=2,
+                 precision=precision)
+    return c, avg, s
+
+
+@pytest.mark.parametrize("dim,C,N", [(2, 16, 4), (2, 12, 3), (3, 6, 2)], ids=["2d_N4", "2d_N3", "3d_N2"])
+def test_kept_subcell_data_matches_oracle(dim, C, N):
+    """A blast with a sharp edge uploaded as subcell averages: the uploaded
+    state is their reconstruction, every element marked limited, the first
+    dt from the averages; then every step's dt, troubled set, state and kept
+    subcell averages against the oracle's kept-data step."""
+    c, avg, s = _sharp_blast(dim, C, N)
+    s.set_subcell_state(avg)
+    Uo, kept = oracle.subcell_init(c, avg)
+    Ug = s.get_state()[0]
+    assert np.abs(Ug - Uo).max() <= 1e-13 * np.abs(Uo).max()
+    flags, cnt = s.troubled()
+    assert cnt == c.cells[0] ** dim and flags.all()
+    seen = 0
+    for _ in range(12):
+        dto = oracle.cfl_dt_kept(c, Uo, kept)
+        dt = s.step(1e30, sync_dt=True)
+        assert abs(dt - dto) <= 1e-13 * dto
+        Uo, flags_o, cnt_o = oracle.step_limited_kept(c, Uo, kept, dt)
+        flags, cnt = s.troubled()
+        np.testing.assert_array_equal(flags, flags_o)
+        seen = max(seen, cnt)
+        Ug = s.get_state()[0]
+        assert np.abs(Ug - Uo).max() <= 1e-11 * max(1.0, np.abs(Uo).max())
+        sub = s.get_subcell_state()[flags == 1]
+        assert np.abs(sub - kept.sub[flags == 1]).max() <= 1e-11 * max(1.0, np.abs(kept.sub).max())
+    assert 0 < seen < c.cells[0] ** dim
+    s.close()
+
+
+def test_kept_mode_from_a_nodal_state_matches_oracle():
+    """Limiter 2 from an ordinary nodal upload (nothing kept at first): the
+    tanh blast against the oracle's kept-data steps, and the first step
+    bitwise that of the plain limiter."""
+    c, U = _explosion()
+    c.limiter = 2
+    s2 = A.Solver(2, 2, (16, 16), (0, 0), (1, 1), 3, (1.4,), limiter=2)
+    s1 = _solver(c)
+    s1.set_state(U)
+    s2.set_state(U)
+    kept = oracle.Kept(c)
+    Uo = U.copy()
+    for k in range(10):
+        dt = s2.step(1e30, sync_dt=True)
+        if k == 0:
+            s1.step(1e30)
+            np.testing.assert_array_equal(s1.get_state()[0], s2.get_state()[0])
+        Uo, flags_o, _ = oracle.step_limited_kept(c, Uo, kept, dt)
+        np.testing.assert_array_equal(s2.troubled()[0], flags_o)
+        assert np.abs(s2.get_state()[0] - Uo).max() <= 1e-11 * max(1.0, np.abs(Uo).max())
+    s1.close()
+    s2.close()
+
+
+def test_kept_subcell_data_on_the_fp32_path():
+    """The sharp blast on the FP32 path with kept subcell data: troubled sets
+    equal the FP64 oracle's (the GPU's dt fed to it), states within the
+    mixed path's tolerance, mass as on the unlimited FP32 path."""
+    c, avg, s = _sharp_blast(2, 16, 4, A.ADERDG_MIXED_FP32)
+    s.set_subcell_state(avg)
+    Uo, kept = oracle.subcell_init(c, avg)
+    M0 = s.mass()
+    seen = 0
+    for _ in range(10):
+        dt = s.step(1e30, sync_dt=True)
+        assert abs(dt - oracle.cfl_dt_kept(c, Uo, kept)) <= 1e-6 * dt
+        Uo, flags_o, cnt_o = oracle.step_limited_kept(c, Uo, kept, dt)
+        flags, cnt = s.troubled()
+        np.testing.assert_array_equal(flags, flags_o)
+        seen = max(seen, cnt)
+        assert l2_rel(c, s.get_state()[0], Uo) <= 1e-6
+    np.testing.assert_allclose(s.mass(), M0, rtol=1e-9, atol=1e-9)
+    assert seen > 0
+    s.close()
+
+
+def test_kept_subcell_data_refusals():
+    with pytest.raises(A.AderdgError) as ei:
+        A.Solver(2, 2, (4, 4), (0, 0), (1, 1), 3, (1.4,), limiter=3)
+    assert ei.value.code == A.ADERDG_E_INVAL
+    c, _ = _blast2d((4, 4), 3)
+    with pytest.raises(A.AderdgError) as ei:
+        A.Batch([A.make_spec(*c)], limiter=2)
+    assert ei.value.code == A.ADERDG_E_UNSUPPORTED
+    with A.Solver(2, 2, (4, 4), (0, 0), (1, 1), 3, (1.4,), limiter=True) as s:
+        with pytest.raises(A.AderdgError) as ei:
+            s.set_subcell_state(np.ones((16, 49, 4)))
+        assert ei.value.code == A.ADERDG_E_INVAL
