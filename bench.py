@@ -375,7 +375,8 @@ def _guess_variants(A, torch, w, stream, flush, steps, warmup, shapes, l2_steps,
     return out
 
 
-LIMITER_CASES = ("vortex", "blast", "inclusion", "inclusion_unlimited", "vortex_mixed", "blast_mixed")
+LIMITER_CASES = ("vortex", "blast", "blast_sharp", "inclusion", "inclusion_unlimited", "vortex_mixed", "blast_mixed",
+                 "blast_sharp_mixed")
 
 
 def _limiter(A, torch, w, stream, flush, steps, warmup, cases=LIMITER_CASES, shapes=(0, 0)):
@@ -386,6 +387,9 @@ def _limiter(A, torch, w, stream, flush, steps, warmup, cases=LIMITER_CASES, sha
     diffuse-interface system: a soft inclusion (alpha 1 -> 0.3 across r = 2.5,
     tanh width 0.3, lambda = 2, mu = rho = 1) hit by two mirrored velocity
     boxes, limited and unlimited; the vortex and the blast again on the FP32
+    path.  The blast_sharp cases keep the limited elements' subcell data
+    between steps (limiter 2) and start from a blast with a sharp edge given
+    as subcell averages (2 x 2 midpoint samples per subcell), FP64 and FP32
     path.  Each is timed like the headline, with the troubled elements of
     the last step."""
     import numpy as np
@@ -396,12 +400,17 @@ def _limiter(A, torch, w, stream, flush, steps, warmup, cases=LIMITER_CASES, sha
         dim_pde = name.startswith("inclusion")
         pde, params = (A.ADERDG_PDE_DIFFUSE_ELASTICITY, ()) if dim_pde else (w["pde"], w["params"])
         lim = name != "inclusion_unlimited"
+        sharp = name.startswith("blast_sharp")
         prec = A.ADERDG_MIXED_FP32 if name.endswith("_mixed") else A.ADERDG_FP64
         s = A.Solver(pde, w["dim"], w["cells"], w["lo"], w["hi"], w["N"], params, stream=stream.cuda_stream,
-                     limiter=lim, precision=prec, shapes=shapes)
+                     limiter=2 if sharp else int(lim), precision=prec, shapes=shapes)
         X = s.node_coords(w["lo"], w["hi"])
         x, y = X[..., 0], X[..., 1]
-        if name.startswith("vortex"):
+        avg = None
+        if sharp:
+            avg = inputs.subcell_means(inputs.euler_sharp_blast((5.0, 5.0), 2.0), w["cells"], w["lo"], w["hi"],
+                                       w["N"], k=2)
+        elif name.startswith("vortex"):
             U0 = inputs.euler_vortex(X, lo=w["lo"], hi=w["hi"])
         elif name.startswith("blast"):
             r = np.sqrt((x - 5.0) ** 2 + (y - 5.0) ** 2)
@@ -413,7 +422,10 @@ def _limiter(A, torch, w, stream, flush, steps, warmup, cases=LIMITER_CASES, sha
             box = lambda a, b: np.where((a > 1.0) & (a < 3.0) & (b > 3.0) & (b < 6.0), 1.0, 0.0)
             z = 0 * x
             U0 = inputs.diffuse_pack(2, [z, z, z], [alpha * box(x, y), alpha * box(y, x)], alpha, 2.0, 1.0, 1.0)
-        s.set_state(np.ascontiguousarray(U0))
+        if sharp:
+            s.set_subcell_state(avg)
+        else:
+            s.set_state(np.ascontiguousarray(U0))
         with torch.cuda.stream(stream):
             for _ in range(warmup):
                 flush.zero_()
@@ -433,6 +445,8 @@ def _limiter(A, torch, w, stream, flush, steps, warmup, cases=LIMITER_CASES, sha
         out[name] = {"value": info["dofs"] * steps / (sum(ms) / 1e3), "ms_per_step": sum(ms) / steps,
                      "troubled_last_step": int(cnt), "elements": int(info["elements"]),
                      "tile_shapes": [info["pred_shape"], info["corr_shape"]]}
+        if sharp:
+            out[name]["subcell_data"] = "kept (limiter 2); initial state given as subcell averages"
     return out
 
 

@@ -17,6 +17,12 @@
 //   k_lim_couple  unlimited elements next to troubled ones: the DG face
 //                 flux the corrector applied on the common face is replaced
 //                 by the subcell fluxes projected onto the face nodes
+// With kept subcell data (a handle created with limiter 2) an element the
+// previous step limited takes the subcell averages that step's subcell
+// scheme gave it as its subcell data at t^n (k_lim_minmax moves them into
+// place), in the bounds, the subcell scheme and the coupling alike; k_cfl
+// takes its wave speeds from them, and k_lim_subcell_init builds a state
+// from uploaded subcell averages.
 // Both sides of a face between a troubled and an unlimited element, and of
 // a face between two troubled ones, evaluate its subcell fluxes with the
 // same function on the same subcell averages, so the scheme stays

@@ -542,3 +542,29 @@ def test_kept_subcell_data_refusals():
         with pytest.raises(A.AderdgError) as ei:
             s.set_subcell_state(np.ones((16, 49, 4)))
         assert ei.value.code == A.ADERDG_E_INVAL
+
+
+@pytest.mark.parametrize("precision", [A.ADERDG_FP64, A.ADERDG_MIXED_FP32], ids=["fp64", "mixed"])
+def test_sharp_blast_at_the_bench_size_matches_oracle(precision):
+    """The bench's blast_sharp rows at their full size (200 x 200 elements,
+    N = 4, the same subcell averages, kept subcell data), two limited steps:
+    troubled sets equal, states within the path's tolerance."""
+    from paper_1808_03788_gb300 import inputs
+    cells, lo, hi, N = (200, 200), (0.0, 0.0), (10.0, 10.0), 4
+    c = oracle.make_cfg(2, cells, list(lo), list(hi), N, oracle.PDE_EULER, [1.4], limiter=2)
+    avg = inputs.subcell_means(inputs.euler_sharp_blast((5.0, 5.0), 2.0), cells, lo, hi, N, k=2)
+    Uo, kept = oracle.subcell_init(c, avg)
+    with A.Solver(2, 2, cells, lo, hi, N, (1.4,), limiter=2, precision=precision) as s:
+        s.set_subcell_state(avg)
+        for _ in range(2):
+            dt = s.step(1e30, sync_dt=True)
+            assert abs(dt - oracle.cfl_dt_kept(c, Uo, kept)) <= (1e-13 if precision == A.ADERDG_FP64 else 1e-6) * dt
+            Uo, flags_o, cnt = oracle.step_limited_kept(c, Uo, kept, dt)
+            flags, _ = s.troubled()
+            np.testing.assert_array_equal(flags, flags_o)
+            assert cnt > 0
+            Ug = s.get_state()[0]
+            if precision == A.ADERDG_FP64:
+                assert np.abs(Ug - Uo).max() <= 1e-11 * max(1.0, np.abs(Uo).max())
+            else:
+                assert l2_rel(c, Ug, Uo) <= 1e-6
