@@ -568,3 +568,35 @@ def test_sharp_blast_at_the_bench_size_matches_oracle(precision):
                 assert np.abs(Ug - Uo).max() <= 1e-11 * max(1.0, np.abs(Uo).max())
             else:
                 assert l2_rel(c, Ug, Uo) <= 1e-6
+
+
+@pytest.mark.parametrize("case", ["inclusion", "reaction"])
+def test_kept_mode_on_other_systems_matches_oracle(case):
+    """Limiter 2 on the path-conservative diffuse-interface system (material
+    fields kept as they were; the kept averages carry them unchanged) and on
+    advection with a reaction source: troubled sets, states and kept
+    subcell averages against the oracle's kept-data steps."""
+    if case == "inclusion":
+        spec, U = _inclusion2d((12, 12), 3)
+        c = oracle.make_cfg(2, (12, 12), [0, 0], [1, 1], 3, oracle.PDE_DIFFUSE_ELASTICITY, [], limiter=2)
+    else:
+        spec = (A.ADERDG_PDE_ADVECTION, 2, (16, 8), (0, 0), (1, 1), 3, (1.0, 0.5, 0.0, 1.5))
+        c = oracle.make_cfg(2, (16, 8), [0, 0], [1, 1], 3, oracle.PDE_ADVECTION, [1.0, 0.5, 0.0, 1.5], limiter=2)
+        x = oracle.node_coords(c)[..., 0]
+        U = (0.2 + np.where((x > 0.25) & (x < 0.5), 1.0, 0.0))[..., None]
+    kept = oracle.Kept(c)
+    Uo = U.copy()
+    seen = 0
+    with A.Solver(*spec, limiter=2) as s:
+        s.set_state(U)
+        for _ in range(8):
+            dt = s.step(1e30, sync_dt=True)
+            Uo, flags_o, cnt = oracle.step_limited_kept(c, Uo, kept, dt)
+            flags, _ = s.troubled()
+            np.testing.assert_array_equal(flags, flags_o)
+            seen = max(seen, cnt)
+            assert np.abs(s.get_state()[0] - Uo).max() <= 1e-11 * max(1.0, np.abs(Uo).max())
+            if cnt:
+                sub = s.get_subcell_state()[flags == 1]
+                assert np.abs(sub - kept.sub[flags == 1]).max() <= 1e-11 * max(1.0, np.abs(kept.sub).max())
+    assert seen > 0
