@@ -252,8 +252,8 @@ def cerk_scheme(N: int):
     """The continuous Runge-Kutta scheme of the CERK guess for degree N:
     (A [s, s] strictly lower triangular, beta [s, p]) with the dense-output
     weights b_i(theta) = sum_k beta[i, k] theta^(k+1); p is its order."""
-    a = np.zeros(100)
-    beta = np.zeros(60)
+    a = np.zeros(256)  # s <= 16 stages, order <= 16
+    beta = np.zeros(256)
     p = C.c_int()
     s = lib().orc_cerk_scheme(int(N), _p(a), _p(beta), C.byref(p))
     return a[:s * s].reshape(s, s).copy(), beta[:s * p.value].reshape(s, p.value).copy()
@@ -261,7 +261,7 @@ def cerk_scheme(N: int):
 
 def cerk_weights(theta: float, N: int = 4) -> np.ndarray:
     """The dense-output weights b_i(theta) of the CERK guess for degree N."""
-    out = np.zeros(10)
+    out = np.zeros(16)
     lib().orc_cerk_weights(int(N), float(theta), _p(out))
     return out[:cerk_scheme(N)[0].shape[0]].copy()
 

@@ -239,11 +239,12 @@ def test_extrapolation_guess_vortex_error_matches_trivial():
 # The guess for degree N uses a continuous explicit Runge-Kutta scheme of
 # order p = max(3, N - 1), capped at the highest order built: the classical
 # fourth-order method with its cubic dense output (p = 3) up to N = 4, a
-# six-stage scheme with quartic weights (p = 4) from N = 5.
+# six-stage scheme with quartic weights (p = 4) at N = 5, an eleven-stage
+# scheme with quintic weights (p = 5) from N = 6.
 
 RK_C = np.array([0.0, 0.5, 0.5, 1.0])
 RK_A = np.array([[0, 0, 0, 0], [0.5, 0, 0, 0], [0, 0.5, 0, 0], [0, 0, 1.0, 0]])
-CERK_ORDER = {1: 3, 2: 3, 3: 3, 4: 3, 5: 4, 6: 4, 7: 4}
+CERK_ORDER = {1: 3, 2: 3, 3: 3, 4: 3, 5: 4, 6: 5, 7: 5}
 
 
 def _trees(A, p):
@@ -269,7 +270,7 @@ def test_cerk_schemes_have_the_orders_the_guess_needs():
     np.testing.assert_array_equal(oracle.cerk_scheme(4)[0], RK_A)  # the classical method
 
 
-@pytest.mark.parametrize("N", [4, 5])
+@pytest.mark.parametrize("N", [4, 5, 6])
 @pytest.mark.parametrize("theta", [0.0, 0.1, 0.3, 0.5, 0.77, 1.0])
 def test_cerk_weights_satisfy_the_continuous_order_conditions(theta, N):
     """The dense-output weights b_i(theta) meet every order condition of a
@@ -279,9 +280,12 @@ def test_cerk_weights_satisfy_the_continuous_order_conditions(theta, N):
     A, beta = oracle.cerk_scheme(N)
     p = CERK_ORDER[N]
     b = oracle.cerk_weights(theta, N)
-    np.testing.assert_allclose(b, beta @ theta ** np.arange(1, p + 1), rtol=0, atol=1e-15)
+    # rounding of the weight polynomials: a few ulps of sum_k |beta_ik theta^(k+1)|
+    # (up to 19 in the eleven-stage scheme's coefficients)
+    mag = np.abs(beta) @ theta ** np.arange(1, p + 1)
+    np.testing.assert_allclose(b, beta @ theta ** np.arange(1, p + 1), rtol=0, atol=1e-15 + 4e-16 * mag.max())
     for order_, gamma, phi in _trees(A, p):
-        assert abs(b @ phi - theta ** order_ / gamma) < 2e-15, (order_, gamma)
+        assert abs(b @ phi - theta ** order_ / gamma) < 2e-15 + 4e-16 * (mag @ np.abs(phi)), (order_, gamma)
     if N <= 4:
         for order_, gamma, phi in _trees(RK_A, 3):
             assert abs(b @ phi - theta ** order_ / gamma) < 1e-15
@@ -296,6 +300,23 @@ def test_cerk_order4_scheme_misses_an_order5_condition():
     b = oracle.cerk_weights(1.0, 5)
     misses = [abs(b @ phi - 1 / g) for o, g, phi in _trees(A, 5) if o == 5]
     assert max(misses) > 1e-4
+
+
+def test_cerk_order5_scheme_is_explicit_bounded_and_consistent():
+    """The eleven-stage scheme: nodes c = A 1 inside [0, 1], weights summing
+    to theta (the first-order condition) with the b_i(theta) small on a fine
+    grid (the scheme does not cancel large terms), and b(1) . A^5 1 away
+    from 1/6!, so it is not of order 6 on the tall tree."""
+    A, beta = oracle.cerk_scheme(6)
+    assert A.shape == (11, 11) and beta.shape == (11, 5)
+    c = A.sum(axis=1)
+    assert c.min() >= 0.0 and c.max() <= 1.0
+    th = np.linspace(0, 1, 201)
+    B = np.array([oracle.cerk_weights(t, 6) for t in th])
+    np.testing.assert_allclose(B.sum(axis=1), th, rtol=0, atol=2e-14)  # coefficients up to 19: a few ulps
+    assert np.abs(B).max() < 0.35
+    chain = np.linalg.matrix_power(A, 5) @ np.ones(11)
+    assert abs(oracle.cerk_weights(1.0, 6) @ chain - 1 / 720) > 1e-5
 
 
 @pytest.mark.parametrize("dim,N", [(1, 3), (2, 3), (2, 4), (3, 3), (1, 5), (2, 5), (2, 6)])
@@ -315,7 +336,7 @@ def test_cerk_guess_is_exact_for_data_of_its_order(dim, N):
     assert np.abs(oracle.initial_guess(cfg, _eval(coef, X)[:, None], dt) - ex).max() > 1e-6
 
 
-@pytest.mark.parametrize("N", [4, 5])
+@pytest.mark.parametrize("N", [4, 5, 6])
 def test_cerk_guess_misses_exactly_the_next_taylor_term(N):
     """u0 = x^(p+1), L = -a d/dx: the stages give k = sum_j dt^j A^j 1
     L^(j+1) u, so the dense output carries dt^(p+1) (b(theta) . A^p 1)
@@ -372,7 +393,7 @@ def test_cerk_guess_converged_for_linear_advection(N):
             assert np.abs(short - ref).max() > 1e-12
 
 
-@pytest.mark.parametrize("N", [3, 4, 5])
+@pytest.mark.parametrize("N", [3, 4, 5, 6])
 def test_cerk_guess_design_order_with_one_iteration(N):
     """A guess of degree N-1 (or more) in time needs one Picard iteration
     (Sec. 2.2): Euler density wave, CERK guess, one iteration per step,
