@@ -148,10 +148,13 @@ namespace {
 // uniform order 4), from a numerical search over the stage matrix that kept
 // max |b_i(th)| small (0.35), refined to 40 digits by Newton's method on the
 // order conditions; shown here to 20 digits.
+// Order 5: an eleven-stage scheme with quintic weights from the same kind of
+// search (the 17 tree conditions of order <= 5; max |b_i(th)| 0.31, max
+// |a_ij| 0.48), refined and shown the same way.
 struct CerkScheme {
     int s, p;
     double a[CERK_SMAX][CERK_SMAX];
-    double beta[CERK_SMAX][4];
+    double beta[CERK_SMAX][5];
 };
 const CerkScheme kCerkOrder3 = {
     4, 3,
@@ -175,6 +178,46 @@ const CerkScheme kCerkOrder4 = {
      {0.0, 0.31288713514090078845, -1.2668811066683743739, 1.3044535662878009984}},
 };
 
+const CerkScheme kCerkOrder5 = {
+    11, 5,
+    {{0},
+     {0.21396406893114929941},
+     {0.034520790017671977007, 0.41372592912176714349},
+     {0.088416642665365227537, 0.13683623308249277562, 0.47755326751379046974},
+     {-0.0266719632876990541, 0.12845891088304249121, 0.073770359528602792921, -0.029901862330888622484},
+     {0.15811896403112403656, 0.062824176896518388083, -0.040310351902863277689, -0.19180775673017479455,
+      0.093904496963942459173},
+     {0.095444096258275612407, 0.029612493702906972604, 0.042065059631820178293, 0.056639453843974274155,
+      0.23157141256193104679, -0.082321405762062763284},
+     {-0.0099858386067894141076, -0.004311214382797107593, 0.042484710026669023005, -0.061702579717549094049,
+      0.1360902187699344359, 0.089703158714395027355, 0.093344465039202374441},
+     {0.044225647283319301368, 0.038507705255559191753, -0.12347160217482120146, 0.013995747001842868748,
+      0.091397903235836837048, 0.017790975806619039112, 0.022029539570705958954, -0.0069441602114276107782},
+     {0.040551492362699865282, 0.12072433771358202958, 0.042059965202631322386, 0.36018691033467310849,
+      0.038926340292962444834, -0.0061070210341534810037, 0.16681162009247751788, 0.019144269354406344107,
+      0.08877318014754002403},
+     {0.080638694974360216797, 0.01205941886818835392, 0.018096630449363849, 0.055867998305249973877,
+      0.091187420805903382723, -0.0089338243342328581078, 0.24597832827170908575, 0.04717166509034146719,
+      0.048963914391693246618, 0.021076563758733234774}},
+    {{1.0, -6.6143117173026234553, 17.178359569284717945, -18.86793234430243545, 7.3659907185475543609},
+     {0.0, 2.1719103255203805044, -7.2952295061885010417, 8.9606564533760370553, -3.8193824401789661292},
+     {0.0, -1.5854789298302827005, 9.4423133346087880382, -15.145534664537743023, 7.4773099169377650253},
+     {0.0, 0.88423518048995741019, -5.35768986153765167, 10.111281515466986061, -5.6462993048931384541},
+     {0.0, 3.2971257036516648115, -12.513611374370090692, 16.088923484236408098, -6.8449476884926829149},
+     {0.0, -0.31163502670566630635, 1.0070308771872418124, -1.1615838865360656713, 0.45679117132443454501},
+     {0.0, -0.78236688921344789434, 6.1477951147591089282, -10.406910275786306437, 5.1537555111704861162},
+     {0.0, -1.5146597261084853013, 8.8458108856981437369, -13.086412777562555403, 5.8623322128438347029},
+     {0.0, 4.3645676908433573827, -15.732556849961202994, 19.346795749644294217, -7.8916086488488356334},
+     {0.0, -0.33452411430651430281, 2.3248704578988559346, -5.0045221963152205875, 3.3202049045619430229},
+     {0.0, 0.42513750296165985198, -4.0470926473794099978, 9.1652389423166011406, -5.4341463529723946416}},
+};
+
+// the scheme of the CERK guess for degree N (cerk_stages / cerk_order)
+const CerkScheme &cerk_scheme_for(int N)
+{
+    return cerk_stages(N) == 11 ? kCerkOrder5 : (cerk_stages(N) == 6 ? kCerkOrder4 : kCerkOrder3);
+}
+
 template <typename T>
 void fill_typed(const Basis &b, Ops<T> &o)
 {
@@ -197,7 +240,7 @@ void fill_typed(const Basis &b, Ops<T> &o)
         o.xi[t] = T(b.x[t]);
         o.hxi2[t] = T(0.5 * b.x[t] * b.x[t]);
         {  // CERK dense-output weights at xi_t
-            const CerkScheme &cs = cerk_stages(n - 1) == 6 ? kCerkOrder4 : kCerkOrder3;
+            const CerkScheme &cs = cerk_scheme_for(n - 1);
             for (int i = 0; i < cs.s; ++i) {
                 double v = 0.0, thk = b.x[t];
                 for (int k = 0; k < cs.p; ++k) {
@@ -213,9 +256,9 @@ void fill_typed(const Basis &b, Ops<T> &o)
         o.bw[t] = T(1.0 / prod);
     }
     {
-        const CerkScheme &cs = cerk_stages(n - 1) == 6 ? kCerkOrder4 : kCerkOrder3;
+        const CerkScheme &cs = cerk_scheme_for(n - 1);
         for (int i = 0; i < cs.s; ++i)
-            for (int j = 0; j < i; ++j) o.ck_a[i][j] = T(cs.a[i][j]);
+            for (int j = 0; j < i; ++j) o.ck_a[i * (i - 1) / 2 + j] = T(cs.a[i][j]);
     }
 }
 }  // namespace

@@ -79,11 +79,12 @@ __host__ __device__ __forceinline__ float pconst<float>(const PdeParams &P, int 
 
 // The continuous Runge-Kutta scheme of the CERK guess (Sec. 2.2) for
 // degree N: the classical fourth-order method with its cubic dense output
-// up to N = 4, a six-stage scheme with quartic weights from N = 5 (the
-// degree N - 1 that one Picard iteration wants at N = 5).
-constexpr int CERK_SMAX = 6;
-__host__ __device__ constexpr int cerk_stages(int N) { return N >= 5 ? 6 : 4; }
-__host__ __device__ constexpr int cerk_order(int N) { return N >= 5 ? 4 : 3; }
+// up to N = 4, a six-stage scheme with quartic weights at N = 5, an
+// eleven-stage scheme with quintic weights from N = 6 (the degree N - 1
+// that one Picard iteration wants at N = 5 and N = 6).
+constexpr int CERK_SMAX = 11;
+__host__ __device__ constexpr int cerk_stages(int N) { return N >= 6 ? 11 : (N >= 5 ? 6 : 4); }
+__host__ __device__ constexpr int cerk_order(int N) { return N >= 6 ? 5 : (N >= 5 ? 4 : 3); }
 
 // Operators in the compute type (filled on the host by fill_ops).  Indexed
 // with compile-time constants inside unrolled loops, they are read straight
@@ -100,7 +101,8 @@ struct Ops {
     T hxi2[NMAX];          // xi^2 / 2
     T bw[NMAX];            // barycentric weights 1 / prod_{j != k} (xi_k - xi_j)
     T ck_b[CERK_SMAX][NMAX];        // CERK dense-output weights b_i(xi_t)
-    T ck_a[CERK_SMAX][CERK_SMAX];   // CERK stage matrix (strictly lower triangular)
+    T ck_a[CERK_SMAX * (CERK_SMAX - 1) / 2];  // CERK stage matrix, strictly lower triangle by rows:
+                                              // a_ij at i (i - 1) / 2 + j
 };
 
 // Unsigned division by a divisor fixed for a solve (its cell counts) as a

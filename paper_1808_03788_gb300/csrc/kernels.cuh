@@ -777,7 +777,7 @@ k_predictor(const KParams P)
                             for (int j = 0; j < st; ++j) {
                                 T kj[C::MX];
                                 NodeIO<T, C::MX>::load(kslot(j), kj);
-                                const T a = O.ck_a[st][j];
+                                const T a = O.ck_a[st * (st - 1) / 2 + j];
 #pragma unroll
                                 for (int v = 0; v < C::MX; ++v) w[v] += a * kj[v];
                             }

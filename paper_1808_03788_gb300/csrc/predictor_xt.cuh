@@ -292,7 +292,7 @@ k_predictor_xt(const KParams P)
                                 for (int v = 0; v < M; ++v) {
                                     float acc = 0.f;
 #pragma unroll
-                                    for (int j = 0; j < st; ++j) acc += O.ck_a[st][j] * K[j][x][v];
+                                    for (int j = 0; j < st; ++j) acc += O.ck_a[st * (st - 1) / 2 + j] * K[j][x][v];
                                     w[x][v] = u[x][v] + dtT * acc;
                                 }
                             spatial_R(w, Rk);

@@ -194,16 +194,20 @@ def test_full_run_euler_vortex_cerk_guess(picard):
         assert l2_rel(cfg, Ug, Uo) <= tol
 
 
-@pytest.mark.parametrize("N", [5, 6])
-def test_full_run_euler_vortex_order4_cerk_guess(N):
-    """The six-stage scheme with quartic weights (N >= 5): a degree N-1
-    guess at N = 5, so one Picard iteration; FP64 and mixed full runs against
-    the oracle, and the default count N + 1 - 4."""
+CERK_ORDER = {5: 4, 6: 5, 7: 5}
+
+
+@pytest.mark.parametrize("N", [5, 6, 7])
+def test_full_run_euler_vortex_high_order_cerk_guess(N):
+    """The six-stage scheme with quartic weights (N = 5) and the
+    eleven-stage scheme with quintic weights (N >= 6): a degree N-1 guess at
+    N = 5 and 6, so one Picard iteration; FP64 and mixed full runs against
+    the oracle, and the default count N + 1 - p."""
     case = (2, 2, N, (14, 12), 10.0, (GAMMA,))
     for picard in (0, 1):
         for prec, tol in ((A.ADERDG_FP64, 1e-11), (A.ADERDG_MIXED_FP32, 1e-6)):
             cfg, s = _pair(*case, guess=A.ADERDG_GUESS_CERK, picard=picard, precision=prec)
-            assert s.info()["picard_iters"] == (picard or N + 1 - 4)
+            assert s.info()["picard_iters"] == (picard or N + 1 - CERK_ORDER[N])
             U0 = inputs.euler_vortex(oracle.node_coords(cfg))
             Uo, to, ko, _ = oracle.run(cfg, U0, t_end=0.3)
             s.set_state(U0)
@@ -214,15 +218,17 @@ def test_full_run_euler_vortex_order4_cerk_guess(N):
             assert l2_rel(cfg, Ug, Uo) <= tol
 
 
+@pytest.mark.parametrize("N", [5, 6])
 @pytest.mark.parametrize("shapes", [(0, 0), (1, 1), (2, 2), (7, 3), (8, 0)])
-def test_order4_cerk_guess_every_predictor_shape(shapes):
+def test_high_order_cerk_guess_every_predictor_shape(shapes, N):
     """Each predictor shape of the FP32 path holds the earlier stages in its
-    exchange field's free time slices (its own layout per shape): within
-    the mixed tolerance of the oracle."""
-    cfg = oracle.make_cfg(2, (9, 7), [0, 0], [10, 10], 5, 2, (GAMMA,), picard=1, guess=oracle.GUESS_CERK)
+    exchange field's free time slices (its own layout per shape; five of
+    them for the six-stage scheme, ten for the eleven-stage one): within the
+    mixed tolerance of the oracle."""
+    cfg = oracle.make_cfg(2, (9, 7), [0, 0], [10, 10], N, 2, (GAMMA,), picard=1, guess=oracle.GUESS_CERK)
     U0 = inputs.euler_vortex(oracle.node_coords(cfg))
     Uo, to, ko, _ = oracle.run(cfg, U0, t_end=0.2)
-    with A.Solver(2, 2, (9, 7), (0, 0), (10, 10), 5, (GAMMA,), precision=A.ADERDG_MIXED_FP32, picard=1,
+    with A.Solver(2, 2, (9, 7), (0, 0), (10, 10), N, (GAMMA,), precision=A.ADERDG_MIXED_FP32, picard=1,
                   guess=A.ADERDG_GUESS_CERK, shapes=shapes) as s:
         s.set_state(U0)
         s.advance(0.2)
@@ -232,11 +238,11 @@ def test_order4_cerk_guess_every_predictor_shape(shapes):
     assert l2_rel(cfg, Ug, Uo) <= 1e-6
 
 
-@pytest.mark.parametrize("N,shapes", [(5, (3, 0)), (6, (4, 1)), (5, (0, 0))])
-def test_order4_cerk_guess_advection_plane_kernel(N, shapes):
-    """2D advection with the order-4 scheme on the plane-owning FP32 kernel
-    (the stages' k in registers) and on k_predictor: one Picard iteration,
-    against the oracle."""
+@pytest.mark.parametrize("N,shapes", [(5, (3, 0)), (6, (4, 1)), (5, (0, 0)), (7, (3, 0)), (6, (0, 0))])
+def test_high_order_cerk_guess_advection_plane_kernel(N, shapes):
+    """2D advection with the order-4 (N = 5) and order-5 (N >= 6) schemes on
+    the plane-owning FP32 kernel (the stages' k in registers) and on
+    k_predictor: one Picard iteration, against the oracle."""
     a = (0.7, -1.1)
     cfg = oracle.make_cfg(2, (6, 5), [0, 0], [1, 1], N, 1, a, picard=1, guess=oracle.GUESS_CERK)
     X = oracle.node_coords(cfg)
@@ -273,8 +279,9 @@ def test_cerk_guess_plane_kernel(shapes):
 def test_batch_with_guess_equals_alone(guess):
     mix = [(2, 2, (6, 5), (0, 0), (10, 10), 2, (GAMMA,)), (2, 2, (8, 8), (0, 0), (10, 10), 4, (GAMMA,)),
            (3, 3, (3, 3, 2), (0, 0, 0), (1, 1, 1), 3, EL),
-           (2, 2, (5, 4), (0, 0), (10, 10), 5, (GAMMA,))]  # N = 5: the six-stage CERK scheme
-    t_end = [0.3, 0.2, 0.02, 0.15]
+           (2, 2, (5, 4), (0, 0), (10, 10), 5, (GAMMA,)),  # N = 5: the six-stage CERK scheme
+           (2, 2, (4, 5), (0, 0), (10, 10), 6, (GAMMA,))]  # N = 6: the eleven-stage one
+    t_end = [0.3, 0.2, 0.02, 0.15, 0.1]
     ics = []
     for c in mix:
         X = oracle.node_coords(oracle.make_cfg(c[1], c[2], c[3], c[4], c[5], c[0], c[6]))
