@@ -140,7 +140,7 @@ int make_slot(const aderdg_solve_spec_t &sp, int prec, int guess, int picard, do
     if (guess < ADERDG_GUESS_TRIVIAL || guess > ADERDG_GUESS_CERK) return fail(ADERDG_E_INVAL, "bad initial guess");
     LimKernels lk{};
     if (limiter) {
-        const int rc = limiter_kernels(sp.pde.kind, m.dim, sp.N, prec, guess, &lk, &why);
+        const int rc = limiter_kernels(sp.pde.kind, m.dim, sp.N, prec, guess, false, &lk, &why);
         if (rc) return fail(rc, why);
     }
     s = Slot();

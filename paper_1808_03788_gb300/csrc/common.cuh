@@ -615,6 +615,9 @@ struct KernelSet {
     // kept subcell data: the state of uploaded subcell averages (their
     // least-squares reconstruction), in the FP64 instance only
     void (*lim_init)(KParams);
+    // the extremes kernels of solves that keep subcell data (FP64, FP32 path)
+    void (*lim_minmax_keep)(KParams);
+    void (*lim_minmax32_keep)(KParams);
     TileShape pshape[NSHAPE_P], pshape_ex[NSHAPE_P], cshape[NSHAPE_C];  // pshape_ex: extrapolation and CERK guesses
     int pred_shape, corr_shape;  // indices of the shapes in use
 };

@@ -1613,7 +1613,7 @@ __global__ void __launch_bounds__(256) k_cfl(const KParams P)
 
 // The limiter's kernels of one (PDE, d, N); K: 0 minmax, 1 detect, 2 fv,
 // 3 couple, 4 / 5 the FP32 path's minmax / detect, 6 the subcell-data
-// upload.  Detection and the subcell scheme work on the FP64 state in
+// upload, 7 / 8 the minmax kernels of solves that keep subcell data.  Detection and the subcell scheme work on the FP64 state in
 // both precisions and are referenced by the FP64 instance only (so that
 // each is compiled once; an FP32-path handle takes them from there); the
 // coupling replaces the face fluxes of the step's own precision.
@@ -1622,10 +1622,12 @@ template <class PDE, int DIM, int N, typename T, int K>
 constexpr KernelFn lim_kernel()
 {
     if constexpr (LimCfg<PDE, DIM, N>::OK && sizeof(T) == 8) {
-        if constexpr (K == 0) return &k_lim_minmax<PDE, DIM, N>;
+        if constexpr (K == 0) return &k_lim_minmax<PDE, DIM, N, false>;
         else if constexpr (K == 1) return &k_lim_detect<PDE, DIM, N>;
         else if constexpr (K == 2) return &k_lim_fv<PDE, DIM, N>;
-        else if constexpr (K == 4) return &k_lim_minmax32<PDE, DIM, N>;
+        else if constexpr (K == 4) return &k_lim_minmax32<PDE, DIM, N, false>;
+        else if constexpr (K == 7) return &k_lim_minmax<PDE, DIM, N, true>;
+        else if constexpr (K == 8) return &k_lim_minmax32<PDE, DIM, N, true>;
         else if constexpr (K == 5) return &k_lim_detect32<PDE, DIM, N>;
         else if constexpr (K == 6) return &k_lim_subcell_init<PDE, DIM, N>;
         else return &k_lim_couple<PDE, DIM, N, T>;
@@ -1693,7 +1695,7 @@ const KernelSet KS<PDE, DIM, N, T>::value = {
     lim_kernel<PDE, DIM, N, T, 0>(), lim_kernel<PDE, DIM, N, T, 1>(), lim_kernel<PDE, DIM, N, T, 2>(),
     lim_kernel<PDE, DIM, N, T, 3>(), LimCfg<PDE, DIM, N>::BYTES, LimWarp<LimCfg<PDE, DIM, N>>::BYTES,
     lim_kernel<PDE, DIM, N, T, 4>(), lim_kernel<PDE, DIM, N, T, 5>(), LimWarp32<LimCfg<PDE, DIM, N>>::BYTES,
-    lim_kernel<PDE, DIM, N, T, 6>(),
+    lim_kernel<PDE, DIM, N, T, 6>(), lim_kernel<PDE, DIM, N, T, 7>(), lim_kernel<PDE, DIM, N, T, 8>(),
     {pred_shape<PDE, DIM, N, T, 0>(), pred_shape<PDE, DIM, N, T, 1>(), pred_shape<PDE, DIM, N, T, 2>(),
      pred_shape<PDE, DIM, N, T, 3>(), pred_shape<PDE, DIM, N, T, 4>(), pred_shape<PDE, DIM, N, T, 5>(),
      pred_shape<PDE, DIM, N, T, 6>(), pred_shape<PDE, DIM, N, T, 7>(), pred_shape<PDE, DIM, N, T, 8>()},

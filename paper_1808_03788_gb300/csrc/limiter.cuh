@@ -448,6 +448,66 @@ __device__ void lim_extremes_warp(const double *avg, int lane, double *mm)
     }
 }
 
+// Kept subcell data: element e's averages from the last limited step
+// (lim_subn) become its subcell data of u^n (lim_sub) and give its extremes
+// (the same set of values as lim_extremes_warp takes, so the same extremes).
+// One warp; lane l takes subcells l, l + 32, ..., their loads issued in
+// groups of up to four subcells before any is used (one memory round trip
+// per group, not one per value).  Out of line, so that the kept elements do
+// not weigh on the registers of the extremes kernels' common path.
+template <class L>
+__device__ __noinline__ void lim_move_kept(const SolveDesc &S, long long e, int lane)
+{
+    constexpr int M = L::M, NSUB = L::NSUB, PER = (NSUB + 31) / 32, CH = PER < 4 ? PER : 4;
+    const double *src = S.lim_subn + e * (NSUB * M);
+    double *dst = S.lim_sub + e * (NSUB * M);
+    long long lo[M], hi[M];
+#pragma unroll
+    for (int v = 0; v < M; ++v) {
+        lo[v] = 0x7fffffffffffffffll;
+        hi[v] = -0x7fffffffffffffffll - 1;
+    }
+#pragma unroll 1
+    for (int r0 = 0; r0 < PER; r0 += CH) {
+        double x[CH][M];
+#pragma unroll
+        for (int r = 0; r < CH; ++r) {
+            const int a = lane + 32 * (r0 + r);
+            if (r0 + r < PER && a < NSUB) {
+#pragma unroll
+                for (int v = 0; v < M; ++v) x[r][v] = src[a * M + v];
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < CH; ++r) {
+            const int a = lane + 32 * (r0 + r);
+            if (r0 + r < PER && a < NSUB) {
+#pragma unroll
+                for (int v = 0; v < M; ++v) {
+                    dst[a * M + v] = x[r][v];
+                    const long long k = lim_key(x[r][v]);
+                    lo[v] = k < lo[v] ? k : lo[v];
+                    hi[v] = k > hi[v] ? k : hi[v];
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < M; ++v) {
+        long long l = lo[v], h = hi[v];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const long long ol = __shfl_xor_sync(0xffffffffu, l, o), oh = __shfl_xor_sync(0xffffffffu, h, o);
+            l = ol < l ? ol : l;
+            h = oh > h ? oh : h;
+        }
+        if (lane == 0) {
+            S.lim_mm[e * (2 * M) + v * 2] = lim_unkey(l);
+            S.lim_mm[e * (2 * M) + v * 2 + 1] = lim_unkey(h);
+        }
+    }
+}
+
 // Extremes of u^n.  After a limited step on the same state (ctl->lim_fresh),
 // an element that was not troubled and had no troubled face neighbour
 // still holds the candidate the detection projected, so its extremes are
@@ -456,8 +516,10 @@ __device__ void lim_extremes_warp(const double *avg, int lane, double *mm)
 // subcell data (ctl->lim_kept_ok), an element the last limited step
 // treated takes the subcell averages that step gave it (lim_subn) as its
 // subcell data at t^n: they move to lim_sub, lim_kept[e] is set, and they
-// give its extremes; lim_kept is cleared for every other element.
-template <class PDE, int DIM, int N>
+// give its extremes; lim_kept is cleared for every other element.  KEEP:
+// the instance for solves that keep subcell data (the other one is the
+// plain limiter's, without that path).
+template <class PDE, int DIM, int N, bool KEEP>
 __global__ void __launch_bounds__(128) k_lim_minmax(const KParams P)
 {
     using L = LimCfg<PDE, DIM, N>;
@@ -475,17 +537,16 @@ __global__ void __launch_bounds__(128) k_lim_minmax(const KParams P)
             const SolveDesc &S = P.solves[si];
             if (!S.u_prev) continue;  // a solve without the limiter
             const bool fresh = S.ctl->lim_fresh != 0;
-            const bool kept_ok = S.lim_sub && S.ctl->lim_kept_ok != 0;
+            const bool kept_ok = KEEP && S.lim_sub && S.ctl->lim_kept_ok != 0;
             for (long long e = (long long)blockIdx.x * W::WARPS + warp; e < S.E; e += (long long)gridDim.x * W::WARPS) {
-                if (S.lim_sub) {
-                    const int kept = kept_ok && S.lim_flags[e] != 0;
-                    if (lane == 0) S.lim_kept[e] = kept;
-                    if (kept) {  // uniform over the warp
-                        const double *src = S.lim_subn + e * (L::NSUB * L::M);
-                        double *dst = S.lim_sub + e * (L::NSUB * L::M);
-                        for (int i = lane; i < L::NSUB * L::M; i += 32) dst[i] = src[i];
-                        lim_extremes_warp<L>(src, lane, S.lim_mm + e * (2 * L::M));
-                        continue;
+                if constexpr (KEEP) {
+                    if (S.lim_sub) {
+                        const int kept = kept_ok && S.lim_flags[e] != 0;
+                        if (lane == 0) S.lim_kept[e] = kept;
+                        if (kept) {  // uniform over the warp
+                            lim_move_kept<L>(S, e, lane);
+                            continue;
+                        }
                     }
                 }
                 bool reuse = fresh;
@@ -745,8 +806,9 @@ __device__ __forceinline__ float *lim32_setup(const KParams &P, unsigned char *s
     return p32 + W::PR32 + (size_t)(threadIdx.x >> 5) * W::FLOATS;
 }
 
-// Extremes of u^n on the FP32 path (as k_lim_minmax, FP32 projections).
-template <class PDE, int DIM, int N>
+// Extremes of u^n on the FP32 path (as k_lim_minmax, FP32 projections;
+// KEEP as there).
+template <class PDE, int DIM, int N, bool KEEP>
 __global__ void __launch_bounds__(128) k_lim_minmax32(const KParams P)
 {
     using L = LimCfg<PDE, DIM, N>;
@@ -764,7 +826,7 @@ __global__ void __launch_bounds__(128) k_lim_minmax32(const KParams P)
             const SolveDesc &S = P.solves[si];
             if (!S.u_prev) continue;  // a solve without the limiter
             const bool fresh = S.ctl->lim_fresh != 0;
-            const bool kept_ok = S.lim_sub && S.ctl->lim_kept_ok != 0;
+            const bool kept_ok = KEEP && S.lim_sub && S.ctl->lim_kept_ok != 0;
             // 32 elements per warp at a time: each lane decides for its own
             // element and copies the kept extremes; the warp then projects
             // the elements that need it (or moves their kept subcell data,
@@ -773,11 +835,14 @@ __global__ void __launch_bounds__(128) k_lim_minmax32(const KParams P)
                  e0 += (long long)gridDim.x * W::WARPS * 32) {
                 const long long el = e0 + lane;
                 bool need = el < S.E, kept = false;
-                if (need && S.lim_sub) {
-                    kept = kept_ok && S.lim_flags[el] != 0;
-                    S.lim_kept[el] = kept;
+                unsigned kmask = 0u;
+                if constexpr (KEEP) {
+                    if (need && S.lim_sub) {
+                        kept = kept_ok && S.lim_flags[el] != 0;
+                        S.lim_kept[el] = kept;
+                    }
+                    kmask = __ballot_sync(0xffffffffu, kept);
                 }
-                const unsigned kmask = __ballot_sync(0xffffffffu, kept);
                 if (need && fresh && !kept) {
                     int touched = S.lim_flags[el];
 #pragma unroll
@@ -797,12 +862,11 @@ __global__ void __launch_bounds__(128) k_lim_minmax32(const KParams P)
                     const int j = __ffs(todo) - 1;
                     const long long e = e0 + j;
                     todo &= todo - 1;
-                    if ((kmask >> j) & 1u) {
-                        const double *src = S.lim_subn + e * (L::NSUB * L::M);
-                        double *dst = S.lim_sub + e * (L::NSUB * L::M);
-                        for (int i = lane; i < L::NSUB * L::M; i += 32) dst[i] = src[i];
-                        lim_extremes_warp<L>(src, lane, S.lim_mm + e * (2 * L::M));
-                        continue;
+                    if constexpr (KEEP) {
+                        if ((kmask >> j) & 1u) {
+                            lim_move_kept<L>(S, e, lane);
+                            continue;
+                        }
                     }
                     double ref[L::M], ref_l;
                     float am_l;

@@ -423,7 +423,7 @@ int aderdg_create(const aderdg_mesh_t *mesh, int N, int nVar, const aderdg_pde_t
     h->limiter = cfg && cfg->limiter;
     h->lim_keep = cfg && cfg->limiter == 2;
     if (h->limiter) {
-        const int rc = limiter_kernels(pde->kind, mesh->dim, N, prec, h->guess, &h->lk, &why);
+        const int rc = limiter_kernels(pde->kind, mesh->dim, N, prec, h->guess, h->lim_keep, &h->lk, &why);
         if (rc) {
             delete h;
             return fail(rc, why);

@@ -48,7 +48,7 @@ const KernelSet *lookup_kernels(int pde, int dim, int N, int prec)
     return nullptr;
 }
 
-int limiter_kernels(int pde, int dim, int N, int prec, int guess, LimKernels *out, const char **why)
+int limiter_kernels(int pde, int dim, int N, int prec, int guess, bool keep, LimKernels *out, const char **why)
 {
     const KernelSet *k64 = lookup_kernels(pde, dim, N, ADERDG_FP64);
     const KernelSet *ks = lookup_kernels(pde, dim, N, prec);
@@ -68,7 +68,9 @@ int limiter_kernels(int pde, int dim, int N, int prec, int guess, LimKernels *ou
     // the FP32 path projects its subcell averages in FP32 (FP64 only for
     // decisions too close to call)
     const bool f32 = prec == ADERDG_MIXED_FP32;
-    *out = LimKernels{f32 ? k64->lim_minmax32 : k64->lim_minmax, f32 ? k64->lim_detect32 : k64->lim_detect,
+    void (*minmax)(KParams) = keep ? (f32 ? k64->lim_minmax32_keep : k64->lim_minmax_keep)
+                                   : (f32 ? k64->lim_minmax32 : k64->lim_minmax);
+    *out = LimKernels{minmax, f32 ? k64->lim_detect32 : k64->lim_detect,
                       k64->lim_fv, ks->lim_couple, k64->lim_smem, f32 ? k64->lim_smem_w32 : k64->lim_smem_w,
                       f32 ? 32 : 1, k64->lim_init};
     const std::pair<void (*)(KParams), size_t> lk[5] = {{out->minmax, out->smem_w},

@@ -30,7 +30,8 @@ int resolve_shapes(const KernelSet *ks, int pde, int dim, int N, int prec, const
 // The subcell limiter's kernels for a step of precision prec (Sec. 2.3):
 // detection and the subcell scheme of the FP64 instance (they work on the
 // FP64 state in both precisions) and the coupling of the step's own
-// precision, with their dynamic shared memory opted in.  Returns ADERDG_OK,
+// precision, with their dynamic shared memory opted in; keep selects the
+// extremes kernel of solves that keep subcell data.  Returns ADERDG_OK,
 // or an ADERDG_* status with *why set to the reason.
 struct LimKernels {
     void (*minmax)(KParams), (*detect)(KParams), (*fv)(KParams), (*couple)(KParams);
@@ -43,6 +44,6 @@ struct LimKernels {
     }
     void (*init)(KParams);  // kept subcell data: the state of uploaded subcell averages
 };
-int limiter_kernels(int pde, int dim, int N, int prec, int guess, LimKernels *out, const char **why);
+int limiter_kernels(int pde, int dim, int N, int prec, int guess, bool keep, LimKernels *out, const char **why);
 
 }  // namespace aderdg

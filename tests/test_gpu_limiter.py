@@ -542,6 +542,47 @@ def test_kept_subcell_data_refusals():
         with pytest.raises(A.AderdgError) as ei:
             s.set_subcell_state(np.ones((16, 49, 4)))
         assert ei.value.code == A.ADERDG_E_INVAL
+        with pytest.raises(A.AderdgError) as ei:
+            s.get_subcell_state()
+        assert ei.value.code == A.ADERDG_E_INVAL
+
+
+@pytest.mark.parametrize("how", ["upload", "explicit_corrector"])
+def test_kept_subcell_data_dropped_when_the_state_changes_otherwise(how):
+    """Kept subcell averages belong to the state the limiter produced: a
+    nodal upload (here of that same state), or an explicit corrector call,
+    drops them, and the next limited step matches the oracle's step with
+    nothing kept (the tanh blast: its troubled elements' kept averages differ
+    from the averages of their reconstruction, so stale data would show)."""
+    c, U = _explosion()
+    c.limiter = 2
+    s = A.Solver(2, 2, (16, 16), (0, 0), (1, 1), 3, (1.4,), limiter=2)
+    s.set_state(U)
+    kept = oracle.Kept(c)
+    Uo = U.copy()
+    for _ in range(3):
+        dt = s.step(1e30, sync_dt=True)
+        Uo, _, _ = oracle.step_limited_kept(c, Uo, kept, dt)
+    assert kept.kept.any()
+    Ug, t, _ = s.get_state()
+    if how == "upload":
+        s.set_state(Ug, t)
+    else:
+        dt = 0.25 * oracle.cfl_dt(c, Ug)
+        s.predictor(dt)
+        s.corrector(dt)
+        c0 = oracle.make_cfg(2, (16, 16), [0, 0], [1, 1], 3, oracle.PDE_EULER, [1.4])
+        Ue = oracle.step(c0, Ug, dt)
+        Ug = s.get_state()[0]
+        assert np.abs(Ug - Ue).max() <= 1e-11 * np.abs(Ue).max()
+    dt = s.step(1e30, sync_dt=True)
+    assert abs(dt - oracle.cfl_dt(c, Ug)) <= 1e-13 * dt  # the nodes' wave speeds again
+    Uo, flags_o, cnt = oracle.step_limited_kept(c, Ug, oracle.Kept(c), dt)
+    flags, _ = s.troubled()
+    np.testing.assert_array_equal(flags, flags_o)
+    assert cnt > 0
+    assert np.abs(s.get_state()[0] - Uo).max() <= 1e-11 * max(1.0, np.abs(Uo).max())
+    s.close()
 
 
 @pytest.mark.parametrize("precision", [A.ADERDG_FP64, A.ADERDG_MIXED_FP32], ids=["fp64", "mixed"])
