@@ -107,6 +107,9 @@ struct Slot {
     LimKernels lk{};
     double *u_prev = nullptr, *lim_mm = nullptr, *lim_mmc = nullptr;
     int *lim_flags = nullptr, *lim_list = nullptr;
+    double *lim_fb = nullptr;  // troubled elements' face fluxes for the coupling
+    int *lim_slot = nullptr;
+    long long lim_fb_slots = 0;
     int ctl_index = -1;
     // placement in the current group arrays (for k_cfl)
     int group = -1, member = -1;
@@ -115,7 +118,10 @@ struct Slot {
 size_t lim_bytes(const Slot &s)
 {
     const size_t ns = (size_t)s.E * s.NS * s.M;
-    return s.limiter ? a256(ns * 8) + 2 * a256((size_t)s.E * s.M * 2 * 8) + 2 * a256((size_t)s.E * 4) : 0;
+    const size_t fb = s.lim_fb_slots > 0 ? a256((size_t)s.lim_fb_slots * limiter_flux_doubles(s.dim, s.N, s.M, s.ks->ncp != 0) * 8) +
+                                               a256((size_t)s.E * 4)
+                                         : 0;
+    return s.limiter ? a256(ns * 8) + 2 * a256((size_t)s.E * s.M * 2 * 8) + 2 * a256((size_t)s.E * 4) + fb : 0;
 }
 
 size_t slot_bytes(const Slot &s)
@@ -167,6 +173,7 @@ int make_slot(const aderdg_solve_spec_t &sp, int prec, int guess, int picard, do
     }
     for (int i = 0; i < 8; ++i) s.pp.p[i] = sp.pde.p[i];
     fill_pde_consts(s.pde, s.pp);
+    s.lim_fb_slots = limiter ? limiter_flux_slots(E, s.dim, s.N, s.M, ks->ncp != 0) : 0;
     s.bytes = slot_bytes(s);
     return ADERDG_OK;
 }
@@ -299,6 +306,12 @@ public:
             s->lim_flags = reinterpret_cast<int *>(l + a256(ns * 8) + 2 * a256((size_t)s->E * s->M * 2 * 8));
             s->lim_list = reinterpret_cast<int *>(reinterpret_cast<unsigned char *>(s->lim_flags) +
                                                   a256((size_t)s->E * 4));
+            if (s->lim_fb_slots > 0) {
+                unsigned char *f = reinterpret_cast<unsigned char *>(s->lim_list) + a256((size_t)s->E * 4);
+                s->lim_fb = reinterpret_cast<double *>(f);
+                s->lim_slot = reinterpret_cast<int *>(
+                    f + a256((size_t)s->lim_fb_slots * limiter_flux_doubles(s->dim, s->N, s->M, s->ks->ncp != 0) * 8));
+            }
             CKB(cudaMemsetAsync(s->lim_flags, 0, sizeof(int) * (size_t)s->E, st));
         }
         s->ctl_index = ctl_free.back();
@@ -389,6 +402,9 @@ public:
                 d.lim_mmc = s->lim_mmc;
                 d.lim_flags = s->lim_flags;
                 d.lim_list = s->lim_list;
+                d.lim_fb = s->lim_fb;
+                d.lim_slot = s->lim_slot;
+                d.lim_fb_slots = s->lim_fb_slots;
             }
             g.ntp = tp;
             g.ntc = tc;

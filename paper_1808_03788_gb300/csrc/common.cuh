@@ -171,6 +171,16 @@ struct SolveDesc {
     double *lim_sub;
     double *lim_subn;
     int *lim_kept;
+    // the subcell fluxes the subcell scheme forms on the element faces of the
+    // first lim_fb_slots troubled elements of the step, for the coupling of
+    // their unlimited neighbours ([slot][d][side][line][FB], slot = the index
+    // in lim_list, FB = M values, or 2M for a non-conservative system: the
+    // fluctuation the neighbour receives and the neighbour's own subcell state
+    // at the face); lim_slot[e]: the slot of troubled element e.  NULL / 0:
+    // the coupling forms them itself
+    double *lim_fb;
+    int *lim_slot;
+    long long lim_fb_slots;
     // domain decomposition (a block of a partitioned mesh, see partition.cu):
     // elist: the predictor's elements, E indices into the block (its
     // boundary or its interior elements); NULL: elements 0 .. E-1.

@@ -49,6 +49,9 @@ struct LimCfg {
     // ghost layers, increments, two projection buffers, face fluxes
     static constexpr size_t DOUBLES = OPS + round_up(NS * M, 2) + 3 * (size_t)NSUB * M + GHOST + 2 * TMP + FACES;
     static constexpr size_t BYTES = sizeof(double) * DOUBLES;
+    // doubles per line of a stored face record, and per troubled element
+    static constexpr int FB = PDE::NCP ? 2 * M : M;
+    static constexpr size_t FB_SLOT = (size_t)2 * DIM * NLINE * FB;
     static constexpr bool FITS = BYTES <= 227 * 1024;
     static constexpr bool OK = FITS;
 };
@@ -646,7 +649,10 @@ __global__ void __launch_bounds__(128) k_lim_detect(const KParams P)
                     if (bad) {
                         // at most E entries a step (the reset after the limiter empties it)
                         const unsigned k = atomicAdd(&S.ctl->lim_count, 1u);
-                        if (k < (unsigned)S.E) S.lim_list[k] = (int)e;
+                        if (k < (unsigned)S.E) {
+                            S.lim_list[k] = (int)e;
+                            if (S.lim_slot) S.lim_slot[e] = (int)k;
+                        }
                     }
                 }
                 __syncwarp();
@@ -1054,7 +1060,10 @@ __global__ void __launch_bounds__(128) k_lim_detect32(const KParams P)
                     if (bad) {
                         // at most E entries a step (the reset after the limiter empties it)
                         const unsigned k = atomicAdd(&S.ctl->lim_count, 1u);
-                        if (k < (unsigned)S.E) S.lim_list[k] = (int)e;
+                        if (k < (unsigned)S.E) {
+                            S.lim_list[k] = (int)e;
+                            if (S.lim_slot) S.lim_slot[e] = (int)k;
+                        }
                     }
                 }
                 __syncwarp();
@@ -1113,15 +1122,35 @@ __global__ void __launch_bounds__(128) k_lim_fv(const KParams P)
                     // every face of this direction (face f between cells f-1 and f):
                     // the flux, or the two fluctuations [lower | upper]
                     constexpr int FW = PDE::NCP ? 2 * M : M;
+                    // the element's own boundary faces (f = 0, S) are kept for the
+                    // coupling of its unlimited neighbours when the solve has a slot
+                    double *keep = S.lim_fb && (long long)k < S.lim_fb_slots
+                                       ? S.lim_fb + (long long)k * L::FB_SLOT + (size_t)d * 2 * L::NLINE * L::FB
+                                       : nullptr;
                     for (int it = threadIdx.x; it < (S_ + 1) * L::NLINE; it += blockDim.x) {
                         const int f = it % (S_ + 1), l = it / (S_ + 1);
                         double *fo = sm.fb + (size_t)it * FW;
-                        if constexpr (PDE::NCP)
+                        // the record of a boundary face: [side][line][FB]
+                        double *rec = keep && (f == 0 || f == S_) ? keep + ((size_t)(f ? 1 : 0) * L::NLINE + l) * L::FB
+                                                                  : nullptr;
+                        if constexpr (PDE::NCP) {
+                            // the neighbour's own state at the face: the lower cell's
+                            // evolved value at f = 0, the upper one's at f = S
                             lim_face_nc<PDE, DIM>(P.pde, cell(l, f - 2), cell(l, f - 1), cell(l, f), cell(l, f + 1),
-                                                  d, r, dt, fo, fo + M, nullptr, nullptr);
-                        else
+                                                  d, r, dt, fo, fo + M, rec && f == 0 ? rec + M : nullptr,
+                                                  rec && f == S_ ? rec + M : nullptr);
+                            if (rec) {
+#pragma unroll
+                                for (int v = 0; v < M; ++v) rec[v] = f == 0 ? fo[v] : fo[M + v];
+                            }
+                        } else {
                             lim_face<PDE, DIM>(P.pde, cell(l, f - 2), cell(l, f - 1), cell(l, f), cell(l, f + 1), d, r,
                                                dt, fo);
+                            if (rec) {
+#pragma unroll
+                                for (int v = 0; v < M; ++v) rec[v] = fo[v];
+                            }
+                        }
                     }
                     __syncthreads();
                     for (int it = threadIdx.x; it < S_ * L::NLINE; it += blockDim.x) {
@@ -1225,20 +1254,36 @@ __global__ void __launch_bounds__(128) k_lim_couple(const KParams P)
                     for (int side = 0; side < 2; ++side)
                         any |= S.lim_flags[neighbour_of(S, (int)e, d, side ? 1 : -1)];
                 if (!any) continue;  // uniform over the CTA
-                lim_un_averages<L, DIM>(S, e, sm, sm.avg);
+                bool own = false;  // this element's subcell averages in sm.avg
 #pragma unroll 1
                 for (int d = 0; d < DIM; ++d)
 #pragma unroll 1
                     for (int side = 0; side < 2; ++side) {
                         const long long nb = neighbour_of(S, (int)e, d, side ? 1 : -1);
                         if (!S.lim_flags[nb]) continue;
-                        lim_un_averages<L, DIM>(S, nb, sm, sm.nb);
+                        // the troubled neighbour's subcell fluxes on this face as its
+                        // subcell scheme formed them (its face toward this element:
+                        // side 0 when this element is below it), or, beyond the
+                        // solve's slots, formed here from the same subcell averages
+                        // with the same function
+                        const long long slot = S.lim_fb ? (long long)S.lim_slot[nb] : S.lim_fb_slots;
+                        const double *stored =
+                            slot < S.lim_fb_slots
+                                ? S.lim_fb + slot * (long long)L::FB_SLOT + ((size_t)d * 2 + (side ? 0 : 1)) * L::NLINE * L::FB
+                                : nullptr;  // uniform over the CTA
                         // the face's four cell layers: lower element's last two,
                         // upper element's first two
                         double *gl = sm.ghost, *gu = sm.ghost + 2 * L::NLINE * M;
-                        lim_layers<L, DIM>(side ? sm.avg : sm.nb, d, 1, gl);
-                        lim_layers<L, DIM>(side ? sm.nb : sm.avg, d, 0, gu);
-                        __syncthreads();
+                        if (!stored) {
+                            if (!own) {
+                                lim_un_averages<L, DIM>(S, e, sm, sm.avg);
+                                own = true;
+                            }
+                            lim_un_averages<L, DIM>(S, nb, sm, sm.nb);
+                            lim_layers<L, DIM>(side ? sm.avg : sm.nb, d, 1, gl);
+                            lim_layers<L, DIM>(side ? sm.nb : sm.avg, d, 0, gu);
+                            __syncthreads();
+                        }
                         const double r = dt * S.inv_dx[d] * S_;
                         const long long el = side ? e : nb, eu = side ? nb : e;
                         // per face node: projected subcell flux minus the DG flux
@@ -1248,6 +1293,11 @@ __global__ void __launch_bounds__(128) k_lim_couple(const KParams P)
                             double *Fl = sm.dq, *dF = sm.dq + (size_t)L::NLINE * 2 * M;  // dF: [p][v]
                             for (int l = threadIdx.x; l < L::NLINE; l += blockDim.x) {
                                 double *o = Fl + (size_t)l * 2 * M;
+                                if (stored) {
+#pragma unroll
+                                    for (int v = 0; v < 2 * M; ++v) o[v] = stored[(size_t)l * 2 * M + v];
+                                    continue;
+                                }
                                 const double *a0 = gl + (size_t)l * M, *a1 = gl + (size_t)(L::NLINE + l) * M;
                                 const double *b0 = gu + (size_t)l * M, *b1 = gu + (size_t)(L::NLINE + l) * M;
                                 if (side)  // this element is the lower one
@@ -1347,10 +1397,16 @@ __global__ void __launch_bounds__(128) k_lim_couple(const KParams P)
                             __syncthreads();
                         } else if constexpr (sizeof(T) == 4) {
                             double *Fl = sm.dq;  // subcell fluxes on the face [line][v]
-                            for (int l = threadIdx.x; l < L::NLINE; l += blockDim.x)
-                                lim_face<PDE, DIM>(P.pde, gl + (size_t)l * M, gl + (size_t)(L::NLINE + l) * M,
-                                                   gu + (size_t)l * M, gu + (size_t)(L::NLINE + l) * M, d, r, dt,
-                                                   Fl + (size_t)l * M);
+                            for (int l = threadIdx.x; l < L::NLINE; l += blockDim.x) {
+                                if (stored) {
+#pragma unroll
+                                    for (int v = 0; v < M; ++v) Fl[(size_t)l * M + v] = stored[(size_t)l * M + v];
+                                } else {
+                                    lim_face<PDE, DIM>(P.pde, gl + (size_t)l * M, gl + (size_t)(L::NLINE + l) * M,
+                                                       gu + (size_t)l * M, gu + (size_t)(L::NLINE + l) * M, d, r, dt,
+                                                       Fl + (size_t)l * M);
+                                }
+                            }
                             __syncthreads();
                             double *dF = sm.dq + (size_t)L::NLINE * M;  // [p][v]
                             const T *trf = reinterpret_cast<const T *>(S.tr);
@@ -1412,10 +1468,16 @@ __global__ void __launch_bounds__(128) k_lim_couple(const KParams P)
                             __syncthreads();
                         } else {
                             double *Fl = sm.dq;  // subcell fluxes on the face [line][v]
-                            for (int l = threadIdx.x; l < L::NLINE; l += blockDim.x)
-                                lim_face<PDE, DIM>(P.pde, gl + (size_t)l * M, gl + (size_t)(L::NLINE + l) * M,
-                                                   gu + (size_t)l * M, gu + (size_t)(L::NLINE + l) * M, d, r, dt,
-                                                   Fl + (size_t)l * M);
+                            for (int l = threadIdx.x; l < L::NLINE; l += blockDim.x) {
+                                if (stored) {
+#pragma unroll
+                                    for (int v = 0; v < M; ++v) Fl[(size_t)l * M + v] = stored[(size_t)l * M + v];
+                                } else {
+                                    lim_face<PDE, DIM>(P.pde, gl + (size_t)l * M, gl + (size_t)(L::NLINE + l) * M,
+                                                       gu + (size_t)l * M, gu + (size_t)(L::NLINE + l) * M, d, r, dt,
+                                                       Fl + (size_t)l * M);
+                                }
+                            }
                             __syncthreads();
                             double *dF = sm.dq + (size_t)L::NLINE * M;  // [p][v]
                             for (int i = threadIdx.x; i < NF * M; i += blockDim.x) {

@@ -173,6 +173,9 @@ struct aderdg_s {
     double *lim_sub = nullptr;  // kept: subcell data of u^n [E][NSUB][M]
     double *lim_subn = nullptr; // kept: new averages of the step's troubled elements [E][NSUB][M]
     int *lim_kept = nullptr;    // kept: lim_sub[e] holds e's subcell data of u^n [E]
+    double *lim_fb = nullptr;   // limiter: troubled elements' face fluxes for the coupling
+    int *lim_slot = nullptr;    // limiter: their slots [E]
+    long long lim_fb_slots = 0;
     double *host_pinned = nullptr;
     KParams kp{};
     Basis basis{};
@@ -482,6 +485,14 @@ int aderdg_create(const aderdg_mesh_t *mesh, int N, int nVar, const aderdg_pde_t
         h->lim_list = (int *)dev_alloc(h, sizeof(int) * (size_t)E);
     }
     h->NSUB = ipow(2 * N + 1, h->dim);
+    if (h->limiter) {
+        h->lim_fb_slots = limiter_flux_slots(E, h->dim, N, m, ks->ncp != 0);
+        if (h->lim_fb_slots > 0) {
+            h->lim_fb = (double *)dev_alloc(
+                h, sizeof(double) * (size_t)h->lim_fb_slots * limiter_flux_doubles(h->dim, N, m, ks->ncp != 0));
+            h->lim_slot = (int *)dev_alloc(h, sizeof(int) * (size_t)E);
+        }
+    }
     if (h->lim_keep) {
         h->lim_sub = (double *)dev_alloc(h, sizeof(double) * (size_t)E * h->NSUB * m);
         h->lim_subn = (double *)dev_alloc(h, sizeof(double) * (size_t)E * h->NSUB * m);
@@ -490,7 +501,8 @@ int aderdg_create(const aderdg_mesh_t *mesh, int N, int nVar, const aderdg_pde_t
     if (!h->u || !h->V || !h->tr || !h->ctl || !h->scratch || !h->d_desc || (ks->rf > 0 && !h->ref) ||
         (h->guess == ADERDG_GUESS_EXTRAP && !h->qprev) ||
         (h->limiter && (!h->u_prev || !h->lim_mm || !h->lim_mmc || !h->lim_flags || !h->lim_list)) ||
-        (h->lim_keep && (!h->lim_sub || !h->lim_subn || !h->lim_kept))) {
+        (h->lim_keep && (!h->lim_sub || !h->lim_subn || !h->lim_kept)) ||
+        (h->lim_fb_slots > 0 && (!h->lim_fb || !h->lim_slot))) {
         aderdg_destroy(h);
         return fail(ADERDG_E_NOMEM, "device allocation failed");
     }
@@ -534,6 +546,9 @@ int aderdg_create(const aderdg_mesh_t *mesh, int N, int nVar, const aderdg_pde_t
     sd.lim_sub = h->lim_sub;
     sd.lim_subn = h->lim_subn;
     sd.lim_kept = h->lim_kept;
+    sd.lim_fb = h->lim_fb;
+    sd.lim_slot = h->lim_slot;
+    sd.lim_fb_slots = h->lim_fb_slots;
     KParams &kp = h->kp;
     std::memset(&kp, 0, sizeof(kp));
     kp.solves = h->d_desc;
@@ -575,6 +590,8 @@ int aderdg_destroy(aderdg_t *h)
     dev_free(h, h->lim_sub);
     dev_free(h, h->lim_subn);
     dev_free(h, h->lim_kept);
+    dev_free(h, h->lim_fb);
+    dev_free(h, h->lim_slot);
     dev_free(h, h->V);
     dev_free(h, h->tr);
     dev_free(h, h->ctl);

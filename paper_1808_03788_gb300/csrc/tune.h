@@ -2,6 +2,7 @@
 #pragma once
 
 #include <algorithm>
+#include <cstdlib>
 #include "common.cuh"
 
 namespace aderdg {
@@ -45,5 +46,28 @@ struct LimKernels {
     void (*init)(KParams);  // kept subcell data: the state of uploaded subcell averages
 };
 int limiter_kernels(int pde, int dim, int N, int prec, int guess, bool keep, LimKernels *out, const char **why);
+
+// Doubles the limiter keeps per troubled element for its neighbours'
+// coupling (SolveDesc::lim_fb: the subcell fluxes of its 2d faces), and the
+// number of such slots of a solve of E elements: all elements where that
+// takes at most 256 MB, else as many as fit; the environment variable
+// ADERDG_LIMITER_FLUX_SLOTS lowers the count (0: none).  The coupling forms
+// the fluxes of troubled elements beyond the slots itself.
+inline long long limiter_flux_doubles(int dim, int N, int m, bool ncp)
+{
+    long long nline = 1;
+    for (int k = 0; k < dim - 1; ++k) nline *= 2 * N + 1;
+    return 2LL * dim * nline * (ncp ? 2 * m : m);
+}
+inline long long limiter_flux_slots(long long E, int dim, int N, int m, bool ncp)
+{
+    const long long per = limiter_flux_doubles(dim, N, m, ncp) * 8;
+    long long slots = std::min<long long>(E, std::max<long long>(1, (256LL << 20) / per));
+    if (const char *env = std::getenv("ADERDG_LIMITER_FLUX_SLOTS")) {
+        const long long v = std::atoll(env);
+        if (v >= 0) slots = std::min(slots, v);
+    }
+    return slots;
+}
 
 }  // namespace aderdg

@@ -641,3 +641,41 @@ def test_kept_mode_on_other_systems_matches_oracle(case):
                 sub = s.get_subcell_state()[flags == 1]
                 assert np.abs(sub - kept.sub[flags == 1]).max() <= 1e-11 * max(1.0, np.abs(kept.sub).max())
     assert seen > 0
+
+
+@pytest.mark.parametrize("case", ["blast", "blast_mixed", "inclusion", "sharp_kept"])
+def test_coupling_from_stored_and_formed_face_fluxes_agree(case, monkeypatch):
+    """The coupling takes a troubled neighbour's face fluxes from the
+    subcell scheme's stored records, or, for troubled elements beyond the
+    solve's slots (ADERDG_LIMITER_FLUX_SLOTS lowers their number), forms
+    them itself from the same subcell averages with the same function: the
+    runs agree bit for bit, states and troubled sets."""
+    def run(slots):
+        if slots is None:
+            monkeypatch.delenv("ADERDG_LIMITER_FLUX_SLOTS", raising=False)
+        else:
+            monkeypatch.setenv("ADERDG_LIMITER_FLUX_SLOTS", str(slots))
+        if case == "sharp_kept":
+            c, avg, s = _sharp_blast(2, 12, 3)
+            s.set_subcell_state(avg)
+        else:
+            spec, U = _inclusion2d((12, 12), 3) if case == "inclusion" else _blast2d((16, 16), 3)
+            prec = A.ADERDG_MIXED_FP32 if case.endswith("mixed") else A.ADERDG_FP64
+            s = A.Solver(*spec, limiter=True, precision=prec)
+            s.set_state(U)
+        flags, seen = [], 0
+        for _ in range(6):
+            s.step(1e30)
+            f, cnt = s.troubled()
+            flags.append(f)
+            seen = max(seen, cnt)
+        U1 = s.get_state()[0]
+        s.close()
+        return U1, flags, seen
+    Ua, fa, seen = run(None)
+    assert seen > 3
+    for slots in (3, 0):
+        Ub, fb, _ = run(slots)
+        np.testing.assert_array_equal(Ua, Ub)
+        for a, b in zip(fa, fb):
+            np.testing.assert_array_equal(a, b)
