@@ -1110,8 +1110,10 @@ __global__ void __launch_bounds__(128) k_lim_fv(const KParams P)
                 double *ctr = sm.nb;
                 for (int i = threadIdx.x; i < L::NSUB * M; i += blockDim.x) sm.dq[i] = ctr[i] = 0.0;
                 __syncthreads();
-#pragma unroll 1
-                for (int d = 0; d < DIM; ++d) {
+                // one direction at a time, d a compile-time constant (the fluxes
+                // of the other directions are then never formed)
+                auto direction = [&](auto dc) {
+                    constexpr int d = decltype(dc)::value;
                     const double r = dt * S.inv_dx[d] * S_;  // dt / subcell width
                     // cell i of line l along d: ghost layers below 0 and from S on
                     auto cell = [&](int l, int i) -> const double * {
@@ -1187,7 +1189,10 @@ __global__ void __launch_bounds__(128) k_lim_fv(const KParams P)
                         }
                     }
                     __syncthreads();
-                }
+                };
+                direction(std::integral_constant<int, 0>{});
+                if constexpr (DIM > 1) direction(std::integral_constant<int, 1>{});
+                if constexpr (DIM > 2) direction(std::integral_constant<int, 2>{});
                 if constexpr (PDE::HAS_SRC) {
                     // the source at the half-step centre of all directions
                     for (int a = threadIdx.x; a < L::NSUB; a += blockDim.x) {
