@@ -110,14 +110,15 @@ extern "C" {
  *          N <= 4: the classical fourth-order method (k2 = L(u + dt k1/2),
  *          k3 = L(u + dt k2/2), k4 = L(u + dt k3)) with the cubics
  *          b1 = th - 3th^2/2 + 2th^3/3, b2 = b3 = th^2 - 2th^3/3,
- *          b4 = -th^2/2 + 2th^3/3 (k = 3).  N >= 5: a six-stage scheme
- *          with quartic weights (k = 4: degree N - 1 at N = 5, where one
- *          Picard iteration suffices).
+ *          b4 = -th^2/2 + 2th^3/3 (k = 3).  N = 5: a six-stage scheme
+ *          with quartic weights (k = 4); N >= 6: an eleven-stage scheme
+ *          with quintic weights (k = 5) -- degree N - 1 at N = 5 and 6,
+ *          where one Picard iteration suffices.
  * with tau = t - t^n and L(w) = -div F(w), the element-local nodal
  * derivative of the flux (plus -B(w) grad w + S(w) where the PDE has
  * them).  The default Picard count after a guess of degree k in time is
  * max(1, N + 1 - k): N+1 for TRIVIAL, N for ORDER2, N-1 for ORDER3, N-2
- * (N <= 4) or N-3 (N >= 5) for CERK (the paper notes N - k iterations
+ * (N <= 4), N-3 (N = 5) or N-4 (N >= 6) for CERK (the paper notes N - k iterations
  * suffice), and 2 for EXTRAP (degree N). */
 #define ADERDG_GUESS_TRIVIAL 0
 #define ADERDG_GUESS_ORDER2 1
