@@ -216,7 +216,16 @@ typedef struct {
                                    (aderdg_set_subcell_state).  Handles
                                    only: aderdg_batch_create returns
                                    ADERDG_E_UNSUPPORTED.  Other values:
-                                   ADERDG_E_INVAL */
+                                   ADERDG_E_INVAL.
+                                   With either mode the subcell scheme keeps
+                                   the face fluxes of the troubled elements
+                                   for their neighbours' coupling: up to 256
+                                   MB per solve, fewer if the environment
+                                   variable ADERDG_LIMITER_FLUX_SLOTS (read
+                                   when the handle or batch is created) sets
+                                   a lower number of elements; the coupling
+                                   forms the others' fluxes itself, with the
+                                   same results */
 } aderdg_config_t;
 
 typedef struct aderdg_s aderdg_t;
