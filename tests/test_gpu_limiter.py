@@ -679,3 +679,35 @@ def test_coupling_from_stored_and_formed_face_fluxes_agree(case, monkeypatch):
         np.testing.assert_array_equal(Ua, Ub)
         for a, b in zip(fa, fb):
             np.testing.assert_array_equal(a, b)
+
+
+def test_limited_batch_with_few_flux_slots_equals_the_default(monkeypatch):
+    """Batch solves keep the troubled elements' face fluxes in slots of
+    their own; with two slots per solve (ADERDG_LIMITER_FLUX_SLOTS) the
+    coupling forms the rest itself, and every solve's states and troubled
+    sets are bitwise those of the default batch."""
+    cases = [_blast2d((16, 16), 3), _inclusion2d((10, 10), 2)]
+
+    def run(slots):
+        if slots is None:
+            monkeypatch.delenv("ADERDG_LIMITER_FLUX_SLOTS", raising=False)
+        else:
+            monkeypatch.setenv("ADERDG_LIMITER_FLUX_SLOTS", str(slots))
+        b = A.Batch([A.make_spec(*c) for c, _ in cases], limiter=True)
+        for i, (_, U) in enumerate(cases):
+            b.set_state(i, U)
+        out = []
+        for _ in range(5):
+            b.step(1e30)
+            out.append([b.troubled(i)[0] for i in range(len(cases))])
+        states = [b.get_state(i)[0] for i in range(len(cases))]
+        b.close()
+        return states, out
+    sa, fa = run(None)
+    sb, fb = run(2)
+    for a, b_ in zip(sa, sb):
+        np.testing.assert_array_equal(a, b_)
+    for ra, rb in zip(fa, fb):
+        for a, b_ in zip(ra, rb):
+            np.testing.assert_array_equal(a, b_)
+    assert any(f.sum() > 2 for r in fa for f in r)
