@@ -26,7 +26,8 @@
  *     finite-volume step of the troubled elements on (2N+1)^d subcells,
  *     least-squares reconstruction of the DG polynomial, and the matching
  *     face fluxes in the unlimited neighbours (readings R25-R29; with
- *     non-conservative products and sources, eq. pde.nc.fv)
+ *     non-conservative products and sources, eq. pde.nc.fv), optionally
+ *     with the limited elements' subcell averages kept between steps (R35)
  *   - PDEs: linear advection with an optional linear reaction source
  *     S = -kappa q, Euler (Sec. 3.1, eq. euler, ideal gas), the
  *     velocity-stress linear elasticity system obtained from Sec. 3.2 with
@@ -90,6 +91,12 @@
  *      integral J from its own DG trace to its own subcell state at that
  *      subcell face (with B the Jacobian of a flux this is R27: the flux
  *      difference between the two states of its own side)
+ *   R35 kept subcell data (limiter mode 2): for an element the step that
+ *      produced u^n limited, the subcell data at t^n (eq. subcellaverage)
+ *      are the averages its subcell scheme produced, not those of their
+ *      least-squares reconstruction; they enter the bounds, the subcell
+ *      scheme and the coupling, and its CFL wave speeds come from them; a
+ *      state may be given as the subcell averages of every element
  *
  * Layout: u[e][s][v] with v fastest, then x, y, z (s = sx + n*sy + n^2*sz);
  * space-time qhat[t][s][v] with time slowest (the AoS layout of Sec. 2.2).

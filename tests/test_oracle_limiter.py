@@ -491,3 +491,24 @@ def test_sharp_blast_with_kept_subcell_data_keeps_symmetry_and_mass():
     Eu = U.reshape(C, C, n, n, 4)  # [ey, ex, sy, sx, v]
     mirror = Eu.transpose(1, 0, 3, 2, 4)[..., [0, 2, 1, 3]]
     assert np.abs(Eu - mirror).max() < 1e-12
+
+
+def test_subcell_means_layout_and_linear_fields():
+    """The subcell-average input generator: for a linear field the midpoint
+    samples average to the field at the subcell centre, in the layout
+    [element (x fastest)][subcell (x fastest)][variable]; a constant field
+    gives the constant."""
+    cells, lo, hi, N = (3, 2), (0.5, -1.0), (2.0, 1.0), 2
+    S = 2 * N + 1
+    field = lambda X: np.stack([1.0 + 2.0 * X[..., 0] + 3.0 * X[..., 1], 0 * X[..., 0] + 7.0], axis=-1)
+    avg = inputs.subcell_means(field, cells, lo, hi, N, k=3)
+    assert avg.shape == (6, S * S, 2)
+    h = [(hi[d] - lo[d]) / (cells[d] * S) for d in range(2)]
+    for e in range(6):
+        ex, ey = e % cells[0], e // cells[0]
+        for a in range(S * S):
+            ax, ay = a % S, a // S
+            x = lo[0] + (ex * S + ax + 0.5) * h[0]
+            y = lo[1] + (ey * S + ay + 0.5) * h[1]
+            assert abs(avg[e, a, 0] - (1.0 + 2.0 * x + 3.0 * y)) < 1e-13
+            assert avg[e, a, 1] == 7.0
