@@ -512,3 +512,23 @@ def test_subcell_means_layout_and_linear_fields():
             y = lo[1] + (ey * S + ay + 0.5) * h[1]
             assert abs(avg[e, a, 0] - (1.0 + 2.0 * x + 3.0 * y)) < 1e-13
             assert avg[e, a, 1] == 7.0
+
+
+def test_kept_run_equals_kept_steps():
+    """The oracle's CFL time loop with kept subcell data is its kept-data
+    step repeated with the kept-data CFL step (the reference the GPU runs
+    are compared with step by step)."""
+    C, N = 8, 3
+    c = oracle.make_cfg(2, (C, C), [0, 0], [1, 1], N, oracle.PDE_EULER, [1.4], limiter=2)
+    avg = inputs.subcell_means(inputs.euler_sharp_blast((0.5, 0.5), 0.25), (C, C), (0.0, 0.0), (1.0, 1.0), N, k=4)
+    U0, k0 = oracle.subcell_init(c, avg)
+    Ur, t, steps, hist = oracle.run_kept(c, U0, oracle.Kept(c, k0.sub, k0.kept), 0.02)
+    U, kept = U0.copy(), oracle.Kept(c, k0.sub, k0.kept)
+    tt = 0.0
+    for k in range(steps):
+        dt = min(oracle.cfl_dt_kept(c, U, kept), 0.02 - tt)
+        assert dt == hist[k]
+        U, _, _ = oracle.step_limited_kept(c, U, kept, dt)
+        tt += dt
+    assert steps > 2 and t == 0.02
+    np.testing.assert_array_equal(U, Ur)
