@@ -711,3 +711,36 @@ def test_limited_batch_with_few_flux_slots_equals_the_default(monkeypatch):
         for a, b_ in zip(ra, rb):
             np.testing.assert_array_equal(a, b_)
     assert any(f.sum() > 2 for r in fa for f in r)
+
+
+def test_sedov_blast_matches_oracle():
+    """The Sedov blast (pressure 1e-14 around a disk holding the energy
+    0.979264, given as subcell averages; kept subcell data): 30 steps against
+    the oracle's kept-data steps, troubled sets equal, states within the
+    FP64 tolerance, pressures of the kept averages positive."""
+    from paper_1808_03788_gb300 import inputs
+    C, N, L = 20, 3, 1.2
+    c = oracle.make_cfg(2, (C, C), [-L, -L], [L, L], N, oracle.PDE_EULER, [1.4], limiter=2)
+    h = 2 * L / (C * (2 * N + 1))
+    r0, E0 = 2.5 * h, 0.979264
+
+    def field(X):
+        r = np.sqrt(X[..., 0] ** 2 + X[..., 1] ** 2)
+        return np.stack([np.ones_like(r), 0 * r, 0 * r, np.where(r < r0, E0 / (np.pi * r0 ** 2), 1e-14 / 0.4)],
+                        axis=-1)
+
+    avg = inputs.subcell_means(field, (C, C), (-L, -L), (L, L), N, k=8)
+    Uo, kept = oracle.subcell_init(c, avg)
+    with A.Solver(2, 2, (C, C), (-L, -L), (L, L), N, (1.4,), limiter=2) as s:
+        s.set_subcell_state(avg)
+        for _ in range(30):
+            dt = s.step(1e30, sync_dt=True)
+            assert abs(dt - oracle.cfl_dt_kept(c, Uo, kept)) <= 1e-12 * dt
+            Uo, flags_o, cnt = oracle.step_limited_kept(c, Uo, kept, dt)
+            flags, _ = s.troubled()
+            np.testing.assert_array_equal(flags, flags_o)
+            assert cnt > 0
+            Ug = s.get_state()[0]
+            assert np.abs(Ug - Uo).max() <= 1e-11 * np.abs(Uo).max()
+        ks = s.get_subcell_state()[flags == 1]
+        assert (0.4 * (ks[..., 3] - 0.5 * (ks[..., 1] ** 2 + ks[..., 2] ** 2) / ks[..., 0])).min() > 0
